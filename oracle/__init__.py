@@ -1,0 +1,234 @@
+"""FP64 CPU oracle for Galerkin assembly (TEST INFRASTRUCTURE ONLY).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The GPU library never calls it, and it
+shares no code, header or constant with the GPU library.
+
+* ``tg_oracle.cpp`` — the C++ scatter-add into a dictionary of keys (DOK),
+  Eq. (scatter_add) with local matrices from Eq. (matlclquad); the load
+  vector; analytic gradients; vector P1 elasticity (Hooke's law, SM B.1).
+* ``exact.py`` — exact rational element matrices by monomial integration
+  (independent of quadrature), used to pin the C++ oracle on tiny meshes.
+* ``solve.py`` — conjugate gradients on the Dirichlet-condensed system.
+
+Parity of every function here is pinned by ``tests/test_oracle_*.py``
+against closed forms, invariants, exact integration and finite differences.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tg_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libtg_oracle.so")
+
+P1_TRI, P2_TRI, P1_TET, P1_TET_VEC3 = 0, 1, 2, 3
+PER_ELEMENT, PER_QP, PER_NODE, CONSTANT = 0, 1, 2, 3
+NV = {P1_TRI: 3, P2_TRI: 6, P1_TET: 4, P1_TET_VEC3: 4}
+DIM = {P1_TRI: 2, P2_TRI: 2, P1_TET: 3, P1_TET_VEC3: 3}
+NQ = {P1_TRI: 3, P2_TRI: 6, P1_TET: 4, P1_TET_VEC3: 4}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (FP64, no contraction, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+                        _SRC, "-o", tmp], check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        d, i64, i32, vp = C.c_double, C.c_int64, C.c_int, C.c_void_p
+        L.orc_quadrature.restype = i32
+        L.orc_quadrature.argtypes = [i32, vp, vp]
+        L.orc_basis.argtypes = [i32, vp, vp, vp]
+        L.orc_element_matrix.argtypes = [i32, vp, vp, d, vp]
+        L.orc_elastic_element_matrix.argtypes = [vp, vp, vp, vp]
+        L.orc_assemble_bilinear.restype = vp
+        L.orc_assemble_bilinear.argtypes = [i32, i64, i64, vp, vp, vp, i32, d, vp]
+        L.orc_assemble_elasticity.restype = vp
+        L.orc_assemble_elasticity.argtypes = [i64, i64, vp, vp, vp, vp, i32, vp]
+        L.orc_csr_nrows.restype = i64
+        L.orc_csr_nrows.argtypes = [vp]
+        L.orc_csr_nnz.restype = i64
+        L.orc_csr_nnz.argtypes = [vp]
+        L.orc_csr_export.argtypes = [vp, vp, vp, vp]
+        L.orc_csr_free.argtypes = [vp]
+        L.orc_assemble_load.argtypes = [i32, i64, i64, vp, vp, vp, i32, i32, vp]
+        L.orc_assemble_backward.restype = i32
+        L.orc_assemble_backward.argtypes = [i32, i64, i64, vp, vp, vp, i32, d, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_elasticity_backward.restype = i32
+        L.orc_elasticity_backward.argtypes = [i64, i64, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+class CSR:
+    """CSR export of the oracle's DOK (int64 row pointers, int32 columns)."""
+
+    def __init__(self, row_ptr, col, val):
+        self.row_ptr, self.col, self.val = row_ptr, col, val
+
+    @property
+    def nnz(self):
+        return int(self.col.shape[0])
+
+    @property
+    def n_rows(self):
+        return int(self.row_ptr.shape[0] - 1)
+
+    def to_scipy(self, n_cols=None):
+        import scipy.sparse as sp
+        n = self.n_rows
+        return sp.csr_matrix((self.val, self.col, self.row_ptr), shape=(n, n_cols or n))
+
+    def rows_of(self):
+        return np.repeat(np.arange(self.n_rows), np.diff(self.row_ptr))
+
+
+def _export(h) -> CSR:
+    L = lib()
+    n = L.orc_csr_nrows(h)
+    nnz = L.orc_csr_nnz(h)
+    rp = np.empty(n + 1, np.int64)
+    col = np.empty(nnz, np.int32)
+    val = np.empty(nnz, np.float64)
+    L.orc_csr_export(h, _p(rp), _p(col), _p(val))
+    L.orc_csr_free(h)
+    return CSR(rp, col, val)
+
+
+def quadrature(el: int):
+    w = np.zeros(8)
+    x = np.zeros(24)
+    nq = lib().orc_quadrature(el, _p(w), _p(x))
+    d = DIM[el]
+    return w[:nq].copy(), x[: nq * d].reshape(nq, d).copy()
+
+
+def basis(el: int, x):
+    x = _f64(x)
+    phi = np.zeros(6)
+    dphi = np.zeros(18)
+    lib().orc_basis(el, _p(x), _p(phi), _p(dphi))
+    nv = NV[el]
+    return phi[:nv].copy(), dphi[: nv * DIM[el]].reshape(nv, DIM[el]).copy()
+
+
+def element_matrix(el: int, X, kq, c: float = 0.0):
+    X = _f64(X)
+    kq = _f64(np.broadcast_to(np.asarray(kq, dtype=np.float64), (NQ[el],)))
+    nv = NV[el]
+    K = np.zeros(nv * nv)
+    lib().orc_element_matrix(el, _p(X), _p(kq), float(c), _p(K))
+    return K.reshape(nv, nv)
+
+
+def elastic_element_matrix(X, lam, mu):
+    X = _f64(X)
+    lq = _f64(np.broadcast_to(np.asarray(lam, dtype=np.float64), (4,)))
+    mq = _f64(np.broadcast_to(np.asarray(mu, dtype=np.float64), (4,)))
+    K = np.zeros(144)
+    lib().orc_elastic_element_matrix(_p(X), _p(lq), _p(mq), _p(K))
+    return K.reshape(12, 12)
+
+
+def assemble_bilinear(el, cells, coords, kappa, kappa_layout, c=0.0, row_mask=None) -> CSR:
+    cells = _i32(cells)
+    coords = _f64(coords)
+    kappa = _f64(np.atleast_1d(kappa))
+    mask = None if row_mask is None else np.ascontiguousarray(row_mask, dtype=np.uint8)
+    h = lib().orc_assemble_bilinear(el, cells.shape[0], coords.shape[0], _p(cells), _p(coords), _p(kappa),
+                                    kappa_layout, float(c), _p(mask))
+    return _export(h)
+
+
+def assemble_elasticity(cells, coords, lam, mu, layout, row_mask=None) -> CSR:
+    cells = _i32(cells)
+    coords = _f64(coords)
+    lam = _f64(np.atleast_1d(lam))
+    mu = _f64(np.atleast_1d(mu))
+    mask = None if row_mask is None else np.ascontiguousarray(row_mask, dtype=np.uint8)
+    h = lib().orc_assemble_elasticity(cells.shape[0], coords.shape[0], _p(cells), _p(coords), _p(lam), _p(mu),
+                                      layout, _p(mask))
+    return _export(h)
+
+
+def assemble_load(el, cells, coords, f, f_layout, ncomp=1):
+    cells = _i32(cells)
+    coords = _f64(coords)
+    f = _f64(np.atleast_1d(f))
+    N = coords.shape[0]
+    F = np.zeros(N * ncomp)
+    lib().orc_assemble_load(el, cells.shape[0], N, _p(cells), _p(coords), _p(f), f_layout, ncomp, _p(F))
+    return F
+
+
+def assemble_backward(el, cells, coords, kappa, kappa_layout, c, grad_csr: CSR | None = None, lam=None, U=None):
+    """Returns (grad_kappa, grad_coords [N, d], grad_c)."""
+    cells = _i32(cells)
+    coords = _f64(coords)
+    kappa = _f64(np.atleast_1d(kappa))
+    E, N = cells.shape[0], coords.shape[0]
+    nq = NQ[el]
+    nk = E * nq if kappa_layout == PER_QP else E if kappa_layout == PER_ELEMENT else 1
+    gk = np.zeros(nk)
+    gx = np.zeros(N * DIM[el])
+    gc = np.zeros(1)
+    if grad_csr is not None:
+        rp, col, val = grad_csr.row_ptr, grad_csr.col, _f64(grad_csr.val)
+        lam_p = U_p = None
+    else:
+        rp = col = val = None
+        lam_p, U_p = _f64(lam), _f64(U)
+    lib().orc_assemble_backward(el, E, N, _p(cells), _p(coords), _p(kappa), kappa_layout, float(c), _p(rp), _p(col),
+                                _p(val), _p(lam_p), _p(U_p), _p(gk), _p(gx), _p(gc))
+    return gk, gx.reshape(N, DIM[el]), float(gc[0])
+
+
+def elasticity_backward(cells, coords, lam, mu, layout, grad_csr: CSR | None = None, lam_adj=None, U=None):
+    """Returns (grad_lam, grad_mu, grad_coords [N, 3])."""
+    cells = _i32(cells)
+    coords = _f64(coords)
+    lam = _f64(np.atleast_1d(lam))
+    mu = _f64(np.atleast_1d(mu))
+    E, N = cells.shape[0], coords.shape[0]
+    nc = E * 4 if layout == PER_QP else E
+    gl = np.zeros(nc)
+    gm = np.zeros(nc)
+    gx = np.zeros(N * 3)
+    if grad_csr is not None:
+        rp, col, val = grad_csr.row_ptr, grad_csr.col, _f64(grad_csr.val)
+        la = Up = None
+    else:
+        rp = col = val = None
+        la, Up = _f64(lam_adj), _f64(U)
+    lib().orc_elasticity_backward(E, N, _p(cells), _p(coords), _p(lam), _p(mu), layout, _p(rp), _p(col), _p(val),
+                                  _p(la), _p(Up), _p(gl), _p(gm), _p(gx))
+    return gl, gm, gx.reshape(N, 3)
