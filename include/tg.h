@@ -1,0 +1,263 @@
+/*
+ * tg.h — C ABI of the GB300 Galerkin-assembly library (libtg.so).
+ *
+ * The library computes the two stages of TensorGalerkin's assembly on one
+ * GPU: the Map (per-element local matrices and vectors by quadrature,
+ * Eq. (kloc1), Algorithm 1, concrete form Eq. (matlclquad) of SM A.2) and the
+ * Reduce (sum of the local entries into a CSR matrix and a vector over the
+ * mesh-induced sparsity graph, Algorithm 2), plus the reverse-mode gradients
+ * of the assembled values (the adjoint relations of Eq. (adj)).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Array arguments are DEVICE pointers owned by the caller, unless a
+ *   parameter says "host".  Outputs are overwritten, never accumulated
+ *   (except where a flag says so).  Element arrays are row-major:
+ *   cells[e][a], coords[node][d], kappa[e][q].
+ * - Floating-point arrays use the dtype argument (TG_F32: float,
+ *   TG_F64: double) for coordinates, coefficients and outputs alike.
+ * - Calls are asynchronous on the given stream (a cudaStream_t; NULL is the
+ *   legacy default stream) unless documented as synchronising.  Nothing
+ *   allocates or synchronises on the assembly path, so those calls may be
+ *   captured in a CUDA graph.
+ * - Host-side validation (null pointers, sizes, enum values, a pattern of
+ *   another element kind) returns an error before any GPU work.
+ *   Data-dependent problems found on the device (an index outside
+ *   [0, n_nodes), a degenerate element with |det J| ~ 0) are recorded in the
+ *   pattern's device status word and read with tg_get_device_status().
+ *   No call aborts, traps or prints.
+ * - Reference elements: the triangle {x, y >= 0, x + y <= 1} of SM A.2 and
+ *   its 3D analogue.  Quadrature: 3-point degree-2 rule for P1 triangles,
+ *   6-point degree-4 (Dunavant) rule for P2 triangles, 4-point degree-2 rule
+ *   for tetrahedra; per-point coefficient arrays follow those rules' point
+ *   order (documented in the design notes and in tg_quadrature()).
+ * - P2 triangles carry 6 nodes per element: the 3 vertices, then the edge
+ *   nodes of edges (0,1), (1,2), (2,0).  Geometry uses the vertices only
+ *   (straight-sided elements).
+ * - Vector elasticity numbers DoFs as 3 * node + component.
+ * - The CSR pattern holds every pair (i, j) of nodes sharing an element,
+ *   columns sorted ascending, structural zeros kept, int32 indices.
+ * - Determinism: for a fixed pattern every forward and backward call is
+ *   bitwise reproducible from run to run (each output is summed in a fixed
+ *   order: incident elements by increasing element index).  The only
+ *   exception is tg_assemble_bilinear_atomic, the atomicAdd comparison
+ *   variant.
+ */
+#ifndef TG_H_
+#define TG_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (identical to cudaStream_t / CUstream). */
+typedef struct CUstream_st* tg_stream;
+
+typedef enum {
+  TG_OK = 0,
+  TG_ERR_INVALID_ARG = 1,        /* null pointer, bad size or enum, mismatched pattern */
+  TG_ERR_INDEX_RANGE = 2,        /* a cell index outside [0, n_nodes) */
+  TG_ERR_DEGENERATE_ELEMENT = 3, /* repeated vertex or |det J| below the dtype's threshold */
+  TG_ERR_INDEX_OVERFLOW = 4,     /* nnz or an index would exceed 2^31 - 1 */
+  TG_ERR_OUT_OF_MEMORY = 5,      /* a device allocation inside a pattern/batch build failed */
+  TG_ERR_CUDA = 6,               /* a CUDA runtime call failed; see tg_last_error_message() */
+  TG_ERR_TIMEOUT = 7,            /* a bounded device-side wait ran out */
+  TG_ERR_UNSUPPORTED = 8         /* a limit of this implementation (e.g. row length > 255) */
+} tg_status;
+
+typedef enum {
+  TG_P1_TRI = 0,      /* linear triangle,      3 nodes, d = 2 */
+  TG_P2_TRI = 1,      /* quadratic triangle,   6 nodes, d = 2 */
+  TG_P1_TET = 2,      /* linear tetrahedron,   4 nodes, d = 3 */
+  TG_P1_TET_VEC3 = 3  /* linear tetrahedron, 3 DoF per node (elasticity), d = 3 */
+} tg_element;
+
+typedef enum { TG_F32 = 0, TG_F64 = 1 } tg_dtype;
+
+typedef enum {
+  TG_PER_ELEMENT = 0, /* one value per element:           [E]      */
+  TG_PER_QP = 1,      /* one value per quadrature point:  [E][Q]   */
+  TG_PER_NODE = 2,    /* one value per node:              [N]      */
+  TG_CONSTANT = 3     /* one value for the whole mesh:    [1]      */
+} tg_layout;
+
+typedef struct tg_pattern tg_pattern; /* opaque; owns its device buffers */
+typedef struct tg_batch tg_batch;     /* opaque; owns its device buffers */
+
+/* ------------------------------------------------------------------------
+ * Status and diagnostics
+ * ---------------------------------------------------------------------- */
+
+/* Human-readable name of a status code (static storage). */
+const char* tg_status_string(tg_status s);
+
+/* Text of the last TG_ERR_CUDA raised on the calling host thread. */
+const char* tg_last_error_message(void);
+
+/* Number of quadrature points of an element kind and, when w / xhat are
+ * non-NULL (host arrays of Q and Q*d doubles), the weights and reference
+ * points in the order per-point coefficient arrays use. */
+int32_t tg_quadrature(tg_element el, double* w, double* xhat);
+
+/* ------------------------------------------------------------------------
+ * Stage II routing: the sparsity pattern (Algorithm 2's routing matrices
+ * S_mat, S_vec and CSR indices "precomputed based solely on mesh topology").
+ * ---------------------------------------------------------------------- */
+
+/* Build the pattern of a mesh on the device.
+ *   cells     device int32 [n_elems][nv] (nv = 3, 6, 4, 4 by element kind);
+ *             copied, so the caller may free it afterwards.
+ *   n_elems   >= 0 (an empty mesh gives an empty pattern); n_nodes >= 1.
+ *   out       receives a new pattern; release it with tg_pattern_destroy().
+ * Allocates device memory and SYNCHRONISES the stream.  Index errors and
+ * repeated vertices are returned directly (TG_ERR_INDEX_RANGE,
+ * TG_ERR_DEGENERATE_ELEMENT; tg_get_device_status gives the element).
+ * Rows longer than 255 entries return TG_ERR_UNSUPPORTED. */
+tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int64_t n_nodes, tg_element el,
+                           tg_stream stream, tg_pattern** out);
+
+/* Borrowed device views of a pattern (valid until tg_pattern_destroy).
+ *   n_rows, nnz   CSR size (DoF level for TG_P1_TET_VEC3: 3N rows, 9 nnz_node)
+ *   row_ptr       int32 [n_rows + 1];  col_idx  int32 [nnz]
+ *   elem_slot     int32 [E][nv][nv]: CSR position of local entry (a, b); for
+ *                 TG_P1_TET_VEC3 the position of DoF entry (3a+0, 3b+0), the
+ *                 entry (3a+i, 3b+j) sits at elem_slot + i*3*len(g_a) + j with
+ *                 len(g_a) the node-row length (row_ptr[3g+1]-row_ptr[3g])/3.
+ *   slot_stride   nv * nv.
+ * Any output pointer may be NULL. */
+tg_status tg_pattern_info(const tg_pattern* p, int64_t* n_rows, int64_t* nnz, const int32_t** row_ptr,
+                          const int32_t** col_idx, const int32_t** elem_slot, int32_t* slot_stride);
+
+/* Shape of a pattern: element kind, element and node counts, the longest
+ * node row and the largest number of elements sharing a node. */
+tg_status tg_pattern_shape(const tg_pattern* p, tg_element* el, int64_t* n_elems, int64_t* n_nodes,
+                           int32_t* max_row_len, int32_t* max_degree);
+
+/* Read and clear the device status word of a pattern.  SYNCHRONISES the
+ * device.  Returns TG_OK or the first recorded data error; *first_bad_elem
+ * (may be NULL) gets the smallest offending element index, or -1. */
+tg_status tg_get_device_status(const tg_pattern* p, int64_t* first_bad_elem);
+
+void tg_pattern_destroy(tg_pattern* p);
+
+/* ------------------------------------------------------------------------
+ * Forward assembly: fused Map + deterministic Reduce (Eq. (matlclquad),
+ * Algorithms 1 and 2).
+ * ---------------------------------------------------------------------- */
+
+/* Scalar bilinear form a(u, v) = int kappa grad u . grad v + c u v
+ * (Eq. (matlclquad) with the mass term of SM A.1):
+ *   vals[s] = sum over elements e and local pairs (a, b) routed to slot s of
+ *             sum_q w_q |det J_e| ( kappa_eq G_qa . G_qb + c phi_a(x_q) phi_b(x_q) ).
+ *   coords      [N][d]; kappa per kappa_layout (PER_QP, PER_ELEMENT or
+ *               CONSTANT); vals_out [nnz] (node-level CSR of the pattern).
+ * Element kinds TG_P1_TRI, TG_P2_TRI, TG_P1_TET. */
+tg_status tg_assemble_bilinear(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
+                               tg_layout kappa_layout, double c, void* vals_out, tg_stream stream);
+
+/* Same result through the classic scatter-add with atomicAdd (Eq.
+ * (scatter_add)): one thread per element, atomics into vals_out after a
+ * clear.  Kept as the comparison point; summation order, hence the last
+ * bits, vary from run to run. */
+tg_status tg_assemble_bilinear_atomic(const tg_pattern* p, tg_dtype dtype, const void* coords,
+                                      const void* kappa, tg_layout kappa_layout, double c, void* vals_out,
+                                      tg_stream stream);
+
+/* Vector P1 linear elasticity, int lambda div u div v + 2 mu eps(u):eps(v)
+ * (Hooke's law, SM B.1 Benchmark II):
+ *   K[(a,i),(b,j)] = sum_q w_q |det J| ( lam_q g_ai g_bj + mu_q g_aj g_bi + mu_q delta_ij g_a . g_b ).
+ *   lam, mu     per layout (PER_ELEMENT, PER_QP or CONSTANT); vals_out [9 nnz_node]
+ *               in the DoF-level CSR.  Pattern kind TG_P1_TET_VEC3. */
+tg_status tg_assemble_elasticity(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* lam,
+                                 const void* mu, tg_layout layout, void* vals_out, tg_stream stream);
+
+/* Load vector (second line of Eq. (matlclquad)):
+ *   F[g(a) * ncomp + k] = sum_e sum_q w_q |det J_e| f_k(x_q) phi_a(x_q).
+ *   f layouts: PER_NODE [N][ncomp] (f is its finite-element interpolant),
+ *   PER_QP [E][Q][ncomp], CONSTANT [ncomp].  ncomp = 1 or 3.
+ *   F_out [N * ncomp]. */
+tg_status tg_assemble_load(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* f,
+                           tg_layout f_layout, int32_t ncomp, void* F_out, tg_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Backward (reverse mode) of the scalar bilinear assembly.
+ * For an upstream gradient W of the assembled values, either
+ *   grad_vals [nnz]  (W_ab^e = grad_vals[slot(e, a, b)], the transpose of the
+ *                     routing, S_mat^T), or
+ *   lam, U    [N]    (W_ab^e = lam[g_a] U[g_b]: the adjoint outer product
+ *                     dGamma/dK = lam U^T of Eq. (adj)) when grad_vals is NULL,
+ * computes the gradients of L = sum_s W_s vals_s:
+ *   grad_kappa  same layout as kappa (PER_QP, PER_ELEMENT or CONSTANT), or NULL;
+ *   grad_coords [N][d], or NULL;
+ *   grad_c      device scalar of dtype, or NULL.
+ * All outputs are overwritten; sums run in a fixed order (deterministic). */
+tg_status tg_assemble_backward(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
+                               tg_layout kappa_layout, double c, const void* grad_vals, const void* lam,
+                               const void* U, void* grad_kappa, void* grad_coords, void* grad_c,
+                               tg_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Support: CSR products and the conjugate-gradient solve of the condensed
+ * system (SM B.1 solver configuration; used by the adjoint of Eq. (adj)).
+ * ---------------------------------------------------------------------- */
+
+/* y = K x over the pattern's CSR (DoF level for elasticity). */
+tg_status tg_spmv(const tg_pattern* p, tg_dtype dtype, const void* vals, const void* x, void* y, tg_stream stream);
+
+/* Conjugate gradients on K x = F restricted to the rows/columns where
+ * dirichlet[i] == 0 (uint8 [n_rows], or NULL for none); entries of x on
+ * Dirichlet rows are set to 0.  x holds the initial guess on entry.
+ * Stops when ||F_I - K_II x_I|| <= rtol ||F_I|| or after maxit iterations.
+ * iters / relres are HOST outputs (may be NULL).  SYNCHRONISES the stream
+ * (the residual is checked on the host every 8 iterations).  Allocates and
+ * frees its work vectors. */
+tg_status tg_cg_solve(const tg_pattern* p, tg_dtype dtype, const void* vals, const void* F,
+                      const uint8_t* dirichlet, void* x, double rtol, int32_t maxit, int32_t* iters,
+                      double* relres, tg_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Batched assembly: many independent instances in one persistent launch
+ * (SM B.1, "Efficient Batch Data Generation": many-query use).
+ * ---------------------------------------------------------------------- */
+
+/* Group n_inst patterns of one element kind (TG_P1_TRI, TG_P2_TRI or
+ * TG_P1_TET).  The patterns must outlive the batch.  Allocates device
+ * memory and SYNCHRONISES the device. */
+tg_status tg_batch_create(const tg_pattern* const* pats, int32_t n_inst, tg_batch** out);
+
+/* Scalar bilinear assembly of every instance in ONE launch of a persistent
+ * kernel.  coords, kappa, vals_out: HOST arrays of n_inst device pointers;
+ * c: HOST array of n_inst values.  Same per-instance result, bit for bit, as
+ * tg_assemble_bilinear on that instance.  Captured-graph safe. */
+tg_status tg_batch_assemble(tg_batch* b, tg_dtype dtype, const void* const* coords, const void* const* kappa,
+                            tg_layout kappa_layout, const double* c, void* const* vals_out, tg_stream stream);
+
+/* The schedule of the persistent launch: threads per CTA, rows per work
+ * item (a multiple of the thread count), CTAs per SM (0 = as many as fit). */
+tg_status tg_batch_set_schedule(tg_batch* b, int32_t threads, int32_t rows_per_item, int32_t ctas_per_sm);
+tg_status tg_batch_get_schedule(const tg_batch* b, int32_t* threads, int32_t* rows_per_item,
+                                int32_t* ctas_per_sm);
+
+/* Autotuner: times every candidate schedule on the given inputs with CUDA
+ * events (reps launches each, after a warm-up), keeps the fastest, and
+ * returns its time per launch in *best_ms (host, may be NULL).  Overwrites
+ * vals_out.  SYNCHRONISES the stream; not for use under graph capture. */
+tg_status tg_batch_autotune(tg_batch* b, tg_dtype dtype, const void* const* coords, const void* const* kappa,
+                            tg_layout kappa_layout, const double* c, void* const* vals_out, int32_t reps,
+                            float* best_ms, tg_stream stream);
+
+void tg_batch_destroy(tg_batch* b);
+
+/* ------------------------------------------------------------------------
+ * Measurement helper (no counterpart in the paper): sustained rate of
+ * dependent-free fused multiply-adds in the given dtype across the whole
+ * GPU, in FLOP/s (2 per FMA), written to *flops (host).  SYNCHRONISES. */
+tg_status tg_diag_fma_rate(tg_dtype dtype, double* flops, tg_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TG_H_ */

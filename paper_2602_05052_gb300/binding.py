@@ -1,0 +1,320 @@
+"""Thin ctypes binding of libtg.so (argument marshalling only).
+
+Every function carries the name of the C entry point it calls and takes
+torch tensors that already live on the GPU; all computation happens in the
+library's CUDA kernels.  There is no CPU fallback: if the library is not
+built, importing raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from .build import LIB
+
+P1_TRI, P2_TRI, P1_TET, P1_TET_VEC3 = 0, 1, 2, 3
+F32, F64 = 0, 1
+PER_ELEMENT, PER_QP, PER_NODE, CONSTANT = 0, 1, 2, 3
+NV = {P1_TRI: 3, P2_TRI: 6, P1_TET: 4, P1_TET_VEC3: 4}
+DIM = {P1_TRI: 2, P2_TRI: 2, P1_TET: 3, P1_TET_VEC3: 3}
+NQ = {P1_TRI: 3, P2_TRI: 6, P1_TET: 4, P1_TET_VEC3: 4}
+
+STATUS = ["TG_OK", "TG_ERR_INVALID_ARG", "TG_ERR_INDEX_RANGE", "TG_ERR_DEGENERATE_ELEMENT", "TG_ERR_INDEX_OVERFLOW",
+          "TG_ERR_OUT_OF_MEMORY", "TG_ERR_CUDA", "TG_ERR_TIMEOUT", "TG_ERR_UNSUPPORTED"]
+
+
+class TGError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        name = STATUS[status] if 0 <= status < len(STATUS) else str(status)
+        super().__init__(f"{where}: {name}" + (f" ({detail})" if detail else ""))
+
+
+_lib = None
+vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise ImportError(f"{LIB} is missing: build it with `python -m paper_2602_05052_gb300.build` "
+                          "(or __graft_entry__.build()); there is no fallback path")
+    L = C.CDLL(LIB)
+    sig = {
+        "tg_status_string": (C.c_char_p, [i32]),
+        "tg_last_error_message": (C.c_char_p, []),
+        "tg_quadrature": (i32, [i32, vp, vp]),
+        "tg_build_pattern": (i32, [vp, i64, i64, i32, vp, C.POINTER(vp)]),
+        "tg_pattern_info": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                  C.POINTER(i32)]),
+        "tg_pattern_shape": (i32, [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32),
+                                   C.POINTER(i32)]),
+        "tg_get_device_status": (i32, [vp, C.POINTER(i64)]),
+        "tg_pattern_destroy": (None, [vp]),
+        "tg_assemble_bilinear": (i32, [vp, i32, vp, vp, i32, dbl, vp, vp]),
+        "tg_assemble_bilinear_atomic": (i32, [vp, i32, vp, vp, i32, dbl, vp, vp]),
+        "tg_assemble_elasticity": (i32, [vp, i32, vp, vp, vp, i32, vp, vp]),
+        "tg_assemble_load": (i32, [vp, i32, vp, vp, i32, i32, vp, vp]),
+        "tg_assemble_backward": (i32, [vp, i32, vp, vp, i32, dbl, vp, vp, vp, vp, vp, vp, vp]),
+        "tg_spmv": (i32, [vp, i32, vp, vp, vp, vp]),
+        "tg_cg_solve": (i32, [vp, i32, vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl), vp]),
+        "tg_batch_create": (i32, [C.POINTER(vp), i32, C.POINTER(vp)]),
+        "tg_batch_assemble": (i32, [vp, i32, C.POINTER(vp), C.POINTER(vp), i32, C.POINTER(dbl), C.POINTER(vp), vp]),
+        "tg_batch_set_schedule": (i32, [vp, i32, i32, i32]),
+        "tg_batch_get_schedule": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+        "tg_batch_autotune": (i32, [vp, i32, C.POINTER(vp), C.POINTER(vp), i32, C.POINTER(dbl), C.POINTER(vp), i32,
+                                    C.POINTER(C.c_float), vp]),
+        "tg_batch_destroy": (None, [vp]),
+        "tg_diag_fma_rate": (i32, [i32, C.POINTER(dbl), vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        msg = lib().tg_last_error_message()
+        raise TGError(st, where, msg.decode() if msg else "")
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dt(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+class _DevView:
+    """__cuda_array_interface__ view of a library-owned device buffer."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr or 0), False),
+                                         "version": 2, "strides": None}
+
+
+def tg_quadrature(el: int):
+    L = lib()
+    nq = L.tg_quadrature(el, None, None)
+    w = (C.c_double * nq)()
+    x = (C.c_double * (nq * 3))()
+    L.tg_quadrature(el, w, x)
+    d = DIM[el]
+    import numpy as np
+    return np.array(w[:]), np.array(x[: nq * d]).reshape(nq, d)
+
+
+class Pattern:
+    """Owns a tg_pattern handle (tg_build_pattern / tg_pattern_destroy)."""
+
+    def __init__(self, handle, device):
+        self.handle = handle
+        self.device = device
+        L = lib()
+        el, E, N, mrl, mdeg = i32(), i64(), i64(), i32(), i32()
+        _check(L.tg_pattern_shape(handle, C.byref(el), C.byref(E), C.byref(N), C.byref(mrl), C.byref(mdeg)),
+               "tg_pattern_shape")
+        self.el, self.n_elems, self.n_nodes = el.value, E.value, N.value
+        self.max_row_len, self.max_degree = mrl.value, mdeg.value
+        nr, nnz, rp, ci, es, ss = i64(), i64(), vp(), vp(), vp(), i32()
+        _check(L.tg_pattern_info(handle, C.byref(nr), C.byref(nnz), C.byref(rp), C.byref(ci), C.byref(es),
+                                 C.byref(ss)), "tg_pattern_info")
+        self.n_rows, self.nnz = nr.value, nnz.value
+        self._rp, self._ci, self._es, self.slot_stride = rp.value, ci.value, es.value, ss.value
+
+    def _view(self, ptr, n):
+        if n == 0:
+            return torch.empty(0, dtype=torch.int32, device=self.device)
+        t = torch.as_tensor(_DevView(ptr, n, "<i4"), device=self.device)
+        return t
+
+    @property
+    def row_ptr(self):
+        return self._view(self._rp, self.n_rows + 1)
+
+    @property
+    def col_idx(self):
+        return self._view(self._ci, self.nnz)
+
+    @property
+    def elem_slot(self):
+        return self._view(self._es, self.n_elems * self.slot_stride)
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.tg_pattern_destroy(h)
+
+
+def tg_build_pattern(cells: torch.Tensor, n_nodes: int, el: int, stream=None) -> Pattern:
+    if cells.dim() != 2 or cells.shape[1] != NV[el]:
+        raise ValueError("cells must be [E, nv]")
+    h = vp()
+    _check(lib().tg_build_pattern(_ptr(cells, torch.int32, "cells"), cells.shape[0], int(n_nodes), el,
+                                  _stream(stream), C.byref(h)), "tg_build_pattern")
+    return Pattern(h, cells.device)
+
+
+def tg_get_device_status(p: Pattern):
+    bad = i64()
+    st = lib().tg_get_device_status(p.handle, C.byref(bad))
+    return st, bad.value
+
+
+def tg_assemble_bilinear(p: Pattern, coords, kappa, layout: int, c: float = 0.0, vals_out=None, stream=None):
+    if vals_out is None:
+        vals_out = torch.empty(p.nnz, dtype=coords.dtype, device=coords.device)
+    dt = _dt(coords)
+    _check(lib().tg_assemble_bilinear(p.handle, dt, _ptr(coords, coords.dtype, "coords"),
+                                      _ptr(kappa, coords.dtype, "kappa"), layout, float(c),
+                                      _ptr(vals_out, coords.dtype, "vals_out"), _stream(stream)),
+           "tg_assemble_bilinear")
+    return vals_out
+
+
+def tg_assemble_bilinear_atomic(p: Pattern, coords, kappa, layout: int, c: float = 0.0, vals_out=None, stream=None):
+    if vals_out is None:
+        vals_out = torch.empty(p.nnz, dtype=coords.dtype, device=coords.device)
+    _check(lib().tg_assemble_bilinear_atomic(p.handle, _dt(coords), _ptr(coords, coords.dtype, "coords"),
+                                             _ptr(kappa, coords.dtype, "kappa"), layout, float(c),
+                                             _ptr(vals_out, coords.dtype, "vals_out"), _stream(stream)),
+           "tg_assemble_bilinear_atomic")
+    return vals_out
+
+
+def tg_assemble_elasticity(p: Pattern, coords, lam, mu, layout: int, vals_out=None, stream=None):
+    if vals_out is None:
+        vals_out = torch.empty(p.nnz, dtype=coords.dtype, device=coords.device)
+    _check(lib().tg_assemble_elasticity(p.handle, _dt(coords), _ptr(coords, coords.dtype, "coords"),
+                                        _ptr(lam, coords.dtype, "lam"), _ptr(mu, coords.dtype, "mu"), layout,
+                                        _ptr(vals_out, coords.dtype, "vals_out"), _stream(stream)),
+           "tg_assemble_elasticity")
+    return vals_out
+
+
+def tg_assemble_load(p: Pattern, coords, f, layout: int, ncomp: int = 1, F_out=None, stream=None):
+    if F_out is None:
+        F_out = torch.empty(p.n_nodes * ncomp, dtype=coords.dtype, device=coords.device)
+    _check(lib().tg_assemble_load(p.handle, _dt(coords), _ptr(coords, coords.dtype, "coords"),
+                                  _ptr(f, coords.dtype, "f"), layout, int(ncomp), _ptr(F_out, coords.dtype, "F_out"),
+                                  _stream(stream)), "tg_assemble_load")
+    return F_out
+
+
+def tg_assemble_backward(p: Pattern, coords, kappa, layout: int, c: float = 0.0, grad_vals=None, lam=None, U=None,
+                         grad_kappa=True, grad_coords=True, grad_c=True, stream=None):
+    """Returns (grad_kappa, grad_coords [N, d], grad_c [1]); pass False to skip one."""
+    dt = coords.dtype
+    dev = coords.device
+    gk = torch.empty_like(kappa) if grad_kappa is True else (grad_kappa or None)
+    gx = torch.empty_like(coords) if grad_coords is True else (grad_coords or None)
+    gc = torch.empty(1, dtype=dt, device=dev) if grad_c is True else (grad_c or None)
+    _check(lib().tg_assemble_backward(p.handle, _dt(coords), _ptr(coords, dt, "coords"), _ptr(kappa, dt, "kappa"),
+                                      layout, float(c), _ptr(grad_vals, dt, "grad_vals"), _ptr(lam, dt, "lam"),
+                                      _ptr(U, dt, "U"), _ptr(gk, dt, "grad_kappa"), _ptr(gx, dt, "grad_coords"),
+                                      _ptr(gc, dt, "grad_c"), _stream(stream)), "tg_assemble_backward")
+    return gk, gx, gc
+
+
+def tg_spmv(p: Pattern, vals, x, y=None, stream=None):
+    if y is None:
+        y = torch.empty(p.n_rows, dtype=vals.dtype, device=vals.device)
+    _check(lib().tg_spmv(p.handle, _dt(vals), _ptr(vals, vals.dtype, "vals"), _ptr(x, vals.dtype, "x"),
+                         _ptr(y, vals.dtype, "y"), _stream(stream)), "tg_spmv")
+    return y
+
+
+def tg_cg_solve(p: Pattern, vals, F, dirichlet=None, x=None, rtol: float = 1e-10, maxit: int = 100000, stream=None):
+    if x is None:
+        x = torch.zeros(p.n_rows, dtype=vals.dtype, device=vals.device)
+    it, rr = i32(), dbl()
+    _check(lib().tg_cg_solve(p.handle, _dt(vals), _ptr(vals, vals.dtype, "vals"), _ptr(F, vals.dtype, "F"),
+                             _ptr(dirichlet, torch.uint8, "dirichlet"), _ptr(x, vals.dtype, "x"), float(rtol),
+                             int(maxit), C.byref(it), C.byref(rr), _stream(stream)), "tg_cg_solve")
+    return x, it.value, rr.value
+
+
+class Batch:
+    """Owns a tg_batch handle (tg_batch_create / tg_batch_destroy)."""
+
+    def __init__(self, handle, pats):
+        self.handle = handle
+        self.pats = pats  # keep the patterns alive
+
+    def schedule(self):
+        t, r, c = i32(), i32(), i32()
+        _check(lib().tg_batch_get_schedule(self.handle, C.byref(t), C.byref(r), C.byref(c)), "tg_batch_get_schedule")
+        return t.value, r.value, c.value
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.tg_batch_destroy(h)
+
+
+def tg_batch_create(pats: list[Pattern]) -> Batch:
+    arr = (vp * len(pats))(*[p.handle for p in pats])
+    h = vp()
+    _check(lib().tg_batch_create(arr, len(pats), C.byref(h)), "tg_batch_create")
+    return Batch(h, list(pats))
+
+
+def _ptr_array(ts, dtype, name):
+    return (vp * len(ts))(*[_ptr(t, dtype, name) for t in ts])
+
+
+def tg_batch_assemble(b: Batch, coords: list, kappa: list, layout: int, c: list, vals_out: list, stream=None):
+    dt = coords[0].dtype
+    n = len(coords)
+    _check(lib().tg_batch_assemble(b.handle, _dt(coords[0]), _ptr_array(coords, dt, "coords"),
+                                   _ptr_array(kappa, dt, "kappa"), layout, (dbl * n)(*map(float, c)),
+                                   _ptr_array(vals_out, dt, "vals_out"), _stream(stream)), "tg_batch_assemble")
+    return vals_out
+
+
+def tg_batch_set_schedule(b: Batch, threads: int, rows_per_item: int, ctas_per_sm: int = 0):
+    _check(lib().tg_batch_set_schedule(b.handle, threads, rows_per_item, ctas_per_sm), "tg_batch_set_schedule")
+
+
+def tg_batch_autotune(b: Batch, coords: list, kappa: list, layout: int, c: list, vals_out: list, reps: int = 5,
+                      stream=None):
+    dt = coords[0].dtype
+    n = len(coords)
+    ms = C.c_float()
+    _check(lib().tg_batch_autotune(b.handle, _dt(coords[0]), _ptr_array(coords, dt, "coords"),
+                                   _ptr_array(kappa, dt, "kappa"), layout, (dbl * n)(*map(float, c)),
+                                   _ptr_array(vals_out, dt, "vals_out"), int(reps), C.byref(ms), _stream(stream)),
+           "tg_batch_autotune")
+    return ms.value
+
+
+def tg_diag_fma_rate(dtype=torch.float64, stream=None) -> float:
+    out = dbl()
+    _check(lib().tg_diag_fma_rate(F64 if dtype == torch.float64 else F32, C.byref(out), _stream(stream)),
+           "tg_diag_fma_rate")
+    return out.value

@@ -1,0 +1,329 @@
+// Batched assembly: many independent instances (meshes of uneven size, each
+// with its own coefficient field) in ONE launch of a persistent kernel.
+//
+// The work is a flat list of items (instance, first row, last row) built on
+// the host when the batch is created or its schedule changes; every CTA of a
+// persistent grid (SMs x resident CTAs) walks the list with a static stride,
+// so the schedule is deterministic and each row is computed by exactly the
+// same device routine as the single-instance kernel (gather.cuh): the result
+// of every instance is bit-identical to tg_assemble_bilinear on it.
+// Per-call pointers (coordinates, coefficients, outputs, c) travel in the
+// kernel parameters (up to kMaxInst instances per launch), so a call is a
+// single kernel launch with no host->device copy: safe to capture in a graph.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gather.cuh"
+
+namespace {
+
+constexpr int kMaxInst = 256;
+
+struct InstDesc {
+  const int32_t* row_ptr;
+  const int32_t* inc_ptr;
+  const int32_t* inc_e;
+  const uint32_t* inc_pos;
+  const int32_t* cells;
+  int64_t N;
+  unsigned long long* status;
+};
+
+template <typename T>
+struct BatchCall {
+  int inst0;
+  int layout;
+  const T* coords[kMaxInst];
+  const T* kappa[kMaxInst];
+  T* vals[kMaxInst];
+  T c[kMaxInst];
+};
+
+template <int EL, typename T, int BSZ>
+__global__ void __launch_bounds__(BSZ) k_batch(const InstDesc* __restrict__ desc, const int4* __restrict__ items,
+                                               int64_t n_items, const __grid_constant__ BatchCall<T> call,
+                                               const __grid_constant__ tg::RefTab<T> tab) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  auto& ts = *reinterpret_cast<tg::RefTab<T>*>(smem);
+  T* acc = reinterpret_cast<T*>(smem + tg::tab_bytes<T>()) + threadIdx.x;
+  tg::copy_table(ts, tab);
+  for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int4 w = items[it];
+    const InstDesc d = desc[w.x];
+    const int k = w.x - call.inst0;
+    tg::FwdArgs<T> a;
+    a.row_ptr = d.row_ptr;
+    a.inc_ptr = d.inc_ptr;
+    a.inc_e = d.inc_e;
+    a.inc_pos = d.inc_pos;
+    a.cells = d.cells;
+    a.elem_slot = nullptr;
+    a.coords = call.coords[k];
+    a.coef = call.kappa[k];
+    a.coef2 = nullptr;
+    a.layout = call.layout;
+    a.c = call.c[k];
+    a.out = call.vals[k];
+    a.n = d.N;
+    a.status = d.status;
+    for (int64_t i = w.y + threadIdx.x; i < w.z; i += BSZ) tg::gather_row<EL, T, BSZ>(a, ts, acc, i);
+  }
+}
+
+struct Sched {
+  int threads, rows_per_item, ctas_per_sm;
+};
+
+std::mutex g_cache_mu;
+std::map<std::string, Sched> g_cache;  // autotuned schedules of this process
+
+}  // namespace
+
+struct tg_batch {
+  int device = 0;
+  tg_element el = TG_P1_TRI;
+  int n_inst = 0;
+  int max_row_len = 0;
+  int64_t total_rows = 0;
+  std::vector<const tg_pattern*> pats;
+  InstDesc* d_desc = nullptr;
+  int4* d_items = nullptr;
+  std::vector<int64_t> chunk_items;  // item range of each chunk of kMaxInst instances
+  Sched sched{128, 512, 0};
+};
+
+namespace {
+
+tg_status build_items(tg_batch* b) {
+  std::vector<int4> items;
+  b->chunk_items.assign(1, 0);
+  for (int i = 0; i < b->n_inst; ++i) {
+    const int64_t N = b->pats[i]->N;
+    for (int64_t r = 0; r < N; r += b->sched.rows_per_item)
+      items.push_back(make_int4(i, (int)r, (int)std::min<int64_t>(N, r + b->sched.rows_per_item), 0));
+    if ((i + 1) % kMaxInst == 0 || i + 1 == b->n_inst) b->chunk_items.push_back((int64_t)items.size());
+  }
+  if (b->d_items) cudaFree(b->d_items);
+  b->d_items = nullptr;
+  TG_CK(cudaMalloc(&b->d_items, std::max<size_t>(items.size(), 1) * sizeof(int4)));
+  if (!items.empty()) TG_CK(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  return TG_OK;
+}
+
+template <int EL, typename T, int BSZ>
+tg_status launch_t(tg_batch* b, const void* const* coords, const void* const* kappa, tg_layout kl, const double* c,
+                   void* const* vals, cudaStream_t s) {
+  auto kern = k_batch<EL, T, BSZ>;
+  const size_t smem = tg::tab_bytes<T>() + (size_t)BSZ * b->max_row_len * sizeof(T);
+  tg_status st = tg::set_smem((const void*)kern, smem);
+  if (st != TG_OK) return st;
+  int per_sm = b->sched.ctas_per_sm;
+  if (per_sm <= 0) {
+    TG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BSZ, smem));
+    per_sm = std::max(per_sm, 1);
+  }
+  const tg::RefTab<T>& tab = tg::table<T>(b->el);
+  const size_t nchunks = b->chunk_items.size() - 1;
+  for (size_t ch = 0; ch < nchunks; ++ch) {
+    BatchCall<T> call;
+    std::memset(&call, 0, sizeof(call));
+    call.inst0 = (int)(ch * kMaxInst);
+    call.layout = kl;
+    const int n = std::min(kMaxInst, b->n_inst - call.inst0);
+    for (int k = 0; k < n; ++k) {
+      call.coords[k] = static_cast<const T*>(coords[call.inst0 + k]);
+      call.kappa[k] = static_cast<const T*>(kappa[call.inst0 + k]);
+      call.vals[k] = static_cast<T*>(vals[call.inst0 + k]);
+      call.c[k] = (T)c[call.inst0 + k];
+    }
+    const int64_t i0 = b->chunk_items[ch], n_items = b->chunk_items[ch + 1] - i0;
+    if (n_items == 0) continue;
+    const int grid = (int)std::min<int64_t>(n_items, (int64_t)per_sm * tg::sm_count());
+    kern<<<grid, BSZ, smem, s>>>(b->d_desc, b->d_items + i0, n_items, call, tab);
+    TG_CK_LAUNCH("k_batch");
+  }
+  return TG_OK;
+}
+
+template <typename T, int BSZ>
+tg_status launch_el(tg_batch* b, const void* const* coords, const void* const* kappa, tg_layout kl, const double* c,
+                    void* const* vals, cudaStream_t s) {
+  switch (b->el) {
+    case TG_P1_TRI: return launch_t<TG_P1_TRI, T, BSZ>(b, coords, kappa, kl, c, vals, s);
+    case TG_P2_TRI: return launch_t<TG_P2_TRI, T, BSZ>(b, coords, kappa, kl, c, vals, s);
+    default: return launch_t<TG_P1_TET, T, BSZ>(b, coords, kappa, kl, c, vals, s);
+  }
+}
+
+template <typename T>
+tg_status launch(tg_batch* b, const void* const* coords, const void* const* kappa, tg_layout kl, const double* c,
+                 void* const* vals, cudaStream_t s) {
+  switch (b->sched.threads) {
+    case 64: return launch_el<T, 64>(b, coords, kappa, kl, c, vals, s);
+    case 256: return launch_el<T, 256>(b, coords, kappa, kl, c, vals, s);
+    default: return launch_el<T, 128>(b, coords, kappa, kl, c, vals, s);
+  }
+}
+
+tg_status check_call(const tg_batch* b, tg_dtype dtype, const void* const* coords, const void* const* kappa,
+                     tg_layout kl, const double* c, void* const* vals) {
+  if (!b || (dtype != TG_F32 && dtype != TG_F64) || !coords || !kappa || !c || !vals) return TG_ERR_INVALID_ARG;
+  if (!(kl == TG_PER_QP || kl == TG_PER_ELEMENT || kl == TG_CONSTANT)) return TG_ERR_INVALID_ARG;
+  const size_t es = dtype == TG_F32 ? 4 : 8;
+  for (int i = 0; i < b->n_inst; ++i) {
+    if (!coords[i] || !kappa[i] || (!vals[i] && b->pats[i]->nnz > 0)) return TG_ERR_INVALID_ARG;
+    if (((uintptr_t)coords[i] % (b->el == TG_P1_TET ? es : 2 * es)) != 0) return TG_ERR_INVALID_ARG;
+  }
+  return TG_OK;
+}
+
+std::string cache_key(const tg_batch* b, tg_dtype dtype) {
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, b->device);
+  int bucket = 0;
+  for (int64_t r = b->total_rows; r > 1; r >>= 1) ++bucket;
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "%s|el%d|dt%d|rows2^%d|inst%d", prop.name, (int)b->el, (int)dtype, bucket,
+                b->n_inst);
+  return buf;
+}
+
+}  // namespace
+
+extern "C" {
+
+tg_status tg_batch_create(const tg_pattern* const* pats, int32_t n_inst, tg_batch** out) {
+  if (!out || !pats || n_inst < 1) return TG_ERR_INVALID_ARG;
+  *out = nullptr;
+  const tg_element el = pats[0] ? pats[0]->el : TG_P1_TRI;
+  if (el == TG_P1_TET_VEC3) return TG_ERR_INVALID_ARG;
+  tg_batch* b = new tg_batch;
+  b->el = el;
+  b->n_inst = n_inst;
+  std::vector<InstDesc> h(n_inst);
+  for (int i = 0; i < n_inst; ++i) {
+    const tg_pattern* p = pats[i];
+    if (!p || p->el != el || p->N > INT32_MAX) {
+      delete b;
+      return TG_ERR_INVALID_ARG;
+    }
+    b->pats.push_back(p);
+    b->max_row_len = std::max(b->max_row_len, p->max_row_len);
+    b->total_rows += p->N;
+    h[i] = InstDesc{p->row_ptr, p->inc_ptr, p->inc_e, p->inc_pos, p->cells, p->N, p->status};
+  }
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_desc, n_inst * sizeof(InstDesc));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_desc, h.data(), n_inst * sizeof(InstDesc), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    tg_batch_destroy(b);
+    return tg::cuda_fail(e, "tg_batch_create", __FILE__, __LINE__);
+  }
+  tg_status st = build_items(b);
+  if (st != TG_OK) {
+    tg_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return TG_OK;
+}
+
+tg_status tg_batch_set_schedule(tg_batch* b, int32_t threads, int32_t rows_per_item, int32_t ctas_per_sm) {
+  if (!b || !(threads == 64 || threads == 128 || threads == 256) || rows_per_item < threads ||
+      rows_per_item % threads != 0 || ctas_per_sm < 0)
+    return TG_ERR_INVALID_ARG;
+  b->sched = Sched{threads, rows_per_item, ctas_per_sm};
+  return build_items(b);
+}
+
+tg_status tg_batch_get_schedule(const tg_batch* b, int32_t* threads, int32_t* rows_per_item, int32_t* ctas_per_sm) {
+  if (!b) return TG_ERR_INVALID_ARG;
+  if (threads) *threads = b->sched.threads;
+  if (rows_per_item) *rows_per_item = b->sched.rows_per_item;
+  if (ctas_per_sm) *ctas_per_sm = b->sched.ctas_per_sm;
+  return TG_OK;
+}
+
+tg_status tg_batch_assemble(tg_batch* b, tg_dtype dtype, const void* const* coords, const void* const* kappa,
+                            tg_layout kappa_layout, const double* c, void* const* vals_out, tg_stream stream) {
+  tg_status st = check_call(b, dtype, coords, kappa, kappa_layout, c, vals_out);
+  if (st != TG_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  return dtype == TG_F32 ? launch<float>(b, coords, kappa, kappa_layout, c, vals_out, s)
+                         : launch<double>(b, coords, kappa, kappa_layout, c, vals_out, s);
+}
+
+tg_status tg_batch_autotune(tg_batch* b, tg_dtype dtype, const void* const* coords, const void* const* kappa,
+                            tg_layout kappa_layout, const double* c, void* const* vals_out, int32_t reps,
+                            float* best_ms, tg_stream stream) {
+  tg_status st = check_call(b, dtype, coords, kappa, kappa_layout, c, vals_out);
+  if (st != TG_OK) return st;
+  if (reps < 1) return TG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const std::string key = cache_key(b, dtype);
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end() && !best_ms) {
+      b->sched = it->second;
+      return build_items(b);
+    }
+  }
+  std::vector<Sched> cands;
+  for (int t : {64, 128, 256})
+    for (int m : {1, 2, 4, 8, 16})
+      for (int cps : {0, 2})
+        cands.push_back(Sched{t, t * m, cps});
+  cudaEvent_t e0, e1;
+  TG_CK(cudaEventCreate(&e0));
+  TG_CK(cudaEventCreate(&e1));
+  Sched best = b->sched;
+  float best_t = 1e30f;
+  for (const Sched& sc : cands) {
+    b->sched = sc;
+    if ((st = build_items(b)) != TG_OK) break;
+    auto run = [&]() {
+      return dtype == TG_F32 ? launch<float>(b, coords, kappa, kappa_layout, c, vals_out, s)
+                             : launch<double>(b, coords, kappa, kappa_layout, c, vals_out, s);
+    };
+    if ((st = run()) != TG_OK) break;  // warm-up
+    TG_CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps && st == TG_OK; ++r) st = run();
+    TG_CK(cudaEventRecord(e1, s));
+    TG_CK(cudaEventSynchronize(e1));
+    if (st != TG_OK) break;
+    float ms = 0;
+    TG_CK(cudaEventElapsedTime(&ms, e0, e1));
+    ms /= reps;
+    if (ms < best_t) {
+      best_t = ms;
+      best = sc;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->sched = best;
+  tg_status st2 = build_items(b);
+  if (st != TG_OK) return st;
+  if (st2 != TG_OK) return st2;
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    g_cache[key] = best;
+  }
+  if (best_ms) *best_ms = best_t;
+  return TG_OK;
+}
+
+void tg_batch_destroy(tg_batch* b) {
+  if (!b) return;
+  if (b->d_desc) cudaFree(b->d_desc);
+  if (b->d_items) cudaFree(b->d_items);
+  delete b;
+}
+
+}  // extern "C"

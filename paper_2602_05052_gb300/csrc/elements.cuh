@@ -1,0 +1,147 @@
+// Per-element geometry and local-matrix rows (Stage I Map, Algorithm 1) for
+// the kernels of libtg.so.  Affine simplices: J, det J and the push-forward
+// are constant over the element (SM A.2), so geometry is computed once per
+// (element, visit) from the vertex coordinates.
+//
+// Notation: for P1, n_b = det(J) * grad(phi_b) ("det-scaled gradients"):
+// rows of det(J) J^{-1} for b >= 1 (2D: (e2y, -e2x), (-e1y, e1x); 3D: the
+// cross products e2 x e3, e3 x e1, e1 x e2 of the edge vectors), and
+// n_0 = -(sum of the others).  Then |det J| grad(phi_a).grad(phi_b) =
+// n_a.n_b / |det J|, so one reciprocal per element suffices.
+#pragma once
+
+#include "tg_internal.cuh"
+
+namespace tg {
+
+template <typename T>
+__device__ __forceinline__ typename Vec2<T>::type ldg2(const T* __restrict__ coords, int v) {
+  using V2 = typename Vec2<T>::type;
+  return __ldg(reinterpret_cast<const V2*>(coords) + v);
+}
+
+template <typename T, int N>
+__device__ __forceinline__ T sel(int k, const T (&a)[N]) {
+  T r = a[0];
+#pragma unroll
+  for (int m = 1; m < N; ++m) r = (k == m) ? a[m] : r;
+  return r;
+}
+
+// Geometry of one element.  dim 2: n[b][0..1]; dim 3: n[b][0..2].
+template <int DIM, typename T>
+struct Geom {
+  T n[DIM + 1][DIM];
+  T det;
+};
+
+template <typename T>
+__device__ __forceinline__ void tri_geom(const T* __restrict__ coords, int v0, int v1, int v2, Geom<2, T>& g) {
+  const auto x0 = ldg2(coords, v0);
+  const auto x1 = ldg2(coords, v1);
+  const auto x2 = ldg2(coords, v2);
+  const T e1x = x1.x - x0.x, e1y = x1.y - x0.y;
+  const T e2x = x2.x - x0.x, e2y = x2.y - x0.y;
+  g.n[1][0] = e2y;
+  g.n[1][1] = -e2x;
+  g.n[2][0] = -e1y;
+  g.n[2][1] = e1x;
+  g.n[0][0] = -(g.n[1][0] + g.n[2][0]);
+  g.n[0][1] = -(g.n[1][1] + g.n[2][1]);
+  g.det = e1x * e2y - e1y * e2x;
+}
+
+template <typename T>
+__device__ __forceinline__ void cross3(const T (&a)[3], const T (&b)[3], T (&c)[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+template <typename T>
+__device__ __forceinline__ void tet_geom(const T* __restrict__ coords, int v0, int v1, int v2, int v3,
+                                         Geom<3, T>& g) {
+  T x0[3], e[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) x0[r] = __ldg(coords + 3ll * v0 + r);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    e[0][r] = __ldg(coords + 3ll * v1 + r) - x0[r];
+    e[1][r] = __ldg(coords + 3ll * v2 + r) - x0[r];
+    e[2][r] = __ldg(coords + 3ll * v3 + r) - x0[r];
+  }
+  cross3(e[1], e[2], g.n[1]);
+  cross3(e[2], e[0], g.n[2]);
+  cross3(e[0], e[1], g.n[3]);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) g.n[0][r] = -(g.n[1][r] + g.n[2][r] + g.n[3][r]);
+  g.det = e[0][0] * g.n[1][0] + e[0][1] * g.n[1][1] + e[0][2] * g.n[1][2];
+}
+
+// Determinant only (load vector).
+template <typename T>
+__device__ __forceinline__ T tri_det(const T* __restrict__ coords, int v0, int v1, int v2) {
+  const auto x0 = ldg2(coords, v0);
+  const auto x1 = ldg2(coords, v1);
+  const auto x2 = ldg2(coords, v2);
+  return (x1.x - x0.x) * (x2.y - x0.y) - (x1.y - x0.y) * (x2.x - x0.x);
+}
+
+template <typename T>
+__device__ __forceinline__ T tet_det(const T* __restrict__ coords, int v0, int v1, int v2, int v3) {
+  Geom<3, T> g;
+  tet_geom(coords, v0, v1, v2, v3, g);
+  return g.det;
+}
+
+// Row la of the scalar local matrix of a P1 element (triangle or tet):
+//   K[la][b] = s * n_la.n_b + mc * M[la][b],  s = (sum_q w_q kappa_q)/|det|, mc = c |det|.
+template <int DIM, typename T>
+__device__ __forceinline__ void p1_row(const Geom<DIM, T>& g, int la, T s, T mc, const T (&Mla)[6],
+                                       T (&Krow)[DIM + 1]) {
+  T na[DIM];
+#pragma unroll
+  for (int r = 0; r < DIM; ++r) {
+    T col[DIM + 1];
+#pragma unroll
+    for (int b = 0; b <= DIM; ++b) col[b] = g.n[b][r];
+    na[r] = sel(la, col);
+  }
+#pragma unroll
+  for (int b = 0; b <= DIM; ++b) {
+    T d = T(0);
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) d += na[r] * g.n[b][r];
+    Krow[b] = s * d + mc * Mla[b];
+  }
+}
+
+// Row la of the P2 triangle matrix with kappa at the 6 points:
+//   K[la][b] = (1/|det|) sum_q w_q kappa_q gh_q,la^T C gh_q,b + c |det| M[la][b]
+// with C = det^2 J^{-1} J^{-T} = [[n1.n1, n1.n2], [n1.n2, n2.n2]].
+template <typename T>
+__device__ __forceinline__ void p2_row(const Geom<2, T>& g, int la, const T (&kq)[6], T inv, T mc,
+                                       const RefTab<T>& ts, T (&Krow)[6]) {
+  const T c00 = g.n[1][0] * g.n[1][0] + g.n[1][1] * g.n[1][1];
+  const T c01 = g.n[1][0] * g.n[2][0] + g.n[1][1] * g.n[2][1];
+  const T c11 = g.n[2][0] * g.n[2][0] + g.n[2][1] * g.n[2][1];
+#pragma unroll
+  for (int b = 0; b < 6; ++b) Krow[b] = T(0);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const T ga0 = ts.gh[q][la][0], ga1 = ts.gh[q][la][1];
+    const T wk = ts.w[q] * kq[q];
+    const T hx = wk * (c00 * ga0 + c01 * ga1);
+    const T hy = wk * (c01 * ga0 + c11 * ga1);
+#pragma unroll
+    for (int b = 0; b < 6; ++b) Krow[b] += hx * ts.gh[q][b][0] + hy * ts.gh[q][b][1];
+  }
+#pragma unroll
+  for (int b = 0; b < 6; ++b) Krow[b] = Krow[b] * inv + mc * ts.M[la][b];
+}
+
+__device__ __forceinline__ int pos_of(uint32_t w0, uint32_t w1, int b) {
+  return (int)(((b < 4 ? w0 : w1) >> (8 * (b & 3))) & 0xffu);
+}
+
+}  // namespace tg

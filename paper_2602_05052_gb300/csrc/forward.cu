@@ -1,0 +1,343 @@
+// Forward assembly kernels: fused Map (Algorithm 1) + deterministic Reduce
+// (Algorithm 2) as a row-owner gather.
+//
+// Design.  Algorithm 2 sums local entries into CSR slots through the
+// routing matrices S_mat / S_vec.  Here every CSR row (mesh node) is owned by
+// one thread, which walks the node's incident elements in increasing element
+// order, evaluates the element's local row for that node directly from the
+// vertex coordinates and coefficients (Map fused in), and accumulates it into
+// a per-thread strip of shared memory at the column positions the pattern
+// stored (the row-owned form of S_mat).  Each row is then written to HBM
+// exactly once, contiguously.  There are no atomics, no intermediate
+// K_local array in HBM, and the summation order of every slot is fixed, so
+// results are bitwise reproducible.  The price is that an element's geometry
+// is evaluated once per vertex (nv times), which is cheap in FP32 next to
+// the memory traffic.
+#include <cstdint>
+
+#include "gather.cuh"
+
+namespace {
+
+constexpr int BS = 128;  // rows per CTA (scalar kernels)
+constexpr int EB = 64;   // rows per CTA (elasticity: 9 * row length accumulators per thread)
+
+using tg::FwdArgs;
+using tg::tab_bytes;
+using tg::copy_table;
+using tg::absv;
+using tg::load_kq;
+using tg::scalar_row;
+
+// One thread per CSR row.  Shared memory: the reference tables, then the
+// row accumulators acc[p * BS + tid] (conflict-free: one bank column per thread).
+template <int EL, typename T>
+__global__ void __launch_bounds__(BS) k_bilinear_gather(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  auto& ts = *reinterpret_cast<tg::RefTab<T>*>(smem);
+  T* acc = reinterpret_cast<T*>(smem + tab_bytes<T>()) + threadIdx.x;
+  copy_table(ts, tab);
+  const int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
+  if (i >= a.n) return;
+  tg::gather_row<EL, T, BS>(a, ts, acc, i);
+}
+
+// Comparison point: classic scatter-add (Eq. (scatter_add)) with atomics,
+// one thread per element, output cleared beforehand.
+template <int EL, typename T>
+__global__ void __launch_bounds__(BS) k_bilinear_atomic(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab) {
+  using El = tg::Elem<EL>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  auto& ts = *reinterpret_cast<tg::RefTab<T>*>(smem);
+  copy_table(ts, tab);
+  const int64_t e = (int64_t)blockIdx.x * BS + threadIdx.x;
+  if (e >= a.n) return;
+  const int32_t* slot = a.elem_slot + e * El::nv * El::nv;
+#pragma unroll 1
+  for (int la = 0; la < El::nv; ++la) {
+    T Krow[El::nv];
+    if (!scalar_row<EL, T>(a, ts, e, la, Krow)) {
+      tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
+      return;
+    }
+#pragma unroll
+    for (int b = 0; b < El::nv; ++b) atomicAdd(a.out + __ldg(slot + la * El::nv + b), Krow[b]);
+  }
+}
+
+// Load vector, one thread per node (NC components per node).
+template <int EL, typename T, int NC>
+__global__ void __launch_bounds__(BS) k_load_gather(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab) {
+  using El = tg::Elem<EL>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  auto& ts = *reinterpret_cast<tg::RefTab<T>*>(smem);
+  copy_table(ts, tab);
+  const int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
+  if (i >= a.n) return;
+  T F[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) F[k] = T(0);
+  const int j0 = __ldg(a.inc_ptr + i), j1 = __ldg(a.inc_ptr + i + 1);
+  for (int j = j0; j < j1; ++j) {
+    const int ea = __ldg(a.inc_e + j);
+    const int64_t e = ea >> 3;
+    const int la = ea & 7;
+    const int32_t* cl = a.cells + e * El::nv;
+    T det;
+    if constexpr (El::dim == 2) det = tg::tri_det(a.coords, __ldg(cl), __ldg(cl + 1), __ldg(cl + 2));
+    else det = tg::tet_det(a.coords, __ldg(cl), __ldg(cl + 1), __ldg(cl + 2), __ldg(cl + 3));
+    const T adet = absv(det);
+    if (!(adet > tg::det_tiny<T>())) {
+      tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
+      continue;
+    }
+    if (a.layout == TG_PER_NODE) {
+      int v[El::nv];
+#pragma unroll
+      for (int b = 0; b < El::nv; ++b) v[b] = __ldg(cl + b);
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        T s = T(0);
+#pragma unroll
+        for (int b = 0; b < El::nv; ++b) s += ts.M[la][b] * __ldg(a.coef + (int64_t)v[b] * NC + k);
+        F[k] += adet * s;
+      }
+    } else if (a.layout == TG_PER_QP) {
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        T s = T(0);
+#pragma unroll
+        for (int q = 0; q < El::nq; ++q) s += ts.w[q] * ts.phi[q][la] * __ldg(a.coef + (e * El::nq + q) * NC + k);
+        F[k] += adet * s;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < NC; ++k) F[k] += adet * ts.m1[la] * __ldg(a.coef + k);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NC; ++k) a.out[i * NC + k] = F[k];
+}
+
+// Vector P1 elasticity, one thread per node: the node's three DoF rows are
+// consecutive in the DoF CSR and together hold 9 * len entries in the order
+// [component i][column node p][component j], accumulated in shared memory.
+//   block (a, b) = (1/|det|) ( L n_a n_b^T + M n_b n_a^T + M (n_a.n_b) I ),
+//   L = sum_q w_q lam_q, M = sum_q w_q mu_q.
+template <typename T>
+__global__ void __launch_bounds__(EB) k_elastic_gather(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  auto& ts = *reinterpret_cast<tg::RefTab<T>*>(smem);
+  T* acc = reinterpret_cast<T*>(smem + tab_bytes<T>()) + threadIdx.x;
+  copy_table(ts, tab);
+  const int64_t i = (int64_t)blockIdx.x * EB + threadIdx.x;
+  if (i >= a.n) return;
+  const int r0 = __ldg(a.row_ptr + i), len = __ldg(a.row_ptr + i + 1) - r0;
+  for (int p = 0; p < 9 * len; ++p) acc[p * EB] = T(0);
+  const int j0 = __ldg(a.inc_ptr + i), j1 = __ldg(a.inc_ptr + i + 1);
+  for (int j = j0; j < j1; ++j) {
+    const int ea = __ldg(a.inc_e + j);
+    const int64_t e = ea >> 3;
+    const int la = ea & 7;
+    const uint32_t w0 = __ldg(a.inc_pos + j);
+    const int32_t* cl = a.cells + e * 4;
+    tg::Geom<3, T> g;
+    tg::tet_geom(a.coords, __ldg(cl), __ldg(cl + 1), __ldg(cl + 2), __ldg(cl + 3), g);
+    const T adet = absv(g.det);
+    if (!(adet > tg::det_tiny<T>())) {
+      tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
+      continue;
+    }
+    const T inv = T(1) / adet;
+    const T L = tg::weighted_coef<T, 4>(a.coef, a.layout, e, ts.w, ts.wsum) * inv;
+    const T M = tg::weighted_coef<T, 4>(a.coef2, a.layout, e, ts.w, ts.wsum) * inv;
+    T na[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const T col[4] = {g.n[0][r], g.n[1][r], g.n[2][r], g.n[3][r]};
+      na[r] = tg::sel(la, col);
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int pos = tg::pos_of(w0, 0u, b);
+      const T d = na[0] * g.n[b][0] + na[1] * g.n[b][1] + na[2] * g.n[b][2];
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+          T v = L * na[ii] * g.n[b][jj] + M * g.n[b][ii] * na[jj];
+          if (ii == jj) v += M * d;
+          acc[((ii * len + pos) * 3 + jj) * EB] += v;
+        }
+    }
+  }
+  T* out = a.out + 9ll * r0;
+  for (int p = 0; p < 9 * len; ++p) out[p] = acc[p * EB];
+}
+
+// ---------------------------------------------------------------- host side
+using tg::table;
+using tg::set_smem;
+
+template <typename T>
+FwdArgs<T> base_args(const tg_pattern* p, const void* coords) {
+  FwdArgs<T> a;
+  a.row_ptr = p->row_ptr;
+  a.inc_ptr = p->inc_ptr;
+  a.inc_e = p->inc_e;
+  a.inc_pos = p->inc_pos;
+  a.cells = p->cells;
+  a.elem_slot = p->elem_slot;
+  a.coords = static_cast<const T*>(coords);
+  a.coef = nullptr;
+  a.coef2 = nullptr;
+  a.layout = 0;
+  a.c = T(0);
+  a.out = nullptr;
+  a.n = p->N;
+  a.status = p->status;
+  return a;
+}
+
+bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+template <int EL, typename T>
+tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, bool atomic) {
+  const tg::RefTab<T>& tab = table<T>(p->el);
+  if (atomic) {
+    a.n = p->E;
+    if (p->nnz) TG_CK(cudaMemsetAsync(a.out, 0, p->nnz * sizeof(T), s));
+    if (p->E == 0) return TG_OK;
+    const size_t smem = tab_bytes<T>();
+    k_bilinear_atomic<EL, T><<<tg::grid_for(p->E, BS), BS, smem, s>>>(a, tab);
+    TG_CK_LAUNCH("k_bilinear_atomic");
+    return TG_OK;
+  }
+  const size_t smem = tab_bytes<T>() + (size_t)BS * p->max_row_len * sizeof(T);
+  tg_status st = set_smem((const void*)k_bilinear_gather<EL, T>, smem);
+  if (st != TG_OK) return st;
+  k_bilinear_gather<EL, T><<<tg::grid_for(p->N, BS), BS, smem, s>>>(a, tab);
+  TG_CK_LAUNCH("k_bilinear_gather");
+  return TG_OK;
+}
+
+template <typename T>
+tg_status bilinear(const tg_pattern* p, const void* coords, const void* kappa, tg_layout kl, double c, void* vals,
+                   cudaStream_t s, bool atomic) {
+  FwdArgs<T> a = base_args<T>(p, coords);
+  a.coef = static_cast<const T*>(kappa);
+  a.layout = kl;
+  a.c = (T)c;
+  a.out = static_cast<T*>(vals);
+  switch (p->el) {
+    case TG_P1_TRI: return launch_bilinear<TG_P1_TRI, T>(p, a, s, atomic);
+    case TG_P2_TRI: return launch_bilinear<TG_P2_TRI, T>(p, a, s, atomic);
+    default: return launch_bilinear<TG_P1_TET, T>(p, a, s, atomic);
+  }
+}
+
+tg_status check_common(const tg_pattern* p, tg_dtype dtype, const void* coords) {
+  if (!p || (dtype != TG_F32 && dtype != TG_F64)) return TG_ERR_INVALID_ARG;
+  if (p->N > 0 && !coords) return TG_ERR_INVALID_ARG;
+  const size_t es = dtype == TG_F32 ? 4 : 8;
+  if (!aligned(coords, p->dim == 2 ? 2 * es : es)) {
+    tg::set_error("coords must be aligned to 2 * sizeof(dtype) for 2D meshes");
+    return TG_ERR_INVALID_ARG;
+  }
+  return TG_OK;
+}
+
+template <typename T>
+tg_status load(const tg_pattern* p, const void* coords, const void* f, tg_layout fl, int ncomp, void* F,
+               cudaStream_t s) {
+  FwdArgs<T> a = base_args<T>(p, coords);
+  a.coef = static_cast<const T*>(f);
+  a.layout = fl;
+  a.out = static_cast<T*>(F);
+  const tg_element el = p->el == TG_P1_TET_VEC3 ? TG_P1_TET : p->el;
+  const tg::RefTab<T>& tab = table<T>(el);
+  const size_t smem = tab_bytes<T>();
+  const int grid = tg::grid_for(p->N, BS);
+  if (el == TG_P1_TRI) {
+    if (ncomp == 1) k_load_gather<TG_P1_TRI, T, 1><<<grid, BS, smem, s>>>(a, tab);
+    else k_load_gather<TG_P1_TRI, T, 3><<<grid, BS, smem, s>>>(a, tab);
+  } else if (el == TG_P2_TRI) {
+    if (ncomp == 1) k_load_gather<TG_P2_TRI, T, 1><<<grid, BS, smem, s>>>(a, tab);
+    else k_load_gather<TG_P2_TRI, T, 3><<<grid, BS, smem, s>>>(a, tab);
+  } else {
+    if (ncomp == 1) k_load_gather<TG_P1_TET, T, 1><<<grid, BS, smem, s>>>(a, tab);
+    else k_load_gather<TG_P1_TET, T, 3><<<grid, BS, smem, s>>>(a, tab);
+  }
+  TG_CK_LAUNCH("k_load_gather");
+  return TG_OK;
+}
+
+template <typename T>
+tg_status elastic(const tg_pattern* p, const void* coords, const void* lam, const void* mu, tg_layout l, void* vals,
+                  cudaStream_t s) {
+  FwdArgs<T> a = base_args<T>(p, coords);
+  a.coef = static_cast<const T*>(lam);
+  a.coef2 = static_cast<const T*>(mu);
+  a.layout = l;
+  a.out = static_cast<T*>(vals);
+  const size_t smem = tab_bytes<T>() + (size_t)EB * 9 * p->max_row_len * sizeof(T);
+  tg_status st = set_smem((const void*)k_elastic_gather<T>, smem);
+  if (st != TG_OK) return st;
+  k_elastic_gather<T><<<tg::grid_for(p->N, EB), EB, smem, s>>>(a, table<T>(TG_P1_TET));
+  TG_CK_LAUNCH("k_elastic_gather");
+  return TG_OK;
+}
+
+bool layout_ok(tg_layout l, bool allow_node) {
+  return l == TG_PER_ELEMENT || l == TG_PER_QP || l == TG_CONSTANT || (allow_node && l == TG_PER_NODE);
+}
+
+tg_status bilinear_entry(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa, tg_layout kl,
+                         double c, void* vals, tg_stream stream, bool atomic) {
+  tg_status st = check_common(p, dtype, coords);
+  if (st != TG_OK) return st;
+  if (p->el == TG_P1_TET_VEC3 || !layout_ok(kl, false) || !kappa || (p->nnz > 0 && !vals)) return TG_ERR_INVALID_ARG;
+  if (p->N == 0) return TG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  return dtype == TG_F32 ? bilinear<float>(p, coords, kappa, kl, c, vals, s, atomic)
+                         : bilinear<double>(p, coords, kappa, kl, c, vals, s, atomic);
+}
+
+}  // namespace
+
+extern "C" {
+
+tg_status tg_assemble_bilinear(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
+                               tg_layout kappa_layout, double c, void* vals_out, tg_stream stream) {
+  return bilinear_entry(p, dtype, coords, kappa, kappa_layout, c, vals_out, stream, false);
+}
+
+tg_status tg_assemble_bilinear_atomic(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
+                                      tg_layout kappa_layout, double c, void* vals_out, tg_stream stream) {
+  return bilinear_entry(p, dtype, coords, kappa, kappa_layout, c, vals_out, stream, true);
+}
+
+tg_status tg_assemble_elasticity(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* lam,
+                                 const void* mu, tg_layout layout, void* vals_out, tg_stream stream) {
+  tg_status st = check_common(p, dtype, coords);
+  if (st != TG_OK) return st;
+  if (p->el != TG_P1_TET_VEC3 || !layout_ok(layout, false) || !lam || !mu || (p->nnz > 0 && !vals_out))
+    return TG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  return dtype == TG_F32 ? elastic<float>(p, coords, lam, mu, layout, vals_out, s)
+                         : elastic<double>(p, coords, lam, mu, layout, vals_out, s);
+}
+
+tg_status tg_assemble_load(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* f, tg_layout f_layout,
+                           int32_t ncomp, void* F_out, tg_stream stream) {
+  tg_status st = check_common(p, dtype, coords);
+  if (st != TG_OK) return st;
+  if ((ncomp != 1 && ncomp != 3) || !f || !F_out || !(f_layout == TG_PER_NODE || f_layout == TG_PER_QP ||
+                                                       f_layout == TG_CONSTANT))
+    return TG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  return dtype == TG_F32 ? load<float>(p, coords, f, f_layout, ncomp, F_out, s)
+                         : load<double>(p, coords, f, f_layout, ncomp, F_out, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,386 @@
+// Pattern construction: the "routing" of Algorithm 2, precomputed from the
+// mesh topology alone (Stage II of the method).
+//
+// Steps, all on the device:
+//   1. validate the cells and count the incidences of every node;
+//   2. exclusive scan -> inc_ptr; scatter (element, local index) pairs and
+//      sort every node's list by element index (fixed Reduce order);
+//   3. per node: the sorted, de-duplicated set of nodes of its incident
+//      elements is its CSR row (structural zeros kept); scan -> row_ptr;
+//   4. per incidence: 8-bit positions of the element's nodes inside the
+//      owning row (inc_pos) and the element-to-slot map (elem_slot);
+//   5. vector elasticity: expansion of the node CSR to the DoF CSR
+//      (DoF = 3 * node + component, 3x3 blocks).
+#include <cstdio>
+#include <vector>
+
+#include "tg_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__global__ void k_count(const int32_t* __restrict__ cells, int64_t E, int nv, int64_t N, int32_t* __restrict__ deg,
+                        unsigned long long* status) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride) {
+    int v[6];
+    bool bad = false;
+    for (int a = 0; a < nv; ++a) {
+      v[a] = cells[e * nv + a];
+      if (v[a] < 0 || (int64_t)v[a] >= N) bad = true;
+    }
+    if (bad) {
+      tg::record_error(status, TG_ERR_INDEX_RANGE, e);
+      continue;
+    }
+    for (int a = 0; a < nv; ++a)
+      for (int b = a + 1; b < nv; ++b)
+        if (v[a] == v[b]) bad = true;
+    if (bad) {
+      tg::record_error(status, TG_ERR_DEGENERATE_ELEMENT, e);
+      continue;
+    }
+    for (int a = 0; a < nv; ++a) atomicAdd(deg + v[a], 1);
+  }
+}
+
+// Exclusive scan of one tile of kScanTile values; the tile total goes to
+// tile_sums[blockIdx.x].
+template <typename Tin>
+__global__ void __launch_bounds__(kScanThreads) k_scan_tile(const Tin* __restrict__ in, int64_t* __restrict__ out,
+                                                            int64_t* __restrict__ tile_sums, int64_t n) {
+  __shared__ int64_t warp_sums[kScanThreads / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (base + k < n) ? (int64_t)in[base + k] : 0;
+    s += v[k];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int64_t w = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kScanThreads / 32) warp_sums[lane] = w;
+  }
+  __syncthreads();
+  int64_t run = x - s + (wid > 0 ? warp_sums[wid - 1] : 0);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == kScanThreads - 1) tile_sums[blockIdx.x] = run;
+}
+
+__global__ void k_scan_add(int64_t* __restrict__ out, const int64_t* __restrict__ tile_off, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += tile_off[i / kScanTile];
+}
+
+__global__ void k_narrow(const int64_t* __restrict__ in, int32_t* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (int32_t)in[i];
+}
+
+__global__ void k_fill(const int32_t* __restrict__ cells, int64_t E, int nv, int32_t* __restrict__ cursor,
+                       int32_t* __restrict__ inc_e) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride)
+    for (int a = 0; a < nv; ++a) {
+      const int v = cells[e * nv + a];
+      const int slot = atomicAdd(cursor + v, 1);
+      inc_e[slot] = (int32_t)(e * 8 + a);
+    }
+}
+
+// Sort each node's incidence list by element index (insertion sort; lists
+// are short).  Fixes the order in which every Reduce sums.
+__global__ void k_sort_incidence(const int32_t* __restrict__ inc_ptr, int32_t* __restrict__ inc_e, int64_t N) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int j0 = inc_ptr[i], j1 = inc_ptr[i + 1];
+  for (int j = j0 + 1; j < j1; ++j) {
+    const int x = inc_e[j];
+    int k = j - 1;
+    while (k >= j0 && inc_e[k] > x) {
+      inc_e[k + 1] = inc_e[k];
+      --k;
+    }
+    inc_e[k + 1] = x;
+  }
+}
+
+// Insert v into the sorted unique list cols[0..len); false when full.
+__device__ __forceinline__ bool insert_unique(int* cols, int& len, int v) {
+  int k = len - 1;
+  while (k >= 0 && cols[k] > v) --k;
+  if (k >= 0 && cols[k] == v) return true;
+  if (len >= TG_MAX_ROW) return false;
+  for (int m = len - 1; m > k; --m) cols[m + 1] = cols[m];
+  cols[k + 1] = v;
+  ++len;
+  return true;
+}
+
+__device__ __forceinline__ int lower_bound(const int* cols, int len, int v) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (cols[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// FILL = false: row lengths, largest row and degree.  FILL = true: columns,
+// per-incidence positions and the element-to-slot map.
+template <bool FILL>
+__global__ void __launch_bounds__(128) k_rows(const int32_t* __restrict__ cells, const int32_t* __restrict__ inc_ptr,
+                                              const int32_t* __restrict__ inc_e, int64_t N, int nv, int npw, bool vec3,
+                                              int32_t* __restrict__ row_len, int* __restrict__ maxes,
+                                              const int32_t* __restrict__ row_ptr, int32_t* __restrict__ col_idx,
+                                              uint32_t* __restrict__ inc_pos, int32_t* __restrict__ elem_slot,
+                                              unsigned long long* status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int cols[TG_MAX_ROW];
+  int len = 0;
+  bool ok = true;
+  const int j0 = inc_ptr[i], j1 = inc_ptr[i + 1];
+  for (int j = j0; j < j1 && ok; ++j) {
+    const int e = inc_e[j] >> 3;
+    for (int b = 0; b < nv && ok; ++b) ok = insert_unique(cols, len, cells[(int64_t)e * nv + b]);
+  }
+  if (!FILL) {
+    if (!ok) tg::record_error(status, TG_ERR_UNSUPPORTED, j0 < j1 ? (inc_e[j0] >> 3) : 0);
+    row_len[i] = len;
+    atomicMax(maxes + 0, len);
+    atomicMax(maxes + 1, j1 - j0);
+    return;
+  }
+  const int r0 = row_ptr[i];
+  for (int p = 0; p < len; ++p) col_idx[r0 + p] = cols[p];
+  for (int j = j0; j < j1; ++j) {
+    const int e = inc_e[j] >> 3, a = inc_e[j] & 7;
+    uint32_t w0 = 0, w1 = 0;
+    for (int b = 0; b < nv; ++b) {
+      const uint32_t pos = (uint32_t)lower_bound(cols, len, cells[(int64_t)e * nv + b]);
+      if (b < 4) w0 |= pos << (8 * b);
+      else w1 |= pos << (8 * (b - 4));
+      const int64_t slot = vec3 ? 9ll * r0 + 3ll * pos : (int64_t)r0 + pos;
+      elem_slot[((int64_t)e * nv + a) * nv + b] = (int32_t)slot;
+    }
+    inc_pos[(int64_t)j * npw] = w0;
+    if (npw == 2) inc_pos[(int64_t)j * npw + 1] = w1;
+  }
+}
+
+__global__ void k_expand3(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int64_t N,
+                          int32_t* __restrict__ row_ptr3, int32_t* __restrict__ col_idx3) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int r0 = row_ptr[n], len = row_ptr[n + 1] - r0;
+  for (int i = 0; i < 3; ++i) {
+    row_ptr3[3 * n + i] = 9 * r0 + 3 * i * len;
+    for (int p = 0; p < len; ++p)
+      for (int j = 0; j < 3; ++j) col_idx3[9ll * r0 + (i * len + p) * 3 + j] = 3 * col_idx[r0 + p] + j;
+  }
+  if (n == N - 1) row_ptr3[3 * N] = 9 * row_ptr[N];
+}
+
+// Device buffers freed on scope exit unless released.
+struct Tmp {
+  std::vector<void*> bufs;
+  ~Tmp() {
+    for (void* b : bufs) cudaFree(b);
+  }
+  template <typename T>
+  cudaError_t alloc(T** p, size_t n) {
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) + 16);
+    if (e == cudaSuccess) bufs.push_back(*p);
+    return e;
+  }
+};
+
+// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
+template <typename Tin>
+tg_status scan_exclusive(const Tin* in, int64_t* out, int64_t n, cudaStream_t s) {
+  Tmp tmp;
+  const int64_t tiles = n > 0 ? (n + kScanTile - 1) / kScanTile : 0;
+  if (tiles == 0) {
+    TG_CK(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+    return TG_OK;
+  }
+  int64_t* sums = nullptr;
+  TG_CK(tmp.alloc(&sums, tiles));
+  k_scan_tile<Tin><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, sums, n);
+  TG_CK_LAUNCH("k_scan_tile");
+  if (tiles == 1) {
+    TG_CK(cudaMemcpyAsync(out + n, sums, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    return TG_OK;
+  }
+  int64_t* offs = nullptr;
+  TG_CK(tmp.alloc(&offs, tiles + 1));
+  tg_status st = scan_exclusive<int64_t>(sums, offs, tiles, s);
+  if (st != TG_OK) return st;
+  k_scan_add<<<tg::grid_for(n, kThreads), kThreads, 0, s>>>(out, offs, n);
+  TG_CK_LAUNCH("k_scan_add");
+  TG_CK(cudaMemcpyAsync(out + n, offs + tiles, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  TG_CK(cudaStreamSynchronize(s));  // tmp buffers are freed on return
+  return TG_OK;
+}
+
+tg_status read_status(const tg_pattern* p, cudaStream_t s, const char* stage) {
+  unsigned long long h[2];
+  TG_CK(cudaMemcpyAsync(h, p->status, sizeof(h), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  if (h[0] != 0) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "%s: %s at element %llu", stage, tg_status_string((tg_status)h[0]), h[1]);
+    tg::set_error(buf);
+    return (tg_status)h[0];
+  }
+  return TG_OK;
+}
+
+}  // namespace
+
+extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int64_t n_nodes, tg_element el,
+                                      tg_stream stream, tg_pattern** out) {
+  if (!out) return TG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (el < TG_P1_TRI || el > TG_P1_TET_VEC3 || n_elems < 0 || n_nodes < 1) return TG_ERR_INVALID_ARG;
+  if (n_elems > 0 && !cells) return TG_ERR_INVALID_ARG;
+  const int nv = tg::nv_of(el);
+  if (n_nodes > INT32_MAX || n_elems >= (1ll << 28) || n_elems * nv > INT32_MAX) return TG_ERR_INDEX_OVERFLOW;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  tg_pattern* p = new tg_pattern;
+  p->el = el;
+  p->nv = nv;
+  p->dim = tg::dim_of(el);
+  p->nq = tg::nq_of(el);
+  p->ngeo = el == TG_P2_TRI ? 3 : nv;
+  p->npw = nv > 4 ? 2 : 1;
+  p->E = n_elems;
+  p->N = n_nodes;
+  struct Guard {
+    tg_pattern*& p;
+    bool ok = false;
+    ~Guard() {
+      if (!ok) tg_pattern_destroy(p);
+    }
+  } guard{p};
+  Tmp tmp;
+  const int64_t E = n_elems, N = n_nodes, nvE = n_elems * nv;
+
+  cudaError_t ce = cudaGetDevice(&p->device);
+  if (ce != cudaSuccess) return tg::cuda_fail(ce, "cudaGetDevice", __FILE__, __LINE__);
+  TG_CK(cudaMalloc(&p->status, 2 * sizeof(unsigned long long)));
+  const unsigned long long init[2] = {0ull, ~0ull};
+  TG_CK(cudaMemcpyAsync(p->status, init, sizeof(init), cudaMemcpyHostToDevice, s));
+  TG_CK(cudaMalloc(&p->cells, nvE * sizeof(int32_t) + 16));
+  if (nvE) TG_CK(cudaMemcpyAsync(p->cells, cells, nvE * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+
+  // 1. validation and incidence counts
+  int32_t* deg = nullptr;
+  TG_CK(tmp.alloc(&deg, N));
+  TG_CK(cudaMemsetAsync(deg, 0, N * sizeof(int32_t), s));
+  const int sms = tg::sm_count();
+  const int gE = (int)std::min<int64_t>(std::max<int64_t>(tg::grid_for(E, kThreads), 1), 16ll * sms);
+  if (E > 0) {
+    k_count<<<gE, kThreads, 0, s>>>(p->cells, E, nv, N, deg, p->status);
+    TG_CK_LAUNCH("k_count");
+  }
+  tg_status st = read_status(p, s, "tg_build_pattern");
+  if (st != TG_OK) return st;
+
+  // 2. incidence lists
+  int64_t* tmp64 = nullptr;
+  TG_CK(tmp.alloc(&tmp64, N + 1));
+  if ((st = scan_exclusive<int32_t>(deg, tmp64, N, s)) != TG_OK) return st;
+  TG_CK(cudaMalloc(&p->inc_ptr, (N + 1) * sizeof(int32_t)));
+  k_narrow<<<tg::grid_for(N + 1, kThreads), kThreads, 0, s>>>(tmp64, p->inc_ptr, N + 1);
+  TG_CK_LAUNCH("k_narrow");
+  TG_CK(cudaMalloc(&p->inc_e, nvE * sizeof(int32_t) + 16));
+  int32_t* cursor = deg;  // reuse: cursor starts at inc_ptr
+  TG_CK(cudaMemcpyAsync(cursor, p->inc_ptr, N * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  if (E > 0) {
+    k_fill<<<gE, kThreads, 0, s>>>(p->cells, E, nv, cursor, p->inc_e);
+    TG_CK_LAUNCH("k_fill");
+  }
+  k_sort_incidence<<<tg::grid_for(N, kThreads), kThreads, 0, s>>>(p->inc_ptr, p->inc_e, N);
+  TG_CK_LAUNCH("k_sort_incidence");
+
+  // 3. rows
+  int32_t* row_len = nullptr;
+  int* maxes = nullptr;
+  TG_CK(tmp.alloc(&row_len, N));
+  TG_CK(tmp.alloc(&maxes, 2));
+  TG_CK(cudaMemsetAsync(maxes, 0, 2 * sizeof(int), s));
+  const bool vec3 = el == TG_P1_TET_VEC3;
+  k_rows<false><<<tg::grid_for(N, 128), 128, 0, s>>>(p->cells, p->inc_ptr, p->inc_e, N, nv, p->npw, vec3, row_len,
+                                                      maxes, nullptr, nullptr, nullptr, nullptr, p->status);
+  TG_CK_LAUNCH("k_rows<false>");
+  int hmax[2];
+  TG_CK(cudaMemcpyAsync(hmax, maxes, sizeof(hmax), cudaMemcpyDeviceToHost, s));
+  if ((st = read_status(p, s, "tg_build_pattern (row longer than 255)")) != TG_OK) return st;
+  p->max_row_len = hmax[0];
+  p->max_deg = hmax[1];
+  if ((st = scan_exclusive<int32_t>(row_len, tmp64, N, s)) != TG_OK) return st;
+  int64_t nnz = 0;
+  TG_CK(cudaMemcpyAsync(&nnz, tmp64 + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  if (nnz > INT32_MAX || (vec3 && 9 * nnz > INT32_MAX)) {
+    tg::set_error("tg_build_pattern: nnz exceeds int32 indices");
+    return TG_ERR_INDEX_OVERFLOW;
+  }
+  p->nnz = nnz;
+  TG_CK(cudaMalloc(&p->row_ptr, (N + 1) * sizeof(int32_t)));
+  k_narrow<<<tg::grid_for(N + 1, kThreads), kThreads, 0, s>>>(tmp64, p->row_ptr, N + 1);
+  TG_CK_LAUNCH("k_narrow");
+
+  // 4. columns, positions, element-to-slot map
+  TG_CK(cudaMalloc(&p->col_idx, nnz * sizeof(int32_t) + 16));
+  TG_CK(cudaMalloc(&p->inc_pos, nvE * p->npw * sizeof(uint32_t) + 16));
+  TG_CK(cudaMalloc(&p->elem_slot, nvE * nv * sizeof(int32_t) + 16));
+  k_rows<true><<<tg::grid_for(N, 128), 128, 0, s>>>(p->cells, p->inc_ptr, p->inc_e, N, nv, p->npw, vec3, nullptr,
+                                                     nullptr, p->row_ptr, p->col_idx, p->inc_pos, p->elem_slot,
+                                                     p->status);
+  TG_CK_LAUNCH("k_rows<true>");
+
+  // 5. DoF-level CSR for elasticity
+  if (vec3) {
+    TG_CK(cudaMalloc(&p->row_ptr3, (3 * N + 1) * sizeof(int32_t)));
+    TG_CK(cudaMalloc(&p->col_idx3, 9 * nnz * sizeof(int32_t) + 16));
+    k_expand3<<<tg::grid_for(N, kThreads), kThreads, 0, s>>>(p->row_ptr, p->col_idx, N, p->row_ptr3, p->col_idx3);
+    TG_CK_LAUNCH("k_expand3");
+  }
+
+  // per-CTA partials of the backward's global sums (2 values per CTA)
+  p->n_partials = 2 * ((N + 127) / 128) + 2;
+  TG_CK(cudaMalloc(&p->partials, p->n_partials * sizeof(double)));
+  TG_CK(cudaStreamSynchronize(s));
+  if ((st = read_status(p, s, "tg_build_pattern")) != TG_OK) return st;
+  guard.ok = true;
+  *out = p;
+  return TG_OK;
+}

@@ -1,0 +1,254 @@
+// Support kernels: CSR matrix-vector product, deterministic dot products and
+// the conjugate-gradient solve of the Dirichlet-condensed system (the
+// iterative solve that follows assembly, SM B.1 solver configuration, and the
+// adjoint solve K^T lam = -dGamma/dU of Eq. (adj)); plus the FMA-rate probe
+// used to report the arithmetic roof.
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include "tg_internal.cuh"
+
+namespace {
+
+constexpr int ST = 256;
+
+// Four lanes per row, fixed-order shuffle sum.  Rows with mask[row] != 0
+// (Dirichlet) produce 0.
+template <typename T>
+__global__ void __launch_bounds__(ST) k_spmv(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                             const T* __restrict__ v, const T* __restrict__ x, T* __restrict__ y,
+                                             int64_t n, const uint8_t* __restrict__ mask) {
+  const int64_t t = (int64_t)blockIdx.x * ST + threadIdx.x;
+  const int64_t row = t >> 2;
+  const int lane = threadIdx.x & 3;
+  const unsigned grp = 0xfu << (threadIdx.x & 28);
+  if (row >= n) return;  // the four lanes of a row leave together
+  T s = T(0);
+  const int k1 = __ldg(rp + row + 1);
+  for (int k = __ldg(rp + row) + lane; k < k1; k += 4) s += __ldg(v + k) * __ldg(x + __ldg(ci + k));
+  s += __shfl_xor_sync(grp, s, 1, 4);
+  s += __shfl_xor_sync(grp, s, 2, 4);
+  if (lane == 0) y[row] = (mask && mask[row]) ? T(0) : s;
+}
+
+// Partial dot products (double accumulation) over a fixed grid; the final
+// kernel sums the partials in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(ST) k_dot_partial(const T* __restrict__ a, const T* __restrict__ b, int64_t n,
+                                                    double* __restrict__ partials) {
+  __shared__ double red[ST];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * ST + threadIdx.x; i < n; i += (int64_t)gridDim.x * ST)
+    s += (double)a[i] * (double)b[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = ST / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(ST) k_dot_final(const double* __restrict__ partials, int nb, double* __restrict__ out) {
+  __shared__ double red[ST];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nb; k += ST) s += partials[k];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = ST / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// r = mask ? 0 : F - Kx ;  b = mask ? 0 : F ;  x = mask ? 0 : x ;  p = r
+template <typename T>
+__global__ void k_cg_init(const T* __restrict__ F, const T* __restrict__ Kx, const uint8_t* __restrict__ mask,
+                          T* __restrict__ x, T* __restrict__ r, T* __restrict__ p, T* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * ST + threadIdx.x;
+  if (i >= n) return;
+  const bool d = mask && mask[i];
+  const T ri = d ? T(0) : F[i] - Kx[i];
+  r[i] = ri;
+  p[i] = ri;
+  b[i] = d ? T(0) : F[i];
+  if (d) x[i] = T(0);
+}
+
+// sc = {rr, pAp, rr_new}: x += alpha p, r -= alpha Ap, alpha = rr / pAp
+template <typename T>
+__global__ void k_cg_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ Ap,
+                        const double* __restrict__ sc, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * ST + threadIdx.x;
+  if (i >= n) return;
+  const T alpha = (T)(sc[0] / sc[1]);
+  x[i] += alpha * p[i];
+  r[i] -= alpha * Ap[i];
+}
+
+// p = r + beta p, beta = rr_new / rr
+template <typename T>
+__global__ void k_cg_p(T* __restrict__ p, const T* __restrict__ r, const double* __restrict__ sc, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * ST + threadIdx.x;
+  if (i >= n) return;
+  const T beta = (T)(sc[2] / sc[0]);
+  p[i] = r[i] + beta * p[i];
+}
+
+__global__ void k_cg_shift(double* sc) { sc[0] = sc[2]; }
+
+struct Dev {
+  std::vector<void*> bufs;
+  ~Dev() {
+    for (void* b : bufs) cudaFree(b);
+  }
+  cudaError_t alloc(void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) bufs.push_back(*p);
+    return e;
+  }
+};
+
+template <typename T>
+tg_status dot(const T* a, const T* b, int64_t n, double* partials, int nb, double* out, cudaStream_t s) {
+  k_dot_partial<T><<<nb, ST, 0, s>>>(a, b, n, partials);
+  k_dot_final<<<1, ST, 0, s>>>(partials, nb, out);
+  TG_CK_LAUNCH("k_dot");
+  return TG_OK;
+}
+
+template <typename T>
+tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8_t* mask, void* x_, double rtol,
+             int maxit, int* iters, double* relres, cudaStream_t s) {
+  const bool vec = p->el == TG_P1_TET_VEC3;
+  const int64_t n = vec ? 3 * p->N : p->N;
+  const int32_t* rp = vec ? p->row_ptr3 : p->row_ptr;
+  const int32_t* ci = vec ? p->col_idx3 : p->col_idx;
+  const T* vals = static_cast<const T*>(vals_);
+  const T* F = static_cast<const T*>(F_);
+  T* x = static_cast<T*>(x_);
+  Dev d;
+  T *r, *pp, *Ap, *b;
+  double *sc, *partials;
+  const int nb = 2 * tg::sm_count();
+  TG_CK(d.alloc((void**)&r, n * sizeof(T)));
+  TG_CK(d.alloc((void**)&pp, n * sizeof(T)));
+  TG_CK(d.alloc((void**)&Ap, n * sizeof(T)));
+  TG_CK(d.alloc((void**)&b, n * sizeof(T)));
+  TG_CK(d.alloc((void**)&sc, 4 * sizeof(double)));
+  TG_CK(d.alloc((void**)&partials, nb * sizeof(double)));
+  const int gv = tg::grid_for(n, ST), gs = tg::grid_for(4 * n, ST);
+  k_spmv<T><<<gs, ST, 0, s>>>(rp, ci, vals, x, Ap, n, mask);
+  k_cg_init<T><<<gv, ST, 0, s>>>(F, Ap, mask, x, r, pp, b, n);
+  TG_CK_LAUNCH("cg init");
+  tg_status st;
+  if ((st = dot<T>(b, b, n, partials, nb, sc + 3, s)) != TG_OK) return st;
+  if ((st = dot<T>(r, r, n, partials, nb, sc + 0, s)) != TG_OK) return st;
+  double h[4];
+  TG_CK(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  const double fnorm = std::sqrt(h[3]);
+  double rel = fnorm > 0 ? std::sqrt(h[0]) / fnorm : 0.0;
+  int it = 0;
+  while (fnorm > 0 && rel > rtol && it < maxit) {
+    k_spmv<T><<<gs, ST, 0, s>>>(rp, ci, vals, pp, Ap, n, mask);
+    if ((st = dot<T>(pp, Ap, n, partials, nb, sc + 1, s)) != TG_OK) return st;
+    k_cg_xr<T><<<gv, ST, 0, s>>>(x, r, pp, Ap, sc, n);
+    if ((st = dot<T>(r, r, n, partials, nb, sc + 2, s)) != TG_OK) return st;
+    k_cg_p<T><<<gv, ST, 0, s>>>(pp, r, sc, n);
+    k_cg_shift<<<1, 1, 0, s>>>(sc);
+    TG_CK_LAUNCH("cg iteration");
+    ++it;
+    if ((it & 7) == 0 || it == maxit) {
+      TG_CK(cudaMemcpyAsync(h, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+      TG_CK(cudaStreamSynchronize(s));
+      rel = std::sqrt(h[0]) / fnorm;
+    }
+  }
+  TG_CK(cudaMemcpyAsync(h, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  if (iters) *iters = it;
+  if (relres) *relres = fnorm > 0 ? std::sqrt(h[0]) / fnorm : 0.0;
+  return TG_OK;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_rate(T* __restrict__ out, int iters, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = T(threadIdx.x + k) * T(1e-3);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace
+
+extern "C" {
+
+tg_status tg_spmv(const tg_pattern* p, tg_dtype dtype, const void* vals, const void* x, void* y, tg_stream stream) {
+  if (!p || (dtype != TG_F32 && dtype != TG_F64) || !vals || !x || !y) return TG_ERR_INVALID_ARG;
+  const bool vec = p->el == TG_P1_TET_VEC3;
+  const int64_t n = vec ? 3 * p->N : p->N;
+  const int32_t* rp = vec ? p->row_ptr3 : p->row_ptr;
+  const int32_t* ci = vec ? p->col_idx3 : p->col_idx;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int g = tg::grid_for(4 * n, ST);
+  if (dtype == TG_F32)
+    k_spmv<float><<<g, ST, 0, s>>>(rp, ci, (const float*)vals, (const float*)x, (float*)y, n, nullptr);
+  else
+    k_spmv<double><<<g, ST, 0, s>>>(rp, ci, (const double*)vals, (const double*)x, (double*)y, n, nullptr);
+  TG_CK_LAUNCH("k_spmv");
+  return TG_OK;
+}
+
+tg_status tg_cg_solve(const tg_pattern* p, tg_dtype dtype, const void* vals, const void* F, const uint8_t* dirichlet,
+                      void* x, double rtol, int32_t maxit, int32_t* iters, double* relres, tg_stream stream) {
+  if (!p || (dtype != TG_F32 && dtype != TG_F64) || !vals || !F || !x || maxit < 0 || !(rtol >= 0))
+    return TG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int it = 0;
+  double rr = 0;
+  tg_status st = dtype == TG_F32 ? cg<float>(p, vals, F, dirichlet, x, rtol, maxit, &it, &rr, s)
+                                 : cg<double>(p, vals, F, dirichlet, x, rtol, maxit, &it, &rr, s);
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  return st;
+}
+
+tg_status tg_diag_fma_rate(tg_dtype dtype, double* flops, tg_stream stream) {
+  if (!flops || (dtype != TG_F32 && dtype != TG_F64)) return TG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int blocks = 8 * tg::sm_count(), threads = 256;
+  const int iters = dtype == TG_F64 ? 2048 : 65536;
+  void* out = nullptr;
+  TG_CK(cudaMalloc(&out, (size_t)blocks * threads * 8));
+  cudaEvent_t e0, e1;
+  TG_CK(cudaEventCreate(&e0));
+  TG_CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    TG_CK(cudaEventRecord(e0, s));
+    if (dtype == TG_F64) k_fma_rate<double><<<blocks, threads, 0, s>>>((double*)out, iters, 0.999999, 1e-6);
+    else k_fma_rate<float><<<blocks, threads, 0, s>>>((float*)out, iters, 0.999999f, 1e-6f);
+    TG_CK(cudaEventRecord(e1, s));
+    TG_CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    TG_CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  *flops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3);
+  return TG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// Internal declarations of libtg.so (GB300 / sm_103a Galerkin assembly).
+//
+// Data layout of a pattern in HBM (all int32 unless noted):
+//   cells    [E][nv]          copy of the connectivity
+//   inc_ptr  [N+1]            node -> incident (element, local index) list
+//   inc_e    [E*nv]           e * 8 + a, sorted by e within each node
+//   inc_pos  [E*nv][npw] u32  8-bit positions of the element's nv nodes in
+//                             the row of the owning node (npw = 1 for nv <= 4,
+//                             2 for P2); this is the routing S_mat of
+//                             Algorithm 2 in compressed, row-owned form
+//   row_ptr  [N+1], col_idx [nnz]   node-level CSR
+//   elem_slot [E][nv][nv]     CSR slot of each local entry (API view)
+//   row_ptr3 [3N+1], col_idx3 [9 nnz]  DoF-level CSR (vector elasticity)
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "tg.h"
+
+#define TG_MAX_ROW 255  // positions are stored in 8 bits
+
+struct tg_pattern {
+  tg_element el;
+  int nv = 0, dim = 0, nq = 0, ngeo = 0, npw = 1;
+  int64_t E = 0, N = 0, nnz = 0;
+  int device = 0;
+  int max_row_len = 0, max_deg = 0;
+  int32_t* cells = nullptr;
+  int32_t* inc_ptr = nullptr;
+  int32_t* inc_e = nullptr;
+  uint32_t* inc_pos = nullptr;
+  int32_t* row_ptr = nullptr;
+  int32_t* col_idx = nullptr;
+  int32_t* elem_slot = nullptr;
+  int32_t* row_ptr3 = nullptr;
+  int32_t* col_idx3 = nullptr;
+  // device status: [0] error code (first one wins), [1] smallest bad element
+  unsigned long long* status = nullptr;
+  // per-CTA partial sums of global reductions (backward of c / constant kappa)
+  double* partials = nullptr;
+  int64_t n_partials = 0;
+};
+
+namespace tg {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+tg_status cuda_fail(cudaError_t err, const char* what, const char* file, int line);
+
+#define TG_CK(call)                                                         \
+  do {                                                                      \
+    cudaError_t err__ = (call);                                             \
+    if (err__ != cudaSuccess) return tg::cuda_fail(err__, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define TG_CK_LAUNCH(what) TG_CK(cudaGetLastError())
+
+// ------------------------------------------------------------------ element traits
+template <int EL>
+struct Elem;
+template <>
+struct Elem<TG_P1_TRI> {
+  static constexpr int nv = 3, dim = 2, nq = 3, ngeo = 3, npw = 1;
+};
+template <>
+struct Elem<TG_P2_TRI> {
+  static constexpr int nv = 6, dim = 2, nq = 6, ngeo = 3, npw = 2;
+};
+template <>
+struct Elem<TG_P1_TET> {
+  static constexpr int nv = 4, dim = 3, nq = 4, ngeo = 4, npw = 1;
+};
+
+inline int nv_of(tg_element el) { return el == TG_P1_TRI ? 3 : el == TG_P2_TRI ? 6 : 4; }
+inline int dim_of(tg_element el) { return (el == TG_P1_TRI || el == TG_P2_TRI) ? 2 : 3; }
+inline int nq_of(tg_element el) { return el == TG_P1_TRI ? 3 : el == TG_P2_TRI ? 6 : 4; }
+
+// Reference tables of one element kind, built on the host from the
+// quadrature rule and the reference basis, passed to kernels by value.
+template <typename T>
+struct RefTab {
+  T w[6];          // quadrature weights (sum = reference measure)
+  T phi[6][6];     // phi[q][a]   basis value at point q
+  T gh[6][6][3];   // gh[q][a][s] reference gradient at point q
+  T M[6][6];       // sum_q w_q phi_a phi_b  (reference mass matrix)
+  T m1[6];         // sum_q w_q phi_a
+  T wsum;          // sum_q w_q
+};
+
+// Host-side: rule and tables of an element kind (kernel side of the code,
+// independent of the oracle).
+int quadrature_rule(tg_element el, double* w, double* x);
+template <typename T>
+RefTab<T> ref_table(tg_element el);
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ void record_error(unsigned long long* status, int code, long long e) {
+  atomicCAS(status, 0ull, (unsigned long long)code);
+  atomicMin(status + 1, (unsigned long long)e);
+}
+
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) {
+  return __ldg(p);
+}
+
+template <typename T>
+__host__ __device__ constexpr T det_tiny();
+template <>
+__host__ __device__ constexpr float det_tiny<float>() {
+  return 1e-37f;
+}
+template <>
+__host__ __device__ constexpr double det_tiny<double>() {
+  return 1e-300;
+}
+
+// Coefficient sum over quadrature points with the rule's weights.
+template <typename T, int NQ>
+__device__ __forceinline__ T weighted_coef(const T* __restrict__ v, int layout, int64_t e, const T (&w)[6], T wsum) {
+  if (layout == TG_PER_QP) {
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) s += w[q] * ldg(v + e * NQ + q);
+    return s;
+  } else if (layout == TG_PER_ELEMENT) {
+    return wsum * ldg(v + e);
+  }
+  return wsum * ldg(v);
+}
+
+template <typename T, int NQ>
+__device__ __forceinline__ T coef_q(const T* __restrict__ v, int layout, int64_t e, int q) {
+  if (layout == TG_PER_QP) return ldg(v + e * NQ + q);
+  if (layout == TG_PER_ELEMENT) return ldg(v + e);
+  return ldg(v);
+}
+
+inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+int sm_count();
+
+}  // namespace tg

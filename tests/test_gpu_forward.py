@@ -1,0 +1,245 @@
+"""GPU parity of the pattern and the forward assembly against the FP64 oracle."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import meshgen as mg
+import oracle as O
+from gpu_helpers import TOL, coef, dev, host_as, jittered_tri, mesh_for, relfro
+
+pytestmark = pytest.mark.gpu
+
+ELS = [mg.P1_TRI, mg.P2_TRI, mg.P1_TET]
+DTYPES = [torch.float64, torch.float32]
+
+
+@pytest.fixture(scope="module")
+def tg():
+    import paper_2602_05052_gb300 as tg
+    return tg
+
+
+# ---------------------------------------------------------------- pattern
+@pytest.mark.parametrize("el", ELS + [mg.P1_TET_VEC3])
+def test_pattern_bit_exact(tg, el):
+    m = mesh_for(el)
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, el)
+    if el == mg.P1_TET_VEC3:
+        ref = O.assemble_elasticity(m.cells, m.coords, np.ones(m.n_elems), np.ones(m.n_elems), O.PER_ELEMENT)
+    else:
+        ref = O.assemble_bilinear(el, m.cells, m.coords, np.ones(1), O.CONSTANT, 1.0)
+    assert p.nnz == ref.nnz
+    assert np.array_equal(p.row_ptr.cpu().numpy().astype(np.int64), ref.row_ptr)
+    assert np.array_equal(p.col_idx.cpu().numpy(), ref.col)
+    # element-to-slot map: slot (e, a, b) lies in row g_a at column g_b
+    es = p.elem_slot.cpu().numpy().reshape(m.n_elems, m.cells.shape[1], m.cells.shape[1]).astype(np.int64)
+    rows = ref.rows_of()
+    if el == mg.P1_TET_VEC3:
+        assert np.array_equal(rows[es] // 3, np.repeat(m.cells[:, :, None], 4, axis=2))
+        assert np.array_equal(ref.col[es] // 3, np.repeat(m.cells[:, None, :], 4, axis=1))
+        assert np.all(rows[es] % 3 == 0) and np.all(ref.col[es] % 3 == 0)
+    else:
+        nv = m.cells.shape[1]
+        assert np.array_equal(rows[es], np.repeat(m.cells[:, :, None], nv, axis=2))
+        assert np.array_equal(ref.col[es], np.repeat(m.cells[:, None, :], nv, axis=1))
+
+
+# ---------------------------------------------------------------- bilinear forms
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("layout", [mg.PER_QP, mg.PER_ELEMENT, mg.CONSTANT])
+@pytest.mark.parametrize("el", ELS)
+def test_bilinear_matches_oracle(tg, el, layout, dtype):
+    m = mesh_for(el)
+    nq = mg.NQ[el]
+    k = coef(layout, m.n_elems, nq, seed=10 + el)
+    c = 0.75
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, el)
+    vals = tg.tg_assemble_bilinear(p, dev(m.coords, dtype), dev(k, dtype), layout, c)
+    ref = O.assemble_bilinear(el, m.cells, host_as(m.coords, dtype), host_as(k, dtype), layout, c)
+    err = relfro(vals.cpu().numpy(), ref.val)
+    assert err <= TOL[dtype], err
+    assert tg.tg_get_device_status(p) == (0, -1)
+
+
+def test_structured_poisson_bit_exact(tg):
+    m = mg.tri_grid(64)
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
+    vals = tg.tg_assemble_bilinear(p, dev(m.coords, torch.float64), dev(np.ones(1), torch.float64), mg.CONSTANT, 0.0)
+    ref = O.assemble_bilinear(mg.P1_TRI, m.cells, m.coords, np.ones(1), O.CONSTANT, 0.0)
+    assert p.nnz == 29057
+    assert np.array_equal(vals.cpu().numpy(), ref.val)
+    F = tg.tg_assemble_load(p, dev(m.coords, torch.float64), dev(np.ones(1), torch.float64), mg.CONSTANT)
+    Fr = O.assemble_load(mg.P1_TRI, m.cells, m.coords, np.ones(1), O.CONSTANT)
+    assert relfro(F.cpu().numpy(), Fr) <= 1e-15
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_forward_is_bitwise_deterministic(tg, dtype):
+    m = jittered_tri(128)
+    k = mg.lognormal(m.n_elems * 3, 7)
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
+    x, kk = dev(m.coords, dtype), dev(k, dtype)
+    first = tg.tg_assemble_bilinear(p, x, kk, mg.PER_QP, 1.0).clone()
+    for _ in range(9):
+        again = tg.tg_assemble_bilinear(p, x, kk, mg.PER_QP, 1.0)
+        assert torch.equal(first, again)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("el", ELS)
+def test_atomic_variant_within_tolerance(tg, el, dtype):
+    m = mesh_for(el)
+    k = coef(mg.PER_QP, m.n_elems, mg.NQ[el], seed=3)
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, el)
+    a = tg.tg_assemble_bilinear_atomic(p, dev(m.coords, dtype), dev(k, dtype), mg.PER_QP, 0.5)
+    ref = O.assemble_bilinear(el, m.cells, host_as(m.coords, dtype), host_as(k, dtype), O.PER_QP, 0.5)
+    assert relfro(a.cpu().numpy(), ref.val) <= TOL[dtype]
+
+
+# ---------------------------------------------------------------- load vector
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("layout", [mg.PER_NODE, mg.PER_QP, mg.CONSTANT])
+@pytest.mark.parametrize("el", ELS + [mg.P1_TET_VEC3])
+def test_load_matches_oracle(tg, el, layout, dtype):
+    m = mesh_for(el)
+    ncomp = 3 if el == mg.P1_TET_VEC3 else 1
+    nq = mg.NQ[el]
+    g = np.random.default_rng(20 + el)
+    n = {mg.PER_NODE: m.n_nodes, mg.PER_QP: m.n_elems * nq, mg.CONSTANT: 1}[layout] * ncomp
+    f = g.uniform(-1, 1, size=n)
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, el)
+    F = tg.tg_assemble_load(p, dev(m.coords, dtype), dev(f, dtype), layout, ncomp)
+    ref = O.assemble_load(el, m.cells, host_as(m.coords, dtype), host_as(f, dtype), layout, ncomp)
+    assert relfro(F.cpu().numpy(), ref) <= TOL[dtype]
+
+
+# ---------------------------------------------------------------- elasticity
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("layout", [mg.PER_ELEMENT, mg.PER_QP])
+def test_elasticity_matches_oracle(tg, layout, dtype):
+    m = mesh_for(mg.P1_TET_VEC3)
+    lam = coef(layout, m.n_elems, 4, seed=31, lo=0.5, hi=2.0)
+    mu = coef(layout, m.n_elems, 4, seed=32, lo=0.3, hi=1.0)
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TET_VEC3)
+    vals = tg.tg_assemble_elasticity(p, dev(m.coords, dtype), dev(lam, dtype), dev(mu, dtype), layout)
+    ref = O.assemble_elasticity(m.cells, host_as(m.coords, dtype), host_as(lam, dtype), host_as(mu, dtype), layout)
+    assert p.nnz == ref.nnz
+    assert relfro(vals.cpu().numpy(), ref.val) <= TOL[dtype]
+
+
+# ---------------------------------------------------------------- full-size workloads, sampled rows
+def _sampled_rows_check(tg, p, vals, ref_fn, n_rows, rows_per_node, seed, tol):
+    g = np.random.default_rng(seed)
+    nodes = np.unique(g.integers(0, n_rows // rows_per_node, size=400))
+    mask = np.zeros(n_rows // rows_per_node, np.uint8)
+    mask[nodes] = 1
+    ref = ref_fn(mask)
+    rp = p.row_ptr.cpu().numpy().astype(np.int64)
+    v = vals.cpu().numpy()
+    got, want = [], []
+    for nd in nodes:
+        for r in range(rows_per_node * nd, rows_per_node * nd + rows_per_node):
+            assert rp[r + 1] - rp[r] == ref.row_ptr[r + 1] - ref.row_ptr[r]
+            got.append(v[rp[r]:rp[r + 1]])
+            want.append(ref.val[ref.row_ptr[r]:ref.row_ptr[r + 1]])
+            assert np.array_equal(p.col_idx[int(rp[r]):int(rp[r + 1])].cpu().numpy(),
+                                  ref.col[ref.row_ptr[r]:ref.row_ptr[r + 1]])
+    assert relfro(np.concatenate(got), np.concatenate(want)) <= tol
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_diffusion2d_full_size_sampled(tg, dtype):
+    cfg = mg.diffusion2d(1024)
+    m = cfg["mesh"]
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
+    assert p.nnz == 7346177
+    vals = tg.tg_assemble_bilinear(p, dev(m.coords, dtype), dev(cfg["kappa"], dtype), mg.PER_QP, cfg["c"])
+    xs, ks = host_as(m.coords, dtype), host_as(cfg["kappa"], dtype)
+    _sampled_rows_check(tg, p, vals,
+                        lambda mask: O.assemble_bilinear(O.P1_TRI, m.cells, xs, ks, O.PER_QP, cfg["c"], row_mask=mask),
+                        m.n_nodes, 1, 5, TOL[dtype])
+    F = tg.tg_assemble_load(p, dev(m.coords, dtype), dev(cfg["f"], dtype), mg.PER_NODE)
+    Fr = O.assemble_load(O.P1_TRI, m.cells, xs, host_as(cfg["f"], dtype), O.PER_NODE)
+    assert relfro(F.cpu().numpy(), Fr) <= TOL[dtype]
+    assert tg.tg_get_device_status(p) == (0, -1)
+
+
+def test_elasticity3d_full_size_sampled(tg):
+    cfg = mg.elasticity3d(64)
+    m = cfg["mesh"]
+    dtype = torch.float32
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TET_VEC3)
+    assert p.nnz == 36168777
+    vals = tg.tg_assemble_elasticity(p, dev(m.coords, dtype), dev(cfg["lam"], dtype), dev(cfg["mu"], dtype),
+                                     mg.PER_ELEMENT)
+    xs, ls, ms = host_as(m.coords, dtype), host_as(cfg["lam"], dtype), host_as(cfg["mu"], dtype)
+    _sampled_rows_check(tg, p, vals,
+                        lambda mask: O.assemble_elasticity(m.cells, xs, ls, ms, O.PER_ELEMENT, row_mask=mask),
+                        3 * m.n_nodes, 3, 6, TOL[dtype])
+
+
+# ---------------------------------------------------------------- edge cases
+def test_empty_mesh(tg):
+    cells = torch.empty((0, 3), dtype=torch.int32, device="cuda")
+    p = tg.tg_build_pattern(cells, 5, mg.P1_TRI)
+    assert p.nnz == 0 and p.max_row_len == 0
+    assert torch.all(p.row_ptr == 0)
+    x = torch.zeros((5, 2), dtype=torch.float64, device="cuda")
+    vals = tg.tg_assemble_bilinear(p, x, torch.ones(1, dtype=torch.float64, device="cuda"), mg.CONSTANT, 1.0)
+    assert vals.numel() == 0
+    F = tg.tg_assemble_load(p, x, torch.ones(1, dtype=torch.float64, device="cuda"), mg.CONSTANT)
+    assert torch.all(F == 0)
+
+
+def test_single_element_each_kind(tg):
+    cases = [(mg.P1_TRI, [[0, 1, 2]], [[0, 0], [1, 0], [0.25, 0.8]]),
+             (mg.P2_TRI, [[0, 1, 2, 3, 4, 5]], [[0, 0], [1, 0], [0.25, 0.8], [0.5, 0], [0.625, 0.4], [0.125, 0.4]]),
+             (mg.P1_TET, [[0, 1, 2, 3]], [[0, 0, 0], [1, 0, 0], [0.2, 0.9, 0], [0.1, 0.2, 0.7]])]
+    for el, cells, X in cases:
+        cells, X = np.array(cells), np.array(X, float)
+        p = tg.tg_build_pattern(dev(cells, torch.int32), X.shape[0], el)
+        v = tg.tg_assemble_bilinear(p, dev(X, torch.float64), dev([1.3], torch.float64), mg.CONSTANT, 0.4)
+        ref = O.assemble_bilinear(el, cells, X, np.array([1.3]), O.CONSTANT, 0.4)
+        assert relfro(v.cpu().numpy(), ref.val) <= 1e-14
+
+
+def test_degenerate_element_is_flagged(tg):
+    m = mg.tri_grid(8)  # dyadic coordinates: the collinear triangle has det exactly 0
+    X = m.coords.copy()
+    e_bad = 17
+    a, b, c = m.cells[e_bad]
+    X[c] = 0.5 * (X[a] + X[b])
+    P = X[m.cells]
+    det = (P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1]) - (P[:, 1, 1] - P[:, 0, 1]) * (P[:, 2, 0] - P[:, 0, 0])
+    assert np.flatnonzero(det == 0).min() == e_bad
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
+    tg.tg_assemble_bilinear(p, dev(X, torch.float64), dev([1.0], torch.float64), mg.CONSTANT, 0.0)
+    st, bad = tg.tg_get_device_status(p)
+    assert st == 3 and bad == e_bad
+    assert tg.tg_get_device_status(p) == (0, -1)  # read clears
+
+
+def test_bad_cells_rejected_at_build(tg):
+    m = mg.tri_grid(4)
+    cells = m.cells.copy()
+    cells[5, 1] = m.n_nodes + 3
+    with pytest.raises(tg.TGError) as ei:
+        tg.tg_build_pattern(dev(cells, torch.int32), m.n_nodes, mg.P1_TRI)
+    assert ei.value.status == 2 and "element 5" in str(ei.value)
+    cells = m.cells.copy()
+    cells[7, 2] = cells[7, 0]
+    with pytest.raises(tg.TGError) as ei:
+        tg.tg_build_pattern(dev(cells, torch.int32), m.n_nodes, mg.P1_TRI)
+    assert ei.value.status == 3 and "element 7" in str(ei.value)
+
+
+def test_wrong_kind_and_dtype_rejected(tg):
+    m = mesh_for(mg.P1_TET_VEC3)
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TET_VEC3)
+    with pytest.raises(tg.TGError):
+        tg.tg_assemble_bilinear(p, dev(m.coords, torch.float64), dev([1.0], torch.float64), mg.CONSTANT, 0.0)
+    with pytest.raises(TypeError):
+        tg.tg_assemble_elasticity(p, dev(m.coords, torch.float64), dev([1.0], torch.float32), dev([1.0], torch.float64),
+                                  mg.CONSTANT)
