@@ -1,0 +1,459 @@
+"""Benchmark of the Galerkin-assembly hot path on one GB300 (or N replicas).
+
+Step = one pass of the hot path over the 2D diffusion workload (P1
+triangles, 1024 x 1024 jittered grid, Hilbert element order, lognormal kappa
+at 3 points per element, c = 1, f ~ U(-1, 1) per node; 2,097,152 elements),
+FP32: forward stiffness values (fused Map + deterministic Reduce), load
+vector, and the backward assembly for an upstream gradient of the values
+(grad kappa, grad coords, grad c).  Inputs live in HBM before timing; L2 is
+flushed between steps (outside the per-step CUDA events).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the same workload instead.  Under torchrun every rank runs its own
+replica (no data-path collective: weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import meshgen as mg  # noqa: E402
+
+METRIC = "elements assembled/sec and achieved HBM GB/s (fwd, fwd+bwd, batched vs looped)"
+WORKLOAD = ("2D diffusion, P1 triangles, 1024x1024 grid jittered +-0.2h, Hilbert element order, "
+            "kappa lognormal at 3 points per element, c=1, f~U(-1,1) per node")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / elasticity / batched breakdown")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ workload
+def workload(n=1024):
+    cfg = mg.diffusion2d(n)
+    m = cfg["mesh"]
+    return m, cfg
+
+
+def alg_bytes(kind, E, N, nnz, s, nv=3, Q=3, d=2):
+    """Compulsory bytes: read cells, coords and coefficients once, write outputs once."""
+    if kind == "fwd":
+        return E * nv * 4 + N * d * s + E * Q * s + nnz * s
+    if kind == "load":
+        return E * nv * 4 + N * d * s + N * s + N * s
+    if kind == "bwd":
+        return E * nv * 4 + N * d * s + E * Q * s + nnz * s + E * Q * s + N * d * s
+    if kind == "elastic":
+        return E * 4 * 4 + N * 3 * s + 2 * E * s + nnz * s
+    raise ValueError(kind)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_2602_05052_gb300", "csrc")
+    for f in sorted(os.listdir(cs)):
+        with open(os.path.join(cs, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernels changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("source_hash") != source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel_key)
+    return None if k is None else k.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ reference arm: the CPU oracle
+def oracle_step(m, cfg, G):
+    import oracle as O
+    K = O.assemble_bilinear(O.P1_TRI, m.cells, m.coords, cfg["kappa"], O.PER_QP, cfg["c"])
+    O.assemble_load(O.P1_TRI, m.cells, m.coords, cfg["f"], O.PER_NODE)
+    O.assemble_backward(O.P1_TRI, m.cells, m.coords, cfg["kappa"], O.PER_QP, cfg["c"],
+                        grad_csr=O.CSR(K.row_ptr, K.col, G))
+    return K.nnz
+
+
+def cpu_oracle_rate(m, cfg, reps):
+    nnz = int(m.n_nodes + 2 * (3 * 1024 ** 2 + 2 * 1024))
+    G = np.random.default_rng(0).normal(size=nnz)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle_step(m, cfg, G)
+    dt = time.perf_counter() - t0
+    return m.n_elems * reps / dt, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    m, cfg = workload()
+    G = np.random.default_rng(0).normal(size=int(m.n_nodes + 2 * (3 * 1024 ** 2 + 2 * 1024)))
+    for _ in range(args.warmup):
+        oracle_step(m, cfg, G)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(m, cfg, G)
+    dt = time.perf_counter() - t0
+    v = m.n_elems * args.steps / dt
+    sample = f"the full workload ({m.n_elems} elements) per step; forward, load and backward by the FP64 oracle"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "elements/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "elements": m.n_elems, "nodes": m.n_nodes},
+        "cpu_baseline": {"value": v, "unit": "elements/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    import paper_2602_05052_gb300 as tg
+    from paper_2602_05052_gb300 import build
+    build.build_library()
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    dt = torch.float32
+    s = 4
+    m, cfg = workload()
+    E, N = m.n_elems, m.n_nodes
+    d = lambda a, t=dt: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device=dev)
+    p = tg.tg_build_pattern(d(m.cells, torch.int32), N, tg.P1_TRI)
+    nnz = p.nnz
+    coords, kappa, f = d(m.coords), d(cfg["kappa"]), d(cfg["f"])
+    gvals = d(np.random.default_rng(1).normal(size=nnz))
+    vals = torch.empty(nnz, dtype=dt, device=dev)
+    F = torch.empty(N, dtype=dt, device=dev)
+    gk, gx, gc = torch.empty_like(kappa), torch.empty_like(coords), torch.empty(1, dtype=dt, device=dev)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    c = cfg["c"]
+
+    def step(ev=None):
+        if ev:
+            ev[0].record()
+        tg.tg_assemble_bilinear(p, coords, kappa, tg.PER_QP, c, vals)
+        if ev:
+            ev[1].record()
+        tg.tg_assemble_load(p, coords, f, tg.PER_NODE, 1, F)
+        if ev:
+            ev[2].record()
+        tg.tg_assemble_backward(p, coords, kappa, tg.PER_QP, c, grad_vals=gvals, grad_kappa=gk, grad_coords=gx,
+                                grad_c=gc)
+        if ev:
+            ev[3].record()
+
+    launches_per_step = 4  # forward gather, load gather, backward gather, backward final sum
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            step(evs[k])
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - w0
+    clocks = clk.summary()
+    t_fwd = [e[0].elapsed_time(e[1]) for e in evs]
+    t_load = [e[1].elapsed_time(e[2]) for e in evs]
+    t_bwd = [e[2].elapsed_time(e[3]) for e in evs]
+    t_step = [a + b + c_ for a, b, c_ in zip(t_fwd, t_load, t_bwd)]
+    ms = max_over_ranks(sum(t_step) / args.steps)
+    value = world * E / (ms * 1e-3)
+    st, bad = tg.tg_get_device_status(p)
+    if st != 0:
+        raise RuntimeError(f"device status {st} at element {bad}")
+
+    peak, peak_src = load_peaks()
+    kern = {"fwd": (statistics.mean(t_fwd), alg_bytes("fwd", E, N, nnz, s)),
+            "load": (statistics.mean(t_load), alg_bytes("load", E, N, nnz, s)),
+            "bwd": (statistics.mean(t_bwd), alg_bytes("bwd", E, N, nnz, s))}
+    dom = max(kern, key=lambda k: kern[k][0])
+    names = {"fwd": "k_bilinear_gather<P1_TRI,float>", "load": "k_load_gather<P1_TRI,float,1>",
+             "bwd": "k_backward_gather<P1_TRI,float,gvals>"}
+    ach = kern[dom][1] / (kern[dom][0] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": ncu_traffic(dom), "peak_source": f"{peak_src} (copy, burst)",
+                "algorithmic_bytes_per_launch": kern[dom][1]}
+    per_kernel = {k: {"ms": v[0], "alg_GBps": v[1] / (v[0] * 1e-3) / 1e9, "frac_of_peak": v[1] / (v[0] * 1e-3) / 1e9 / peak,
+                      "elements_per_s": E / (v[0] * 1e-3)} for k, v in kern.items()}
+
+    # ---------------- end to end: pinned host inputs -> C-ABI calls -> host results
+    h_in = [t.cpu().pin_memory() for t in (coords, kappa, f, gvals)]
+    h_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (vals, F, gk, gx, gc)]
+    bi = sum(t.numel() * t.element_size() for t in h_in)
+    bo = sum(t.numel() * t.element_size() for t in h_out)
+
+    def e2e_step():
+        for hd, dd in zip(h_in, (coords, kappa, f, gvals)):
+            dd.copy_(hd, non_blocking=True)
+        step()
+        for hd, dd in zip(h_out, (vals, F, gk, gx, gc)):
+            hd.copy_(dd, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+
+    out = {"metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
+           "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "elements": E, "nodes": N, "nnz": nnz,
+                      "step": "forward K values + load vector F + backward (grad kappa, grad coords, grad c) "
+                              "for an upstream gradient of the values",
+                      "l2": "flushed (512 MB write) between steps, outside the per-step CUDA events",
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+           "wall_s_timed_region": wall, "gpu_launches": launches_per_step * args.steps,
+           "roofline": roofline, "kernels": per_kernel,
+           "e2e": {"value": world * E / (e2e_ms * 1e-3), "unit": "elements/s", "h2d_bytes_per_step": bi,
+                   "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms},
+           "clocks": clocks}
+
+    if not args.no_extras and rank == 0:
+        out["breakdown"] = extras(tg, torch, dev, m, cfg, p, peak, flush)
+    if not args.no_cpu_baseline and rank == 0:
+        reps = 3
+        rate, secs = cpu_oracle_rate(m, cfg, reps)
+        out["cpu_baseline"] = {"value": rate, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{reps} passes over the full workload ({E} elements: forward DOK "
+                                         f"scatter-add, load, backward), {secs:.1f} s, FP64, one host core"}
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def timed(torch, fn, flush, reps=10, warm=3):
+    """Median of per-call CUDA-event times, L2 flushed before each call."""
+    for _ in range(warm):
+        flush.zero_()
+        fn()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def extras(tg, torch, dev, m, cfg, p, peak, flush):
+    """Breakdown: FP64, atomic comparison, elasticity, batched vs looped."""
+    out = {}
+    E, N, nnz = m.n_elems, m.n_nodes, p.nnz
+    for dtn, dt, s in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
+        d = lambda a, t=dt: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device=dev)
+        x, k, f = d(m.coords), d(cfg["kappa"]), d(cfg["f"])
+        v = torch.empty(nnz, dtype=dt, device=dev)
+        gv = d(np.random.default_rng(1).normal(size=nnz))
+        ms_f = timed(torch, lambda: tg.tg_assemble_bilinear(p, x, k, tg.PER_QP, 1.0, v), flush)
+        ms_a = timed(torch, lambda: tg.tg_assemble_bilinear_atomic(p, x, k, tg.PER_QP, 1.0, v), flush)
+        ms_b = timed(torch, lambda: tg.tg_assemble_backward(p, x, k, tg.PER_QP, 1.0, grad_vals=gv), flush)
+        ms_l = timed(torch, lambda: tg.tg_assemble_load(p, x, f, tg.PER_NODE), flush)
+        bf, bb = alg_bytes("fwd", E, N, nnz, s), alg_bytes("bwd", E, N, nnz, s)
+        out[f"diffusion2d_{dtn}"] = {
+            "fwd_ms": ms_f, "fwd_elements_per_s": E / ms_f * 1e3, "fwd_alg_GBps": bf / ms_f / 1e6,
+            "fwd_frac_hbm": bf / ms_f / 1e6 / peak,
+            "atomic_fwd_ms": ms_a, "gather_vs_atomic_speedup": ms_a / ms_f,
+            "bwd_ms": ms_b, "bwd_alg_GBps": bb / ms_b / 1e6, "bwd_frac_hbm": bb / ms_b / 1e6 / peak,
+            "fwd_plus_bwd_elements_per_s": E / (ms_f + ms_b) * 1e3, "load_ms": ms_l}
+    out["fp64_fma_peak_tflops"] = tg.tg_diag_fma_rate(torch.float64) / 1e12
+    out["fp32_fma_peak_tflops"] = tg.tg_diag_fma_rate(torch.float32) / 1e12
+    # elasticity 64^3
+    ce = mg.elasticity3d(64)
+    me = ce["mesh"]
+    pe = tg.tg_build_pattern(torch.as_tensor(me.cells, device=dev), me.n_nodes, tg.P1_TET_VEC3)
+    for dtn, dt, s in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
+        d = lambda a, t=dt: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device=dev)
+        x, lam, mu = d(me.coords), d(ce["lam"]), d(ce["mu"])
+        v = torch.empty(pe.nnz, dtype=dt, device=dev)
+        ms_e = timed(torch, lambda: tg.tg_assemble_elasticity(pe, x, lam, mu, tg.PER_ELEMENT, v), flush)
+        be = alg_bytes("elastic", me.n_elems, me.n_nodes, pe.nnz, s)
+        out[f"elasticity3d_{dtn}"] = {"ms": ms_e, "elements_per_s": me.n_elems / ms_e * 1e3,
+                                      "alg_GBps": be / ms_e / 1e6, "frac_hbm": be / ms_e / 1e6 / peak}
+    del pe
+    # batched P2: 256 instances, one persistent launch vs 256 launches
+    insts = mg.batched_p2(256, seed=4)
+    dt = torch.float32
+    pats, xs, ks, vs = [], [], [], []
+    tot_e = tot_b = 0
+    for ins in insts:
+        mi = ins["mesh"]
+        pi = tg.tg_build_pattern(torch.as_tensor(mi.cells, device=dev), mi.n_nodes, tg.P2_TRI)
+        pats.append(pi)
+        xs.append(torch.as_tensor(mi.coords, dtype=dt, device=dev))
+        ks.append(torch.as_tensor(ins["kappa"], dtype=dt, device=dev))
+        vs.append(torch.empty(pi.nnz, dtype=dt, device=dev))
+        tot_e += mi.n_elems
+        tot_b += alg_bytes("fwd", mi.n_elems, mi.n_nodes, pi.nnz, 4, nv=6, Q=6)
+    b = tg.tg_batch_create(pats)
+    cs = [0.0] * len(pats)
+    tune_ms = tg.tg_batch_autotune(b, xs, ks, tg.PER_QP, cs, vs, reps=3)
+    ms_b = timed(torch, lambda: tg.tg_batch_assemble(b, xs, ks, tg.PER_QP, cs, vs), flush)
+
+    def looped():
+        for pi, xi, ki, vi in zip(pats, xs, ks, vs):
+            tg.tg_assemble_bilinear(pi, xi, ki, tg.PER_QP, 0.0, vi)
+
+    ms_l = timed(torch, looped, flush, reps=5)
+    g_b, g_l = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(g_b, stream=st):
+        tg.tg_batch_assemble(b, xs, ks, tg.PER_QP, cs, vs, stream=st)
+    with torch.cuda.graph(g_l, stream=st):
+        for pi, xi, ki, vi in zip(pats, xs, ks, vs):
+            tg.tg_assemble_bilinear(pi, xi, ki, tg.PER_QP, 0.0, vi, stream=st)
+    torch.cuda.synchronize()
+    ms_bg = timed(torch, g_b.replay, flush)
+    ms_lg = timed(torch, g_l.replay, flush)
+    ref = [v.clone() for v in vs]
+    looped()
+    same = all(torch.equal(a, b_) for a, b_ in zip(ref, vs))
+    out["batched_p2_f32"] = {
+        "instances": len(pats), "elements": tot_e, "alg_bytes": tot_b, "schedule": b.schedule(),
+        "autotune_best_ms": tune_ms,
+        "batched_ms": ms_b, "batched_graph_ms": ms_bg, "looped_ms": ms_l, "looped_graph_ms": ms_lg,
+        "batched_elements_per_s": tot_e / ms_b * 1e3, "batched_alg_GBps": tot_b / ms_b / 1e6,
+        "batched_frac_hbm": tot_b / ms_b / 1e6 / peak, "speedup_vs_looped": ms_l / ms_b,
+        "speedup_vs_looped_graph": ms_lg / ms_bg, "bitwise_equal_to_looped": same}
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -113,7 +113,8 @@ int32_t tg_quadrature(tg_element el, double* w, double* xhat);
  *   out       receives a new pattern; release it with tg_pattern_destroy().
  * Allocates device memory and SYNCHRONISES the stream.  Index errors and
  * repeated vertices are returned directly (TG_ERR_INDEX_RANGE,
- * TG_ERR_DEGENERATE_ELEMENT; tg_get_device_status gives the element).
+ * TG_ERR_DEGENERATE_ELEMENT, *out stays NULL); tg_last_error_message()
+ * names the smallest offending element.
  * Rows longer than 255 entries return TG_ERR_UNSUPPORTED. */
 tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int64_t n_nodes, tg_element el,
                            tg_stream stream, tg_pattern** out);
@@ -198,6 +199,16 @@ tg_status tg_assemble_backward(const tg_pattern* p, tg_dtype dtype, const void* 
                                const void* U, void* grad_kappa, void* grad_coords, void* grad_c,
                                tg_stream stream);
 
+/* Backward of the load vector (second line of Eq. (matlclquad)).  For an
+ * upstream gradient grad_F [N * ncomp] of F, computes
+ *   grad_f       same layout as f (PER_NODE, PER_QP or CONSTANT), or NULL;
+ *   grad_coords  [N][d] (only |det J| depends on the coordinates), or NULL.
+ * accumulate != 0 adds to grad_f / grad_coords instead of overwriting them
+ * (used to sum the load and bilinear contributions of one objective). */
+tg_status tg_assemble_load_backward(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* f,
+                                    tg_layout f_layout, int32_t ncomp, const void* grad_F, void* grad_f,
+                                    void* grad_coords, int32_t accumulate, tg_stream stream);
+
 /* ------------------------------------------------------------------------
  * Support: CSR products and the conjugate-gradient solve of the condensed
  * system (SM B.1 solver configuration; used by the adjoint of Eq. (adj)).
@@ -205,6 +216,12 @@ tg_status tg_assemble_backward(const tg_pattern* p, tg_dtype dtype, const void* 
 
 /* y = K x over the pattern's CSR (DoF level for elasticity). */
 tg_status tg_spmv(const tg_pattern* p, tg_dtype dtype, const void* vals, const void* x, void* y, tg_stream stream);
+
+/* out[s] = alpha * lam[row(s)] * U[col(s)] for every CSR slot s: the adjoint
+ * outer product dGamma/dK = lam U^T of Eq. (adj) on the pattern (DoF level
+ * for elasticity).  lam, U [n_rows]; out [nnz]. */
+tg_status tg_csr_outer(const tg_pattern* p, tg_dtype dtype, const void* lam, const void* U, double alpha, void* out,
+                       tg_stream stream);
 
 /* Conjugate gradients on K x = F restricted to the rows/columns where
  * dirichlet[i] == 0 (uint8 [n_rows], or NULL for none); entries of x on

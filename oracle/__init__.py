@@ -71,6 +71,8 @@ def lib():
         L.orc_assemble_load.argtypes = [i32, i64, i64, vp, vp, vp, i32, i32, vp]
         L.orc_assemble_backward.restype = i32
         L.orc_assemble_backward.argtypes = [i32, i64, i64, vp, vp, vp, i32, d, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_load_backward.restype = i32
+        L.orc_load_backward.argtypes = [i32, i64, i64, vp, vp, vp, i32, i32, vp, vp, vp]
         L.orc_elasticity_backward.restype = i32
         L.orc_elasticity_backward.argtypes = [i64, i64, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         _lib = L
@@ -232,3 +234,19 @@ def elasticity_backward(cells, coords, lam, mu, layout, grad_csr: CSR | None = N
     lib().orc_elasticity_backward(E, N, _p(cells), _p(coords), _p(lam), _p(mu), layout, _p(rp), _p(col), _p(val),
                                   _p(la), _p(Up), _p(gl), _p(gm), _p(gx))
     return gl, gm, gx.reshape(N, 3)
+
+
+def load_backward(el, cells, coords, f, f_layout, ncomp, gF):
+    """Returns (grad_f, grad_coords [N, d]) of L = gF . F."""
+    cells = _i32(cells)
+    coords = _f64(coords)
+    f = _f64(np.atleast_1d(f))
+    gF = _f64(gF)
+    E, N = cells.shape[0], coords.shape[0]
+    nq = NQ[el]
+    nf = E * nq * ncomp if f_layout == PER_QP else N * ncomp if f_layout == PER_NODE else ncomp
+    gf = np.zeros(nf)
+    d = DIM[el]
+    gx = np.zeros(N * d)
+    lib().orc_load_backward(el, E, N, _p(cells), _p(coords), _p(f), f_layout, ncomp, _p(gF), _p(gf), _p(gx))
+    return gf, gx.reshape(N, d)

@@ -538,6 +538,61 @@ int orc_assemble_backward(int el, int64_t E, int64_t N, const int32_t* cells, co
   return 0;
 }
 
+// Gradients of L = sum_i sum_k gF[i*ncomp + k] F[i*ncomp + k] for the load
+// vector: grad_f (layout of f) and grad_coords [N][dim] (overwritten).  F
+// depends on the coordinates through |det J| only: dL/dJ = L_e J^{-T}.
+int orc_load_backward(int el, int64_t E, int64_t N, const int32_t* cells, const double* coords, const double* f,
+                      int f_layout, int ncomp, const double* gF, double* grad_f, double* grad_coords) {
+  const int gel = (el == EL_P1_TET_VEC3) ? EL_P1_TET : el;
+  const Rule R = rule_for(gel);
+  const int nv = nv_of(gel), dim = dim_of(gel);
+  const int64_t nf = f_layout == LAYOUT_PER_QP ? E * R.nq * ncomp : f_layout == LAYOUT_PER_NODE ? N * ncomp : ncomp;
+  if (grad_f)
+    for (int64_t i = 0; i < nf; ++i) grad_f[i] = 0.0;
+  if (grad_coords)
+    for (int64_t i = 0; i < N * dim; ++i) grad_coords[i] = 0.0;
+  std::vector<double> X(nv * dim);
+  for (int64_t e = 0; e < E; ++e) {
+    gather_X(dim, nv, cells, coords, e, X.data());
+    const Geo g = geometry(dim, X.data());
+    const double adet = std::fabs(g.det);
+    double Le = 0.0;
+    for (int q = 0; q < R.nq; ++q) {
+      double phi[6], dphi[18];
+      basis(gel, &R.x[q * dim], phi, dphi);
+      for (int k = 0; k < ncomp; ++k) {
+        // s = sum_a gF[g_a, k] phi_a(x_q): the weight of f_k(x_q) in L
+        double s = 0.0;
+        for (int a = 0; a < nv; ++a) s += gF[(int64_t)cells[e * nv + a] * ncomp + k] * phi[a];
+        double fq;
+        if (f_layout == LAYOUT_PER_QP) {
+          fq = f[(e * R.nq + q) * ncomp + k];
+          if (grad_f) grad_f[(e * R.nq + q) * ncomp + k] += R.w[q] * adet * s;
+        } else if (f_layout == LAYOUT_PER_NODE) {
+          fq = 0.0;
+          for (int b = 0; b < nv; ++b) {
+            fq += f[(int64_t)cells[e * nv + b] * ncomp + k] * phi[b];
+            if (grad_f) grad_f[(int64_t)cells[e * nv + b] * ncomp + k] += R.w[q] * adet * s * phi[b];
+          }
+        } else {
+          fq = f[k];
+          if (grad_f) grad_f[k] += R.w[q] * adet * s;
+        }
+        Le += R.w[q] * adet * fq * s;
+      }
+    }
+    if (grad_coords) {
+      for (int j = 0; j < dim; ++j)
+        for (int r = 0; r < dim; ++r) {
+          const double v = Le * g.Jinv[j][r];  // (L_e J^{-T})[r][j]
+          grad_coords[(int64_t)cells[e * nv + j + 1] * dim + r] += v;
+          grad_coords[(int64_t)cells[e * nv + 0] * dim + r] -= v;
+        }
+    }
+  }
+  return 0;
+}
+
 // Gradients of L = sum_e sum W^e K^e for vector P1 elasticity with respect to
 // lambda, mu (layout PER_ELEMENT or PER_QP) and the coordinates.  W^e is
 // looked up in (g_row_ptr, g_col, gvals) at DoF level, or lam_adj[ga] U[gb].

@@ -60,7 +60,9 @@ def lib():
         "tg_assemble_elasticity": (i32, [vp, i32, vp, vp, vp, i32, vp, vp]),
         "tg_assemble_load": (i32, [vp, i32, vp, vp, i32, i32, vp, vp]),
         "tg_assemble_backward": (i32, [vp, i32, vp, vp, i32, dbl, vp, vp, vp, vp, vp, vp, vp]),
+        "tg_assemble_load_backward": (i32, [vp, i32, vp, vp, i32, i32, vp, vp, vp, i32, vp]),
         "tg_spmv": (i32, [vp, i32, vp, vp, vp, vp]),
+        "tg_csr_outer": (i32, [vp, i32, vp, vp, dbl, vp, vp]),
         "tg_cg_solve": (i32, [vp, i32, vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl), vp]),
         "tg_batch_create": (i32, [C.POINTER(vp), i32, C.POINTER(vp)]),
         "tg_batch_assemble": (i32, [vp, i32, C.POINTER(vp), C.POINTER(vp), i32, C.POINTER(dbl), C.POINTER(vp), vp]),
@@ -108,6 +110,15 @@ def _ptr(t, dtype=None, name="tensor"):
     if dtype is not None and t.dtype != dtype:
         raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
     return C.c_void_p(t.data_ptr())
+
+
+def _out(arg, make):
+    """Output argument: True allocates, False/None skips, a tensor is filled."""
+    if arg is True:
+        return make()
+    if arg is None or arg is False:
+        return None
+    return arg
 
 
 class _DevView:
@@ -231,14 +242,35 @@ def tg_assemble_backward(p: Pattern, coords, kappa, layout: int, c: float = 0.0,
     """Returns (grad_kappa, grad_coords [N, d], grad_c [1]); pass False to skip one."""
     dt = coords.dtype
     dev = coords.device
-    gk = torch.empty_like(kappa) if grad_kappa is True else (grad_kappa or None)
-    gx = torch.empty_like(coords) if grad_coords is True else (grad_coords or None)
-    gc = torch.empty(1, dtype=dt, device=dev) if grad_c is True else (grad_c or None)
+    gk = _out(grad_kappa, lambda: torch.empty_like(kappa))
+    gx = _out(grad_coords, lambda: torch.empty_like(coords))
+    gc = _out(grad_c, lambda: torch.empty(1, dtype=dt, device=dev))
     _check(lib().tg_assemble_backward(p.handle, _dt(coords), _ptr(coords, dt, "coords"), _ptr(kappa, dt, "kappa"),
                                       layout, float(c), _ptr(grad_vals, dt, "grad_vals"), _ptr(lam, dt, "lam"),
                                       _ptr(U, dt, "U"), _ptr(gk, dt, "grad_kappa"), _ptr(gx, dt, "grad_coords"),
                                       _ptr(gc, dt, "grad_c"), _stream(stream)), "tg_assemble_backward")
     return gk, gx, gc
+
+
+def tg_assemble_load_backward(p: Pattern, coords, f, layout: int, ncomp: int, grad_F, grad_f=True,
+                              grad_coords=True, accumulate: bool = False, stream=None):
+    """Returns (grad_f, grad_coords); pass False to skip one, or tensors to fill."""
+    dt = coords.dtype
+    gf = _out(grad_f, lambda: torch.empty_like(f))
+    gx = _out(grad_coords, lambda: torch.empty_like(coords))
+    _check(lib().tg_assemble_load_backward(p.handle, _dt(coords), _ptr(coords, dt, "coords"), _ptr(f, dt, "f"), layout,
+                                           int(ncomp), _ptr(grad_F, dt, "grad_F"), _ptr(gf, dt, "grad_f"),
+                                           _ptr(gx, dt, "grad_coords"), int(bool(accumulate)), _stream(stream)),
+           "tg_assemble_load_backward")
+    return gf, gx
+
+
+def tg_csr_outer(p: Pattern, lam, U, alpha: float = 1.0, out=None, stream=None):
+    if out is None:
+        out = torch.empty(p.nnz, dtype=lam.dtype, device=lam.device)
+    _check(lib().tg_csr_outer(p.handle, _dt(lam), _ptr(lam, lam.dtype, "lam"), _ptr(U, lam.dtype, "U"), float(alpha),
+                              _ptr(out, lam.dtype, "out"), _stream(stream)), "tg_csr_outer")
+    return out
 
 
 def tg_spmv(p: Pattern, vals, x, y=None, stream=None):

@@ -28,6 +28,7 @@
 namespace {
 
 constexpr int BB = 128;
+constexpr int kSlots = 4;  // partial sums per CTA (must match the pattern allocation)
 
 template <typename T>
 struct BwdArgs {
@@ -259,35 +260,40 @@ __global__ void __launch_bounds__(BB) k_backward_gather(const BwdArgs<T> a, cons
   }
   block_sum2(pc, pk, red);
   if (threadIdx.x == 0) {
-    a.partials[2 * blockIdx.x] = pc;
-    a.partials[2 * blockIdx.x + 1] = pk;
+    a.partials[kSlots * blockIdx.x] = pc;
+    a.partials[kSlots * blockIdx.x + 1] = pk;
   }
 }
 
-// Sum the per-CTA partials in a fixed order and write the global gradients.
+// Sum the per-CTA partials (kSlots doubles per CTA) in a fixed order and
+// write (or add to) the global gradients out[k], k < nslots (NULL = skip).
+struct FinalOut {
+  void* out[kSlots];
+  int nslots;
+  int accumulate;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_backward_final(const double* __restrict__ partials, int nblocks,
-                                                        T* __restrict__ grad_c, T* __restrict__ grad_kappa_const) {
-  __shared__ double s[2][256];
-  double a = 0.0, b = 0.0;
-  for (int k = threadIdx.x; k < nblocks; k += 256) {
-    a += partials[2 * k];
-    b += partials[2 * k + 1];
+                                                        const FinalOut o) {
+  __shared__ double s[kSlots][256];
+  for (int k = 0; k < kSlots; ++k) {
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 256) a += partials[kSlots * b + k];
+    s[k][threadIdx.x] = a;
   }
-  s[0][threadIdx.x] = a;
-  s[1][threadIdx.x] = b;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      s[0][threadIdx.x] += s[0][threadIdx.x + w];
-      s[1][threadIdx.x] += s[1][threadIdx.x + w];
-    }
+    if (threadIdx.x < w)
+      for (int k = 0; k < kSlots; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    if (grad_c) *grad_c = (T)s[0][0];
-    if (grad_kappa_const) *grad_kappa_const = (T)s[1][0];
-  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < o.nslots; ++k)
+      if (o.out[k]) {
+        T* d = static_cast<T*>(o.out[k]);
+        *d = o.accumulate ? *d + (T)s[k][0] : (T)s[k][0];
+      }
 }
 
 template <int EL, typename T>
@@ -299,7 +305,8 @@ tg_status launch(const tg_pattern* p, const BwdArgs<T>& a, bool fused, T* grad_c
   TG_CK_LAUNCH("k_backward_gather");
   T* gk_const = (a.layout == TG_CONSTANT) ? a.grad_kappa : nullptr;
   if (grad_c || gk_const) {
-    k_backward_final<T><<<1, 256, 0, s>>>(a.partials, grid, grad_c, gk_const);
+    FinalOut o{{grad_c, gk_const, nullptr, nullptr}, 2, 0};
+    k_backward_final<T><<<1, 256, 0, s>>>(a.partials, grid, o);
     TG_CK_LAUNCH("k_backward_final");
   }
   return TG_OK;
@@ -335,6 +342,219 @@ tg_status backward(const tg_pattern* p, const void* coords, const void* kappa, t
   }
 }
 
+// ------------------------------------------------------------------ load vector
+// Reverse mode of F[g(a) nc + k] = |det J| h_ak, with h_ak = sum_b Mhat_ab f_bk
+// (PER_NODE), sum_q w_q phi_qa f_eqk (PER_QP) or m1_a f_k (CONSTANT).
+// For an upstream gradient gF:
+//   dL/df           the transpose of each of those maps, times |det J|;
+//   dL/dx_b         = sign(det J) (sum_ak gF_ak h_ak) n_b   for the vertices b
+// (only |det J| depends on the coordinates: d|det J| = |det J| tr(J^{-1} dJ)).
+template <typename T>
+struct LoadBwdArgs {
+  const int32_t* __restrict__ inc_ptr;
+  const int32_t* __restrict__ inc_e;
+  const int32_t* __restrict__ cells;
+  const T* __restrict__ coords;
+  const T* __restrict__ f;
+  int layout;
+  const T* __restrict__ gF;
+  T* __restrict__ grad_f;
+  T* __restrict__ grad_coords;
+  int accumulate;
+  double* __restrict__ partials;
+  int64_t N;
+  unsigned long long* status;
+};
+
+template <int EL, typename T, int NC>
+__global__ void __launch_bounds__(BB) k_load_backward(const LoadBwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab) {
+  using El = tg::Elem<EL>;
+  constexpr int NV = El::nv, D = El::dim, NQ = El::nq;
+  __shared__ tg::RefTab<T> ts;
+  __shared__ double red[BB / 32][NC];
+  tg::copy_table(ts, tab);
+  const int64_t i = (int64_t)blockIdx.x * BB + threadIdx.x;
+  double pk[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) pk[k] = 0.0;
+  if (i < a.N) {
+    T gx[D], gf[NC];
+#pragma unroll
+    for (int r = 0; r < D; ++r) gx[r] = T(0);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) gf[k] = T(0);
+    const int j0 = __ldg(a.inc_ptr + i), j1 = __ldg(a.inc_ptr + i + 1);
+    for (int j = j0; j < j1; ++j) {
+      const int ea = __ldg(a.inc_e + j);
+      const int64_t e = ea >> 3;
+      const int la = ea & 7;
+      const int32_t* cl = a.cells + e * NV;
+      int v[NV];
+#pragma unroll
+      for (int b = 0; b < NV; ++b) v[b] = __ldg(cl + b);
+      tg::Geom<D, T> g;
+      if constexpr (D == 2) tg::tri_geom(a.coords, v[0], v[1], v[2], g);
+      else tg::tet_geom(a.coords, v[0], v[1], v[2], v[3], g);
+      const T adet = tg::absv(g.det);
+      if (!(adet > tg::det_tiny<T>())) {
+        tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
+        continue;
+      }
+      T gv[NV][NC];
+#pragma unroll
+      for (int b = 0; b < NV; ++b)
+#pragma unroll
+        for (int k = 0; k < NC; ++k) gv[b][k] = __ldg(a.gF + (int64_t)v[b] * NC + k);
+      // dL/df
+      if (a.grad_f) {
+        if (a.layout == TG_PER_NODE) {
+#pragma unroll
+          for (int k = 0; k < NC; ++k) {
+            T s = T(0);
+#pragma unroll
+            for (int b = 0; b < NV; ++b) s += ts.M[b][la] * gv[b][k];
+            gf[k] += adet * s;
+          }
+        } else if (la == 0) {
+          if (a.layout == TG_PER_QP) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+#pragma unroll
+              for (int k = 0; k < NC; ++k) {
+                T s = T(0);
+#pragma unroll
+                for (int b = 0; b < NV; ++b) s += ts.phi[q][b] * gv[b][k];
+                T* d = a.grad_f + (e * NQ + q) * NC + k;
+                const T val = adet * ts.w[q] * s;
+                *d = a.accumulate ? *d + val : val;
+              }
+          } else {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+              T s = T(0);
+#pragma unroll
+              for (int b = 0; b < NV; ++b) s += ts.m1[b] * gv[b][k];
+              pk[k] += (double)(adet * s);
+            }
+          }
+        }
+      }
+      // dL/dx for the geometric vertices
+      if (a.grad_coords && la <= D) {
+        T Le = T(0);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          if (a.layout == TG_PER_NODE) {
+            T fb[NV];
+#pragma unroll
+            for (int b = 0; b < NV; ++b) fb[b] = __ldg(a.f + (int64_t)v[b] * NC + k);
+#pragma unroll
+            for (int p = 0; p < NV; ++p) {
+              T h = T(0);
+#pragma unroll
+              for (int b = 0; b < NV; ++b) h += ts.M[p][b] * fb[b];
+              Le += gv[p][k] * h;
+            }
+          } else if (a.layout == TG_PER_QP) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+              T s = T(0);
+#pragma unroll
+              for (int p = 0; p < NV; ++p) s += ts.phi[q][p] * gv[p][k];
+              Le += ts.w[q] * __ldg(a.f + (e * NQ + q) * NC + k) * s;
+            }
+          } else {
+            T s = T(0);
+#pragma unroll
+            for (int p = 0; p < NV; ++p) s += ts.m1[p] * gv[p][k];
+            Le += __ldg(a.f + k) * s;
+          }
+        }
+        const T sgn = g.det > T(0) ? T(1) : T(-1);
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+          T col[D + 1];
+#pragma unroll
+          for (int b = 0; b <= D; ++b) col[b] = g.n[b][r];
+          gx[r] += sgn * Le * tg::sel(la, col);
+        }
+      }
+    }
+    if (a.grad_coords) {
+#pragma unroll
+      for (int r = 0; r < D; ++r) {
+        T* d = a.grad_coords + i * D + r;
+        *d = a.accumulate ? *d + gx[r] : gx[r];
+      }
+    }
+    if (a.grad_f && a.layout == TG_PER_NODE) {
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        T* d = a.grad_f + i * NC + k;
+        *d = a.accumulate ? *d + gf[k] : gf[k];
+      }
+    }
+  }
+  // fixed-order block sums of the CONSTANT-layout partials
+#pragma unroll
+  for (int k = 0; k < NC; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pk[k] += __shfl_down_sync(0xffffffffu, pk[k], o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) red[wid][k] = pk[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kSlots; ++k) {
+      double s = 0.0;
+      if (k < NC)
+        for (int w = 0; w < BB / 32; ++w) s += red[w][k];
+      a.partials[kSlots * blockIdx.x + k] = s;
+    }
+  }
+}
+
+template <int EL, typename T>
+tg_status launch_load_bwd(const tg_pattern* p, const LoadBwdArgs<T>& a, int ncomp, cudaStream_t s) {
+  const int grid = tg::grid_for(p->N, BB);
+  const tg::RefTab<T>& tab = tg::table<T>((tg_element)EL);
+  if (ncomp == 1) k_load_backward<EL, T, 1><<<grid, BB, 0, s>>>(a, tab);
+  else k_load_backward<EL, T, 3><<<grid, BB, 0, s>>>(a, tab);
+  TG_CK_LAUNCH("k_load_backward");
+  if (a.grad_f && a.layout == TG_CONSTANT) {
+    FinalOut o{{nullptr, nullptr, nullptr, nullptr}, ncomp, a.accumulate};
+    for (int k = 0; k < ncomp; ++k) o.out[k] = a.grad_f + k;
+    k_backward_final<T><<<1, 256, 0, s>>>(a.partials, grid, o);
+    TG_CK_LAUNCH("k_backward_final");
+  }
+  return TG_OK;
+}
+
+template <typename T>
+tg_status load_backward(const tg_pattern* p, const void* coords, const void* f, tg_layout fl, int ncomp,
+                        const void* gF, void* grad_f, void* grad_coords, int accumulate, cudaStream_t s) {
+  LoadBwdArgs<T> a;
+  a.inc_ptr = p->inc_ptr;
+  a.inc_e = p->inc_e;
+  a.cells = p->cells;
+  a.coords = static_cast<const T*>(coords);
+  a.f = static_cast<const T*>(f);
+  a.layout = fl;
+  a.gF = static_cast<const T*>(gF);
+  a.grad_f = static_cast<T*>(grad_f);
+  a.grad_coords = static_cast<T*>(grad_coords);
+  a.accumulate = accumulate;
+  a.partials = p->partials;
+  a.N = p->N;
+  a.status = p->status;
+  switch (p->el) {
+    case TG_P1_TRI: return launch_load_bwd<TG_P1_TRI, T>(p, a, ncomp, s);
+    case TG_P2_TRI: return launch_load_bwd<TG_P2_TRI, T>(p, a, ncomp, s);
+    default: return launch_load_bwd<TG_P1_TET, T>(p, a, ncomp, s);
+  }
+}
+
 }  // namespace
 
 extern "C" tg_status tg_assemble_backward(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
@@ -354,4 +574,18 @@ extern "C" tg_status tg_assemble_backward(const tg_pattern* p, tg_dtype dtype, c
                                            grad_coords, grad_c, s)
                          : backward<double>(p, coords, kappa, kappa_layout, c, grad_vals, lam, U, grad_kappa,
                                             grad_coords, grad_c, s);
+}
+
+extern "C" tg_status tg_assemble_load_backward(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* f,
+                                               tg_layout f_layout, int32_t ncomp, const void* grad_F, void* grad_f,
+                                               void* grad_coords, int32_t accumulate, tg_stream stream) {
+  if (!p || (dtype != TG_F32 && dtype != TG_F64) || !f || !grad_F || (p->N > 0 && !coords)) return TG_ERR_INVALID_ARG;
+  if ((ncomp != 1 && ncomp != 3) || !(f_layout == TG_PER_NODE || f_layout == TG_PER_QP || f_layout == TG_CONSTANT))
+    return TG_ERR_INVALID_ARG;
+  const size_t es = dtype == TG_F32 ? 4 : 8;
+  if (((uintptr_t)coords % (p->dim == 2 ? 2 * es : es)) != 0) return TG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  return dtype == TG_F32 ? load_backward<float>(p, coords, f, f_layout, ncomp, grad_F, grad_f, grad_coords, accumulate, s)
+                         : load_backward<double>(p, coords, f, f_layout, ncomp, grad_F, grad_f, grad_coords, accumulate,
+                                                 s);
 }

@@ -375,8 +375,8 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
     TG_CK_LAUNCH("k_expand3");
   }
 
-  // per-CTA partials of the backward's global sums (2 values per CTA)
-  p->n_partials = 2 * ((N + 127) / 128) + 2;
+  // per-CTA partials of the backward's global sums (4 values per 128-row CTA)
+  p->n_partials = 4 * ((N + 127) / 128) + 4;
   TG_CK(cudaMalloc(&p->partials, p->n_partials * sizeof(double)));
   TG_CK(cudaStreamSynchronize(s));
   if ((st = read_status(p, s, "tg_build_pattern")) != TG_OK) return st;

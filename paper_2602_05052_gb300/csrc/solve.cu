@@ -174,6 +174,19 @@ tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8
   return TG_OK;
 }
 
+// out[s] = alpha * lam[row(s)] * U[col(s)]: the adjoint outer product
+// dGamma/dK = lam U^T of Eq. (adj) restricted to the CSR pattern.
+template <typename T>
+__global__ void __launch_bounds__(ST) k_csr_outer(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                  const T* __restrict__ lam, const T* __restrict__ U, T alpha,
+                                                  T* __restrict__ out, int64_t n) {
+  const int64_t row = (int64_t)blockIdx.x * (ST / 8) + (threadIdx.x >> 3);
+  if (row >= n) return;
+  const T l = alpha * lam[row];
+  const int k1 = __ldg(rp + row + 1);
+  for (int k = __ldg(rp + row) + (threadIdx.x & 7); k < k1; k += 8) out[k] = l * __ldg(U + __ldg(ci + k));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_fma_rate(T* __restrict__ out, int iters, T a, T b) {
   T x[8];
@@ -221,6 +234,23 @@ tg_status tg_cg_solve(const tg_pattern* p, tg_dtype dtype, const void* vals, con
   if (iters) *iters = it;
   if (relres) *relres = rr;
   return st;
+}
+
+tg_status tg_csr_outer(const tg_pattern* p, tg_dtype dtype, const void* lam, const void* U, double alpha, void* out,
+                       tg_stream stream) {
+  if (!p || (dtype != TG_F32 && dtype != TG_F64) || !lam || !U || !out) return TG_ERR_INVALID_ARG;
+  const bool vec = p->el == TG_P1_TET_VEC3;
+  const int64_t n = vec ? 3 * p->N : p->N;
+  const int32_t* rp = vec ? p->row_ptr3 : p->row_ptr;
+  const int32_t* ci = vec ? p->col_idx3 : p->col_idx;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int g = tg::grid_for(n, ST / 8);
+  if (dtype == TG_F32)
+    k_csr_outer<float><<<g, ST, 0, s>>>(rp, ci, (const float*)lam, (const float*)U, (float)alpha, (float*)out, n);
+  else
+    k_csr_outer<double><<<g, ST, 0, s>>>(rp, ci, (const double*)lam, (const double*)U, alpha, (double*)out, n);
+  TG_CK_LAUNCH("k_csr_outer");
+  return TG_OK;
 }
 
 tg_status tg_diag_fma_rate(tg_dtype dtype, double* flops, tg_stream stream) {

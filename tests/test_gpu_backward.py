@@ -1,0 +1,178 @@
+"""GPU parity of the reverse-mode assembly against the oracle's analytic
+gradients and against finite differences (differentiable 3D Poisson)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import meshgen as mg
+import oracle as O
+from gpu_helpers import TOL, coef, dev, host_as, mesh_for, relfro
+
+pytestmark = pytest.mark.gpu
+
+ELS = [mg.P1_TRI, mg.P2_TRI, mg.P1_TET]
+DTYPES = [torch.float64, torch.float32]
+# gradients carry one more level of cancellation than the forward values
+GTOL = {torch.float64: 1e-12, torch.float32: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def tg():
+    import paper_2602_05052_gb300 as tg
+    return tg
+
+
+@pytest.mark.parametrize("fused", [False, True])
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("layout", [mg.PER_QP, mg.PER_ELEMENT, mg.CONSTANT])
+@pytest.mark.parametrize("el", ELS)
+def test_backward_matches_oracle(tg, el, layout, dtype, fused):
+    m = mesh_for(el)
+    k = coef(layout, m.n_elems, mg.NQ[el], seed=50 + el)
+    c = 0.6
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, el)
+    g = np.random.default_rng(51)
+    xs, ks = host_as(m.coords, dtype), host_as(k, dtype)
+    if fused:
+        lam, U = host_as(g.normal(size=m.n_nodes), dtype), host_as(g.normal(size=m.n_nodes), dtype)
+        gk, gx, gc = tg.tg_assemble_backward(p, dev(m.coords, dtype), dev(k, dtype), layout, c, lam=dev(lam, dtype),
+                                             U=dev(U, dtype))
+        rk, rx, rc = O.assemble_backward(el, m.cells, xs, ks, layout, c, lam=lam, U=U)
+    else:
+        ref = O.assemble_bilinear(el, m.cells, xs, ks, layout, c)
+        gv = host_as(g.normal(size=p.nnz), dtype)
+        gk, gx, gc = tg.tg_assemble_backward(p, dev(m.coords, dtype), dev(k, dtype), layout, c, grad_vals=dev(gv, dtype))
+        rk, rx, rc = O.assemble_backward(el, m.cells, xs, ks, layout, c, grad_csr=O.CSR(ref.row_ptr, ref.col, gv))
+    assert relfro(gk.cpu().numpy(), rk) <= GTOL[dtype]
+    assert relfro(gx.cpu().numpy(), rx) <= GTOL[dtype]
+    assert relfro(gc.cpu().numpy(), [rc]) <= GTOL[dtype]
+    assert tg.tg_get_device_status(p) == (0, -1)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("layout", [mg.PER_NODE, mg.PER_QP, mg.CONSTANT])
+@pytest.mark.parametrize("el", ELS + [mg.P1_TET_VEC3])
+def test_load_backward_matches_oracle(tg, el, layout, dtype):
+    m = mesh_for(el)
+    ncomp = 3 if el == mg.P1_TET_VEC3 else 1
+    g = np.random.default_rng(60 + el)
+    nf = {mg.PER_NODE: m.n_nodes, mg.PER_QP: m.n_elems * mg.NQ[el], mg.CONSTANT: 1}[layout] * ncomp
+    f = host_as(g.uniform(-1, 1, size=nf), dtype)
+    gF = host_as(g.normal(size=m.n_nodes * ncomp), dtype)
+    xs = host_as(m.coords, dtype)
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, el)
+    gf, gx = tg.tg_assemble_load_backward(p, dev(m.coords, dtype), dev(f, dtype), layout, ncomp, dev(gF, dtype))
+    rf, rx = O.load_backward(el, m.cells, xs, f, layout, ncomp, gF)
+    assert relfro(gf.cpu().numpy(), rf) <= GTOL[dtype]
+    assert relfro(gx.cpu().numpy(), rx) <= GTOL[dtype]
+    # accumulate adds to what is there
+    gf2, gx2 = gf.clone(), gx.clone()
+    tg.tg_assemble_load_backward(p, dev(m.coords, dtype), dev(f, dtype), layout, ncomp, dev(gF, dtype), grad_f=gf2,
+                                 grad_coords=gx2, accumulate=True)
+    assert torch.allclose(gf2, 2 * gf) and torch.allclose(gx2, 2 * gx)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_backward_is_bitwise_deterministic(tg, dtype):
+    m = mesh_for(mg.P1_TRI, "large")
+    k = coef(mg.PER_QP, m.n_elems, 3, seed=5)
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
+    gv = dev(np.random.default_rng(2).normal(size=p.nnz), dtype)
+    x, kk = dev(m.coords, dtype), dev(k, dtype)
+    first = [t.clone() for t in tg.tg_assemble_backward(p, x, kk, mg.PER_QP, 1.0, grad_vals=gv)]
+    for _ in range(9):
+        again = tg.tg_assemble_backward(p, x, kk, mg.PER_QP, 1.0, grad_vals=gv)
+        for a, b in zip(first, again):
+            assert torch.equal(a, b)
+
+
+def test_autograd_gradcheck(tg):
+    from paper_2602_05052_gb300 import autograd as A
+    m = mg.jitter(mg.tri_grid(3), 4)
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
+    x = dev(m.coords, torch.float64).requires_grad_(True)
+    k = dev(np.random.default_rng(1).uniform(0.5, 2, size=m.n_elems * 3), torch.float64).requires_grad_(True)
+    f = dev(np.random.default_rng(2).uniform(-1, 1, size=m.n_nodes), torch.float64).requires_grad_(True)
+    assert torch.autograd.gradcheck(lambda x_, k_: A.assemble(p, x_, k_, mg.PER_QP, 0.3), (x, k), eps=1e-6, atol=1e-8)
+    assert torch.autograd.gradcheck(lambda x_, f_: A.load(p, x_, f_, mg.PER_NODE), (x, f), eps=1e-6, atol=1e-8)
+    mask = dev(m.boundary.astype(np.uint8), torch.uint8)
+    vals = A.assemble(p, x, k, mg.PER_QP, 0.0).detach().requires_grad_(True)
+    F = A.load(p, x, f, mg.PER_NODE).detach().requires_grad_(True)
+    assert torch.autograd.gradcheck(lambda v_, F_: A.solve(p, v_, F_, mask, rtol=1e-14), (vals, F), eps=1e-6,
+                                    atol=1e-7)
+
+
+def _poisson3d_loss(tg, A, p, coords, kappa, f, mask, u_t, rtol=1e-13):
+    u = A.solve_assembled(p, coords, kappa, mg.PER_ELEMENT, f, mg.CONSTANT, mask, rtol=rtol)
+    return ((u - u_t) ** 2).sum()
+
+
+def test_differentiable3d_full_size_finite_differences(tg):
+    """48^3 Kuhn mesh: dL/dkappa and dL/dcoords of L = ||u - u_target||^2
+    (forward assembly + CG, adjoint CG + backward assembly) against central
+    differences along 16 random directions each."""
+    from paper_2602_05052_gb300 import autograd as A
+    cfg = mg.differentiable3d(48)
+    m = cfg["mesh"]
+    assert m.n_elems == 663552
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TET)
+    mask = dev(m.boundary.astype(np.uint8), torch.uint8)
+    x0 = dev(m.coords, torch.float64)
+    f = dev([1.0], torch.float64)
+    with torch.no_grad():
+        u_t = A.solve_assembled(p, x0, dev(cfg["kappa_star"], torch.float64), mg.PER_ELEMENT, f, mg.CONSTANT, mask,
+                                rtol=1e-13)
+    k0 = dev(cfg["kappa"], torch.float64)
+    k = k0.clone().requires_grad_(True)
+    x = x0.clone().requires_grad_(True)
+    L = _poisson3d_loss(tg, A, p, x, k, f, mask, u_t)
+    L.backward()
+    gk, gx = k.grad.clone(), x.grad.clone()
+    dk = mg.fd_directions(16, m.n_elems, seed=55)
+    dxs = mg.fd_directions(16, m.n_nodes * 3, seed=56).reshape(16, m.n_nodes, 3)
+    dxs[:, m.boundary, :] = 0  # keep the domain fixed
+    with torch.no_grad():
+        for i in range(16):
+            d = dev(dk[i], torch.float64)
+            eps = 1e-2
+            num = (_poisson3d_loss(tg, A, p, x0, k0 + eps * d, f, mask, u_t)
+                   - _poisson3d_loss(tg, A, p, x0, k0 - eps * d, f, mask, u_t)).item() / (2 * eps)
+            ana = float((gk * d).sum())
+            assert abs(num - ana) <= 1e-6 * max(abs(ana), 1e-12 * float(L)), (i, num, ana)
+            dx = dev(dxs[i], torch.float64)
+            eps = 1e-3
+            num = (_poisson3d_loss(tg, A, p, x0 + eps * dx, k0, f, mask, u_t)
+                   - _poisson3d_loss(tg, A, p, x0 - eps * dx, k0, f, mask, u_t)).item() / (2 * eps)
+            ana = float((gx * dx).sum())
+            assert abs(num - ana) <= 1e-6 * max(abs(ana), 1e-12 * float(L)), (i, num, ana)
+
+
+def test_differentiable3d_small_matches_oracle_gradient(tg):
+    """Same pipeline on 12^3 against the oracle: assembly, CG, adjoint CG,
+    analytic backward, all on the CPU."""
+    from oracle import solve as S
+    from paper_2602_05052_gb300 import autograd as A
+    cfg = mg.differentiable3d(12)
+    m = cfg["mesh"]
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TET)
+    mask = dev(m.boundary.astype(np.uint8), torch.uint8)
+    f1 = np.array([1.0])
+    # oracle pipeline
+    Ks = O.assemble_bilinear(O.P1_TET, m.cells, m.coords, cfg["kappa_star"], O.PER_ELEMENT, 0.0).to_scipy()
+    F = O.assemble_load(O.P1_TET, m.cells, m.coords, f1, O.CONSTANT)
+    ut, _, _ = S.solve_dirichlet(Ks, F, m.boundary, tol=1e-14)
+    Kc = O.assemble_bilinear(O.P1_TET, m.cells, m.coords, cfg["kappa"], O.PER_ELEMENT, 0.0)
+    u, _, _ = S.solve_dirichlet(Kc.to_scipy(), F, m.boundary, tol=1e-14)
+    lam, _, _ = S.solve_dirichlet(Kc.to_scipy(), 2 * (u - ut), m.boundary, tol=1e-14)
+    rk, rx, _ = O.assemble_backward(O.P1_TET, m.cells, m.coords, cfg["kappa"], O.PER_ELEMENT, 0.0, lam=-lam, U=u)
+    _, rx2 = O.load_backward(O.P1_TET, m.cells, m.coords, f1, O.CONSTANT, 1, lam)
+    # GPU pipeline
+    k = dev(cfg["kappa"], torch.float64).requires_grad_(True)
+    x = dev(m.coords, torch.float64).requires_grad_(True)
+    u_t = dev(ut, torch.float64)
+    L = _poisson3d_loss(tg, A, p, x, k, dev(f1, torch.float64), mask, u_t, rtol=1e-14)
+    L.backward()
+    assert relfro(k.grad.cpu().numpy(), rk) <= 1e-9
+    assert relfro(x.grad.cpu().numpy(), rx + rx2) <= 1e-9

@@ -1,0 +1,133 @@
+"""Batched persistent assembly (bitwise equal to per-instance launches, and to
+the oracle within tolerance), its CUDA-graph capture and autotuner, and the
+CG solve of the structured Poisson problem against its closed form."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import meshgen as mg
+import oracle as O
+from gpu_helpers import TOL, dev, host_as, relfro
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tg():
+    import paper_2602_05052_gb300 as tg
+    return tg
+
+
+def _instances(sizes, dtype):
+    insts = mg.batched_p2(len(sizes), seed=4, sizes=sizes)
+    out = []
+    for k in insts:
+        m = k["mesh"]
+        out.append(dict(mesh=m, x=dev(m.coords, dtype), kappa=dev(k["kappa"], dtype), kappa_np=k["kappa"]))
+    return out
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_batch_bitwise_equals_single_launches(tg, dtype):
+    sizes = [1, 2, 3, 5, 8, 13, 21, 34, 7, 4, 30, 17]
+    insts = _instances(sizes, dtype)
+    pats = [tg.tg_build_pattern(dev(i["mesh"].cells, torch.int32), i["mesh"].n_nodes, mg.P2_TRI) for i in insts]
+    b = tg.tg_batch_create(pats)
+    cs = [0.1 * j for j in range(len(insts))]
+    out = [torch.full((p.nnz,), float("nan"), dtype=dtype, device="cuda") for p in pats]
+    for sched in [(128, 512, 0), (64, 64, 2), (256, 2048, 0)]:
+        tg.tg_batch_set_schedule(b, *sched)
+        tg.tg_batch_assemble(b, [i["x"] for i in insts], [i["kappa"] for i in insts], mg.PER_QP, cs, out)
+        for j, (i, p) in enumerate(zip(insts, pats)):
+            single = tg.tg_assemble_bilinear(p, i["x"], i["kappa"], mg.PER_QP, cs[j])
+            assert torch.equal(out[j], single), (sched, j)
+    for j in (0, 5, 10):
+        m = insts[j]["mesh"]
+        ref = O.assemble_bilinear(O.P2_TRI, m.cells, host_as(m.coords, dtype), host_as(insts[j]["kappa_np"], dtype),
+                                  O.PER_QP, cs[j])
+        assert relfro(out[j].cpu().numpy(), ref.val) <= TOL[dtype]
+
+
+def test_batch_graph_capture_and_autotune(tg):
+    dtype = torch.float32
+    sizes = mg.batch_sizes(48, seed=9)
+    insts = _instances(sizes, dtype)
+    pats = [tg.tg_build_pattern(dev(i["mesh"].cells, torch.int32), i["mesh"].n_nodes, mg.P2_TRI) for i in insts]
+    b = tg.tg_batch_create(pats)
+    xs, ks = [i["x"] for i in insts], [i["kappa"] for i in insts]
+    cs = [0.0] * len(insts)
+    out = [torch.empty(p.nnz, dtype=dtype, device="cuda") for p in pats]
+    ms = tg.tg_batch_autotune(b, xs, ks, mg.PER_QP, cs, out, reps=2)
+    assert ms > 0
+    t, r, c = b.schedule()
+    assert t in (64, 128, 256) and r % t == 0
+    want = [torch.empty_like(o) for o in out]
+    tg.tg_batch_assemble(b, xs, ks, mg.PER_QP, cs, want)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    for o in out:
+        o.fill_(float("nan"))
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        tg.tg_batch_assemble(b, xs, ks, mg.PER_QP, cs, out, stream=s)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    for o, w in zip(out, want):
+        assert torch.equal(o, w)
+
+
+def test_batch_many_instances_spanning_launch_chunks(tg):
+    # more instances than one launch's parameter table holds
+    dtype = torch.float32
+    sizes = [1 + (j % 4) for j in range(300)]
+    insts = _instances(sizes, dtype)
+    pats = [tg.tg_build_pattern(dev(i["mesh"].cells, torch.int32), i["mesh"].n_nodes, mg.P2_TRI) for i in insts]
+    b = tg.tg_batch_create(pats)
+    out = [torch.empty(p.nnz, dtype=dtype, device="cuda") for p in pats]
+    cs = [1.0] * len(insts)
+    tg.tg_batch_assemble(b, [i["x"] for i in insts], [i["kappa"] for i in insts], mg.PER_QP, cs, out)
+    for j in (0, 255, 256, 299):
+        single = tg.tg_assemble_bilinear(pats[j], insts[j]["x"], insts[j]["kappa"], mg.PER_QP, 1.0)
+        assert torch.equal(out[j], single)
+
+
+def test_cg_poisson_structured_matches_closed_form(tg):
+    from test_oracle_pins import _dst_solution
+    n = 64
+    m = mg.tri_grid(n)
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
+    x = dev(m.coords, torch.float64)
+    one = dev([1.0], torch.float64)
+    vals = tg.tg_assemble_bilinear(p, x, one, mg.CONSTANT, 0.0)
+    F = tg.tg_assemble_load(p, x, one, mg.CONSTANT)
+    mask = dev(m.boundary.astype(np.uint8), torch.uint8)
+    u, it, rel = tg.tg_cg_solve(p, vals, F, mask, rtol=1e-10)
+    assert rel <= 1e-10 and 0 < it < 1000
+    U = _dst_solution(n)
+    ii = np.arange(m.n_nodes) % (n + 1)
+    jj = np.arange(m.n_nodes) // (n + 1)
+    un = u.cpu().numpy()
+    inner = ~m.boundary
+    assert np.all(un[m.boundary] == 0)
+    assert np.allclose(un[inner], U[jj[inner] - 1, ii[inner] - 1], rtol=1e-8, atol=1e-12)
+    # true residual of the condensed system
+    r = tg.tg_spmv(p, vals, u).cpu().numpy() - F.cpu().numpy()
+    assert np.linalg.norm(r[inner]) / np.linalg.norm(F.cpu().numpy()[inner]) <= 1e-9
+
+
+def test_spmv_and_outer_match_scipy(tg):
+    m = mg.jitter(mg.tri_grid(30), 3)
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
+    k = np.random.default_rng(3).uniform(0.5, 2, size=m.n_elems * 3)
+    vals = tg.tg_assemble_bilinear(p, dev(m.coords, torch.float64), dev(k, torch.float64), mg.PER_QP, 0.2)
+    ref = O.assemble_bilinear(O.P1_TRI, m.cells, m.coords, k, O.PER_QP, 0.2)
+    xv = np.random.default_rng(4).normal(size=m.n_nodes)
+    y = tg.tg_spmv(p, vals, dev(xv, torch.float64)).cpu().numpy()
+    assert relfro(y, ref.to_scipy() @ xv) <= 1e-13
+    lam = np.random.default_rng(5).normal(size=m.n_nodes)
+    o = tg.tg_csr_outer(p, dev(lam, torch.float64), dev(xv, torch.float64), alpha=-2.0).cpu().numpy()
+    assert np.array_equal(o, -2.0 * lam[ref.rows_of()] * xv[ref.col])

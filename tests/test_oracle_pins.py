@@ -489,3 +489,33 @@ def test_planted_mistake_is_caught():
     K1 = O.element_matrix(O.P1_TRI, Va, 1.0, 0.5)
     K2 = O.element_matrix(O.P1_TRI, Va[[0, 2, 1]], 1.0, 0.5)
     assert np.allclose(K1, K2[np.ix_([0, 2, 1], [0, 2, 1])], rtol=1e-14)
+
+
+@pytest.mark.parametrize("el,layout,ncomp", [(O.P1_TRI, O.PER_NODE, 1), (O.P2_TRI, O.PER_QP, 1),
+                                             (O.P1_TET, O.CONSTANT, 1), (O.P1_TET_VEC3, O.PER_NODE, 3)])
+def test_load_backward_matches_central_differences(el, layout, ncomp):
+    gel = O.P1_TET if el == O.P1_TET_VEC3 else el
+    m = _jittered(gel, n=3, seed=6)
+    g = np.random.default_rng(41)
+    nf = {O.PER_NODE: m.n_nodes, O.PER_QP: m.n_elems * O.NQ[el], O.CONSTANT: 1}[layout] * ncomp
+    f = g.uniform(-1, 1, size=nf)
+    gF = g.normal(size=m.n_nodes * ncomp)
+    gf, gx = O.load_backward(el, m.cells, m.coords, f, layout, ncomp, gF)
+
+    def L(f_, x_):
+        return float(gF @ O.assemble_load(el, m.cells, x_, f_, layout, ncomp))
+
+    eps = 1e-6
+    for i in range(0, nf, max(1, nf // 15)):
+        d = np.zeros(nf)
+        d[i] = eps
+        num = (L(f + d, m.coords) - L(f - d, m.coords)) / (2 * eps)
+        assert abs(num - gf[i]) < 1e-8 * max(1, abs(gf[i]))
+    geo = np.unique(m.cells[:, :3] if el == O.P2_TRI else m.cells)
+    for node in geo[:10]:
+        for r in range(m.coords.shape[1]):
+            cp, cm = m.coords.copy(), m.coords.copy()
+            cp[node, r] += eps
+            cm[node, r] -= eps
+            num = (L(f, cp) - L(f, cm)) / (2 * eps)
+            assert abs(num - gx[node, r]) < 1e-7 * max(1, abs(gx[node, r])), (node, r, num, gx[node, r])
