@@ -66,31 +66,39 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double (*red)[B
   if (threadIdx.x == 0) {
     a = 0;
     b = 0;
-    for (int w = 0; w < BB / 32; ++w) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
       a += red[0][w];
       b += red[1][w];
     }
   }
 }
 
+// Staged like the forward (gather.cuh): a CTA owns R = blockDim.x rows; in
+// phase 1 its threads stride over the rows' contiguous incidence range, one
+// incidence each, and leave the coordinate-gradient contribution of the
+// visit in shared memory (contrib [D][cap]); in phase 2 each row sums its
+// contributions in increasing element order.
 template <int EL, typename T, bool FUSED>
-__global__ void __launch_bounds__(BB) k_backward_gather(const BwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab) {
+__global__ void __launch_bounds__(BB) k_backward_gather(const BwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
+                                                        int cap) {
   using El = tg::Elem<EL>;
   constexpr int NV = El::nv, D = El::dim, NQ = El::nq;
   __shared__ tg::RefTab<T> ts;
   __shared__ double red[2][BB / 32];
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T* contrib = reinterpret_cast<T*>(dsm);
   tg::copy_table(ts, tab);
-  const int64_t i = (int64_t)blockIdx.x * BB + threadIdx.x;
+  const int R = blockDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  const int64_t r1 = r0 + R < a.N ? r0 + R : a.N;
   double pc = 0.0, pk = 0.0;
-  if (i < a.N) {
-    T gx[D];
-#pragma unroll
-    for (int r = 0; r < D; ++r) gx[r] = T(0);
-    const int j0 = __ldg(a.inc_ptr + i), j1 = __ldg(a.inc_ptr + i + 1);
-    for (int j = j0; j < j1; ++j) {
+  {
+    const int J0 = __ldg(a.inc_ptr + r0), J1 = __ldg(a.inc_ptr + r1);
+    for (int j = J0 + (int)threadIdx.x; j < J1; j += R) {
       const int ea = __ldg(a.inc_e + j);
       const int64_t e = ea >> 3;
       const int la = ea & 7;
+      const int kk = j - J0;
       const int32_t* cl = a.cells + e * NV;
       int v[NV];
 #pragma unroll
@@ -106,6 +114,8 @@ __global__ void __launch_bounds__(BB) k_backward_gather(const BwdArgs<T> a, cons
             for (int q = 0; q < NQ; ++q) a.grad_kappa[e * NQ + q] = T(0);
           else if (a.layout == TG_PER_ELEMENT) a.grad_kappa[e] = T(0);
         }
+#pragma unroll
+        for (int r = 0; r < D; ++r) contrib[r * cap + kk] = T(0);
         continue;
       }
       // symmetric part of the upstream weights of this element
@@ -233,6 +243,9 @@ __global__ void __launch_bounds__(BB) k_backward_gather(const BwdArgs<T> a, cons
         }
         pc += (double)(adet * wm);
       }
+      T gxc[D];
+#pragma unroll
+      for (int r = 0; r < D; ++r) gxc[r] = T(0);
       if (a.grad_coords && la <= D) {
         T na[D];
 #pragma unroll
@@ -249,14 +262,26 @@ __global__ void __launch_bounds__(BB) k_backward_gather(const BwdArgs<T> a, cons
           T qn = T(0);
 #pragma unroll
           for (int s2 = 0; s2 < D; ++s2) qn += Q[r][s2] * na[s2];
-          gx[r] += sgn * (inv2 * (t * na[r] - T(2) * qn) + cw * na[r]);
+          gxc[r] = sgn * (inv2 * (t * na[r] - T(2) * qn) + cw * na[r]);
         }
       }
-    }
-    if (a.grad_coords) {
 #pragma unroll
-      for (int r = 0; r < D; ++r) a.grad_coords[i * D + r] = gx[r];
+      for (int r = 0; r < D; ++r) contrib[r * cap + kk] = gxc[r];
     }
+  }
+  __syncthreads();
+  const int64_t i = r0 + threadIdx.x;
+  if (a.grad_coords && i < r1) {
+    const int J0 = __ldg(a.inc_ptr + r0);
+    const int js = __ldg(a.inc_ptr + i) - J0, je = __ldg(a.inc_ptr + i + 1) - J0;
+    T gx[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) gx[r] = T(0);
+    for (int k = js; k < je; ++k)
+#pragma unroll
+      for (int r = 0; r < D; ++r) gx[r] += contrib[r * cap + k];
+#pragma unroll
+    for (int r = 0; r < D; ++r) a.grad_coords[i * D + r] = gx[r];
   }
   block_sum2(pc, pk, red);
   if (threadIdx.x == 0) {
@@ -273,17 +298,34 @@ struct FinalOut {
   int accumulate;
 };
 
+constexpr int kFinal = 1024;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_backward_final(const double* __restrict__ partials, int nblocks,
-                                                        const FinalOut o) {
-  __shared__ double s[kSlots][256];
-  for (int k = 0; k < kSlots; ++k) {
-    double a = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += 256) a += partials[kSlots * b + k];
-    s[k][threadIdx.x] = a;
+__global__ void __launch_bounds__(kFinal) k_backward_final(const double* __restrict__ partials, int nblocks,
+                                                           const FinalOut o) {
+  __shared__ double s[kSlots][kFinal];
+  double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
+  // 8 CTAs' partials per thread and trip, loads independent of each other
+  for (int b0 = threadIdx.x; b0 < nblocks; b0 += 8 * kFinal) {
+    double2 v[8][2];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int b = b0 + u * kFinal;
+      const double2 z = make_double2(0.0, 0.0);
+      v[u][0] = b < nblocks ? reinterpret_cast<const double2*>(partials)[2 * b] : z;
+      v[u][1] = b < nblocks ? reinterpret_cast<const double2*>(partials)[2 * b + 1] : z;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      acc[0] += v[u][0].x;
+      acc[1] += v[u][0].y;
+      acc[2] += v[u][1].x;
+      acc[3] += v[u][1].y;
+    }
   }
+  for (int k = 0; k < kSlots; ++k) s[k][threadIdx.x] = acc[k];
   __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
+  for (int w = kFinal / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w)
       for (int k = 0; k < kSlots; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + w];
     __syncthreads();
@@ -296,17 +338,39 @@ __global__ void __launch_bounds__(256) k_backward_final(const double* __restrict
       }
 }
 
+// Rows per CTA of the staged backward kernels: the largest R in {128, 64, 32}
+// whose stage (nval values per incidence) fits in 64 KB, else in 160 KB.
+template <typename T>
+int bwd_rows(const tg_pattern* p, int nval, size_t* bytes) {
+  for (size_t lim : {64u * 1024u, 160u * 1024u})
+    for (int R : {128, 64, 32}) {
+      const size_t b = (size_t)nval * std::max(1, R * p->max_deg) * sizeof(T);
+      if (b <= lim) {
+        *bytes = b;
+        return R;
+      }
+    }
+  return 0;
+}
+
 template <int EL, typename T>
 tg_status launch(const tg_pattern* p, const BwdArgs<T>& a, bool fused, T* grad_c, cudaStream_t s) {
-  const int grid = tg::grid_for(p->N, BB);
+  size_t smem = 0;
+  const int R = bwd_rows<T>(p, tg::Elem<EL>::dim, &smem);
+  if (R == 0) return TG_ERR_UNSUPPORTED;
+  const int grid = tg::grid_for(p->N, R);
+  const int cap = std::max(1, R * p->max_deg);
   const tg::RefTab<T>& tab = tg::table<T>(p->el);
-  if (fused) k_backward_gather<EL, T, true><<<grid, BB, 0, s>>>(a, tab);
-  else k_backward_gather<EL, T, false><<<grid, BB, 0, s>>>(a, tab);
+  tg_status st = tg::set_smem(fused ? (const void*)k_backward_gather<EL, T, true>
+                                    : (const void*)k_backward_gather<EL, T, false>, smem);
+  if (st != TG_OK) return st;
+  if (fused) k_backward_gather<EL, T, true><<<grid, R, smem, s>>>(a, tab, cap);
+  else k_backward_gather<EL, T, false><<<grid, R, smem, s>>>(a, tab, cap);
   TG_CK_LAUNCH("k_backward_gather");
   T* gk_const = (a.layout == TG_CONSTANT) ? a.grad_kappa : nullptr;
   if (grad_c || gk_const) {
     FinalOut o{{grad_c, gk_const, nullptr, nullptr}, 2, 0};
-    k_backward_final<T><<<1, 256, 0, s>>>(a.partials, grid, o);
+    k_backward_final<T><<<1, kFinal, 0, s>>>(a.partials, grid, o);
     TG_CK_LAUNCH("k_backward_final");
   }
   return TG_OK;
@@ -367,39 +431,43 @@ struct LoadBwdArgs {
 };
 
 template <int EL, typename T, int NC>
-__global__ void __launch_bounds__(BB) k_load_backward(const LoadBwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab) {
+__global__ void __launch_bounds__(BB) k_load_backward(const LoadBwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
+                                                      int cap) {
   using El = tg::Elem<EL>;
   constexpr int NV = El::nv, D = El::dim, NQ = El::nq;
   __shared__ tg::RefTab<T> ts;
   __shared__ double red[BB / 32][NC];
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T* contrib = reinterpret_cast<T*>(dsm);  // [D + NC][cap]
   tg::copy_table(ts, tab);
-  const int64_t i = (int64_t)blockIdx.x * BB + threadIdx.x;
+  const int R = blockDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  const int64_t r1 = r0 + R < a.N ? r0 + R : a.N;
   double pk[NC];
 #pragma unroll
   for (int k = 0; k < NC; ++k) pk[k] = 0.0;
-  if (i < a.N) {
-    T gx[D], gf[NC];
+  const int J0 = __ldg(a.inc_ptr + r0), J1 = __ldg(a.inc_ptr + r1);
+  for (int j = J0 + (int)threadIdx.x; j < J1; j += R) {
+    const int ea = __ldg(a.inc_e + j);
+    const int64_t e = ea >> 3;
+    const int la = ea & 7;
+    const int kk = j - J0;
+    const int32_t* cl = a.cells + e * NV;
+    int v[NV];
 #pragma unroll
-    for (int r = 0; r < D; ++r) gx[r] = T(0);
+    for (int b = 0; b < NV; ++b) v[b] = __ldg(cl + b);
+    tg::Geom<D, T> g;
+    if constexpr (D == 2) tg::tri_geom(a.coords, v[0], v[1], v[2], g);
+    else tg::tet_geom(a.coords, v[0], v[1], v[2], v[3], g);
+    const T adet = tg::absv(g.det);
+    T gxc[D], gfc[NC];
 #pragma unroll
-    for (int k = 0; k < NC; ++k) gf[k] = T(0);
-    const int j0 = __ldg(a.inc_ptr + i), j1 = __ldg(a.inc_ptr + i + 1);
-    for (int j = j0; j < j1; ++j) {
-      const int ea = __ldg(a.inc_e + j);
-      const int64_t e = ea >> 3;
-      const int la = ea & 7;
-      const int32_t* cl = a.cells + e * NV;
-      int v[NV];
+    for (int r = 0; r < D; ++r) gxc[r] = T(0);
 #pragma unroll
-      for (int b = 0; b < NV; ++b) v[b] = __ldg(cl + b);
-      tg::Geom<D, T> g;
-      if constexpr (D == 2) tg::tri_geom(a.coords, v[0], v[1], v[2], g);
-      else tg::tet_geom(a.coords, v[0], v[1], v[2], v[3], g);
-      const T adet = tg::absv(g.det);
-      if (!(adet > tg::det_tiny<T>())) {
-        tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
-        continue;
-      }
+    for (int k = 0; k < NC; ++k) gfc[k] = T(0);
+    if (!(adet > tg::det_tiny<T>())) {
+      tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
+    } else {
       T gv[NV][NC];
 #pragma unroll
       for (int b = 0; b < NV; ++b)
@@ -413,7 +481,7 @@ __global__ void __launch_bounds__(BB) k_load_backward(const LoadBwdArgs<T> a, co
             T s = T(0);
 #pragma unroll
             for (int b = 0; b < NV; ++b) s += ts.M[b][la] * gv[b][k];
-            gf[k] += adet * s;
+            gfc[k] = adet * s;
           }
         } else if (la == 0) {
           if (a.layout == TG_PER_QP) {
@@ -476,22 +544,35 @@ __global__ void __launch_bounds__(BB) k_load_backward(const LoadBwdArgs<T> a, co
           T col[D + 1];
 #pragma unroll
           for (int b = 0; b <= D; ++b) col[b] = g.n[b][r];
-          gx[r] += sgn * Le * tg::sel(la, col);
+          gxc[r] = sgn * Le * tg::sel(la, col);
         }
       }
     }
+#pragma unroll
+    for (int r = 0; r < D; ++r) contrib[r * cap + kk] = gxc[r];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) contrib[(D + k) * cap + kk] = gfc[k];
+  }
+  __syncthreads();
+  const int64_t i = r0 + threadIdx.x;
+  if (i < r1) {
+    const int js = __ldg(a.inc_ptr + i) - J0, je = __ldg(a.inc_ptr + i + 1) - J0;
     if (a.grad_coords) {
 #pragma unroll
       for (int r = 0; r < D; ++r) {
+        T gx = T(0);
+        for (int k = js; k < je; ++k) gx += contrib[r * cap + k];
         T* d = a.grad_coords + i * D + r;
-        *d = a.accumulate ? *d + gx[r] : gx[r];
+        *d = a.accumulate ? *d + gx : gx;
       }
     }
     if (a.grad_f && a.layout == TG_PER_NODE) {
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
+        T gf = T(0);
+        for (int m = js; m < je; ++m) gf += contrib[(D + k) * cap + m];
         T* d = a.grad_f + i * NC + k;
-        *d = a.accumulate ? *d + gf[k] : gf[k];
+        *d = a.accumulate ? *d + gf : gf;
       }
     }
   }
@@ -509,7 +590,7 @@ __global__ void __launch_bounds__(BB) k_load_backward(const LoadBwdArgs<T> a, co
     for (int k = 0; k < kSlots; ++k) {
       double s = 0.0;
       if (k < NC)
-        for (int w = 0; w < BB / 32; ++w) s += red[w][k];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][k];
       a.partials[kSlots * blockIdx.x + k] = s;
     }
   }
@@ -517,15 +598,22 @@ __global__ void __launch_bounds__(BB) k_load_backward(const LoadBwdArgs<T> a, co
 
 template <int EL, typename T>
 tg_status launch_load_bwd(const tg_pattern* p, const LoadBwdArgs<T>& a, int ncomp, cudaStream_t s) {
-  const int grid = tg::grid_for(p->N, BB);
+  size_t smem = 0;
+  const int R = bwd_rows<T>(p, tg::Elem<EL>::dim + ncomp, &smem);
+  if (R == 0) return TG_ERR_UNSUPPORTED;
+  const int grid = tg::grid_for(p->N, R);
+  const int cap = std::max(1, R * p->max_deg);
   const tg::RefTab<T>& tab = tg::table<T>((tg_element)EL);
-  if (ncomp == 1) k_load_backward<EL, T, 1><<<grid, BB, 0, s>>>(a, tab);
-  else k_load_backward<EL, T, 3><<<grid, BB, 0, s>>>(a, tab);
+  tg_status st = tg::set_smem(ncomp == 1 ? (const void*)k_load_backward<EL, T, 1>
+                                         : (const void*)k_load_backward<EL, T, 3>, smem);
+  if (st != TG_OK) return st;
+  if (ncomp == 1) k_load_backward<EL, T, 1><<<grid, R, smem, s>>>(a, tab, cap);
+  else k_load_backward<EL, T, 3><<<grid, R, smem, s>>>(a, tab, cap);
   TG_CK_LAUNCH("k_load_backward");
   if (a.grad_f && a.layout == TG_CONSTANT) {
     FinalOut o{{nullptr, nullptr, nullptr, nullptr}, ncomp, a.accumulate};
     for (int k = 0; k < ncomp; ++k) o.out[k] = a.grad_f + k;
-    k_backward_final<T><<<1, 256, 0, s>>>(a.partials, grid, o);
+    k_backward_final<T><<<1, kFinal, 0, s>>>(a.partials, grid, o);
     TG_CK_LAUNCH("k_backward_final");
   }
   return TG_OK;

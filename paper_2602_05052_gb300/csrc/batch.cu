@@ -32,6 +32,8 @@ struct InstDesc {
   const int32_t* cells;
   int64_t N;
   unsigned long long* status;
+  const uint32_t* rec;
+  int64_t rec_stride;
 };
 
 template <typename T>
@@ -47,10 +49,10 @@ struct BatchCall {
 template <int EL, typename T, int BSZ>
 __global__ void __launch_bounds__(BSZ) k_batch(const InstDesc* __restrict__ desc, const int4* __restrict__ items,
                                                int64_t n_items, const __grid_constant__ BatchCall<T> call,
-                                               const __grid_constant__ tg::RefTab<T> tab) {
+                                               const __grid_constant__ tg::RefTab<T> tab, int cap) {
   extern __shared__ __align__(16) unsigned char smem[];
   auto& ts = *reinterpret_cast<tg::RefTab<T>*>(smem);
-  T* acc = reinterpret_cast<T*>(smem + tg::tab_bytes<T>()) + threadIdx.x;
+  unsigned char* buf = smem + tg::tab_bytes<T>();
   tg::copy_table(ts, tab);
   for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4 w = items[it];
@@ -71,7 +73,9 @@ __global__ void __launch_bounds__(BSZ) k_batch(const InstDesc* __restrict__ desc
     a.out = call.vals[k];
     a.n = d.N;
     a.status = d.status;
-    for (int64_t i = w.y + threadIdx.x; i < w.z; i += BSZ) tg::gather_row<EL, T, BSZ>(a, ts, acc, i);
+    a.rec = d.rec;
+    a.rec_stride = d.rec_stride;
+    for (int64_t r = w.y; r < w.z; r += BSZ) tg::assemble_block<EL, T>(a, ts, buf, cap, r, r + BSZ < w.z ? r + BSZ : w.z);
   }
 }
 
@@ -89,6 +93,7 @@ struct tg_batch {
   tg_element el = TG_P1_TRI;
   int n_inst = 0;
   int max_row_len = 0;
+  int max_deg = 0;
   int64_t total_rows = 0;
   std::vector<const tg_pattern*> pats;
   InstDesc* d_desc = nullptr;
@@ -119,7 +124,9 @@ template <int EL, typename T, int BSZ>
 tg_status launch_t(tg_batch* b, const void* const* coords, const void* const* kappa, tg_layout kl, const double* c,
                    void* const* vals, cudaStream_t s) {
   auto kern = k_batch<EL, T, BSZ>;
-  const size_t smem = tg::tab_bytes<T>() + (size_t)BSZ * b->max_row_len * sizeof(T);
+  using El = tg::Elem<EL>;
+  const int cap = std::max(1, BSZ * b->max_deg);
+  const size_t smem = tg::tab_bytes<T>() + tg::staged_bytes<T, El::nv, El::npw>(BSZ, cap, b->max_row_len);
   tg_status st = tg::set_smem((const void*)kern, smem);
   if (st != TG_OK) return st;
   int per_sm = b->sched.ctas_per_sm;
@@ -144,7 +151,7 @@ tg_status launch_t(tg_batch* b, const void* const* coords, const void* const* ka
     const int64_t i0 = b->chunk_items[ch], n_items = b->chunk_items[ch + 1] - i0;
     if (n_items == 0) continue;
     const int grid = (int)std::min<int64_t>(n_items, (int64_t)per_sm * tg::sm_count());
-    kern<<<grid, BSZ, smem, s>>>(b->d_desc, b->d_items + i0, n_items, call, tab);
+    kern<<<grid, BSZ, smem, s>>>(b->d_desc, b->d_items + i0, n_items, call, tab, cap);
     TG_CK_LAUNCH("k_batch");
   }
   return TG_OK;
@@ -214,8 +221,10 @@ tg_status tg_batch_create(const tg_pattern* const* pats, int32_t n_inst, tg_batc
     }
     b->pats.push_back(p);
     b->max_row_len = std::max(b->max_row_len, p->max_row_len);
+    b->max_deg = std::max(b->max_deg, p->max_deg);
     b->total_rows += p->N;
-    h[i] = InstDesc{p->row_ptr, p->inc_ptr, p->inc_e, p->inc_pos, p->cells, p->N, p->status};
+    h[i] = InstDesc{p->row_ptr, p->inc_ptr, p->inc_e, p->inc_pos, p->cells, p->N, p->status, p->rec,
+                    (p->E * p->nv + 3) & ~3ll};
   }
   cudaError_t e = cudaGetDevice(&b->device);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_desc, n_inst * sizeof(InstDesc));

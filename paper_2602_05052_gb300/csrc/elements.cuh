@@ -36,12 +36,9 @@ struct Geom {
 };
 
 template <typename T>
-__device__ __forceinline__ void tri_geom(const T* __restrict__ coords, int v0, int v1, int v2, Geom<2, T>& g) {
-  const auto x0 = ldg2(coords, v0);
-  const auto x1 = ldg2(coords, v1);
-  const auto x2 = ldg2(coords, v2);
-  const T e1x = x1.x - x0.x, e1y = x1.y - x0.y;
-  const T e2x = x2.x - x0.x, e2y = x2.y - x0.y;
+__device__ __forceinline__ void tri_geom_x(const T (&x0)[2], const T (&x1)[2], const T (&x2)[2], Geom<2, T>& g) {
+  const T e1x = x1[0] - x0[0], e1y = x1[1] - x0[1];
+  const T e2x = x2[0] - x0[0], e2y = x2[1] - x0[1];
   g.n[1][0] = e2y;
   g.n[1][1] = -e2x;
   g.n[2][0] = -e1y;
@@ -52,6 +49,15 @@ __device__ __forceinline__ void tri_geom(const T* __restrict__ coords, int v0, i
 }
 
 template <typename T>
+__device__ __forceinline__ void tri_geom(const T* __restrict__ coords, int v0, int v1, int v2, Geom<2, T>& g) {
+  const auto p0 = ldg2(coords, v0);
+  const auto p1 = ldg2(coords, v1);
+  const auto p2 = ldg2(coords, v2);
+  const T x0[2] = {p0.x, p0.y}, x1[2] = {p1.x, p1.y}, x2[2] = {p2.x, p2.y};
+  tri_geom_x(x0, x1, x2, g);
+}
+
+template <typename T>
 __device__ __forceinline__ void cross3(const T (&a)[3], const T (&b)[3], T (&c)[3]) {
   c[0] = a[1] * b[2] - a[2] * b[1];
   c[1] = a[2] * b[0] - a[0] * b[2];
@@ -59,16 +65,14 @@ __device__ __forceinline__ void cross3(const T (&a)[3], const T (&b)[3], T (&c)[
 }
 
 template <typename T>
-__device__ __forceinline__ void tet_geom(const T* __restrict__ coords, int v0, int v1, int v2, int v3,
-                                         Geom<3, T>& g) {
-  T x0[3], e[3][3];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) x0[r] = __ldg(coords + 3ll * v0 + r);
+__device__ __forceinline__ void tet_geom_x(const T (&x0)[3], const T (&x1)[3], const T (&x2)[3], const T (&x3)[3],
+                                           Geom<3, T>& g) {
+  T e[3][3];
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    e[0][r] = __ldg(coords + 3ll * v1 + r) - x0[r];
-    e[1][r] = __ldg(coords + 3ll * v2 + r) - x0[r];
-    e[2][r] = __ldg(coords + 3ll * v3 + r) - x0[r];
+    e[0][r] = x1[r] - x0[r];
+    e[1][r] = x2[r] - x0[r];
+    e[2][r] = x3[r] - x0[r];
   }
   cross3(e[1], e[2], g.n[1]);
   cross3(e[2], e[0], g.n[2]);
@@ -76,6 +80,18 @@ __device__ __forceinline__ void tet_geom(const T* __restrict__ coords, int v0, i
 #pragma unroll
   for (int r = 0; r < 3; ++r) g.n[0][r] = -(g.n[1][r] + g.n[2][r] + g.n[3][r]);
   g.det = e[0][0] * g.n[1][0] + e[0][1] * g.n[1][1] + e[0][2] * g.n[1][2];
+}
+
+template <typename T>
+__device__ __forceinline__ void tet_geom(const T* __restrict__ coords, int v0, int v1, int v2, int v3,
+                                         Geom<3, T>& g) {
+  T x[4][3];
+  const int v[4] = {v0, v1, v2, v3};
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) x[k][r] = __ldg(coords + 3ll * v[k] + r);
+  tet_geom_x(x[0], x[1], x[2], x[3], g);
 }
 
 // Determinant only (load vector).

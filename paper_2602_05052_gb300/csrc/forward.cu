@@ -15,6 +15,7 @@
 // the memory traffic.
 #include <cstdint>
 
+#include "async.cuh"
 #include "gather.cuh"
 
 namespace {
@@ -29,17 +30,183 @@ using tg::absv;
 using tg::load_kq;
 using tg::scalar_row;
 
-// One thread per CSR row.  Shared memory: the reference tables, then the
-// row accumulators acc[p * BS + tid] (conflict-free: one bank column per thread).
+// One CTA per block of R consecutive rows (staged gather, gather.cuh).
+// Shared memory: the reference tables, then the stage buffer.
 template <int EL, typename T>
-__global__ void __launch_bounds__(BS) k_bilinear_gather(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab) {
+__global__ void __launch_bounds__(BS) k_bilinear_gather(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
+                                                        int cap) {
   extern __shared__ __align__(16) unsigned char smem[];
   auto& ts = *reinterpret_cast<tg::RefTab<T>*>(smem);
-  T* acc = reinterpret_cast<T*>(smem + tab_bytes<T>()) + threadIdx.x;
   copy_table(ts, tab);
-  const int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
-  if (i >= a.n) return;
-  tg::gather_row<EL, T, BS>(a, ts, acc, i);
+  const int64_t r0 = (int64_t)blockIdx.x * blockDim.x;
+  const int64_t r1 = r0 + blockDim.x < a.n ? r0 + blockDim.x : a.n;
+  tg::assemble_rows<EL, T>(a, ts, smem + tab_bytes<T>(), cap, r0, r1);
+}
+
+// P1 fast path (incidence records) as a persistent, software-pipelined
+// kernel.  Each CTA walks row blocks b = blockIdx.x, + gridDim.x, ...; the
+// contiguous streams of a block (its slices of inc_ptr, row_ptr and the
+// records) are brought into one of two shared-memory stages by 1D bulk
+// copies that thread 0 issues one block ahead, completing on the stage's
+// mbarrier, while the whole CTA processes the previous block.  Only the
+// gathers of coordinates and coefficients remain on the critical path.
+//
+// Stage s: ip [IPN] | rp [IPN] | rec [NV][RECN], IPN = R + 8, RECN = cap + 8
+// (bulk copies move whole 16-byte groups, so ranges are widened to
+// multiples of 4 words; the pattern arrays carry 16 bytes of tail padding).
+template <int D, typename T>
+__global__ void __launch_bounds__(BS, (D == 2 && sizeof(T) == 4) ? 5 : 1) k_bilinear_p1(
+    const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab, int cap, int64_t nblocks) {
+  constexpr int NV = D + 1, NQ = D == 2 ? 3 : 4;
+  constexpr int UB = (D == 2 && sizeof(T) == 4) ? 3 : 2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  auto& ts = *reinterpret_cast<tg::RefTab<T>*>(smem);
+  const int R = blockDim.x;
+  const int IPN = R + 8, RECN = cap + 8;
+  unsigned char* p = smem + tab_bytes<T>();
+  uint64_t* bar = reinterpret_cast<uint64_t*>(p);
+  p += 16;
+  int* meta = reinterpret_cast<int*>(p);  // [2][8]: r0, r1, J0, J1, a0, j0a
+  p += 64;
+  int* st_ip[2];
+  int* st_rp[2];
+  uint32_t* st_rec[2];
+  for (int s = 0; s < 2; ++s) {
+    st_ip[s] = reinterpret_cast<int*>(p);
+    p += IPN * 4;
+    st_rp[s] = reinterpret_cast<int*>(p);
+    p += IPN * 4;
+    st_rec[s] = reinterpret_cast<uint32_t*>(p);
+    p += (size_t)NV * RECN * 4;
+  }
+  T* contrib = reinterpret_cast<T*>(p);
+  uint32_t* posw = reinterpret_cast<uint32_t*>(contrib + (size_t)NV * cap);
+  uint8_t* owner = reinterpret_cast<uint8_t*>(posw + cap);
+  T* acc = reinterpret_cast<T*>(p + tg::staged_head<T, NV, 1>(cap));
+  if (threadIdx.x == 0) {
+    tg::mbar_init(&bar[0], 1);
+    tg::mbar_init(&bar[1], 1);
+    tg::fence_mbar_init();
+  }
+  copy_table(ts, tab);  // includes a CTA barrier
+
+  const int64_t G = gridDim.x;
+  const int64_t stride = a.rec_stride;
+  // issue the copies of block blk into stage s (thread 0)
+  auto issue = [&](int s, int64_t blk, int J0, int J1) {
+    const int r0 = (int)(blk * R), r1 = (int)(blk * R + R < a.n ? blk * R + R : a.n);
+    const int a0 = r0 & ~3, nip = (r1 + 1 - a0 + 3) & ~3;
+    const int j0a = J0 & ~3, nrec = (J1 - j0a + 3) & ~3;
+    int* m = meta + 8 * s;
+    m[0] = r0;
+    m[1] = r1;
+    m[2] = J0;
+    m[3] = J1;
+    m[4] = a0;
+    m[5] = j0a;
+    const uint32_t bytes = 2u * nip * 4 + (J1 > J0 ? (uint32_t)NV * nrec * 4 : 0u);
+    tg::fence_proxy_async();
+    tg::mbar_arrive_expect_tx(&bar[s], bytes);
+    tg::bulk_copy_g2s(st_ip[s], a.inc_ptr + a0, nip * 4, &bar[s]);
+    tg::bulk_copy_g2s(st_rp[s], a.row_ptr + a0, nip * 4, &bar[s]);
+    if (J1 > J0)
+      for (int k = 0; k < NV; ++k) tg::bulk_copy_g2s(st_rec[s] + k * RECN, a.rec + k * stride + j0a, nrec * 4, &bar[s]);
+  };
+  auto block_J = [&](int64_t blk, int& J0, int& J1) {
+    J0 = __ldg(a.inc_ptr + blk * R);
+    J1 = __ldg(a.inc_ptr + (blk * R + R < a.n ? blk * R + R : a.n));
+  };
+
+  int64_t b = blockIdx.x;
+  int nJ0 = 0, nJ1 = 0;
+  if (threadIdx.x == 0 && b < nblocks) {
+    int J0, J1;
+    block_J(b, J0, J1);
+    issue(0, b, J0, J1);
+    if (b + G < nblocks) block_J(b + G, nJ0, nJ1);
+  }
+  for (int k = 0; b < nblocks; ++k, b += G) {
+    const int s = k & 1;
+    if (threadIdx.x == 0 && b + G < nblocks) {
+      issue(s ^ 1, b + G, nJ0, nJ1);
+      if (b + 2 * G < nblocks) block_J(b + 2 * G, nJ0, nJ1);
+    }
+    if (!tg::mbar_wait(&bar[s], (k >> 1) & 1)) {
+      tg::record_error(a.status, TG_ERR_TIMEOUT, 0);
+      return;
+    }
+    const int* m = meta + 8 * s;
+    const int r0 = m[0], r1 = m[1], J0 = m[2], J1 = m[3], a0 = m[4], j0a = m[5];
+    const int* ip = st_ip[s] - a0;  // ip[i] = inc_ptr[i] for i in [r0, r1]
+    const int* rp = st_rp[s] - a0;
+    const uint32_t* rc = st_rec[s] - j0a;
+    // phase 0: incidence -> row map
+    const int i = r0 + (int)threadIdx.x;
+    int js = 0, je = 0;
+    if (i < r1) {
+      js = ip[i] - J0;
+      je = ip[i + 1] - J0;
+      for (int q = js; q < je; ++q) owner[q] = (uint8_t)threadIdx.x;
+    }
+    __syncthreads();
+    // phase 1: element rows of every incidence of the block
+    for (int base = J0 + (int)threadIdx.x; base < J1; base += UB * R) {
+      uint32_t ra[UB], rv[UB][D];
+      int own[UB];
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int j = base + u * R;
+        const bool ok = j < J1;
+        ra[u] = ok ? rc[j] : 0u;
+#pragma unroll
+        for (int q = 0; q < D; ++q) rv[u][q] = ok ? rc[(q + 1) * RECN + j] : 0u;
+        own[u] = r0 + (ok ? owner[j - J0] : 0);
+      }
+      T x[UB][NV][D];
+      T kq[UB][NQ];
+#pragma unroll
+      for (int u = 0; u < UB; ++u) tg::p1_gather<D, T>(a, ra[u], rv[u], own[u], x[u], kq[u]);
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int j = base + u * R;
+        if (j >= J1) continue;
+        T Krow[NV];
+        if (!tg::p1_local_row<D, T>(x[u], kq[u], a.c, ts, Krow)) {
+          tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, ra[u] & 0xffffffu);
+#pragma unroll
+          for (int q = 0; q < NV; ++q) Krow[q] = T(0);
+        }
+        posw[j - J0] = tg::p1_positions<D>(ra[u], rv[u]);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) contrib[q * cap + (j - J0)] = Krow[q];
+      }
+    }
+    __syncthreads();
+    // phase 2: rows summed in increasing element order into the CSR-local copy
+    const int rbase = rp[r0];
+    if (i < r1) {
+      T* row = acc + (rp[i] - rbase);
+      const int len = rp[i + 1] - rp[i];
+      for (int q = 0; q < len; ++q) row[q] = T(0);
+      for (int q = js; q < je; ++q) {
+        const uint32_t w0 = posw[q];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) row[tg::pos_of(w0, 0u, c)] += contrib[c * cap + q];
+      }
+    }
+    __syncthreads();
+    const int nz = rp[r1] - rbase;
+    T* out = a.out + rbase;
+    for (int q = threadIdx.x; q < nz; q += R) out[q] = acc[q];
+    __syncthreads();  // stage s and the work buffers are free again
+  }
+}
+
+template <int D, typename T>
+size_t p1_pipe_smem(int R, int cap, int max_row) {
+  constexpr int NV = D + 1;
+  return tab_bytes<T>() + 16 + 64 + 2 * ((size_t)(R + 8) * 8 + (size_t)NV * (cap + 8) * 4) +
+         tg::staged_bytes<T, NV, 1>(R, cap, max_row);
 }
 
 // Comparison point: classic scatter-add (Eq. (scatter_add)) with atomics,
@@ -65,33 +232,37 @@ __global__ void __launch_bounds__(BS) k_bilinear_atomic(const FwdArgs<T> a, cons
   }
 }
 
-// Load vector, one thread per node (NC components per node).
+// Load vector, staged like the bilinear kernel: phase 1 evaluates one
+// (element, local node) visit per thread into contrib [NC][cap], phase 2
+// sums each node's visits in increasing element order.
 template <int EL, typename T, int NC>
-__global__ void __launch_bounds__(BS) k_load_gather(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab) {
+__global__ void __launch_bounds__(BS) k_load_gather(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
+                                                    int cap) {
   using El = tg::Elem<EL>;
   extern __shared__ __align__(16) unsigned char smem[];
   auto& ts = *reinterpret_cast<tg::RefTab<T>*>(smem);
+  T* contrib = reinterpret_cast<T*>(smem + tab_bytes<T>());
   copy_table(ts, tab);
-  const int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
-  if (i >= a.n) return;
-  T F[NC];
-#pragma unroll
-  for (int k = 0; k < NC; ++k) F[k] = T(0);
-  const int j0 = __ldg(a.inc_ptr + i), j1 = __ldg(a.inc_ptr + i + 1);
-  for (int j = j0; j < j1; ++j) {
+  const int R = blockDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  const int64_t r1 = r0 + R < a.n ? r0 + R : a.n;
+  const int J0 = __ldg(a.inc_ptr + r0), J1 = __ldg(a.inc_ptr + r1);
+#pragma unroll 2
+  for (int j = J0 + (int)threadIdx.x; j < J1; j += R) {
     const int ea = __ldg(a.inc_e + j);
     const int64_t e = ea >> 3;
     const int la = ea & 7;
     const int32_t* cl = a.cells + e * El::nv;
+    T F[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) F[k] = T(0);
     T det;
     if constexpr (El::dim == 2) det = tg::tri_det(a.coords, __ldg(cl), __ldg(cl + 1), __ldg(cl + 2));
     else det = tg::tet_det(a.coords, __ldg(cl), __ldg(cl + 1), __ldg(cl + 2), __ldg(cl + 3));
     const T adet = absv(det);
     if (!(adet > tg::det_tiny<T>())) {
       tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
-      continue;
-    }
-    if (a.layout == TG_PER_NODE) {
+    } else if (a.layout == TG_PER_NODE) {
       int v[El::nv];
 #pragma unroll
       for (int b = 0; b < El::nv; ++b) v[b] = __ldg(cl + b);
@@ -114,9 +285,19 @@ __global__ void __launch_bounds__(BS) k_load_gather(const FwdArgs<T> a, const __
 #pragma unroll
       for (int k = 0; k < NC; ++k) F[k] += adet * ts.m1[la] * __ldg(a.coef + k);
     }
-  }
 #pragma unroll
-  for (int k = 0; k < NC; ++k) a.out[i * NC + k] = F[k];
+    for (int k = 0; k < NC; ++k) contrib[k * cap + (j - J0)] = F[k];
+  }
+  __syncthreads();
+  const int64_t i = r0 + threadIdx.x;
+  if (i >= r1) return;
+  const int js = __ldg(a.inc_ptr + i) - J0, je = __ldg(a.inc_ptr + i + 1) - J0;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    T s = T(0);
+    for (int m = js; m < je; ++m) s += contrib[k * cap + m];
+    a.out[i * NC + k] = s;
+  }
 }
 
 // Vector P1 elasticity, one thread per node: the node's three DoF rows are
@@ -196,6 +377,8 @@ FwdArgs<T> base_args(const tg_pattern* p, const void* coords) {
   a.out = nullptr;
   a.n = p->N;
   a.status = p->status;
+  a.rec = p->rec;
+  a.rec_stride = (p->E * p->nv + 3) & ~3ll;
   return a;
 }
 
@@ -213,10 +396,39 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
     TG_CK_LAUNCH("k_bilinear_atomic");
     return TG_OK;
   }
-  const size_t smem = tab_bytes<T>() + (size_t)BS * p->max_row_len * sizeof(T);
+  using El = tg::Elem<EL>;
+  size_t stage = 0;
+  const int R = tg::staged_rows<T, El::nv, El::npw>(p->max_deg, p->max_row_len, &stage);
+  if (R == 0) {
+    tg::set_error("mesh degree too large for the staged gather");
+    return TG_ERR_UNSUPPORTED;
+  }
+  const size_t smem = tab_bytes<T>() + stage;
+  const int cap = std::max(1, R * p->max_deg);
+  if constexpr (EL == TG_P1_TRI || EL == TG_P1_TET) {
+    if (p->rec) {
+      constexpr int D = El::dim;
+      // rows per block: the largest R in {128, 64, 32} whose two stages and
+      // work buffers fit in 100 KB (at least two CTAs per SM)
+      int Rp = 128;
+      while (Rp > 32 && p1_pipe_smem<D, T>(Rp, Rp * std::max(1, p->max_deg), p->max_row_len) > 100 * 1024) Rp /= 2;
+      const int capp = Rp * std::max(1, p->max_deg);
+      const size_t smp = p1_pipe_smem<D, T>(Rp, capp, p->max_row_len);
+      auto kern = k_bilinear_p1<D, T>;
+      tg_status st = set_smem((const void*)kern, smp);
+      if (st != TG_OK) return st;
+      int per_sm = 0;
+      TG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Rp, smp));
+      const int64_t nblocks = (p->N + Rp - 1) / Rp;
+      const int grid = (int)std::min<int64_t>(nblocks, (int64_t)std::max(per_sm, 1) * tg::sm_count());
+      kern<<<grid, Rp, smp, s>>>(a, tab, capp, nblocks);
+      TG_CK_LAUNCH("k_bilinear_p1");
+      return TG_OK;
+    }
+  }
   tg_status st = set_smem((const void*)k_bilinear_gather<EL, T>, smem);
   if (st != TG_OK) return st;
-  k_bilinear_gather<EL, T><<<tg::grid_for(p->N, BS), BS, smem, s>>>(a, tab);
+  k_bilinear_gather<EL, T><<<tg::grid_for(p->N, R), R, smem, s>>>(a, tab, cap);
   TG_CK_LAUNCH("k_bilinear_gather");
   return TG_OK;
 }
@@ -256,18 +468,28 @@ tg_status load(const tg_pattern* p, const void* coords, const void* f, tg_layout
   a.out = static_cast<T*>(F);
   const tg_element el = p->el == TG_P1_TET_VEC3 ? TG_P1_TET : p->el;
   const tg::RefTab<T>& tab = table<T>(el);
-  const size_t smem = tab_bytes<T>();
-  const int grid = tg::grid_for(p->N, BS);
+  // rows per CTA: the largest R in {128, 64, 32} whose stage fits in 64 KB
+  int R = BS;
+  while (R > 32 && (size_t)ncomp * R * p->max_deg * sizeof(T) > 64 * 1024) R /= 2;
+  const int cap = std::max(1, R * p->max_deg);
+  const size_t smem = tab_bytes<T>() + (size_t)ncomp * cap * sizeof(T);
+  const int grid = tg::grid_for(p->N, R);
+  tg_status st = TG_OK;
+  auto go = [&](auto kern) {
+    if ((st = set_smem((const void*)kern, smem)) != TG_OK) return;
+    kern<<<grid, R, smem, s>>>(a, tab, cap);
+  };
   if (el == TG_P1_TRI) {
-    if (ncomp == 1) k_load_gather<TG_P1_TRI, T, 1><<<grid, BS, smem, s>>>(a, tab);
-    else k_load_gather<TG_P1_TRI, T, 3><<<grid, BS, smem, s>>>(a, tab);
+    if (ncomp == 1) go(k_load_gather<TG_P1_TRI, T, 1>);
+    else go(k_load_gather<TG_P1_TRI, T, 3>);
   } else if (el == TG_P2_TRI) {
-    if (ncomp == 1) k_load_gather<TG_P2_TRI, T, 1><<<grid, BS, smem, s>>>(a, tab);
-    else k_load_gather<TG_P2_TRI, T, 3><<<grid, BS, smem, s>>>(a, tab);
+    if (ncomp == 1) go(k_load_gather<TG_P2_TRI, T, 1>);
+    else go(k_load_gather<TG_P2_TRI, T, 3>);
   } else {
-    if (ncomp == 1) k_load_gather<TG_P1_TET, T, 1><<<grid, BS, smem, s>>>(a, tab);
-    else k_load_gather<TG_P1_TET, T, 3><<<grid, BS, smem, s>>>(a, tab);
+    if (ncomp == 1) go(k_load_gather<TG_P1_TET, T, 1>);
+    else go(k_load_gather<TG_P1_TET, T, 3>);
   }
+  if (st != TG_OK) return st;
   TG_CK_LAUNCH("k_load_gather");
   return TG_OK;
 }

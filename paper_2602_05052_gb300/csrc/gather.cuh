@@ -1,8 +1,9 @@
 // Row-owner gather shared by the single-instance and batched kernels:
 // the fused Map (Algorithm 1) and the deterministic Reduce (Algorithm 2) of
-// one CSR row.  See forward.cu for the design.
+// a block of CSR rows.  See forward.cu for the design.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 
 #include "elements.cuh"
@@ -25,6 +26,8 @@ struct FwdArgs {
   T* __restrict__ out;
   int64_t n;  // rows (gather kernels) or elements (atomic kernel)
   unsigned long long* status;
+  const uint32_t* __restrict__ rec;  // P1 incidence records (NULL: generic path)
+  int64_t rec_stride;                // incidences (E * nv)
 };
 
 template <typename T>
@@ -56,65 +59,335 @@ __device__ __forceinline__ void load_kq(const T* __restrict__ v, int layout, int
   }
 }
 
-// Local row la of element e for the scalar form; false for a degenerate element.
+// Element inputs of the scalar Map, loaded in two dependent levels so that
+// several elements can be in flight per thread: ids (vertex indices), then
+// data (vertex coordinates and the coefficient at the points).
 template <int EL, typename T>
-__device__ __forceinline__ bool scalar_row(const FwdArgs<T>& a, const RefTab<T>& ts, int64_t e, int la,
-                                           T (&Krow)[Elem<EL>::nv]) {
-  using El = Elem<EL>;
-  const int32_t* cl = a.cells + e * El::nv;
-  if constexpr (EL == TG_P1_TRI) {
-    Geom<2, T> g;
-    tri_geom(a.coords, __ldg(cl), __ldg(cl + 1), __ldg(cl + 2), g);
-    const T adet = absv(g.det);
-    if (!(adet > det_tiny<T>())) return false;
-    const T inv = T(1) / adet;
-    const T s = weighted_coef<T, El::nq>(a.coef, a.layout, e, ts.w, ts.wsum) * inv;
-    p1_row<2, T>(g, la, s, a.c * adet, ts.M[la], Krow);
-  } else if constexpr (EL == TG_P1_TET) {
-    Geom<3, T> g;
-    tet_geom(a.coords, __ldg(cl), __ldg(cl + 1), __ldg(cl + 2), __ldg(cl + 3), g);
-    const T adet = absv(g.det);
-    if (!(adet > det_tiny<T>())) return false;
-    const T inv = T(1) / adet;
-    const T s = weighted_coef<T, El::nq>(a.coef, a.layout, e, ts.w, ts.wsum) * inv;
-    p1_row<3, T>(g, la, s, a.c * adet, ts.M[la], Krow);
+struct ElemIn {
+  static constexpr int NG = Elem<EL>::ngeo, D = Elem<EL>::dim, NQ = Elem<EL>::nq;
+  int v[NG];
+  T x[NG][D];
+  T kq[NQ];
+};
+
+template <int EL, typename T>
+__device__ __forceinline__ void elem_ids(const FwdArgs<T>& a, int64_t e, ElemIn<EL, T>& in) {
+  const int32_t* cl = a.cells + e * Elem<EL>::nv;
+#pragma unroll
+  for (int k = 0; k < ElemIn<EL, T>::NG; ++k) in.v[k] = __ldg(cl + k);
+}
+
+template <int EL, typename T>
+__device__ __forceinline__ void elem_data(const FwdArgs<T>& a, int64_t e, ElemIn<EL, T>& in) {
+  constexpr int NG = ElemIn<EL, T>::NG, D = ElemIn<EL, T>::D, NQ = ElemIn<EL, T>::NQ;
+#pragma unroll
+  for (int k = 0; k < NG; ++k) {
+    if constexpr (D == 2) {
+      const auto p = ldg2(a.coords, in.v[k]);
+      in.x[k][0] = p.x;
+      in.x[k][1] = p.y;
+    } else {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) in.x[k][r] = __ldg(a.coords + 3ll * in.v[k] + r);
+    }
+  }
+  if (a.layout == TG_PER_QP) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) in.kq[q] = __ldg(a.coef + e * NQ + q);
   } else {
+    const T k = a.layout == TG_PER_ELEMENT ? __ldg(a.coef + e) : __ldg(a.coef);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) in.kq[q] = k;
+  }
+}
+
+// Row la of the local matrix from loaded inputs; false for a degenerate
+// element.  Same arithmetic, operation for operation, as scalar_row.
+template <int EL, typename T>
+__device__ __forceinline__ bool elem_row(const ElemIn<EL, T>& in, T c, const RefTab<T>& ts, int la,
+                                         T (&Krow)[Elem<EL>::nv]) {
+  if constexpr (EL == TG_P1_TRI || EL == TG_P2_TRI) {
     Geom<2, T> g;
-    tri_geom(a.coords, __ldg(cl), __ldg(cl + 1), __ldg(cl + 2), g);
+    tri_geom_x(in.x[0], in.x[1], in.x[2], g);
     const T adet = absv(g.det);
     if (!(adet > det_tiny<T>())) return false;
-    T kq[6];
-    load_kq<T, 6>(a.coef, a.layout, e, kq);
-    p2_row<T>(g, la, kq, T(1) / adet, a.c * adet, ts, Krow);
+    if constexpr (EL == TG_P1_TRI) {
+      const T inv = T(1) / adet;
+      T s = T(0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) s += ts.w[q] * in.kq[q];
+      p1_row<2, T>(g, la, s * inv, c * adet, ts.M[la], Krow);
+    } else {
+      p2_row<T>(g, la, in.kq, T(1) / adet, c * adet, ts, Krow);
+    }
+  } else {
+    Geom<3, T> g;
+    tet_geom_x(in.x[0], in.x[1], in.x[2], in.x[3], g);
+    const T adet = absv(g.det);
+    if (!(adet > det_tiny<T>())) return false;
+    const T inv = T(1) / adet;
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s += ts.w[q] * in.kq[q];
+    p1_row<3, T>(g, la, s * inv, c * adet, ts.M[la], Krow);
   }
   return true;
 }
 
+// Local row la of element e for the scalar form; false for a degenerate element.
+template <int EL, typename T>
+__device__ __forceinline__ bool scalar_row(const FwdArgs<T>& a, const RefTab<T>& ts, int64_t e, int la,
+                                           T (&Krow)[Elem<EL>::nv]) {
+  ElemIn<EL, T> in;
+  elem_ids<EL, T>(a, e, in);
+  elem_data<EL, T>(a, e, in);
+  return elem_row<EL, T>(in, a.c, ts, la, Krow);
+}
 
-// Accumulate and store CSR row i.  acc points at this thread's column of
-// the shared accumulators (stride BSZ).
-template <int EL, typename T, int BSZ>
-__device__ __forceinline__ void gather_row(const FwdArgs<T>& a, const RefTab<T>& ts, T* acc, int64_t i) {
-  using El = Elem<EL>;
-  const int r0 = __ldg(a.row_ptr + i), len = __ldg(a.row_ptr + i + 1) - r0;
-  for (int p = 0; p < len; ++p) acc[p * BSZ] = T(0);
-  const int j0 = __ldg(a.inc_ptr + i), j1 = __ldg(a.inc_ptr + i + 1);
-  for (int j = j0; j < j1; ++j) {
-    const int ea = __ldg(a.inc_e + j);
-    const int64_t e = ea >> 3;
-    const int la = ea & 7;
-    const uint32_t w0 = __ldg(a.inc_pos + (int64_t)j * El::npw);
-    const uint32_t w1 = El::npw == 2 ? __ldg(a.inc_pos + (int64_t)j * El::npw + 1) : 0u;
-    T Krow[El::nv];
-    if (!scalar_row<EL, T>(a, ts, e, la, Krow)) {
-      record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
-      continue;
-    }
+// Accumulate and store CSR rows.
+//
+// Staged form used by every scalar forward kernel: a CTA owns the rows
+// [r0, r1) (R = blockDim.x of them) and therefore the contiguous incidence
+// range [inc_ptr[r0], inc_ptr[r1]) and the contiguous CSR value range
+// [row_ptr[r0], row_ptr[r1]).
+//   phase 1: all threads stride over the incidence range, UB incidences in
+//            flight per thread, and evaluate the element rows (independent
+//            loads: high memory-level parallelism); the rows and their
+//            column positions go to shared memory;
+//   phase 2: thread t sums the incidences of row r0 + t from shared memory
+//            in increasing element order into the row's slice of a CSR-local
+//            shared copy of the CTA's values;
+//   store:   the CTA writes its value range with coalesced stores.
+// Every slot is summed in the order of the one-thread-per-row formulation,
+// so the results are bitwise reproducible and independent of R.
+//
+// Shared buffer: contrib [NV][cap] T | posw [NPW][cap] u32 | owner [cap] u8 |
+// acc [R * max_row] T, with cap >= R * max_degree.
+template <typename T, int NV, int NPW>
+__host__ __device__ constexpr size_t staged_head(int cap) {
+  return ((size_t)NV * cap * sizeof(T) + (size_t)NPW * cap * 4 + (size_t)cap + 15) & ~size_t(15);
+}
+
+template <typename T, int NV, int NPW>
+__host__ __device__ constexpr size_t staged_bytes(int R, int cap, int max_row) {
+  return staged_head<T, NV, NPW>(cap) + (size_t)max_row * R * sizeof(T);
+}
+
+// Phase 2 and the coalesced store, shared by both phase-1 variants.
+template <typename T, int NV, int NPW>
+__device__ __forceinline__ void reduce_rows(const FwdArgs<T>& a, const T* contrib, const uint32_t* posw, T* acc,
+                                            int cap, int64_t r0, int64_t r1, int J0) {
+  const int R = blockDim.x;
+  const int64_t i = r0 + threadIdx.x;
+  const int rbase = __ldg(a.row_ptr + r0);
+  if (i < r1) {
+    const int rs = __ldg(a.row_ptr + i) - rbase, len = __ldg(a.row_ptr + i + 1) - rbase - rs;
+    T* row = acc + rs;
+    for (int p = 0; p < len; ++p) row[p] = T(0);
+    const int js = __ldg(a.inc_ptr + i) - J0, je = __ldg(a.inc_ptr + i + 1) - J0;
+    for (int k = js; k < je; ++k) {
+      const uint32_t w0 = posw[k];
+      const uint32_t w1 = NPW == 2 ? posw[cap + k] : 0u;
 #pragma unroll
-    for (int b = 0; b < El::nv; ++b) acc[pos_of(w0, w1, b) * BSZ] += Krow[b];
+      for (int b = 0; b < NV; ++b) row[pos_of(w0, w1, b)] += contrib[b * cap + k];
+    }
   }
-  T* out = a.out + r0;
-  for (int p = 0; p < len; ++p) out[p] = acc[p * BSZ];
+  __syncthreads();
+  const int nz = __ldg(a.row_ptr + r1) - rbase;
+  T* out = a.out + rbase;
+  for (int k = threadIdx.x; k < nz; k += R) out[k] = acc[k];
+  __syncthreads();  // the buffer is reused by the next row block
+}
+
+// Incidences in flight per thread in phase 1 (bounded by registers).
+template <int EL, typename T>
+__host__ __device__ constexpr int ub_of() {
+  return EL == TG_P1_TRI ? 4 : EL == TG_P2_TRI ? 2 : (sizeof(T) == 4 ? 3 : 2);
+}
+
+template <int EL, typename T>
+__device__ __forceinline__ void assemble_rows(const FwdArgs<T>& a, const RefTab<T>& ts, unsigned char* buf, int cap,
+                                              int64_t r0, int64_t r1) {
+  using El = Elem<EL>;
+  constexpr int NV = El::nv, NPW = El::npw;
+  const int R = blockDim.x;
+  T* contrib = reinterpret_cast<T*>(buf);
+  uint32_t* posw = reinterpret_cast<uint32_t*>(contrib + (size_t)NV * cap);
+  T* acc = reinterpret_cast<T*>(buf + staged_head<T, NV, NPW>(cap));
+  const int J0 = __ldg(a.inc_ptr + r0), J1 = __ldg(a.inc_ptr + r1);
+  // UB incidences per thread in flight: every load of one dependency level
+  // (incidence record, then vertex ids, then coordinates and coefficients)
+  // is issued for all of them before any is used.
+  constexpr int UB = ub_of<EL, T>();
+  for (int base = J0 + (int)threadIdx.x; base < J1; base += UB * R) {
+    int ea[UB];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int j = base + u * R;
+      ea[u] = j < J1 ? __ldg(a.inc_e + j) : 0;
+      if (j < J1) {
+        posw[j - J0] = __ldg(a.inc_pos + (int64_t)j * NPW);
+        if (NPW == 2) posw[cap + j - J0] = __ldg(a.inc_pos + (int64_t)j * NPW + 1);
+      }
+    }
+    ElemIn<EL, T> in[UB];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) elem_ids<EL, T>(a, ea[u] >> 3, in[u]);
+#pragma unroll
+    for (int u = 0; u < UB; ++u) elem_data<EL, T>(a, ea[u] >> 3, in[u]);
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int j = base + u * R;
+      if (j < J1) {
+        T Krow[NV];
+        if (!elem_row<EL, T>(in[u], a.c, ts, ea[u] & 7, Krow)) {
+          record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, ea[u] >> 3);
+#pragma unroll
+          for (int b = 0; b < NV; ++b) Krow[b] = T(0);
+        }
+#pragma unroll
+        for (int b = 0; b < NV; ++b) contrib[b * cap + (j - J0)] = Krow[b];
+      }
+    }
+  }
+  __syncthreads();
+  reduce_rows<T, NV, NPW>(a, contrib, posw, acc, cap, r0, r1, J0);
+}
+
+// P1 fast path of assemble_rows, reading the incidence records (rec): the
+// record carries the element index and the other vertex ids with their
+// column positions, and the own vertex is the row itself (found through a
+// shared-memory map from incidence to row), so phase 1 is two dependent
+// loads deep (record, then coordinates and coefficients) instead of three.
+// With the own vertex first, the row is row 0 of the local matrix of the
+// cyclically reordered element; |det J|, the gradients and the symmetric P1
+// rules do not depend on the vertex order, so the entries are those of the
+// generic path up to rounding (and bitwise identical across runs).
+// Vertex coordinates (own vertex first) and the coefficient at the points of
+// one incidence from its record words.
+template <int D, typename T>
+__device__ __forceinline__ void p1_gather(const FwdArgs<T>& a, uint32_t ra, const uint32_t (&rv)[D], int own,
+                                          T (&x)[D + 1][D], T (&kq)[D == 2 ? 3 : 4]) {
+  constexpr int NV = D + 1, NQ = D == 2 ? 3 : 4;
+  int vid[NV];
+  vid[0] = own;
+#pragma unroll
+  for (int k = 0; k < D; ++k) vid[k + 1] = (int)(rv[k] & 0xffffffu);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    if constexpr (D == 2) {
+      const auto p = ldg2(a.coords, vid[k]);
+      x[k][0] = p.x;
+      x[k][1] = p.y;
+    } else {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) x[k][r] = __ldg(a.coords + 3ll * vid[k] + r);
+    }
+  }
+  const int64_t e = ra & 0xffffffu;
+  if (a.layout == TG_PER_QP) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) kq[q] = __ldg(a.coef + e * NQ + q);
+  } else {
+    const T k = a.layout == TG_PER_ELEMENT ? __ldg(a.coef + e) : __ldg(a.coef);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) kq[q] = k;
+  }
+}
+
+// Row 0 (the own vertex) of the local P1 matrix; false for a degenerate element.
+template <int D, typename T>
+__device__ __forceinline__ bool p1_local_row(const T (&x)[D + 1][D], const T (&kq)[D == 2 ? 3 : 4], T c,
+                                             const RefTab<T>& ts, T (&Krow)[D + 1]) {
+  constexpr int NQ = D == 2 ? 3 : 4;
+  Geom<D, T> g;
+  if constexpr (D == 2) tri_geom_x(x[0], x[1], x[2], g);
+  else tet_geom_x(x[0], x[1], x[2], x[3], g);
+  const T adet = absv(g.det);
+  if (!(adet > det_tiny<T>())) return false;
+  const T inv = T(1) / adet;
+  T s = T(0);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) s += ts.w[q] * kq[q];
+  p1_row<D, T>(g, 0, s * inv, c * adet, ts.M[0], Krow);
+  return true;
+}
+
+// Packed column positions (own first) of an incidence.
+template <int D>
+__device__ __forceinline__ uint32_t p1_positions(uint32_t ra, const uint32_t (&rv)[D]) {
+  uint32_t pw = ra >> 24;
+#pragma unroll
+  for (int k = 0; k < D; ++k) pw |= (rv[k] >> 24) << (8 * (k + 1));
+  return pw;
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void assemble_rows_p1(const FwdArgs<T>& a, const RefTab<T>& ts, unsigned char* buf, int cap,
+                                                 int64_t r0, int64_t r1) {
+  constexpr int NV = D + 1, NQ = D == 2 ? 3 : 4;
+  constexpr int UB = (D == 2 && sizeof(T) == 4) ? 3 : 2;
+  const int R = blockDim.x;
+  T* contrib = reinterpret_cast<T*>(buf);
+  uint32_t* posw = reinterpret_cast<uint32_t*>(contrib + (size_t)NV * cap);
+  uint8_t* owner = reinterpret_cast<uint8_t*>(posw + cap);
+  T* acc = reinterpret_cast<T*>(buf + staged_head<T, NV, 1>(cap));
+  const int J0 = __ldg(a.inc_ptr + r0), J1 = __ldg(a.inc_ptr + r1);
+  {
+    const int64_t i = r0 + threadIdx.x;
+    if (i < r1) {
+      const int js = __ldg(a.inc_ptr + i) - J0, je = __ldg(a.inc_ptr + i + 1) - J0;
+      for (int k = js; k < je; ++k) owner[k] = (uint8_t)threadIdx.x;
+    }
+  }
+  __syncthreads();
+  const int64_t stride = a.rec_stride;
+  for (int base = J0 + (int)threadIdx.x; base < J1; base += UB * R) {
+    uint32_t ra[UB], rv[UB][D];
+    int own[UB];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int j = base + u * R;
+      const bool ok = j < J1;
+      ra[u] = ok ? __ldg(a.rec + j) : 0u;
+#pragma unroll
+      for (int k = 0; k < D; ++k) rv[u][k] = ok ? __ldg(a.rec + (k + 1) * stride + j) : 0u;
+      own[u] = (int)r0 + (ok ? owner[j - J0] : 0);
+    }
+    T x[UB][NV][D];
+    T kq[UB][NQ];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) p1_gather<D, T>(a, ra[u], rv[u], own[u], x[u], kq[u]);
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int j = base + u * R;
+      if (j >= J1) continue;
+      T Krow[NV];
+      if (!p1_local_row<D, T>(x[u], kq[u], a.c, ts, Krow)) {
+        record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, ra[u] & 0xffffffu);
+#pragma unroll
+        for (int b = 0; b < NV; ++b) Krow[b] = T(0);
+      }
+      posw[j - J0] = p1_positions<D>(ra[u], rv[u]);
+#pragma unroll
+      for (int b = 0; b < NV; ++b) contrib[b * cap + (j - J0)] = Krow[b];
+    }
+  }
+  __syncthreads();
+  reduce_rows<T, NV, 1>(a, contrib, posw, acc, cap, r0, r1, J0);
+}
+
+// One row block through the fast path when the pattern has records.
+template <int EL, typename T>
+__device__ __forceinline__ void assemble_block(const FwdArgs<T>& a, const RefTab<T>& ts, unsigned char* buf, int cap,
+                                               int64_t r0, int64_t r1) {
+  if constexpr (EL == TG_P1_TRI || EL == TG_P1_TET) {
+    if (a.rec != nullptr) {
+      assemble_rows_p1<Elem<EL>::dim, T>(a, ts, buf, cap, r0, r1);
+      return;
+    }
+  }
+  assemble_rows<EL, T>(a, ts, buf, cap, r0, r1);
 }
 
 // Host: reference tables of each element kind, built once per process.
@@ -126,13 +399,33 @@ inline const RefTab<T>& table(tg_element el) {
   return el == TG_P1_TRI ? t0 : el == TG_P2_TRI ? t1 : t2;
 }
 
+// Host: rows per CTA of the staged kernels and the shared-memory bytes of the
+// stage (without the reference table): the largest R in {128, 64, 32}
+// whose stage fits in 64 KB, else the largest that fits in 200 KB.
+template <typename T, int NV, int NPW>
+inline int staged_rows(int max_deg, int max_row, size_t* bytes) {
+  const int cands[3] = {128, 64, 32};
+  for (int lim : {64 * 1024, 200 * 1024})
+    for (int R : cands) {
+      const size_t b = staged_bytes<T, NV, NPW>(R, std::max(1, R * max_deg), max_row);
+      if (b <= (size_t)lim) {
+        *bytes = b;
+        return R;
+      }
+    }
+  *bytes = 0;
+  return 0;
+}
+
 // Host: allow a kernel the dynamic shared memory it needs (<= 227 KB).
 inline tg_status set_smem(const void* func, size_t bytes) {
   if (bytes > 227 * 1024) {
     set_error("row too long for the shared-memory accumulators");
     return TG_ERR_UNSUPPORTED;
   }
-  if (bytes > 48 * 1024) TG_CK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  // The 48 KB default covers static plus dynamic shared memory; kernels here
+  // keep at most a few KB static, so the limit is raised above 40 KB dynamic.
+  if (bytes > 40 * 1024) TG_CK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   return TG_OK;
 }
 

@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(128) k_rows(const int32_t* __restrict__ cells,
                                               int32_t* __restrict__ row_len, int* __restrict__ maxes,
                                               const int32_t* __restrict__ row_ptr, int32_t* __restrict__ col_idx,
                                               uint32_t* __restrict__ inc_pos, int32_t* __restrict__ elem_slot,
+                                              uint32_t* __restrict__ rec, int64_t rec_stride,
                                               unsigned long long* status) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -190,6 +191,17 @@ __global__ void __launch_bounds__(128) k_rows(const int32_t* __restrict__ cells,
     }
     inc_pos[(int64_t)j * npw] = w0;
     if (npw == 2) inc_pos[(int64_t)j * npw + 1] = w1;
+    if (rec) {
+      // own position with the element index, then the other vertices in
+      // cyclic order after a with their positions
+      const int64_t stride = rec_stride;
+      rec[j] = (uint32_t)e | ((uint32_t)lower_bound(cols, len, cells[(int64_t)e * nv + a]) << 24);
+      for (int k = 1; k < nv; ++k) {
+        const int b = (a + k) % nv;
+        const int v = cells[(int64_t)e * nv + b];
+        rec[k * stride + j] = (uint32_t)v | ((uint32_t)lower_bound(cols, len, v) << 24);
+      }
+    }
   }
 }
 
@@ -317,7 +329,7 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   int64_t* tmp64 = nullptr;
   TG_CK(tmp.alloc(&tmp64, N + 1));
   if ((st = scan_exclusive<int32_t>(deg, tmp64, N, s)) != TG_OK) return st;
-  TG_CK(cudaMalloc(&p->inc_ptr, (N + 1) * sizeof(int32_t)));
+  TG_CK(cudaMalloc(&p->inc_ptr, (N + 1) * sizeof(int32_t) + 16));
   k_narrow<<<tg::grid_for(N + 1, kThreads), kThreads, 0, s>>>(tmp64, p->inc_ptr, N + 1);
   TG_CK_LAUNCH("k_narrow");
   TG_CK(cudaMalloc(&p->inc_e, nvE * sizeof(int32_t) + 16));
@@ -338,7 +350,8 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   TG_CK(cudaMemsetAsync(maxes, 0, 2 * sizeof(int), s));
   const bool vec3 = el == TG_P1_TET_VEC3;
   k_rows<false><<<tg::grid_for(N, 128), 128, 0, s>>>(p->cells, p->inc_ptr, p->inc_e, N, nv, p->npw, vec3, row_len,
-                                                      maxes, nullptr, nullptr, nullptr, nullptr, p->status);
+                                                      maxes, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
+                                                      p->status);
   TG_CK_LAUNCH("k_rows<false>");
   int hmax[2];
   TG_CK(cudaMemcpyAsync(hmax, maxes, sizeof(hmax), cudaMemcpyDeviceToHost, s));
@@ -354,7 +367,7 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
     return TG_ERR_INDEX_OVERFLOW;
   }
   p->nnz = nnz;
-  TG_CK(cudaMalloc(&p->row_ptr, (N + 1) * sizeof(int32_t)));
+  TG_CK(cudaMalloc(&p->row_ptr, (N + 1) * sizeof(int32_t) + 16));
   k_narrow<<<tg::grid_for(N + 1, kThreads), kThreads, 0, s>>>(tmp64, p->row_ptr, N + 1);
   TG_CK_LAUNCH("k_narrow");
 
@@ -362,9 +375,11 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   TG_CK(cudaMalloc(&p->col_idx, nnz * sizeof(int32_t) + 16));
   TG_CK(cudaMalloc(&p->inc_pos, nvE * p->npw * sizeof(uint32_t) + 16));
   TG_CK(cudaMalloc(&p->elem_slot, nvE * nv * sizeof(int32_t) + 16));
+  if (el != TG_P2_TRI && N < (1ll << 24) && E < (1ll << 24))
+    TG_CK(cudaMalloc(&p->rec, (size_t)nv * ((nvE + 3) & ~3ll) * sizeof(uint32_t) + 16));
   k_rows<true><<<tg::grid_for(N, 128), 128, 0, s>>>(p->cells, p->inc_ptr, p->inc_e, N, nv, p->npw, vec3, nullptr,
                                                      nullptr, p->row_ptr, p->col_idx, p->inc_pos, p->elem_slot,
-                                                     p->status);
+                                                     p->rec, (nvE + 3) & ~3ll, p->status);
   TG_CK_LAUNCH("k_rows<true>");
 
   // 5. DoF-level CSR for elasticity
@@ -375,8 +390,9 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
     TG_CK_LAUNCH("k_expand3");
   }
 
-  // per-CTA partials of the backward's global sums (4 values per 128-row CTA)
-  p->n_partials = 4 * ((N + 127) / 128) + 4;
+  // per-CTA partials of the backward's global sums (4 values per CTA of at
+  // least 32 rows)
+  p->n_partials = 4 * ((N + 31) / 32) + 4;
   TG_CK(cudaMalloc(&p->partials, p->n_partials * sizeof(double)));
   TG_CK(cudaStreamSynchronize(s));
   if ((st = read_status(p, s, "tg_build_pattern")) != TG_OK) return st;

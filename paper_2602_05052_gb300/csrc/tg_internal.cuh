@@ -37,6 +37,15 @@ struct tg_pattern {
   int32_t* elem_slot = nullptr;
   int32_t* row_ptr3 = nullptr;
   int32_t* col_idx3 = nullptr;
+  // P1 incidence records (built when E, N < 2^24), structure of arrays with
+  // stride E*nv, in the incidence order of inc_e: for incidence j of node i
+  // in element e with local index a,
+  //   rec[j]            = e | p_i << 24
+  //   rec[k*E*nv + j]   = v_k | p_k << 24,  k = 1 .. nv-1,
+  // v_k the element's vertex (a + k) mod nv and p the column positions in
+  // row i.  The vertex ids arrive with the (coalesced) record, so the gather
+  // needs no second dependent load of the connectivity.
+  uint32_t* rec = nullptr;
   // device status: [0] error code (first one wins), [1] smallest bad element
   unsigned long long* status = nullptr;
   // per-CTA partial sums of global reductions (backward of c / constant kappa)
