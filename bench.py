@@ -53,6 +53,30 @@ def dist_env():
     return rank, world, local
 
 
+def replica_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def replica_max(x, world, device):
+    """The maximum of a per-rank scalar over all ranks (the slowest replica's
+    time); x itself on a single rank."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, ms_max):
+    """Whole-job throughput of N independent replicas: every rank's units over
+    the slowest rank's time (weak scaling)."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 # ------------------------------------------------------------------ workload
 def workload(n=1024):
     cfg = mg.diffusion2d(n)
@@ -82,27 +106,37 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def source_hash():
+# translation units and headers each timed kernel is built from
+KERNEL_SOURCES = {
+    "fwd": ["forward.cu", "gather.cuh", "elements.cuh", "async.cuh", "tg_internal.cuh"],
+    "load": ["forward.cu", "gather.cuh", "elements.cuh", "async.cuh", "tg_internal.cuh"],
+    "bwd": ["backward.cu", "gather.cuh", "elements.cuh", "async.cuh", "tg_internal.cuh"],
+}
+
+
+def source_hash(kernel_key):
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2602_05052_gb300", "csrc")
-    for f in sorted(os.listdir(cs)):
-        with open(os.path.join(cs, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+    for f in sorted(KERNEL_SOURCES[kernel_key]):
+        p = os.path.join(cs, f)
+        if os.path.exists(p):
+            with open(p, "rb") as fh:
+                h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernels changed since it was captured."""
+    """DRAM bytes (read + write) per launch from the committed ncu summary, or
+    None when the kernel's sources changed since it was captured."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    if d.get("source_hash") != source_hash():
-        return None
     k = d.get("kernels", {}).get(kernel_key)
-    return None if k is None else k.get("dram_bytes_per_launch")
+    if k is None or k.get("source_hash") != source_hash(kernel_key):
+        return None
+    return k.get("dram_bytes_per_launch")
 
 
 class Clocks:
@@ -160,23 +194,37 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ reference arm: the CPU oracle
-def oracle_step(m, cfg, G):
+def oracle_sample(m, cfg, n_elems=None):
+    """The workload restricted to its first n_elems elements (a contiguous run
+    of the Hilbert order, so a compact patch of the domain); all nodes kept."""
+    if n_elems is None or n_elems >= m.n_elems:
+        return m.cells, cfg["kappa"]
+    return m.cells[:n_elems], cfg["kappa"][:n_elems]
+
+
+def oracle_step(m, cfg, cells, kappa, G=None):
+    """One pass of the path by the FP64 oracle: forward DOK scatter-add, load,
+    backward for an upstream gradient G of the values (drawn once per sample)."""
     import oracle as O
-    K = O.assemble_bilinear(O.P1_TRI, m.cells, m.coords, cfg["kappa"], O.PER_QP, cfg["c"])
-    O.assemble_load(O.P1_TRI, m.cells, m.coords, cfg["f"], O.PER_NODE)
-    O.assemble_backward(O.P1_TRI, m.cells, m.coords, cfg["kappa"], O.PER_QP, cfg["c"],
-                        grad_csr=O.CSR(K.row_ptr, K.col, G))
-    return K.nnz
+    K = O.assemble_bilinear(O.P1_TRI, cells, m.coords, kappa, O.PER_QP, cfg["c"])
+    O.assemble_load(O.P1_TRI, cells, m.coords, cfg["f"], O.PER_NODE)
+    if G is None or len(G) != K.nnz:
+        G = np.random.default_rng(0).normal(size=K.nnz)
+    O.assemble_backward(O.P1_TRI, cells, m.coords, kappa, O.PER_QP, cfg["c"], grad_csr=O.CSR(K.row_ptr, K.col, G))
+    return G
 
 
 def cpu_oracle_rate(m, cfg, reps):
-    nnz = int(m.n_nodes + 2 * (3 * 1024 ** 2 + 2 * 1024))
-    G = np.random.default_rng(0).normal(size=nnz)
+    cells, kappa = oracle_sample(m, cfg)
+    G = oracle_step(m, cfg, cells, kappa)  # untimed: sizes G
     t0 = time.perf_counter()
     for _ in range(reps):
-        oracle_step(m, cfg, G)
+        oracle_step(m, cfg, cells, kappa, G)
     dt = time.perf_counter() - t0
-    return m.n_elems * reps / dt, dt
+    return len(cells) * reps / dt, dt
+
+
+REF_SAMPLE = 262144  # elements per reference-arm step: 1/8 of the workload, about 1 s of oracle work
 
 
 def run_reference(args):
@@ -184,15 +232,17 @@ def run_reference(args):
     if rank != 0:
         return
     m, cfg = workload()
-    G = np.random.default_rng(0).normal(size=int(m.n_nodes + 2 * (3 * 1024 ** 2 + 2 * 1024)))
-    for _ in range(args.warmup):
-        oracle_step(m, cfg, G)
+    cells, kappa = oracle_sample(m, cfg, REF_SAMPLE)
+    G = None
+    for _ in range(max(args.warmup, 1)):
+        G = oracle_step(m, cfg, cells, kappa, G)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle_step(m, cfg, G)
+        oracle_step(m, cfg, cells, kappa, G)
     dt = time.perf_counter() - t0
-    v = m.n_elems * args.steps / dt
-    sample = f"the full workload ({m.n_elems} elements) per step; forward, load and backward by the FP64 oracle"
+    v = len(cells) * args.steps / dt
+    sample = (f"each step: the first {len(cells)} of {m.n_elems} Hilbert-ordered elements of the workload (all "
+              f"{m.n_nodes} nodes); forward DOK scatter-add, load and backward by the FP64 oracle, one host core")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "elements/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
@@ -219,18 +269,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier = lambda: replica_barrier(world)
+    max_over_ranks = lambda x: replica_max(x, world, dev)
 
     dt = torch.float32
     s = 4
@@ -283,7 +323,7 @@ def main():
     t_bwd = [e[2].elapsed_time(e[3]) for e in evs]
     t_step = [a + b + c_ for a, b, c_ in zip(t_fwd, t_load, t_bwd)]
     ms = max_over_ranks(sum(t_step) / args.steps)
-    value = world * E / (ms * 1e-3)
+    value = replica_throughput(E, world, ms)
     st, bad = tg.tg_get_device_status(p)
     if st != 0:
         raise RuntimeError(f"device status {st} at element {bad}")
@@ -293,8 +333,8 @@ def main():
             "load": (statistics.mean(t_load), alg_bytes("load", E, N, nnz, s)),
             "bwd": (statistics.mean(t_bwd), alg_bytes("bwd", E, N, nnz, s))}
     dom = max(kern, key=lambda k: kern[k][0])
-    names = {"fwd": "k_bilinear_gather<P1_TRI,float>", "load": "k_load_gather<P1_TRI,float,1>",
-             "bwd": "k_backward_gather<P1_TRI,float,gvals>"}
+    names = {"fwd": "k_bilinear_p1<2,float>", "load": "k_load_gather<P1_TRI,float,PER_NODE>",
+             "bwd": "k_backward_gather<P1_TRI,float,gvals> + k_backward_final"}
     ach = kern[dom][1] / (kern[dom][0] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "traffic": ncu_traffic(dom), "peak_source": f"{peak_src} (copy, burst)",
@@ -337,7 +377,7 @@ def main():
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "wall_s_timed_region": wall, "gpu_launches": launches_per_step * args.steps,
            "roofline": roofline, "kernels": per_kernel,
-           "e2e": {"value": world * E / (e2e_ms * 1e-3), "unit": "elements/s", "h2d_bytes_per_step": bi,
+           "e2e": {"value": replica_throughput(E, world, e2e_ms), "unit": "elements/s", "h2d_bytes_per_step": bi,
                    "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms},
            "clocks": clocks}
 
