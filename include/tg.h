@@ -234,6 +234,36 @@ tg_status tg_cg_solve(const tg_pattern* p, tg_dtype dtype, const void* vals, con
                       const uint8_t* dirichlet, void* x, double rtol, int32_t maxit, int32_t* iters,
                       double* relres, tg_stream stream);
 
+/* Bytes of the fixed device scratch of tg_cg_solve_noalloc (16 MiB): 4 KB of
+ * scalars and partial sums, then four work vectors of n_rows values each
+ * (each rounded up to 256 bytes).  That admits up to 1,048,320 rows in
+ * TG_F32 and 524,160 rows in TG_F64. */
+#define TG_CG_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* tg_cg_solve without any device allocation.  The paper has no counterpart:
+ * it is a library variant of the solver above for callers that cannot
+ * allocate device memory at solve time, e.g. a caller whose device memory is
+ * held by a framework's caching allocator (cudaMalloc would fail or force
+ * that cache to be emptied), or one solving inside a latency-critical loop
+ * such as the adjoint solve of every optimisation step, where cudaMalloc and
+ * cudaFree would synchronise the whole device and stall work queued on other
+ * streams.  Same arguments, arithmetic and results (bitwise) as tg_cg_solve.
+ *
+ * The work vectors live in one fixed array of TG_CG_NOALLOC_SCRATCH_BYTES in
+ * the library's device memory (one per device, allocated when the module is
+ * loaded).  Consequences:
+ * - A system whose work vectors do not fit returns TG_ERR_UNSUPPORTED before
+ *   any GPU work (message in tg_last_error_message()).
+ * - Calls that overlap on the same device (from several host threads, or on
+ *   several streams) share the scratch and race; the caller serialises them.
+ * - The first call on each device looks up the scratch address
+ *   (cudaGetSymbolAddress, checked) and may load the module; make that first
+ *   call outside any stream capture.  Like tg_cg_solve, every call
+ *   SYNCHRONISES the stream. */
+tg_status tg_cg_solve_noalloc(const tg_pattern* p, tg_dtype dtype, const void* vals, const void* F,
+                              const uint8_t* dirichlet, void* x, double rtol, int32_t maxit, int32_t* iters,
+                              double* relres, tg_stream stream);
+
 /* ------------------------------------------------------------------------
  * Batched assembly: many independent instances in one persistent launch
  * (SM B.1, "Efficient Batch Data Generation": many-query use).

@@ -64,6 +64,7 @@ def lib():
         "tg_spmv": (i32, [vp, i32, vp, vp, vp, vp]),
         "tg_csr_outer": (i32, [vp, i32, vp, vp, dbl, vp, vp]),
         "tg_cg_solve": (i32, [vp, i32, vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl), vp]),
+        "tg_cg_solve_noalloc": (i32, [vp, i32, vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl), vp]),
         "tg_batch_create": (i32, [C.POINTER(vp), i32, C.POINTER(vp)]),
         "tg_batch_assemble": (i32, [vp, i32, C.POINTER(vp), C.POINTER(vp), i32, C.POINTER(dbl), C.POINTER(vp), vp]),
         "tg_batch_set_schedule": (i32, [vp, i32, i32, i32]),
@@ -288,6 +289,23 @@ def tg_cg_solve(p: Pattern, vals, F, dirichlet=None, x=None, rtol: float = 1e-10
     _check(lib().tg_cg_solve(p.handle, _dt(vals), _ptr(vals, vals.dtype, "vals"), _ptr(F, vals.dtype, "F"),
                              _ptr(dirichlet, torch.uint8, "dirichlet"), _ptr(x, vals.dtype, "x"), float(rtol),
                              int(maxit), C.byref(it), C.byref(rr), _stream(stream)), "tg_cg_solve")
+    return x, it.value, rr.value
+
+
+TG_CG_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def tg_cg_solve_noalloc(p: Pattern, vals, F, dirichlet=None, x=None, rtol: float = 1e-10, maxit: int = 100000,
+                        stream=None):
+    """tg_cg_solve with its work vectors in the library's fixed device
+    scratch (no allocation; calls on one device must not overlap)."""
+    if x is None:
+        x = torch.zeros(p.n_rows, dtype=vals.dtype, device=vals.device)
+    it, rr = i32(), dbl()
+    _check(lib().tg_cg_solve_noalloc(p.handle, _dt(vals), _ptr(vals, vals.dtype, "vals"), _ptr(F, vals.dtype, "F"),
+                                     _ptr(dirichlet, torch.uint8, "dirichlet"), _ptr(x, vals.dtype, "x"),
+                                     float(rtol), int(maxit), C.byref(it), C.byref(rr), _stream(stream)),
+           "tg_cg_solve_noalloc")
     return x, it.value, rr.value
 
 

@@ -3,8 +3,11 @@
 // iterative solve that follows assembly, SM B.1 solver configuration, and the
 // adjoint solve K^T lam = -dGamma/dU of Eq. (adj)); plus the FMA-rate probe
 // used to report the arithmetic roof.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "tg_internal.cuh"
@@ -119,9 +122,18 @@ tg_status dot(const T* a, const T* b, int64_t n, double* partials, int nb, doubl
   return TG_OK;
 }
 
+// Work vectors of one CG solve (n entries each) and its scalars.
+template <typename T>
+struct CgWork {
+  T *r, *pp, *Ap, *b;
+  double* sc;        // [4]: rr, pAp, rr_new, ||F_I||^2
+  double* partials;  // [nb]
+  int nb;
+};
+
 template <typename T>
 tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8_t* mask, void* x_, double rtol,
-             int maxit, int* iters, double* relres, cudaStream_t s) {
+             int maxit, int* iters, double* relres, const CgWork<T>& w, cudaStream_t s) {
   const bool vec = p->el == TG_P1_TET_VEC3;
   const int64_t n = vec ? 3 * p->N : p->N;
   const int32_t* rp = vec ? p->row_ptr3 : p->row_ptr;
@@ -129,16 +141,9 @@ tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8
   const T* vals = static_cast<const T*>(vals_);
   const T* F = static_cast<const T*>(F_);
   T* x = static_cast<T*>(x_);
-  Dev d;
-  T *r, *pp, *Ap, *b;
-  double *sc, *partials;
-  const int nb = 2 * tg::sm_count();
-  TG_CK(d.alloc((void**)&r, n * sizeof(T)));
-  TG_CK(d.alloc((void**)&pp, n * sizeof(T)));
-  TG_CK(d.alloc((void**)&Ap, n * sizeof(T)));
-  TG_CK(d.alloc((void**)&b, n * sizeof(T)));
-  TG_CK(d.alloc((void**)&sc, 4 * sizeof(double)));
-  TG_CK(d.alloc((void**)&partials, nb * sizeof(double)));
+  T *r = w.r, *pp = w.pp, *Ap = w.Ap, *b = w.b;
+  double *sc = w.sc, *partials = w.partials;
+  const int nb = w.nb;
   const int gv = tg::grid_for(n, ST), gs = tg::grid_for(4 * n, ST);
   k_spmv<T><<<gs, ST, 0, s>>>(rp, ci, vals, x, Ap, n, mask);
   k_cg_init<T><<<gv, ST, 0, s>>>(F, Ap, mask, x, r, pp, b, n);
@@ -172,6 +177,92 @@ tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8
   if (iters) *iters = it;
   if (relres) *relres = fnorm > 0 ? std::sqrt(h[0]) / fnorm : 0.0;
   return TG_OK;
+}
+
+// Allocating form: the work vectors live for one call.
+template <typename T>
+tg_status cg_alloc(const tg_pattern* p, const void* vals, const void* F, const uint8_t* mask, void* x, double rtol,
+                   int maxit, int* iters, double* relres, cudaStream_t s) {
+  const int64_t n = p->el == TG_P1_TET_VEC3 ? 3 * p->N : p->N;
+  Dev d;
+  CgWork<T> w;
+  w.nb = 2 * tg::sm_count();
+  TG_CK(d.alloc((void**)&w.r, n * sizeof(T)));
+  TG_CK(d.alloc((void**)&w.pp, n * sizeof(T)));
+  TG_CK(d.alloc((void**)&w.Ap, n * sizeof(T)));
+  TG_CK(d.alloc((void**)&w.b, n * sizeof(T)));
+  TG_CK(d.alloc((void**)&w.sc, 4 * sizeof(double)));
+  TG_CK(d.alloc((void**)&w.partials, w.nb * sizeof(double)));
+  return cg<T>(p, vals, F, mask, x, rtol, maxit, iters, relres, w, s);
+}
+
+// ---------------------------------------------------------------- no-alloc form
+// Scratch of tg_cg_solve_noalloc: a fixed device array in this module, so the
+// call never allocates.  Layout: [0, 4 KB) scalars (4 doubles) and partial
+// dot products (up to kNoAllocMaxPartials doubles), then the four work
+// vectors, each rounded up to 256 bytes.
+constexpr size_t kNoAllocBytes = TG_CG_NOALLOC_SCRATCH_BYTES;
+constexpr size_t kNoAllocHead = 4096;
+constexpr int kNoAllocMaxPartials = (int)(kNoAllocHead / sizeof(double)) - 4;
+static __device__ __align__(256) unsigned char g_cg_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_cg_scratch on the current device, looked up once per
+// device (the lookup may load this module; it must not happen inside a
+// stream capture, so the first call on a device has to come before any).
+tg_status noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  TG_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    tg::set_error("device ordinal beyond the no-alloc scratch table");
+    return TG_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (g_scratch_addr[dev] == nullptr) {
+    void* a = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&a, g_cg_scratch);
+    if (e != cudaSuccess) return tg::cuda_fail(e, "cudaGetSymbolAddress(g_cg_scratch)", __FILE__, __LINE__);
+    if (a == nullptr) {
+      tg::set_error("cudaGetSymbolAddress(g_cg_scratch) returned a null address");
+      return TG_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = a;
+  }
+  *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  return TG_OK;
+}
+
+inline size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+template <typename T>
+tg_status cg_noalloc(const tg_pattern* p, const void* vals, const void* F, const uint8_t* mask, void* x,
+                     double rtol, int maxit, int* iters, double* relres, cudaStream_t s) {
+  const int64_t n = p->el == TG_P1_TET_VEC3 ? 3 * p->N : p->N;
+  const size_t vb = round256((size_t)n * sizeof(T));
+  if (kNoAllocHead + 4 * vb > kNoAllocBytes) {
+    tg::set_error("tg_cg_solve_noalloc: " + std::to_string(n) + " rows need " +
+                  std::to_string(kNoAllocHead + 4 * vb) + " bytes of scratch; the static scratch holds " +
+                  std::to_string(kNoAllocBytes));
+    return TG_ERR_UNSUPPORTED;
+  }
+  unsigned char* base = nullptr;
+  tg_status st = noalloc_scratch(&base);
+  if (st != TG_OK) return st;
+  CgWork<T> w;
+  w.sc = reinterpret_cast<double*>(base);
+  w.partials = w.sc + 4;
+  w.nb = std::min(2 * tg::sm_count(), kNoAllocMaxPartials);
+  w.r = reinterpret_cast<T*>(base + kNoAllocHead);
+  w.pp = reinterpret_cast<T*>(base + kNoAllocHead + vb);
+  w.Ap = reinterpret_cast<T*>(base + kNoAllocHead + 2 * vb);
+  w.b = reinterpret_cast<T*>(base + kNoAllocHead + 3 * vb);
+  // The scalars start at zero so that nothing of an earlier call can be read
+  // back; the vectors and partials are fully written before they are read.
+  TG_CK(cudaMemsetAsync(w.sc, 0, 4 * sizeof(double), s));
+  return cg<T>(p, vals, F, mask, x, rtol, maxit, iters, relres, w, s);
 }
 
 // out[s] = alpha * lam[row(s)] * U[col(s)]: the adjoint outer product
@@ -229,8 +320,23 @@ tg_status tg_cg_solve(const tg_pattern* p, tg_dtype dtype, const void* vals, con
   cudaStream_t s = (cudaStream_t)stream;
   int it = 0;
   double rr = 0;
-  tg_status st = dtype == TG_F32 ? cg<float>(p, vals, F, dirichlet, x, rtol, maxit, &it, &rr, s)
-                                 : cg<double>(p, vals, F, dirichlet, x, rtol, maxit, &it, &rr, s);
+  tg_status st = dtype == TG_F32 ? cg_alloc<float>(p, vals, F, dirichlet, x, rtol, maxit, &it, &rr, s)
+                                 : cg_alloc<double>(p, vals, F, dirichlet, x, rtol, maxit, &it, &rr, s);
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  return st;
+}
+
+tg_status tg_cg_solve_noalloc(const tg_pattern* p, tg_dtype dtype, const void* vals, const void* F,
+                              const uint8_t* dirichlet, void* x, double rtol, int32_t maxit, int32_t* iters,
+                              double* relres, tg_stream stream) {
+  if (!p || (dtype != TG_F32 && dtype != TG_F64) || !vals || !F || !x || maxit < 0 || !(rtol >= 0))
+    return TG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int it = 0;
+  double rr = 0;
+  tg_status st = dtype == TG_F32 ? cg_noalloc<float>(p, vals, F, dirichlet, x, rtol, maxit, &it, &rr, s)
+                                 : cg_noalloc<double>(p, vals, F, dirichlet, x, rtol, maxit, &it, &rr, s);
   if (iters) *iters = it;
   if (relres) *relres = rr;
   return st;
