@@ -122,12 +122,12 @@ RefTab<T> ref_table(tg_element el) {
       t.phi[q][a] = (T)v[a];
       for (int s = 0; s < 3; ++s) t.gh[q][a][s] = (T)g[a][s];
       m1[a] += w[q] * v[a];
-      for (int b = 0; b < nv; ++b) M[a][b] += w[q] * v[a] * v[b];
+      for (int b = a; b < nv; ++b) M[a][b] += w[q] * v[a] * v[b];
     }
   }
   for (int a = 0; a < nv; ++a) {
     t.m1[a] = (T)m1[a];
-    for (int b = 0; b < nv; ++b) t.M[a][b] = (T)M[a][b];
+    for (int b = 0; b < nv; ++b) t.M[a][b] = (T)(b >= a ? M[a][b] : M[b][a]);  // exactly symmetric
   }
   t.wsum = (T)ws;
   return t;
@@ -209,8 +209,9 @@ void tg_pattern_destroy(tg_pattern* p) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(p->device);
-  void* bufs[] = {p->cells,    p->inc_ptr,  p->inc_e,   p->inc_pos, p->row_ptr,   p->col_idx, p->elem_slot,
-                  p->row_ptr3, p->col_idx3, p->status, p->partials, p->rec};
+  void* bufs[] = {p->cells,    p->inc_ptr,  p->inc_e,   p->inc_pos, p->row_ptr, p->col_idx, p->elem_slot,
+                  p->row_ptr3, p->col_idx3, p->status, p->partials, p->bel, p->bel_cnt, p->brec,
+                  p->elem_pos};
   for (void* b : bufs)
     if (b) cudaFree(b);
   cudaSetDevice(prev);

@@ -32,8 +32,6 @@ struct InstDesc {
   const int32_t* cells;
   int64_t N;
   unsigned long long* status;
-  const uint32_t* rec;
-  int64_t rec_stride;
 };
 
 template <typename T>
@@ -73,8 +71,6 @@ __global__ void __launch_bounds__(BSZ) k_batch(const InstDesc* __restrict__ desc
     a.out = call.vals[k];
     a.n = d.N;
     a.status = d.status;
-    a.rec = d.rec;
-    a.rec_stride = d.rec_stride;
     for (int64_t r = w.y; r < w.z; r += BSZ) tg::assemble_block<EL, T>(a, ts, buf, cap, r, r + BSZ < w.z ? r + BSZ : w.z);
   }
 }
@@ -223,8 +219,7 @@ tg_status tg_batch_create(const tg_pattern* const* pats, int32_t n_inst, tg_batc
     b->max_row_len = std::max(b->max_row_len, p->max_row_len);
     b->max_deg = std::max(b->max_deg, p->max_deg);
     b->total_rows += p->N;
-    h[i] = InstDesc{p->row_ptr, p->inc_ptr, p->inc_e, p->inc_pos, p->cells, p->N, p->status, p->rec,
-                    (p->E * p->nv + 3) & ~3ll};
+    h[i] = InstDesc{p->row_ptr, p->inc_ptr, p->inc_e, p->inc_pos, p->cells, p->N, p->status};
   }
   cudaError_t e = cudaGetDevice(&b->device);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_desc, n_inst * sizeof(InstDesc));

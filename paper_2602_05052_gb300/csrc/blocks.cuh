@@ -1,0 +1,189 @@
+// Element-once row blocks (P1 triangles and tetrahedra): the pipeline that
+// the forward, load and backward kernels share.
+//
+// A persistent CTA walks the row blocks b = blockIdx.x, + gridDim.x, ...
+// Block b owns R = blockDim.x consecutive rows.  Its contiguous streams are:
+//   - its slices of inc_ptr and row_ptr;
+//   - the records of its incidences (brec);
+//   - its list of distinct elements (bel).
+// Thread 0 prefetches them into the other of two shared stages with bulk
+// copies one block ahead, while the CTA works on the current block:
+//   Map    - one thread per distinct element computes that element's local
+//            quantities once and leaves them in shared memory;
+//   Reduce - one thread per row sums the quantities of its incidences in
+//            increasing element order (the fixed order that makes every
+//            output bitwise reproducible) and the block's results leave
+//            with coalesced stores.
+// An element shared by several blocks is computed once in each of them.
+#pragma once
+
+#include <cstdint>
+
+#include "async.cuh"
+#include "gather.cuh"
+
+namespace tg {
+
+struct BlkArgs {
+  const int32_t* __restrict__ inc_ptr;
+  const int32_t* __restrict__ row_ptr;
+  const uint32_t* __restrict__ bel;
+  const int32_t* __restrict__ bel_cnt;
+  const uint32_t* __restrict__ brec;
+  int64_t N;
+  int64_t nblocks;
+  int capE, capJ;  // stage capacities (multiples of 4): distinct elements, incidences
+  int pb;          // bits per position field of a record
+};
+
+// Host: BlkArgs of a pattern with row blocks.
+inline BlkArgs blk_args(const tg_pattern* p) {
+  BlkArgs g;
+  g.inc_ptr = p->inc_ptr;
+  g.row_ptr = p->row_ptr;
+  g.bel = p->bel;
+  g.bel_cnt = p->bel_cnt;
+  g.brec = p->brec;
+  g.N = p->N;
+  g.nblocks = p->n_blk;
+  g.capE = (p->blk_max_elems + 3) & ~3;
+  g.capJ = (p->blk_max_inc + 3) & ~3;
+  g.pb = p->blk_pb;
+  return g;
+}
+
+// Shared-memory bytes of the two stages plus barriers and block metadata.
+__host__ __device__ inline size_t blk_stage_bytes(int R, int capJ, int capE) {
+  return 16 + 128 + 2 * ((size_t)(R + 8) * 8 + (size_t)(capJ + 8) * 4 + (size_t)(capE + 8) * 4);
+}
+
+// Geometry of one row block as seen through its stage.
+struct BlkView {
+  int r0, r1, J0, J1, nbe;
+  const int* ip;       // ip[i] = inc_ptr[i], i in [r0, r1]
+  const int* rp;       // rp[i] = row_ptr[i]
+  const uint32_t* rc;  // rc[j] = brec[j], j in [J0, J1)
+  const uint32_t* be;  // be[k] = bel[J0 + k], k < nbe
+};
+
+class BlkPipe {
+ public:
+  // Carves the stages out of shared memory at p (16-byte aligned); returns
+  // the first byte after them.  Thread 0 initialises the barriers; the
+  // caller's next CTA barrier publishes them.
+  __device__ unsigned char* init(unsigned char* p, const BlkArgs& g) {
+    R_ = blockDim.x;
+    IPN_ = R_ + 8;
+    RECN_ = g.capJ + 8;
+    ELN_ = g.capE + 8;
+    SW_ = 2 * IPN_ + RECN_ + ELN_;  // words per stage (a multiple of 4)
+    bar_ = reinterpret_cast<uint64_t*>(p);
+    meta_ = reinterpret_cast<int*>(p + 16);
+    st_ = reinterpret_cast<int*>(p + 16 + 128);
+    if (threadIdx.x == 0) {
+      mbar_init(&bar_[0], 1);
+      mbar_init(&bar_[1], 1);
+      fence_mbar_init();
+    }
+    return reinterpret_cast<unsigned char*>(st_ + 2 * SW_);
+  }
+
+  // Thread 0: incidence range and element count of block blk (plain loads,
+  // issued early so that they are in flight while the CTA works).
+  __device__ static void peek(const BlkArgs& g, int64_t blk, int& J0, int& J1, int& nbe) {
+    const int R = blockDim.x;
+    J0 = __ldg(g.inc_ptr + blk * R);
+    J1 = __ldg(g.inc_ptr + (blk * R + R < g.N ? blk * R + R : g.N));
+    nbe = __ldg(g.bel_cnt + blk);
+  }
+
+  // Thread 0: copy block blk's streams into stage s.  Every source range is
+  // widened to whole 16-byte groups (the pattern arrays carry 16 bytes of
+  // tail padding); the stage capacities hold the widened ranges.
+  __device__ void issue(const BlkArgs& g, int s, int64_t blk, int J0, int J1, int nbe) {
+    const int r0 = (int)(blk * R_), r1 = (int)(blk * R_ + R_ < g.N ? blk * R_ + R_ : g.N);
+    const int a0 = r0 & ~3, nip = (r1 + 1 - a0 + 3) & ~3;
+    const int j0a = J0 & ~3, nrec = (J1 - j0a + 3) & ~3, nel = (J0 + nbe - j0a + 3) & ~3;
+    int* m = meta_ + 16 * s;
+    m[0] = r0;
+    m[1] = r1;
+    m[2] = J0;
+    m[3] = J1;
+    m[4] = a0;
+    m[5] = j0a;
+    m[6] = nbe;
+    const uint32_t bytes = 4u * (2u * nip + (J1 > J0 ? nrec : 0) + (nbe > 0 ? nel : 0));
+    fence_proxy_async();
+    mbar_arrive_expect_tx(&bar_[s], bytes);
+    bulk_copy_g2s(ip(s), g.inc_ptr + a0, nip * 4, &bar_[s]);
+    bulk_copy_g2s(rp(s), g.row_ptr + a0, nip * 4, &bar_[s]);
+    if (J1 > J0) bulk_copy_g2s(rec(s), g.brec + j0a, nrec * 4, &bar_[s]);
+    if (nbe > 0) bulk_copy_g2s(el(s), g.bel + j0a, nel * 4, &bar_[s]);
+  }
+
+  // All threads: wait (bounded) for stage s of use k; the outcome is made
+  // uniform across the CTA.  On failure thread 0 records TG_ERR_TIMEOUT and
+  // waits, again bounded, for the copies it issued, and the CTA must return.
+  __device__ bool wait(int s, int k, bool other_issued, unsigned long long* status) {
+    const bool ok = mbar_wait(&bar_[s], (k >> 1) & 1);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        record_error(status, TG_ERR_TIMEOUT, 0);
+        mbar_wait(&bar_[s], (k >> 1) & 1);
+        if (other_issued) mbar_wait(&bar_[s ^ 1], ((k + 1) >> 1) & 1);
+      }
+      return false;
+    }
+    return true;
+  }
+
+  __device__ BlkView view(int s) const {
+    const int* m = meta_ + 16 * s;
+    BlkView v;
+    v.r0 = m[0];
+    v.r1 = m[1];
+    v.J0 = m[2];
+    v.J1 = m[3];
+    v.nbe = m[6];
+    v.ip = ip(s) - m[4];
+    v.rp = rp(s) - m[4];
+    v.rc = rec(s) - m[5];
+    v.be = el(s) + (m[2] - m[5]);
+    return v;
+  }
+
+ private:
+  // stage s: ip [IPN] | rp [IPN] | rec [RECN] | el [ELN]
+  __device__ int* ip(int s) const { return st_ + s * SW_; }
+  __device__ int* rp(int s) const { return ip(s) + IPN_; }
+  __device__ uint32_t* rec(int s) const { return reinterpret_cast<uint32_t*>(rp(s) + IPN_); }
+  __device__ uint32_t* el(int s) const { return rec(s) + RECN_; }
+
+  int R_, IPN_, RECN_, ELN_, SW_;
+  uint64_t* bar_;
+  int* meta_;
+  int* st_;
+};
+
+// Fields of an incidence record.
+struct BlkRec {
+  uint32_t w;
+  int sh;  // nv * pb
+  __device__ int le() const { return (int)(w >> (sh + 2)); }
+  __device__ int a() const { return (int)(w >> sh) & 3; }
+  __device__ int pos(int b, int pb) const { return (int)(w >> (b * pb)) & ((1 << pb) - 1); }
+};
+
+// Index of entry (a, b) of a symmetric NV x NV matrix stored as its upper
+// triangle row by row; b is a compile-time constant in the unrolled loops.
+template <int NV>
+__device__ __forceinline__ int sym_index(int a, int b) {
+  const int lo = a < b ? a : b, hi = a < b ? b : a;
+  return lo * NV - lo * (lo - 1) / 2 + (hi - lo);
+}
+
+// The element of a bel entry (without the owner bit).
+__device__ __forceinline__ int64_t bel_elem(uint32_t w) { return (int64_t)(w & 0x7fffffffu); }
+__device__ __forceinline__ bool bel_owner(uint32_t w) { return (w >> 31) != 0u; }
+
+}  // namespace tg

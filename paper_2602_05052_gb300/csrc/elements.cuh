@@ -112,6 +112,18 @@ __device__ __forceinline__ T tet_det(const T* __restrict__ coords, int v0, int v
 
 // Row la of the scalar local matrix of a P1 element (triangle or tet):
 //   K[la][b] = s * n_la.n_b + mc * M[la][b],  s = (sum_q w_q kappa_q)/|det|, mc = c |det|.
+// One entry of the P1 matrix from det-scaled gradients:
+//   K_ab = s (n_a . n_b) + mc M_ab,  s = sum_q w_q kappa_q / |det J|,  mc = c |det J|.
+// Written with explicit fused multiply-adds in a fixed order, so that the
+// entry is bitwise the same wherever it is evaluated (and K_ab == K_ba).
+template <int DIM, typename T>
+__device__ __forceinline__ T p1_entry(const T (&na)[DIM], const T (&nb)[DIM], T s, T mc, T Mab) {
+  T d = na[0] * nb[0];
+#pragma unroll
+  for (int r = 1; r < DIM; ++r) d = fma(na[r], nb[r], d);
+  return fma(s, d, mc * Mab);
+}
+
 template <int DIM, typename T>
 __device__ __forceinline__ void p1_row(const Geom<DIM, T>& g, int la, T s, T mc, const T (&Mla)[6],
                                        T (&Krow)[DIM + 1]) {
@@ -124,14 +136,8 @@ __device__ __forceinline__ void p1_row(const Geom<DIM, T>& g, int la, T s, T mc,
     na[r] = sel(la, col);
   }
 #pragma unroll
-  for (int b = 0; b <= DIM; ++b) {
-    T d = T(0);
-#pragma unroll
-    for (int r = 0; r < DIM; ++r) d += na[r] * g.n[b][r];
-    Krow[b] = s * d + mc * Mla[b];
-  }
+  for (int b = 0; b <= DIM; ++b) Krow[b] = p1_entry<DIM, T>(na, g.n[b], s, mc, Mla[b]);
 }
-
 // Row la of the P2 triangle matrix with kappa at the 6 points:
 //   K[la][b] = (1/|det|) sum_q w_q kappa_q gh_q,la^T C gh_q,b + c |det| M[la][b]
 // with C = det^2 J^{-1} J^{-T} = [[n1.n1, n1.n2], [n1.n2, n2.n2]].

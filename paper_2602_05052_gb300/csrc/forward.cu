@@ -15,13 +15,15 @@
 // the memory traffic.
 #include <cstdint>
 
-#include "async.cuh"
-#include "gather.cuh"
+#include "blocks.cuh"
 
 namespace {
 
 constexpr int BS = 128;  // rows per CTA (scalar kernels)
 constexpr int EB = 64;   // rows per CTA (elasticity: 9 * row length accumulators per thread)
+// Largest shared memory of an element-once CTA (two CTAs per SM); patterns
+// that need more use the generic kernels.
+constexpr size_t kBlkSmemMax = 113 * 1024;
 
 using tg::FwdArgs;
 using tg::tab_bytes;
@@ -43,159 +45,89 @@ __global__ void __launch_bounds__(BS) k_bilinear_gather(const FwdArgs<T> a, cons
   tg::assemble_rows<EL, T>(a, ts, smem + tab_bytes<T>(), cap, r0, r1);
 }
 
-// P1 fast path (incidence records) as a persistent, software-pipelined
-// kernel.  Each CTA walks row blocks b = blockIdx.x, + gridDim.x, ...; the
-// contiguous streams of a block (its slices of inc_ptr, row_ptr and the
-// records) are brought into one of two shared-memory stages by 1D bulk
-// copies that thread 0 issues one block ahead, completing on the stage's
-// mbarrier, while the whole CTA processes the previous block.  Only the
-// gathers of coordinates and coefficients remain on the critical path.
-//
-// Stage s: ip [IPN] | rp [IPN] | rec [NV][RECN], IPN = R + 8, RECN = cap + 8
-// (bulk copies move whole 16-byte groups, so ranges are widened to
-// multiples of 4 words; the pattern arrays carry 16 bytes of tail padding).
+// P1 forward over element-once row blocks (blocks.cuh):
+//   Map    - the local matrix K_e of every distinct element of the block,
+//            upper triangle (NS entries), into Ke[NS][capE];
+//   Reduce - row i adds, for each incidence (e, a) in increasing e, row a of
+//            K_e into its CSR-local slice of acc; the block's slice of the
+//            CSR values is then stored with coalesced writes.
 template <int D, typename T>
-__global__ void __launch_bounds__(BS, (D == 2 && sizeof(T) == 4) ? 5 : 1) k_bilinear_p1(
-    const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab, int cap, int64_t nblocks) {
-  constexpr int NV = D + 1, NQ = D == 2 ? 3 : 4;
-  constexpr int UB = (D == 2 && sizeof(T) == 4) ? 3 : 2;
+__global__ void __launch_bounds__(BS, D == 2 ? 4 : 2) k_bilinear_blk(const FwdArgs<T> a,
+                                                                      const __grid_constant__ tg::RefTab<T> tab,
+                                                                      const tg::BlkArgs g) {
+  constexpr int EL = D == 2 ? TG_P1_TRI : TG_P1_TET;
+  constexpr int NV = D + 1, NS = NV * (NV + 1) / 2;
+  constexpr int UB = sizeof(T) == 4 ? 4 : 2;
   extern __shared__ __align__(16) unsigned char smem[];
   auto& ts = *reinterpret_cast<tg::RefTab<T>*>(smem);
+  tg::BlkPipe pipe;
+  T* Ke = reinterpret_cast<T*>(pipe.init(smem + tab_bytes<T>(), g));
+  T* acc = Ke + (size_t)NS * g.capE;
+  copy_table(ts, tab);  // CTA barrier: also publishes the mbarrier initialisation
   const int R = blockDim.x;
-  const int IPN = R + 8, RECN = cap + 8;
-  unsigned char* p = smem + tab_bytes<T>();
-  uint64_t* bar = reinterpret_cast<uint64_t*>(p);
-  p += 16;
-  int* meta = reinterpret_cast<int*>(p);  // [2][8]: r0, r1, J0, J1, a0, j0a
-  p += 64;
-  int* st_ip[2];
-  int* st_rp[2];
-  uint32_t* st_rec[2];
-  for (int s = 0; s < 2; ++s) {
-    st_ip[s] = reinterpret_cast<int*>(p);
-    p += IPN * 4;
-    st_rp[s] = reinterpret_cast<int*>(p);
-    p += IPN * 4;
-    st_rec[s] = reinterpret_cast<uint32_t*>(p);
-    p += (size_t)NV * RECN * 4;
-  }
-  T* contrib = reinterpret_cast<T*>(p);
-  uint32_t* posw = reinterpret_cast<uint32_t*>(contrib + (size_t)NV * cap);
-  uint8_t* owner = reinterpret_cast<uint8_t*>(posw + cap);
-  T* acc = reinterpret_cast<T*>(p + tg::staged_head<T, NV, 1>(cap));
-  if (threadIdx.x == 0) {
-    tg::mbar_init(&bar[0], 1);
-    tg::mbar_init(&bar[1], 1);
-    tg::fence_mbar_init();
-  }
-  copy_table(ts, tab);  // includes a CTA barrier
-
   const int64_t G = gridDim.x;
-  const int64_t stride = a.rec_stride;
-  // issue the copies of block blk into stage s (thread 0)
-  auto issue = [&](int s, int64_t blk, int J0, int J1) {
-    const int r0 = (int)(blk * R), r1 = (int)(blk * R + R < a.n ? blk * R + R : a.n);
-    const int a0 = r0 & ~3, nip = (r1 + 1 - a0 + 3) & ~3;
-    const int j0a = J0 & ~3, nrec = (J1 - j0a + 3) & ~3;
-    int* m = meta + 8 * s;
-    m[0] = r0;
-    m[1] = r1;
-    m[2] = J0;
-    m[3] = J1;
-    m[4] = a0;
-    m[5] = j0a;
-    const uint32_t bytes = 2u * nip * 4 + (J1 > J0 ? (uint32_t)NV * nrec * 4 : 0u);
-    tg::fence_proxy_async();
-    tg::mbar_arrive_expect_tx(&bar[s], bytes);
-    tg::bulk_copy_g2s(st_ip[s], a.inc_ptr + a0, nip * 4, &bar[s]);
-    tg::bulk_copy_g2s(st_rp[s], a.row_ptr + a0, nip * 4, &bar[s]);
-    if (J1 > J0)
-      for (int k = 0; k < NV; ++k) tg::bulk_copy_g2s(st_rec[s] + k * RECN, a.rec + k * stride + j0a, nrec * 4, &bar[s]);
-  };
-  auto block_J = [&](int64_t blk, int& J0, int& J1) {
-    J0 = __ldg(a.inc_ptr + blk * R);
-    J1 = __ldg(a.inc_ptr + (blk * R + R < a.n ? blk * R + R : a.n));
-  };
-
+  const int sh = NV * g.pb;
   int64_t b = blockIdx.x;
-  int nJ0 = 0, nJ1 = 0;
-  if (threadIdx.x == 0 && b < nblocks) {
-    int J0, J1;
-    block_J(b, J0, J1);
-    issue(0, b, J0, J1);
-    if (b + G < nblocks) block_J(b + G, nJ0, nJ1);
+  int nJ0 = 0, nJ1 = 0, nE = 0;
+  if (threadIdx.x == 0 && b < g.nblocks) {
+    int J0, J1, ne;
+    tg::BlkPipe::peek(g, b, J0, J1, ne);
+    pipe.issue(g, 0, b, J0, J1, ne);
+    if (b + G < g.nblocks) tg::BlkPipe::peek(g, b + G, nJ0, nJ1, nE);
   }
-  for (int k = 0; b < nblocks; ++k, b += G) {
+  for (int k = 0; b < g.nblocks; ++k, b += G) {
     const int s = k & 1;
-    if (threadIdx.x == 0 && b + G < nblocks) {
-      issue(s ^ 1, b + G, nJ0, nJ1);
-      if (b + 2 * G < nblocks) block_J(b + 2 * G, nJ0, nJ1);
+    const bool ahead = b + G < g.nblocks;
+    if (threadIdx.x == 0 && ahead) {
+      pipe.issue(g, s ^ 1, b + G, nJ0, nJ1, nE);
+      if (b + 2 * G < g.nblocks) tg::BlkPipe::peek(g, b + 2 * G, nJ0, nJ1, nE);
     }
-    if (!tg::mbar_wait(&bar[s], (k >> 1) & 1)) {
-      tg::record_error(a.status, TG_ERR_TIMEOUT, 0);
-      return;
-    }
-    const int* m = meta + 8 * s;
-    const int r0 = m[0], r1 = m[1], J0 = m[2], J1 = m[3], a0 = m[4], j0a = m[5];
-    const int* ip = st_ip[s] - a0;  // ip[i] = inc_ptr[i] for i in [r0, r1]
-    const int* rp = st_rp[s] - a0;
-    const uint32_t* rc = st_rec[s] - j0a;
-    // phase 0: incidence -> row map
-    const int i = r0 + (int)threadIdx.x;
-    int js = 0, je = 0;
-    if (i < r1) {
-      js = ip[i] - J0;
-      je = ip[i + 1] - J0;
-      for (int q = js; q < je; ++q) owner[q] = (uint8_t)threadIdx.x;
-    }
-    __syncthreads();
-    // phase 1: element rows of every incidence of the block
-    for (int base = J0 + (int)threadIdx.x; base < J1; base += UB * R) {
-      uint32_t ra[UB], rv[UB][D];
-      int own[UB];
+    if (!pipe.wait(s, k, ahead, a.status)) return;
+    const tg::BlkView v = pipe.view(s);
+    // Map: UB elements per thread in flight (ids, then coordinates and kappa)
+    for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * R) {
+      int64_t e[UB];
+      tg::ElemIn<EL, T> in[UB];
 #pragma unroll
       for (int u = 0; u < UB; ++u) {
-        const int j = base + u * R;
-        const bool ok = j < J1;
-        ra[u] = ok ? rc[j] : 0u;
-#pragma unroll
-        for (int q = 0; q < D; ++q) rv[u][q] = ok ? rc[(q + 1) * RECN + j] : 0u;
-        own[u] = r0 + (ok ? owner[j - J0] : 0);
+        const int j = j0 + u * R;
+        e[u] = j < v.nbe ? tg::bel_elem(v.be[j]) : 0;
+        tg::elem_ids<EL, T>(a, e[u], in[u]);
       }
-      T x[UB][NV][D];
-      T kq[UB][NQ];
 #pragma unroll
-      for (int u = 0; u < UB; ++u) tg::p1_gather<D, T>(a, ra[u], rv[u], own[u], x[u], kq[u]);
+      for (int u = 0; u < UB; ++u) tg::elem_data<EL, T>(a, e[u], in[u]);
 #pragma unroll
       for (int u = 0; u < UB; ++u) {
-        const int j = base + u * R;
-        if (j >= J1) continue;
-        T Krow[NV];
-        if (!tg::p1_local_row<D, T>(x[u], kq[u], a.c, ts, Krow)) {
-          tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, ra[u] & 0xffffffu);
+        const int j = j0 + u * R;
+        if (j >= v.nbe) continue;
+        T K[NS];
+        if (!tg::p1_elem_sym<EL, T>(in[u], a.c, ts, K)) {
+          tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e[u]);
 #pragma unroll
-          for (int q = 0; q < NV; ++q) Krow[q] = T(0);
+          for (int q = 0; q < NS; ++q) K[q] = T(0);
         }
-        posw[j - J0] = tg::p1_positions<D>(ra[u], rv[u]);
 #pragma unroll
-        for (int q = 0; q < NV; ++q) contrib[q * cap + (j - J0)] = Krow[q];
+        for (int q = 0; q < NS; ++q) Ke[q * g.capE + j] = K[q];
       }
     }
     __syncthreads();
-    // phase 2: rows summed in increasing element order into the CSR-local copy
-    const int rbase = rp[r0];
-    if (i < r1) {
-      T* row = acc + (rp[i] - rbase);
-      const int len = rp[i + 1] - rp[i];
+    // Reduce: rows summed in increasing element order
+    const int i = v.r0 + (int)threadIdx.x;
+    const int rbase = v.rp[v.r0];
+    if (i < v.r1) {
+      T* row = acc + (v.rp[i] - rbase);
+      const int len = v.rp[i + 1] - v.rp[i];
       for (int q = 0; q < len; ++q) row[q] = T(0);
-      for (int q = js; q < je; ++q) {
-        const uint32_t w0 = posw[q];
+      const int je = v.ip[i + 1];
+      for (int j = v.ip[i]; j < je; ++j) {
+        const tg::BlkRec r{v.rc[j], sh};
+        const int le = r.le(), la = r.a();
 #pragma unroll
-        for (int c = 0; c < NV; ++c) row[tg::pos_of(w0, 0u, c)] += contrib[c * cap + q];
+        for (int c = 0; c < NV; ++c) row[r.pos(c, g.pb)] += Ke[tg::sym_index<NV>(la, c) * g.capE + le];
       }
     }
     __syncthreads();
-    const int nz = rp[r1] - rbase;
+    const int nz = v.rp[v.r1] - rbase;
     T* out = a.out + rbase;
     for (int q = threadIdx.x; q < nz; q += R) out[q] = acc[q];
     __syncthreads();  // stage s and the work buffers are free again
@@ -203,10 +135,140 @@ __global__ void __launch_bounds__(BS, (D == 2 && sizeof(T) == 4) ? 5 : 1) k_bili
 }
 
 template <int D, typename T>
-size_t p1_pipe_smem(int R, int cap, int max_row) {
-  constexpr int NV = D + 1;
-  return tab_bytes<T>() + 16 + 64 + 2 * ((size_t)(R + 8) * 8 + (size_t)NV * (cap + 8) * 4) +
-         tg::staged_bytes<T, NV, 1>(R, cap, max_row);
+size_t bilinear_blk_smem(const tg_pattern* p) {
+  constexpr int NV = D + 1, NS = NV * (NV + 1) / 2;
+  const tg::BlkArgs g = tg::blk_args(p);
+  return tab_bytes<T>() + tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE) +
+         ((size_t)NS * g.capE + p->blk_max_nz) * sizeof(T);
+}
+
+// P1 load vector over element-once row blocks: Map F_e (NV values) per
+// distinct element, Reduce F[i] = sum of the incidences' entries in
+// increasing element order (second line of Eq. (matlclquad)).
+template <int D, typename T>
+__global__ void __launch_bounds__(BS) k_load_blk(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
+                                                 const tg::BlkArgs g) {
+  constexpr int EL = D == 2 ? TG_P1_TRI : TG_P1_TET;
+  constexpr int NV = D + 1, NQ = D == 2 ? 3 : 4;
+  constexpr int UB = sizeof(T) == 4 ? 4 : 2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  auto& ts = *reinterpret_cast<tg::RefTab<T>*>(smem);
+  tg::BlkPipe pipe;
+  T* Fe = reinterpret_cast<T*>(pipe.init(smem + tab_bytes<T>(), g));
+  copy_table(ts, tab);
+  const int R = blockDim.x;
+  const int64_t G = gridDim.x;
+  const int sh = NV * g.pb;
+  int64_t b = blockIdx.x;
+  int nJ0 = 0, nJ1 = 0, nE = 0;
+  if (threadIdx.x == 0 && b < g.nblocks) {
+    int J0, J1, ne;
+    tg::BlkPipe::peek(g, b, J0, J1, ne);
+    pipe.issue(g, 0, b, J0, J1, ne);
+    if (b + G < g.nblocks) tg::BlkPipe::peek(g, b + G, nJ0, nJ1, nE);
+  }
+  for (int k = 0; b < g.nblocks; ++k, b += G) {
+    const int s = k & 1;
+    const bool ahead = b + G < g.nblocks;
+    if (threadIdx.x == 0 && ahead) {
+      pipe.issue(g, s ^ 1, b + G, nJ0, nJ1, nE);
+      if (b + 2 * G < g.nblocks) tg::BlkPipe::peek(g, b + 2 * G, nJ0, nJ1, nE);
+    }
+    if (!pipe.wait(s, k, ahead, a.status)) return;
+    const tg::BlkView v = pipe.view(s);
+    for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * R) {
+      int64_t e[UB];
+      int vid[UB][NV];
+      T x[UB][NV][D];
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int j = j0 + u * R;
+        e[u] = j < v.nbe ? tg::bel_elem(v.be[j]) : 0;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) vid[u][c] = __ldg(a.cells + e[u] * NV + c);
+      }
+      T fv[UB][NV > NQ ? NV : NQ];
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) tg::load_x<D, T>(a.coords, vid[u][c], x[u][c]);
+        if (a.layout == TG_PER_NODE) {
+#pragma unroll
+          for (int c = 0; c < NV; ++c) fv[u][c] = __ldg(a.coef + vid[u][c]);
+        } else if (a.layout == TG_PER_QP) {
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) fv[u][q] = __ldg(a.coef + e[u] * NQ + q);
+        } else {
+          fv[u][0] = __ldg(a.coef);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int j = j0 + u * R;
+        if (j >= v.nbe) continue;
+        tg::Geom<D, T> gm;
+        if constexpr (D == 2) tg::tri_geom_x(x[u][0], x[u][1], x[u][2], gm);
+        else tg::tet_geom_x(x[u][0], x[u][1], x[u][2], x[u][3], gm);
+        const T adet = absv(gm.det);
+        const bool ok = adet > tg::det_tiny<T>();
+        if (!ok) tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e[u]);
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          T val;
+          if (a.layout == TG_PER_NODE) {
+            T s2 = T(0);
+#pragma unroll
+            for (int bb = 0; bb < NV; ++bb) s2 = fma(ts.M[c][bb], fv[u][bb], s2);
+            val = adet * s2;
+          } else if (a.layout == TG_PER_QP) {
+            T s2 = T(0);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) s2 = fma(ts.w[q] * ts.phi[q][c], fv[u][q], s2);
+            val = adet * s2;
+          } else {
+            val = adet * ts.m1[c] * fv[u][0];
+          }
+          Fe[c * g.capE + j] = ok ? val : T(0);
+        }
+      }
+    }
+    __syncthreads();
+    const int i = v.r0 + (int)threadIdx.x;
+    if (i < v.r1) {
+      T f = T(0);
+      const int je = v.ip[i + 1];
+      for (int j = v.ip[i]; j < je; ++j) {
+        const tg::BlkRec r{v.rc[j], sh};
+        f += Fe[r.a() * g.capE + r.le()];
+      }
+      a.out[i] = f;
+    }
+    __syncthreads();
+  }
+}
+
+template <int D, typename T>
+size_t load_blk_smem(const tg_pattern* p) {
+  const tg::BlkArgs g = tg::blk_args(p);
+  return tab_bytes<T>() + tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE) + (size_t)(D + 1) * g.capE * sizeof(T);
+}
+
+// Persistent launch of an element-once kernel: one CTA of blk_rows threads
+// per resident slot, at most one per row block.
+template <typename K>
+tg_status launch_blk(K kern, size_t smem, const tg_pattern* p, dim3* grid_out) {
+  tg_status st = tg::set_smem((const void*)kern, smem);
+  if (st != TG_OK) return st;
+  int per_sm = 0;
+  TG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, p->blk_rows, smem));
+  *grid_out = dim3((unsigned)std::min<int64_t>(p->n_blk, (int64_t)std::max(per_sm, 1) * tg::sm_count()));
+  return TG_OK;
+}
+
+// Whether the element-once kernels serve this pattern at this precision.
+template <typename T>
+bool use_blk(const tg_pattern* p, size_t smem) {
+  return p->bel != nullptr && smem <= kBlkSmemMax;
 }
 
 // Comparison point: classic scatter-add (Eq. (scatter_add)) with atomics,
@@ -377,8 +439,6 @@ FwdArgs<T> base_args(const tg_pattern* p, const void* coords) {
   a.out = nullptr;
   a.n = p->N;
   a.status = p->status;
-  a.rec = p->rec;
-  a.rec_stride = (p->E * p->nv + 3) & ~3ll;
   return a;
 }
 
@@ -406,23 +466,15 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
   const size_t smem = tab_bytes<T>() + stage;
   const int cap = std::max(1, R * p->max_deg);
   if constexpr (EL == TG_P1_TRI || EL == TG_P1_TET) {
-    if (p->rec) {
-      constexpr int D = El::dim;
-      // rows per block: the largest R in {128, 64, 32} whose two stages and
-      // work buffers fit in 100 KB (at least two CTAs per SM)
-      int Rp = 128;
-      while (Rp > 32 && p1_pipe_smem<D, T>(Rp, Rp * std::max(1, p->max_deg), p->max_row_len) > 100 * 1024) Rp /= 2;
-      const int capp = Rp * std::max(1, p->max_deg);
-      const size_t smp = p1_pipe_smem<D, T>(Rp, capp, p->max_row_len);
-      auto kern = k_bilinear_p1<D, T>;
-      tg_status st = set_smem((const void*)kern, smp);
+    constexpr int D = El::dim;
+    const size_t sb = bilinear_blk_smem<D, T>(p);
+    if (use_blk<T>(p, sb)) {
+      auto kern = k_bilinear_blk<D, T>;
+      dim3 grid;
+      tg_status st = launch_blk(kern, sb, p, &grid);
       if (st != TG_OK) return st;
-      int per_sm = 0;
-      TG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Rp, smp));
-      const int64_t nblocks = (p->N + Rp - 1) / Rp;
-      const int grid = (int)std::min<int64_t>(nblocks, (int64_t)std::max(per_sm, 1) * tg::sm_count());
-      kern<<<grid, Rp, smp, s>>>(a, tab, capp, nblocks);
-      TG_CK_LAUNCH("k_bilinear_p1");
+      kern<<<grid, p->blk_rows, sb, s>>>(a, tab, tg::blk_args(p));
+      TG_CK_LAUNCH("k_bilinear_blk");
       return TG_OK;
     }
   }
@@ -468,6 +520,19 @@ tg_status load(const tg_pattern* p, const void* coords, const void* f, tg_layout
   a.out = static_cast<T*>(F);
   const tg_element el = p->el == TG_P1_TET_VEC3 ? TG_P1_TET : p->el;
   const tg::RefTab<T>& tab = table<T>(el);
+  if (ncomp == 1 && (el == TG_P1_TRI || el == TG_P1_TET) && p->bel) {
+    const bool tri = el == TG_P1_TRI;
+    const size_t sb = tri ? load_blk_smem<2, T>(p) : load_blk_smem<3, T>(p);
+    if (use_blk<T>(p, sb)) {
+      dim3 grid;
+      tg_status st = tri ? launch_blk(k_load_blk<2, T>, sb, p, &grid) : launch_blk(k_load_blk<3, T>, sb, p, &grid);
+      if (st != TG_OK) return st;
+      if (tri) k_load_blk<2, T><<<grid, p->blk_rows, sb, s>>>(a, tab, tg::blk_args(p));
+      else k_load_blk<3, T><<<grid, p->blk_rows, sb, s>>>(a, tab, tg::blk_args(p));
+      TG_CK_LAUNCH("k_load_blk");
+      return TG_OK;
+    }
+  }
   // rows per CTA: the largest R in {128, 64, 32} whose stage fits in 64 KB
   int R = BS;
   while (R > 32 && (size_t)ncomp * R * p->max_deg * sizeof(T) > 64 * 1024) R /= 2;

@@ -26,8 +26,6 @@ struct FwdArgs {
   T* __restrict__ out;
   int64_t n;  // rows (gather kernels) or elements (atomic kernel)
   unsigned long long* status;
-  const uint32_t* __restrict__ rec;  // P1 incidence records (NULL: generic path)
-  int64_t rec_stride;                // incidences (E * nv)
 };
 
 template <typename T>
@@ -101,6 +99,30 @@ __device__ __forceinline__ void elem_data(const FwdArgs<T>& a, int64_t e, ElemIn
   }
 }
 
+// Scales of a P1 matrix: sc = (sum_q w_q kappa_q) / |det J| and mc = c |det J|
+// (fixed-order fused multiply-adds).
+template <int NQ, typename T>
+__device__ __forceinline__ void p1_scales(const T (&kq)[NQ], const RefTab<T>& ts, T adet, T c, T& sc, T& mc) {
+  T s = ts.w[0] * kq[0];
+#pragma unroll
+  for (int q = 1; q < NQ; ++q) s = fma(ts.w[q], kq[q], s);
+  sc = s * (T(1) / adet);
+  mc = c * adet;
+}
+
+// Coordinates of node v.
+template <int D, typename T>
+__device__ __forceinline__ void load_x(const T* __restrict__ coords, int v, T (&x)[D]) {
+  if constexpr (D == 2) {
+    const auto p = ldg2(coords, v);
+    x[0] = p.x;
+    x[1] = p.y;
+  } else {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) x[r] = __ldg(coords + 3ll * v + r);
+  }
+}
+
 // Row la of the local matrix from loaded inputs; false for a degenerate
 // element.  Same arithmetic, operation for operation, as scalar_row.
 template <int EL, typename T>
@@ -112,11 +134,9 @@ __device__ __forceinline__ bool elem_row(const ElemIn<EL, T>& in, T c, const Ref
     const T adet = absv(g.det);
     if (!(adet > det_tiny<T>())) return false;
     if constexpr (EL == TG_P1_TRI) {
-      const T inv = T(1) / adet;
-      T s = T(0);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) s += ts.w[q] * in.kq[q];
-      p1_row<2, T>(g, la, s * inv, c * adet, ts.M[la], Krow);
+      T sc, mc;
+      p1_scales<3, T>(in.kq, ts, adet, c, sc, mc);
+      p1_row<2, T>(g, la, sc, mc, ts.M[la], Krow);
     } else {
       p2_row<T>(g, la, in.kq, T(1) / adet, c * adet, ts, Krow);
     }
@@ -125,12 +145,31 @@ __device__ __forceinline__ bool elem_row(const ElemIn<EL, T>& in, T c, const Ref
     tet_geom_x(in.x[0], in.x[1], in.x[2], in.x[3], g);
     const T adet = absv(g.det);
     if (!(adet > det_tiny<T>())) return false;
-    const T inv = T(1) / adet;
-    T s = T(0);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) s += ts.w[q] * in.kq[q];
-    p1_row<3, T>(g, la, s * inv, c * adet, ts.M[la], Krow);
+    T sc, mc;
+    p1_scales<4, T>(in.kq, ts, adet, c, sc, mc);
+    p1_row<3, T>(g, la, sc, mc, ts.M[la], Krow);
   }
+  return true;
+}
+
+// Upper triangle (row by row) of the P1 local matrix of an element; false
+// for a degenerate element.  Entry for entry the arithmetic of elem_row.
+template <int EL, typename T>
+__device__ __forceinline__ bool p1_elem_sym(const ElemIn<EL, T>& in, T c, const RefTab<T>& ts,
+                                            T (&K)[Elem<EL>::nv * (Elem<EL>::nv + 1) / 2]) {
+  constexpr int D = Elem<EL>::dim, NV = D + 1;
+  Geom<D, T> g;
+  if constexpr (D == 2) tri_geom_x(in.x[0], in.x[1], in.x[2], g);
+  else tet_geom_x(in.x[0], in.x[1], in.x[2], in.x[3], g);
+  const T adet = absv(g.det);
+  if (!(adet > det_tiny<T>())) return false;
+  T sc, mc;
+  p1_scales<Elem<EL>::nq, T>(in.kq, ts, adet, c, sc, mc);
+  int k = 0;
+#pragma unroll
+  for (int a = 0; a < NV; ++a)
+#pragma unroll
+    for (int b = a; b < NV; ++b) K[k++] = p1_entry<D, T>(g.n[a], g.n[b], sc, mc, ts.M[a][b]);
   return true;
 }
 
@@ -254,139 +293,10 @@ __device__ __forceinline__ void assemble_rows(const FwdArgs<T>& a, const RefTab<
   reduce_rows<T, NV, NPW>(a, contrib, posw, acc, cap, r0, r1, J0);
 }
 
-// P1 fast path of assemble_rows, reading the incidence records (rec): the
-// record carries the element index and the other vertex ids with their
-// column positions, and the own vertex is the row itself (found through a
-// shared-memory map from incidence to row), so phase 1 is two dependent
-// loads deep (record, then coordinates and coefficients) instead of three.
-// With the own vertex first, the row is row 0 of the local matrix of the
-// cyclically reordered element; |det J|, the gradients and the symmetric P1
-// rules do not depend on the vertex order, so the entries are those of the
-// generic path up to rounding (and bitwise identical across runs).
-// Vertex coordinates (own vertex first) and the coefficient at the points of
-// one incidence from its record words.
-template <int D, typename T>
-__device__ __forceinline__ void p1_gather(const FwdArgs<T>& a, uint32_t ra, const uint32_t (&rv)[D], int own,
-                                          T (&x)[D + 1][D], T (&kq)[D == 2 ? 3 : 4]) {
-  constexpr int NV = D + 1, NQ = D == 2 ? 3 : 4;
-  int vid[NV];
-  vid[0] = own;
-#pragma unroll
-  for (int k = 0; k < D; ++k) vid[k + 1] = (int)(rv[k] & 0xffffffu);
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    if constexpr (D == 2) {
-      const auto p = ldg2(a.coords, vid[k]);
-      x[k][0] = p.x;
-      x[k][1] = p.y;
-    } else {
-#pragma unroll
-      for (int r = 0; r < 3; ++r) x[k][r] = __ldg(a.coords + 3ll * vid[k] + r);
-    }
-  }
-  const int64_t e = ra & 0xffffffu;
-  if (a.layout == TG_PER_QP) {
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) kq[q] = __ldg(a.coef + e * NQ + q);
-  } else {
-    const T k = a.layout == TG_PER_ELEMENT ? __ldg(a.coef + e) : __ldg(a.coef);
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) kq[q] = k;
-  }
-}
-
-// Row 0 (the own vertex) of the local P1 matrix; false for a degenerate element.
-template <int D, typename T>
-__device__ __forceinline__ bool p1_local_row(const T (&x)[D + 1][D], const T (&kq)[D == 2 ? 3 : 4], T c,
-                                             const RefTab<T>& ts, T (&Krow)[D + 1]) {
-  constexpr int NQ = D == 2 ? 3 : 4;
-  Geom<D, T> g;
-  if constexpr (D == 2) tri_geom_x(x[0], x[1], x[2], g);
-  else tet_geom_x(x[0], x[1], x[2], x[3], g);
-  const T adet = absv(g.det);
-  if (!(adet > det_tiny<T>())) return false;
-  const T inv = T(1) / adet;
-  T s = T(0);
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) s += ts.w[q] * kq[q];
-  p1_row<D, T>(g, 0, s * inv, c * adet, ts.M[0], Krow);
-  return true;
-}
-
-// Packed column positions (own first) of an incidence.
-template <int D>
-__device__ __forceinline__ uint32_t p1_positions(uint32_t ra, const uint32_t (&rv)[D]) {
-  uint32_t pw = ra >> 24;
-#pragma unroll
-  for (int k = 0; k < D; ++k) pw |= (rv[k] >> 24) << (8 * (k + 1));
-  return pw;
-}
-
-template <int D, typename T>
-__device__ __forceinline__ void assemble_rows_p1(const FwdArgs<T>& a, const RefTab<T>& ts, unsigned char* buf, int cap,
-                                                 int64_t r0, int64_t r1) {
-  constexpr int NV = D + 1, NQ = D == 2 ? 3 : 4;
-  constexpr int UB = (D == 2 && sizeof(T) == 4) ? 3 : 2;
-  const int R = blockDim.x;
-  T* contrib = reinterpret_cast<T*>(buf);
-  uint32_t* posw = reinterpret_cast<uint32_t*>(contrib + (size_t)NV * cap);
-  uint8_t* owner = reinterpret_cast<uint8_t*>(posw + cap);
-  T* acc = reinterpret_cast<T*>(buf + staged_head<T, NV, 1>(cap));
-  const int J0 = __ldg(a.inc_ptr + r0), J1 = __ldg(a.inc_ptr + r1);
-  {
-    const int64_t i = r0 + threadIdx.x;
-    if (i < r1) {
-      const int js = __ldg(a.inc_ptr + i) - J0, je = __ldg(a.inc_ptr + i + 1) - J0;
-      for (int k = js; k < je; ++k) owner[k] = (uint8_t)threadIdx.x;
-    }
-  }
-  __syncthreads();
-  const int64_t stride = a.rec_stride;
-  for (int base = J0 + (int)threadIdx.x; base < J1; base += UB * R) {
-    uint32_t ra[UB], rv[UB][D];
-    int own[UB];
-#pragma unroll
-    for (int u = 0; u < UB; ++u) {
-      const int j = base + u * R;
-      const bool ok = j < J1;
-      ra[u] = ok ? __ldg(a.rec + j) : 0u;
-#pragma unroll
-      for (int k = 0; k < D; ++k) rv[u][k] = ok ? __ldg(a.rec + (k + 1) * stride + j) : 0u;
-      own[u] = (int)r0 + (ok ? owner[j - J0] : 0);
-    }
-    T x[UB][NV][D];
-    T kq[UB][NQ];
-#pragma unroll
-    for (int u = 0; u < UB; ++u) p1_gather<D, T>(a, ra[u], rv[u], own[u], x[u], kq[u]);
-#pragma unroll
-    for (int u = 0; u < UB; ++u) {
-      const int j = base + u * R;
-      if (j >= J1) continue;
-      T Krow[NV];
-      if (!p1_local_row<D, T>(x[u], kq[u], a.c, ts, Krow)) {
-        record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, ra[u] & 0xffffffu);
-#pragma unroll
-        for (int b = 0; b < NV; ++b) Krow[b] = T(0);
-      }
-      posw[j - J0] = p1_positions<D>(ra[u], rv[u]);
-#pragma unroll
-      for (int b = 0; b < NV; ++b) contrib[b * cap + (j - J0)] = Krow[b];
-    }
-  }
-  __syncthreads();
-  reduce_rows<T, NV, 1>(a, contrib, posw, acc, cap, r0, r1, J0);
-}
-
-// One row block through the fast path when the pattern has records.
+// One row block of the batched kernel.
 template <int EL, typename T>
 __device__ __forceinline__ void assemble_block(const FwdArgs<T>& a, const RefTab<T>& ts, unsigned char* buf, int cap,
                                                int64_t r0, int64_t r1) {
-  if constexpr (EL == TG_P1_TRI || EL == TG_P1_TET) {
-    if (a.rec != nullptr) {
-      assemble_rows_p1<Elem<EL>::dim, T>(a, ts, buf, cap, r0, r1);
-      return;
-    }
-  }
   assemble_rows<EL, T>(a, ts, buf, cap, r0, r1);
 }
 

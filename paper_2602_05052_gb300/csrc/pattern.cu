@@ -9,7 +9,9 @@
 //      elements is its CSR row (structural zeros kept); scan -> row_ptr;
 //   4. per incidence: 8-bit positions of the element's nodes inside the
 //      owning row (inc_pos) and the element-to-slot map (elem_slot);
-//   5. vector elasticity: expansion of the node CSR to the DoF CSR
+//   5. P1: row blocks with their distinct elements and packed incidence
+//      records (the element-once kernels);
+//   6. vector elasticity: expansion of the node CSR to the DoF CSR
 //      (DoF = 3 * node + component, 3x3 blocks).
 #include <cstdio>
 #include <vector>
@@ -158,7 +160,6 @@ __global__ void __launch_bounds__(128) k_rows(const int32_t* __restrict__ cells,
                                               int32_t* __restrict__ row_len, int* __restrict__ maxes,
                                               const int32_t* __restrict__ row_ptr, int32_t* __restrict__ col_idx,
                                               uint32_t* __restrict__ inc_pos, int32_t* __restrict__ elem_slot,
-                                              uint32_t* __restrict__ rec, int64_t rec_stride,
                                               unsigned long long* status) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -191,17 +192,6 @@ __global__ void __launch_bounds__(128) k_rows(const int32_t* __restrict__ cells,
     }
     inc_pos[(int64_t)j * npw] = w0;
     if (npw == 2) inc_pos[(int64_t)j * npw + 1] = w1;
-    if (rec) {
-      // own position with the element index, then the other vertices in
-      // cyclic order after a with their positions
-      const int64_t stride = rec_stride;
-      rec[j] = (uint32_t)e | ((uint32_t)lower_bound(cols, len, cells[(int64_t)e * nv + a]) << 24);
-      for (int k = 1; k < nv; ++k) {
-        const int b = (a + k) % nv;
-        const int v = cells[(int64_t)e * nv + b];
-        rec[k * stride + j] = (uint32_t)v | ((uint32_t)lower_bound(cols, len, v) << 24);
-      }
-    }
   }
 }
 
@@ -216,6 +206,95 @@ __global__ void k_expand3(const int32_t* __restrict__ row_ptr, const int32_t* __
       for (int j = 0; j < 3; ++j) col_idx3[9ll * r0 + (i * len + p) * 3 + j] = 3 * col_idx[r0 + p] + j;
   }
   if (n == N - 1) row_ptr3[3 * N] = 9 * row_ptr[N];
+}
+
+// ------------------------------------------------------------------ row blocks
+// Per block of R rows: its incidence count and its CSR value count.
+__global__ void k_blk_stats(const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ row_ptr, int64_t N, int R,
+                            int64_t nblk, int* __restrict__ maxes) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblk) return;
+  const int64_t r0 = b * R, r1 = r0 + R < N ? r0 + R : N;
+  atomicMax(maxes + 0, inc_ptr[r1] - inc_ptr[r0]);
+  atomicMax(maxes + 1, row_ptr[r1] - row_ptr[r0]);
+}
+
+// One CTA per row block: sort the elements of the block's incidences,
+// keep the distinct ones (bel, with the owner bit), and pack every
+// incidence's record (brec).  P = power of two >= the block's incidences.
+__global__ void __launch_bounds__(256) k_blocks(const int32_t* __restrict__ cells, int nv,
+                                                const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc_e,
+                                                const uint32_t* __restrict__ inc_pos, int64_t N, int R, int pb, int P,
+                                                uint32_t* __restrict__ bel, int32_t* __restrict__ bel_cnt,
+                                                uint32_t* __restrict__ brec, int* __restrict__ max_elems) {
+  extern __shared__ int sk[];
+  int* key = sk;      // [P]
+  int* uq = sk + P;   // [P]
+  __shared__ int s_nbe;
+  const int64_t b = blockIdx.x;
+  const int64_t r0 = b * R, r1 = r0 + R < N ? r0 + R : N;
+  const int J0 = inc_ptr[r0], J1 = inc_ptr[r1], n = J1 - J0;
+  for (int k = threadIdx.x; k < P; k += blockDim.x) key[k] = k < n ? (inc_e[J0 + k] >> 3) : INT32_MAX;
+  __syncthreads();
+  // bitonic sort, ascending
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const int x = key[i], y = key[ixj];
+          if ((x > y) == ((i & k) == 0)) {
+            key[i] = y;
+            key[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int k = 0; k < n; ++k)
+      if (k == 0 || key[k] != key[k - 1]) uq[m++] = key[k];
+    s_nbe = m;
+    bel_cnt[b] = m;
+    atomicMax(max_elems, m);
+  }
+  __syncthreads();
+  const int nbe = s_nbe;
+  for (int k = threadIdx.x; k < nbe; k += blockDim.x) {
+    const int e = uq[k];
+    int vmin = INT32_MAX;
+    for (int a = 0; a < nv; ++a) vmin = min(vmin, cells[(int64_t)e * nv + a]);
+    bel[J0 + k] = (uint32_t)e | ((int64_t)vmin / R == b ? 0x80000000u : 0u);
+  }
+  const uint32_t pmask = (1u << pb) - 1u;
+  for (int j = J0 + (int)threadIdx.x; j < J1; j += blockDim.x) {
+    const int e = inc_e[j] >> 3, a = inc_e[j] & 7;
+    int lo = 0, hi = nbe;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (uq[mid] < e) lo = mid + 1;
+      else hi = mid;
+    }
+    const uint32_t w = inc_pos[j];  // 8-bit positions (nv <= 4)
+    uint32_t r = 0;
+    for (int c = 0; c < nv; ++c) r |= ((w >> (8 * c)) & pmask) << (c * pb);
+    brec[j] = r | ((uint32_t)a << (nv * pb)) | ((uint32_t)lo << (nv * pb + 2));
+  }
+}
+
+// Per element: the position of every vertex's column in every vertex's row.
+__global__ void k_elem_pos(const int32_t* __restrict__ cells, const int32_t* __restrict__ elem_slot,
+                           const int32_t* __restrict__ row_ptr, int64_t E, int nv, int pb, uint64_t* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  uint64_t w = 0;
+  for (int a = 0; a < nv; ++a) {
+    const int ra = row_ptr[cells[e * nv + a]];
+    for (int b = 0; b < nv; ++b)
+      w |= (uint64_t)(elem_slot[(e * nv + a) * nv + b] - ra) << ((a * nv + b) * pb);
+  }
+  out[e] = w;
 }
 
 // Device buffers freed on scope exit unless released.
@@ -269,6 +348,69 @@ tg_status read_status(const tg_pattern* p, cudaStream_t s, const char* stage) {
     std::snprintf(buf, sizeof(buf), "%s: %s at element %llu", stage, tg_status_string((tg_status)h[0]), h[1]);
     tg::set_error(buf);
     return (tg_status)h[0];
+  }
+  return TG_OK;
+}
+
+
+// Rows per block of the element-once kernels.
+int blk_rows_of(tg_element el) { return el == TG_P1_TRI ? 128 : 64; }
+
+// Row blocks (step 5).  Leaves p->bel == NULL when the packed fields do not
+// fit (the generic kernels are used then).
+tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
+  const int nv = p->nv, R = blk_rows_of(p->el);
+  const int64_t N = p->N, E = p->E, nvE = E * nv, nblk = (N + R - 1) / R;
+  int pb = 1;
+  while ((1 << pb) < p->max_row_len) ++pb;
+  const int le_bits = 32 - nv * pb - 2;
+  if (le_bits < 8) return TG_OK;
+  Tmp tmp;
+  int* maxes = nullptr;
+  TG_CK(tmp.alloc(&maxes, 3));
+  TG_CK(cudaMemsetAsync(maxes, 0, 3 * sizeof(int), s));
+  k_blk_stats<<<tg::grid_for(nblk, kThreads), kThreads, 0, s>>>(p->inc_ptr, p->row_ptr, N, R, nblk, maxes);
+  TG_CK_LAUNCH("k_blk_stats");
+  int h[3];
+  TG_CK(cudaMemcpyAsync(h, maxes, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  int P = 1;
+  while (P < h[0]) P <<= 1;
+  if (P > 4096) return TG_OK;  // blocks of very high degree: generic kernels
+  uint32_t *bel = nullptr, *brec = nullptr;
+  int32_t* cnt = nullptr;
+  TG_CK(cudaMalloc(&bel, nvE * sizeof(uint32_t) + 16));
+  TG_CK(cudaMalloc(&brec, nvE * sizeof(uint32_t) + 16));
+  TG_CK(cudaMalloc(&cnt, nblk * sizeof(int32_t) + 16));
+  p->bel = bel;  // owned by the pattern from here on
+  p->brec = brec;
+  p->bel_cnt = cnt;
+  TG_CK(cudaMemsetAsync(bel, 0, nvE * sizeof(uint32_t) + 16, s));
+  TG_CK(cudaMemsetAsync(brec, 0, nvE * sizeof(uint32_t) + 16, s));
+  k_blocks<<<(unsigned)nblk, 256, 2 * P * sizeof(int), s>>>(p->cells, nv, p->inc_ptr, p->inc_e, p->inc_pos, N, R, pb,
+                                                             P, bel, cnt, brec, maxes + 2);
+  TG_CK_LAUNCH("k_blocks");
+  TG_CK(cudaMemcpyAsync(h + 2, maxes + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  if (h[2] > (1 << le_bits)) {  // local element indices do not fit: no blocks
+    cudaFree(bel);
+    cudaFree(brec);
+    cudaFree(cnt);
+    p->bel = p->brec = nullptr;
+    p->bel_cnt = nullptr;
+    return TG_OK;
+  }
+  p->blk_rows = R;
+  p->blk_pb = pb;
+  p->n_blk = nblk;
+  p->blk_max_inc = h[0];
+  p->blk_max_nz = h[1];
+  p->blk_max_elems = h[2];
+  if (nv * nv * pb <= 64) {
+    TG_CK(cudaMalloc(&p->elem_pos, E * sizeof(uint64_t) + 16));
+    k_elem_pos<<<tg::grid_for(E, kThreads), kThreads, 0, s>>>(p->cells, p->elem_slot, p->row_ptr, E, nv, pb,
+                                                              p->elem_pos);
+    TG_CK_LAUNCH("k_elem_pos");
   }
   return TG_OK;
 }
@@ -350,8 +492,7 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   TG_CK(cudaMemsetAsync(maxes, 0, 2 * sizeof(int), s));
   const bool vec3 = el == TG_P1_TET_VEC3;
   k_rows<false><<<tg::grid_for(N, 128), 128, 0, s>>>(p->cells, p->inc_ptr, p->inc_e, N, nv, p->npw, vec3, row_len,
-                                                      maxes, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
-                                                      p->status);
+                                                      maxes, nullptr, nullptr, nullptr, nullptr, p->status);
   TG_CK_LAUNCH("k_rows<false>");
   int hmax[2];
   TG_CK(cudaMemcpyAsync(hmax, maxes, sizeof(hmax), cudaMemcpyDeviceToHost, s));
@@ -375,14 +516,18 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   TG_CK(cudaMalloc(&p->col_idx, nnz * sizeof(int32_t) + 16));
   TG_CK(cudaMalloc(&p->inc_pos, nvE * p->npw * sizeof(uint32_t) + 16));
   TG_CK(cudaMalloc(&p->elem_slot, nvE * nv * sizeof(int32_t) + 16));
-  if (el != TG_P2_TRI && N < (1ll << 24) && E < (1ll << 24))
-    TG_CK(cudaMalloc(&p->rec, (size_t)nv * ((nvE + 3) & ~3ll) * sizeof(uint32_t) + 16));
   k_rows<true><<<tg::grid_for(N, 128), 128, 0, s>>>(p->cells, p->inc_ptr, p->inc_e, N, nv, p->npw, vec3, nullptr,
                                                      nullptr, p->row_ptr, p->col_idx, p->inc_pos, p->elem_slot,
-                                                     p->rec, (nvE + 3) & ~3ll, p->status);
+                                                     p->status);
   TG_CK_LAUNCH("k_rows<true>");
 
-  // 5. DoF-level CSR for elasticity
+
+  // 5. row blocks of the element-once P1 kernels
+  if ((el == TG_P1_TRI || el == TG_P1_TET) && E > 0) {
+    if ((st = build_blocks(p, s)) != TG_OK) return st;
+  }
+
+  // 6. DoF-level CSR for elasticity
   if (vec3) {
     TG_CK(cudaMalloc(&p->row_ptr3, (3 * N + 1) * sizeof(int32_t)));
     TG_CK(cudaMalloc(&p->col_idx3, 9 * nnz * sizeof(int32_t) + 16));

@@ -37,15 +37,26 @@ struct tg_pattern {
   int32_t* elem_slot = nullptr;
   int32_t* row_ptr3 = nullptr;
   int32_t* col_idx3 = nullptr;
-  // P1 incidence records (built when E, N < 2^24), structure of arrays with
-  // stride E*nv, in the incidence order of inc_e: for incidence j of node i
-  // in element e with local index a,
-  //   rec[j]            = e | p_i << 24
-  //   rec[k*E*nv + j]   = v_k | p_k << 24,  k = 1 .. nv-1,
-  // v_k the element's vertex (a + k) mod nv and p the column positions in
-  // row i.  The vertex ids arrive with the (coalesced) record, so the gather
-  // needs no second dependent load of the connectivity.
-  uint32_t* rec = nullptr;
+  // Row blocks of the element-once P1 kernels (P1 triangles and tetrahedra,
+  // built when the packed fields fit; bel == NULL otherwise).  Block b owns
+  // the rows [b*blk_rows, (b+1)*blk_rows) and hence the incidences
+  // [J0, J1) = [inc_ptr[b*blk_rows], inc_ptr[min((b+1)*blk_rows, N)]).
+  //   bel[J0 + k], k < bel_cnt[b]: the distinct elements incident to the
+  //     block's rows, ascending; bit 31 set in the one block that owns the
+  //     element (the block of its smallest vertex) for per-element outputs.
+  //   brec[j], j in [J0, J1), per incidence (row i, element e, local vertex
+  //     a), in the order of inc_e:  bits [b*pb, (b+1)*pb) the position of
+  //     vertex b's column in row i (b < nv), then a (2 bits), then the local
+  //     index of e in bel (the rest).
+  //   elem_pos[e] (64 bit): position of vertex b's column in vertex a's row
+  //     at bits [(a*nv + b)*pb, ...) (built when nv*nv*pb <= 64).
+  int blk_rows = 0, blk_pb = 0;
+  int blk_max_elems = 0, blk_max_inc = 0, blk_max_nz = 0;  // per-block maxima
+  int64_t n_blk = 0;
+  uint32_t* bel = nullptr;
+  int32_t* bel_cnt = nullptr;
+  uint32_t* brec = nullptr;
+  uint64_t* elem_pos = nullptr;
   // device status: [0] error code (first one wins), [1] smallest bad element
   unsigned long long* status = nullptr;
   // per-CTA partial sums of global reductions (backward of c / constant kappa)

@@ -50,6 +50,29 @@ def test_batch_bitwise_equals_single_launches(tg, dtype):
         assert relfro(out[j].cpu().numpy(), ref.val) <= TOL[dtype]
 
 
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("el", [mg.P1_TRI, mg.P1_TET])
+def test_batch_p1_bitwise_equals_single_launches(tg, dtype, el):
+    """P1 single launches take the element-once row blocks, the batch the
+    per-incidence rows; the entries and the summation order are the same, so
+    the results are bitwise equal."""
+    meshes = []
+    for k, n in enumerate([3, 17, 40] if el == mg.P1_TRI else [2, 5, 9]):
+        m = mg.jitter(mg.tri_grid(n), 50 + k) if el == mg.P1_TRI else mg.kuhn_tet_grid(n)
+        meshes.append(m)
+    nq = 3 if el == mg.P1_TRI else 4
+    pats = [tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, el) for m in meshes]
+    xs = [dev(m.coords, dtype) for m in meshes]
+    ks = [dev(mg.lognormal((m.n_elems, nq), 60 + k), dtype) for k, m in enumerate(meshes)]
+    cs = [0.0, 0.5, 2.0]
+    b = tg.tg_batch_create(pats)
+    out = [torch.full((p.nnz,), float("nan"), dtype=dtype, device="cuda") for p in pats]
+    tg.tg_batch_assemble(b, xs, ks, mg.PER_QP, cs, out)
+    for j, p in enumerate(pats):
+        single = tg.tg_assemble_bilinear(p, xs[j], ks[j], mg.PER_QP, cs[j])
+        assert torch.equal(out[j], single), j
+
 def test_batch_graph_capture_and_autotune(tg):
     dtype = torch.float32
     sizes = mg.batch_sizes(48, seed=9)
