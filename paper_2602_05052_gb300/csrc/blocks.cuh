@@ -2,7 +2,8 @@
 // the forward, load and backward kernels share.
 //
 // A persistent CTA walks the row blocks b = blockIdx.x, + gridDim.x, ...
-// Block b owns R = blockDim.x consecutive rows.  Its contiguous streams are:
+// Block b owns R consecutive rows (R <= the CTA's threads).  Its contiguous
+// streams are:
 //   - its slices of inc_ptr and row_ptr;
 //   - the records of its incidences (brec);
 //   - its list of distinct elements (bel).
@@ -28,12 +29,14 @@ struct BlkArgs {
   const int32_t* __restrict__ inc_ptr;
   const int32_t* __restrict__ row_ptr;
   const uint32_t* __restrict__ bel;
+  const int64_t* __restrict__ boff;
   const int32_t* __restrict__ bel_cnt;
   const uint32_t* __restrict__ brec;
   int64_t N;
   int64_t nblocks;
   int capE, capJ;  // stage capacities (multiples of 4): distinct elements, incidences
-  int pb;          // bits per position field of a record
+  int nv;          // vertices per element
+  int R;           // rows per block (at most the CTA's threads)
 };
 
 // Host: BlkArgs of a pattern with row blocks.
@@ -42,28 +45,31 @@ inline BlkArgs blk_args(const tg_pattern* p) {
   g.inc_ptr = p->inc_ptr;
   g.row_ptr = p->row_ptr;
   g.bel = p->bel;
+  g.boff = p->boff;
   g.bel_cnt = p->bel_cnt;
   g.brec = p->brec;
   g.N = p->N;
   g.nblocks = p->n_blk;
   g.capE = (p->blk_max_elems + 3) & ~3;
   g.capJ = (p->blk_max_inc + 3) & ~3;
-  g.pb = p->blk_pb;
+  g.nv = p->nv;
+  g.R = p->blk_rows;
   return g;
 }
 
 // Shared-memory bytes of the two stages plus barriers and block metadata.
-__host__ __device__ inline size_t blk_stage_bytes(int R, int capJ, int capE) {
-  return 16 + 128 + 2 * ((size_t)(R + 8) * 8 + (size_t)(capJ + 8) * 4 + (size_t)(capE + 8) * 4);
+__host__ __device__ inline size_t blk_stage_bytes(int R, int capJ, int capE, int nv) {
+  return 16 + 128 + 2 * ((size_t)(R + 8) * 8 + (size_t)(capJ + 8) * 4 + (size_t)(nv + 1) * capE * 4);
 }
 
 // Geometry of one row block as seen through its stage.
 struct BlkView {
   int r0, r1, J0, J1, nbe;
+  int bs;              // row stride of be
   const int* ip;       // ip[i] = inc_ptr[i], i in [r0, r1]
   const int* rp;       // rp[i] = row_ptr[i]
   const uint32_t* rc;  // rc[j] = brec[j], j in [J0, J1)
-  const uint32_t* be;  // be[k] = bel[J0 + k], k < nbe
+  const uint32_t* be;  // be[k] element k (with owner bit), be[(c+1)*bs + k] its vertex c; k < nbe
 };
 
 class BlkPipe {
@@ -72,10 +78,10 @@ class BlkPipe {
   // the first byte after them.  Thread 0 initialises the barriers; the
   // caller's next CTA barrier publishes them.
   __device__ unsigned char* init(unsigned char* p, const BlkArgs& g) {
-    R_ = blockDim.x;
+    R_ = g.R;
     IPN_ = R_ + 8;
     RECN_ = g.capJ + 8;
-    ELN_ = g.capE + 8;
+    ELN_ = (g.nv + 1) * g.capE;
     SW_ = 2 * IPN_ + RECN_ + ELN_;  // words per stage (a multiple of 4)
     bar_ = reinterpret_cast<uint64_t*>(p);
     meta_ = reinterpret_cast<int*>(p + 16);
@@ -88,37 +94,46 @@ class BlkPipe {
     return reinterpret_cast<unsigned char*>(st_ + 2 * SW_);
   }
 
-  // Thread 0: incidence range and element count of block blk (plain loads,
-  // issued early so that they are in flight while the CTA works).
-  __device__ static void peek(const BlkArgs& g, int64_t blk, int& J0, int& J1, int& nbe) {
-    const int R = blockDim.x;
-    J0 = __ldg(g.inc_ptr + blk * R);
-    J1 = __ldg(g.inc_ptr + (blk * R + R < g.N ? blk * R + R : g.N));
-    nbe = __ldg(g.bel_cnt + blk);
+  // Thread 0: incidence range, element count and element-list offset of
+  // block blk (plain loads, issued early so that they are in flight while
+  // the CTA works).
+  struct Peek {
+    int J0, J1, nbe;
+    int64_t bo;
+  };
+  __device__ static void peek(const BlkArgs& g, int64_t blk, int R, Peek& q) {
+    q.J0 = __ldg(g.inc_ptr + blk * R);
+    q.J1 = __ldg(g.inc_ptr + (blk * R + R < g.N ? blk * R + R : g.N));
+    q.nbe = __ldg(g.bel_cnt + blk);
+    q.bo = __ldg(g.boff + blk);
   }
 
-  // Thread 0: copy block blk's streams into stage s.  Every source range is
-  // widened to whole 16-byte groups (the pattern arrays carry 16 bytes of
-  // tail padding); the stage capacities hold the widened ranges.
-  __device__ void issue(const BlkArgs& g, int s, int64_t blk, int J0, int J1, int nbe) {
+  // Thread 0: copy block blk's streams into stage s.  The inc_ptr, row_ptr
+  // and brec ranges are widened to whole 16-byte groups (the pattern arrays
+  // carry 16 bytes of tail padding); the element list is a 16-byte aligned
+  // region of (nv + 1) * ((nbe + 3) & ~3) words.  The stage capacities hold
+  // all of them.
+  __device__ void issue(const BlkArgs& g, int s, int64_t blk, const Peek& q) {
     const int r0 = (int)(blk * R_), r1 = (int)(blk * R_ + R_ < g.N ? blk * R_ + R_ : g.N);
     const int a0 = r0 & ~3, nip = (r1 + 1 - a0 + 3) & ~3;
-    const int j0a = J0 & ~3, nrec = (J1 - j0a + 3) & ~3, nel = (J0 + nbe - j0a + 3) & ~3;
+    const int j0a = q.J0 & ~3, nrec = (q.J1 - j0a + 3) & ~3;
+    const int bs = (q.nbe + 3) & ~3, nel = (g.nv + 1) * bs;
     int* m = meta_ + 16 * s;
     m[0] = r0;
     m[1] = r1;
-    m[2] = J0;
-    m[3] = J1;
+    m[2] = q.J0;
+    m[3] = q.J1;
     m[4] = a0;
     m[5] = j0a;
-    m[6] = nbe;
-    const uint32_t bytes = 4u * (2u * nip + (J1 > J0 ? nrec : 0) + (nbe > 0 ? nel : 0));
+    m[6] = q.nbe;
+    m[7] = bs;
+    const uint32_t bytes = 4u * (2u * nip + (q.J1 > q.J0 ? nrec : 0) + nel);
     fence_proxy_async();
     mbar_arrive_expect_tx(&bar_[s], bytes);
     bulk_copy_g2s(ip(s), g.inc_ptr + a0, nip * 4, &bar_[s]);
     bulk_copy_g2s(rp(s), g.row_ptr + a0, nip * 4, &bar_[s]);
-    if (J1 > J0) bulk_copy_g2s(rec(s), g.brec + j0a, nrec * 4, &bar_[s]);
-    if (nbe > 0) bulk_copy_g2s(el(s), g.bel + j0a, nel * 4, &bar_[s]);
+    if (q.J1 > q.J0) bulk_copy_g2s(rec(s), g.brec + j0a, nrec * 4, &bar_[s]);
+    if (nel > 0) bulk_copy_g2s(el(s), g.bel + q.bo, nel * 4, &bar_[s]);
   }
 
   // All threads: wait (bounded) for stage s of use k; the outcome is made
@@ -145,10 +160,11 @@ class BlkPipe {
     v.J0 = m[2];
     v.J1 = m[3];
     v.nbe = m[6];
+    v.bs = m[7];
     v.ip = ip(s) - m[4];
     v.rp = rp(s) - m[4];
     v.rc = rec(s) - m[5];
-    v.be = el(s) + (m[2] - m[5]);
+    v.be = el(s);
     return v;
   }
 
@@ -165,22 +181,15 @@ class BlkPipe {
   int* st_;
 };
 
-// Fields of an incidence record.
+// Fields of an incidence record: 4-bit column positions, the local vertex
+// a (2 bits) and the local index of the element in the block's list.
+template <int NV>
 struct BlkRec {
   uint32_t w;
-  int sh;  // nv * pb
-  __device__ int le() const { return (int)(w >> (sh + 2)); }
-  __device__ int a() const { return (int)(w >> sh) & 3; }
-  __device__ int pos(int b, int pb) const { return (int)(w >> (b * pb)) & ((1 << pb) - 1); }
+  __device__ int le() const { return (int)(w >> (4 * NV + 2)); }
+  __device__ int a() const { return (int)(w >> (4 * NV)) & 3; }
+  __device__ int pos(int b) const { return (int)(w >> (4 * b)) & 15; }
 };
-
-// Index of entry (a, b) of a symmetric NV x NV matrix stored as its upper
-// triangle row by row; b is a compile-time constant in the unrolled loops.
-template <int NV>
-__device__ __forceinline__ int sym_index(int a, int b) {
-  const int lo = a < b ? a : b, hi = a < b ? b : a;
-  return lo * NV - lo * (lo - 1) / 2 + (hi - lo);
-}
 
 // The element of a bel entry (without the owner bit).
 __device__ __forceinline__ int64_t bel_elem(uint32_t w) { return (int64_t)(w & 0x7fffffffu); }

@@ -45,222 +45,235 @@ __global__ void __launch_bounds__(BS) k_bilinear_gather(const FwdArgs<T> a, cons
   tg::assemble_rows<EL, T>(a, ts, smem + tab_bytes<T>(), cap, r0, r1);
 }
 
+// Pipeline prologue and per-block step shared by the element-once kernels:
+// thread 0 issues block b + G into the other stage and peeks at b + 2G.
+#define TG_BLK_PIPELINE_BEGIN(pipe, g, status)                                          \
+  const int64_t G_ = gridDim.x;                                                         \
+  const int R_ = (g).R;                                                                 \
+  const int NT_ = blockDim.x;                                                           \
+  int64_t b_ = blockIdx.x;                                                              \
+  tg::BlkPipe::Peek nq_;                                                                \
+  if (threadIdx.x == 0 && b_ < (g).nblocks) {                                           \
+    tg::BlkPipe::Peek q0;                                                               \
+    tg::BlkPipe::peek(g, b_, R_, q0);                                                   \
+    (pipe).issue(g, 0, b_, q0);                                                         \
+    if (b_ + G_ < (g).nblocks) tg::BlkPipe::peek(g, b_ + G_, R_, nq_);                 \
+  }                                                                                     \
+  for (int k_ = 0; b_ < (g).nblocks; ++k_, b_ += G_) {                                  \
+    const int s_ = k_ & 1;                                                              \
+    const bool ahead_ = b_ + G_ < (g).nblocks;                                          \
+    if (threadIdx.x == 0 && ahead_) {                                                   \
+      (pipe).issue(g, s_ ^ 1, b_ + G_, nq_);                                            \
+      if (b_ + 2 * G_ < (g).nblocks) tg::BlkPipe::peek(g, b_ + 2 * G_, R_, nq_);        \
+    }                                                                                   \
+    if (!(pipe).wait(s_, k_, ahead_, status)) return;                                   \
+    const tg::BlkView v = (pipe).view(s_);
+
+#define TG_BLK_PIPELINE_END }
+
 // P1 forward over element-once row blocks (blocks.cuh):
-//   Map    - the local matrix K_e of every distinct element of the block,
-//            upper triangle (NS entries), into Ke[NS][capE];
+//   Map    - the local matrix K_e of every distinct element of the block into
+//            Ke[NV*NV][capE] (UB elements per thread, one round when
+//            UB * R >= the block's element count);
 //   Reduce - row i adds, for each incidence (e, a) in increasing e, row a of
 //            K_e into its CSR-local slice of acc; the block's slice of the
-//            CSR values is then stored with coalesced writes.
-template <int D, typename T>
+//            CSR values is then stored with coalesced writes (and acc is
+//            cleared for the next block on the way).
+template <int D, typename T, int UB>
 __global__ void __launch_bounds__(BS, D == 2 ? 4 : 2) k_bilinear_blk(const FwdArgs<T> a,
                                                                       const __grid_constant__ tg::RefTab<T> tab,
-                                                                      const tg::BlkArgs g) {
+                                                                      const tg::BlkArgs g, int cap_nz) {
   constexpr int EL = D == 2 ? TG_P1_TRI : TG_P1_TET;
   constexpr int NV = D + 1, NS = NV * (NV + 1) / 2;
-  constexpr int UB = sizeof(T) == 4 ? 4 : 2;
   extern __shared__ __align__(16) unsigned char smem[];
-  auto& ts = *reinterpret_cast<tg::RefTab<T>*>(smem);
   tg::BlkPipe pipe;
-  T* Ke = reinterpret_cast<T*>(pipe.init(smem + tab_bytes<T>(), g));
-  T* acc = Ke + (size_t)NS * g.capE;
-  copy_table(ts, tab);  // CTA barrier: also publishes the mbarrier initialisation
-  const int R = blockDim.x;
-  const int64_t G = gridDim.x;
-  const int sh = NV * g.pb;
-  int64_t b = blockIdx.x;
-  int nJ0 = 0, nJ1 = 0, nE = 0;
-  if (threadIdx.x == 0 && b < g.nblocks) {
-    int J0, J1, ne;
-    tg::BlkPipe::peek(g, b, J0, J1, ne);
-    pipe.issue(g, 0, b, J0, J1, ne);
-    if (b + G < g.nblocks) tg::BlkPipe::peek(g, b + G, nJ0, nJ1, nE);
-  }
-  for (int k = 0; b < g.nblocks; ++k, b += G) {
-    const int s = k & 1;
-    const bool ahead = b + G < g.nblocks;
-    if (threadIdx.x == 0 && ahead) {
-      pipe.issue(g, s ^ 1, b + G, nJ0, nJ1, nE);
-      if (b + 2 * G < g.nblocks) tg::BlkPipe::peek(g, b + 2 * G, nJ0, nJ1, nE);
+  T* Ke = reinterpret_cast<T*>(pipe.init(smem, g));
+  T* acc = Ke + (size_t)NV * NV * g.capE;
+  for (int q = threadIdx.x; q < cap_nz; q += blockDim.x) acc[q] = T(0);
+  __syncthreads();  // publishes the mbarrier initialisation and the cleared acc
+  TG_BLK_PIPELINE_BEGIN(pipe, g, a.status)
+  // Map
+  for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * NT_) {
+    int e[UB];
+    tg::ElemIn<EL, T> in[UB];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int j = j0 + u * NT_ < v.nbe ? j0 + u * NT_ : 0;  // idle slots load element 0 of the list
+      e[u] = (int)tg::bel_elem(v.be[j]);
+#pragma unroll
+      for (int c = 0; c < NV; ++c) in[u].v[c] = (int)v.be[(c + 1) * v.bs + j];
     }
-    if (!pipe.wait(s, k, ahead, a.status)) return;
-    const tg::BlkView v = pipe.view(s);
-    // Map: UB elements per thread in flight (ids, then coordinates and kappa)
-    for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * R) {
-      int64_t e[UB];
-      tg::ElemIn<EL, T> in[UB];
 #pragma unroll
-      for (int u = 0; u < UB; ++u) {
-        const int j = j0 + u * R;
-        e[u] = j < v.nbe ? tg::bel_elem(v.be[j]) : 0;
-        tg::elem_ids<EL, T>(a, e[u], in[u]);
+    for (int u = 0; u < UB; ++u) tg::elem_data<EL, T>(a, e[u], in[u]);
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int j = j0 + u * NT_;
+      if (j >= v.nbe) continue;
+      T K[NS];
+      if (!tg::p1_elem_sym<EL, T>(in[u], a.c, tab, K)) {
+        tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e[u]);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) K[q] = T(0);
       }
+      int q = 0;
 #pragma unroll
-      for (int u = 0; u < UB; ++u) tg::elem_data<EL, T>(a, e[u], in[u]);
+      for (int r = 0; r < NV; ++r)
 #pragma unroll
-      for (int u = 0; u < UB; ++u) {
-        const int j = j0 + u * R;
-        if (j >= v.nbe) continue;
-        T K[NS];
-        if (!tg::p1_elem_sym<EL, T>(in[u], a.c, ts, K)) {
-          tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e[u]);
-#pragma unroll
-          for (int q = 0; q < NS; ++q) K[q] = T(0);
+        for (int c = r; c < NV; ++c, ++q) {
+          Ke[(r * NV + c) * g.capE + j] = K[q];
+          if (c != r) Ke[(c * NV + r) * g.capE + j] = K[q];
         }
-#pragma unroll
-        for (int q = 0; q < NS; ++q) Ke[q * g.capE + j] = K[q];
-      }
     }
-    __syncthreads();
-    // Reduce: rows summed in increasing element order
+  }
+  __syncthreads();
+  // Reduce: rows summed in increasing element order
+  {
     const int i = v.r0 + (int)threadIdx.x;
     const int rbase = v.rp[v.r0];
     if (i < v.r1) {
       T* row = acc + (v.rp[i] - rbase);
-      const int len = v.rp[i + 1] - v.rp[i];
-      for (int q = 0; q < len; ++q) row[q] = T(0);
       const int je = v.ip[i + 1];
       for (int j = v.ip[i]; j < je; ++j) {
-        const tg::BlkRec r{v.rc[j], sh};
-        const int le = r.le(), la = r.a();
+        const tg::BlkRec<NV> r{v.rc[j]};
+        const T* kr = Ke + r.a() * NV * g.capE + r.le();
 #pragma unroll
-        for (int c = 0; c < NV; ++c) row[r.pos(c, g.pb)] += Ke[tg::sym_index<NV>(la, c) * g.capE + le];
+        for (int c = 0; c < NV; ++c) row[r.pos(c)] += kr[c * g.capE];
       }
     }
     __syncthreads();
     const int nz = v.rp[v.r1] - rbase;
     T* out = a.out + rbase;
-    for (int q = threadIdx.x; q < nz; q += R) out[q] = acc[q];
+    for (int q = threadIdx.x; q < nz; q += NT_) {
+      out[q] = acc[q];
+      acc[q] = T(0);
+    }
     __syncthreads();  // stage s and the work buffers are free again
   }
+  TG_BLK_PIPELINE_END
 }
 
 template <int D, typename T>
 size_t bilinear_blk_smem(const tg_pattern* p) {
-  constexpr int NV = D + 1, NS = NV * (NV + 1) / 2;
+  constexpr int NV = D + 1;
   const tg::BlkArgs g = tg::blk_args(p);
-  return tab_bytes<T>() + tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE) +
-         ((size_t)NS * g.capE + p->blk_max_nz) * sizeof(T);
+  return tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE, NV) + ((size_t)NV * NV * g.capE + p->blk_max_nz) * sizeof(T);
 }
 
 // P1 load vector over element-once row blocks: Map F_e (NV values) per
 // distinct element, Reduce F[i] = sum of the incidences' entries in
 // increasing element order (second line of Eq. (matlclquad)).
-template <int D, typename T>
+template <int D, typename T, int UB>
 __global__ void __launch_bounds__(BS) k_load_blk(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
                                                  const tg::BlkArgs g) {
-  constexpr int EL = D == 2 ? TG_P1_TRI : TG_P1_TET;
   constexpr int NV = D + 1, NQ = D == 2 ? 3 : 4;
-  constexpr int UB = sizeof(T) == 4 ? 4 : 2;
   extern __shared__ __align__(16) unsigned char smem[];
-  auto& ts = *reinterpret_cast<tg::RefTab<T>*>(smem);
+  const tg::RefTab<T>& ts = tab;
   tg::BlkPipe pipe;
-  T* Fe = reinterpret_cast<T*>(pipe.init(smem + tab_bytes<T>(), g));
-  copy_table(ts, tab);
-  const int R = blockDim.x;
-  const int64_t G = gridDim.x;
-  const int sh = NV * g.pb;
-  int64_t b = blockIdx.x;
-  int nJ0 = 0, nJ1 = 0, nE = 0;
-  if (threadIdx.x == 0 && b < g.nblocks) {
-    int J0, J1, ne;
-    tg::BlkPipe::peek(g, b, J0, J1, ne);
-    pipe.issue(g, 0, b, J0, J1, ne);
-    if (b + G < g.nblocks) tg::BlkPipe::peek(g, b + G, nJ0, nJ1, nE);
-  }
-  for (int k = 0; b < g.nblocks; ++k, b += G) {
-    const int s = k & 1;
-    const bool ahead = b + G < g.nblocks;
-    if (threadIdx.x == 0 && ahead) {
-      pipe.issue(g, s ^ 1, b + G, nJ0, nJ1, nE);
-      if (b + 2 * G < g.nblocks) tg::BlkPipe::peek(g, b + 2 * G, nJ0, nJ1, nE);
+  T* Fe = reinterpret_cast<T*>(pipe.init(smem, g));
+  __syncthreads();  // publishes the mbarrier initialisation
+  TG_BLK_PIPELINE_BEGIN(pipe, g, a.status)
+  for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * NT_) {
+    int e[UB];
+    int vid[UB][NV];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int j = j0 + u * NT_ < v.nbe ? j0 + u * NT_ : 0;
+      e[u] = tg::bel_elem(v.be[j]);
+#pragma unroll
+      for (int c = 0; c < NV; ++c) vid[u][c] = (int)v.be[(c + 1) * v.bs + j];
     }
-    if (!pipe.wait(s, k, ahead, a.status)) return;
-    const tg::BlkView v = pipe.view(s);
-    for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * R) {
-      int64_t e[UB];
-      int vid[UB][NV];
-      T x[UB][NV][D];
+    T x[UB][NV][D];
+    T fv[UB][NV > NQ ? NV : NQ];
 #pragma unroll
-      for (int u = 0; u < UB; ++u) {
-        const int j = j0 + u * R;
-        e[u] = j < v.nbe ? tg::bel_elem(v.be[j]) : 0;
+    for (int u = 0; u < UB; ++u) {
 #pragma unroll
-        for (int c = 0; c < NV; ++c) vid[u][c] = __ldg(a.cells + e[u] * NV + c);
+      for (int c = 0; c < NV; ++c) tg::load_x<D, T>(a.coords, vid[u][c], x[u][c]);
+      if (a.layout == TG_PER_NODE) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) fv[u][c] = __ldg(a.coef + vid[u][c]);
+      } else if (a.layout == TG_PER_QP) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) fv[u][q] = __ldg(a.coef + (int64_t)e[u] * NQ + q);
+      } else {
+        fv[u][0] = __ldg(a.coef);
       }
-      T fv[UB][NV > NQ ? NV : NQ];
+    }
 #pragma unroll
-      for (int u = 0; u < UB; ++u) {
+    for (int u = 0; u < UB; ++u) {
+      const int j = j0 + u * NT_;
+      if (j >= v.nbe) continue;
+      tg::Geom<D, T> gm;
+      if constexpr (D == 2) tg::tri_geom_x(x[u][0], x[u][1], x[u][2], gm);
+      else tg::tet_geom_x(x[u][0], x[u][1], x[u][2], x[u][3], gm);
+      const T adet = absv(gm.det);
+      const bool ok = adet > tg::det_tiny<T>();
+      if (!ok) tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e[u]);
 #pragma unroll
-        for (int c = 0; c < NV; ++c) tg::load_x<D, T>(a.coords, vid[u][c], x[u][c]);
+      for (int c = 0; c < NV; ++c) {
+        T val;
         if (a.layout == TG_PER_NODE) {
+          T s2 = T(0);
 #pragma unroll
-          for (int c = 0; c < NV; ++c) fv[u][c] = __ldg(a.coef + vid[u][c]);
+          for (int bb = 0; bb < NV; ++bb) s2 = fma(ts.M[c][bb], fv[u][bb], s2);
+          val = adet * s2;
         } else if (a.layout == TG_PER_QP) {
+          T s2 = T(0);
 #pragma unroll
-          for (int q = 0; q < NQ; ++q) fv[u][q] = __ldg(a.coef + e[u] * NQ + q);
+          for (int q = 0; q < NQ; ++q) s2 = fma(ts.w[q] * ts.phi[q][c], fv[u][q], s2);
+          val = adet * s2;
         } else {
-          fv[u][0] = __ldg(a.coef);
+          val = adet * ts.m1[c] * fv[u][0];
         }
-      }
-#pragma unroll
-      for (int u = 0; u < UB; ++u) {
-        const int j = j0 + u * R;
-        if (j >= v.nbe) continue;
-        tg::Geom<D, T> gm;
-        if constexpr (D == 2) tg::tri_geom_x(x[u][0], x[u][1], x[u][2], gm);
-        else tg::tet_geom_x(x[u][0], x[u][1], x[u][2], x[u][3], gm);
-        const T adet = absv(gm.det);
-        const bool ok = adet > tg::det_tiny<T>();
-        if (!ok) tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e[u]);
-#pragma unroll
-        for (int c = 0; c < NV; ++c) {
-          T val;
-          if (a.layout == TG_PER_NODE) {
-            T s2 = T(0);
-#pragma unroll
-            for (int bb = 0; bb < NV; ++bb) s2 = fma(ts.M[c][bb], fv[u][bb], s2);
-            val = adet * s2;
-          } else if (a.layout == TG_PER_QP) {
-            T s2 = T(0);
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) s2 = fma(ts.w[q] * ts.phi[q][c], fv[u][q], s2);
-            val = adet * s2;
-          } else {
-            val = adet * ts.m1[c] * fv[u][0];
-          }
-          Fe[c * g.capE + j] = ok ? val : T(0);
-        }
+        Fe[c * g.capE + j] = ok ? val : T(0);
       }
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  {
     const int i = v.r0 + (int)threadIdx.x;
     if (i < v.r1) {
       T f = T(0);
       const int je = v.ip[i + 1];
       for (int j = v.ip[i]; j < je; ++j) {
-        const tg::BlkRec r{v.rc[j], sh};
+        const tg::BlkRec<NV> r{v.rc[j]};
         f += Fe[r.a() * g.capE + r.le()];
       }
       a.out[i] = f;
     }
     __syncthreads();
   }
+  TG_BLK_PIPELINE_END
 }
 
 template <int D, typename T>
 size_t load_blk_smem(const tg_pattern* p) {
   const tg::BlkArgs g = tg::blk_args(p);
-  return tab_bytes<T>() + tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE) + (size_t)(D + 1) * g.capE * sizeof(T);
+  return tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE, D + 1) + (size_t)(D + 1) * g.capE * sizeof(T);
 }
 
-// Persistent launch of an element-once kernel: one CTA of blk_rows threads
-// per resident slot, at most one per row block.
+// Elements per thread of a Map round: enough for one round over the largest
+// block where registers allow (FP32), else a smaller batch over several
+// rounds.
+template <typename T>
+int blk_ub(const tg_pattern* p) {
+  const int nt = (p->blk_rows + 31) & ~31;
+  const int need = (p->blk_max_elems + nt - 1) / nt;
+  if (sizeof(T) == 8) return need <= 2 ? 2 : 3;
+  return need <= 4 ? 4 : need <= 5 ? 5 : 6;
+}
+
+// Threads per CTA of the element-once kernels: the rows per block rounded
+// up to whole warps.
+inline int blk_threads(const tg_pattern* p) { return (p->blk_rows + 31) & ~31; }
+
+// Persistent launch of an element-once kernel: one CTA per resident slot,
+// at most one per row block.
 template <typename K>
 tg_status launch_blk(K kern, size_t smem, const tg_pattern* p, dim3* grid_out) {
   tg_status st = tg::set_smem((const void*)kern, smem);
   if (st != TG_OK) return st;
   int per_sm = 0;
-  TG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, p->blk_rows, smem));
+  TG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, blk_threads(p), smem));
   *grid_out = dim3((unsigned)std::min<int64_t>(p->n_blk, (int64_t)std::max(per_sm, 1) * tg::sm_count()));
   return TG_OK;
 }
@@ -469,11 +482,22 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
     constexpr int D = El::dim;
     const size_t sb = bilinear_blk_smem<D, T>(p);
     if (use_blk<T>(p, sb)) {
-      auto kern = k_bilinear_blk<D, T>;
-      dim3 grid;
-      tg_status st = launch_blk(kern, sb, p, &grid);
+      const int ub = blk_ub<T>(p);
+      tg_status st = TG_OK;
+      auto go = [&](auto kern) {
+        dim3 grid;
+        if ((st = launch_blk(kern, sb, p, &grid)) != TG_OK) return;
+        kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::blk_args(p), p->blk_max_nz);
+      };
+      if constexpr (sizeof(T) == 8) {
+        if (ub == 2) go(k_bilinear_blk<D, T, 2>);
+        else go(k_bilinear_blk<D, T, 3>);
+      } else {
+        if (ub == 4) go(k_bilinear_blk<D, T, 4>);
+        else if (ub == 5) go(k_bilinear_blk<D, T, 5>);
+        else go(k_bilinear_blk<D, T, 6>);
+      }
       if (st != TG_OK) return st;
-      kern<<<grid, p->blk_rows, sb, s>>>(a, tab, tg::blk_args(p));
       TG_CK_LAUNCH("k_bilinear_blk");
       return TG_OK;
     }
@@ -524,11 +548,26 @@ tg_status load(const tg_pattern* p, const void* coords, const void* f, tg_layout
     const bool tri = el == TG_P1_TRI;
     const size_t sb = tri ? load_blk_smem<2, T>(p) : load_blk_smem<3, T>(p);
     if (use_blk<T>(p, sb)) {
-      dim3 grid;
-      tg_status st = tri ? launch_blk(k_load_blk<2, T>, sb, p, &grid) : launch_blk(k_load_blk<3, T>, sb, p, &grid);
+      const int ub = sizeof(T) == 8 ? 2 : blk_ub<T>(p) <= 4 ? 4 : 6;
+      tg_status st = TG_OK;
+      auto go = [&](auto kern) {
+        dim3 grid;
+        if ((st = launch_blk(kern, sb, p, &grid)) != TG_OK) return;
+        kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::blk_args(p));
+      };
+      if constexpr (sizeof(T) == 8) {
+        if (tri) go(k_load_blk<2, T, 2>);
+        else go(k_load_blk<3, T, 2>);
+      } else {
+        if (tri) {
+          if (ub == 4) go(k_load_blk<2, T, 4>);
+          else go(k_load_blk<2, T, 6>);
+        } else {
+          if (ub == 4) go(k_load_blk<3, T, 4>);
+          else go(k_load_blk<3, T, 6>);
+        }
+      }
       if (st != TG_OK) return st;
-      if (tri) k_load_blk<2, T><<<grid, p->blk_rows, sb, s>>>(a, tab, tg::blk_args(p));
-      else k_load_blk<3, T><<<grid, p->blk_rows, sb, s>>>(a, tab, tg::blk_args(p));
       TG_CK_LAUNCH("k_load_blk");
       return TG_OK;
     }

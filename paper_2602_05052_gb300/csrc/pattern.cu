@@ -219,13 +219,14 @@ __global__ void k_blk_stats(const int32_t* __restrict__ inc_ptr, const int32_t* 
   atomicMax(maxes + 1, row_ptr[r1] - row_ptr[r0]);
 }
 
-// One CTA per row block: sort the elements of the block's incidences,
-// keep the distinct ones (bel, with the owner bit), and pack every
-// incidence's record (brec).  P = power of two >= the block's incidences.
+// One CTA per row block: sort the elements of the block's incidences, keep
+// the distinct ones (written at uq_out[J0 ...], count in bel_cnt), and pack
+// every incidence's record (brec).  P = power of two >= the block's
+// incidences.
 __global__ void __launch_bounds__(256) k_blocks(const int32_t* __restrict__ cells, int nv,
                                                 const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc_e,
-                                                const uint32_t* __restrict__ inc_pos, int64_t N, int R, int pb, int P,
-                                                uint32_t* __restrict__ bel, int32_t* __restrict__ bel_cnt,
+                                                const uint32_t* __restrict__ inc_pos, int64_t N, int R, int P,
+                                                int32_t* __restrict__ uq_out, int32_t* __restrict__ bel_cnt,
                                                 uint32_t* __restrict__ brec, int* __restrict__ max_elems) {
   extern __shared__ int sk[];
   int* key = sk;      // [P]
@@ -261,13 +262,7 @@ __global__ void __launch_bounds__(256) k_blocks(const int32_t* __restrict__ cell
   }
   __syncthreads();
   const int nbe = s_nbe;
-  for (int k = threadIdx.x; k < nbe; k += blockDim.x) {
-    const int e = uq[k];
-    int vmin = INT32_MAX;
-    for (int a = 0; a < nv; ++a) vmin = min(vmin, cells[(int64_t)e * nv + a]);
-    bel[J0 + k] = (uint32_t)e | ((int64_t)vmin / R == b ? 0x80000000u : 0u);
-  }
-  const uint32_t pmask = (1u << pb) - 1u;
+  for (int k = threadIdx.x; k < nbe; k += blockDim.x) uq_out[J0 + k] = uq[k];
   for (int j = J0 + (int)threadIdx.x; j < J1; j += blockDim.x) {
     const int e = inc_e[j] >> 3, a = inc_e[j] & 7;
     int lo = 0, hi = nbe;
@@ -276,11 +271,44 @@ __global__ void __launch_bounds__(256) k_blocks(const int32_t* __restrict__ cell
       if (uq[mid] < e) lo = mid + 1;
       else hi = mid;
     }
-    const uint32_t w = inc_pos[j];  // 8-bit positions (nv <= 4)
+    const uint32_t w = inc_pos[j];  // 8-bit positions (nv <= 4), each < 16 here
     uint32_t r = 0;
-    for (int c = 0; c < nv; ++c) r |= ((w >> (8 * c)) & pmask) << (c * pb);
-    brec[j] = r | ((uint32_t)a << (nv * pb)) | ((uint32_t)lo << (nv * pb + 2));
+    for (int c = 0; c < nv; ++c) r |= ((w >> (8 * c)) & 15u) << (4 * c);
+    brec[j] = r | ((uint32_t)a << (4 * nv)) | ((uint32_t)lo << (4 * nv + 2));
   }
+}
+
+// Element lists of the blocks, structure of arrays per block: at word
+// boff[b], (nv + 1) rows of stride (bel_cnt[b] + 3) & ~3: the element
+// (bit 31: owner block, the block of its smallest vertex), then its
+// vertices.  One thread per (block, slot).
+__global__ void k_bel(const int32_t* __restrict__ cells, int nv, const int32_t* __restrict__ inc_ptr,
+                      const int32_t* __restrict__ uq, const int32_t* __restrict__ bel_cnt,
+                      const int64_t* __restrict__ boff, int64_t N, int R, int64_t nblk, uint32_t* __restrict__ bel) {
+  const int64_t b = blockIdx.y * (int64_t)gridDim.x + blockIdx.x;
+  if (b >= nblk) return;
+  const int nbe = bel_cnt[b], stride = (nbe + 3) & ~3;
+  const int J0 = inc_ptr[b * R];
+  uint32_t* out = bel + boff[b];
+  for (int k = threadIdx.x; k < stride; k += blockDim.x) {
+    if (k >= nbe) {
+      for (int a = 0; a <= nv; ++a) out[a * stride + k] = 0u;
+      continue;
+    }
+    const int e = uq[J0 + k];
+    int vmin = INT32_MAX;
+    for (int a = 0; a < nv; ++a) {
+      const int v = cells[(int64_t)e * nv + a];
+      out[(a + 1) * stride + k] = (uint32_t)v;
+      vmin = min(vmin, v);
+    }
+    out[k] = (uint32_t)e | ((int64_t)vmin / R == b ? 0x80000000u : 0u);
+  }
+}
+
+__global__ void k_bel_words(const int32_t* __restrict__ cnt, int64_t nblk, int rows, int32_t* __restrict__ words) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < nblk) words[b] = rows * ((cnt[b] + 3) & ~3);
 }
 
 // Per element: the position of every vertex's column in every vertex's row.
@@ -354,17 +382,19 @@ tg_status read_status(const tg_pattern* p, cudaStream_t s, const char* stage) {
 
 
 // Rows per block of the element-once kernels.
-int blk_rows_of(tg_element el) { return el == TG_P1_TRI ? 128 : 64; }
+// Triangles: 120 rows of a strip of a numbered mesh touch about 4 * 120 + 2
+// distinct elements, one Map round of 4 per thread on 128 threads.
+int blk_rows_of(tg_element el) { return el == TG_P1_TRI ? 120 : 64; }
 
 // Row blocks (step 5).  Leaves p->bel == NULL when the packed fields do not
-// fit (the generic kernels are used then).
+// fit (rows longer than 16, too many distinct elements per block): the
+// generic kernels are used then.
 tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
   const int nv = p->nv, R = blk_rows_of(p->el);
   const int64_t N = p->N, E = p->E, nvE = E * nv, nblk = (N + R - 1) / R;
-  int pb = 1;
-  while ((1 << pb) < p->max_row_len) ++pb;
+  const int pb = 4;
+  if (p->max_row_len > (1 << pb)) return TG_OK;
   const int le_bits = 32 - nv * pb - 2;
-  if (le_bits < 8) return TG_OK;
   Tmp tmp;
   int* maxes = nullptr;
   TG_CK(tmp.alloc(&maxes, 3));
@@ -376,30 +406,38 @@ tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
   TG_CK(cudaStreamSynchronize(s));
   int P = 1;
   while (P < h[0]) P <<= 1;
-  if (P > 4096) return TG_OK;  // blocks of very high degree: generic kernels
-  uint32_t *bel = nullptr, *brec = nullptr;
+  if (P > 4096) return TG_OK;  // blocks of very high degree
+  int32_t* uq = nullptr;
   int32_t* cnt = nullptr;
-  TG_CK(cudaMalloc(&bel, nvE * sizeof(uint32_t) + 16));
-  TG_CK(cudaMalloc(&brec, nvE * sizeof(uint32_t) + 16));
+  int64_t* boff = nullptr;
+  TG_CK(tmp.alloc(&uq, nvE));
+  TG_CK(tmp.alloc(&boff, nblk + 1));
   TG_CK(cudaMalloc(&cnt, nblk * sizeof(int32_t) + 16));
-  p->bel = bel;  // owned by the pattern from here on
-  p->brec = brec;
-  p->bel_cnt = cnt;
-  TG_CK(cudaMemsetAsync(bel, 0, nvE * sizeof(uint32_t) + 16, s));
-  TG_CK(cudaMemsetAsync(brec, 0, nvE * sizeof(uint32_t) + 16, s));
-  k_blocks<<<(unsigned)nblk, 256, 2 * P * sizeof(int), s>>>(p->cells, nv, p->inc_ptr, p->inc_e, p->inc_pos, N, R, pb,
-                                                             P, bel, cnt, brec, maxes + 2);
+  p->bel_cnt = cnt;  // owned by the pattern from here on
+  TG_CK(cudaMalloc(&p->brec, nvE * sizeof(uint32_t) + 16));
+  TG_CK(cudaMemsetAsync(p->brec, 0, nvE * sizeof(uint32_t) + 16, s));
+  k_blocks<<<(unsigned)nblk, 256, 2 * P * sizeof(int), s>>>(p->cells, nv, p->inc_ptr, p->inc_e, p->inc_pos, N, R, P,
+                                                             uq, cnt, p->brec, maxes + 2);
   TG_CK_LAUNCH("k_blocks");
   TG_CK(cudaMemcpyAsync(h + 2, maxes + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
   TG_CK(cudaStreamSynchronize(s));
-  if (h[2] > (1 << le_bits)) {  // local element indices do not fit: no blocks
-    cudaFree(bel);
-    cudaFree(brec);
-    cudaFree(cnt);
-    p->bel = p->brec = nullptr;
-    p->bel_cnt = nullptr;
-    return TG_OK;
-  }
+  if (h[2] > (1 << le_bits)) return TG_OK;  // local element indices do not fit
+  // region sizes (nv + 1) * padded count -> word offsets
+  int32_t* words = nullptr;
+  TG_CK(tmp.alloc(&words, nblk));
+  k_bel_words<<<tg::grid_for(nblk, kThreads), kThreads, 0, s>>>(cnt, nblk, nv + 1, words);
+  TG_CK_LAUNCH("k_bel_words");
+  tg_status st = scan_exclusive<int32_t>(words, boff, nblk, s);
+  if (st != TG_OK) return st;
+  int64_t total = 0;
+  TG_CK(cudaMemcpyAsync(&total, boff + nblk, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  TG_CK(cudaMalloc(&p->bel, total * sizeof(uint32_t) + 16));
+  TG_CK(cudaMalloc(&p->boff, (nblk + 1) * sizeof(int64_t) + 16));
+  TG_CK(cudaMemcpyAsync(p->boff, boff, (nblk + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  const unsigned gx = (unsigned)std::min<int64_t>(nblk, 65535), gy = (unsigned)((nblk + gx - 1) / gx);
+  k_bel<<<dim3(gx, gy), 128, 0, s>>>(p->cells, nv, p->inc_ptr, uq, cnt, p->boff, N, R, nblk, p->bel);
+  TG_CK_LAUNCH("k_bel");
   p->blk_rows = R;
   p->blk_pb = pb;
   p->n_blk = nblk;
@@ -412,6 +450,7 @@ tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
                                                               p->elem_pos);
     TG_CK_LAUNCH("k_elem_pos");
   }
+  TG_CK(cudaStreamSynchronize(s));  // tmp buffers are freed on return
   return TG_OK;
 }
 

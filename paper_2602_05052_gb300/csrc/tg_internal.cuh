@@ -41,19 +41,21 @@ struct tg_pattern {
   // built when the packed fields fit; bel == NULL otherwise).  Block b owns
   // the rows [b*blk_rows, (b+1)*blk_rows) and hence the incidences
   // [J0, J1) = [inc_ptr[b*blk_rows], inc_ptr[min((b+1)*blk_rows, N)]).
-  //   bel[J0 + k], k < bel_cnt[b]: the distinct elements incident to the
-  //     block's rows, ascending; bit 31 set in the one block that owns the
-  //     element (the block of its smallest vertex) for per-element outputs.
+  //   bel + boff[b]: the block's distinct elements (bel_cnt[b] of them,
+  //     ascending), structure of arrays with row stride (bel_cnt[b]+3) & ~3:
+  //     row 0 the element (bit 31 set in the one block that owns it, the
+  //     block of its smallest vertex), rows 1..nv its vertices.
   //   brec[j], j in [J0, J1), per incidence (row i, element e, local vertex
-  //     a), in the order of inc_e:  bits [b*pb, (b+1)*pb) the position of
+  //     a), in the order of inc_e:  4-bit fields [4b, 4b+4) the position of
   //     vertex b's column in row i (b < nv), then a (2 bits), then the local
-  //     index of e in bel (the rest).
+  //     index of e in the block's list (the rest).
   //   elem_pos[e] (64 bit): position of vertex b's column in vertex a's row
-  //     at bits [(a*nv + b)*pb, ...) (built when nv*nv*pb <= 64).
+  //     at bits [4(a*nv + b), ...).
   int blk_rows = 0, blk_pb = 0;
   int blk_max_elems = 0, blk_max_inc = 0, blk_max_nz = 0;  // per-block maxima
   int64_t n_blk = 0;
   uint32_t* bel = nullptr;
+  int64_t* boff = nullptr;
   int32_t* bel_cnt = nullptr;
   uint32_t* brec = nullptr;
   uint64_t* elem_pos = nullptr;
