@@ -23,7 +23,7 @@
 // order by a second kernel.  Everything is deterministic.
 #include <cstdint>
 
-#include "gather.cuh"
+#include "blocks.cuh"
 
 namespace {
 
@@ -290,6 +290,203 @@ __global__ void __launch_bounds__(BB) k_backward_gather(const BwdArgs<T> a, cons
   }
 }
 
+// P1 backward over element-once row blocks (blocks.cuh).  Each distinct
+// element of a block gathers its upstream weights W (through row_ptr and
+// the element's packed column positions, or from lam and U) and computes
+// the coordinate-gradient contributions of all its vertices into
+// Gx[NV*D][capE]; the block that owns the element also writes its
+// coefficient gradient and adds its dL/dc term.  Rows then sum their
+// incidences' contributions in increasing element order.  Per-CTA FP64
+// partials of the global sums are reduced by k_backward_final.
+template <int D, typename T, bool FUSED, int UB>
+__global__ void __launch_bounds__(BB) k_backward_blk(const BwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
+                                                     const tg::BlkArgs g, const uint64_t* __restrict__ elem_pos,
+                                                     const int32_t* __restrict__ row_ptr) {
+  constexpr int NV = D + 1, NQ = D == 2 ? 3 : 4;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[2][BB / 32];
+  tg::BlkPipe pipe;
+  T* Gx = reinterpret_cast<T*>(pipe.init(smem, g));
+  __syncthreads();  // publishes the mbarrier initialisation
+  double pc = 0.0, pk = 0.0;
+  TG_BLK_PIPELINE_BEGIN(pipe, g, a.status)
+  for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * NT_) {
+    int e[UB], vid[UB][NV];
+    bool own[UB];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const bool live = j0 + u * NT_ < v.nbe;
+      const int j = live ? j0 + u * NT_ : 0;
+      const uint32_t w0 = v.be[j];
+      e[u] = (int)tg::bel_elem(w0);
+      own[u] = live && tg::bel_owner(w0);
+#pragma unroll
+      for (int c = 0; c < NV; ++c) vid[u][c] = (int)v.be[(c + 1) * v.bs + j];
+    }
+    T x[UB][NV][D], kq[UB][NQ], W[UB][NV][NV];
+    uint64_t ep[UB];
+    int rpv[UB][NV];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+#pragma unroll
+      for (int c = 0; c < NV; ++c) tg::load_x<D, T>(a.coords, vid[u][c], x[u][c]);
+      if (a.layout == TG_PER_QP) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) kq[u][q] = __ldg(a.kappa + (int64_t)e[u] * NQ + q);
+      } else {
+        const T k = a.layout == TG_PER_ELEMENT ? __ldg(a.kappa + e[u]) : __ldg(a.kappa);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) kq[u][q] = k;
+      }
+      if constexpr (FUSED) {
+        T l[NV], uu[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          l[c] = __ldg(a.lam + vid[u][c]);
+          uu[c] = __ldg(a.U + vid[u][c]);
+        }
+#pragma unroll
+        for (int p = 0; p < NV; ++p)
+#pragma unroll
+          for (int q = 0; q < NV; ++q) W[u][p][q] = l[p] * uu[q];
+      } else {
+        ep[u] = __ldg(reinterpret_cast<const unsigned long long*>(elem_pos) + e[u]);
+#pragma unroll
+        for (int c = 0; c < NV; ++c) rpv[u][c] = __ldg(row_ptr + vid[u][c]);
+      }
+    }
+    if constexpr (!FUSED) {
+#pragma unroll
+      for (int u = 0; u < UB; ++u)
+#pragma unroll
+        for (int p = 0; p < NV; ++p)
+#pragma unroll
+          for (int q = 0; q < NV; ++q)
+            W[u][p][q] = __ldg(a.gvals + rpv[u][p] + (int)((ep[u] >> (4 * (p * NV + q))) & 15u));
+    }
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int j = j0 + u * NT_;
+      if (j >= v.nbe) continue;
+      tg::Geom<D, T> gm;
+      if constexpr (D == 2) tg::tri_geom_x(x[u][0], x[u][1], x[u][2], gm);
+      else tg::tet_geom_x(x[u][0], x[u][1], x[u][2], x[u][3], gm);
+      const T adet = tg::absv(gm.det);
+      T gx[NV][D];
+      if (!(adet > tg::det_tiny<T>())) {
+        tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e[u]);
+        if (own[u] && a.grad_kappa) {
+          if (a.layout == TG_PER_QP)
+            for (int q = 0; q < NQ; ++q) a.grad_kappa[(int64_t)e[u] * NQ + q] = T(0);
+          else if (a.layout == TG_PER_ELEMENT) a.grad_kappa[e[u]] = T(0);
+        }
+#pragma unroll
+        for (int c = 0; c < NV; ++c)
+#pragma unroll
+          for (int r = 0; r < D; ++r) gx[c][r] = T(0);
+      } else {
+        T Ws[NV][NV];
+#pragma unroll
+        for (int p = 0; p < NV; ++p)
+#pragma unroll
+          for (int q = 0; q < NV; ++q) Ws[p][q] = T(0.5) * (W[u][p][q] + W[u][q][p]);
+        T wm = T(0);
+#pragma unroll
+        for (int p = 0; p < NV; ++p)
+#pragma unroll
+          for (int q = 0; q < NV; ++q) wm += Ws[p][q] * tab.M[p][q];
+        const T inv = T(1) / adet;
+        const T sgn = gm.det > T(0) ? T(1) : T(-1);
+        // Q = N W_s N^T (d x d), trq = tr Q; gk[q] = w_q trq / |det J|
+        T y[NV][D];
+#pragma unroll
+        for (int b2 = 0; b2 < NV; ++b2)
+#pragma unroll
+          for (int r = 0; r < D; ++r) {
+            T sacc = T(0);
+#pragma unroll
+            for (int p = 0; p < NV; ++p) sacc += Ws[p][b2] * gm.n[p][r];
+            y[b2][r] = sacc;
+          }
+        T Q[D][D], trq = T(0);
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+          for (int s2 = 0; s2 < D; ++s2) {
+            T sacc = T(0);
+#pragma unroll
+            for (int b2 = 0; b2 < NV; ++b2) sacc += y[b2][r] * gm.n[b2][s2];
+            Q[r][s2] = sacc;
+          }
+#pragma unroll
+        for (int r = 0; r < D; ++r) trq += Q[r][r];
+        T S = T(0);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) S += tab.w[q] * kq[u][q];
+        if (own[u]) {
+          T gk[NQ];
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) gk[q] = tab.w[q] * trq * inv;
+          if (a.grad_kappa) {
+            if (a.layout == TG_PER_QP) {
+#pragma unroll
+              for (int q = 0; q < NQ; ++q) a.grad_kappa[(int64_t)e[u] * NQ + q] = gk[q];
+            } else {
+              T sg = T(0);
+#pragma unroll
+              for (int q = 0; q < NQ; ++q) sg += gk[q];
+              if (a.layout == TG_PER_ELEMENT) a.grad_kappa[e[u]] = sg;
+              else pk += (double)sg;
+            }
+          }
+          pc += (double)(adet * wm);
+        }
+        const T t = S * trq;
+        const T inv2 = inv * inv;
+        const T cw = a.c * wm;
+#pragma unroll
+        for (int c = 0; c < NV; ++c)
+#pragma unroll
+          for (int r = 0; r < D; ++r) {
+            T qn = T(0);
+#pragma unroll
+            for (int s2 = 0; s2 < D; ++s2) qn += (S * Q[r][s2]) * gm.n[c][s2];
+            gx[c][r] = sgn * (inv2 * (t * gm.n[c][r] - T(2) * qn) + cw * gm.n[c][r]);
+          }
+      }
+#pragma unroll
+      for (int c = 0; c < NV; ++c)
+#pragma unroll
+        for (int r = 0; r < D; ++r) Gx[(c * D + r) * g.capE + j] = gx[c][r];
+    }
+  }
+  __syncthreads();
+  if (a.grad_coords) {
+    const int i = v.r0 + (int)threadIdx.x;
+    if (i < v.r1) {
+      T gs[D];
+#pragma unroll
+      for (int r = 0; r < D; ++r) gs[r] = T(0);
+      const int je = v.ip[i + 1];
+      for (int j = v.ip[i]; j < je; ++j) {
+        const tg::BlkRec<NV> rr{v.rc[j]};
+        const T* gp = Gx + rr.a() * D * g.capE + rr.le();
+#pragma unroll
+        for (int r = 0; r < D; ++r) gs[r] += gp[r * g.capE];
+      }
+#pragma unroll
+      for (int r = 0; r < D; ++r) a.grad_coords[(int64_t)i * D + r] = gs[r];
+    }
+  }
+  __syncthreads();  // stage s and Gx are free again
+  TG_BLK_PIPELINE_END
+  block_sum2(pc, pk, red);
+  if (threadIdx.x == 0) {
+    a.partials[kSlots * blockIdx.x] = pc;
+    a.partials[kSlots * blockIdx.x + 1] = pk;
+  }
+}
+
 // Sum the per-CTA partials (kSlots doubles per CTA) in a fixed order and
 // write (or add to) the global gradients out[k], k < nslots (NULL = skip).
 struct FinalOut {
@@ -353,8 +550,60 @@ int bwd_rows(const tg_pattern* p, int nval, size_t* bytes) {
   return 0;
 }
 
+// Element-once launch (P1 with row blocks and packed positions); false in
+// *used when the pattern or the shared-memory budget does not allow it.
+template <int D, typename T>
+tg_status launch_blk(const tg_pattern* p, const BwdArgs<T>& a, bool fused, int* grid_out, bool* used,
+                     cudaStream_t s) {
+  *used = false;
+  if (!p->bel || !p->elem_pos) return TG_OK;
+  const tg::BlkArgs g = tg::blk_args(p);
+  const size_t smem = tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE, D + 1) +
+                      (size_t)(D + 1) * D * g.capE * sizeof(T);
+  if (smem > 113 * 1024) return TG_OK;
+  const int nt = (p->blk_rows + 31) & ~31;
+  if (nt > BB) return TG_OK;
+  const tg::RefTab<T>& tab = tg::table<T>(p->el);
+  constexpr int UB = sizeof(T) == 4 ? 2 : 1;
+  tg_status st = TG_OK;
+  auto go = [&](auto kern) {
+    if ((st = tg::set_smem((const void*)kern, smem)) != TG_OK) return;
+    int per_sm = 0;
+    cudaError_t ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem);
+    if (ce != cudaSuccess) {
+      st = tg::cuda_fail(ce, "cudaOccupancyMaxActiveBlocksPerMultiprocessor", __FILE__, __LINE__);
+      return;
+    }
+    const int64_t cap_ctas = (p->n_partials - 4) / kSlots;  // partial slots of the pattern
+    const int grid = (int)std::min<int64_t>({p->n_blk, (int64_t)std::max(per_sm, 1) * tg::sm_count(), cap_ctas});
+    kern<<<grid, nt, smem, s>>>(a, tab, g, p->elem_pos, p->row_ptr);
+    *grid_out = grid;
+  };
+  if (fused) go(k_backward_blk<D, T, true, UB>);
+  else go(k_backward_blk<D, T, false, UB>);
+  if (st != TG_OK) return st;
+  TG_CK_LAUNCH("k_backward_blk");
+  *used = true;
+  return TG_OK;
+}
+
 template <int EL, typename T>
 tg_status launch(const tg_pattern* p, const BwdArgs<T>& a, bool fused, T* grad_c, cudaStream_t s) {
+  if constexpr (EL == TG_P1_TRI || EL == TG_P1_TET) {
+    bool used = false;
+    int grid = 0;
+    tg_status st = launch_blk<tg::Elem<EL>::dim, T>(p, a, fused, &grid, &used, s);
+    if (st != TG_OK) return st;
+    if (used) {
+      T* gk_const = (a.layout == TG_CONSTANT) ? a.grad_kappa : nullptr;
+      if (grad_c || gk_const) {
+        FinalOut o{{grad_c, gk_const, nullptr, nullptr}, 2, 0};
+        k_backward_final<T><<<1, kFinal, 0, s>>>(a.partials, grid, o);
+        TG_CK_LAUNCH("k_backward_final");
+      }
+      return TG_OK;
+    }
+  }
   size_t smem = 0;
   const int R = bwd_rows<T>(p, tg::Elem<EL>::dim, &smem);
   if (R == 0) return TG_ERR_UNSUPPORTED;

@@ -196,3 +196,31 @@ __device__ __forceinline__ int64_t bel_elem(uint32_t w) { return (int64_t)(w & 0
 __device__ __forceinline__ bool bel_owner(uint32_t w) { return (w >> 31) != 0u; }
 
 }  // namespace tg
+
+// The persistent loop of an element-once kernel.  Inside, `v` is the
+// current block's view, R_ the rows per block and NT_ the CTA's threads;
+// thread 0 has already issued block b + G into the other stage and peeked
+// at b + 2G.  A timed-out wait makes the whole CTA return.
+#define TG_BLK_PIPELINE_BEGIN(pipe, g, status)                                          \
+  const int64_t G_ = gridDim.x;                                                         \
+  const int R_ = (g).R;                                                                 \
+  const int NT_ = blockDim.x;                                                           \
+  int64_t b_ = blockIdx.x;                                                              \
+  tg::BlkPipe::Peek nq_;                                                                \
+  if (threadIdx.x == 0 && b_ < (g).nblocks) {                                           \
+    tg::BlkPipe::Peek q0;                                                               \
+    tg::BlkPipe::peek(g, b_, R_, q0);                                                   \
+    (pipe).issue(g, 0, b_, q0);                                                         \
+    if (b_ + G_ < (g).nblocks) tg::BlkPipe::peek(g, b_ + G_, R_, nq_);                 \
+  }                                                                                     \
+  for (int k_ = 0; b_ < (g).nblocks; ++k_, b_ += G_) {                                  \
+    const int s_ = k_ & 1;                                                              \
+    const bool ahead_ = b_ + G_ < (g).nblocks;                                          \
+    if (threadIdx.x == 0 && ahead_) {                                                   \
+      (pipe).issue(g, s_ ^ 1, b_ + G_, nq_);                                            \
+      if (b_ + 2 * G_ < (g).nblocks) tg::BlkPipe::peek(g, b_ + 2 * G_, R_, nq_);        \
+    }                                                                                   \
+    if (!(pipe).wait(s_, k_, ahead_, status)) return;                                   \
+    const tg::BlkView v = (pipe).view(s_);
+
+#define TG_BLK_PIPELINE_END }

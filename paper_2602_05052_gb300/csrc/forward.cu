@@ -45,31 +45,6 @@ __global__ void __launch_bounds__(BS) k_bilinear_gather(const FwdArgs<T> a, cons
   tg::assemble_rows<EL, T>(a, ts, smem + tab_bytes<T>(), cap, r0, r1);
 }
 
-// Pipeline prologue and per-block step shared by the element-once kernels:
-// thread 0 issues block b + G into the other stage and peeks at b + 2G.
-#define TG_BLK_PIPELINE_BEGIN(pipe, g, status)                                          \
-  const int64_t G_ = gridDim.x;                                                         \
-  const int R_ = (g).R;                                                                 \
-  const int NT_ = blockDim.x;                                                           \
-  int64_t b_ = blockIdx.x;                                                              \
-  tg::BlkPipe::Peek nq_;                                                                \
-  if (threadIdx.x == 0 && b_ < (g).nblocks) {                                           \
-    tg::BlkPipe::Peek q0;                                                               \
-    tg::BlkPipe::peek(g, b_, R_, q0);                                                   \
-    (pipe).issue(g, 0, b_, q0);                                                         \
-    if (b_ + G_ < (g).nblocks) tg::BlkPipe::peek(g, b_ + G_, R_, nq_);                 \
-  }                                                                                     \
-  for (int k_ = 0; b_ < (g).nblocks; ++k_, b_ += G_) {                                  \
-    const int s_ = k_ & 1;                                                              \
-    const bool ahead_ = b_ + G_ < (g).nblocks;                                          \
-    if (threadIdx.x == 0 && ahead_) {                                                   \
-      (pipe).issue(g, s_ ^ 1, b_ + G_, nq_);                                            \
-      if (b_ + 2 * G_ < (g).nblocks) tg::BlkPipe::peek(g, b_ + 2 * G_, R_, nq_);        \
-    }                                                                                   \
-    if (!(pipe).wait(s_, k_, ahead_, status)) return;                                   \
-    const tg::BlkView v = (pipe).view(s_);
-
-#define TG_BLK_PIPELINE_END }
 
 // P1 forward over element-once row blocks (blocks.cuh):
 //   Map    - the local matrix K_e of every distinct element of the block into
