@@ -94,6 +94,8 @@ def alg_bytes(kind, E, N, nnz, s, nv=3, Q=3, d=2):
         return E * nv * 4 + N * d * s + E * Q * s + nnz * s + E * Q * s + N * d * s
     if kind == "elastic":
         return E * 4 * 4 + N * 3 * s + 2 * E * s + nnz * s
+    if kind == "elastic_bwd":  # + read grad_vals, write grad_lam, grad_mu, grad_coords
+        return E * 4 * 4 + N * 3 * s + 2 * E * s + nnz * s + 2 * E * s + N * 3 * s
     raise ValueError(kind)
 
 
@@ -463,8 +465,15 @@ def extras(tg, torch, dev, m, cfg, p, peak, flush):
         v = torch.empty(pe.nnz, dtype=dt, device=dev)
         ms_e = timed(torch, lambda: tg.tg_assemble_elasticity(pe, x, lam, mu, tg.PER_ELEMENT, v), flush)
         be = alg_bytes("elastic", me.n_elems, me.n_nodes, pe.nnz, s)
+        gv = d(np.random.default_rng(7).normal(size=pe.nnz))
+        gl, gm, gx = torch.empty_like(lam), torch.empty_like(mu), torch.empty_like(x)
+        ms_eb = timed(torch, lambda: tg.tg_assemble_elasticity_backward(pe, x, lam, mu, tg.PER_ELEMENT, grad_vals=gv,
+                                                                        grad_lam=gl, grad_mu=gm, grad_coords=gx), flush)
+        bb = alg_bytes("elastic_bwd", me.n_elems, me.n_nodes, pe.nnz, s)
         out[f"elasticity3d_{dtn}"] = {"ms": ms_e, "elements_per_s": me.n_elems / ms_e * 1e3,
-                                      "alg_GBps": be / ms_e / 1e6, "frac_hbm": be / ms_e / 1e6 / peak}
+                                      "alg_GBps": be / ms_e / 1e6, "frac_hbm": be / ms_e / 1e6 / peak,
+                                      "bwd_ms": ms_eb, "bwd_alg_GBps": bb / ms_eb / 1e6,
+                                      "bwd_frac_hbm": bb / ms_eb / 1e6 / peak}
     del pe
     # batched P2: 256 instances, one persistent launch vs 256 launches
     insts = mg.batched_p2(256, seed=4)

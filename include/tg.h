@@ -199,6 +199,22 @@ tg_status tg_assemble_backward(const tg_pattern* p, tg_dtype dtype, const void* 
                                const void* U, void* grad_kappa, void* grad_coords, void* grad_c,
                                tg_stream stream);
 
+/* Backward of the vector P1 elasticity assembly (tg_assemble_elasticity;
+ * the SM form with lambda div u div v + 2 mu eps(u):eps(v)).  For an upstream
+ * gradient W of the DoF-level values, either
+ *   grad_vals [nnz of the DoF-level CSR], or
+ *   lam_adj, U [3 N]  (W = lam_adj U^T, Eq. (adj)) when grad_vals is NULL,
+ * computes the gradients of L = sum_s W_s vals_s:
+ *   grad_lam, grad_mu  in the layout of lam and mu (PER_ELEMENT [E] or
+ *                      PER_QP [E][4]), or NULL;
+ *   grad_coords        [N][3], or NULL.
+ * All outputs are overwritten; sums run in a fixed order (deterministic).
+ * Needs node rows of at most 16 entries (TG_ERR_UNSUPPORTED otherwise). */
+tg_status tg_assemble_elasticity_backward(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* lam,
+                                          const void* mu, tg_layout layout, const void* grad_vals,
+                                          const void* lam_adj, const void* U, void* grad_lam, void* grad_mu,
+                                          void* grad_coords, tg_stream stream);
+
 /* Backward of the load vector (second line of Eq. (matlclquad)).  For an
  * upstream gradient grad_F [N * ncomp] of F, computes
  *   grad_f       same layout as f (PER_NODE, PER_QP or CONSTANT), or NULL;

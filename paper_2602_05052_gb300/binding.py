@@ -61,6 +61,7 @@ def lib():
         "tg_assemble_load": (i32, [vp, i32, vp, vp, i32, i32, vp, vp]),
         "tg_assemble_backward": (i32, [vp, i32, vp, vp, i32, dbl, vp, vp, vp, vp, vp, vp, vp]),
         "tg_assemble_load_backward": (i32, [vp, i32, vp, vp, i32, i32, vp, vp, vp, i32, vp]),
+        "tg_assemble_elasticity_backward": (i32, [vp, i32, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]),
         "tg_spmv": (i32, [vp, i32, vp, vp, vp, vp]),
         "tg_csr_outer": (i32, [vp, i32, vp, vp, dbl, vp, vp]),
         "tg_cg_solve": (i32, [vp, i32, vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl), vp]),
@@ -264,6 +265,22 @@ def tg_assemble_load_backward(p: Pattern, coords, f, layout: int, ncomp: int, gr
                                            _ptr(gx, dt, "grad_coords"), int(bool(accumulate)), _stream(stream)),
            "tg_assemble_load_backward")
     return gf, gx
+
+
+def tg_assemble_elasticity_backward(p: Pattern, coords, lam, mu, layout: int, grad_vals=None, lam_adj=None, U=None,
+                                    grad_lam=True, grad_mu=True, grad_coords=True, stream=None):
+    """Returns (grad_lam, grad_mu, grad_coords [N, 3]); pass False to skip one."""
+    dt = coords.dtype
+    gl = _out(grad_lam, lambda: torch.empty_like(lam))
+    gm = _out(grad_mu, lambda: torch.empty_like(mu))
+    gx = _out(grad_coords, lambda: torch.empty_like(coords))
+    _check(lib().tg_assemble_elasticity_backward(p.handle, _dt(coords), _ptr(coords, dt, "coords"), _ptr(lam, dt, "lam"),
+                                                 _ptr(mu, dt, "mu"), layout, _ptr(grad_vals, dt, "grad_vals"),
+                                                 _ptr(lam_adj, dt, "lam_adj"), _ptr(U, dt, "U"),
+                                                 _ptr(gl, dt, "grad_lam"), _ptr(gm, dt, "grad_mu"),
+                                                 _ptr(gx, dt, "grad_coords"), _stream(stream)),
+           "tg_assemble_elasticity_backward")
+    return gl, gm, gx
 
 
 def tg_csr_outer(p: Pattern, lam, U, alpha: float = 1.0, out=None, stream=None):

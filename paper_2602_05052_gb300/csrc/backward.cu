@@ -487,6 +487,220 @@ __global__ void __launch_bounds__(BB) k_backward_blk(const BwdArgs<T> a, const _
   }
 }
 
+// ------------------------------------------------------------ elasticity
+// Backward of the vector P1 elasticity assembly over element-once row
+// blocks.  With G = grad(phi) (G[:, a] = n_a / det J) and the upstream
+// weights W of one element (12 x 12, DoF (a, i) = 3a + i), the element's
+//   L_e = |det J| (sl T1 + sm (T2 + T3)),  sl = sum_q w_q lam_q, sm likewise,
+//   T1 = sum W_{ai,bj} G_ia G_jb,  T2 = sum W_{ai,bj} G_ja G_ib,
+//   T3 = sum_ab (sum_i W_{ai,bi}) G_a . G_b,
+// give dL/dlam_q = w_q |det J| T1, dL/dmu_q = w_q |det J| (T2 + T3), and,
+// from d|det J| = |det J| tr(J^{-1} dJ) and dG = -J^{-T} dJ^T G,
+//   dL/dx_c = P G[:, c],  P = L_e I - G Gam^T,  Gam = |det J| (sl dT1 + sm (dT2 + dT3))
+// for every vertex c (dT = derivatives of T with respect to G).  W is
+// streamed one 3 x 3 vertex-pair block at a time: the DoF-level CSR keeps
+// block (a, b) at 9 row_ptr[v_a] + 3 (i len_a + pos_ab) + j.
+template <typename T>
+struct ElBwdArgs {
+  const T* __restrict__ coords;
+  const T* __restrict__ lam;
+  const T* __restrict__ mu;
+  int layout;
+  const T* __restrict__ gvals;
+  const T* __restrict__ lam_adj;
+  const T* __restrict__ U;
+  T* __restrict__ grad_lam;
+  T* __restrict__ grad_mu;
+  T* __restrict__ grad_coords;
+  unsigned long long* status;
+};
+
+template <typename T, bool FUSED>
+__global__ void __launch_bounds__(BB) k_elastic_backward_blk(const ElBwdArgs<T> a,
+                                                             const __grid_constant__ tg::RefTab<T> tab,
+                                                             const tg::BlkArgs g, const uint64_t* __restrict__ elem_pos,
+                                                             const int32_t* __restrict__ row_ptr) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  tg::BlkPipe pipe;
+  T* Gx = reinterpret_cast<T*>(pipe.init(smem, g));  // [12][capE]
+  __syncthreads();
+  TG_BLK_PIPELINE_BEGIN(pipe, g, a.status)
+  for (int j = threadIdx.x; j < v.nbe; j += NT_) {
+    const uint32_t w0 = v.be[j];
+    const int e = (int)tg::bel_elem(w0);
+    const bool own = tg::bel_owner(w0);
+    int vid[4];
+    T x[4][3];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      vid[c] = (int)v.be[(c + 1) * v.bs + j];
+      tg::load_x<3, T>(a.coords, vid[c], x[c]);
+    }
+    T lq[4], mq[4];
+    if (a.layout == TG_PER_QP) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        lq[q] = __ldg(a.lam + 4ll * e + q);
+        mq[q] = __ldg(a.mu + 4ll * e + q);
+      }
+    } else {
+      const T l0 = __ldg(a.lam + e), m0 = __ldg(a.mu + e);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        lq[q] = l0;
+        mq[q] = m0;
+      }
+    }
+    tg::Geom<3, T> gm;
+    tg::tet_geom_x(x[0], x[1], x[2], x[3], gm);
+    const T adet = tg::absv(gm.det);
+    T gx[4][3];
+    if (!(adet > tg::det_tiny<T>())) {
+      tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
+      if (own) {
+        const int nc = a.layout == TG_PER_QP ? 4 : 1;
+        for (int q = 0; q < nc; ++q) {
+          if (a.grad_lam) a.grad_lam[(int64_t)e * nc + q] = T(0);
+          if (a.grad_mu) a.grad_mu[(int64_t)e * nc + q] = T(0);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) gx[c][r] = T(0);
+    } else {
+      const T id = T(1) / gm.det;
+      T G[3][4];  // G[r][c] = d phi_c / d x_r
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) G[r][c] = gm.n[c][r] * id;
+      T t1 = T(0), t2 = T(0), t3 = T(0);
+      T d1[3][4], d2[3][4], d3[3][4];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) d1[r][c] = d2[r][c] = d3[r][c] = T(0);
+      uint64_t ep = 0;
+      int rpa[4] = {0, 0, 0, 0}, lena[4] = {0, 0, 0, 0};
+      T la[4][3], ua[4][3];
+      if constexpr (FUSED) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            la[c][i] = __ldg(a.lam_adj + 3ll * vid[c] + i);
+            ua[c][i] = __ldg(a.U + 3ll * vid[c] + i);
+          }
+      } else {
+        ep = __ldg(reinterpret_cast<const unsigned long long*>(elem_pos) + e);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          rpa[c] = __ldg(row_ptr + vid[c]);
+          lena[c] = __ldg(row_ptr + vid[c] + 1) - rpa[c];
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          T w[3][3];
+          if constexpr (FUSED) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+              for (int jj = 0; jj < 3; ++jj) w[i][jj] = la[p][i] * ua[q][jj];
+          } else {
+            const int pos = (int)((ep >> (4 * (p * 4 + q))) & 15u);
+            const T* base = a.gvals + 9ll * rpa[p] + 3ll * pos;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+              for (int jj = 0; jj < 3; ++jj) w[i][jj] = __ldg(base + 3ll * i * lena[p] + jj);
+          }
+          // w G_q, w^T G_q, w G_p, w^T G_p
+          T wGq[3], wtGq[3], wGp[3], wtGp[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            wGq[i] = w[i][0] * G[0][q] + w[i][1] * G[1][q] + w[i][2] * G[2][q];
+            wtGq[i] = w[0][i] * G[0][q] + w[1][i] * G[1][q] + w[2][i] * G[2][q];
+            wGp[i] = w[i][0] * G[0][p] + w[i][1] * G[1][p] + w[i][2] * G[2][p];
+            wtGp[i] = w[0][i] * G[0][p] + w[1][i] * G[1][p] + w[2][i] * G[2][p];
+          }
+          const T cpq = w[0][0] + w[1][1] + w[2][2];
+          const T gpq = G[0][p] * G[0][q] + G[1][p] * G[1][q] + G[2][p] * G[2][q];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            t1 += G[i][p] * wGq[i];
+            t2 += G[i][q] * wGp[i];
+            d1[i][p] += wGq[i];
+            d1[i][q] += wtGp[i];
+            d2[i][p] += wtGq[i];
+            d2[i][q] += wGp[i];
+            d3[i][p] += cpq * G[i][q];
+            d3[i][q] += cpq * G[i][p];
+          }
+          t3 += cpq * gpq;
+        }
+      T sl = T(0), sm = T(0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        sl += tab.w[q] * lq[q];
+        sm += tab.w[q] * mq[q];
+      }
+      if (own) {
+        if (a.layout == TG_PER_QP) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (a.grad_lam) a.grad_lam[4ll * e + q] = tab.w[q] * adet * t1;
+            if (a.grad_mu) a.grad_mu[4ll * e + q] = tab.w[q] * adet * (t2 + t3);
+          }
+        } else {
+          if (a.grad_lam) a.grad_lam[e] = tab.wsum * adet * t1;
+          if (a.grad_mu) a.grad_mu[e] = tab.wsum * adet * (t2 + t3);
+        }
+      }
+      const T Le = adet * (sl * t1 + sm * (t2 + t3));
+      T P[3][3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int s2 = 0; s2 < 3; ++s2) {
+          T acc = T(0);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc += G[r][c] * (adet * (sl * d1[s2][c] + sm * (d2[s2][c] + d3[s2][c])));
+          P[r][s2] = (r == s2 ? Le : T(0)) - acc;
+        }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) gx[c][r] = P[r][0] * G[0][c] + P[r][1] * G[1][c] + P[r][2] * G[2][c];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) Gx[(c * 3 + r) * g.capE + j] = gx[c][r];
+  }
+  __syncthreads();
+  if (a.grad_coords) {
+    const int i = v.r0 + (int)threadIdx.x;
+    if (i < v.r1) {
+      T gs[3] = {T(0), T(0), T(0)};
+      const int je = v.ip[i + 1];
+      for (int j = v.ip[i]; j < je; ++j) {
+        const tg::BlkRec<4> rr{v.rc[j]};
+        const T* gp = Gx + rr.a() * 3 * g.capE + rr.le();
+#pragma unroll
+        for (int r = 0; r < 3; ++r) gs[r] += gp[r * g.capE];
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r) a.grad_coords[3ll * i + r] = gs[r];
+    }
+  }
+  __syncthreads();
+  TG_BLK_PIPELINE_END
+}
+
 // Sum the per-CTA partials (kSlots doubles per CTA) in a fixed order and
 // write (or add to) the global gradients out[k], k < nslots (NULL = skip).
 struct FinalOut {
@@ -561,8 +775,8 @@ tg_status launch_blk(const tg_pattern* p, const BwdArgs<T>& a, bool fused, int* 
   const size_t smem = tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE, D + 1) +
                       (size_t)(D + 1) * D * g.capE * sizeof(T);
   if (smem > 113 * 1024) return TG_OK;
-  const int nt = (p->blk_rows + 31) & ~31;
-  if (nt > BB) return TG_OK;
+  const int nt = BB;
+  if (p->blk_rows > BB) return TG_OK;
   const tg::RefTab<T>& tab = tg::table<T>(p->el);
   constexpr int UB = sizeof(T) == 4 ? 2 : 1;
   tg_status st = TG_OK;
@@ -925,4 +1139,65 @@ extern "C" tg_status tg_assemble_load_backward(const tg_pattern* p, tg_dtype dty
   return dtype == TG_F32 ? load_backward<float>(p, coords, f, f_layout, ncomp, grad_F, grad_f, grad_coords, accumulate, s)
                          : load_backward<double>(p, coords, f, f_layout, ncomp, grad_F, grad_f, grad_coords, accumulate,
                                                  s);
+}
+
+extern "C" tg_status tg_assemble_elasticity_backward(const tg_pattern* p, tg_dtype dtype, const void* coords,
+                                                     const void* lam, const void* mu, tg_layout layout,
+                                                     const void* grad_vals, const void* lam_adj, const void* U,
+                                                     void* grad_lam, void* grad_mu, void* grad_coords,
+                                                     tg_stream stream) {
+  if (!p || (dtype != TG_F32 && dtype != TG_F64) || p->el != TG_P1_TET_VEC3) return TG_ERR_INVALID_ARG;
+  if (!(layout == TG_PER_ELEMENT || layout == TG_PER_QP) || (p->N > 0 && !coords) || !lam || !mu)
+    return TG_ERR_INVALID_ARG;
+  if (!grad_vals && (!lam_adj || !U)) return TG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p->E == 0) {
+    if (grad_coords && p->N > 0) TG_CK(cudaMemsetAsync(grad_coords, 0, 3 * p->N * (dtype == TG_F32 ? 4 : 8), s));
+    return TG_OK;
+  }
+  if (!grad_lam && !grad_mu && !grad_coords) return TG_OK;
+  if (!p->bel || !p->elem_pos) {
+    tg::set_error("tg_assemble_elasticity_backward: the mesh has node rows longer than 16");
+    return TG_ERR_UNSUPPORTED;
+  }
+  const tg::BlkArgs g = tg::blk_args(p);
+  auto run = [&](auto zero) -> tg_status {
+    using T = decltype(zero);
+    ElBwdArgs<T> a;
+    a.coords = static_cast<const T*>(coords);
+    a.lam = static_cast<const T*>(lam);
+    a.mu = static_cast<const T*>(mu);
+    a.layout = layout;
+    a.gvals = static_cast<const T*>(grad_vals);
+    a.lam_adj = static_cast<const T*>(lam_adj);
+    a.U = static_cast<const T*>(U);
+    a.grad_lam = static_cast<T*>(grad_lam);
+    a.grad_mu = static_cast<T*>(grad_mu);
+    a.grad_coords = static_cast<T*>(grad_coords);
+    a.status = p->status;
+    const size_t smem = tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE, 4) + (size_t)12 * g.capE * sizeof(T);
+    if (smem > 200 * 1024 || p->blk_rows > BB) {
+      tg::set_error("tg_assemble_elasticity_backward: row blocks too large for shared memory");
+      return TG_ERR_UNSUPPORTED;
+    }
+    const tg::RefTab<T>& tab = tg::table<T>(TG_P1_TET);
+    tg_status st = TG_OK;
+    auto go = [&](auto kern) {
+      if ((st = tg::set_smem((const void*)kern, smem)) != TG_OK) return;
+      int per_sm = 0;
+      cudaError_t ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BB, smem);
+      if (ce != cudaSuccess) {
+        st = tg::cuda_fail(ce, "cudaOccupancyMaxActiveBlocksPerMultiprocessor", __FILE__, __LINE__);
+        return;
+      }
+      const int grid = (int)std::min<int64_t>(p->n_blk, (int64_t)std::max(per_sm, 1) * tg::sm_count());
+      kern<<<grid, BB, smem, s>>>(a, tab, g, p->elem_pos, p->row_ptr);
+    };
+    if (grad_vals) go(k_elastic_backward_blk<T, false>);
+    else go(k_elastic_backward_blk<T, true>);
+    if (st != TG_OK) return st;
+    TG_CK_LAUNCH("k_elastic_backward_blk");
+    return TG_OK;
+  };
+  return dtype == TG_F32 ? run(0.0f) : run(0.0);
 }

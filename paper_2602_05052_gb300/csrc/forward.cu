@@ -231,15 +231,13 @@ size_t load_blk_smem(const tg_pattern* p) {
 // rounds.
 template <typename T>
 int blk_ub(const tg_pattern* p) {
-  const int nt = (p->blk_rows + 31) & ~31;
-  const int need = (p->blk_max_elems + nt - 1) / nt;
+  const int need = (p->blk_max_elems + BS - 1) / BS;
   if (sizeof(T) == 8) return need <= 2 ? 2 : 3;
   return need <= 4 ? 4 : need <= 5 ? 5 : 6;
 }
 
-// Threads per CTA of the element-once kernels: the rows per block rounded
-// up to whole warps.
-inline int blk_threads(const tg_pattern* p) { return (p->blk_rows + 31) & ~31; }
+// Threads per CTA of the element-once kernels (rows per block <= BS).
+inline int blk_threads(const tg_pattern*) { return BS; }
 
 // Persistent launch of an element-once kernel: one CTA per resident slot,
 // at most one per row block.

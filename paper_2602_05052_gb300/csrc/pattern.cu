@@ -312,15 +312,20 @@ __global__ void k_bel_words(const int32_t* __restrict__ cnt, int64_t nblk, int r
 }
 
 // Per element: the position of every vertex's column in every vertex's row.
+// (Vector elasticity: the slot map is DoF-level, slot = 9 * row_ptr + 3 * pos.)
 __global__ void k_elem_pos(const int32_t* __restrict__ cells, const int32_t* __restrict__ elem_slot,
-                           const int32_t* __restrict__ row_ptr, int64_t E, int nv, int pb, uint64_t* __restrict__ out) {
+                           const int32_t* __restrict__ row_ptr, int64_t E, int nv, int pb, bool vec3,
+                           uint64_t* __restrict__ out) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   uint64_t w = 0;
   for (int a = 0; a < nv; ++a) {
     const int ra = row_ptr[cells[e * nv + a]];
-    for (int b = 0; b < nv; ++b)
-      w |= (uint64_t)(elem_slot[(e * nv + a) * nv + b] - ra) << ((a * nv + b) * pb);
+    for (int b = 0; b < nv; ++b) {
+      const int sl = elem_slot[(e * nv + a) * nv + b];
+      const int pos = vec3 ? (sl - 9 * ra) / 3 : sl - ra;
+      w |= (uint64_t)pos << ((a * nv + b) * pb);
+    }
   }
   out[e] = w;
 }
@@ -382,9 +387,11 @@ tg_status read_status(const tg_pattern* p, cudaStream_t s, const char* stage) {
 
 
 // Rows per block of the element-once kernels.
-// Triangles: 120 rows of a strip of a numbered mesh touch about 4 * 120 + 2
-// distinct elements, one Map round of 4 per thread on 128 threads.
-int blk_rows_of(tg_element el) { return el == TG_P1_TRI ? 120 : 64; }
+// Rows per block.  Triangles: 120 rows of a strip of a numbered mesh touch
+// about 4 * 120 + 2 distinct elements, one Map round of 4 per thread on 128
+// threads.  Tetrahedra touch about 18 distinct elements per row; vector
+// elasticity keeps 12 values per element in shared memory, hence 32 rows.
+int blk_rows_of(tg_element el) { return el == TG_P1_TRI ? 120 : el == TG_P1_TET ? 64 : 32; }
 
 // Row blocks (step 5).  Leaves p->bel == NULL when the packed fields do not
 // fit (rows longer than 16, too many distinct elements per block): the
@@ -447,7 +454,7 @@ tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
   if (nv * nv * pb <= 64) {
     TG_CK(cudaMalloc(&p->elem_pos, E * sizeof(uint64_t) + 16));
     k_elem_pos<<<tg::grid_for(E, kThreads), kThreads, 0, s>>>(p->cells, p->elem_slot, p->row_ptr, E, nv, pb,
-                                                              p->elem_pos);
+                                                              p->el == TG_P1_TET_VEC3, p->elem_pos);
     TG_CK_LAUNCH("k_elem_pos");
   }
   TG_CK(cudaStreamSynchronize(s));  // tmp buffers are freed on return
@@ -562,7 +569,7 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
 
 
   // 5. row blocks of the element-once P1 kernels
-  if ((el == TG_P1_TRI || el == TG_P1_TET) && E > 0) {
+  if ((el == TG_P1_TRI || el == TG_P1_TET || el == TG_P1_TET_VEC3) && E > 0) {
     if ((st = build_blocks(p, s)) != TG_OK) return st;
   }
 

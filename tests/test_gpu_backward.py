@@ -8,7 +8,7 @@ import torch
 
 import meshgen as mg
 import oracle as O
-from gpu_helpers import TOL, coef, dev, host_as, mesh_for, relfro
+from gpu_helpers import TOL, coef, dev, host_as, jittered_tet, mesh_for, relfro
 
 pytestmark = pytest.mark.gpu
 
@@ -176,3 +176,59 @@ def test_differentiable3d_small_matches_oracle_gradient(tg):
     L.backward()
     assert relfro(k.grad.cpu().numpy(), rk) <= 1e-9
     assert relfro(x.grad.cpu().numpy(), rx + rx2) <= 1e-9
+
+
+# ---------------------------------------------------------------- vector P1 elasticity
+@pytest.mark.parametrize("fused", [False, True])
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("layout", [mg.PER_ELEMENT, mg.PER_QP])
+def test_elasticity_backward_matches_oracle(tg, layout, dtype, fused):
+    m = jittered_tet(6)  # 343 nodes: 10 full row blocks of 32 and a ragged one
+    lam = coef(layout, m.n_elems, 4, seed=71, lo=0.5, hi=2.0)
+    mu = coef(layout, m.n_elems, 4, seed=72, lo=0.3, hi=1.0)
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TET_VEC3)
+    xs, ls, ms = host_as(m.coords, dtype), host_as(lam, dtype), host_as(mu, dtype)
+    g = np.random.default_rng(73)
+    args = (p, dev(m.coords, dtype), dev(lam, dtype), dev(mu, dtype), layout)
+    if fused:
+        la = host_as(g.normal(size=3 * m.n_nodes), dtype)
+        U = host_as(g.normal(size=3 * m.n_nodes), dtype)
+        kw = dict(lam_adj=dev(la, dtype), U=dev(U, dtype))
+        want = O.elasticity_backward(m.cells, xs, ls, ms, layout, lam_adj=la, U=U)
+    else:
+        ref = O.assemble_elasticity(m.cells, xs, ls, ms, layout)
+        gv = host_as(g.normal(size=ref.nnz), dtype)
+        kw = dict(grad_vals=dev(gv, dtype))
+        want = O.elasticity_backward(m.cells, xs, ls, ms, layout, grad_csr=O.CSR(ref.row_ptr, ref.col, gv))
+    got = tg.tg_assemble_elasticity_backward(*args, **kw)
+    for a, b in zip(got, want):
+        assert relfro(a.cpu().numpy().reshape(-1), np.asarray(b).reshape(-1)) <= GTOL[dtype]
+    again = tg.tg_assemble_elasticity_backward(*args, **kw)
+    assert all(torch.equal(a, b) for a, b in zip(got, again))
+    assert tg.tg_get_device_status(p) == (0, -1)
+
+
+def test_elasticity_backward_central_differences(tg):
+    """FP64: directional derivatives of L = <W, K(lam, mu, x)> against central
+    differences of the GPU forward."""
+    m = mesh_for(mg.P1_TET_VEC3)
+    g = np.random.default_rng(74)
+    lam = g.uniform(0.5, 2.0, m.n_elems)
+    mu = g.uniform(0.3, 1.0, m.n_elems)
+    dt = torch.float64
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TET_VEC3)
+    gv = dev(g.normal(size=p.nnz), dt)
+    x, l, u = dev(m.coords, dt), dev(lam, dt), dev(mu, dt)
+    gl, gm, gx = tg.tg_assemble_elasticity_backward(p, x, l, u, mg.PER_ELEMENT, grad_vals=gv)
+
+    def L(xx, ll, uu):
+        return float(torch.dot(tg.tg_assemble_elasticity(p, xx, ll, uu, mg.PER_ELEMENT), gv))
+
+    for k in range(3):
+        dx = dev(g.normal(size=m.coords.shape) * 0.05 * m.h, dt)
+        dl = dev(g.normal(size=m.n_elems), dt)
+        du = dev(g.normal(size=m.n_elems), dt)
+        eps = 1e-4
+        fd = (L(x + eps * dx, l + eps * dl, u + eps * du) - L(x - eps * dx, l - eps * dl, u - eps * du)) / (2 * eps)
+        an = float((gx * dx).sum() + (gl * dl).sum() + (gm * du).sum())
+        assert abs(fd - an) <= 1e-7 * max(1.0, abs(an)), (k, fd, an)
