@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(BB) k_backward_gather(const BwdArgs<T> a, cons
 // incidences' contributions in increasing element order.  Per-CTA FP64
 // partials of the global sums are reduced by k_backward_final.
 template <int D, typename T, bool FUSED, int UB>
-__global__ void __launch_bounds__(BB) k_backward_blk(const BwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
+__global__ void __launch_bounds__(BB, (D == 2 && sizeof(T) == 4) ? 6 : 2) k_backward_blk(const BwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
                                                      const tg::BlkArgs g, const uint64_t* __restrict__ elem_pos,
                                                      const int32_t* __restrict__ row_ptr) {
   constexpr int NV = D + 1, NQ = D == 2 ? 3 : 4;
@@ -310,6 +310,7 @@ __global__ void __launch_bounds__(BB) k_backward_blk(const BwdArgs<T> a, const _
   __syncthreads();  // publishes the mbarrier initialisation
   double pc = 0.0, pk = 0.0;
   TG_BLK_PIPELINE_BEGIN(pipe, g, a.status)
+  T bc = T(0), bk = T(0);  // this thread's terms of the block, added to pc, pk once per block
   for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * NT_) {
     int e[UB], vid[UB][NV];
     bool own[UB];
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(BB) k_backward_blk(const BwdArgs<T> a, const _
       e[u] = (int)tg::bel_elem(w0);
       own[u] = live && tg::bel_owner(w0);
 #pragma unroll
-      for (int c = 0; c < NV; ++c) vid[u][c] = (int)v.be[(c + 1) * v.bs + j];
+      for (int c = 0; c < NV; ++c) vid[u][c] = v.vtx(c, j);
     }
     T x[UB][NV][D], kq[UB][NQ], W[UB][NV][NV];
     uint64_t ep[UB];
@@ -385,30 +386,26 @@ __global__ void __launch_bounds__(BB) k_backward_blk(const BwdArgs<T> a, const _
 #pragma unroll
           for (int r = 0; r < D; ++r) gx[c][r] = T(0);
       } else {
-        T Ws[NV][NV];
-#pragma unroll
-        for (int p = 0; p < NV; ++p)
-#pragma unroll
-          for (int q = 0; q < NV; ++q) Ws[p][q] = T(0.5) * (W[u][p][q] + W[u][q][p]);
+        // <W, M> = <W_s, M> and tr(N W N^T) = tr(N W_s N^T): only the
+        // symmetric part of P = N W N^T needs W_s.
         T wm = T(0);
 #pragma unroll
         for (int p = 0; p < NV; ++p)
 #pragma unroll
-          for (int q = 0; q < NV; ++q) wm += Ws[p][q] * tab.M[p][q];
+          for (int q = 0; q < NV; ++q) wm += W[u][p][q] * tab.M[p][q];
         const T inv = T(1) / adet;
         const T sgn = gm.det > T(0) ? T(1) : T(-1);
-        // Q = N W_s N^T (d x d), trq = tr Q; gk[q] = w_q trq / |det J|
-        T y[NV][D];
+        T y[NV][D];  // y[b][r] = sum_p W[p][b] n[p][r]
 #pragma unroll
         for (int b2 = 0; b2 < NV; ++b2)
 #pragma unroll
           for (int r = 0; r < D; ++r) {
             T sacc = T(0);
 #pragma unroll
-            for (int p = 0; p < NV; ++p) sacc += Ws[p][b2] * gm.n[p][r];
+            for (int p = 0; p < NV; ++p) sacc += W[u][p][b2] * gm.n[p][r];
             y[b2][r] = sacc;
           }
-        T Q[D][D], trq = T(0);
+        T P[D][D];  // P[s][r] = sum_b n[b][s] y[b][r] = (N W^T-ish) contraction, P^T = N W N^T
 #pragma unroll
         for (int r = 0; r < D; ++r)
 #pragma unroll
@@ -416,10 +413,11 @@ __global__ void __launch_bounds__(BB) k_backward_blk(const BwdArgs<T> a, const _
             T sacc = T(0);
 #pragma unroll
             for (int b2 = 0; b2 < NV; ++b2) sacc += y[b2][r] * gm.n[b2][s2];
-            Q[r][s2] = sacc;
+            P[r][s2] = sacc;
           }
+        T trq = T(0);
 #pragma unroll
-        for (int r = 0; r < D; ++r) trq += Q[r][r];
+        for (int r = 0; r < D; ++r) trq += P[r][r];
         T S = T(0);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) S += tab.w[q] * kq[u][q];
@@ -436,22 +434,29 @@ __global__ void __launch_bounds__(BB) k_backward_blk(const BwdArgs<T> a, const _
 #pragma unroll
               for (int q = 0; q < NQ; ++q) sg += gk[q];
               if (a.layout == TG_PER_ELEMENT) a.grad_kappa[e[u]] = sg;
-              else pk += (double)sg;
+              else bk += sg;
             }
           }
-          pc += (double)(adet * wm);
+          bc += adet * wm;
         }
-        const T t = S * trq;
+        // dL/dx_c = A n_c with A = sgn [ (S tr Q / det^2 + c <W,M>) I - (2 S / det^2) Q ],
+        // Q = (P + P^T) / 2
         const T inv2 = inv * inv;
-        const T cw = a.c * wm;
+        const T d0 = sgn * (S * trq * inv2 + a.c * wm);
+        const T f2 = -sgn * S * inv2;  // times 2 Q = P + P^T
+        T A[D][D];
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+          for (int s2 = 0; s2 < D; ++s2) A[r][s2] = f2 * (P[r][s2] + P[s2][r]) + (r == s2 ? d0 : T(0));
 #pragma unroll
         for (int c = 0; c < NV; ++c)
 #pragma unroll
           for (int r = 0; r < D; ++r) {
-            T qn = T(0);
+            T sacc = T(0);
 #pragma unroll
-            for (int s2 = 0; s2 < D; ++s2) qn += (S * Q[r][s2]) * gm.n[c][s2];
-            gx[c][r] = sgn * (inv2 * (t * gm.n[c][r] - T(2) * qn) + cw * gm.n[c][r]);
+            for (int s2 = 0; s2 < D; ++s2) sacc += A[r][s2] * gm.n[c][s2];
+            gx[c][r] = sacc;
           }
       }
 #pragma unroll
@@ -460,6 +465,8 @@ __global__ void __launch_bounds__(BB) k_backward_blk(const BwdArgs<T> a, const _
         for (int r = 0; r < D; ++r) Gx[(c * D + r) * g.capE + j] = gx[c][r];
     }
   }
+  pc += (double)bc;
+  pk += (double)bk;
   __syncthreads();
   if (a.grad_coords) {
     const int i = v.r0 + (int)threadIdx.x;
@@ -533,7 +540,7 @@ __global__ void __launch_bounds__(BB) k_elastic_backward_blk(const ElBwdArgs<T> 
     T x[4][3];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      vid[c] = (int)v.be[(c + 1) * v.bs + j];
+      vid[c] = v.vtx(c, j);
       tg::load_x<3, T>(a.coords, vid[c], x[c]);
     }
     T lq[4], mq[4];
@@ -709,40 +716,32 @@ struct FinalOut {
   int accumulate;
 };
 
-constexpr int kFinal = 1024;
+constexpr int kFinal = 256;
 
+// One CTA; FP64 adds are slow on this part, so every thread adds only
+// partials that exist (in a fixed order), then a fixed shared-memory tree.
 template <typename T>
 __global__ void __launch_bounds__(kFinal) k_backward_final(const double* __restrict__ partials, int nblocks,
                                                            const FinalOut o) {
   __shared__ double s[kSlots][kFinal];
   double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
-  // 8 CTAs' partials per thread and trip, loads independent of each other
-  for (int b0 = threadIdx.x; b0 < nblocks; b0 += 8 * kFinal) {
-    double2 v[8][2];
+  const int ns = o.nslots;
+  for (int b = threadIdx.x; b < nblocks; b += kFinal)
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int b = b0 + u * kFinal;
-      const double2 z = make_double2(0.0, 0.0);
-      v[u][0] = b < nblocks ? reinterpret_cast<const double2*>(partials)[2 * b] : z;
-      v[u][1] = b < nblocks ? reinterpret_cast<const double2*>(partials)[2 * b + 1] : z;
-    }
+    for (int k = 0; k < kSlots; ++k)
+      if (k < ns) acc[k] += partials[kSlots * b + k];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      acc[0] += v[u][0].x;
-      acc[1] += v[u][0].y;
-      acc[2] += v[u][1].x;
-      acc[3] += v[u][1].y;
-    }
-  }
   for (int k = 0; k < kSlots; ++k) s[k][threadIdx.x] = acc[k];
   __syncthreads();
   for (int w = kFinal / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w)
-      for (int k = 0; k < kSlots; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + w];
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k)
+        if (k < ns) s[k][threadIdx.x] += s[k][threadIdx.x + w];
     __syncthreads();
   }
   if (threadIdx.x == 0)
-    for (int k = 0; k < o.nslots; ++k)
+    for (int k = 0; k < ns; ++k)
       if (o.out[k]) {
         T* d = static_cast<T*>(o.out[k]);
         *d = o.accumulate ? *d + (T)s[k][0] : (T)s[k][0];

@@ -30,11 +30,13 @@ struct BlkArgs {
   const int32_t* __restrict__ row_ptr;
   const uint32_t* __restrict__ bel;
   const int64_t* __restrict__ boff;
+  const int32_t* __restrict__ bvbase;
   const int32_t* __restrict__ bel_cnt;
   const uint32_t* __restrict__ brec;
   int64_t N;
   int64_t nblocks;
   int capE, capJ;  // stage capacities (multiples of 4): distinct elements, incidences
+  int capE16;      // capE rounded up to a multiple of 8 (16-bit vertex rows)
   int nv;          // vertices per element
   int R;           // rows per block (at most the CTA's threads)
 };
@@ -46,12 +48,14 @@ inline BlkArgs blk_args(const tg_pattern* p) {
   g.row_ptr = p->row_ptr;
   g.bel = p->bel;
   g.boff = p->boff;
+  g.bvbase = p->bvbase;
   g.bel_cnt = p->bel_cnt;
   g.brec = p->brec;
   g.N = p->N;
   g.nblocks = p->n_blk;
   g.capE = (p->blk_max_elems + 3) & ~3;
   g.capJ = (p->blk_max_inc + 3) & ~3;
+  g.capE16 = (p->blk_max_elems + 7) & ~7;
   g.nv = p->nv;
   g.R = p->blk_rows;
   return g;
@@ -59,17 +63,21 @@ inline BlkArgs blk_args(const tg_pattern* p) {
 
 // Shared-memory bytes of the two stages plus barriers and block metadata.
 __host__ __device__ inline size_t blk_stage_bytes(int R, int capJ, int capE, int nv) {
-  return 16 + 128 + 2 * ((size_t)(R + 8) * 8 + (size_t)(capJ + 8) * 4 + (size_t)(nv + 1) * capE * 4);
+  const size_t el_words = (size_t)capE + (size_t)nv * (((capE + 7) & ~7) / 2);
+  return 16 + 128 + 2 * ((size_t)(R + 8) * 8 + (size_t)(capJ + 8) * 4 + el_words * 4);
 }
 
 // Geometry of one row block as seen through its stage.
 struct BlkView {
   int r0, r1, J0, J1, nbe;
-  int bs;              // row stride of be
+  int bs16;            // row stride of vo
+  int vbase;           // smallest vertex id of the block's elements
   const int* ip;       // ip[i] = inc_ptr[i], i in [r0, r1]
   const int* rp;       // rp[i] = row_ptr[i]
   const uint32_t* rc;  // rc[j] = brec[j], j in [J0, J1)
-  const uint32_t* be;  // be[k] element k (with owner bit), be[(c+1)*bs + k] its vertex c; k < nbe
+  const uint32_t* be;  // be[k]: element k (with the owner bit), k < nbe
+  const uint16_t* vo;  // vo[c * bs16 + k]: vertex c of element k, minus vbase
+  __device__ int vtx(int c, int k) const { return vbase + (int)vo[c * bs16 + k]; }
 };
 
 class BlkPipe {
@@ -81,7 +89,7 @@ class BlkPipe {
     R_ = g.R;
     IPN_ = R_ + 8;
     RECN_ = g.capJ + 8;
-    ELN_ = (g.nv + 1) * g.capE;
+    ELN_ = g.capE + g.nv * (g.capE16 / 2);
     SW_ = 2 * IPN_ + RECN_ + ELN_;  // words per stage (a multiple of 4)
     bar_ = reinterpret_cast<uint64_t*>(p);
     meta_ = reinterpret_cast<int*>(p + 16);
@@ -98,7 +106,7 @@ class BlkPipe {
   // block blk (plain loads, issued early so that they are in flight while
   // the CTA works).
   struct Peek {
-    int J0, J1, nbe;
+    int J0, J1, nbe, vb;
     int64_t bo;
   };
   __device__ static void peek(const BlkArgs& g, int64_t blk, int R, Peek& q) {
@@ -106,18 +114,19 @@ class BlkPipe {
     q.J1 = __ldg(g.inc_ptr + (blk * R + R < g.N ? blk * R + R : g.N));
     q.nbe = __ldg(g.bel_cnt + blk);
     q.bo = __ldg(g.boff + blk);
+    q.vb = __ldg(g.bvbase + blk);
   }
 
   // Thread 0: copy block blk's streams into stage s.  The inc_ptr, row_ptr
   // and brec ranges are widened to whole 16-byte groups (the pattern arrays
   // carry 16 bytes of tail padding); the element list is a 16-byte aligned
-  // region of (nv + 1) * ((nbe + 3) & ~3) words.  The stage capacities hold
-  // all of them.
+  // region of (nbe + 3) & ~3 element words and nv rows of (nbe + 7) & ~7
+  // 16-bit vertex offsets.  The stage capacities hold all of them.
   __device__ void issue(const BlkArgs& g, int s, int64_t blk, const Peek& q) {
     const int r0 = (int)(blk * R_), r1 = (int)(blk * R_ + R_ < g.N ? blk * R_ + R_ : g.N);
     const int a0 = r0 & ~3, nip = (r1 + 1 - a0 + 3) & ~3;
     const int j0a = q.J0 & ~3, nrec = (q.J1 - j0a + 3) & ~3;
-    const int bs = (q.nbe + 3) & ~3, nel = (g.nv + 1) * bs;
+    const int nel = ((q.nbe + 3) & ~3) + g.nv * (((q.nbe + 7) & ~7) / 2);
     int* m = meta_ + 16 * s;
     m[0] = r0;
     m[1] = r1;
@@ -126,7 +135,7 @@ class BlkPipe {
     m[4] = a0;
     m[5] = j0a;
     m[6] = q.nbe;
-    m[7] = bs;
+    m[7] = q.vb;
     const uint32_t bytes = 4u * (2u * nip + (q.J1 > q.J0 ? nrec : 0) + nel);
     fence_proxy_async();
     mbar_arrive_expect_tx(&bar_[s], bytes);
@@ -160,11 +169,13 @@ class BlkPipe {
     v.J0 = m[2];
     v.J1 = m[3];
     v.nbe = m[6];
-    v.bs = m[7];
+    v.vbase = m[7];
+    v.bs16 = (v.nbe + 7) & ~7;
     v.ip = ip(s) - m[4];
     v.rp = rp(s) - m[4];
     v.rc = rec(s) - m[5];
     v.be = el(s);
+    v.vo = reinterpret_cast<const uint16_t*>(el(s) + ((v.nbe + 3) & ~3));
     return v;
   }
 

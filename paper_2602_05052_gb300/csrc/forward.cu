@@ -46,6 +46,15 @@ __global__ void __launch_bounds__(BS) k_bilinear_gather(const FwdArgs<T> a, cons
 }
 
 
+// Resident CTAs per SM the element-once kernels are compiled for (register
+// budget 64K / (128 * n)): 7 for FP32 triangles with up to 4 elements per
+// thread (70-72 registers, no spills), fewer where more live values need
+// more registers.
+template <int D, typename T, int UB>
+constexpr int blk_min_ctas() {
+  return D == 3 ? 2 : sizeof(T) == 8 ? 4 : UB <= 4 ? 7 : 5;
+}
+
 // P1 forward over element-once row blocks (blocks.cuh):
 //   Map    - the local matrix K_e of every distinct element of the block into
 //            Ke[NV*NV][capE] (UB elements per thread, one round when
@@ -55,7 +64,7 @@ __global__ void __launch_bounds__(BS) k_bilinear_gather(const FwdArgs<T> a, cons
 //            CSR values is then stored with coalesced writes (and acc is
 //            cleared for the next block on the way).
 template <int D, typename T, int UB>
-__global__ void __launch_bounds__(BS, D == 2 ? 4 : 2) k_bilinear_blk(const FwdArgs<T> a,
+__global__ void __launch_bounds__(BS, blk_min_ctas<D, T, UB>()) k_bilinear_blk(const FwdArgs<T> a,
                                                                       const __grid_constant__ tg::RefTab<T> tab,
                                                                       const tg::BlkArgs g, int cap_nz) {
   constexpr int EL = D == 2 ? TG_P1_TRI : TG_P1_TET;
@@ -76,7 +85,7 @@ __global__ void __launch_bounds__(BS, D == 2 ? 4 : 2) k_bilinear_blk(const FwdAr
       const int j = j0 + u * NT_ < v.nbe ? j0 + u * NT_ : 0;  // idle slots load element 0 of the list
       e[u] = (int)tg::bel_elem(v.be[j]);
 #pragma unroll
-      for (int c = 0; c < NV; ++c) in[u].v[c] = (int)v.be[(c + 1) * v.bs + j];
+      for (int c = 0; c < NV; ++c) in[u].v[c] = v.vtx(c, j);
     }
 #pragma unroll
     for (int u = 0; u < UB; ++u) tg::elem_data<EL, T>(a, e[u], in[u]);
@@ -111,8 +120,15 @@ __global__ void __launch_bounds__(BS, D == 2 ? 4 : 2) k_bilinear_blk(const FwdAr
       for (int j = v.ip[i]; j < je; ++j) {
         const tg::BlkRec<NV> r{v.rc[j]};
         const T* kr = Ke + r.a() * NV * g.capE + r.le();
+        // the NV columns of one incidence are distinct: all loads first
+        T cur[NV], add[NV];
 #pragma unroll
-        for (int c = 0; c < NV; ++c) row[r.pos(c)] += kr[c * g.capE];
+        for (int c = 0; c < NV; ++c) {
+          cur[c] = row[r.pos(c)];
+          add[c] = kr[c * g.capE];
+        }
+#pragma unroll
+        for (int c = 0; c < NV; ++c) row[r.pos(c)] = cur[c] + add[c];
       }
     }
     __syncthreads();
@@ -155,7 +171,7 @@ __global__ void __launch_bounds__(BS) k_load_blk(const FwdArgs<T> a, const __gri
       const int j = j0 + u * NT_ < v.nbe ? j0 + u * NT_ : 0;
       e[u] = tg::bel_elem(v.be[j]);
 #pragma unroll
-      for (int c = 0; c < NV; ++c) vid[u][c] = (int)v.be[(c + 1) * v.bs + j];
+      for (int c = 0; c < NV; ++c) vid[u][c] = v.vtx(c, j);
     }
     T x[UB][NV][D];
     T fv[UB][NV > NQ ? NV : NQ];

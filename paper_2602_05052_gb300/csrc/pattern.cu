@@ -278,37 +278,61 @@ __global__ void __launch_bounds__(256) k_blocks(const int32_t* __restrict__ cell
   }
 }
 
-// Element lists of the blocks, structure of arrays per block: at word
-// boff[b], (nv + 1) rows of stride (bel_cnt[b] + 3) & ~3: the element
-// (bit 31: owner block, the block of its smallest vertex), then its
-// vertices.  One thread per (block, slot).
-__global__ void k_bel(const int32_t* __restrict__ cells, int nv, const int32_t* __restrict__ inc_ptr,
-                      const int32_t* __restrict__ uq, const int32_t* __restrict__ bel_cnt,
-                      const int64_t* __restrict__ boff, int64_t N, int R, int64_t nblk, uint32_t* __restrict__ bel) {
+// Element lists of the blocks, at word boff[b] of bel, for a block with
+// nbe = bel_cnt[b] elements, bs = (nbe + 3) & ~3 and bs16 = (nbe + 7) & ~7:
+//   words [0, bs):  the elements, ascending (bit 31: owner block, the block
+//                   of the element's smallest vertex);
+//   then nv rows of bs16 16-bit offsets: vertex c of element k is
+//                   bvbase[b] + row c [k], bvbase[b] the smallest vertex id
+//                   of the block's elements.
+// One CTA per block; a block whose vertex ids span 2^16 or more sets *wide.
+__global__ void __launch_bounds__(128) k_bel(const int32_t* __restrict__ cells, int nv,
+                                             const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ uq,
+                                             const int32_t* __restrict__ bel_cnt, const int64_t* __restrict__ boff,
+                                             int64_t N, int R, int64_t nblk, uint32_t* __restrict__ bel,
+                                             int32_t* __restrict__ bvbase, int* __restrict__ wide) {
+  __shared__ int s_min, s_max;
   const int64_t b = blockIdx.y * (int64_t)gridDim.x + blockIdx.x;
   if (b >= nblk) return;
-  const int nbe = bel_cnt[b], stride = (nbe + 3) & ~3;
+  const int nbe = bel_cnt[b], bs = (nbe + 3) & ~3, bs16 = (nbe + 7) & ~7;
   const int J0 = inc_ptr[b * R];
+  if (threadIdx.x == 0) {
+    s_min = INT32_MAX;
+    s_max = INT32_MIN;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nbe; k += blockDim.x)
+    for (int a = 0; a < nv; ++a) {
+      const int v = cells[(int64_t)uq[J0 + k] * nv + a];
+      atomicMin(&s_min, v);
+      atomicMax(&s_max, v);
+    }
+  __syncthreads();
+  const int vb = nbe > 0 ? s_min : 0;
+  if (nbe > 0 && s_max - s_min > 65535) atomicOr(wide, 1);
+  if (threadIdx.x == 0) bvbase[b] = vb;
   uint32_t* out = bel + boff[b];
-  for (int k = threadIdx.x; k < stride; k += blockDim.x) {
+  uint16_t* o16 = reinterpret_cast<uint16_t*>(out + bs);
+  for (int k = threadIdx.x; k < bs16; k += blockDim.x) {
     if (k >= nbe) {
-      for (int a = 0; a <= nv; ++a) out[a * stride + k] = 0u;
+      if (k < bs) out[k] = 0u;
+      for (int a = 0; a < nv; ++a) o16[a * bs16 + k] = 0;
       continue;
     }
     const int e = uq[J0 + k];
     int vmin = INT32_MAX;
     for (int a = 0; a < nv; ++a) {
       const int v = cells[(int64_t)e * nv + a];
-      out[(a + 1) * stride + k] = (uint32_t)v;
+      o16[a * bs16 + k] = (uint16_t)(v - vb);
       vmin = min(vmin, v);
     }
     out[k] = (uint32_t)e | ((int64_t)vmin / R == b ? 0x80000000u : 0u);
   }
 }
 
-__global__ void k_bel_words(const int32_t* __restrict__ cnt, int64_t nblk, int rows, int32_t* __restrict__ words) {
+__global__ void k_bel_words(const int32_t* __restrict__ cnt, int64_t nblk, int nv, int32_t* __restrict__ words) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < nblk) words[b] = rows * ((cnt[b] + 3) & ~3);
+  if (b < nblk) words[b] = ((cnt[b] + 3) & ~3) + nv * (((cnt[b] + 7) & ~7) / 2);
 }
 
 // Per element: the position of every vertex's column in every vertex's row.
@@ -432,7 +456,7 @@ tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
   // region sizes (nv + 1) * padded count -> word offsets
   int32_t* words = nullptr;
   TG_CK(tmp.alloc(&words, nblk));
-  k_bel_words<<<tg::grid_for(nblk, kThreads), kThreads, 0, s>>>(cnt, nblk, nv + 1, words);
+  k_bel_words<<<tg::grid_for(nblk, kThreads), kThreads, 0, s>>>(cnt, nblk, nv, words);
   TG_CK_LAUNCH("k_bel_words");
   tg_status st = scan_exclusive<int32_t>(words, boff, nblk, s);
   if (st != TG_OK) return st;
@@ -441,10 +465,26 @@ tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
   TG_CK(cudaStreamSynchronize(s));
   TG_CK(cudaMalloc(&p->bel, total * sizeof(uint32_t) + 16));
   TG_CK(cudaMalloc(&p->boff, (nblk + 1) * sizeof(int64_t) + 16));
+  TG_CK(cudaMalloc(&p->bvbase, nblk * sizeof(int32_t) + 16));
   TG_CK(cudaMemcpyAsync(p->boff, boff, (nblk + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  int* wide = maxes;  // reuse: maxima already read back
+  TG_CK(cudaMemsetAsync(wide, 0, sizeof(int), s));
   const unsigned gx = (unsigned)std::min<int64_t>(nblk, 65535), gy = (unsigned)((nblk + gx - 1) / gx);
-  k_bel<<<dim3(gx, gy), 128, 0, s>>>(p->cells, nv, p->inc_ptr, uq, cnt, p->boff, N, R, nblk, p->bel);
+  k_bel<<<dim3(gx, gy), 128, 0, s>>>(p->cells, nv, p->inc_ptr, uq, cnt, p->boff, N, R, nblk, p->bel, p->bvbase,
+                                      wide);
   TG_CK_LAUNCH("k_bel");
+  int hw = 0;
+  TG_CK(cudaMemcpyAsync(&hw, wide, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  if (hw) {  // vertex ids of some block span 2^16 or more: no blocks
+    cudaFree(p->bel);
+    cudaFree(p->boff);
+    cudaFree(p->bvbase);
+    p->bel = nullptr;
+    p->boff = nullptr;
+    p->bvbase = nullptr;
+    return TG_OK;
+  }
   p->blk_rows = R;
   p->blk_pb = pb;
   p->n_blk = nblk;

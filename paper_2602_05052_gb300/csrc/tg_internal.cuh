@@ -41,10 +41,11 @@ struct tg_pattern {
   // built when the packed fields fit; bel == NULL otherwise).  Block b owns
   // the rows [b*blk_rows, (b+1)*blk_rows) and hence the incidences
   // [J0, J1) = [inc_ptr[b*blk_rows], inc_ptr[min((b+1)*blk_rows, N)]).
-  //   bel + boff[b]: the block's distinct elements (bel_cnt[b] of them,
-  //     ascending), structure of arrays with row stride (bel_cnt[b]+3) & ~3:
-  //     row 0 the element (bit 31 set in the one block that owns it, the
-  //     block of its smallest vertex), rows 1..nv its vertices.
+  //   bel + boff[b]: the block's distinct elements (nbe = bel_cnt[b] of
+  //     them, ascending): (nbe + 3) & ~3 words of element ids (bit 31 set in
+  //     the one block that owns the element, the block of its smallest
+  //     vertex), then nv rows of (nbe + 7) & ~7 16-bit vertex offsets from
+  //     bvbase[b] (built only when every block's vertex ids span < 2^16).
   //   brec[j], j in [J0, J1), per incidence (row i, element e, local vertex
   //     a), in the order of inc_e:  4-bit fields [4b, 4b+4) the position of
   //     vertex b's column in row i (b < nv), then a (2 bits), then the local
@@ -56,6 +57,7 @@ struct tg_pattern {
   int64_t n_blk = 0;
   uint32_t* bel = nullptr;
   int64_t* boff = nullptr;
+  int32_t* bvbase = nullptr;
   int32_t* bel_cnt = nullptr;
   uint32_t* brec = nullptr;
   uint64_t* elem_pos = nullptr;
