@@ -3,9 +3,9 @@
 Step = one pass of the hot path over the 2D diffusion workload (P1
 triangles, 1024 x 1024 jittered grid, Hilbert element order, lognormal kappa
 at 3 points per element, c = 1, f ~ U(-1, 1) per node; 2,097,152 elements),
-FP32: forward stiffness values (fused Map + deterministic Reduce), load
-vector, and the backward assembly for an upstream gradient of the values
-(grad kappa, grad coords, grad c).  Inputs live in HBM before timing; L2 is
+FP32: the linear system in one pass (stiffness CSR values and load vector,
+fused Map + deterministic Reduce), and the backward assembly for an upstream
+gradient of the values (grad kappa, grad coords, grad c).  Inputs live in HBM before timing; L2 is
 flushed between steps (outside the per-step CUDA events).
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
@@ -88,6 +88,8 @@ def alg_bytes(kind, E, N, nnz, s, nv=3, Q=3, d=2):
     """Compulsory bytes: read cells, coords and coefficients once, write outputs once."""
     if kind == "fwd":
         return E * nv * 4 + N * d * s + E * Q * s + nnz * s
+    if kind == "system":  # forward and load together: cells and coords read once
+        return E * nv * 4 + N * d * s + E * Q * s + N * s + nnz * s + N * s
     if kind == "load":
         return E * nv * 4 + N * d * s + N * s + N * s
     if kind == "bwd":
@@ -110,9 +112,10 @@ def load_peaks():
 
 # translation units and headers each timed kernel is built from
 KERNEL_SOURCES = {
+    "system": ["forward.cu", "gather.cuh", "elements.cuh", "blocks.cuh", "async.cuh", "tg_internal.cuh"],
     "fwd": ["forward.cu", "gather.cuh", "elements.cuh", "async.cuh", "tg_internal.cuh"],
     "load": ["forward.cu", "gather.cuh", "elements.cuh", "async.cuh", "tg_internal.cuh"],
-    "bwd": ["backward.cu", "gather.cuh", "elements.cuh", "async.cuh", "tg_internal.cuh"],
+    "bwd": ["backward.cu", "gather.cuh", "elements.cuh", "blocks.cuh", "async.cuh", "tg_internal.cuh"],
 }
 
 
@@ -292,23 +295,21 @@ def main():
     def step(ev=None):
         if ev:
             ev[0].record()
-        tg.tg_assemble_bilinear(p, coords, kappa, tg.PER_QP, c, vals)
+        # the linear system (K, F) in one pass: fused Map + Reduce of both
+        tg.tg_assemble_system(p, coords, kappa, tg.PER_QP, c, f, tg.PER_NODE, vals=vals, F=F)
         if ev:
             ev[1].record()
-        tg.tg_assemble_load(p, coords, f, tg.PER_NODE, 1, F)
-        if ev:
-            ev[2].record()
         tg.tg_assemble_backward(p, coords, kappa, tg.PER_QP, c, grad_vals=gvals, grad_kappa=gk, grad_coords=gx,
                                 grad_c=gc)
         if ev:
-            ev[3].record()
+            ev[2].record()
 
-    launches_per_step = 4  # forward gather, load gather, backward gather, backward final sum
+    launches_per_step = 3  # system (K and F), backward, backward final sum
     for _ in range(max(args.warmup, 3)):
         flush()
         step()
     torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     with Clocks(local) as clk:
         barrier()
         torch.cuda.synchronize()
@@ -320,10 +321,9 @@ def main():
         barrier()
         wall = time.perf_counter() - w0
     clocks = clk.summary()
-    t_fwd = [e[0].elapsed_time(e[1]) for e in evs]
-    t_load = [e[1].elapsed_time(e[2]) for e in evs]
-    t_bwd = [e[2].elapsed_time(e[3]) for e in evs]
-    t_step = [a + b + c_ for a, b, c_ in zip(t_fwd, t_load, t_bwd)]
+    t_sys = [e[0].elapsed_time(e[1]) for e in evs]
+    t_bwd = [e[1].elapsed_time(e[2]) for e in evs]
+    t_step = [a + b for a, b in zip(t_sys, t_bwd)]
     ms = max_over_ranks(sum(t_step) / args.steps)
     value = replica_throughput(E, world, ms)
     st, bad = tg.tg_get_device_status(p)
@@ -331,12 +331,10 @@ def main():
         raise RuntimeError(f"device status {st} at element {bad}")
 
     peak, peak_src = load_peaks()
-    kern = {"fwd": (statistics.mean(t_fwd), alg_bytes("fwd", E, N, nnz, s)),
-            "load": (statistics.mean(t_load), alg_bytes("load", E, N, nnz, s)),
+    kern = {"system": (statistics.mean(t_sys), alg_bytes("system", E, N, nnz, s)),
             "bwd": (statistics.mean(t_bwd), alg_bytes("bwd", E, N, nnz, s))}
     dom = max(kern, key=lambda k: kern[k][0])
-    names = {"fwd": "k_bilinear_p1<2,float>", "load": "k_load_gather<P1_TRI,float,PER_NODE>",
-             "bwd": "k_backward_gather<P1_TRI,float,gvals> + k_backward_final"}
+    names = {"system": "k_bilinear_blk<2,float,4,load>", "bwd": "k_backward_blk<2,float,gvals,2> + k_backward_final"}
     ach = kern[dom][1] / (kern[dom][0] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "traffic": ncu_traffic(dom), "peak_source": f"{peak_src} (copy, burst)",
@@ -446,13 +444,16 @@ def extras(tg, torch, dev, m, cfg, p, peak, flush):
         ms_a = timed(torch, lambda: tg.tg_assemble_bilinear_atomic(p, x, k, tg.PER_QP, 1.0, v), flush)
         ms_b = timed(torch, lambda: tg.tg_assemble_backward(p, x, k, tg.PER_QP, 1.0, grad_vals=gv), flush)
         ms_l = timed(torch, lambda: tg.tg_assemble_load(p, x, f, tg.PER_NODE), flush)
+        F_ = torch.empty(N, dtype=dt, device=dev)
+        ms_s = timed(torch, lambda: tg.tg_assemble_system(p, x, k, tg.PER_QP, 1.0, f, tg.PER_NODE, vals=v, F=F_), flush)
         bf, bb = alg_bytes("fwd", E, N, nnz, s), alg_bytes("bwd", E, N, nnz, s)
         out[f"diffusion2d_{dtn}"] = {
             "fwd_ms": ms_f, "fwd_elements_per_s": E / ms_f * 1e3, "fwd_alg_GBps": bf / ms_f / 1e6,
             "fwd_frac_hbm": bf / ms_f / 1e6 / peak,
             "atomic_fwd_ms": ms_a, "gather_vs_atomic_speedup": ms_a / ms_f,
             "bwd_ms": ms_b, "bwd_alg_GBps": bb / ms_b / 1e6, "bwd_frac_hbm": bb / ms_b / 1e6 / peak,
-            "fwd_plus_bwd_elements_per_s": E / (ms_f + ms_b) * 1e3, "load_ms": ms_l}
+            "fwd_plus_bwd_elements_per_s": E / (ms_f + ms_b) * 1e3, "load_ms": ms_l,
+            "system_ms": ms_s, "system_alg_GBps": alg_bytes("system", E, N, nnz, s) / ms_s / 1e6}
     out["fp64_fma_peak_tflops"] = tg.tg_diag_fma_rate(torch.float64) / 1e12
     out["fp32_fma_peak_tflops"] = tg.tg_diag_fma_rate(torch.float32) / 1e12
     # elasticity 64^3

@@ -174,6 +174,17 @@ tg_status tg_assemble_bilinear_atomic(const tg_pattern* p, tg_dtype dtype, const
 tg_status tg_assemble_elasticity(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* lam,
                                  const void* mu, tg_layout layout, void* vals_out, tg_stream stream);
 
+/* The linear system of one scalar problem in one pass: the CSR values of
+ * tg_assemble_bilinear and the load vector of tg_assemble_load (ncomp = 1)
+ * together, as the Map of Algorithm 1 computes an element's local matrix and
+ * load vector together.  Same arguments as those two calls, same outputs,
+ * bitwise; on P1 meshes with row blocks one kernel shares the geometry and
+ * the streams of both, otherwise the two assemblies run one after the other.
+ * vals_out [nnz], F_out [N]. */
+tg_status tg_assemble_system(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
+                             tg_layout kappa_layout, double c, const void* f, tg_layout f_layout, void* vals_out,
+                             void* F_out, tg_stream stream);
+
 /* Load vector (second line of Eq. (matlclquad)):
  *   F[g(a) * ncomp + k] = sum_e sum_q w_q |det J_e| f_k(x_q) phi_a(x_q).
  *   f layouts: PER_NODE [N][ncomp] (f is its finite-element interpolant),

@@ -59,6 +59,7 @@ def lib():
         "tg_assemble_bilinear_atomic": (i32, [vp, i32, vp, vp, i32, dbl, vp, vp]),
         "tg_assemble_elasticity": (i32, [vp, i32, vp, vp, vp, i32, vp, vp]),
         "tg_assemble_load": (i32, [vp, i32, vp, vp, i32, i32, vp, vp]),
+        "tg_assemble_system": (i32, [vp, i32, vp, vp, i32, dbl, vp, i32, vp, vp, vp]),
         "tg_assemble_backward": (i32, [vp, i32, vp, vp, i32, dbl, vp, vp, vp, vp, vp, vp, vp]),
         "tg_assemble_load_backward": (i32, [vp, i32, vp, vp, i32, i32, vp, vp, vp, i32, vp]),
         "tg_assemble_elasticity_backward": (i32, [vp, i32, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]),
@@ -237,6 +238,18 @@ def tg_assemble_load(p: Pattern, coords, f, layout: int, ncomp: int = 1, F_out=N
                                   _ptr(f, coords.dtype, "f"), layout, int(ncomp), _ptr(F_out, coords.dtype, "F_out"),
                                   _stream(stream)), "tg_assemble_load")
     return F_out
+
+
+def tg_assemble_system(p: Pattern, coords, kappa, kappa_layout: int, c: float, f, f_layout: int, vals=True, F=True,
+                       stream=None):
+    """Returns (vals [nnz], F [N]): the bilinear values and the load vector in one call (pass tensors to fill)."""
+    dt = coords.dtype
+    vals = _out(vals, lambda: torch.empty(p.nnz, dtype=dt, device=coords.device))
+    F = _out(F, lambda: torch.empty(p.n_nodes, dtype=dt, device=coords.device))
+    _check(lib().tg_assemble_system(p.handle, _dt(coords), _ptr(coords, dt, "coords"), _ptr(kappa, dt, "kappa"),
+                                    kappa_layout, float(c), _ptr(f, dt, "f"), f_layout, _ptr(vals, dt, "vals"),
+                                    _ptr(F, dt, "F"), _stream(stream)), "tg_assemble_system")
+    return vals, F
 
 
 def tg_assemble_backward(p: Pattern, coords, kappa, layout: int, c: float = 0.0, grad_vals=None, lam=None, U=None,

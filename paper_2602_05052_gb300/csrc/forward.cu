@@ -63,16 +63,18 @@ constexpr int blk_min_ctas() {
 //            K_e into its CSR-local slice of acc; the block's slice of the
 //            CSR values is then stored with coalesced writes (and acc is
 //            cleared for the next block on the way).
-template <int D, typename T, int UB>
-__global__ void __launch_bounds__(BS, blk_min_ctas<D, T, UB>()) k_bilinear_blk(const FwdArgs<T> a,
-                                                                      const __grid_constant__ tg::RefTab<T> tab,
-                                                                      const tg::BlkArgs g, int cap_nz) {
+//   LOAD   - also the load vector F (a.f, a.f_layout -> a.F), entry for entry
+//            the arithmetic of k_load_blk: the system (K, F) in one pass.
+template <int D, typename T, int UB, bool LOAD>
+__global__ void __launch_bounds__(BS, blk_min_ctas<D, T, UB>() - (LOAD ? 1 : 0)) k_bilinear_blk(
+    const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab, const tg::BlkArgs g, int cap_nz) {
   constexpr int EL = D == 2 ? TG_P1_TRI : TG_P1_TET;
   constexpr int NV = D + 1, NS = NV * (NV + 1) / 2;
   extern __shared__ __align__(16) unsigned char smem[];
   tg::BlkPipe pipe;
   T* Ke = reinterpret_cast<T*>(pipe.init(smem, g));
-  T* acc = Ke + (size_t)NV * NV * g.capE;
+  T* Fe = Ke + (size_t)NV * NV * g.capE;
+  T* acc = Fe + (LOAD ? (size_t)NV * g.capE : 0);
   for (int q = threadIdx.x; q < cap_nz; q += blockDim.x) acc[q] = T(0);
   __syncthreads();  // publishes the mbarrier initialisation and the cleared acc
   TG_BLK_PIPELINE_BEGIN(pipe, g, a.status)
@@ -89,15 +91,26 @@ __global__ void __launch_bounds__(BS, blk_min_ctas<D, T, UB>()) k_bilinear_blk(c
     }
 #pragma unroll
     for (int u = 0; u < UB; ++u) tg::elem_data<EL, T>(a, e[u], in[u]);
+    T fv[LOAD ? UB : 1][NV];
+    if constexpr (LOAD) {
+#pragma unroll
+      for (int u = 0; u < UB; ++u) tg::p1_load_f<NV, T>(a.f, a.f_layout, e[u], in[u].v, fv[u]);
+    }
 #pragma unroll
     for (int u = 0; u < UB; ++u) {
       const int j = j0 + u * NT_;
       if (j >= v.nbe) continue;
       T K[NS];
-      if (!tg::p1_elem_sym<EL, T>(in[u], a.c, tab, K)) {
+      T adet;
+      const bool ok = tg::p1_elem_sym<EL, T>(in[u], a.c, tab, K, &adet);
+      if (!ok) {
         tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e[u]);
 #pragma unroll
         for (int q = 0; q < NS; ++q) K[q] = T(0);
+      }
+      if constexpr (LOAD) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) Fe[c * g.capE + j] = ok ? tg::p1_load_entry<NV, T>(a.f_layout, adet, fv[u], tab, c) : T(0);
       }
       int q = 0;
 #pragma unroll
@@ -117,6 +130,7 @@ __global__ void __launch_bounds__(BS, blk_min_ctas<D, T, UB>()) k_bilinear_blk(c
     if (i < v.r1) {
       T* row = acc + (v.rp[i] - rbase);
       const int je = v.ip[i + 1];
+      T fs = T(0);
       for (int j = v.ip[i]; j < je; ++j) {
         const tg::BlkRec<NV> r{v.rc[j]};
         const T* kr = Ke + r.a() * NV * g.capE + r.le();
@@ -129,7 +143,9 @@ __global__ void __launch_bounds__(BS, blk_min_ctas<D, T, UB>()) k_bilinear_blk(c
         }
 #pragma unroll
         for (int c = 0; c < NV; ++c) row[r.pos(c)] = cur[c] + add[c];
+        if constexpr (LOAD) fs += Fe[r.a() * g.capE + r.le()];
       }
+      if constexpr (LOAD) a.F[i] = fs;
     }
     __syncthreads();
     const int nz = v.rp[v.r1] - rbase;
@@ -144,10 +160,11 @@ __global__ void __launch_bounds__(BS, blk_min_ctas<D, T, UB>()) k_bilinear_blk(c
 }
 
 template <int D, typename T>
-size_t bilinear_blk_smem(const tg_pattern* p) {
+size_t bilinear_blk_smem(const tg_pattern* p, bool load = false) {
   constexpr int NV = D + 1;
   const tg::BlkArgs g = tg::blk_args(p);
-  return tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE, NV) + ((size_t)NV * NV * g.capE + p->blk_max_nz) * sizeof(T);
+  return tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE, NV) +
+         ((size_t)NV * (NV + (load ? 1 : 0)) * g.capE + p->blk_max_nz) * sizeof(T);
 }
 
 // P1 load vector over element-once row blocks: Map F_e (NV values) per
@@ -174,20 +191,12 @@ __global__ void __launch_bounds__(BS) k_load_blk(const FwdArgs<T> a, const __gri
       for (int c = 0; c < NV; ++c) vid[u][c] = v.vtx(c, j);
     }
     T x[UB][NV][D];
-    T fv[UB][NV > NQ ? NV : NQ];
+    T fv[UB][NV];
 #pragma unroll
     for (int u = 0; u < UB; ++u) {
 #pragma unroll
       for (int c = 0; c < NV; ++c) tg::load_x<D, T>(a.coords, vid[u][c], x[u][c]);
-      if (a.layout == TG_PER_NODE) {
-#pragma unroll
-        for (int c = 0; c < NV; ++c) fv[u][c] = __ldg(a.coef + vid[u][c]);
-      } else if (a.layout == TG_PER_QP) {
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) fv[u][q] = __ldg(a.coef + (int64_t)e[u] * NQ + q);
-      } else {
-        fv[u][0] = __ldg(a.coef);
-      }
+      tg::p1_load_f<NV, T>(a.coef, a.layout, e[u], vid[u], fv[u]);
     }
 #pragma unroll
     for (int u = 0; u < UB; ++u) {
@@ -200,23 +209,7 @@ __global__ void __launch_bounds__(BS) k_load_blk(const FwdArgs<T> a, const __gri
       const bool ok = adet > tg::det_tiny<T>();
       if (!ok) tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e[u]);
 #pragma unroll
-      for (int c = 0; c < NV; ++c) {
-        T val;
-        if (a.layout == TG_PER_NODE) {
-          T s2 = T(0);
-#pragma unroll
-          for (int bb = 0; bb < NV; ++bb) s2 = fma(ts.M[c][bb], fv[u][bb], s2);
-          val = adet * s2;
-        } else if (a.layout == TG_PER_QP) {
-          T s2 = T(0);
-#pragma unroll
-          for (int q = 0; q < NQ; ++q) s2 = fma(ts.w[q] * ts.phi[q][c], fv[u][q], s2);
-          val = adet * s2;
-        } else {
-          val = adet * ts.m1[c] * fv[u][0];
-        }
-        Fe[c * g.capE + j] = ok ? val : T(0);
-      }
+      for (int c = 0; c < NV; ++c) Fe[c * g.capE + j] = ok ? tg::p1_load_entry<NV, T>(a.layout, adet, fv[u], ts, c) : T(0);
     }
   }
   __syncthreads();
@@ -441,6 +434,9 @@ FwdArgs<T> base_args(const tg_pattern* p, const void* coords) {
   a.out = nullptr;
   a.n = p->N;
   a.status = p->status;
+  a.f = nullptr;
+  a.f_layout = 0;
+  a.F = nullptr;
   return a;
 }
 
@@ -479,12 +475,12 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
         kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::blk_args(p), p->blk_max_nz);
       };
       if constexpr (sizeof(T) == 8) {
-        if (ub == 2) go(k_bilinear_blk<D, T, 2>);
-        else go(k_bilinear_blk<D, T, 3>);
+        if (ub == 2) go(k_bilinear_blk<D, T, 2, false>);
+        else go(k_bilinear_blk<D, T, 3, false>);
       } else {
-        if (ub == 4) go(k_bilinear_blk<D, T, 4>);
-        else if (ub == 5) go(k_bilinear_blk<D, T, 5>);
-        else go(k_bilinear_blk<D, T, 6>);
+        if (ub == 4) go(k_bilinear_blk<D, T, 4, false>);
+        else if (ub == 5) go(k_bilinear_blk<D, T, 5, false>);
+        else go(k_bilinear_blk<D, T, 6, false>);
       }
       if (st != TG_OK) return st;
       TG_CK_LAUNCH("k_bilinear_blk");
@@ -603,6 +599,53 @@ tg_status elastic(const tg_pattern* p, const void* coords, const void* lam, cons
   return TG_OK;
 }
 
+// The system (K, F) in one pass where the element-once kernels apply, else
+// the two assemblies one after the other (same values either way).
+template <typename T>
+tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa, tg_layout kl, double c,
+                     const void* f, tg_layout fl, void* vals, void* F, cudaStream_t s) {
+  if ((p->el == TG_P1_TRI || p->el == TG_P1_TET) && p->bel) {
+    FwdArgs<T> a = base_args<T>(p, coords);
+    a.coef = static_cast<const T*>(kappa);
+    a.layout = kl;
+    a.c = (T)c;
+    a.out = static_cast<T*>(vals);
+    a.f = static_cast<const T*>(f);
+    a.f_layout = fl;
+    a.F = static_cast<T*>(F);
+    const bool tri = p->el == TG_P1_TRI;
+    const size_t sb = tri ? bilinear_blk_smem<2, T>(p, true) : bilinear_blk_smem<3, T>(p, true);
+    if (use_blk<T>(p, sb)) {
+      const int ub = blk_ub<T>(p);
+      const tg::RefTab<T>& tab = table<T>(p->el);
+      tg_status st = TG_OK;
+      auto go = [&](auto kern) {
+        dim3 grid;
+        if ((st = launch_blk(kern, sb, p, &grid)) != TG_OK) return;
+        kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::blk_args(p), p->blk_max_nz);
+      };
+      if constexpr (sizeof(T) == 8) {
+        if (tri) go(k_bilinear_blk<2, T, 2, true>);
+        else go(k_bilinear_blk<3, T, 2, true>);
+      } else {
+        if (tri) {
+          if (ub <= 4) go(k_bilinear_blk<2, T, 4, true>);
+          else go(k_bilinear_blk<2, T, 6, true>);
+        } else {
+          if (ub <= 4) go(k_bilinear_blk<3, T, 4, true>);
+          else go(k_bilinear_blk<3, T, 6, true>);
+        }
+      }
+      if (st != TG_OK) return st;
+      TG_CK_LAUNCH("k_bilinear_blk<load>");
+      return TG_OK;
+    }
+  }
+  tg_status st = bilinear<T>(p, coords, kappa, kl, c, vals, s, false);
+  if (st != TG_OK) return st;
+  return load<T>(p, coords, f, fl, 1, F, s);
+}
+
 bool layout_ok(tg_layout l, bool allow_node) {
   return l == TG_PER_ELEMENT || l == TG_PER_QP || l == TG_CONSTANT || (allow_node && l == TG_PER_NODE);
 }
@@ -641,6 +684,20 @@ tg_status tg_assemble_elasticity(const tg_pattern* p, tg_dtype dtype, const void
   cudaStream_t s = (cudaStream_t)stream;
   return dtype == TG_F32 ? elastic<float>(p, coords, lam, mu, layout, vals_out, s)
                          : elastic<double>(p, coords, lam, mu, layout, vals_out, s);
+}
+
+tg_status tg_assemble_system(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
+                             tg_layout kappa_layout, double c, const void* f, tg_layout f_layout, void* vals_out,
+                             void* F_out, tg_stream stream) {
+  tg_status st = check_common(p, dtype, coords);
+  if (st != TG_OK) return st;
+  if (p->el == TG_P1_TET_VEC3 || !layout_ok(kappa_layout, false) || !kappa || (p->nnz > 0 && !vals_out) || !f ||
+      !F_out || !(f_layout == TG_PER_NODE || f_layout == TG_PER_QP || f_layout == TG_CONSTANT))
+    return TG_ERR_INVALID_ARG;
+  if (p->N == 0) return TG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  return dtype == TG_F32 ? system_asm<float>(p, coords, kappa, kappa_layout, c, f, f_layout, vals_out, F_out, s)
+                         : system_asm<double>(p, coords, kappa, kappa_layout, c, f, f_layout, vals_out, F_out, s);
 }
 
 tg_status tg_assemble_load(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* f, tg_layout f_layout,

@@ -26,6 +26,9 @@ struct FwdArgs {
   T* __restrict__ out;
   int64_t n;  // rows (gather kernels) or elements (atomic kernel)
   unsigned long long* status;
+  const T* __restrict__ f;  // load of the fused system assembly (NULL otherwise)
+  int f_layout;
+  T* __restrict__ F;
 };
 
 template <typename T>
@@ -123,6 +126,43 @@ __device__ __forceinline__ void load_x(const T* __restrict__ coords, int v, T (&
   }
 }
 
+// Load values f of a P1 element as its F_e needs them: at the vertices
+// (PER_NODE), at the points (PER_QP; NQ == NV for P1) or one constant.
+template <int NV, typename T>
+__device__ __forceinline__ void p1_load_f(const T* __restrict__ f, int layout, int64_t e, const int (&vid)[NV],
+                                          T (&fv)[NV]) {
+  if (layout == TG_PER_NODE) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) fv[c] = __ldg(f + vid[c]);
+  } else if (layout == TG_PER_QP) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) fv[q] = __ldg(f + e * NV + q);
+  } else {
+    fv[0] = __ldg(f);
+#pragma unroll
+    for (int q = 1; q < NV; ++q) fv[q] = fv[0];
+  }
+}
+
+// F_e[c] = sum_q w_q |det J| f(x_q) phi_c(x_q) (second line of Eq.
+// (matlclquad)); for nodal f the interpolant, F_e = |det J| M f_e.
+template <int NV, typename T>
+__device__ __forceinline__ T p1_load_entry(int layout, T adet, const T (&fv)[NV], const RefTab<T>& ts, int c) {
+  if (layout == TG_PER_NODE) {
+    T s2 = T(0);
+#pragma unroll
+    for (int b = 0; b < NV; ++b) s2 = fma(ts.M[c][b], fv[b], s2);
+    return adet * s2;
+  }
+  if (layout == TG_PER_QP) {
+    T s2 = T(0);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) s2 = fma(ts.w[q] * ts.phi[q][c], fv[q], s2);
+    return adet * s2;
+  }
+  return adet * ts.m1[c] * fv[0];
+}
+
 // Row la of the local matrix from loaded inputs; false for a degenerate
 // element.  Same arithmetic, operation for operation, as scalar_row.
 template <int EL, typename T>
@@ -156,12 +196,13 @@ __device__ __forceinline__ bool elem_row(const ElemIn<EL, T>& in, T c, const Ref
 // for a degenerate element.  Entry for entry the arithmetic of elem_row.
 template <int EL, typename T>
 __device__ __forceinline__ bool p1_elem_sym(const ElemIn<EL, T>& in, T c, const RefTab<T>& ts,
-                                            T (&K)[Elem<EL>::nv * (Elem<EL>::nv + 1) / 2]) {
+                                            T (&K)[Elem<EL>::nv * (Elem<EL>::nv + 1) / 2], T* adet_out = nullptr) {
   constexpr int D = Elem<EL>::dim, NV = D + 1;
   Geom<D, T> g;
   if constexpr (D == 2) tri_geom_x(in.x[0], in.x[1], in.x[2], g);
   else tet_geom_x(in.x[0], in.x[1], in.x[2], in.x[3], g);
   const T adet = absv(g.det);
+  if (adet_out) *adet_out = adet;
   if (!(adet > det_tiny<T>())) return false;
   T sc, mc;
   p1_scales<Elem<EL>::nq, T>(in.kq, ts, adet, c, sc, mc);

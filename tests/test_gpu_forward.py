@@ -129,6 +129,26 @@ def test_elasticity_matches_oracle(tg, layout, dtype):
     assert relfro(vals.cpu().numpy(), ref.val) <= TOL[dtype]
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("fl", [mg.PER_NODE, mg.PER_QP, mg.CONSTANT])
+@pytest.mark.parametrize("el", [mg.P1_TRI, mg.P2_TRI, mg.P1_TET])
+def test_system_equals_bilinear_and_load_bitwise(tg, el, fl, dtype):
+    """The one-pass system assembly returns exactly the separate calls' values."""
+    m = mesh_for(el)
+    nq = mg.NQ[el]
+    k = coef(mg.PER_QP, m.n_elems, nq, seed=81)
+    g = np.random.default_rng(82)
+    nf = {mg.PER_NODE: m.n_nodes, mg.PER_QP: m.n_elems * nq, mg.CONSTANT: 1}[fl]
+    f = g.uniform(-1, 1, size=nf)
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, el)
+    x, kd, fd = dev(m.coords, dtype), dev(k, dtype), dev(f, dtype)
+    vals, F = tg.tg_assemble_system(p, x, kd, mg.PER_QP, 0.7, fd, fl)
+    assert torch.equal(vals, tg.tg_assemble_bilinear(p, x, kd, mg.PER_QP, 0.7))
+    assert torch.equal(F, tg.tg_assemble_load(p, x, fd, fl))
+    ref = O.assemble_load(el, m.cells, host_as(m.coords, dtype), host_as(f, dtype), fl)
+    assert relfro(F.cpu().numpy(), ref) <= TOL[dtype]
+
+
 # ---------------------------------------------------------------- full-size workloads, sampled rows
 def _sampled_rows_check(tg, p, vals, ref_fn, n_rows, rows_per_node, seed, tol):
     g = np.random.default_rng(seed)
