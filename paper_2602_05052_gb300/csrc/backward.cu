@@ -48,6 +48,10 @@ struct BwdArgs {
   double* __restrict__ partials;
   int64_t N;
   unsigned long long* status;
+  // element-once kernel: arrival counter and the global sums' outputs
+  // (dL/dc, constant-kappa gradient; NULL = not requested)
+  unsigned int* arrivals;
+  T* sum_out[2];
 };
 
 // Fixed-order block sum of two doubles (warp tree, then warp 0 over warps).
@@ -487,10 +491,40 @@ __global__ void __launch_bounds__(BB, (D == 2 && sizeof(T) == 4) ? 6 : 2) k_back
   }
   __syncthreads();  // stage s and Gx are free again
   TG_BLK_PIPELINE_END
+  // Global sums: per-CTA partials, then the last CTA to arrive adds them all
+  // in a fixed order (no CTA waits for another).
   block_sum2(pc, pk, red);
+  __shared__ bool s_last;
   if (threadIdx.x == 0) {
     a.partials[kSlots * blockIdx.x] = pc;
     a.partials[kSlots * blockIdx.x + 1] = pk;
+    __threadfence();
+    s_last = atomicInc(a.arrivals, gridDim.x - 1) == gridDim.x - 1;  // wraps to 0 for the next launch
+  }
+  __syncthreads();
+  if (s_last && (a.sum_out[0] || a.sum_out[1])) {
+    __threadfence();
+    double c0 = 0.0, c1 = 0.0;
+    for (int b0 = threadIdx.x; b0 < (int)gridDim.x; b0 += 8 * blockDim.x) {
+      double2 q[8];  // independent loads first, then the adds in order
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int b2 = b0 + u * blockDim.x;
+        q[u] = b2 < (int)gridDim.x ? __ldcg(reinterpret_cast<const double2*>(a.partials + kSlots * b2))
+                                   : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (b0 + u * (int)blockDim.x < (int)gridDim.x) {
+          c0 += q[u].x;
+          c1 += q[u].y;
+        }
+    }
+    block_sum2(c0, c1, red);
+    if (threadIdx.x == 0) {
+      if (a.sum_out[0]) *a.sum_out[0] = (T)c0;
+      if (a.sum_out[1]) *a.sum_out[1] = (T)c1;
+    }
   }
 }
 
@@ -805,17 +839,13 @@ tg_status launch(const tg_pattern* p, const BwdArgs<T>& a, bool fused, T* grad_c
   if constexpr (EL == TG_P1_TRI || EL == TG_P1_TET) {
     bool used = false;
     int grid = 0;
-    tg_status st = launch_blk<tg::Elem<EL>::dim, T>(p, a, fused, &grid, &used, s);
+    BwdArgs<T> ab = a;
+    ab.arrivals = p->arrivals;
+    ab.sum_out[0] = grad_c;
+    ab.sum_out[1] = (a.layout == TG_CONSTANT) ? a.grad_kappa : nullptr;
+    tg_status st = launch_blk<tg::Elem<EL>::dim, T>(p, ab, fused, &grid, &used, s);
     if (st != TG_OK) return st;
-    if (used) {
-      T* gk_const = (a.layout == TG_CONSTANT) ? a.grad_kappa : nullptr;
-      if (grad_c || gk_const) {
-        FinalOut o{{grad_c, gk_const, nullptr, nullptr}, 2, 0};
-        k_backward_final<T><<<1, kFinal, 0, s>>>(a.partials, grid, o);
-        TG_CK_LAUNCH("k_backward_final");
-      }
-      return TG_OK;
-    }
+    if (used) return TG_OK;
   }
   size_t smem = 0;
   const int R = bwd_rows<T>(p, tg::Elem<EL>::dim, &smem);
@@ -859,6 +889,8 @@ tg_status backward(const tg_pattern* p, const void* coords, const void* kappa, t
   a.partials = p->partials;
   a.N = p->N;
   a.status = p->status;
+  a.arrivals = nullptr;
+  a.sum_out[0] = a.sum_out[1] = nullptr;
   const bool fused = gvals == nullptr;
   T* gc = static_cast<T*>(grad_c);
   switch (p->el) {
@@ -890,6 +922,10 @@ struct LoadBwdArgs {
   double* __restrict__ partials;
   int64_t N;
   unsigned long long* status;
+  // element-once kernel: arrival counter and the global sums' outputs
+  // (dL/dc, constant-kappa gradient; NULL = not requested)
+  unsigned int* arrivals;
+  T* sum_out[2];
 };
 
 template <int EL, typename T, int NC>

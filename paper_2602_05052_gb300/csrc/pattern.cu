@@ -625,6 +625,8 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   // least 32 rows)
   p->n_partials = 4 * ((N + 31) / 32) + 4;
   TG_CK(cudaMalloc(&p->partials, p->n_partials * sizeof(double)));
+  TG_CK(cudaMalloc(&p->arrivals, 16));
+  TG_CK(cudaMemsetAsync(p->arrivals, 0, 16, s));
   TG_CK(cudaStreamSynchronize(s));
   if ((st = read_status(p, s, "tg_build_pattern")) != TG_OK) return st;
   guard.ok = true;

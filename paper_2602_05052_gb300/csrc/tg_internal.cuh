@@ -66,6 +66,9 @@ struct tg_pattern {
   // per-CTA partial sums of global reductions (backward of c / constant kappa)
   double* partials = nullptr;
   int64_t n_partials = 0;
+  // arrival counter of the element-once backward's CTAs (zero between
+  // launches: the last CTA to arrive wraps it back to zero)
+  unsigned int* arrivals = nullptr;
 };
 
 namespace tg {
