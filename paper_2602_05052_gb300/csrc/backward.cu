@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(BB) k_backward_gather(const BwdArgs<T> a, cons
 // incidences' contributions in increasing element order.  Per-CTA FP64
 // partials of the global sums are reduced by k_backward_final.
 template <int D, typename T, bool FUSED, int UB>
-__global__ void __launch_bounds__(BB, (D == 2 && sizeof(T) == 4) ? 6 : 2) k_backward_blk(const BwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
+__global__ void __launch_bounds__(BB, (D == 2 && sizeof(T) == 4) ? (UB >= 3 ? 5 : 6) : 2) k_backward_blk(const BwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
                                                      const tg::BlkArgs g, const uint64_t* __restrict__ elem_pos,
                                                      const int32_t* __restrict__ row_ptr) {
   constexpr int NV = D + 1, NQ = D == 2 ? 3 : 4;
@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(BB, (D == 2 && sizeof(T) == 4) ? 6 : 2) k_back
         for (int r = 0; r < D; ++r) gs[r] += gp[r * g.capE];
       }
 #pragma unroll
-      for (int r = 0; r < D; ++r) a.grad_coords[(int64_t)i * D + r] = gs[r];
+      for (int r = 0; r < D; ++r) a.grad_coords[(int64_t)v.pm[i] * D + r] = gs[r];
     }
   }
   __syncthreads();  // stage s and Gx are free again
@@ -735,7 +735,7 @@ __global__ void __launch_bounds__(BB) k_elastic_backward_blk(const ElBwdArgs<T> 
         for (int r = 0; r < 3; ++r) gs[r] += gp[r * g.capE];
       }
 #pragma unroll
-      for (int r = 0; r < 3; ++r) a.grad_coords[3ll * i + r] = gs[r];
+      for (int r = 0; r < 3; ++r) a.grad_coords[3ll * v.pm[i] + r] = gs[r];
     }
   }
   __syncthreads();
@@ -811,7 +811,7 @@ tg_status launch_blk(const tg_pattern* p, const BwdArgs<T>& a, bool fused, int* 
   const int nt = BB;
   if (p->blk_rows > BB) return TG_OK;
   const tg::RefTab<T>& tab = tg::table<T>(p->el);
-  constexpr int UB = sizeof(T) == 4 ? 2 : 1;
+  const int need = (p->blk_max_elems + BB - 1) / BB;  // elements per thread for one Map round
   tg_status st = TG_OK;
   auto go = [&](auto kern) {
     if ((st = tg::set_smem((const void*)kern, smem)) != TG_OK) return;
@@ -826,8 +826,18 @@ tg_status launch_blk(const tg_pattern* p, const BwdArgs<T>& a, bool fused, int* 
     kern<<<grid, nt, smem, s>>>(a, tab, g, p->elem_pos, p->row_ptr);
     *grid_out = grid;
   };
-  if (fused) go(k_backward_blk<D, T, true, UB>);
-  else go(k_backward_blk<D, T, false, UB>);
+  if constexpr (sizeof(T) == 8) {
+    if (fused) go(k_backward_blk<D, T, true, 1>);
+    else go(k_backward_blk<D, T, false, 1>);
+  } else {
+    if (need >= 3) {
+      if (fused) go(k_backward_blk<D, T, true, 3>);
+      else go(k_backward_blk<D, T, false, 3>);
+    } else {
+      if (fused) go(k_backward_blk<D, T, true, 2>);
+      else go(k_backward_blk<D, T, false, 2>);
+    }
+  }
   if (st != TG_OK) return st;
   TG_CK_LAUNCH("k_backward_blk");
   *used = true;
@@ -1219,8 +1229,16 @@ extern "C" tg_status tg_assemble_elasticity_backward(const tg_pattern* p, tg_dty
     tg_status st = TG_OK;
     auto go = [&](auto kern) {
       if ((st = tg::set_smem((const void*)kern, smem)) != TG_OK) return;
+      // The W gathers of neighbouring elements hit in L1: prefer a shared
+      // memory carveout of 3/4, leaving L1 room (measured: about 1.9x
+      // faster than the largest carveout on the 64^3 workload).
+      cudaError_t ce = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 75);
+      if (ce != cudaSuccess) {
+        st = tg::cuda_fail(ce, "cudaFuncSetAttribute(carveout)", __FILE__, __LINE__);
+        return;
+      }
       int per_sm = 0;
-      cudaError_t ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BB, smem);
+      ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BB, smem);
       if (ce != cudaSuccess) {
         st = tg::cuda_fail(ce, "cudaOccupancyMaxActiveBlocksPerMultiprocessor", __FILE__, __LINE__);
         return;

@@ -2,9 +2,11 @@
 // the forward, load and backward kernels share.
 //
 // A persistent CTA walks the row blocks b = blockIdx.x, + gridDim.x, ...
-// Block b owns R consecutive rows (R <= the CTA's threads).  Its contiguous
-// streams are:
-//   - its slices of inc_ptr and row_ptr;
+// Block b owns R consecutive rows of the pattern's internal row order (R <=
+// the CTA's threads; a block is a compact patch of the mesh when the
+// elements come in a space-filling-curve order).  Its contiguous streams are:
+//   - its slices of the internal incidence and CSR-value prefix sums, of the
+//     rows' CSR starts and of the rows' node ids;
 //   - the records of its incidences (brec);
 //   - its list of distinct elements (bel).
 // Thread 0 prefetches them into the other of two shared stages with bulk
@@ -13,8 +15,7 @@
 //            quantities once and leaves them in shared memory;
 //   Reduce - one thread per row sums the quantities of its incidences in
 //            increasing element order (the fixed order that makes every
-//            output bitwise reproducible) and the block's results leave
-//            with coalesced stores.
+//            output bitwise reproducible) and writes its node's outputs.
 // An element shared by several blocks is computed once in each of them.
 #pragma once
 
@@ -26,8 +27,10 @@
 namespace tg {
 
 struct BlkArgs {
-  const int32_t* __restrict__ inc_ptr;
-  const int32_t* __restrict__ row_ptr;
+  const int32_t* __restrict__ inc_ptr;  // internal incidence prefix sums (iinc)
+  const int32_t* __restrict__ row_ptr;  // internal CSR-value prefix sums (irp)
+  const int32_t* __restrict__ urp;      // CSR row start of each internal row
+  const int32_t* __restrict__ iperm;    // node of each internal row
   const uint32_t* __restrict__ bel;
   const int64_t* __restrict__ boff;
   const int32_t* __restrict__ bvbase;
@@ -44,8 +47,10 @@ struct BlkArgs {
 // Host: BlkArgs of a pattern with row blocks.
 inline BlkArgs blk_args(const tg_pattern* p) {
   BlkArgs g;
-  g.inc_ptr = p->inc_ptr;
-  g.row_ptr = p->row_ptr;
+  g.inc_ptr = p->iinc;
+  g.row_ptr = p->irp;
+  g.urp = p->urp;
+  g.iperm = p->iperm;
   g.bel = p->bel;
   g.boff = p->boff;
   g.bvbase = p->bvbase;
@@ -64,7 +69,7 @@ inline BlkArgs blk_args(const tg_pattern* p) {
 // Shared-memory bytes of the two stages plus barriers and block metadata.
 __host__ __device__ inline size_t blk_stage_bytes(int R, int capJ, int capE, int nv) {
   const size_t el_words = (size_t)capE + (size_t)nv * (((capE + 7) & ~7) / 2);
-  return 16 + 128 + 2 * ((size_t)(R + 8) * 8 + (size_t)(capJ + 8) * 4 + el_words * 4);
+  return 16 + 128 + 2 * ((size_t)(R + 8) * 16 + (size_t)(capJ + 8) * 4 + el_words * 4);
 }
 
 // Geometry of one row block as seen through its stage.
@@ -72,8 +77,10 @@ struct BlkView {
   int r0, r1, J0, J1, nbe;
   int bs16;            // row stride of vo
   int vbase;           // smallest vertex id of the block's elements
-  const int* ip;       // ip[i] = inc_ptr[i], i in [r0, r1]
-  const int* rp;       // rp[i] = row_ptr[i]
+  const int* ip;       // ip[i]: internal incidence prefix, i in [r0, r1]
+  const int* rp;       // rp[i]: internal CSR-value prefix (rp[i] - rp[r0] = offset in the block)
+  const int* up;       // up[i]: CSR start of internal row i's node, i in [r0, r1)
+  const int* pm;       // pm[i]: node of internal row i
   const uint32_t* rc;  // rc[j] = brec[j], j in [J0, J1)
   const uint32_t* be;  // be[k]: element k (with the owner bit), k < nbe
   const uint16_t* vo;  // vo[c * bs16 + k]: vertex c of element k, minus vbase
@@ -90,7 +97,7 @@ class BlkPipe {
     IPN_ = R_ + 8;
     RECN_ = g.capJ + 8;
     ELN_ = g.capE + g.nv * (g.capE16 / 2);
-    SW_ = 2 * IPN_ + RECN_ + ELN_;  // words per stage (a multiple of 4)
+    SW_ = 4 * IPN_ + RECN_ + ELN_;  // words per stage (a multiple of 4)
     bar_ = reinterpret_cast<uint64_t*>(p);
     meta_ = reinterpret_cast<int*>(p + 16);
     st_ = reinterpret_cast<int*>(p + 16 + 128);
@@ -136,11 +143,14 @@ class BlkPipe {
     m[5] = j0a;
     m[6] = q.nbe;
     m[7] = q.vb;
-    const uint32_t bytes = 4u * (2u * nip + (q.J1 > q.J0 ? nrec : 0) + nel);
+    const int nup = (r1 - a0 + 3) & ~3;
+    const uint32_t bytes = 4u * (2u * nip + 2u * nup + (q.J1 > q.J0 ? nrec : 0) + nel);
     fence_proxy_async();
     mbar_arrive_expect_tx(&bar_[s], bytes);
     bulk_copy_g2s(ip(s), g.inc_ptr + a0, nip * 4, &bar_[s]);
     bulk_copy_g2s(rp(s), g.row_ptr + a0, nip * 4, &bar_[s]);
+    bulk_copy_g2s(up(s), g.urp + a0, nup * 4, &bar_[s]);
+    bulk_copy_g2s(pm(s), g.iperm + a0, nup * 4, &bar_[s]);
     if (q.J1 > q.J0) bulk_copy_g2s(rec(s), g.brec + j0a, nrec * 4, &bar_[s]);
     if (nel > 0) bulk_copy_g2s(el(s), g.bel + q.bo, nel * 4, &bar_[s]);
   }
@@ -173,6 +183,8 @@ class BlkPipe {
     v.bs16 = (v.nbe + 7) & ~7;
     v.ip = ip(s) - m[4];
     v.rp = rp(s) - m[4];
+    v.up = up(s) - m[4];
+    v.pm = pm(s) - m[4];
     v.rc = rec(s) - m[5];
     v.be = el(s);
     v.vo = reinterpret_cast<const uint16_t*>(el(s) + ((v.nbe + 3) & ~3));
@@ -180,10 +192,12 @@ class BlkPipe {
   }
 
  private:
-  // stage s: ip [IPN] | rp [IPN] | rec [RECN] | el [ELN]
+  // stage s: ip [IPN] | rp [IPN] | up [IPN] | pm [IPN] | rec [RECN] | el [ELN]
   __device__ int* ip(int s) const { return st_ + s * SW_; }
   __device__ int* rp(int s) const { return ip(s) + IPN_; }
-  __device__ uint32_t* rec(int s) const { return reinterpret_cast<uint32_t*>(rp(s) + IPN_); }
+  __device__ int* up(int s) const { return rp(s) + IPN_; }
+  __device__ int* pm(int s) const { return up(s) + IPN_; }
+  __device__ uint32_t* rec(int s) const { return reinterpret_cast<uint32_t*>(pm(s) + IPN_); }
   __device__ uint32_t* el(int s) const { return rec(s) + RECN_; }
 
   int R_, IPN_, RECN_, ELN_, SW_;

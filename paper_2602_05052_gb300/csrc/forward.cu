@@ -123,12 +123,12 @@ __global__ void __launch_bounds__(BS, blk_min_ctas<D, T, UB>() - (LOAD ? 1 : 0))
     }
   }
   __syncthreads();
-  // Reduce: rows summed in increasing element order
+  // Reduce: rows summed in increasing element order, each row's values
+  // written to its node's CSR row (acc cleared on the way for the next block)
   {
     const int i = v.r0 + (int)threadIdx.x;
-    const int rbase = v.rp[v.r0];
     if (i < v.r1) {
-      T* row = acc + (v.rp[i] - rbase);
+      T* row = acc + (v.rp[i] - v.rp[v.r0]);
       const int je = v.ip[i + 1];
       T fs = T(0);
       for (int j = v.ip[i]; j < je; ++j) {
@@ -145,14 +145,13 @@ __global__ void __launch_bounds__(BS, blk_min_ctas<D, T, UB>() - (LOAD ? 1 : 0))
         for (int c = 0; c < NV; ++c) row[r.pos(c)] = cur[c] + add[c];
         if constexpr (LOAD) fs += Fe[r.a() * g.capE + r.le()];
       }
-      if constexpr (LOAD) a.F[i] = fs;
-    }
-    __syncthreads();
-    const int nz = v.rp[v.r1] - rbase;
-    T* out = a.out + rbase;
-    for (int q = threadIdx.x; q < nz; q += NT_) {
-      out[q] = acc[q];
-      acc[q] = T(0);
+      if constexpr (LOAD) a.F[v.pm[i]] = fs;
+      const int len = v.rp[i + 1] - v.rp[i];
+      T* out = a.out + v.up[i];
+      for (int q = 0; q < len; ++q) {
+        out[q] = row[q];
+        row[q] = T(0);
+      }
     }
     __syncthreads();  // stage s and the work buffers are free again
   }
@@ -222,7 +221,7 @@ __global__ void __launch_bounds__(BS) k_load_blk(const FwdArgs<T> a, const __gri
         const tg::BlkRec<NV> r{v.rc[j]};
         f += Fe[r.a() * g.capE + r.le()];
       }
-      a.out[i] = f;
+      a.out[v.pm[i]] = f;
     }
     __syncthreads();
   }
@@ -242,7 +241,7 @@ template <typename T>
 int blk_ub(const tg_pattern* p) {
   const int need = (p->blk_max_elems + BS - 1) / BS;
   if (sizeof(T) == 8) return need <= 2 ? 2 : 3;
-  return need <= 4 ? 4 : need <= 5 ? 5 : 6;
+  return need <= 3 ? 3 : need <= 4 ? 4 : need <= 5 ? 5 : 6;
 }
 
 // Threads per CTA of the element-once kernels (rows per block <= BS).
@@ -478,7 +477,8 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
         if (ub == 2) go(k_bilinear_blk<D, T, 2, false>);
         else go(k_bilinear_blk<D, T, 3, false>);
       } else {
-        if (ub == 4) go(k_bilinear_blk<D, T, 4, false>);
+        if (ub == 3) go(k_bilinear_blk<D, T, 3, false>);
+        else if (ub == 4) go(k_bilinear_blk<D, T, 4, false>);
         else if (ub == 5) go(k_bilinear_blk<D, T, 5, false>);
         else go(k_bilinear_blk<D, T, 6, false>);
       }
@@ -629,7 +629,8 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
         else go(k_bilinear_blk<3, T, 2, true>);
       } else {
         if (tri) {
-          if (ub <= 4) go(k_bilinear_blk<2, T, 4, true>);
+          if (ub <= 3) go(k_bilinear_blk<2, T, 3, true>);
+          else if (ub <= 4) go(k_bilinear_blk<2, T, 4, true>);
           else go(k_bilinear_blk<2, T, 6, true>);
         } else {
           if (ub <= 4) go(k_bilinear_blk<3, T, 4, true>);

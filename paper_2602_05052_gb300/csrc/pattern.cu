@@ -209,23 +209,116 @@ __global__ void k_expand3(const int32_t* __restrict__ row_ptr, const int32_t* __
 }
 
 // ------------------------------------------------------------------ row blocks
-// Per block of R rows: its incidence count and its CSR value count.
-__global__ void k_blk_stats(const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ row_ptr, int64_t N, int R,
+// The element-once kernels walk the rows in an internal order: nodes sorted
+// by their smallest incident element (a space-filling-curve element order
+// makes consecutive rows a compact patch), cut into blocks of R rows, each
+// block in ascending node id.
+//
+// key[u]: smallest element incident to node u (E for an isolated node).
+__global__ void k_row_key(const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc_e, int64_t N,
+                          int64_t E, int32_t* __restrict__ key, int32_t* __restrict__ iso) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= N) return;
+  const int j0 = inc_ptr[u], j1 = inc_ptr[u + 1];
+  key[u] = j1 > j0 ? (inc_e[j0] >> 3) : (int32_t)E;
+  iso[u] = j1 > j0 ? 0 : 1;
+}
+
+// Bucket sizes: the vertices of element e whose key is e.
+__global__ void k_key_count(const int32_t* __restrict__ cells, int nv, int64_t E, const int32_t* __restrict__ key,
+                            int32_t* __restrict__ cnt) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  int c = 0;
+  for (int a = 0; a < nv; ++a) c += key[cells[e * nv + a]] == (int32_t)e;
+  cnt[e] = c;
+}
+
+// Bucket e lists the vertices keyed to e in ascending id.
+__global__ void k_key_place(const int32_t* __restrict__ cells, int nv, int64_t E, const int32_t* __restrict__ key,
+                            const int64_t* __restrict__ off, int32_t* __restrict__ order) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  int vs[4], n = 0;
+  for (int a = 0; a < nv; ++a) {
+    const int v = cells[e * nv + a];
+    if (key[v] == (int32_t)e) {
+      int k = n++;
+      while (k > 0 && vs[k - 1] > v) {
+        vs[k] = vs[k - 1];
+        --k;
+      }
+      vs[k] = v;
+    }
+  }
+  for (int k = 0; k < n; ++k) order[off[e] + k] = vs[k];
+}
+
+// Isolated nodes last, ascending.
+__global__ void k_iso_place(const int32_t* __restrict__ iso, const int64_t* __restrict__ rank, int64_t N, int64_t base,
+                            int32_t* __restrict__ order) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < N && iso[u]) order[base + rank[u]] = (int32_t)u;
+}
+
+// Ascending node ids inside every block of R (<= 128) internal rows; the
+// inverse permutation.
+__global__ void __launch_bounds__(128) k_blk_sort(const int32_t* __restrict__ order, int64_t N, int R,
+                                                  int32_t* __restrict__ iperm, int32_t* __restrict__ ipos) {
+  __shared__ int sk[128];
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  const int n = (int)(r0 + R < N ? R : N - r0);
+  for (int k = threadIdx.x; k < 128; k += blockDim.x) sk[k] = k < n ? order[r0 + k] : INT32_MAX;
+  __syncthreads();
+  for (int k = 2; k <= 128; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < 128; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const int x = sk[i], y = sk[ixj];
+          if ((x > y) == ((i & k) == 0)) {
+            sk[i] = y;
+            sk[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    iperm[r0 + k] = sk[k];
+    ipos[sk[k]] = (int32_t)(r0 + k);
+  }
+}
+
+// Per internal row: incidence count, CSR row length and CSR row start.
+__global__ void k_irow(const int32_t* __restrict__ iperm, const int32_t* __restrict__ inc_ptr,
+                       const int32_t* __restrict__ row_ptr, int64_t N, int32_t* __restrict__ deg_i,
+                       int32_t* __restrict__ len_i, int32_t* __restrict__ urp) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int u = iperm[i];
+  deg_i[i] = inc_ptr[u + 1] - inc_ptr[u];
+  len_i[i] = row_ptr[u + 1] - row_ptr[u];
+  urp[i] = row_ptr[u];
+}
+
+// Per block of R internal rows: its incidence count and its CSR value count.
+__global__ void k_blk_stats(const int32_t* __restrict__ iinc, const int32_t* __restrict__ irp, int64_t N, int R,
                             int64_t nblk, int* __restrict__ maxes) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nblk) return;
   const int64_t r0 = b * R, r1 = r0 + R < N ? r0 + R : N;
-  atomicMax(maxes + 0, inc_ptr[r1] - inc_ptr[r0]);
-  atomicMax(maxes + 1, row_ptr[r1] - row_ptr[r0]);
+  atomicMax(maxes + 0, iinc[r1] - iinc[r0]);
+  atomicMax(maxes + 1, irp[r1] - irp[r0]);
 }
 
 // One CTA per row block: sort the elements of the block's incidences, keep
 // the distinct ones (written at uq_out[J0 ...], count in bel_cnt), and pack
-// every incidence's record (brec).  P = power of two >= the block's
-// incidences.
-__global__ void __launch_bounds__(256) k_blocks(const int32_t* __restrict__ cells, int nv,
+// every incidence's record (brec, internal incidence order).  P = power of
+// two >= the block's incidences.
+__global__ void __launch_bounds__(256) k_blocks(const int32_t* __restrict__ iperm, const int32_t* __restrict__ iinc,
                                                 const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc_e,
-                                                const uint32_t* __restrict__ inc_pos, int64_t N, int R, int P,
+                                                const uint32_t* __restrict__ inc_pos, int nv, int64_t N, int R, int P,
                                                 int32_t* __restrict__ uq_out, int32_t* __restrict__ bel_cnt,
                                                 uint32_t* __restrict__ brec, int* __restrict__ max_elems) {
   extern __shared__ int sk[];
@@ -234,8 +327,12 @@ __global__ void __launch_bounds__(256) k_blocks(const int32_t* __restrict__ cell
   __shared__ int s_nbe;
   const int64_t b = blockIdx.x;
   const int64_t r0 = b * R, r1 = r0 + R < N ? r0 + R : N;
-  const int J0 = inc_ptr[r0], J1 = inc_ptr[r1], n = J1 - J0;
-  for (int k = threadIdx.x; k < P; k += blockDim.x) key[k] = k < n ? (inc_e[J0 + k] >> 3) : INT32_MAX;
+  const int J0 = iinc[r0], J1 = iinc[r1], n = J1 - J0;
+  for (int k = n + (int)threadIdx.x; k < P; k += blockDim.x) key[k] = INT32_MAX;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const int u = iperm[i], src = inc_ptr[u], dst = iinc[i] - J0, deg = iinc[i + 1] - iinc[i];
+    for (int m = 0; m < deg; ++m) key[dst + m] = inc_e[src + m] >> 3;
+  }
   __syncthreads();
   // bitonic sort, ascending
   for (int k = 2; k <= P; k <<= 1)
@@ -263,39 +360,43 @@ __global__ void __launch_bounds__(256) k_blocks(const int32_t* __restrict__ cell
   __syncthreads();
   const int nbe = s_nbe;
   for (int k = threadIdx.x; k < nbe; k += blockDim.x) uq_out[J0 + k] = uq[k];
-  for (int j = J0 + (int)threadIdx.x; j < J1; j += blockDim.x) {
-    const int e = inc_e[j] >> 3, a = inc_e[j] & 7;
-    int lo = 0, hi = nbe;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (uq[mid] < e) lo = mid + 1;
-      else hi = mid;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const int u = iperm[i], src = inc_ptr[u], dst = iinc[i], deg = iinc[i + 1] - iinc[i];
+    for (int m = 0; m < deg; ++m) {
+      const int e = inc_e[src + m] >> 3, a = inc_e[src + m] & 7;
+      int lo = 0, hi = nbe;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (uq[mid] < e) lo = mid + 1;
+        else hi = mid;
+      }
+      const uint32_t w = inc_pos[src + m];  // 8-bit positions (nv <= 4), each < 16 here
+      uint32_t r = 0;
+      for (int c = 0; c < nv; ++c) r |= ((w >> (8 * c)) & 15u) << (4 * c);
+      brec[dst + m] = r | ((uint32_t)a << (4 * nv)) | ((uint32_t)lo << (4 * nv + 2));
     }
-    const uint32_t w = inc_pos[j];  // 8-bit positions (nv <= 4), each < 16 here
-    uint32_t r = 0;
-    for (int c = 0; c < nv; ++c) r |= ((w >> (8 * c)) & 15u) << (4 * c);
-    brec[j] = r | ((uint32_t)a << (4 * nv)) | ((uint32_t)lo << (4 * nv + 2));
   }
 }
 
 // Element lists of the blocks, at word boff[b] of bel, for a block with
 // nbe = bel_cnt[b] elements, bs = (nbe + 3) & ~3 and bs16 = (nbe + 7) & ~7:
 //   words [0, bs):  the elements, ascending (bit 31: owner block, the block
-//                   of the element's smallest vertex);
+//                   holding the element's vertex of smallest internal row);
 //   then nv rows of bs16 16-bit offsets: vertex c of element k is
 //                   bvbase[b] + row c [k], bvbase[b] the smallest vertex id
 //                   of the block's elements.
 // One CTA per block; a block whose vertex ids span 2^16 or more sets *wide.
 __global__ void __launch_bounds__(128) k_bel(const int32_t* __restrict__ cells, int nv,
-                                             const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ uq,
-                                             const int32_t* __restrict__ bel_cnt, const int64_t* __restrict__ boff,
-                                             int64_t N, int R, int64_t nblk, uint32_t* __restrict__ bel,
-                                             int32_t* __restrict__ bvbase, int* __restrict__ wide) {
+                                             const int32_t* __restrict__ iinc, const int32_t* __restrict__ ipos,
+                                             const int32_t* __restrict__ uq, const int32_t* __restrict__ bel_cnt,
+                                             const int64_t* __restrict__ boff, int64_t N, int R, int64_t nblk,
+                                             uint32_t* __restrict__ bel, int32_t* __restrict__ bvbase,
+                                             int* __restrict__ wide) {
   __shared__ int s_min, s_max;
   const int64_t b = blockIdx.y * (int64_t)gridDim.x + blockIdx.x;
   if (b >= nblk) return;
   const int nbe = bel_cnt[b], bs = (nbe + 3) & ~3, bs16 = (nbe + 7) & ~7;
-  const int J0 = inc_ptr[b * R];
+  const int J0 = iinc[b * R];
   if (threadIdx.x == 0) {
     s_min = INT32_MAX;
     s_max = INT32_MIN;
@@ -320,13 +421,13 @@ __global__ void __launch_bounds__(128) k_bel(const int32_t* __restrict__ cells, 
       continue;
     }
     const int e = uq[J0 + k];
-    int vmin = INT32_MAX;
+    int pmin = INT32_MAX;
     for (int a = 0; a < nv; ++a) {
       const int v = cells[(int64_t)e * nv + a];
       o16[a * bs16 + k] = (uint16_t)(v - vb);
-      vmin = min(vmin, v);
+      pmin = min(pmin, ipos[v]);
     }
-    out[k] = (uint32_t)e | ((int64_t)vmin / R == b ? 0x80000000u : 0u);
+    out[k] = (uint32_t)e | ((int64_t)pmin / R == b ? 0x80000000u : 0u);
   }
 }
 
@@ -427,10 +528,50 @@ tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
   if (p->max_row_len > (1 << pb)) return TG_OK;
   const int le_bits = 32 - nv * pb - 2;
   Tmp tmp;
+  // internal row order: nodes by smallest incident element, isolated nodes
+  // last, each block of R rows in ascending node id
+  int32_t *key = nullptr, *iso = nullptr, *cnt_e = nullptr, *order = nullptr, *ipos = nullptr;
+  int64_t *off = nullptr, *iso_rank = nullptr, *tmp64 = nullptr;
+  TG_CK(tmp.alloc(&key, N));
+  TG_CK(tmp.alloc(&iso, N));
+  TG_CK(tmp.alloc(&cnt_e, E));
+  TG_CK(tmp.alloc(&order, N));
+  TG_CK(tmp.alloc(&ipos, N));
+  TG_CK(tmp.alloc(&off, E + 1));
+  TG_CK(tmp.alloc(&iso_rank, N + 1));
+  TG_CK(tmp.alloc(&tmp64, N + 1));
+  k_row_key<<<tg::grid_for(N, kThreads), kThreads, 0, s>>>(p->inc_ptr, p->inc_e, N, E, key, iso);
+  k_key_count<<<tg::grid_for(E, kThreads), kThreads, 0, s>>>(p->cells, nv, E, key, cnt_e);
+  TG_CK_LAUNCH("k_key_count");
+  tg_status st = scan_exclusive<int32_t>(cnt_e, off, E, s);
+  if (st != TG_OK) return st;
+  k_key_place<<<tg::grid_for(E, kThreads), kThreads, 0, s>>>(p->cells, nv, E, key, off, order);
+  TG_CK_LAUNCH("k_key_place");
+  if ((st = scan_exclusive<int32_t>(iso, iso_rank, N, s)) != TG_OK) return st;
+  int64_t base = 0;
+  TG_CK(cudaMemcpyAsync(&base, off + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  k_iso_place<<<tg::grid_for(N, kThreads), kThreads, 0, s>>>(iso, iso_rank, N, base, order);
+  TG_CK_LAUNCH("k_iso_place");
+  TG_CK(cudaMalloc(&p->iperm, N * sizeof(int32_t) + 16));
+  TG_CK(cudaMalloc(&p->urp, N * sizeof(int32_t) + 16));
+  TG_CK(cudaMalloc(&p->iinc, (N + 1) * sizeof(int32_t) + 16));
+  TG_CK(cudaMalloc(&p->irp, (N + 1) * sizeof(int32_t) + 16));
+  k_blk_sort<<<(unsigned)nblk, 128, 0, s>>>(order, N, R, p->iperm, ipos);
+  TG_CK_LAUNCH("k_blk_sort");
+  int32_t *deg_i = key, *len_i = iso;  // reuse
+  k_irow<<<tg::grid_for(N, kThreads), kThreads, 0, s>>>(p->iperm, p->inc_ptr, p->row_ptr, N, deg_i, len_i, p->urp);
+  TG_CK_LAUNCH("k_irow");
+  if ((st = scan_exclusive<int32_t>(deg_i, tmp64, N, s)) != TG_OK) return st;
+  k_narrow<<<tg::grid_for(N + 1, kThreads), kThreads, 0, s>>>(tmp64, p->iinc, N + 1);
+  TG_CK_LAUNCH("k_narrow");
+  if ((st = scan_exclusive<int32_t>(len_i, tmp64, N, s)) != TG_OK) return st;
+  k_narrow<<<tg::grid_for(N + 1, kThreads), kThreads, 0, s>>>(tmp64, p->irp, N + 1);
+  TG_CK_LAUNCH("k_narrow");
   int* maxes = nullptr;
   TG_CK(tmp.alloc(&maxes, 3));
   TG_CK(cudaMemsetAsync(maxes, 0, 3 * sizeof(int), s));
-  k_blk_stats<<<tg::grid_for(nblk, kThreads), kThreads, 0, s>>>(p->inc_ptr, p->row_ptr, N, R, nblk, maxes);
+  k_blk_stats<<<tg::grid_for(nblk, kThreads), kThreads, 0, s>>>(p->iinc, p->irp, N, R, nblk, maxes);
   TG_CK_LAUNCH("k_blk_stats");
   int h[3];
   TG_CK(cudaMemcpyAsync(h, maxes, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -447,8 +588,8 @@ tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
   p->bel_cnt = cnt;  // owned by the pattern from here on
   TG_CK(cudaMalloc(&p->brec, nvE * sizeof(uint32_t) + 16));
   TG_CK(cudaMemsetAsync(p->brec, 0, nvE * sizeof(uint32_t) + 16, s));
-  k_blocks<<<(unsigned)nblk, 256, 2 * P * sizeof(int), s>>>(p->cells, nv, p->inc_ptr, p->inc_e, p->inc_pos, N, R, P,
-                                                             uq, cnt, p->brec, maxes + 2);
+  k_blocks<<<(unsigned)nblk, 256, 2 * P * sizeof(int), s>>>(p->iperm, p->iinc, p->inc_ptr, p->inc_e, p->inc_pos, nv,
+                                                             N, R, P, uq, cnt, p->brec, maxes + 2);
   TG_CK_LAUNCH("k_blocks");
   TG_CK(cudaMemcpyAsync(h + 2, maxes + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
   TG_CK(cudaStreamSynchronize(s));
@@ -458,8 +599,7 @@ tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
   TG_CK(tmp.alloc(&words, nblk));
   k_bel_words<<<tg::grid_for(nblk, kThreads), kThreads, 0, s>>>(cnt, nblk, nv, words);
   TG_CK_LAUNCH("k_bel_words");
-  tg_status st = scan_exclusive<int32_t>(words, boff, nblk, s);
-  if (st != TG_OK) return st;
+  if ((st = scan_exclusive<int32_t>(words, boff, nblk, s)) != TG_OK) return st;
   int64_t total = 0;
   TG_CK(cudaMemcpyAsync(&total, boff + nblk, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   TG_CK(cudaStreamSynchronize(s));
@@ -470,7 +610,7 @@ tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
   int* wide = maxes;  // reuse: maxima already read back
   TG_CK(cudaMemsetAsync(wide, 0, sizeof(int), s));
   const unsigned gx = (unsigned)std::min<int64_t>(nblk, 65535), gy = (unsigned)((nblk + gx - 1) / gx);
-  k_bel<<<dim3(gx, gy), 128, 0, s>>>(p->cells, nv, p->inc_ptr, uq, cnt, p->boff, N, R, nblk, p->bel, p->bvbase,
+  k_bel<<<dim3(gx, gy), 128, 0, s>>>(p->cells, nv, p->iinc, ipos, uq, cnt, p->boff, N, R, nblk, p->bel, p->bvbase,
                                       wide);
   TG_CK_LAUNCH("k_bel");
   int hw = 0;

@@ -37,17 +37,22 @@ struct tg_pattern {
   int32_t* elem_slot = nullptr;
   int32_t* row_ptr3 = nullptr;
   int32_t* col_idx3 = nullptr;
-  // Row blocks of the element-once P1 kernels (P1 triangles and tetrahedra,
-  // built when the packed fields fit; bel == NULL otherwise).  Block b owns
-  // the rows [b*blk_rows, (b+1)*blk_rows) and hence the incidences
-  // [J0, J1) = [inc_ptr[b*blk_rows], inc_ptr[min((b+1)*blk_rows, N)]).
+  // Row blocks of the element-once P1 kernels (P1 triangles, tetrahedra and
+  // vector elasticity, built when the packed fields fit; bel == NULL
+  // otherwise).  The kernels walk the rows in an internal order: iperm[i] is
+  // the node of internal row i (nodes by smallest incident element, then
+  // each block of blk_rows rows in ascending node id); iinc and irp are the
+  // incidence and CSR-value prefix sums in that order, urp[i] =
+  // row_ptr[iperm[i]].  Block b owns the internal rows [b*blk_rows,
+  // (b+1)*blk_rows) and hence the internal incidences [J0, J1) =
+  // [iinc[b*blk_rows], iinc[min((b+1)*blk_rows, N)]).
   //   bel + boff[b]: the block's distinct elements (nbe = bel_cnt[b] of
   //     them, ascending): (nbe + 3) & ~3 words of element ids (bit 31 set in
   //     the one block that owns the element, the block of its smallest
   //     vertex), then nv rows of (nbe + 7) & ~7 16-bit vertex offsets from
   //     bvbase[b] (built only when every block's vertex ids span < 2^16).
   //   brec[j], j in [J0, J1), per incidence (row i, element e, local vertex
-  //     a), in the order of inc_e:  4-bit fields [4b, 4b+4) the position of
+  //     a), rows in internal order, each row's incidences in element order:  4-bit fields [4b, 4b+4) the position of
   //     vertex b's column in row i (b < nv), then a (2 bits), then the local
   //     index of e in the block's list (the rest).
   //   elem_pos[e] (64 bit): position of vertex b's column in vertex a's row
@@ -55,6 +60,10 @@ struct tg_pattern {
   int blk_rows = 0, blk_pb = 0;
   int blk_max_elems = 0, blk_max_inc = 0, blk_max_nz = 0;  // per-block maxima
   int64_t n_blk = 0;
+  int32_t* iperm = nullptr;
+  int32_t* urp = nullptr;
+  int32_t* iinc = nullptr;
+  int32_t* irp = nullptr;
   uint32_t* bel = nullptr;
   int64_t* boff = nullptr;
   int32_t* bvbase = nullptr;
