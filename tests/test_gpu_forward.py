@@ -225,6 +225,39 @@ def test_single_element_each_kind(tg):
         assert relfro(v.cpu().numpy(), ref.val) <= 1e-14
 
 
+@pytest.mark.parametrize("el", [mg.P1_TRI, mg.P1_TET])
+def test_isolated_nodes_and_shuffled_numbering(tg, el):
+    """Nodes that no element uses (zero rows, zero load, zero gradient) and a
+    random node numbering (the row blocks' internal order then differs from
+    the node order everywhere) match the oracle."""
+    m = mesh_for(el)
+    g = np.random.default_rng(90)
+    n_iso = 37
+    N = m.n_nodes + n_iso
+    relabel = g.permutation(N)[:m.n_nodes]  # used nodes get random ids; the rest are isolated
+    cells = relabel[m.cells]
+    X = np.zeros((N, m.coords.shape[1]))
+    X[relabel] = m.coords
+    X[np.setdiff1d(np.arange(N), relabel)] = g.uniform(0, 1, size=(n_iso, m.coords.shape[1]))
+    nq = mg.NQ[el]
+    k = coef(mg.PER_QP, len(cells), nq, seed=91)
+    f = g.uniform(-1, 1, N)
+    p = tg.tg_build_pattern(dev(cells, torch.int32), N, el)
+    x = dev(X, torch.float64)
+    vals, F = tg.tg_assemble_system(p, x, dev(k, torch.float64), mg.PER_QP, 0.3, dev(f, torch.float64), mg.PER_NODE)
+    ref = O.assemble_bilinear(el, cells, X, k, O.PER_QP, 0.3)
+    assert np.array_equal(p.row_ptr.cpu().numpy(), ref.row_ptr) and np.array_equal(p.col_idx.cpu().numpy(), ref.col)
+    assert relfro(vals.cpu().numpy(), ref.val) <= 1e-12
+    assert relfro(F.cpu().numpy(), O.assemble_load(el, cells, X, f, O.PER_NODE)) <= 1e-12
+    gv = g.normal(size=p.nnz)
+    gk, gx, gc = tg.tg_assemble_backward(p, x, dev(k, torch.float64), mg.PER_QP, 0.3, grad_vals=dev(gv, torch.float64))
+    rk, rx, rc = O.assemble_backward(el, cells, X, k, O.PER_QP, 0.3, grad_csr=O.CSR(ref.row_ptr, ref.col, gv))
+    assert relfro(gk.cpu().numpy(), rk) <= 1e-12 and relfro(gx.cpu().numpy(), rx) <= 1e-12
+    assert relfro(gc.cpu().numpy(), [rc]) <= 1e-12
+    iso = np.setdiff1d(np.arange(N), relabel)
+    assert np.all(F.cpu().numpy()[iso] == 0) and np.all(gx.cpu().numpy()[iso] == 0)
+
+
 def test_degenerate_element_is_flagged(tg):
     m = mg.tri_grid(8)  # dyadic coordinates: the collinear triangle has det exactly 0
     X = m.coords.copy()
