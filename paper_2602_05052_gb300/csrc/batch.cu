@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(BSZ) k_batch(const InstDesc* __restrict__ desc
     a.out = call.vals[k];
     a.n = d.N;
     a.status = d.status;
-    for (int64_t r = w.y; r < w.z; r += BSZ) tg::assemble_block<EL, T>(a, ts, buf, cap, r, r + BSZ < w.z ? r + BSZ : w.z);
+    for (int64_t r = w.y; r < w.z; r += BSZ) tg::assemble_block<EL, T>(a, ts, tab, buf, cap, r, r + BSZ < w.z ? r + BSZ : w.z);
   }
 }
 

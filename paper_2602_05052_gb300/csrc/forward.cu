@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(BS) k_bilinear_gather(const FwdArgs<T> a, cons
   copy_table(ts, tab);
   const int64_t r0 = (int64_t)blockIdx.x * blockDim.x;
   const int64_t r1 = r0 + blockDim.x < a.n ? r0 + blockDim.x : a.n;
-  tg::assemble_rows<EL, T>(a, ts, smem + tab_bytes<T>(), cap, r0, r1);
+  tg::assemble_rows<EL, T>(a, ts, tab, smem + tab_bytes<T>(), cap, r0, r1);
 }
 
 
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(BS) k_bilinear_atomic(const FwdArgs<T> a, cons
 #pragma unroll 1
   for (int la = 0; la < El::nv; ++la) {
     T Krow[El::nv];
-    if (!scalar_row<EL, T>(a, ts, e, la, Krow)) {
+    if (!scalar_row<EL, T>(a, ts, tab, e, la, Krow)) {
       tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
       return;
     }

@@ -166,7 +166,7 @@ __device__ __forceinline__ T p1_load_entry(int layout, T adet, const T (&fv)[NV]
 // Row la of the local matrix from loaded inputs; false for a degenerate
 // element.  Same arithmetic, operation for operation, as scalar_row.
 template <int EL, typename T>
-__device__ __forceinline__ bool elem_row(const ElemIn<EL, T>& in, T c, const RefTab<T>& ts, int la,
+__device__ __forceinline__ bool elem_row(const ElemIn<EL, T>& in, T c, const RefTab<T>& ts, const RefTab<T>& tc, int la,
                                          T (&Krow)[Elem<EL>::nv]) {
   if constexpr (EL == TG_P1_TRI || EL == TG_P2_TRI) {
     Geom<2, T> g;
@@ -178,7 +178,7 @@ __device__ __forceinline__ bool elem_row(const ElemIn<EL, T>& in, T c, const Ref
       p1_scales<3, T>(in.kq, ts, adet, c, sc, mc);
       p1_row<2, T>(g, la, sc, mc, ts.M[la], Krow);
     } else {
-      p2_row<T>(g, la, in.kq, T(1) / adet, c * adet, ts, Krow);
+      p2_row<T>(g, la, in.kq, T(1) / adet, c * adet, ts, tc, Krow);
     }
   } else {
     Geom<3, T> g;
@@ -216,12 +216,12 @@ __device__ __forceinline__ bool p1_elem_sym(const ElemIn<EL, T>& in, T c, const 
 
 // Local row la of element e for the scalar form; false for a degenerate element.
 template <int EL, typename T>
-__device__ __forceinline__ bool scalar_row(const FwdArgs<T>& a, const RefTab<T>& ts, int64_t e, int la,
+__device__ __forceinline__ bool scalar_row(const FwdArgs<T>& a, const RefTab<T>& ts, const RefTab<T>& tc, int64_t e, int la,
                                            T (&Krow)[Elem<EL>::nv]) {
   ElemIn<EL, T> in;
   elem_ids<EL, T>(a, e, in);
   elem_data<EL, T>(a, e, in);
-  return elem_row<EL, T>(in, a.c, ts, la, Krow);
+  return elem_row<EL, T>(in, a.c, ts, tc, la, Krow);
 }
 
 // Accumulate and store CSR rows.
@@ -286,7 +286,7 @@ __host__ __device__ constexpr int ub_of() {
 }
 
 template <int EL, typename T>
-__device__ __forceinline__ void assemble_rows(const FwdArgs<T>& a, const RefTab<T>& ts, unsigned char* buf, int cap,
+__device__ __forceinline__ void assemble_rows(const FwdArgs<T>& a, const RefTab<T>& ts, const RefTab<T>& tc, unsigned char* buf, int cap,
                                               int64_t r0, int64_t r1) {
   using El = Elem<EL>;
   constexpr int NV = El::nv, NPW = El::npw;
@@ -320,7 +320,7 @@ __device__ __forceinline__ void assemble_rows(const FwdArgs<T>& a, const RefTab<
       const int j = base + u * R;
       if (j < J1) {
         T Krow[NV];
-        if (!elem_row<EL, T>(in[u], a.c, ts, ea[u] & 7, Krow)) {
+        if (!elem_row<EL, T>(in[u], a.c, ts, tc, ea[u] & 7, Krow)) {
           record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, ea[u] >> 3);
 #pragma unroll
           for (int b = 0; b < NV; ++b) Krow[b] = T(0);
@@ -336,9 +336,9 @@ __device__ __forceinline__ void assemble_rows(const FwdArgs<T>& a, const RefTab<
 
 // One row block of the batched kernel.
 template <int EL, typename T>
-__device__ __forceinline__ void assemble_block(const FwdArgs<T>& a, const RefTab<T>& ts, unsigned char* buf, int cap,
+__device__ __forceinline__ void assemble_block(const FwdArgs<T>& a, const RefTab<T>& ts, const RefTab<T>& tc, unsigned char* buf, int cap,
                                                int64_t r0, int64_t r1) {
-  assemble_rows<EL, T>(a, ts, buf, cap, r0, r1);
+  assemble_rows<EL, T>(a, ts, tc, buf, cap, r0, r1);
 }
 
 // Host: reference tables of each element kind, built once per process.
