@@ -309,7 +309,11 @@ tg_status tg_batch_assemble(tg_batch* b, tg_dtype dtype, const void* const* coor
                             tg_layout kappa_layout, const double* c, void* const* vals_out, tg_stream stream);
 
 /* The schedule of the persistent launch: threads per CTA, rows per work
- * item (a multiple of the thread count), CTAs per SM (0 = as many as fit). */
+ * item (a multiple of the thread count), CTAs per SM (0 = as many as fit).
+ * When every instance's pattern has element-once row blocks (the element
+ * kinds and meshes the single-instance element-once kernels take), the
+ * batch walks (instance, row block) items with 128-thread CTAs and only
+ * ctas_per_sm applies. */
 tg_status tg_batch_set_schedule(tg_batch* b, int32_t threads, int32_t rows_per_item, int32_t ctas_per_sm);
 tg_status tg_batch_get_schedule(const tg_batch* b, int32_t* threads, int32_t* rows_per_item,
                                 int32_t* ctas_per_sm);

@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(BB, (D == 2 && sizeof(T) == 4) ? (UB >= 3 ? 5 
       for (int r = 0; r < D; ++r) gs[r] = T(0);
       const int je = v.ip[i + 1];
       for (int j = v.ip[i]; j < je; ++j) {
-        const tg::BlkRec<NV> rr{v.rc[j]};
+        const auto rr = tg::blk_rec<NV>(v.rc, j);
         const T* gp = Gx + rr.a() * D * g.capE + rr.le();
 #pragma unroll
         for (int r = 0; r < D; ++r) gs[r] += gp[r * g.capE];
@@ -729,7 +729,7 @@ __global__ void __launch_bounds__(BB) k_elastic_backward_blk(const ElBwdArgs<T> 
       T gs[3] = {T(0), T(0), T(0)};
       const int je = v.ip[i + 1];
       for (int j = v.ip[i]; j < je; ++j) {
-        const tg::BlkRec<4> rr{v.rc[j]};
+        const auto rr = tg::blk_rec<4>(v.rc, j);
         const T* gp = Gx + rr.a() * 3 * g.capE + rr.le();
 #pragma unroll
         for (int r = 0; r < 3; ++r) gs[r] += gp[r * g.capE];

@@ -18,7 +18,7 @@
 #include <string>
 #include <vector>
 
-#include "gather.cuh"
+#include "blk_bilinear.cuh"
 
 namespace {
 
@@ -75,6 +75,77 @@ __global__ void __launch_bounds__(BSZ) k_batch(const InstDesc* __restrict__ desc
   }
 }
 
+// Block mode (every instance has element-once row blocks): one work item per
+// (instance, row block), the same Map and Reduce as the single-instance
+// kernel (blk_bilinear.cuh) on block views that read the pattern arrays in
+// global memory.  Results are bitwise those of tg_assemble_bilinear.
+struct InstBlk {
+  const int32_t* iinc;
+  const int32_t* irp;
+  const int32_t* urp;
+  const int32_t* iperm;
+  const uint32_t* bel;
+  const int64_t* boff;
+  const int32_t* bvbase;
+  const int32_t* bel_cnt;
+  const uint32_t* brec;
+  int64_t N;
+  int R;
+  unsigned long long* status;
+};
+
+template <int EL, typename T, int UB>
+__global__ void __launch_bounds__(128) k_batch_blk(const InstBlk* __restrict__ desc, const int2* __restrict__ items,
+                                                   int64_t n_items, const __grid_constant__ BatchCall<T> call,
+                                                   const __grid_constant__ tg::RefTab<T> tab, int capE, int cap_nz) {
+  constexpr int NV = tg::Elem<EL>::nv;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* Ke = reinterpret_cast<T*>(smem);
+  T* acc = Ke + (size_t)NV * NV * capE;
+  for (int q = threadIdx.x; q < cap_nz; q += blockDim.x) acc[q] = T(0);
+  __syncthreads();
+  for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int2 w = items[it];
+    const InstBlk d = desc[w.x];
+    const int k = w.x - call.inst0;
+    tg::FwdArgs<T> a;
+    a.row_ptr = nullptr;
+    a.inc_ptr = nullptr;
+    a.inc_e = nullptr;
+    a.inc_pos = nullptr;
+    a.cells = nullptr;
+    a.elem_slot = nullptr;
+    a.coords = call.coords[k];
+    a.coef = call.kappa[k];
+    a.coef2 = nullptr;
+    a.layout = call.layout;
+    a.c = call.c[k];
+    a.out = call.vals[k];
+    a.n = d.N;
+    a.status = d.status;
+    a.f = nullptr;
+    a.f_layout = 0;
+    a.F = nullptr;
+    tg::BlkView v;
+    const int64_t r0 = (int64_t)w.y * d.R;
+    v.r0 = (int)r0;
+    v.r1 = (int)(r0 + d.R < d.N ? r0 + d.R : d.N);
+    v.J0 = d.iinc[v.r0];
+    v.J1 = d.iinc[v.r1];
+    v.nbe = d.bel_cnt[w.y];
+    v.vbase = d.bvbase[w.y];
+    v.bs16 = (v.nbe + 7) & ~7;
+    v.ip = d.iinc;
+    v.rp = d.irp;
+    v.up = d.urp;
+    v.pm = d.iperm;
+    v.rc = d.brec;
+    v.be = d.bel + d.boff[w.y];
+    v.vo = reinterpret_cast<const uint16_t*>(v.be + ((v.nbe + 3) & ~3));
+    tg::blk_bilinear_block<EL, T, UB, false>(a, tab, capE, v, Ke, nullptr, acc);
+  }
+}
+
 struct Sched {
   int threads, rows_per_item, ctas_per_sm;
 };
@@ -96,6 +167,12 @@ struct tg_batch {
   int4* d_items = nullptr;
   std::vector<int64_t> chunk_items;  // item range of each chunk of kMaxInst instances
   Sched sched{128, 512, 0};
+  // block mode (all instances have row blocks)
+  bool blk = false;
+  InstBlk* d_blk = nullptr;
+  int2* d_blk_items = nullptr;
+  std::vector<int64_t> blk_chunk_items;
+  int capE = 0, cap_nz = 0, max_elems = 0;
 };
 
 namespace {
@@ -163,9 +240,74 @@ tg_status launch_el(tg_batch* b, const void* const* coords, const void* const* k
   }
 }
 
+template <int EL, typename T, int UB>
+tg_status launch_blk_t(tg_batch* b, const void* const* coords, const void* const* kappa, tg_layout kl, const double* c,
+                       void* const* vals, cudaStream_t s) {
+  constexpr int NV = tg::Elem<EL>::nv;
+  auto kern = k_batch_blk<EL, T, UB>;
+  const size_t smem = ((size_t)NV * NV * b->capE + b->cap_nz) * sizeof(T);
+  tg_status st = tg::set_smem((const void*)kern, smem);
+  if (st != TG_OK) return st;
+  int per_sm = b->sched.ctas_per_sm;
+  if (per_sm <= 0) {
+    TG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem));
+    per_sm = std::max(per_sm, 1);
+  }
+  const tg::RefTab<T>& tab = tg::table<T>(b->el);
+  const size_t nchunks = b->blk_chunk_items.size() - 1;
+  for (size_t ch = 0; ch < nchunks; ++ch) {
+    BatchCall<T> call;
+    std::memset(&call, 0, sizeof(call));
+    call.inst0 = (int)(ch * kMaxInst);
+    call.layout = kl;
+    const int n = std::min(kMaxInst, b->n_inst - call.inst0);
+    for (int k = 0; k < n; ++k) {
+      call.coords[k] = static_cast<const T*>(coords[call.inst0 + k]);
+      call.kappa[k] = static_cast<const T*>(kappa[call.inst0 + k]);
+      call.vals[k] = static_cast<T*>(vals[call.inst0 + k]);
+      call.c[k] = (T)c[call.inst0 + k];
+    }
+    const int64_t i0 = b->blk_chunk_items[ch], n_items = b->blk_chunk_items[ch + 1] - i0;
+    if (n_items == 0) continue;
+    const int grid = (int)std::min<int64_t>(n_items, (int64_t)per_sm * tg::sm_count());
+    kern<<<grid, 128, smem, s>>>(b->d_blk, b->d_blk_items + i0, n_items, call, tab, b->capE, b->cap_nz);
+    TG_CK_LAUNCH("k_batch_blk");
+  }
+  return TG_OK;
+}
+
+// UB as the single-instance kernel picks it for the largest block
+template <typename T>
+tg_status launch_blk(tg_batch* b, const void* const* coords, const void* const* kappa, tg_layout kl, const double* c,
+                     void* const* vals, cudaStream_t s) {
+  const int need = (b->max_elems + 127) / 128;
+  switch (b->el) {
+    case TG_P2_TRI:
+      return need <= 1 ? launch_blk_t<TG_P2_TRI, T, 1>(b, coords, kappa, kl, c, vals, s)
+                       : launch_blk_t<TG_P2_TRI, T, 2>(b, coords, kappa, kl, c, vals, s);
+    case TG_P1_TRI:
+      if constexpr (sizeof(T) == 8) {
+        return need <= 2 ? launch_blk_t<TG_P1_TRI, T, 2>(b, coords, kappa, kl, c, vals, s)
+                         : launch_blk_t<TG_P1_TRI, T, 3>(b, coords, kappa, kl, c, vals, s);
+      } else {
+        return need <= 3 ? launch_blk_t<TG_P1_TRI, T, 3>(b, coords, kappa, kl, c, vals, s)
+                         : launch_blk_t<TG_P1_TRI, T, 6>(b, coords, kappa, kl, c, vals, s);
+      }
+    default:
+      if constexpr (sizeof(T) == 8) {
+        return need <= 2 ? launch_blk_t<TG_P1_TET, T, 2>(b, coords, kappa, kl, c, vals, s)
+                         : launch_blk_t<TG_P1_TET, T, 3>(b, coords, kappa, kl, c, vals, s);
+      } else {
+        return need <= 4 ? launch_blk_t<TG_P1_TET, T, 4>(b, coords, kappa, kl, c, vals, s)
+                         : launch_blk_t<TG_P1_TET, T, 6>(b, coords, kappa, kl, c, vals, s);
+      }
+  }
+}
+
 template <typename T>
 tg_status launch(tg_batch* b, const void* const* coords, const void* const* kappa, tg_layout kl, const double* c,
                  void* const* vals, cudaStream_t s) {
+  if (b->blk) return launch_blk<T>(b, coords, kappa, kl, c, vals, s);
   switch (b->sched.threads) {
     case 64: return launch_el<T, 64>(b, coords, kappa, kl, c, vals, s);
     case 256: return launch_el<T, 256>(b, coords, kappa, kl, c, vals, s);
@@ -185,14 +327,49 @@ tg_status check_call(const tg_batch* b, tg_dtype dtype, const void* const* coord
   return TG_OK;
 }
 
+// Block mode when every instance has element-once row blocks that fit the
+// shared-memory budget: descriptors and the (instance, block) item list.
+tg_status setup_blocks(tg_batch* b) {
+  const int nv = tg::nv_of(b->el);
+  int capE = 0, cap_nz = 0, max_elems = 0;
+  for (const tg_pattern* p : b->pats) {
+    if (p->E > 0 && !p->bel) return TG_OK;  // stays in row-range mode
+    capE = std::max(capE, (p->blk_max_elems + 3) & ~3);
+    cap_nz = std::max(cap_nz, p->blk_max_nz);
+    max_elems = std::max(max_elems, p->blk_max_elems);
+  }
+  if (((size_t)nv * nv * capE + cap_nz) * 8 > 113 * 1024) return TG_OK;
+  std::vector<InstBlk> h(b->n_inst);
+  std::vector<int2> items;
+  b->blk_chunk_items.assign(1, 0);
+  for (int i = 0; i < b->n_inst; ++i) {
+    const tg_pattern* p = b->pats[i];
+    h[i] = InstBlk{p->iinc, p->irp, p->urp, p->iperm, p->bel, p->boff, p->bvbase, p->bel_cnt, p->brec,
+                   p->N, p->blk_rows, p->status};
+    if (p->E > 0)
+      for (int64_t k = 0; k < p->n_blk; ++k) items.push_back(make_int2(i, (int)k));
+    if ((i + 1) % kMaxInst == 0 || i + 1 == b->n_inst) b->blk_chunk_items.push_back((int64_t)items.size());
+  }
+  TG_CK(cudaMalloc(&b->d_blk, b->n_inst * sizeof(InstBlk)));
+  TG_CK(cudaMemcpy(b->d_blk, h.data(), b->n_inst * sizeof(InstBlk), cudaMemcpyHostToDevice));
+  TG_CK(cudaMalloc(&b->d_blk_items, std::max<size_t>(items.size(), 1) * sizeof(int2)));
+  if (!items.empty())
+    TG_CK(cudaMemcpy(b->d_blk_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  b->capE = capE;
+  b->cap_nz = cap_nz;
+  b->max_elems = max_elems;
+  b->blk = true;
+  return TG_OK;
+}
+
 std::string cache_key(const tg_batch* b, tg_dtype dtype) {
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, b->device);
   int bucket = 0;
   for (int64_t r = b->total_rows; r > 1; r >>= 1) ++bucket;
   char buf[256];
-  std::snprintf(buf, sizeof(buf), "%s|el%d|dt%d|rows2^%d|inst%d", prop.name, (int)b->el, (int)dtype, bucket,
-                b->n_inst);
+  std::snprintf(buf, sizeof(buf), "%s|el%d|dt%d|rows2^%d|inst%d|blk%d", prop.name, (int)b->el, (int)dtype, bucket,
+                b->n_inst, b->blk ? 1 : 0);
   return buf;
 }
 
@@ -229,6 +406,7 @@ tg_status tg_batch_create(const tg_pattern* const* pats, int32_t n_inst, tg_batc
     return tg::cuda_fail(e, "tg_batch_create", __FILE__, __LINE__);
   }
   tg_status st = build_items(b);
+  if (st == TG_OK) st = setup_blocks(b);
   if (st != TG_OK) {
     tg_batch_destroy(b);
     return st;
@@ -279,10 +457,14 @@ tg_status tg_batch_autotune(tg_batch* b, tg_dtype dtype, const void* const* coor
     }
   }
   std::vector<Sched> cands;
-  for (int t : {64, 128, 256})
-    for (int m : {1, 2, 4, 8, 16})
-      for (int cps : {0, 2})
-        cands.push_back(Sched{t, t * m, cps});
+  if (b->blk) {  // block mode: only the resident CTAs per SM apply
+    for (int cps : {0, 2, 3, 4, 6}) cands.push_back(Sched{128, 128, cps});
+  } else {
+    for (int t : {64, 128, 256})
+      for (int m : {1, 2, 4, 8, 16})
+        for (int cps : {0, 2})
+          cands.push_back(Sched{t, t * m, cps});
+  }
   cudaEvent_t e0, e1;
   TG_CK(cudaEventCreate(&e0));
   TG_CK(cudaEventCreate(&e1));
@@ -327,6 +509,8 @@ void tg_batch_destroy(tg_batch* b) {
   if (!b) return;
   if (b->d_desc) cudaFree(b->d_desc);
   if (b->d_items) cudaFree(b->d_items);
+  if (b->d_blk) cudaFree(b->d_blk);
+  if (b->d_blk_items) cudaFree(b->d_blk_items);
   delete b;
 }
 

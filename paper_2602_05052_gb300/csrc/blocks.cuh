@@ -42,6 +42,7 @@ struct BlkArgs {
   int capE16;      // capE rounded up to a multiple of 8 (16-bit vertex rows)
   int nv;          // vertices per element
   int R;           // rows per block (at most the CTA's threads)
+  int rw;          // 32-bit words per incidence record (1; 2 for P2)
 };
 
 // Host: BlkArgs of a pattern with row blocks.
@@ -63,13 +64,15 @@ inline BlkArgs blk_args(const tg_pattern* p) {
   g.capE16 = (p->blk_max_elems + 7) & ~7;
   g.nv = p->nv;
   g.R = p->blk_rows;
+  g.rw = p->nv > 4 ? 2 : 1;
   return g;
 }
 
 // Shared-memory bytes of the two stages plus barriers and block metadata.
 __host__ __device__ inline size_t blk_stage_bytes(int R, int capJ, int capE, int nv) {
   const size_t el_words = (size_t)capE + (size_t)nv * (((capE + 7) & ~7) / 2);
-  return 16 + 128 + 2 * ((size_t)(R + 8) * 16 + (size_t)(capJ + 8) * 4 + el_words * 4);
+  const size_t rw = nv > 4 ? 2 : 1;
+  return 16 + 128 + 2 * ((size_t)(R + 8) * 16 + ((size_t)capJ * rw + 8) * 4 + el_words * 4);
 }
 
 // Geometry of one row block as seen through its stage.
@@ -81,7 +84,7 @@ struct BlkView {
   const int* rp;       // rp[i]: internal CSR-value prefix (rp[i] - rp[r0] = offset in the block)
   const int* up;       // up[i]: CSR start of internal row i's node, i in [r0, r1)
   const int* pm;       // pm[i]: node of internal row i
-  const uint32_t* rc;  // rc[j] = brec[j], j in [J0, J1)
+  const uint32_t* rc;  // rc[j * rw ...] = record j, j in [J0, J1)
   const uint32_t* be;  // be[k]: element k (with the owner bit), k < nbe
   const uint16_t* vo;  // vo[c * bs16 + k]: vertex c of element k, minus vbase
   __device__ int vtx(int c, int k) const { return vbase + (int)vo[c * bs16 + k]; }
@@ -95,7 +98,7 @@ class BlkPipe {
   __device__ unsigned char* init(unsigned char* p, const BlkArgs& g) {
     R_ = g.R;
     IPN_ = R_ + 8;
-    RECN_ = g.capJ + 8;
+    RECN_ = g.capJ * g.rw + 8;
     ELN_ = g.capE + g.nv * (g.capE16 / 2);
     SW_ = 4 * IPN_ + RECN_ + ELN_;  // words per stage (a multiple of 4)
     bar_ = reinterpret_cast<uint64_t*>(p);
@@ -132,7 +135,7 @@ class BlkPipe {
   __device__ void issue(const BlkArgs& g, int s, int64_t blk, const Peek& q) {
     const int r0 = (int)(blk * R_), r1 = (int)(blk * R_ + R_ < g.N ? blk * R_ + R_ : g.N);
     const int a0 = r0 & ~3, nip = (r1 + 1 - a0 + 3) & ~3;
-    const int j0a = q.J0 & ~3, nrec = (q.J1 - j0a + 3) & ~3;
+    const int j0a = q.J0 & ~(4 / g.rw - 1), nrec = ((q.J1 - j0a) * g.rw + 3) & ~3;
     const int nel = ((q.nbe + 3) & ~3) + g.nv * (((q.nbe + 7) & ~7) / 2);
     int* m = meta_ + 16 * s;
     m[0] = r0;
@@ -140,7 +143,7 @@ class BlkPipe {
     m[2] = q.J0;
     m[3] = q.J1;
     m[4] = a0;
-    m[5] = j0a;
+    m[5] = j0a * g.rw;
     m[6] = q.nbe;
     m[7] = q.vb;
     const int nup = (r1 - a0 + 3) & ~3;
@@ -151,7 +154,7 @@ class BlkPipe {
     bulk_copy_g2s(rp(s), g.row_ptr + a0, nip * 4, &bar_[s]);
     bulk_copy_g2s(up(s), g.urp + a0, nup * 4, &bar_[s]);
     bulk_copy_g2s(pm(s), g.iperm + a0, nup * 4, &bar_[s]);
-    if (q.J1 > q.J0) bulk_copy_g2s(rec(s), g.brec + j0a, nrec * 4, &bar_[s]);
+    if (q.J1 > q.J0) bulk_copy_g2s(rec(s), g.brec + (int64_t)j0a * g.rw, nrec * 4, &bar_[s]);
     if (nel > 0) bulk_copy_g2s(el(s), g.bel + q.bo, nel * 4, &bar_[s]);
   }
 
@@ -206,8 +209,10 @@ class BlkPipe {
   int* st_;
 };
 
-// Fields of an incidence record: 4-bit column positions, the local vertex
-// a (2 bits) and the local index of the element in the block's list.
+// Fields of an incidence record.  nv <= 4: one word, 4-bit column
+// positions, the local vertex a (2 bits), the local index of the element in
+// the block's list (the rest).  P2 (nv = 6): word 0 the six 5-bit positions,
+// word 1 a (3 bits) and the local element index.
 template <int NV>
 struct BlkRec {
   uint32_t w;
@@ -215,6 +220,25 @@ struct BlkRec {
   __device__ int a() const { return (int)(w >> (4 * NV)) & 3; }
   __device__ int pos(int b) const { return (int)(w >> (4 * b)) & 15; }
 };
+
+template <>
+struct BlkRec<6> {
+  uint32_t x, y;
+  __device__ int le() const { return (int)(y >> 3); }
+  __device__ int a() const { return (int)(y & 7u); }
+  __device__ int pos(int b) const { return (int)(x >> (5 * b)) & 31; }
+};
+
+// Record j of a block view.
+template <int NV>
+__device__ __forceinline__ BlkRec<NV> blk_rec(const uint32_t* rc, int j) {
+  if constexpr (NV == 6) {
+    const uint2 w = *reinterpret_cast<const uint2*>(rc + 2 * j);
+    return BlkRec<6>{w.x, w.y};
+  } else {
+    return BlkRec<NV>{rc[j]};
+  }
+}
 
 // The element of a bel entry (without the owner bit).
 __device__ __forceinline__ int64_t bel_elem(uint32_t w) { return (int64_t)(w & 0x7fffffffu); }

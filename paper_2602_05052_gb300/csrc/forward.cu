@@ -15,7 +15,7 @@
 // the memory traffic.
 #include <cstdint>
 
-#include "blocks.cuh"
+#include "blk_bilinear.cuh"
 
 namespace {
 
@@ -50,9 +50,9 @@ __global__ void __launch_bounds__(BS) k_bilinear_gather(const FwdArgs<T> a, cons
 // budget 64K / (128 * n)): 7 for FP32 triangles with up to 4 elements per
 // thread (70-72 registers, no spills), fewer where more live values need
 // more registers.
-template <int D, typename T, int UB>
+template <int EL, typename T, int UB>
 constexpr int blk_min_ctas() {
-  return D == 3 ? 2 : sizeof(T) == 8 ? 4 : UB <= 4 ? 7 : 5;
+  return EL == TG_P1_TET ? 2 : EL == TG_P2_TRI ? 4 : sizeof(T) == 8 ? 4 : UB <= 4 ? 7 : 5;
 }
 
 // P1 forward over element-once row blocks (blocks.cuh):
@@ -65,11 +65,11 @@ constexpr int blk_min_ctas() {
 //            cleared for the next block on the way).
 //   LOAD   - also the load vector F (a.f, a.f_layout -> a.F), entry for entry
 //            the arithmetic of k_load_blk: the system (K, F) in one pass.
-template <int D, typename T, int UB, bool LOAD>
-__global__ void __launch_bounds__(BS, blk_min_ctas<D, T, UB>() - (LOAD ? 1 : 0)) k_bilinear_blk(
+template <int EL, typename T, int UB, bool LOAD>
+__global__ void __launch_bounds__(BS, blk_min_ctas<EL, T, UB>() - (LOAD ? 1 : 0)) k_bilinear_blk(
     const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab, const tg::BlkArgs g, int cap_nz) {
-  constexpr int EL = D == 2 ? TG_P1_TRI : TG_P1_TET;
-  constexpr int NV = D + 1, NS = NV * (NV + 1) / 2;
+  constexpr int NV = tg::Elem<EL>::nv, NG = tg::Elem<EL>::ngeo, NS = NV * (NV + 1) / 2;
+  static_assert(!LOAD || EL != TG_P2_TRI, "the one-pass system is built for P1");
   extern __shared__ __align__(16) unsigned char smem[];
   tg::BlkPipe pipe;
   T* Ke = reinterpret_cast<T*>(pipe.init(smem, g));
@@ -78,89 +78,12 @@ __global__ void __launch_bounds__(BS, blk_min_ctas<D, T, UB>() - (LOAD ? 1 : 0))
   for (int q = threadIdx.x; q < cap_nz; q += blockDim.x) acc[q] = T(0);
   __syncthreads();  // publishes the mbarrier initialisation and the cleared acc
   TG_BLK_PIPELINE_BEGIN(pipe, g, a.status)
-  // Map
-  for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * NT_) {
-    int e[UB];
-    tg::ElemIn<EL, T> in[UB];
-#pragma unroll
-    for (int u = 0; u < UB; ++u) {
-      const int j = j0 + u * NT_ < v.nbe ? j0 + u * NT_ : 0;  // idle slots load element 0 of the list
-      e[u] = (int)tg::bel_elem(v.be[j]);
-#pragma unroll
-      for (int c = 0; c < NV; ++c) in[u].v[c] = v.vtx(c, j);
-    }
-#pragma unroll
-    for (int u = 0; u < UB; ++u) tg::elem_data<EL, T>(a, e[u], in[u]);
-    T fv[LOAD ? UB : 1][NV];
-    if constexpr (LOAD) {
-#pragma unroll
-      for (int u = 0; u < UB; ++u) tg::p1_load_f<NV, T>(a.f, a.f_layout, e[u], in[u].v, fv[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < UB; ++u) {
-      const int j = j0 + u * NT_;
-      if (j >= v.nbe) continue;
-      T K[NS];
-      T adet;
-      const bool ok = tg::p1_elem_sym<EL, T>(in[u], a.c, tab, K, &adet);
-      if (!ok) {
-        tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e[u]);
-#pragma unroll
-        for (int q = 0; q < NS; ++q) K[q] = T(0);
-      }
-      if constexpr (LOAD) {
-#pragma unroll
-        for (int c = 0; c < NV; ++c) Fe[c * g.capE + j] = ok ? tg::p1_load_entry<NV, T>(a.f_layout, adet, fv[u], tab, c) : T(0);
-      }
-      int q = 0;
-#pragma unroll
-      for (int r = 0; r < NV; ++r)
-#pragma unroll
-        for (int c = r; c < NV; ++c, ++q) {
-          Ke[(r * NV + c) * g.capE + j] = K[q];
-          if (c != r) Ke[(c * NV + r) * g.capE + j] = K[q];
-        }
-    }
-  }
-  __syncthreads();
-  // Reduce: rows summed in increasing element order, each row's values
-  // written to its node's CSR row (acc cleared on the way for the next block)
-  {
-    const int i = v.r0 + (int)threadIdx.x;
-    if (i < v.r1) {
-      T* row = acc + (v.rp[i] - v.rp[v.r0]);
-      const int je = v.ip[i + 1];
-      T fs = T(0);
-      for (int j = v.ip[i]; j < je; ++j) {
-        const tg::BlkRec<NV> r{v.rc[j]};
-        const T* kr = Ke + r.a() * NV * g.capE + r.le();
-        // the NV columns of one incidence are distinct: all loads first
-        T cur[NV], add[NV];
-#pragma unroll
-        for (int c = 0; c < NV; ++c) {
-          cur[c] = row[r.pos(c)];
-          add[c] = kr[c * g.capE];
-        }
-#pragma unroll
-        for (int c = 0; c < NV; ++c) row[r.pos(c)] = cur[c] + add[c];
-        if constexpr (LOAD) fs += Fe[r.a() * g.capE + r.le()];
-      }
-      if constexpr (LOAD) a.F[v.pm[i]] = fs;
-      const int len = v.rp[i + 1] - v.rp[i];
-      T* out = a.out + v.up[i];
-      for (int q = 0; q < len; ++q) {
-        out[q] = row[q];
-        row[q] = T(0);
-      }
-    }
-    __syncthreads();  // stage s and the work buffers are free again
-  }
+  tg::blk_bilinear_block<EL, T, UB, LOAD>(a, tab, g.capE, v, Ke, Fe, acc);
   TG_BLK_PIPELINE_END
 }
 
-template <int D, typename T>
+template <int NV, typename T>
 size_t bilinear_blk_smem(const tg_pattern* p, bool load = false) {
-  constexpr int NV = D + 1;
   const tg::BlkArgs g = tg::blk_args(p);
   return tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE, NV) +
          ((size_t)NV * (NV + (load ? 1 : 0)) * g.capE + p->blk_max_nz) * sizeof(T);
@@ -218,7 +141,7 @@ __global__ void __launch_bounds__(BS) k_load_blk(const FwdArgs<T> a, const __gri
       T f = T(0);
       const int je = v.ip[i + 1];
       for (int j = v.ip[i]; j < je; ++j) {
-        const tg::BlkRec<NV> r{v.rc[j]};
+        const auto r = tg::blk_rec<NV>(v.rc, j);
         f += Fe[r.a() * g.capE + r.le()];
       }
       a.out[v.pm[i]] = f;
@@ -240,6 +163,7 @@ size_t load_blk_smem(const tg_pattern* p) {
 template <typename T>
 int blk_ub(const tg_pattern* p) {
   const int need = (p->blk_max_elems + BS - 1) / BS;
+  if (p->el == TG_P2_TRI) return need <= 1 ? 1 : 2;
   if (sizeof(T) == 8) return need <= 2 ? 2 : 3;
   return need <= 3 ? 3 : need <= 4 ? 4 : need <= 5 ? 5 : 6;
 }
@@ -462,9 +386,8 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
   }
   const size_t smem = tab_bytes<T>() + stage;
   const int cap = std::max(1, R * p->max_deg);
-  if constexpr (EL == TG_P1_TRI || EL == TG_P1_TET) {
-    constexpr int D = El::dim;
-    const size_t sb = bilinear_blk_smem<D, T>(p);
+  {
+    const size_t sb = bilinear_blk_smem<El::nv, T>(p);
     if (use_blk<T>(p, sb)) {
       const int ub = blk_ub<T>(p);
       tg_status st = TG_OK;
@@ -473,14 +396,17 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
         if ((st = launch_blk(kern, sb, p, &grid)) != TG_OK) return;
         kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::blk_args(p), p->blk_max_nz);
       };
-      if constexpr (sizeof(T) == 8) {
-        if (ub == 2) go(k_bilinear_blk<D, T, 2, false>);
-        else go(k_bilinear_blk<D, T, 3, false>);
+      if constexpr (EL == TG_P2_TRI) {
+        if (ub <= 1) go(k_bilinear_blk<EL, T, 1, false>);
+        else go(k_bilinear_blk<EL, T, 2, false>);
+      } else if constexpr (sizeof(T) == 8) {
+        if (ub == 2) go(k_bilinear_blk<EL, T, 2, false>);
+        else go(k_bilinear_blk<EL, T, 3, false>);
       } else {
-        if (ub == 3) go(k_bilinear_blk<D, T, 3, false>);
-        else if (ub == 4) go(k_bilinear_blk<D, T, 4, false>);
-        else if (ub == 5) go(k_bilinear_blk<D, T, 5, false>);
-        else go(k_bilinear_blk<D, T, 6, false>);
+        if (ub == 3) go(k_bilinear_blk<EL, T, 3, false>);
+        else if (ub == 4) go(k_bilinear_blk<EL, T, 4, false>);
+        else if (ub == 5) go(k_bilinear_blk<EL, T, 5, false>);
+        else go(k_bilinear_blk<EL, T, 6, false>);
       }
       if (st != TG_OK) return st;
       TG_CK_LAUNCH("k_bilinear_blk");
@@ -614,7 +540,7 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
     a.f_layout = fl;
     a.F = static_cast<T*>(F);
     const bool tri = p->el == TG_P1_TRI;
-    const size_t sb = tri ? bilinear_blk_smem<2, T>(p, true) : bilinear_blk_smem<3, T>(p, true);
+    const size_t sb = tri ? bilinear_blk_smem<3, T>(p, true) : bilinear_blk_smem<4, T>(p, true);
     if (use_blk<T>(p, sb)) {
       const int ub = blk_ub<T>(p);
       const tg::RefTab<T>& tab = table<T>(p->el);
@@ -625,16 +551,16 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
         kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::blk_args(p), p->blk_max_nz);
       };
       if constexpr (sizeof(T) == 8) {
-        if (tri) go(k_bilinear_blk<2, T, 2, true>);
-        else go(k_bilinear_blk<3, T, 2, true>);
+        if (tri) go(k_bilinear_blk<TG_P1_TRI, T, 2, true>);
+        else go(k_bilinear_blk<TG_P1_TET, T, 2, true>);
       } else {
         if (tri) {
-          if (ub <= 3) go(k_bilinear_blk<2, T, 3, true>);
-          else if (ub <= 4) go(k_bilinear_blk<2, T, 4, true>);
-          else go(k_bilinear_blk<2, T, 6, true>);
+          if (ub <= 3) go(k_bilinear_blk<TG_P1_TRI, T, 3, true>);
+          else if (ub <= 4) go(k_bilinear_blk<TG_P1_TRI, T, 4, true>);
+          else go(k_bilinear_blk<TG_P1_TRI, T, 6, true>);
         } else {
-          if (ub <= 4) go(k_bilinear_blk<3, T, 4, true>);
-          else go(k_bilinear_blk<3, T, 6, true>);
+          if (ub <= 4) go(k_bilinear_blk<TG_P1_TET, T, 4, true>);
+          else go(k_bilinear_blk<TG_P1_TET, T, 6, true>);
         }
       }
       if (st != TG_OK) return st;

@@ -126,6 +126,50 @@ __device__ __forceinline__ void load_x(const T* __restrict__ coords, int v, T (&
   }
 }
 
+// Upper triangle (row by row) of the P2 triangle matrix with kappa at the 6
+// points (the quantity of p2_row for all rows at once):
+//   K[a][b] = (1/|det|) sum_q w_q kappa_q gh_q,a^T C gh_q,b + c |det| M[a][b],
+// the per-point transformed gradients h_a = w_q kappa_q C gh_q,a shared by
+// the row.  All table reads have compile-time indices (tc: the kernel's
+// constant parameter).  False for a degenerate element.
+template <typename T>
+__device__ __forceinline__ bool p2_elem_sym(const ElemIn<TG_P2_TRI, T>& in, T c, const RefTab<T>& tc, T (&K)[21],
+                                            T* adet_out = nullptr) {
+  Geom<2, T> g;
+  tri_geom_x(in.x[0], in.x[1], in.x[2], g);
+  const T adet = absv(g.det);
+  if (adet_out) *adet_out = adet;
+  if (!(adet > det_tiny<T>())) return false;
+  const T c00 = g.n[1][0] * g.n[1][0] + g.n[1][1] * g.n[1][1];
+  const T c01 = g.n[1][0] * g.n[2][0] + g.n[1][1] * g.n[2][1];
+  const T c11 = g.n[2][0] * g.n[2][0] + g.n[2][1] * g.n[2][1];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) K[k] = T(0);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const T wk = tc.w[q] * in.kq[q];
+    T hx[6], hy[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      const T g0 = tc.gh[q][a][0], g1 = tc.gh[q][a][1];
+      hx[a] = wk * (c00 * g0 + c01 * g1);
+      hy[a] = wk * (c01 * g0 + c11 * g1);
+    }
+    int k = 0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int b = a; b < 6; ++b, ++k) K[k] += hx[a] * tc.gh[q][b][0] + hy[a] * tc.gh[q][b][1];
+  }
+  const T inv = T(1) / adet, mc = c * adet;
+  int k = 0;
+#pragma unroll
+  for (int a = 0; a < 6; ++a)
+#pragma unroll
+    for (int b = a; b < 6; ++b, ++k) K[k] = K[k] * inv + mc * tc.M[a][b];
+  return true;
+}
+
 // Load values f of a P1 element as its F_e needs them: at the vertices
 // (PER_NODE), at the points (PER_QP; NQ == NV for P1) or one constant.
 template <int NV, typename T>

@@ -239,7 +239,7 @@ __global__ void k_key_place(const int32_t* __restrict__ cells, int nv, int64_t E
                             const int64_t* __restrict__ off, int32_t* __restrict__ order) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
-  int vs[4], n = 0;
+  int vs[6], n = 0;
   for (int a = 0; a < nv; ++a) {
     const int v = cells[e * nv + a];
     if (key[v] == (int32_t)e) {
@@ -370,10 +370,18 @@ __global__ void __launch_bounds__(256) k_blocks(const int32_t* __restrict__ iper
         if (uq[mid] < e) lo = mid + 1;
         else hi = mid;
       }
-      const uint32_t w = inc_pos[src + m];  // 8-bit positions (nv <= 4), each < 16 here
-      uint32_t r = 0;
-      for (int c = 0; c < nv; ++c) r |= ((w >> (8 * c)) & 15u) << (4 * c);
-      brec[dst + m] = r | ((uint32_t)a << (4 * nv)) | ((uint32_t)lo << (4 * nv + 2));
+      if (nv <= 4) {
+        const uint32_t w = inc_pos[src + m];  // 8-bit positions, each < 16 here
+        uint32_t r = 0;
+        for (int c = 0; c < nv; ++c) r |= ((w >> (8 * c)) & 15u) << (4 * c);
+        brec[dst + m] = r | ((uint32_t)a << (4 * nv)) | ((uint32_t)lo << (4 * nv + 2));
+      } else {  // P2: two inc_pos words of 8-bit positions, each < 32 here
+        const uint32_t w0 = inc_pos[2 * (src + m)], w1 = inc_pos[2 * (src + m) + 1];
+        uint32_t r = 0;
+        for (int c = 0; c < nv; ++c) r |= (((c < 4 ? w0 >> (8 * c) : w1 >> (8 * (c - 4)))) & 31u) << (5 * c);
+        brec[2 * (dst + m)] = r;
+        brec[2 * (dst + m) + 1] = (uint32_t)a | ((uint32_t)lo << 3);
+      }
     }
   }
 }
@@ -516,7 +524,9 @@ tg_status read_status(const tg_pattern* p, cudaStream_t s, const char* stage) {
 // about 4 * 120 + 2 distinct elements, one Map round of 4 per thread on 128
 // threads.  Tetrahedra touch about 18 distinct elements per row; vector
 // elasticity keeps 12 values per element in shared memory, hence 32 rows.
-int blk_rows_of(tg_element el) { return el == TG_P1_TRI ? 120 : el == TG_P1_TET ? 64 : 32; }
+int blk_rows_of(tg_element el) {
+  return el == TG_P1_TRI ? 120 : el == TG_P2_TRI ? 128 : el == TG_P1_TET ? 64 : 32;
+}
 
 // Row blocks (step 5).  Leaves p->bel == NULL when the packed fields do not
 // fit (rows longer than 16, too many distinct elements per block): the
@@ -524,9 +534,12 @@ int blk_rows_of(tg_element el) { return el == TG_P1_TRI ? 120 : el == TG_P1_TET 
 tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
   const int nv = p->nv, R = blk_rows_of(p->el);
   const int64_t N = p->N, E = p->E, nvE = E * nv, nblk = (N + R - 1) / R;
-  const int pb = 4;
+  // positions: 4 bits in 32-bit records (nv <= 4), 5 bits in 64-bit records
+  // (P2: word 0 the six positions, word 1 the local vertex and element)
+  const bool wide_rec = nv > 4;
+  const int pb = wide_rec ? 5 : 4;
   if (p->max_row_len > (1 << pb)) return TG_OK;
-  const int le_bits = 32 - nv * pb - 2;
+  const int le_bits = wide_rec ? 29 : 32 - nv * pb - 2;
   Tmp tmp;
   // internal row order: nodes by smallest incident element, isolated nodes
   // last, each block of R rows in ascending node id
@@ -586,8 +599,9 @@ tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
   TG_CK(tmp.alloc(&boff, nblk + 1));
   TG_CK(cudaMalloc(&cnt, nblk * sizeof(int32_t) + 16));
   p->bel_cnt = cnt;  // owned by the pattern from here on
-  TG_CK(cudaMalloc(&p->brec, nvE * sizeof(uint32_t) + 16));
-  TG_CK(cudaMemsetAsync(p->brec, 0, nvE * sizeof(uint32_t) + 16, s));
+  const size_t rec_bytes = nvE * sizeof(uint32_t) * (wide_rec ? 2 : 1) + 16;
+  TG_CK(cudaMalloc(&p->brec, rec_bytes));
+  TG_CK(cudaMemsetAsync(p->brec, 0, rec_bytes, s));
   k_blocks<<<(unsigned)nblk, 256, 2 * P * sizeof(int), s>>>(p->iperm, p->iinc, p->inc_ptr, p->inc_e, p->inc_pos, nv,
                                                              N, R, P, uq, cnt, p->brec, maxes + 2);
   TG_CK_LAUNCH("k_blocks");
@@ -749,7 +763,7 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
 
 
   // 5. row blocks of the element-once P1 kernels
-  if ((el == TG_P1_TRI || el == TG_P1_TET || el == TG_P1_TET_VEC3) && E > 0) {
+  if (E > 0) {
     if ((st = build_blocks(p, s)) != TG_OK) return st;
   }
 
