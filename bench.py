@@ -552,6 +552,87 @@ def extras(tg, torch, dev, m, cfg, p, peak, flush):
         "batched_elements_per_s": tot_e / ms_b * 1e3, "batched_alg_GBps": tot_b / ms_b / 1e6,
         "batched_frac_hbm": tot_b / ms_b / 1e6 / peak, "speedup_vs_looped": ms_l / ms_b,
         "speedup_vs_looped_graph": ms_lg / ms_bg, "bitwise_equal_to_looped": same}
+    del b, pats, xs, ks, vs
+    out.update(small_configs(tg, torch, dev))
+    return out
+
+
+def small_configs(tg, torch, dev):
+    """The two small configurations, reported as absolute times (latency- and
+    launch-bound at these sizes): the 64^2 Poisson problem (system assembly,
+    then CG to 1e-10 on the Dirichlet-condensed system, FP64) and one full
+    gradient evaluation of the 48^3 differentiable problem (assembly + CG,
+    adjoint CG + backward assembly, FP64)."""
+    from paper_2602_05052_gb300 import autograd as A
+    out = {}
+    d = lambda a, t=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device=dev)
+    cfg = mg.poisson2d(64)
+    m = cfg["mesh"]
+    p = tg.tg_build_pattern(d(m.cells, torch.int32), m.n_nodes, tg.P1_TRI)
+    x, one = d(m.coords), d([1.0])
+    mask = d(m.boundary.astype(np.uint8), torch.uint8)
+    vals = torch.empty(p.nnz, dtype=torch.float64, device=dev)
+    F = torch.empty(m.n_nodes, dtype=torch.float64, device=dev)
+
+    def poisson():
+        tg.tg_assemble_system(p, x, one, tg.CONSTANT, 0.0, one, tg.CONSTANT, vals=vals, F=F)
+        return tg.tg_cg_solve(p, vals, F, mask, rtol=1e-10)
+
+    for _ in range(3):
+        poisson()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = 10
+    for _ in range(reps):
+        _, it, rel = poisson()
+    torch.cuda.synchronize()
+    ms_sys = None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        tg.tg_assemble_system(p, x, one, tg.CONSTANT, 0.0, one, tg.CONSTANT, vals=vals, F=F)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_sys = e0.elapsed_time(e1) / reps
+    out["poisson2d_64_f64"] = {"elements": m.n_elems, "system_assembly_us": 1e3 * ms_sys,
+                               "assembly_plus_cg_ms": 1e3 * (time.perf_counter() - t0) / reps, "cg_iterations": it,
+                               "cg_relres": rel, "note": "host wall time: the CG checks its residual on the host"}
+    del p
+    cfg = mg.differentiable3d(48)
+    m = cfg["mesh"]
+    p = tg.tg_build_pattern(d(m.cells, torch.int32), m.n_nodes, tg.P1_TET)
+    mask = d(m.boundary.astype(np.uint8), torch.uint8)
+    x0, f = d(m.coords), d([1.0])
+    with torch.no_grad():
+        u_t = A.solve_assembled(p, x0, d(cfg["kappa_star"]), tg.PER_ELEMENT, f, tg.CONSTANT, mask, rtol=1e-13)
+    k0 = d(cfg["kappa"])
+
+    def grad_eval():
+        k = k0.clone().requires_grad_(True)
+        x = x0.clone().requires_grad_(True)
+        u = A.solve_assembled(p, x, k, tg.PER_ELEMENT, f, tg.CONSTANT, mask, rtol=1e-13)
+        L = ((u - u_t) ** 2).sum()
+        L.backward()
+        return k.grad, x.grad
+
+    grad_eval()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        grad_eval()
+    torch.cuda.synchronize()
+    t_grad = (time.perf_counter() - t0) / 3
+    vals = torch.empty(p.nnz, dtype=torch.float64, device=dev)
+    F = torch.empty(m.n_nodes, dtype=torch.float64, device=dev)
+    e0.record()
+    for _ in range(reps):
+        tg.tg_assemble_system(p, x0, k0, tg.PER_ELEMENT, 0.0, f, tg.CONSTANT, vals=vals, F=F)
+    e1.record()
+    torch.cuda.synchronize()
+    out["differentiable3d_48_f64"] = {"elements": m.n_elems, "system_assembly_us": 1e3 * e0.elapsed_time(e1) / reps,
+                                      "gradient_evaluation_ms": 1e3 * t_grad,
+                                      "note": "gradient evaluation = assembly + CG (1e-13) + adjoint CG + backward "
+                                              "assembly + load backward, host wall time"}
     return out
 
 
