@@ -112,9 +112,11 @@ def load_peaks():
 
 # translation units and headers each timed kernel is built from
 KERNEL_SOURCES = {
-    "system": ["forward.cu", "gather.cuh", "elements.cuh", "blocks.cuh", "async.cuh", "tg_internal.cuh"],
-    "fwd": ["forward.cu", "gather.cuh", "elements.cuh", "async.cuh", "tg_internal.cuh"],
-    "load": ["forward.cu", "gather.cuh", "elements.cuh", "async.cuh", "tg_internal.cuh"],
+    "system": ["forward.cu", "blk_bilinear.cuh", "gather.cuh", "elements.cuh", "blocks.cuh", "async.cuh",
+               "tg_internal.cuh"],
+    "fwd": ["forward.cu", "blk_bilinear.cuh", "gather.cuh", "elements.cuh", "blocks.cuh", "async.cuh",
+            "tg_internal.cuh"],
+    "load": ["forward.cu", "gather.cuh", "elements.cuh", "blocks.cuh", "async.cuh", "tg_internal.cuh"],
     "bwd": ["backward.cu", "gather.cuh", "elements.cuh", "blocks.cuh", "async.cuh", "tg_internal.cuh"],
 }
 
@@ -334,7 +336,7 @@ def main():
     kern = {"system": (statistics.mean(t_sys), alg_bytes("system", E, N, nnz, s)),
             "bwd": (statistics.mean(t_bwd), alg_bytes("bwd", E, N, nnz, s))}
     dom = max(kern, key=lambda k: kern[k][0])
-    names = {"system": "k_bilinear_blk<2,float,4,load>", "bwd": "k_backward_blk<2,float,gvals,2> + k_backward_final"}
+    names = {"system": "k_bilinear_blk<P1_TRI,float,UB,load>", "bwd": "k_backward_blk<2,float,gvals,UB>"}
     ach = kern[dom][1] / (kern[dom][0] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "traffic": ncu_traffic(dom), "peak_source": f"{peak_src} (copy, burst)",

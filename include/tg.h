@@ -136,6 +136,14 @@ tg_status tg_pattern_info(const tg_pattern* p, int64_t* n_rows, int64_t* nnz, co
 tg_status tg_pattern_shape(const tg_pattern* p, tg_element* el, int64_t* n_elems, int64_t* n_nodes,
                            int32_t* max_row_len, int32_t* max_degree);
 
+/* Row blocks of a pattern (the data layout of the element-once kernels, no
+ * counterpart in the paper).  *rows_per_block receives the rows a block owns
+ * and *n_blocks the block count; both are 0 when the pattern has none (an
+ * empty mesh, rows longer than 16 entries (32 for P2), or a block whose
+ * vertex ids span 2^16 or more, e.g. a random node numbering), in which case
+ * the generic row-owner kernels serve every call.  Either pointer may be NULL. */
+tg_status tg_pattern_row_blocks(const tg_pattern* p, int32_t* rows_per_block, int64_t* n_blocks);
+
 /* Read and clear the device status word of a pattern.  SYNCHRONISES the
  * device.  Returns TG_OK or the first recorded data error; *first_bad_elem
  * (may be NULL) gets the smallest offending element index, or -1. */

@@ -53,6 +53,7 @@ def lib():
                                   C.POINTER(i32)]),
         "tg_pattern_shape": (i32, [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32),
                                    C.POINTER(i32)]),
+        "tg_pattern_row_blocks": (i32, [vp, C.POINTER(i32), C.POINTER(i64)]),
         "tg_get_device_status": (i32, [vp, C.POINTER(i64)]),
         "tg_pattern_destroy": (None, [vp]),
         "tg_assemble_bilinear": (i32, [vp, i32, vp, vp, i32, dbl, vp, vp]),
@@ -159,6 +160,9 @@ class Pattern:
         _check(L.tg_pattern_info(handle, C.byref(nr), C.byref(nnz), C.byref(rp), C.byref(ci), C.byref(es),
                                  C.byref(ss)), "tg_pattern_info")
         self.n_rows, self.nnz = nr.value, nnz.value
+        rb, nb = i32(), i64()
+        _check(L.tg_pattern_row_blocks(handle, C.byref(rb), C.byref(nb)), "tg_pattern_row_blocks")
+        self.rows_per_block, self.n_blocks = rb.value, nb.value
         self._rp, self._ci, self._es, self.slot_stride = rp.value, ci.value, es.value, ss.value
 
     def _view(self, ptr, n):

@@ -192,6 +192,14 @@ tg_status tg_pattern_shape(const tg_pattern* p, tg_element* el, int64_t* n_elems
   return TG_OK;
 }
 
+tg_status tg_pattern_row_blocks(const tg_pattern* p, int32_t* rows_per_block, int64_t* n_blocks) {
+  if (!p) return TG_ERR_INVALID_ARG;
+  const bool on = p->bel != nullptr;
+  if (rows_per_block) *rows_per_block = on ? p->blk_rows : 0;
+  if (n_blocks) *n_blocks = on ? p->n_blk : 0;
+  return TG_OK;
+}
+
 tg_status tg_get_device_status(const tg_pattern* p, int64_t* first_bad_elem) {
   if (!p) return TG_ERR_INVALID_ARG;
   TG_CK(cudaSetDevice(p->device));

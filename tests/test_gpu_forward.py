@@ -296,3 +296,36 @@ def test_wrong_kind_and_dtype_rejected(tg):
     with pytest.raises(TypeError):
         tg.tg_assemble_elasticity(p, dev(m.coords, torch.float64), dev([1.0], torch.float32), dev([1.0], torch.float64),
                                   mg.CONSTANT)
+
+
+def test_generic_path_when_blocks_do_not_fit(tg):
+    """A random numbering of a 90,601-node mesh makes every block's vertex ids
+    span more than 2^16, so the pattern has no row blocks and the generic
+    row-owner kernels serve forward, system, backward and the batch."""
+    m = jittered_tri(300)
+    g = np.random.default_rng(95)
+    relabel = g.permutation(m.n_nodes)
+    cells = relabel[m.cells]
+    X = np.empty_like(m.coords)
+    X[relabel] = m.coords
+    k = coef(mg.PER_QP, len(cells), 3, seed=96)
+    f = g.uniform(-1, 1, m.n_nodes)
+    p = tg.tg_build_pattern(dev(cells, torch.int32), m.n_nodes, mg.P1_TRI)
+    assert (p.rows_per_block, p.n_blocks) == (0, 0)
+    q = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
+    assert q.rows_per_block > 0 and q.n_blocks == -(-m.n_nodes // q.rows_per_block)
+    x, kd, fd = dev(X, torch.float64), dev(k, torch.float64), dev(f, torch.float64)
+    vals, F = tg.tg_assemble_system(p, x, kd, mg.PER_QP, 0.2, fd, mg.PER_NODE)
+    ref = O.assemble_bilinear(mg.P1_TRI, cells, X, k, O.PER_QP, 0.2)
+    assert relfro(vals.cpu().numpy(), ref.val) <= 1e-12
+    assert relfro(F.cpu().numpy(), O.assemble_load(mg.P1_TRI, cells, X, f, O.PER_NODE)) <= 1e-12
+    assert torch.equal(vals, tg.tg_assemble_bilinear(p, x, kd, mg.PER_QP, 0.2))
+    gv = g.normal(size=p.nnz)
+    gk, gx, gc = tg.tg_assemble_backward(p, x, kd, mg.PER_QP, 0.2, grad_vals=dev(gv, torch.float64))
+    rk, rx, rc = O.assemble_backward(mg.P1_TRI, cells, X, k, O.PER_QP, 0.2, grad_csr=O.CSR(ref.row_ptr, ref.col, gv))
+    assert relfro(gk.cpu().numpy(), rk) <= 1e-12 and relfro(gx.cpu().numpy(), rx) <= 1e-12
+    assert relfro(gc.cpu().numpy(), [rc]) <= 1e-12
+    b = tg.tg_batch_create([p, p])
+    out = [torch.empty(p.nnz, dtype=torch.float64, device="cuda") for _ in range(2)]
+    tg.tg_batch_assemble(b, [x, x], [kd, kd], mg.PER_QP, [0.2, 0.2], out)
+    assert torch.equal(out[0], vals) and torch.equal(out[1], vals)
