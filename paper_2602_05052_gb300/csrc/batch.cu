@@ -97,12 +97,11 @@ struct InstBlk {
 template <int EL, typename T, int UB>
 __global__ void __launch_bounds__(128) k_batch_blk(const InstBlk* __restrict__ desc, const int2* __restrict__ items,
                                                    int64_t n_items, const __grid_constant__ BatchCall<T> call,
-                                                   const __grid_constant__ tg::RefTab<T> tab, int capE, int cap_nz) {
+                                                   const __grid_constant__ tg::RefTab<T> tab, int capE, int acc_n) {
   constexpr int NV = tg::Elem<EL>::nv;
   extern __shared__ __align__(16) unsigned char smem[];
-  T* Ke = reinterpret_cast<T*>(smem);
-  T* acc = Ke + (size_t)NV * NV * capE;
-  for (int q = threadIdx.x; q < cap_nz; q += blockDim.x) acc[q] = T(0);
+  T* acc = reinterpret_cast<T*>(smem + (size_t)NV * tg::kf_vecs<NV, T, false>() * capE * 16);
+  for (int q = threadIdx.x; q < acc_n; q += blockDim.x) acc[q] = T(0);
   __syncthreads();
   for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int2 w = items[it];
@@ -142,7 +141,7 @@ __global__ void __launch_bounds__(128) k_batch_blk(const InstBlk* __restrict__ d
     v.rc = d.brec;
     v.be = d.bel + d.boff[w.y];
     v.vo = reinterpret_cast<const uint16_t*>(v.be + ((v.nbe + 3) & ~3));
-    tg::blk_bilinear_block<EL, T, UB, false>(a, tab, capE, v, Ke, nullptr, acc);
+    tg::blk_bilinear_block<EL, T, UB, false>(a, tab, capE, v, smem, acc);
   }
 }
 
@@ -172,7 +171,7 @@ struct tg_batch {
   InstBlk* d_blk = nullptr;
   int2* d_blk_items = nullptr;
   std::vector<int64_t> blk_chunk_items;
-  int capE = 0, cap_nz = 0, max_elems = 0;
+  int capE = 0, max_elems = 0;
 };
 
 namespace {
@@ -245,7 +244,7 @@ tg_status launch_blk_t(tg_batch* b, const void* const* coords, const void* const
                        void* const* vals, cudaStream_t s) {
   constexpr int NV = tg::Elem<EL>::nv;
   auto kern = k_batch_blk<EL, T, UB>;
-  const size_t smem = ((size_t)NV * NV * b->capE + b->cap_nz) * sizeof(T);
+  const size_t smem = tg::blk_bilinear_work_bytes<NV, T, false>(b->capE, b->max_row_len, 128);
   tg_status st = tg::set_smem((const void*)kern, smem);
   if (st != TG_OK) return st;
   int per_sm = b->sched.ctas_per_sm;
@@ -270,7 +269,7 @@ tg_status launch_blk_t(tg_batch* b, const void* const* coords, const void* const
     const int64_t i0 = b->blk_chunk_items[ch], n_items = b->blk_chunk_items[ch + 1] - i0;
     if (n_items == 0) continue;
     const int grid = (int)std::min<int64_t>(n_items, (int64_t)per_sm * tg::sm_count());
-    kern<<<grid, 128, smem, s>>>(b->d_blk, b->d_blk_items + i0, n_items, call, tab, b->capE, b->cap_nz);
+    kern<<<grid, 128, smem, s>>>(b->d_blk, b->d_blk_items + i0, n_items, call, tab, b->capE, b->max_row_len * 128);
     TG_CK_LAUNCH("k_batch_blk");
   }
   return TG_OK;
@@ -331,14 +330,17 @@ tg_status check_call(const tg_batch* b, tg_dtype dtype, const void* const* coord
 // shared-memory budget: descriptors and the (instance, block) item list.
 tg_status setup_blocks(tg_batch* b) {
   const int nv = tg::nv_of(b->el);
-  int capE = 0, cap_nz = 0, max_elems = 0;
+  int capE = 0, max_elems = 0;
   for (const tg_pattern* p : b->pats) {
     if (p->E > 0 && !p->bel) return TG_OK;  // stays in row-range mode
     capE = std::max(capE, (p->blk_max_elems + 3) & ~3);
-    cap_nz = std::max(cap_nz, p->blk_max_nz);
     max_elems = std::max(max_elems, p->blk_max_elems);
   }
-  if (((size_t)nv * nv * capE + cap_nz) * 8 > 113 * 1024) return TG_OK;
+  // the FP64 budget bounds both dtypes
+  const size_t need = nv == 3 ? tg::blk_bilinear_work_bytes<3, double, false>(capE, b->max_row_len, 128)
+                    : nv == 4 ? tg::blk_bilinear_work_bytes<4, double, false>(capE, b->max_row_len, 128)
+                              : tg::blk_bilinear_work_bytes<6, double, false>(capE, b->max_row_len, 128);
+  if (need > 113 * 1024) return TG_OK;
   std::vector<InstBlk> h(b->n_inst);
   std::vector<int2> items;
   b->blk_chunk_items.assign(1, 0);
@@ -356,7 +358,6 @@ tg_status setup_blocks(tg_batch* b) {
   if (!items.empty())
     TG_CK(cudaMemcpy(b->d_blk_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
   b->capE = capE;
-  b->cap_nz = cap_nz;
   b->max_elems = max_elems;
   b->blk = true;
   return TG_OK;

@@ -8,18 +8,60 @@
 
 namespace tg {
 
-//   Map    - the local matrix K_e of every distinct element of the block into
-//            Ke[NV*NV][capE] (UB elements per thread, one round when
-//            UB * blockDim.x >= the block's element count), and with LOAD
-//            F_e into Fe[NV][capE];
-//   Reduce - row i adds, for each incidence (e, a) in increasing e, row a of
-//            K_e into its CSR-local slice of acc and writes the slice to its
-//            node's CSR row (clearing acc for the next block); with LOAD also
-//            F of the node.  Ends with a CTA barrier.
+// 16-byte vector of T (the unit of the Map's output rows).
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int n = 4;
+  __device__ static float get(const float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+  __device__ static float4 make(const float* x) { return make_float4(x[0], x[1], x[2], x[3]); }
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int n = 2;
+  __device__ static double get(const double2& v, int k) { return k == 0 ? v.x : v.y; }
+  __device__ static double2 make(const double* x) { return make_double2(x[0], x[1]); }
+};
+
+// 16-byte vectors per (element, local vertex a) output row of the Map: row a
+// of K_e in rotated column order K[a][a], K[a][a+1 mod NV], ..., then (with
+// LOAD) F_e[a], zero-padded.
+template <int NV, typename T, bool LOAD>
+__host__ __device__ constexpr int kf_vecs() {
+  return ((NV + (LOAD ? 1 : 0)) * (int)sizeof(T) + 15) / 16;
+}
+
+// Shared bytes of the Map's output rows and of the Reduce's accumulators
+// (max_row_len positions x rs threads).
+template <int NV, typename T, bool LOAD>
+size_t blk_bilinear_work_bytes(int capE, int max_row_len, int rs) {
+  return (size_t)NV * kf_vecs<NV, T, LOAD>() * capE * 16 + (size_t)max_row_len * rs * sizeof(T);
+}
+
+//   Map    - every distinct element of the block computes K_e (and with
+//            LOAD F_e) once (UB elements per thread, one round when
+//            UB * blockDim.x >= the block's element count) and stores its
+//            NV output rows: vector w of row a of element j at
+//            KF[(a * NW + w) * capE + j];
+//   Reduce - thread t owns row i = r0 + t; for each incidence (e, a) in
+//            increasing e it adds row a of K_e: the diagonal entry (rotated
+//            column 0) in a register, the others into acc[pos * rs + t]
+//            (pos = the column's position in the row; the records hold the
+//            positions in the same rotated order).  The row is then written
+//            to its node's CSR row and acc cleared for the next block; with
+//            LOAD also F of the node.  Ends with a CTA barrier.
+// Every CSR entry is the sum of its contributions in increasing element
+// order, starting from the first one.
 template <int EL, typename T, int UB, bool LOAD>
 __device__ __forceinline__ void blk_bilinear_block(const FwdArgs<T>& a, const RefTab<T>& tab, int capE,
-                                                   const BlkView& v, T* Ke, T* Fe, T* acc) {
+                                                   const BlkView& v, void* kf_buf, T* acc) {
   constexpr int NV = Elem<EL>::nv, NG = Elem<EL>::ngeo, NS = NV * (NV + 1) / 2;
+  constexpr int NW = kf_vecs<NV, T, LOAD>(), VN = Vec16<T>::n;
+  using V = typename Vec16<T>::type;
+  V* KF = reinterpret_cast<V*>(kf_buf);
   const int NT = blockDim.x;
   // Map
   for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * NT) {
@@ -53,49 +95,56 @@ __device__ __forceinline__ void blk_bilinear_block(const FwdArgs<T>& a, const Re
 #pragma unroll
         for (int q = 0; q < NS; ++q) K[q] = T(0);
       }
-      if constexpr (LOAD) {
 #pragma unroll
-        for (int c = 0; c < NV; ++c) Fe[c * capE + j] = ok ? p1_load_entry<NV, T>(a.f_layout, adet, fv[u], tab, c) : T(0);
-      }
-      int q = 0;
+      for (int r = 0; r < NV; ++r) {
+        T row[NW * VN];
 #pragma unroll
-      for (int r = 0; r < NV; ++r)
-#pragma unroll
-        for (int c = r; c < NV; ++c, ++q) {
-          Ke[(r * NV + c) * capE + j] = K[q];
-          if (c != r) Ke[(c * NV + r) * capE + j] = K[q];
+        for (int c = 0; c < NV; ++c) {
+          const int b = (r + c) % NV, lo = r < b ? r : b, hi = r < b ? b : r;
+          row[c] = K[lo * NV - lo * (lo - 1) / 2 + (hi - lo)];  // K_sym[lo][hi], rows packed upper
         }
+#pragma unroll
+        for (int c = NV; c < NW * VN; ++c) row[c] = T(0);
+        if constexpr (LOAD) row[NV] = ok ? p1_load_entry<NV, T>(a.f_layout, adet, fv[u], tab, r) : T(0);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) KF[(r * NW + w) * capE + j] = Vec16<T>::make(row + w * VN);
+      }
     }
   }
   __syncthreads();
-  // Reduce: rows summed in increasing element order, each row's values
-  // written to its node's CSR row (acc cleared on the way for the next block)
+  // Reduce
   {
-    const int i = v.r0 + (int)threadIdx.x;
+    const int t = (int)threadIdx.x, i = v.r0 + t;
     if (i < v.r1) {
-      T* row = acc + (v.rp[i] - v.rp[v.r0]);
       const int je = v.ip[i + 1];
-      T fs = T(0);
+      T diag = T(0), fs = T(0);
+      int dpos = -1;
       for (int j = v.ip[i]; j < je; ++j) {
         const auto r = blk_rec<NV>(v.rc, j);
-        const T* kr = Ke + r.a() * NV * capE + r.le();
-        // the NV columns of one incidence are distinct: all loads first
-        T cur[NV], add[NV];
+        const V* src = KF + r.a() * NW * capE + r.le();
+        V x[NW];
 #pragma unroll
-        for (int c = 0; c < NV; ++c) {
-          cur[c] = row[r.pos(c)];
-          add[c] = kr[c * capE];
-        }
+        for (int w = 0; w < NW; ++w) x[w] = src[w * capE];
+        T kv[NW * VN];
 #pragma unroll
-        for (int c = 0; c < NV; ++c) row[r.pos(c)] = cur[c] + add[c];
-        if constexpr (LOAD) fs += Fe[r.a() * capE + r.le()];
+        for (int k = 0; k < NW * VN; ++k) kv[k] = Vec16<T>::get(x[k / VN], k % VN);
+        diag += kv[0];
+        dpos = r.pos(0);
+        // the NV - 1 off-diagonal columns of one incidence are distinct: loads first
+        T cur[NV - 1];
+#pragma unroll
+        for (int c = 1; c < NV; ++c) cur[c - 1] = acc[r.pos(c) * NT + t];
+#pragma unroll
+        for (int c = 1; c < NV; ++c) acc[r.pos(c) * NT + t] = cur[c - 1] + kv[c];
+        if constexpr (LOAD) fs += kv[NV];
       }
+      if (dpos >= 0) acc[dpos * NT + t] = diag;
       if constexpr (LOAD) a.F[v.pm[i]] = fs;
       const int len = v.rp[i + 1] - v.rp[i];
       T* out = a.out + v.up[i];
       for (int q = 0; q < len; ++q) {
-        out[q] = row[q];
-        row[q] = T(0);
+        out[q] = acc[q * NT + t];
+        acc[q * NT + t] = T(0);
       }
     }
     __syncthreads();  // stage s and the work buffers are free again

@@ -55,38 +55,32 @@ constexpr int blk_min_ctas() {
   return EL == TG_P1_TET ? 2 : EL == TG_P2_TRI ? 4 : sizeof(T) == 8 ? 4 : UB <= 4 ? 7 : 5;
 }
 
-// P1 forward over element-once row blocks (blocks.cuh):
-//   Map    - the local matrix K_e of every distinct element of the block into
-//            Ke[NV*NV][capE] (UB elements per thread, one round when
-//            UB * R >= the block's element count);
-//   Reduce - row i adds, for each incidence (e, a) in increasing e, row a of
-//            K_e into its CSR-local slice of acc; the block's slice of the
-//            CSR values is then stored with coalesced writes (and acc is
-//            cleared for the next block on the way).
-//   LOAD   - also the load vector F (a.f, a.f_layout -> a.F), entry for entry
-//            the arithmetic of k_load_blk: the system (K, F) in one pass.
+// Scalar forward over element-once row blocks (blocks.cuh): the Map and
+// Reduce of blk_bilinear_block per row block.  LOAD also assembles the load
+// vector F (a.f, a.f_layout -> a.F), entry for entry the arithmetic of
+// k_load_blk: the system (K, F) in one pass.  acc_n = the accumulator count
+// (the longest row x BS), cleared here once and by every block after use.
 template <int EL, typename T, int UB, bool LOAD>
 __global__ void __launch_bounds__(BS, blk_min_ctas<EL, T, UB>() - (LOAD ? 1 : 0)) k_bilinear_blk(
-    const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab, const tg::BlkArgs g, int cap_nz) {
-  constexpr int NV = tg::Elem<EL>::nv, NG = tg::Elem<EL>::ngeo, NS = NV * (NV + 1) / 2;
+    const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab, const tg::BlkArgs g, int acc_n) {
+  constexpr int NV = tg::Elem<EL>::nv;
   static_assert(!LOAD || EL != TG_P2_TRI, "the one-pass system is built for P1");
   extern __shared__ __align__(16) unsigned char smem[];
   tg::BlkPipe pipe;
-  T* Ke = reinterpret_cast<T*>(pipe.init(smem, g));
-  T* Fe = Ke + (size_t)NV * NV * g.capE;
-  T* acc = Fe + (LOAD ? (size_t)NV * g.capE : 0);
-  for (int q = threadIdx.x; q < cap_nz; q += blockDim.x) acc[q] = T(0);
+  unsigned char* kf = pipe.init(smem, g);
+  T* acc = reinterpret_cast<T*>(kf + (size_t)NV * tg::kf_vecs<NV, T, LOAD>() * g.capE * 16);
+  for (int q = threadIdx.x; q < acc_n; q += blockDim.x) acc[q] = T(0);
   __syncthreads();  // publishes the mbarrier initialisation and the cleared acc
   TG_BLK_PIPELINE_BEGIN(pipe, g, a.status)
-  tg::blk_bilinear_block<EL, T, UB, LOAD>(a, tab, g.capE, v, Ke, Fe, acc);
+  tg::blk_bilinear_block<EL, T, UB, LOAD>(a, tab, g.capE, v, kf, acc);
   TG_BLK_PIPELINE_END
 }
 
-template <int NV, typename T>
-size_t bilinear_blk_smem(const tg_pattern* p, bool load = false) {
+template <int NV, typename T, bool LOAD>
+size_t bilinear_blk_smem(const tg_pattern* p) {
   const tg::BlkArgs g = tg::blk_args(p);
   return tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE, NV) +
-         ((size_t)NV * (NV + (load ? 1 : 0)) * g.capE + p->blk_max_nz) * sizeof(T);
+         tg::blk_bilinear_work_bytes<NV, T, LOAD>(g.capE, p->max_row_len, BS);
 }
 
 // P1 load vector over element-once row blocks: Map F_e (NV values) per
@@ -387,14 +381,14 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
   const size_t smem = tab_bytes<T>() + stage;
   const int cap = std::max(1, R * p->max_deg);
   {
-    const size_t sb = bilinear_blk_smem<El::nv, T>(p);
+    const size_t sb = bilinear_blk_smem<El::nv, T, false>(p);
     if (use_blk<T>(p, sb)) {
       const int ub = blk_ub<T>(p);
       tg_status st = TG_OK;
       auto go = [&](auto kern) {
         dim3 grid;
         if ((st = launch_blk(kern, sb, p, &grid)) != TG_OK) return;
-        kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::blk_args(p), p->blk_max_nz);
+        kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::blk_args(p), p->max_row_len * BS);
       };
       if constexpr (EL == TG_P2_TRI) {
         if (ub <= 1) go(k_bilinear_blk<EL, T, 1, false>);
@@ -540,7 +534,7 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
     a.f_layout = fl;
     a.F = static_cast<T*>(F);
     const bool tri = p->el == TG_P1_TRI;
-    const size_t sb = tri ? bilinear_blk_smem<3, T>(p, true) : bilinear_blk_smem<4, T>(p, true);
+    const size_t sb = tri ? bilinear_blk_smem<3, T, true>(p) : bilinear_blk_smem<4, T, true>(p);
     if (use_blk<T>(p, sb)) {
       const int ub = blk_ub<T>(p);
       const tg::RefTab<T>& tab = table<T>(p->el);
@@ -548,7 +542,7 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
       auto go = [&](auto kern) {
         dim3 grid;
         if ((st = launch_blk(kern, sb, p, &grid)) != TG_OK) return;
-        kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::blk_args(p), p->blk_max_nz);
+        kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::blk_args(p), p->max_row_len * BS);
       };
       if constexpr (sizeof(T) == 8) {
         if (tri) go(k_bilinear_blk<TG_P1_TRI, T, 2, true>);

@@ -370,15 +370,20 @@ __global__ void __launch_bounds__(256) k_blocks(const int32_t* __restrict__ iper
         if (uq[mid] < e) lo = mid + 1;
         else hi = mid;
       }
+      // field c of a record: the position of vertex (a + c) mod nv (field 0
+      // the diagonal), the column order of the Map's rotated output rows
       if (nv <= 4) {
         const uint32_t w = inc_pos[src + m];  // 8-bit positions, each < 16 here
         uint32_t r = 0;
-        for (int c = 0; c < nv; ++c) r |= ((w >> (8 * c)) & 15u) << (4 * c);
+        for (int c = 0; c < nv; ++c) r |= ((w >> (8 * ((a + c) % nv))) & 15u) << (4 * c);
         brec[dst + m] = r | ((uint32_t)a << (4 * nv)) | ((uint32_t)lo << (4 * nv + 2));
       } else {  // P2: two inc_pos words of 8-bit positions, each < 32 here
         const uint32_t w0 = inc_pos[2 * (src + m)], w1 = inc_pos[2 * (src + m) + 1];
         uint32_t r = 0;
-        for (int c = 0; c < nv; ++c) r |= (((c < 4 ? w0 >> (8 * c) : w1 >> (8 * (c - 4)))) & 31u) << (5 * c);
+        for (int c = 0; c < nv; ++c) {
+          const int b = (a + c) % nv;
+          r |= (((b < 4 ? w0 >> (8 * b) : w1 >> (8 * (b - 4)))) & 31u) << (5 * c);
+        }
         brec[2 * (dst + m)] = r;
         brec[2 * (dst + m) + 1] = (uint32_t)a | ((uint32_t)lo << 3);
       }

@@ -52,9 +52,12 @@ struct tg_pattern {
   //     vertex), then nv rows of (nbe + 7) & ~7 16-bit vertex offsets from
   //     bvbase[b] (built only when every block's vertex ids span < 2^16).
   //   brec[j], j in [J0, J1), per incidence (row i, element e, local vertex
-  //     a), rows in internal order, each row's incidences in element order:  4-bit fields [4b, 4b+4) the position of
-  //     vertex b's column in row i (b < nv), then a (2 bits), then the local
-  //     index of e in the block's list (the rest).
+  //     a), rows in internal order, each row's incidences in element order.
+  //     nv <= 4: 4-bit fields [4c, 4c+4) the position in row i of the column
+  //     of vertex (a + c) mod nv (c < nv; field 0 is the diagonal), then a
+  //     (2 bits), then the local index of e in the block's list (the rest).
+  //     P2 (two words): six 5-bit fields in the same rotated order, then a
+  //     (3 bits) and the local index in the second word.
   //   elem_pos[e] (64 bit): position of vertex b's column in vertex a's row
   //     at bits [4(a*nv + b), ...).
   int blk_rows = 0, blk_pb = 0;
