@@ -94,6 +94,12 @@ def alg_bytes(kind, E, N, nnz, s, nv=3, Q=3, d=2):
         return E * nv * 4 + N * d * s + N * s + N * s
     if kind == "bwd":
         return E * nv * 4 + N * d * s + E * Q * s + nnz * s + E * Q * s + N * d * s
+    if kind == "residual":  # read cells, coords, kappa, x, f, the Dirichlet mask; write y
+        return E * nv * 4 + N * d * s + E * Q * s + N * s + N * s + N + N * s
+    if kind == "residual_bwd":  # dL/dx = K g, then the adjoint backward (lam = g, U = x) and the load backward
+        return (E * nv * 4 + N * d * s + E * Q * s + N * s + N + N * s  # K g
+                + E * nv * 4 + N * d * s + E * Q * s + 2 * N * s + E * Q * s + N * d * s  # kappa, coords
+                + E * nv * 4 + N * d * s + 2 * N * s + N * d * s)  # f, coords (accumulated)
     if kind == "elastic":
         return E * 4 * 4 + N * 3 * s + 2 * E * s + nnz * s
     if kind == "elastic_bwd":  # + read grad_vals, write grad_lam, grad_mu, grad_coords
@@ -487,6 +493,7 @@ def extras(tg, torch, dev, m, cfg, p, peak, flush):
             "bwd_ms": ms_b, "bwd_alg_GBps": bb / ms_b / 1e6, "bwd_frac_hbm": bb / ms_b / 1e6 / peak,
             "fwd_plus_bwd_elements_per_s": E / (ms_f + ms_b) * 1e3, "load_ms": ms_l,
             "system_ms": ms_s, "system_alg_GBps": alg_bytes("system", E, N, nnz, s) / ms_s / 1e6}
+    out.update(residual_extras(tg, torch, dev, m, cfg, p, peak, flush))
     out["fp64_fma_peak_tflops"] = tg.tg_diag_fma_rate(torch.float64) / 1e12
     out["fp32_fma_peak_tflops"] = tg.tg_diag_fma_rate(torch.float32) / 1e12
     # elasticity 64^3
@@ -556,6 +563,41 @@ def extras(tg, torch, dev, m, cfg, p, peak, flush):
         "speedup_vs_looped_graph": ms_lg / ms_bg, "bitwise_equal_to_looped": same}
     del b, pats, xs, ks, vs
     out.update(small_configs(tg, torch, dev))
+    return out
+
+
+def residual_extras(tg, torch, dev, m, cfg, p, peak, flush):
+    """Matrix-free residual y = K x - F and loss ||y||^2 of Eq. (res1) on the
+    1024^2 workload (x random, u = 0 rows on the boundary), and its reverse
+    mode: dL/dx = K g, dL/dkappa and dL/dcoords (lam = g, U = x), dL/df."""
+    out = {}
+    E, N = m.n_elems, m.n_nodes
+    mask = torch.as_tensor(m.boundary.astype(np.uint8), device=dev)
+    for dtn, dt, s in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
+        d = lambda a, t=dt: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device=dev)
+        X, k, f = d(m.coords), d(cfg["kappa"]), d(cfg["f"])
+        x = d(np.random.default_rng(9).uniform(-1, 1, N))
+        y, loss = torch.empty(N, dtype=dt, device=dev), torch.empty(1, dtype=dt, device=dev)
+        fwd = lambda: tg.tg_residual(p, X, k, tg.PER_QP, 1.0, x, f, tg.PER_NODE, mask, y=y, loss=loss)
+        ms = timed(torch, fwd, flush)
+        fwd()
+        g = 2.0 * y  # dL/dy of L = ||y||^2 (zero on the Dirichlet rows)
+        gx_in, gk, gX, gf = (torch.empty_like(x), torch.empty_like(k), torch.empty_like(X), torch.zeros_like(f))
+        ng = -g
+
+        def bwd():
+            tg.tg_residual(p, X, k, tg.PER_QP, 1.0, g, y=gx_in, loss=False)
+            tg.tg_assemble_backward(p, X, k, tg.PER_QP, 1.0, lam=g, U=x, grad_kappa=gk, grad_coords=gX, grad_c=False)
+            tg.tg_assemble_load_backward(p, X, f, tg.PER_NODE, 1, ng, grad_f=gf, grad_coords=gX, accumulate=True)
+
+        ms_b = timed(torch, bwd, flush)
+        b, bb = alg_bytes("residual", E, N, 0, s), alg_bytes("residual_bwd", E, N, 0, s)
+        out[f"residual2d_{dtn}"] = {
+            "ms": ms, "elements_per_s": E / ms * 1e3, "alg_GBps": b / ms / 1e6, "frac_hbm": b / ms / 1e6 / peak,
+            "bwd_ms": ms_b, "bwd_alg_GBps": bb / ms_b / 1e6, "bwd_frac_hbm": bb / ms_b / 1e6 / peak,
+            "loss": float(loss.item()),
+            "note": "y = K x - F without storing K, Dirichlet rows zeroed, loss = ||y||^2 in FP64; backward = "
+                    "K g (matrix-free) + adjoint backward (lam = g, U = x) + load backward, 3 launches"}
     return out
 
 

@@ -201,6 +201,31 @@ tg_status tg_assemble_system(const tg_pattern* p, tg_dtype dtype, const void* co
 tg_status tg_assemble_load(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* f,
                            tg_layout f_layout, int32_t ncomp, void* F_out, tg_stream stream);
 
+/* Matrix-free residual of the Galerkin system, the vector inside the
+ * physics-informed loss of Eq. (res1), without storing K:
+ *   y[i] = sum_e sum_b K_e[a][b] x[g(b)] - F[i]        (i = g(a)),
+ * with K_e the local matrix of tg_assemble_bilinear (kappa, kappa_layout, c)
+ * and F the load vector of tg_assemble_load (f, f_layout, ncomp = 1); with
+ * f == NULL there is no load term (y = K x).
+ *   dirichlet  uint8 [N] or NULL: y[i] = 0 where dirichlet[i] != 0 (the rows
+ *              the reduced system drops; x holds the boundary values there).
+ *   loss       device scalar of dtype, or NULL: sum_i y[i]^2, summed in FP64
+ *              in a fixed order.
+ *   x, y [N]   distinct buffers (TG_ERR_INVALID_ARG otherwise).
+ * Elements P1_TRI, P2_TRI, P1_TET; the load term on P1 only
+ * (TG_ERR_UNSUPPORTED for P2 with f).  Deterministic: every y[i] sums its
+ * element results in increasing element order.  Uses the pattern's partial-
+ * sum buffer like tg_assemble_backward: calls on one pattern that overlap
+ * (several streams) race.
+ * Reverse mode, for an upstream gradient gy of y that is zero on Dirichlet
+ * rows: dL/dx = K gy (this call with x = gy, f = NULL; K is symmetric);
+ * dL/dkappa, dL/dc and the K part of dL/dcoords from tg_assemble_backward
+ * with lam = gy, U = x; dL/df and the F part of dL/dcoords from
+ * tg_assemble_load_backward with grad_F = -gy. */
+tg_status tg_residual(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
+                      tg_layout kappa_layout, double c, const void* x, const void* f, tg_layout f_layout,
+                      const uint8_t* dirichlet, void* y, void* loss, tg_stream stream);
+
 /* ------------------------------------------------------------------------
  * Backward (reverse mode) of the scalar bilinear assembly.
  * For an upstream gradient W of the assembled values, either

@@ -10,6 +10,8 @@ shares no code, header or constant with the GPU library.
 * ``exact.py`` — exact rational element matrices by monomial integration
   (independent of quadrature), used to pin the C++ oracle on tiny meshes.
 * ``solve.py`` — conjugate gradients on the Dirichlet-condensed system.
+* ``residual()`` — the residual vector of Eq. (res1), K x - F, from the
+  assembled oracle matrix and load vector.
 
 Parity of every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, invariants, exact integration and finite differences.
@@ -250,3 +252,17 @@ def load_backward(el, cells, coords, f, f_layout, ncomp, gF):
     gx = np.zeros(N * d)
     lib().orc_load_backward(el, E, N, _p(cells), _p(coords), _p(f), f_layout, ncomp, _p(gF), _p(gf), _p(gx))
     return gf, gx.reshape(N, d)
+
+
+def residual(el, cells, coords, kappa, kappa_layout, c, x, f=None, f_layout=PER_NODE, dirichlet=None):
+    """Residual of Eq. (res1): y = K(kappa, c) x - F(f) with K and F assembled
+    by scatter-add (F omitted when f is None), y = 0 on the rows where
+    dirichlet != 0 (the rows the reduced system drops), and the loss
+    sum_i y_i^2.  Returns (y, loss)."""
+    K = assemble_bilinear(el, cells, coords, kappa, kappa_layout, c).to_scipy()
+    y = K @ _f64(x)
+    if f is not None:
+        y = y - assemble_load(el, cells, coords, f, f_layout)
+    if dirichlet is not None:
+        y[np.asarray(dirichlet) != 0] = 0.0
+    return y, float(np.dot(y, y))

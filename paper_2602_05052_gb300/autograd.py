@@ -12,6 +12,13 @@ is the adjoint solve of Eq. (adj).
 * ``solve_assembled(p, coords, kappa, layout, f, f_layout, dirichlet)`` -> u
   in one node whose backward calls the fused adjoint kernel (lam U^T enters the
   backward assembly directly; the nnz-sized gradient is never formed).
+* ``residual(p, coords, kappa, layout, c, x, f, f_layout, dirichlet)`` -> the
+  residual vector y = K x - F of Eq. (res1) without storing K (zero on
+  Dirichlet rows); differentiable in x, kappa, f and coords.  Backward, with
+  g the upstream gradient masked to the free rows: dL/dx = K g (the same
+  matrix-free call; K is symmetric), dL/dkappa and dL/dcoords from the fused
+  adjoint backward with lam = g, U = x, and dL/df from the load backward
+  with grad_F = -g.
 """
 from __future__ import annotations
 
@@ -91,9 +98,45 @@ class _SolveAssembled(torch.autograd.Function):
         neg = -lam
         gk, gx, _ = B.tg_assemble_backward(p, coords, kappa, ctx.layout, 0.0, lam=neg, U=u,
                                            grad_kappa=ctx.needs_input_grad[1], grad_coords=True, grad_c=False)
-        gf, _ = B.tg_assemble_load_backward(p, coords, f, ctx.f_layout, 1, lam, grad_f=ctx.needs_input_grad[2],
-                                            grad_coords=gx, accumulate=True)
+        # accumulate adds into both outputs: grad_f starts from zero
+        gf0 = torch.zeros_like(f) if ctx.needs_input_grad[2] else False
+        gf, _ = B.tg_assemble_load_backward(p, coords, f, ctx.f_layout, 1, lam, grad_f=gf0, grad_coords=gx,
+                                            accumulate=True)
         return (gx if ctx.needs_input_grad[0] else None), gk, gf, None, None, None, None, None, None
+
+
+class _Residual(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, coords, kappa, x, f, p, layout, c, f_layout, dirichlet):
+        coords, kappa, x = coords.contiguous(), kappa.contiguous(), x.contiguous()
+        f = f.contiguous() if f is not None else None
+        y, _ = B.tg_residual(p, coords, kappa, layout, c, x, f, f_layout, dirichlet, loss=False)
+        ctx.p, ctx.layout, ctx.c, ctx.f_layout, ctx.dirichlet = p, layout, c, f_layout, dirichlet
+        ctx.has_f = f is not None
+        ctx.save_for_backward(coords, kappa, x, f if f is not None else x)
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        coords, kappa, x, f = ctx.saved_tensors
+        p = ctx.p
+        g = gy.contiguous()
+        if ctx.dirichlet is not None:
+            g = g.masked_fill(ctx.dirichlet.bool(), 0.0)
+        need_x, need_k, need_f = ctx.needs_input_grad[2], ctx.needs_input_grad[1], ctx.needs_input_grad[3]
+        need_c = ctx.needs_input_grad[0]
+        gx_in = B.tg_residual(p, coords, kappa, ctx.layout, ctx.c, g, loss=False)[0] if need_x else None
+        gk = gc = None
+        if need_k or need_c:
+            gk, gc, _ = B.tg_assemble_backward(p, coords, kappa, ctx.layout, ctx.c, lam=g, U=x, grad_kappa=need_k,
+                                               grad_coords=need_c, grad_c=False)
+        gf = None
+        if ctx.has_f and (need_f or need_c):
+            # accumulate adds into both outputs: grad_f starts from zero
+            gf, _ = B.tg_assemble_load_backward(p, coords, f, ctx.f_layout, 1, -g,
+                                                grad_f=torch.zeros_like(f) if need_f else False,
+                                                grad_coords=gc if need_c else False, accumulate=True)
+        return gc, gk, gx_in, gf, None, None, None, None, None
 
 
 def assemble(p, coords, kappa, layout, c=0.0):
@@ -110,3 +153,7 @@ def solve(p, vals, F, dirichlet=None, rtol=1e-12, maxit=100000):
 
 def solve_assembled(p, coords, kappa, layout, f, f_layout, dirichlet=None, rtol=1e-12, maxit=100000):
     return _SolveAssembled.apply(coords, kappa, f, p, layout, f_layout, dirichlet, float(rtol), int(maxit))
+
+
+def residual(p, coords, kappa, layout, c, x, f=None, f_layout=B.PER_NODE, dirichlet=None):
+    return _Residual.apply(coords, kappa, x, f, p, layout, float(c), f_layout, dirichlet)

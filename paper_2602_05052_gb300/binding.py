@@ -64,6 +64,7 @@ def lib():
         "tg_assemble_backward": (i32, [vp, i32, vp, vp, i32, dbl, vp, vp, vp, vp, vp, vp, vp]),
         "tg_assemble_load_backward": (i32, [vp, i32, vp, vp, i32, i32, vp, vp, vp, i32, vp]),
         "tg_assemble_elasticity_backward": (i32, [vp, i32, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]),
+        "tg_residual": (i32, [vp, i32, vp, vp, i32, dbl, vp, vp, i32, vp, vp, vp, vp]),
         "tg_spmv": (i32, [vp, i32, vp, vp, vp, vp]),
         "tg_csr_outer": (i32, [vp, i32, vp, vp, dbl, vp, vp]),
         "tg_cg_solve": (i32, [vp, i32, vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl), vp]),
@@ -298,6 +299,20 @@ def tg_assemble_elasticity_backward(p: Pattern, coords, lam, mu, layout: int, gr
                                                  _ptr(gx, dt, "grad_coords"), _stream(stream)),
            "tg_assemble_elasticity_backward")
     return gl, gm, gx
+
+
+def tg_residual(p: Pattern, coords, kappa, layout: int, c: float, x, f=None, f_layout: int = PER_NODE, dirichlet=None,
+                y=None, loss=True, stream=None):
+    """Matrix-free y = K x - F (F omitted when f is None); returns (y, loss [1] or None)."""
+    dt = coords.dtype
+    if y is None:
+        y = torch.empty_like(x)
+    ls = _out(loss, lambda: torch.empty(1, dtype=dt, device=coords.device))
+    _check(lib().tg_residual(p.handle, _dt(coords), _ptr(coords, dt, "coords"), _ptr(kappa, dt, "kappa"), layout,
+                             float(c), _ptr(x, dt, "x"), _ptr(f, dt, "f"), f_layout,
+                             _ptr(dirichlet, torch.uint8, "dirichlet"), _ptr(y, dt, "y"), _ptr(ls, dt, "loss"),
+                             _stream(stream)), "tg_residual")
+    return y, ls
 
 
 def tg_csr_outer(p: Pattern, lam, U, alpha: float = 1.0, out=None, stream=None):

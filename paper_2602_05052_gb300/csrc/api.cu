@@ -208,6 +208,9 @@ tg_status tg_get_device_status(const tg_pattern* p, int64_t* first_bad_elem) {
   TG_CK(cudaMemcpy(h, p->status, sizeof(h), cudaMemcpyDeviceToHost));
   const unsigned long long reset[2] = {0ull, ~0ull};
   TG_CK(cudaMemcpy(p->status, reset, sizeof(reset), cudaMemcpyHostToDevice));
+  // a CTA that gave up on a timed-out wait never arrived: restart the
+  // arrival counter of the last-CTA sums
+  if (h[0] == TG_ERR_TIMEOUT && p->arrivals) TG_CK(cudaMemset(p->arrivals, 0, 16));
   if (first_bad_elem) *first_bad_elem = (h[1] == ~0ull) ? -1 : (int64_t)h[1];
   return (tg_status)h[0];
 }

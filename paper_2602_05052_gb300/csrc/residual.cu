@@ -1,0 +1,330 @@
+// Matrix-free residual of the Galerkin system, the quantity of the
+// physics-informed loss of Eq. (res1):
+//   y = K(kappa, c) x - F(f),  loss = sum_i y_i^2 over the free rows,
+// computed element by element without storing K: the Map of Algorithm 1
+// evaluates K_e and F_e and contracts K_e with the element's values of x;
+// the Reduce sums the NV element results of every node in increasing
+// element order (the node-level routing S_vec of Algorithm 2).
+//
+// Two kernels:
+//   k_residual_blk    - element-once row blocks (blocks.cuh): each distinct
+//                       element of a block is evaluated once;
+//   k_residual_gather - patterns without row blocks: one thread per
+//                       incidence evaluates its element (the same
+//                       arithmetic, so both give identical bits).
+// The loss is summed in FP64: per thread in row order, per CTA in a fixed
+// tree, then the last CTA to finish adds the CTA partials in CTA order.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+
+#include "blocks.cuh"
+
+namespace {
+
+constexpr int RT = 128;    // threads per CTA (rows per CTA of the gather kernel)
+constexpr int kSlots = 4;  // doubles per CTA in the pattern's partials array
+
+template <typename T>
+struct ResArgs {
+  tg::FwdArgs<T> fa;  // coords, coef (kappa), layout, c, f, f_layout, status, cells, inc_ptr, inc_e
+  const T* __restrict__ x;
+  const uint8_t* __restrict__ dir;
+  T* __restrict__ y;
+  T* loss;
+  double* __restrict__ partials;
+  unsigned int* arrivals;
+};
+
+// Row a of the element's result: sum_b K_e[a][b] x_b (b ascending, first
+// product then fused multiply-adds) minus F_e[a] with the load term.
+template <int NV, typename T>
+__device__ __forceinline__ T kx_row(const T (&K)[NV * (NV + 1) / 2], const T (&xv)[NV], int a) {
+  T s = T(0);
+#pragma unroll
+  for (int b = 0; b < NV; ++b) {
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    const T kab = K[lo * NV - lo * (lo - 1) / 2 + (hi - lo)];
+    s = b == 0 ? kab * xv[0] : fma(kab, xv[b], s);
+  }
+  return s;
+}
+
+// The NV results of element e (vertex ids vid, all NV nodes); zeros and a
+// recorded error for a degenerate element.
+template <int EL, typename T, bool LOADF>
+__device__ __forceinline__ void element_result(const ResArgs<T>& r, const tg::RefTab<T>& tab, int64_t e,
+                                               const int (&vid)[tg::Elem<EL>::nv], T (&ye)[tg::Elem<EL>::nv]) {
+  constexpr int NV = tg::Elem<EL>::nv, NG = tg::Elem<EL>::ngeo;
+  tg::ElemIn<EL, T> in;
+#pragma unroll
+  for (int c = 0; c < NG; ++c) in.v[c] = vid[c];
+  tg::elem_data<EL, T>(r.fa, e, in);
+  T xv[NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) xv[c] = __ldg(r.x + vid[c]);
+  T fv[NV];
+  if constexpr (LOADF) tg::p1_load_f<NV, T>(r.fa.f, r.fa.f_layout, e, vid, fv);
+  T K[NV * (NV + 1) / 2];
+  T adet;
+  bool ok;
+  if constexpr (EL == TG_P2_TRI) ok = tg::p2_elem_sym<T>(in, r.fa.c, tab, K, &adet);
+  else ok = tg::p1_elem_sym<EL, T>(in, r.fa.c, tab, K, &adet);
+  if (!ok) {
+    tg::record_error(r.fa.status, TG_ERR_DEGENERATE_ELEMENT, e);
+#pragma unroll
+    for (int a = 0; a < NV; ++a) ye[a] = T(0);
+    return;
+  }
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    T s = kx_row<NV, T>(K, xv, a);
+    if constexpr (LOADF) s -= tg::p1_load_entry<NV, T>(r.fa.f_layout, adet, fv, tab, a);
+    ye[a] = s;
+  }
+}
+
+// Fixed-order block sum (warp tree, then warp 0 over the warps); the result
+// is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();  // red may still be read by a previous call
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+  }
+  return v;
+}
+
+// CTA partial, then the last CTA to arrive sums all partials in CTA order
+// and writes the loss (no CTA waits for another).
+template <typename T>
+__device__ __forceinline__ void finish_loss(const ResArgs<T>& r, double part) {
+  __shared__ double red[RT / 32];
+  __shared__ bool s_last;
+  part = block_sum(part, red);
+  if (threadIdx.x == 0) {
+    r.partials[kSlots * blockIdx.x] = part;
+    __threadfence();
+    s_last = atomicInc(r.arrivals, gridDim.x - 1) == gridDim.x - 1;  // wraps to 0 for the next launch
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double s = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(r.partials + kSlots * b);
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) *r.loss = (T)s;
+}
+
+// Element-once row blocks: Map the block's distinct elements into
+// Ye[NV][capE], Reduce the rows (increasing element order), apply the
+// Dirichlet mask, write y and add y^2 to this thread's loss term.
+template <int EL, typename T, int UB, bool LOADF>
+__global__ void __launch_bounds__(RT) k_residual_blk(const ResArgs<T> r, const __grid_constant__ tg::RefTab<T> tab,
+                                                    const tg::BlkArgs g) {
+  constexpr int NV = tg::Elem<EL>::nv;
+  extern __shared__ __align__(16) unsigned char smem[];
+  tg::BlkPipe pipe;
+  T* Ye = reinterpret_cast<T*>(pipe.init(smem, g));
+  __syncthreads();  // publishes the mbarrier initialisation
+  double part = 0.0;
+  TG_BLK_PIPELINE_BEGIN(pipe, g, r.fa.status)
+  for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * NT_) {
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int j = j0 + u * NT_;
+      if (j >= v.nbe) break;
+      int vid[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) vid[c] = v.vtx(c, j);
+      T ye[NV];
+      element_result<EL, T, LOADF>(r, tab, tg::bel_elem(v.be[j]), vid, ye);
+#pragma unroll
+      for (int a = 0; a < NV; ++a) Ye[a * g.capE + j] = ye[a];
+    }
+  }
+  __syncthreads();
+  {
+    const int i = v.r0 + (int)threadIdx.x;
+    if (i < v.r1) {
+      T s = T(0);
+      const int je = v.ip[i + 1];
+      for (int j = v.ip[i]; j < je; ++j) {
+        const auto rc = tg::blk_rec<NV>(v.rc, j);
+        s += Ye[rc.a() * g.capE + rc.le()];
+      }
+      const int node = v.pm[i];
+      if (r.dir && r.dir[node]) s = T(0);
+      r.y[node] = s;
+      part += (double)s * (double)s;
+    }
+    __syncthreads();  // stage s and Ye are free again
+  }
+  TG_BLK_PIPELINE_END
+  if (r.loss) finish_loss(r, part);
+}
+
+// Patterns without row blocks: a CTA owns RT consecutive rows and their
+// incidence range; one thread per incidence evaluates its element's result
+// for the incidence's vertex into shared memory, then one thread per row
+// sums in increasing element order.
+template <int EL, typename T, bool LOADF>
+__global__ void __launch_bounds__(RT) k_residual_gather(const ResArgs<T> r, const __grid_constant__ tg::RefTab<T> tab,
+                                                       int cap) {
+  constexpr int NV = tg::Elem<EL>::nv;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* contrib = reinterpret_cast<T*>(smem);
+  const int64_t N = r.fa.n;
+  const int64_t r0 = (int64_t)blockIdx.x * RT;
+  const int64_t r1 = r0 + RT < N ? r0 + RT : N;
+  const int J0 = __ldg(r.fa.inc_ptr + r0), J1 = __ldg(r.fa.inc_ptr + r1);
+  for (int j = J0 + (int)threadIdx.x; j < J1; j += RT) {
+    const int ea = __ldg(r.fa.inc_e + j);
+    const int64_t e = ea >> 3;
+    const int la = ea & 7;
+    int vid[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) vid[c] = __ldg(r.fa.cells + e * NV + c);
+    T ye[NV];
+    element_result<EL, T, LOADF>(r, tab, e, vid, ye);
+    T out = ye[0];
+#pragma unroll
+    for (int a = 1; a < NV; ++a)
+      if (la == a) out = ye[a];
+    contrib[j - J0] = out;
+  }
+  __syncthreads();
+  double part = 0.0;
+  const int64_t i = r0 + threadIdx.x;
+  if (i < r1) {
+    const int js = __ldg(r.fa.inc_ptr + i) - J0, je = __ldg(r.fa.inc_ptr + i + 1) - J0;
+    T s = T(0);
+    for (int m = js; m < je; ++m) s += contrib[m];
+    if (r.dir && r.dir[i]) s = T(0);
+    r.y[i] = s;
+    part = (double)s * (double)s;
+  }
+  if (r.loss) finish_loss(r, part);
+}
+
+template <int EL, typename T, bool LOADF>
+tg_status launch_el(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t s) {
+  constexpr int NV = tg::Elem<EL>::nv;
+  const tg::RefTab<T>& tab = tg::table<T>((tg_element)EL);
+  const int64_t cap_ctas = (p->n_partials - 4) / kSlots;  // partial slots of the pattern
+  if (p->bel && p->blk_rows <= RT) {
+    const tg::BlkArgs g = tg::blk_args(p);
+    const size_t smem = tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE, NV) + (size_t)NV * g.capE * sizeof(T);
+    if (smem <= 113 * 1024) {
+      const int need = (p->blk_max_elems + RT - 1) / RT;
+      tg_status st = TG_OK;
+      auto go = [&](auto kern) {
+        if ((st = tg::set_smem((const void*)kern, smem)) != TG_OK) return;
+        int per_sm = 0;
+        cudaError_t ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RT, smem);
+        if (ce != cudaSuccess) {
+          st = tg::cuda_fail(ce, "cudaOccupancyMaxActiveBlocksPerMultiprocessor", __FILE__, __LINE__);
+          return;
+        }
+        const int grid =
+            (int)std::min<int64_t>({p->n_blk, (int64_t)std::max(per_sm, 1) * tg::sm_count(), cap_ctas});
+        kern<<<grid, RT, smem, s>>>(r, tab, g);
+      };
+      if (need <= 2) go(k_residual_blk<EL, T, 2, LOADF>);
+      else go(k_residual_blk<EL, T, 4, LOADF>);
+      if (st != TG_OK) return st;
+      TG_CK_LAUNCH("k_residual_blk");
+      return TG_OK;
+    }
+  }
+  const int64_t grid = tg::grid_for(p->N, RT);
+  const int cap = std::max(1, RT * p->max_deg);
+  const size_t smem = (size_t)cap * sizeof(T);
+  if (grid > cap_ctas || smem > 200 * 1024) {
+    tg::set_error("tg_residual: mesh degree too large");
+    return TG_ERR_UNSUPPORTED;
+  }
+  auto kern = k_residual_gather<EL, T, LOADF>;
+  tg_status st = tg::set_smem((const void*)kern, smem);
+  if (st != TG_OK) return st;
+  kern<<<(unsigned)grid, RT, smem, s>>>(r, tab, cap);
+  TG_CK_LAUNCH("k_residual_gather");
+  return TG_OK;
+}
+
+template <typename T>
+tg_status residual(const tg_pattern* p, const void* coords, const void* kappa, tg_layout kl, double c, const void* x,
+                   const void* f, tg_layout fl, const uint8_t* dir, void* y, void* loss, cudaStream_t s) {
+  ResArgs<T> r;
+  std::memset(&r, 0, sizeof(r));
+  r.fa.inc_ptr = p->inc_ptr;
+  r.fa.inc_e = p->inc_e;
+  r.fa.cells = p->cells;
+  r.fa.coords = static_cast<const T*>(coords);
+  r.fa.coef = static_cast<const T*>(kappa);
+  r.fa.layout = kl;
+  r.fa.c = (T)c;
+  r.fa.n = p->N;
+  r.fa.status = p->status;
+  r.fa.f = static_cast<const T*>(f);
+  r.fa.f_layout = fl;
+  r.x = static_cast<const T*>(x);
+  r.dir = dir;
+  r.y = static_cast<T*>(y);
+  r.loss = static_cast<T*>(loss);
+  r.partials = p->partials;
+  r.arrivals = p->arrivals;
+  const bool lf = f != nullptr;
+  switch (p->el) {
+    case TG_P1_TRI:
+      return lf ? launch_el<TG_P1_TRI, T, true>(p, r, s) : launch_el<TG_P1_TRI, T, false>(p, r, s);
+    case TG_P1_TET:
+      return lf ? launch_el<TG_P1_TET, T, true>(p, r, s) : launch_el<TG_P1_TET, T, false>(p, r, s);
+    default:
+      return launch_el<TG_P2_TRI, T, false>(p, r, s);
+  }
+}
+
+bool aligned_to(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+tg_status tg_residual(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
+                      tg_layout kappa_layout, double c, const void* x, const void* f, tg_layout f_layout,
+                      const uint8_t* dirichlet, void* y, void* loss, tg_stream stream) {
+  if (!p || (dtype != TG_F32 && dtype != TG_F64)) return TG_ERR_INVALID_ARG;
+  if (p->el == TG_P1_TET_VEC3) return TG_ERR_INVALID_ARG;
+  if (!(kappa_layout == TG_PER_QP || kappa_layout == TG_PER_ELEMENT || kappa_layout == TG_CONSTANT)) return TG_ERR_INVALID_ARG;
+  if (f && !(f_layout == TG_PER_NODE || f_layout == TG_PER_QP || f_layout == TG_CONSTANT)) return TG_ERR_INVALID_ARG;
+  if (f && p->el == TG_P2_TRI) {
+    tg::set_error("tg_residual: the load term is built for P1 elements");
+    return TG_ERR_UNSUPPORTED;
+  }
+  const size_t es = dtype == TG_F32 ? 4 : 8;
+  if (p->N > 0 && (!coords || !kappa || !x || !y)) return TG_ERR_INVALID_ARG;
+  if (x && x == y) {
+    tg::set_error("tg_residual: x and y must be distinct buffers");
+    return TG_ERR_INVALID_ARG;
+  }
+  if (f && f == y) return TG_ERR_INVALID_ARG;
+  if (coords && !aligned_to(coords, tg::dim_of(p->el) == 2 ? 2 * es : es)) {
+    tg::set_error("coords must be aligned to 2 * sizeof(dtype) for 2D meshes");
+    return TG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p->N == 0) {
+    if (loss) TG_CK(cudaMemsetAsync(loss, 0, es, s));
+    return TG_OK;
+  }
+  return dtype == TG_F32 ? residual<float>(p, coords, kappa, kappa_layout, c, x, f, f_layout, dirichlet, y, loss, s)
+                         : residual<double>(p, coords, kappa, kappa_layout, c, x, f, f_layout, dirichlet, y, loss, s);
+}
+
+}  // extern "C"
