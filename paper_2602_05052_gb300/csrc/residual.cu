@@ -50,26 +50,38 @@ __device__ __forceinline__ T kx_row(const T (&K)[NV * (NV + 1) / 2], const T (&x
   return s;
 }
 
-// The NV results of element e (vertex ids vid, all NV nodes); zeros and a
-// recorded error for a degenerate element.
-template <int EL, typename T, bool LOADF>
-__device__ __forceinline__ void element_result(const ResArgs<T>& r, const tg::RefTab<T>& tab, int64_t e,
-                                               const int (&vid)[tg::Elem<EL>::nv], T (&ye)[tg::Elem<EL>::nv]) {
-  constexpr int NV = tg::Elem<EL>::nv, NG = tg::Elem<EL>::ngeo;
+// Inputs of one element's result: geometry and coefficient (ElemIn), the
+// values of x at its NV nodes and, with the load term, f as F_e needs it.
+template <int EL, typename T>
+struct ResIn {
   tg::ElemIn<EL, T> in;
+  T xv[tg::Elem<EL>::nv];
+  T fv[tg::Elem<EL>::nv];
+};
+
+template <int EL, typename T, bool LOADF>
+__device__ __forceinline__ void result_inputs(const ResArgs<T>& r, int64_t e, const int (&vid)[tg::Elem<EL>::nv],
+                                              ResIn<EL, T>& d) {
+  constexpr int NV = tg::Elem<EL>::nv, NG = tg::Elem<EL>::ngeo;
 #pragma unroll
-  for (int c = 0; c < NG; ++c) in.v[c] = vid[c];
-  tg::elem_data<EL, T>(r.fa, e, in);
-  T xv[NV];
+  for (int c = 0; c < NG; ++c) d.in.v[c] = vid[c];
+  tg::elem_data<EL, T>(r.fa, e, d.in);
 #pragma unroll
-  for (int c = 0; c < NV; ++c) xv[c] = __ldg(r.x + vid[c]);
-  T fv[NV];
-  if constexpr (LOADF) tg::p1_load_f<NV, T>(r.fa.f, r.fa.f_layout, e, vid, fv);
+  for (int c = 0; c < NV; ++c) d.xv[c] = __ldg(r.x + vid[c]);
+  if constexpr (LOADF) tg::p1_load_f<NV, T>(r.fa.f, r.fa.f_layout, e, vid, d.fv);
+}
+
+// The NV results of element e; zeros and a recorded error for a degenerate
+// element.
+template <int EL, typename T, bool LOADF>
+__device__ __forceinline__ void result_compute(const ResArgs<T>& r, const tg::RefTab<T>& tab, int64_t e,
+                                               const ResIn<EL, T>& d, T (&ye)[tg::Elem<EL>::nv]) {
+  constexpr int NV = tg::Elem<EL>::nv;
   T K[NV * (NV + 1) / 2];
   T adet;
   bool ok;
-  if constexpr (EL == TG_P2_TRI) ok = tg::p2_elem_sym<T>(in, r.fa.c, tab, K, &adet);
-  else ok = tg::p1_elem_sym<EL, T>(in, r.fa.c, tab, K, &adet);
+  if constexpr (EL == TG_P2_TRI) ok = tg::p2_elem_sym<T>(d.in, r.fa.c, tab, K, &adet);
+  else ok = tg::p1_elem_sym<EL, T>(d.in, r.fa.c, tab, K, &adet);
   if (!ok) {
     tg::record_error(r.fa.status, TG_ERR_DEGENERATE_ELEMENT, e);
 #pragma unroll
@@ -78,8 +90,8 @@ __device__ __forceinline__ void element_result(const ResArgs<T>& r, const tg::Re
   }
 #pragma unroll
   for (int a = 0; a < NV; ++a) {
-    T s = kx_row<NV, T>(K, xv, a);
-    if constexpr (LOADF) s -= tg::p1_load_entry<NV, T>(r.fa.f_layout, adet, fv, tab, a);
+    T s = kx_row<NV, T>(K, d.xv, a);
+    if constexpr (LOADF) s -= tg::p1_load_entry<NV, T>(r.fa.f_layout, adet, d.fv, tab, a);
     ye[a] = s;
   }
 }
@@ -135,15 +147,24 @@ __global__ void __launch_bounds__(RT) k_residual_blk(const ResArgs<T> r, const _
   double part = 0.0;
   TG_BLK_PIPELINE_BEGIN(pipe, g, r.fa.status)
   for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * NT_) {
+    // all loads of the thread's UB elements first, then the arithmetic
+    int64_t e[UB];
+    ResIn<EL, T> d[UB];
 #pragma unroll
     for (int u = 0; u < UB; ++u) {
-      const int j = j0 + u * NT_;
-      if (j >= v.nbe) break;
+      const int j = j0 + u * NT_ < v.nbe ? j0 + u * NT_ : 0;  // idle slots load element 0 of the list
       int vid[NV];
 #pragma unroll
       for (int c = 0; c < NV; ++c) vid[c] = v.vtx(c, j);
+      e[u] = tg::bel_elem(v.be[j]);
+      result_inputs<EL, T, LOADF>(r, e[u], vid, d[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int j = j0 + u * NT_;
+      if (j >= v.nbe) continue;
       T ye[NV];
-      element_result<EL, T, LOADF>(r, tab, tg::bel_elem(v.be[j]), vid, ye);
+      result_compute<EL, T, LOADF>(r, tab, e[u], d[u], ye);
 #pragma unroll
       for (int a = 0; a < NV; ++a) Ye[a * g.capE + j] = ye[a];
     }
@@ -190,8 +211,10 @@ __global__ void __launch_bounds__(RT) k_residual_gather(const ResArgs<T> r, cons
     int vid[NV];
 #pragma unroll
     for (int c = 0; c < NV; ++c) vid[c] = __ldg(r.fa.cells + e * NV + c);
+    ResIn<EL, T> d;
+    result_inputs<EL, T, LOADF>(r, e, vid, d);
     T ye[NV];
-    element_result<EL, T, LOADF>(r, tab, e, vid, ye);
+    result_compute<EL, T, LOADF>(r, tab, e, d, ye);
     T out = ye[0];
 #pragma unroll
     for (int a = 1; a < NV; ++a)
@@ -235,8 +258,13 @@ tg_status launch_el(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t s) {
             (int)std::min<int64_t>({p->n_blk, (int64_t)std::max(per_sm, 1) * tg::sm_count(), cap_ctas});
         kern<<<grid, RT, smem, s>>>(r, tab, g);
       };
-      if (need <= 2) go(k_residual_blk<EL, T, 2, LOADF>);
-      else go(k_residual_blk<EL, T, 4, LOADF>);
+      if constexpr (sizeof(T) == 8 || EL == TG_P2_TRI) {
+        go(k_residual_blk<EL, T, 2, LOADF>);
+      } else {
+        if (need <= 2) go(k_residual_blk<EL, T, 2, LOADF>);
+        else if (need == 3) go(k_residual_blk<EL, T, 3, LOADF>);
+        else go(k_residual_blk<EL, T, 4, LOADF>);
+      }
       if (st != TG_OK) return st;
       TG_CK_LAUNCH("k_residual_blk");
       return TG_OK;
