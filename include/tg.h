@@ -214,9 +214,10 @@ tg_status tg_assemble_load(const tg_pattern* p, tg_dtype dtype, const void* coor
  *   x, y [N]   distinct buffers (TG_ERR_INVALID_ARG otherwise).
  * Elements P1_TRI, P2_TRI, P1_TET; the load term on P1 only
  * (TG_ERR_UNSUPPORTED for P2 with f).  Deterministic: every y[i] sums its
- * element results in increasing element order.  Uses the pattern's partial-
- * sum buffer like tg_assemble_backward: calls on one pattern that overlap
- * (several streams) race.
+ * element results in increasing element order.  Uses the pattern's per-
+ * element scratch and partial-sum buffers (the latter like
+ * tg_assemble_backward): calls on one pattern that overlap (several
+ * streams) race.
  * Reverse mode, for an upstream gradient gy of y that is zero on Dirichlet
  * rows: dL/dx = K gy (this call with x = gy, f = NULL; K is symmetric);
  * dL/dkappa, dL/dc and the K part of dL/dcoords from tg_assemble_backward

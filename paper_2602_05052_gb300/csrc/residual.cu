@@ -6,12 +6,14 @@
 // the Reduce sums the NV element results of every node in increasing
 // element order (the node-level routing S_vec of Algorithm 2).
 //
-// Two kernels:
+// Two forms, with the same per-element arithmetic and the same summation
+// order, hence identical bits:
 //   k_residual_blk    - element-once row blocks (blocks.cuh): each distinct
-//                       element of a block is evaluated once;
-//   k_residual_gather - patterns without row blocks: one thread per
-//                       incidence evaluates its element (the same
-//                       arithmetic, so both give identical bits).
+//                       element of a block is evaluated once (FP32);
+//   k_residual_map +  - two passes through a per-element scratch array:
+//   k_residual_reduce   every element evaluated exactly once (FP64, and
+//                       patterns without row blocks);
+// A mesh without elements has y = 0.
 // The loss is summed in FP64: per thread in row order, per CTA in a fixed
 // tree, then the last CTA to finish adds the CTA partials in CTA order.
 #include <algorithm>
@@ -190,44 +192,48 @@ __global__ void __launch_bounds__(RT) k_residual_blk(const ResArgs<T> r, const _
   if (r.loss) finish_loss(r, part);
 }
 
-// Patterns without row blocks: a CTA owns RT consecutive rows and their
-// incidence range; one thread per incidence evaluates its element's result
-// for the incidence's vertex into shared memory, then one thread per row
-// sums in increasing element order.
-template <int EL, typename T, bool LOADF>
-__global__ void __launch_bounds__(RT) k_residual_gather(const ResArgs<T> r, const __grid_constant__ tg::RefTab<T> tab,
-                                                       int cap) {
+// Two passes.  Map: one thread per element writes its NV results to
+// ye[e][a] (each element evaluated exactly once; consecutive threads write
+// consecutive elements).  Reduce: one thread per node sums its incidences'
+// results in increasing element order (the incidence lists are sorted by
+// element), so every y[i] carries the bits of the one-pass kernels.
+template <int EL, typename T, bool LOADF, int EPT>
+__global__ void __launch_bounds__(RT) k_residual_map(const ResArgs<T> r, const __grid_constant__ tg::RefTab<T> tab,
+                                                    int64_t E, T* __restrict__ ye) {
   constexpr int NV = tg::Elem<EL>::nv;
-  extern __shared__ __align__(16) unsigned char smem[];
-  T* contrib = reinterpret_cast<T*>(smem);
-  const int64_t N = r.fa.n;
-  const int64_t r0 = (int64_t)blockIdx.x * RT;
-  const int64_t r1 = r0 + RT < N ? r0 + RT : N;
-  const int J0 = __ldg(r.fa.inc_ptr + r0), J1 = __ldg(r.fa.inc_ptr + r1);
-  for (int j = J0 + (int)threadIdx.x; j < J1; j += RT) {
-    const int ea = __ldg(r.fa.inc_e + j);
-    const int64_t e = ea >> 3;
-    const int la = ea & 7;
+  const int64_t e0 = (int64_t)blockIdx.x * (RT * EPT) + threadIdx.x;
+  int64_t e[EPT];
+  ResIn<EL, T> d[EPT];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    e[u] = e0 + u * RT;
+    const int64_t ee = e[u] < E ? e[u] : E - 1;
     int vid[NV];
 #pragma unroll
-    for (int c = 0; c < NV; ++c) vid[c] = __ldg(r.fa.cells + e * NV + c);
-    ResIn<EL, T> d;
-    result_inputs<EL, T, LOADF>(r, e, vid, d);
-    T ye[NV];
-    result_compute<EL, T, LOADF>(r, tab, e, d, ye);
-    T out = ye[0];
-#pragma unroll
-    for (int a = 1; a < NV; ++a)
-      if (la == a) out = ye[a];
-    contrib[j - J0] = out;
+    for (int c = 0; c < NV; ++c) vid[c] = __ldg(r.fa.cells + ee * NV + c);
+    result_inputs<EL, T, LOADF>(r, ee, vid, d[u]);
   }
-  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    if (e[u] >= E) break;
+    T out[NV];
+    result_compute<EL, T, LOADF>(r, tab, e[u], d[u], out);
+#pragma unroll
+    for (int a = 0; a < NV; ++a) ye[e[u] * NV + a] = out[a];
+  }
+}
+
+template <int NV, typename T>
+__global__ void __launch_bounds__(RT) k_residual_reduce(const ResArgs<T> r, const T* __restrict__ ye) {
+  const int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x;
   double part = 0.0;
-  const int64_t i = r0 + threadIdx.x;
-  if (i < r1) {
-    const int js = __ldg(r.fa.inc_ptr + i) - J0, je = __ldg(r.fa.inc_ptr + i + 1) - J0;
+  if (i < r.fa.n) {
+    const int j0 = __ldg(r.fa.inc_ptr + i), j1 = __ldg(r.fa.inc_ptr + i + 1);
     T s = T(0);
-    for (int m = js; m < je; ++m) s += contrib[m];
+    for (int j = j0; j < j1; ++j) {
+      const int ea = __ldg(r.fa.inc_e + j);
+      s += ye[(int64_t)(ea >> 3) * NV + (ea & 7)];
+    }
     if (r.dir && r.dir[i]) s = T(0);
     r.y[i] = s;
     part = (double)s * (double)s;
@@ -236,14 +242,34 @@ __global__ void __launch_bounds__(RT) k_residual_gather(const ResArgs<T> r, cons
 }
 
 template <int EL, typename T, bool LOADF>
-tg_status launch_el(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t s) {
-  constexpr int NV = tg::Elem<EL>::nv;
+tg_status launch_two_pass(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t s) {
+  constexpr int NV = tg::Elem<EL>::nv, EPT = 2;
   const tg::RefTab<T>& tab = tg::table<T>((tg_element)EL);
-  const int64_t cap_ctas = (p->n_partials - 4) / kSlots;  // partial slots of the pattern
-  if (p->bel && p->blk_rows <= RT) {
+  T* ye = static_cast<T*>(p->elem_scratch);
+  const int64_t gm = (p->E + RT * EPT - 1) / (RT * EPT);
+  k_residual_map<EL, T, LOADF, EPT><<<(unsigned)gm, RT, 0, s>>>(r, tab, p->E, ye);
+  TG_CK_LAUNCH("k_residual_map");
+  const int64_t gr = tg::grid_for(p->N, RT);
+  if (gr > (p->n_partials - 4) / kSlots) return TG_ERR_UNSUPPORTED;
+  k_residual_reduce<NV, T><<<(unsigned)gr, RT, 0, s>>>(r, ye);
+  TG_CK_LAUNCH("k_residual_reduce");
+  return TG_OK;
+}
+
+template <int EL, typename T, bool LOADF>
+tg_status launch_el(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t s) {
+  // FP32 runs on the row blocks.  FP64, and patterns without row blocks,
+  // take the two passes: FP64 is bound by the FP64 pipe, where evaluating
+  // each element exactly once beats the 1.2 evaluations per element of the
+  // row blocks.
+  constexpr int NV = tg::Elem<EL>::nv;
+  if constexpr (sizeof(T) == 4) {
+    const tg::RefTab<T>& tab = tg::table<T>((tg_element)EL);
+    const int64_t cap_ctas = (p->n_partials - 4) / kSlots;  // partial slots of the pattern
     const tg::BlkArgs g = tg::blk_args(p);
-    const size_t smem = tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE, NV) + (size_t)NV * g.capE * sizeof(T);
-    if (smem <= 113 * 1024) {
+    const size_t smem = p->bel ? tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE, NV) + (size_t)NV * g.capE * sizeof(T)
+                               : 0;
+    if (p->bel && p->blk_rows <= RT && smem <= 113 * 1024) {
       const int need = (p->blk_max_elems + RT - 1) / RT;
       tg_status st = TG_OK;
       auto go = [&](auto kern) {
@@ -258,7 +284,7 @@ tg_status launch_el(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t s) {
             (int)std::min<int64_t>({p->n_blk, (int64_t)std::max(per_sm, 1) * tg::sm_count(), cap_ctas});
         kern<<<grid, RT, smem, s>>>(r, tab, g);
       };
-      if constexpr (sizeof(T) == 8 || EL == TG_P2_TRI) {
+      if constexpr (EL == TG_P2_TRI) {
         go(k_residual_blk<EL, T, 2, LOADF>);
       } else {
         if (need <= 2) go(k_residual_blk<EL, T, 2, LOADF>);
@@ -270,18 +296,10 @@ tg_status launch_el(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t s) {
       return TG_OK;
     }
   }
-  const int64_t grid = tg::grid_for(p->N, RT);
-  const int cap = std::max(1, RT * p->max_deg);
-  const size_t smem = (size_t)cap * sizeof(T);
-  if (grid > cap_ctas || smem > 200 * 1024) {
-    tg::set_error("tg_residual: mesh degree too large");
-    return TG_ERR_UNSUPPORTED;
-  }
-  auto kern = k_residual_gather<EL, T, LOADF>;
-  tg_status st = tg::set_smem((const void*)kern, smem);
-  if (st != TG_OK) return st;
-  kern<<<(unsigned)grid, RT, smem, s>>>(r, tab, cap);
-  TG_CK_LAUNCH("k_residual_gather");
+  if (p->elem_scratch) return launch_two_pass<EL, T, LOADF>(p, r, s);
+  // no elements: y = 0 and loss = 0
+  TG_CK(cudaMemsetAsync(r.y, 0, (size_t)p->N * sizeof(T), s));
+  if (r.loss) TG_CK(cudaMemsetAsync(r.loss, 0, sizeof(T), s));
   return TG_OK;
 }
 

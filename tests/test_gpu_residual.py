@@ -86,8 +86,9 @@ def test_residual_is_bitwise_deterministic(tg, dtype):
 
 def test_residual_without_row_blocks(tg):
     """A random numbering of a 90,601-node mesh leaves the pattern without
-    row blocks: the gather kernel serves the call, with the same bits as the
-    block kernel on the same elements (only the node numbering differs)."""
+    row blocks: the two-pass kernels serve the call, with the same bits as
+    the row-block kernel on the same elements (only the node numbering
+    differs)."""
     m = jittered_tri(300)
     g = np.random.default_rng(72)
     relabel = g.permutation(m.n_nodes)
@@ -101,16 +102,17 @@ def test_residual_without_row_blocks(tg):
     dirichlet[relabel[m.boundary]] = True
     p = tg.tg_build_pattern(dev(cells, torch.int32), m.n_nodes, mg.P1_TRI)
     assert p.n_blocks == 0
-    y, loss = tg.tg_residual(p, dev(X, torch.float64), dev(k, torch.float64), mg.PER_QP, 0.2, dev(xr, torch.float64),
-                             dev(fr, torch.float64), mg.PER_NODE, dev(dirichlet.astype(np.uint8), torch.uint8))
-    want, wl = O.residual(mg.P1_TRI, cells, X, k, O.PER_QP, 0.2, xr, fr, O.PER_NODE, dirichlet)
-    assert relfro(y.cpu().numpy(), want) <= 1e-12 and abs(loss.item() - wl) <= 1e-11 * wl
-    q = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
-    assert q.n_blocks > 0
-    yb, lb = tg.tg_residual(q, dev(m.coords, torch.float64), dev(k, torch.float64), mg.PER_QP, 0.2,
-                            dev(x, torch.float64), dev(f, torch.float64), mg.PER_NODE,
-                            dev(m.boundary.astype(np.uint8), torch.uint8))
-    assert torch.equal(y[torch.as_tensor(relabel, device="cuda")], yb)
+    for dt in DTYPES:
+        y, loss = tg.tg_residual(p, dev(X, dt), dev(k, dt), mg.PER_QP, 0.2, dev(xr, dt), dev(fr, dt), mg.PER_NODE,
+                                 dev(dirichlet.astype(np.uint8), torch.uint8))
+        want, wl = O.residual(mg.P1_TRI, cells, host_as(X, dt), host_as(k, dt), O.PER_QP, 0.2, host_as(xr, dt),
+                              host_as(fr, dt), O.PER_NODE, dirichlet)
+        assert relfro(y.cpu().numpy(), want) <= TOL[dt] and abs(loss.item() - wl) <= LOSS_TOL[dt] * wl
+        q = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
+        assert q.n_blocks > 0
+        yb, lb = tg.tg_residual(q, dev(m.coords, dt), dev(k, dt), mg.PER_QP, 0.2, dev(x, dt), dev(f, dt),
+                                mg.PER_NODE, dev(m.boundary.astype(np.uint8), torch.uint8))
+        assert torch.equal(y[torch.as_tensor(relabel, device="cuda")], yb)
 
 
 def test_reverse_mode_and_gradcheck(tg):
