@@ -81,8 +81,9 @@ struct tg_pattern {
   // arrival counter of the element-once backward's CTAs (zero between
   // launches: the last CTA to arrive wraps it back to zero)
   unsigned int* arrivals = nullptr;
-  // per-element results of the two-pass residual: nv values of up to 8
-  // bytes per element (scalar element kinds)
+  // per-element results of the two-pass kernels (residual: nv values;
+  // backward: nv x dim coordinate gradients), up to 8 bytes each (scalar
+  // element kinds)
   void* elem_scratch = nullptr;
 };
 
