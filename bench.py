@@ -494,6 +494,7 @@ def extras(tg, torch, dev, m, cfg, p, peak, flush):
             "fwd_plus_bwd_elements_per_s": E / (ms_f + ms_b) * 1e3, "load_ms": ms_l,
             "system_ms": ms_s, "system_alg_GBps": alg_bytes("system", E, N, nnz, s) / ms_s / 1e6}
     out.update(residual_extras(tg, torch, dev, m, cfg, p, peak, flush))
+    out.update(facet_extras(tg, torch, dev, m, p, flush))
     out["fp64_fma_peak_tflops"] = tg.tg_diag_fma_rate(torch.float64) / 1e12
     out["fp32_fma_peak_tflops"] = tg.tg_diag_fma_rate(torch.float32) / 1e12
     # elasticity 64^3
@@ -598,6 +599,24 @@ def residual_extras(tg, torch, dev, m, cfg, p, peak, flush):
             "loss": float(loss.item()),
             "note": "y = K x - F without storing K, Dirichlet rows zeroed, loss = ||y||^2 in FP64; backward = "
                     "K g (matrix-free) + adjoint backward (lam = g, U = x) + load backward, 3 launches"}
+    return out
+
+
+def facet_extras(tg, torch, dev, m, p, flush):
+    """Robin matrix term and Neumann/Robin load on the 4,096 boundary edges
+    of the 1024^2 workload, added onto assembled values (one launch)."""
+    fac = mg.boundary_facets(m)
+    fc = tg.tg_build_facets(p, torch.as_tensor(fac, device=dev))
+    out = {}
+    for dtn, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        X = torch.as_tensor(m.coords, dtype=dt, device=dev)
+        al = torch.as_tensor(np.random.default_rng(3).uniform(0.5, 2, len(fac) * 2), dtype=dt, device=dev)
+        g = torch.as_tensor(np.random.default_rng(4).uniform(-1, 1, m.n_nodes), dtype=dt, device=dev)
+        v = torch.zeros(p.nnz, dtype=dt, device=dev)
+        F = torch.zeros(m.n_nodes, dtype=dt, device=dev)
+        ms = timed(torch, lambda: tg.tg_assemble_facets(fc, X, al, tg.PER_QP, g, tg.PER_NODE, v, F), flush)
+        out[f"facets2d_{dtn}"] = {"facets": len(fac), "boundary_nodes": fc.n_boundary_nodes, "us": ms * 1e3,
+                                  "note": "Robin alpha per facet point and nodal g, added into CSR values and F"}
     return out
 
 

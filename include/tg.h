@@ -85,6 +85,7 @@ typedef enum {
 
 typedef struct tg_pattern tg_pattern; /* opaque; owns its device buffers */
 typedef struct tg_batch tg_batch;     /* opaque; owns its device buffers */
+typedef struct tg_facets tg_facets;   /* opaque; owns its device buffers */
 
 /* ------------------------------------------------------------------------
  * Status and diagnostics
@@ -361,6 +362,54 @@ tg_status tg_batch_autotune(tg_batch* b, tg_dtype dtype, const void* const* coor
                             float* best_ms, tg_stream stream);
 
 void tg_batch_destroy(tg_batch* b);
+
+/* ------------------------------------------------------------------------
+ * Boundary facets: the Neumann and Robin terms of a scalar problem, routed
+ * into the same CSR values and load vector as the element terms (the
+ * mixed-boundary-condition Poisson benchmark of the SM; the Map over
+ * boundary quadrature and a boundary routing into Sparse-Reduce).  With the
+ * Robin condition kappa du/dn + alpha u = g_R on Gamma_R and the Neumann
+ * condition kappa du/dn = g_N on Gamma_N, the weak form gains
+ *   sum_f int_f alpha u v ds   (matrix)  and  sum_f int_f g v ds   (load).
+ * Facets of P1 triangles are boundary edges (2 vertices; 2-point Gauss
+ * rule on the edge), of P1 tetrahedra boundary faces (3 vertices; the
+ * 3-point rule of the triangle).  P2 is not supported.
+ * ---------------------------------------------------------------------- */
+
+/* Routing of a facet set on a pattern (P1_TRI or P1_TET).
+ *   facets  device int32 [n_facets][d] (d = 2 for triangles, 3 for
+ *           tetrahedra): node ids; copied.  Every facet's vertex pairs must
+ *           share an element of the pattern (a facet of the mesh).
+ * Errors: TG_ERR_INDEX_RANGE (node id outside [0, N)), TG_ERR_DEGENERATE_
+ * ELEMENT (repeated vertex), TG_ERR_INVALID_ARG (a pair that shares no
+ * element); tg_last_error_message() names the facet.  SYNCHRONISES.  The
+ * facet set reads the pattern's row pointers: destroy it before the
+ * pattern. */
+tg_status tg_build_facets(const tg_pattern* p, const int32_t* facets, int64_t n_facets, tg_stream stream,
+                          tg_facets** out);
+
+/* Adds the facet terms to assembled values, one facet at a time in
+ * increasing facet order (deterministic):
+ *   vals_inout[slot(g_a, g_b)] += sum_q w_q |J_f| alpha_q phi_a phi_b
+ *   F_inout[g_a]               += sum_q w_q |J_f| g_q phi_a
+ * |J_f| = the edge length or twice the face area; quadrature on the
+ * reference facet (weights sum to 1 on the edge, 1/2 on the face).
+ *   alpha  layouts PER_ELEMENT (one per facet, [n_facets]), PER_QP
+ *          ([n_facets][2 or 3]) or CONSTANT; NULL = no matrix term.
+ *   g      layouts PER_NODE ([N], the facet interpolant), PER_QP or
+ *          CONSTANT; NULL = no load term.
+ *   vals_inout [nnz] (the pattern's CSR), F_inout [N]; either may be NULL
+ *          when its term is absent.
+ * A facet of zero measure is recorded as TG_ERR_DEGENERATE_ELEMENT (facet
+ * index) in the pattern's device status. */
+tg_status tg_assemble_facets(const tg_facets* fc, tg_dtype dtype, const void* coords, const void* alpha,
+                             tg_layout alpha_layout, const void* g, tg_layout g_layout, void* vals_inout,
+                             void* F_inout, tg_stream stream);
+
+/* Number of facets and of nodes that carry at least one. */
+tg_status tg_facets_shape(const tg_facets* fc, int64_t* n_facets, int64_t* n_boundary_nodes);
+
+void tg_facets_destroy(tg_facets* fc);
 
 /* ------------------------------------------------------------------------
  * Measurement helper (no counterpart in the paper): sustained rate of

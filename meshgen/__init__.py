@@ -202,6 +202,19 @@ def kuhn_tet_grid(n: int) -> Mesh:
 
 # --------------------------------------------------------------------------
 # coefficient and load draws
+def boundary_facets(mesh: Mesh) -> np.ndarray:
+    """Facets that belong to exactly one element (the domain boundary):
+    edges of P1 triangles ([F, 2]) or faces of P1 tetrahedra ([F, 3]), each
+    with its vertices in ascending order, facets in lexicographic order."""
+    cells = np.asarray(mesh.cells)
+    nv = cells.shape[1]
+    d = nv - 1
+    local = [c for c in __import__("itertools").combinations(range(nv), d)]
+    f = np.sort(np.concatenate([cells[:, list(c)] for c in local]), axis=1)
+    uniq, count = np.unique(f, axis=0, return_counts=True)
+    return uniq[count == 1].astype(np.int32)
+
+
 def lognormal(shape, seed: int, sigma: float = 1.0) -> np.ndarray:
     return np.exp(rng(seed).normal(0.0, sigma, size=shape))
 

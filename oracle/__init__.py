@@ -12,6 +12,9 @@ shares no code, header or constant with the GPU library.
 * ``solve.py`` — conjugate gradients on the Dirichlet-condensed system.
 * ``residual()`` — the residual vector of Eq. (res1), K x - F, from the
   assembled oracle matrix and load vector.
+* ``assemble_facets()`` — the Neumann and Robin boundary terms by
+  scatter-add over boundary facets (edge: Gauss-Legendre; face: the
+  triangle rule).
 
 Parity of every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, invariants, exact integration and finite differences.
@@ -266,3 +269,65 @@ def residual(el, cells, coords, kappa, kappa_layout, c, x, f=None, f_layout=PER_
     if dirichlet is not None:
         y[np.asarray(dirichlet) != 0] = 0.0
     return y, float(np.dot(y, y))
+
+
+def _facet_rule(nf):
+    """Quadrature on the reference facet: (points in facet barycentric-free
+    coordinates, weights); the edge [0, 1] with 2 Gauss-Legendre points
+    (weights sum to 1), or the reference triangle's rule (sum 1/2)."""
+    if nf == 2:
+        x, w = np.polynomial.legendre.leggauss(2)
+        return ((x + 1.0) / 2.0)[:, None], w / 2.0
+    w, x = quadrature(P1_TRI)
+    return x, w
+
+
+def _facet_basis(nf, xq):
+    if nf == 2:
+        return np.array([1.0 - xq[0], xq[0]])
+    return np.array([1.0 - xq[0] - xq[1], xq[0], xq[1]])
+
+
+def assemble_facets(el, facets, coords, alpha=None, alpha_layout=CONSTANT, g=None, g_layout=CONSTANT):
+    """Boundary terms of the Robin condition kappa du/dn + alpha u = g and
+    the Neumann condition kappa du/dn = g, facet by facet in input order:
+      M[(g_a, g_b)] += sum_q w_q |J_f| alpha_q phi_a phi_b,
+      F[g_a]        += sum_q w_q |J_f| g_q phi_a,
+    |J_f| = edge length (triangles) or twice the face area (tetrahedra).
+    alpha layouts PER_ELEMENT (per facet), PER_QP, CONSTANT; g layouts
+    PER_NODE (facet interpolant), PER_QP, CONSTANT.  Returns (dict of matrix
+    entries, F [N])."""
+    facets = np.asarray(facets)
+    X = _f64(coords)
+    nf = facets.shape[1]
+    assert nf == DIM[el]
+    xq, wq = _facet_rule(nf)
+    nq = len(wq)
+    M = {}
+    F = np.zeros(X.shape[0])
+    for f, fv in enumerate(facets):
+        P = X[fv]
+        if nf == 2:
+            J = float(np.linalg.norm(P[1] - P[0]))
+        else:
+            J = float(np.linalg.norm(np.cross(P[1] - P[0], P[2] - P[0])))
+        for q in range(nq):
+            phi = _facet_basis(nf, xq[q])
+            if alpha is not None:
+                a_ = np.atleast_1d(alpha)
+                aq = a_[f * nq + q] if alpha_layout == PER_QP else a_[f] if alpha_layout == PER_ELEMENT else a_[0]
+                for a in range(nf):
+                    for b in range(nf):
+                        key = (int(fv[a]), int(fv[b]))
+                        M[key] = M.get(key, 0.0) + wq[q] * J * aq * phi[a] * phi[b]
+            if g is not None:
+                g_ = np.atleast_1d(g)
+                if g_layout == PER_NODE:
+                    gq = float(phi @ g_[fv])
+                elif g_layout == PER_QP:
+                    gq = g_[f * nq + q]
+                else:
+                    gq = g_[0]
+                for a in range(nf):
+                    F[fv[a]] += wq[q] * J * gq * phi[a]
+    return M, F

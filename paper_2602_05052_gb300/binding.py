@@ -65,6 +65,10 @@ def lib():
         "tg_assemble_load_backward": (i32, [vp, i32, vp, vp, i32, i32, vp, vp, vp, i32, vp]),
         "tg_assemble_elasticity_backward": (i32, [vp, i32, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]),
         "tg_residual": (i32, [vp, i32, vp, vp, i32, dbl, vp, vp, i32, vp, vp, vp, vp]),
+        "tg_build_facets": (i32, [vp, vp, i64, vp, C.POINTER(vp)]),
+        "tg_assemble_facets": (i32, [vp, i32, vp, vp, i32, vp, i32, vp, vp, vp]),
+        "tg_facets_shape": (i32, [vp, C.POINTER(i64), C.POINTER(i64)]),
+        "tg_facets_destroy": (None, [vp]),
         "tg_spmv": (i32, [vp, i32, vp, vp, vp, vp]),
         "tg_csr_outer": (i32, [vp, i32, vp, vp, dbl, vp, vp]),
         "tg_cg_solve": (i32, [vp, i32, vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl), vp]),
@@ -313,6 +317,42 @@ def tg_residual(p: Pattern, coords, kappa, layout: int, c: float, x, f=None, f_l
                              _ptr(dirichlet, torch.uint8, "dirichlet"), _ptr(y, dt, "y"), _ptr(ls, dt, "loss"),
                              _stream(stream)), "tg_residual")
     return y, ls
+
+
+class Facets:
+    """Owns a tg_facets handle (tg_build_facets / tg_facets_destroy); keeps
+    its pattern alive."""
+
+    def __init__(self, handle, pattern):
+        self.handle = handle
+        self.pattern = pattern
+        F, M = i64(), i64()
+        _check(lib().tg_facets_shape(handle, C.byref(F), C.byref(M)), "tg_facets_shape")
+        self.n_facets, self.n_boundary_nodes = F.value, M.value
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.tg_facets_destroy(h)
+
+
+def tg_build_facets(p: Pattern, facets: torch.Tensor, stream=None) -> Facets:
+    if facets.dim() != 2 or facets.shape[1] != DIM[p.el]:
+        raise ValueError("facets must be [F, d]")
+    h = vp()
+    _check(lib().tg_build_facets(p.handle, _ptr(facets, torch.int32, "facets"), facets.shape[0], _stream(stream),
+                                 C.byref(h)), "tg_build_facets")
+    return Facets(h, p)
+
+
+def tg_assemble_facets(fc: Facets, coords, alpha=None, alpha_layout: int = CONSTANT, g=None, g_layout: int = CONSTANT,
+                       vals=None, F=None, stream=None):
+    """Adds the Robin matrix term to vals and the facet load to F (in place)."""
+    dt = coords.dtype
+    _check(lib().tg_assemble_facets(fc.handle, _dt(coords), _ptr(coords, dt, "coords"), _ptr(alpha, dt, "alpha"),
+                                    alpha_layout, _ptr(g, dt, "g"), g_layout, _ptr(vals, dt, "vals"), _ptr(F, dt, "F"),
+                                    _stream(stream)), "tg_assemble_facets")
+    return vals, F
 
 
 def tg_csr_outer(p: Pattern, lam, U, alpha: float = 1.0, out=None, stream=None):
