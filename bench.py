@@ -599,6 +599,19 @@ def residual_extras(tg, torch, dev, m, cfg, p, peak, flush):
             "loss": float(loss.item()),
             "note": "y = K x - F without storing K, Dirichlet rows zeroed, loss = ||y||^2 in FP64; backward = "
                     "K g (matrix-free) + adjoint backward (lam = g, U = x) + load backward, 3 launches"}
+        # Allen-Cahn backward-Euler step residual (method of lines): (1/dt) M (U1 - U0) + a^2 K U1 + N(U1),
+        # N the load of eps^2 (u^3 - u); its x-gradient action K g + J(U1) g
+        r = [0.0, -0.3, 0.0, 0.3]
+        u0 = d(np.random.default_rng(10).uniform(-1, 1, N)) / 1e-3
+        a2 = d([0.01])
+        ac = lambda: tg.tg_semilinear_residual(p, X, a2, tg.PER_QP if a2.numel() > 1 else tg.CONSTANT, 1e3, x, r, u0,
+                                               tg.PER_NODE, dirichlet=mask, y=y, loss=loss)
+        ms_ac = timed(torch, ac, flush)
+        acj = lambda: tg.tg_semilinear_residual(p, X, a2, tg.CONSTANT, 1e3, g, r, x_react=x, y=gx_in, loss=False)
+        ms_acj = timed(torch, acj, flush)
+        out[f"allen_cahn2d_{dtn}"] = {"step_residual_us": ms_ac * 1e3, "jacobian_action_us": ms_acj * 1e3,
+                                      "elements_per_s": E / ms_ac * 1e3,
+                                      "note": "one launch each; constant a^2, nodal U0 / dt, mask and loss"}
     return out
 
 

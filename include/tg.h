@@ -228,6 +228,25 @@ tg_status tg_residual(const tg_pattern* p, tg_dtype dtype, const void* coords, c
                       tg_layout kappa_layout, double c, const void* x, const void* f, tg_layout f_layout,
                       const uint8_t* dirichlet, void* y, void* loss, tg_stream stream);
 
+/* The residual of a semilinear time step (method of lines, SM: M dU/dt +
+ * K U + F_nonlin(U) = F_ext), tg_residual plus a reaction term:
+ *   y[i] = (K x)[i] + N[i] - F[i],
+ *   N[i] = sum_e sum_q w_q |det J_e| s_q phi_a(x_q),   u_q = sum_b phi_b(x_q) x_b,
+ * with s_q = r(u_q), r(u) = reaction[0] + reaction[1] u + reaction[2] u^2 +
+ * reaction[3] u^3 (host array of 4), when x_react is NULL; with x_react
+ * ([N], the state of a linearisation) s_q = r'(ur_q) u_q, ur_q the same
+ * interpolation of x_react: the reaction's Jacobian at x_react applied to
+ * x.  The element's own rule (the points of tg_quadrature) integrates both.
+ * Backward Euler for du/dt = div(a^2 grad u) - r(u):
+ *   (1/dt) M (U1 - U0) + a^2 K U1 + N(U1) = this call with kappa = a^2,
+ *   c = 1/dt, x = U1, f = U0 / dt (PER_NODE: F = M f).
+ * Reverse mode: dL/dx = K gy + J(x) gy (this call with x = gy, f = NULL,
+ * x_react = x).  Other arguments, errors and determinism as tg_residual. */
+tg_status tg_semilinear_residual(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
+                                 tg_layout kappa_layout, double c, const void* x, const void* f, tg_layout f_layout,
+                                 const double* reaction, const void* x_react, const uint8_t* dirichlet, void* y,
+                                 void* loss, tg_stream stream);
+
 /* ------------------------------------------------------------------------
  * Backward (reverse mode) of the scalar bilinear assembly.
  * For an upstream gradient W of the assembled values, either

@@ -12,6 +12,8 @@ shares no code, header or constant with the GPU library.
 * ``solve.py`` — conjugate gradients on the Dirichlet-condensed system.
 * ``residual()`` — the residual vector of Eq. (res1), K x - F, from the
   assembled oracle matrix and load vector.
+* ``reaction_load()``, ``semilinear_residual()`` — the semilinear reaction
+  term of the method of lines by quadrature, and the residual with it.
 * ``assemble_facets()`` — the Neumann and Robin boundary terms by
   scatter-add over boundary facets (edge: Gauss-Legendre; face: the
   triangle rule).
@@ -331,3 +333,54 @@ def assemble_facets(el, facets, coords, alpha=None, alpha_layout=CONSTANT, g=Non
                 for a in range(nf):
                     F[fv[a]] += wq[q] * J * gq * phi[a]
     return M, F
+
+
+def _abs_det(el, cells, X):
+    """|det J_e| of every element from its geometric vertices."""
+    if DIM[el] == 2:
+        a, b, c = X[cells[:, 0]], X[cells[:, 1]], X[cells[:, 2]]
+        e1, e2 = b - a, c - a
+        return np.abs(e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0])
+    a = X[cells[:, 0]]
+    J = np.stack([X[cells[:, k]] - a for k in (1, 2, 3)], axis=2)
+    return np.abs(np.linalg.det(J))
+
+
+def reaction_load(el, cells, coords, x, reaction, x_react=None):
+    """Reaction term of a semilinear form, element by element with the
+    element's quadrature rule:
+      N[g(a)] += |det J_e| sum_q w_q s_q phi_a(x_q),  u_q = sum_b phi_b(x_q) x[g(b)],
+    s_q = r(u_q) with r(u) = sum_k reaction[k] u^k; with x_react, s_q =
+    r'(ur_q) u_q (ur_q interpolating x_react): the Jacobian at x_react
+    applied to x."""
+    cells = np.asarray(cells, dtype=np.int64)
+    X = _f64(coords)
+    x = _f64(x)
+    r = [float(v) for v in reaction]
+    w, xq = quadrature(el)
+    adet = _abs_det(el, cells, X)
+    out = np.zeros(X.shape[0])
+    nv = NV[el]
+    for q in range(len(w)):
+        phi, _ = basis(el, xq[q])
+        u = sum(phi[b] * x[cells[:, b]] for b in range(nv))
+        if x_react is None:
+            s = r[0] + r[1] * u + r[2] * u ** 2 + r[3] * u ** 3
+        else:
+            xr = _f64(x_react)
+            ur = sum(phi[b] * xr[cells[:, b]] for b in range(nv))
+            s = (r[1] + 2 * r[2] * ur + 3 * r[3] * ur ** 2) * u
+        for a in range(nv):
+            np.add.at(out, cells[:, a], adet * w[q] * s * phi[a])
+    return out
+
+
+def semilinear_residual(el, cells, coords, kappa, kappa_layout, c, x, reaction, f=None, f_layout=PER_NODE,
+                        dirichlet=None, x_react=None):
+    """y = K x + N - F (N from reaction_load), y = 0 on Dirichlet rows;
+    returns (y, sum y^2)."""
+    y, _ = residual(el, cells, coords, kappa, kappa_layout, c, x, f, f_layout)
+    y = y + reaction_load(el, cells, coords, x, reaction, x_react)
+    if dirichlet is not None:
+        y[np.asarray(dirichlet) != 0] = 0.0
+    return y, float(np.dot(y, y))

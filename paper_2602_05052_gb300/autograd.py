@@ -18,7 +18,9 @@ is the adjoint solve of Eq. (adj).
   g the upstream gradient masked to the free rows: dL/dx = K g (the same
   matrix-free call; K is symmetric), dL/dkappa and dL/dcoords from the fused
   adjoint backward with lam = g, U = x, and dL/df from the load backward
-  with grad_F = -g.
+  with grad_F = -g.  With ``reaction`` (the four coefficients of r(u)) y
+  gains the semilinear term N(x) and dL/dx gains J(x) g (coordinate
+  gradients of that term are not built).
 """
 from __future__ import annotations
 
@@ -107,11 +109,16 @@ class _SolveAssembled(torch.autograd.Function):
 
 class _Residual(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, coords, kappa, x, f, p, layout, c, f_layout, dirichlet):
+    def forward(ctx, coords, kappa, x, f, p, layout, c, f_layout, dirichlet, reaction):
         coords, kappa, x = coords.contiguous(), kappa.contiguous(), x.contiguous()
         f = f.contiguous() if f is not None else None
-        y, _ = B.tg_residual(p, coords, kappa, layout, c, x, f, f_layout, dirichlet, loss=False)
+        if reaction is None:
+            y, _ = B.tg_residual(p, coords, kappa, layout, c, x, f, f_layout, dirichlet, loss=False)
+        else:
+            y, _ = B.tg_semilinear_residual(p, coords, kappa, layout, c, x, reaction, f, f_layout,
+                                            dirichlet=dirichlet, loss=False)
         ctx.p, ctx.layout, ctx.c, ctx.f_layout, ctx.dirichlet = p, layout, c, f_layout, dirichlet
+        ctx.reaction = reaction
         ctx.has_f = f is not None
         ctx.save_for_backward(coords, kappa, x, f if f is not None else x)
         return y
@@ -125,7 +132,14 @@ class _Residual(torch.autograd.Function):
             g = g.masked_fill(ctx.dirichlet.bool(), 0.0)
         need_x, need_k, need_f = ctx.needs_input_grad[2], ctx.needs_input_grad[1], ctx.needs_input_grad[3]
         need_c = ctx.needs_input_grad[0]
-        gx_in = B.tg_residual(p, coords, kappa, ctx.layout, ctx.c, g, loss=False)[0] if need_x else None
+        if need_c and ctx.reaction is not None:
+            raise NotImplementedError("coordinate gradients of the reaction term are not built")
+        gx_in = None
+        if need_x and ctx.reaction is None:
+            gx_in = B.tg_residual(p, coords, kappa, ctx.layout, ctx.c, g, loss=False)[0]
+        elif need_x:  # K g + J(x) g (K and the reaction's Jacobian are symmetric)
+            gx_in = B.tg_semilinear_residual(p, coords, kappa, ctx.layout, ctx.c, g, ctx.reaction, x_react=x,
+                                             loss=False)[0]
         gk = gc = None
         if need_k or need_c:
             gk, gc, _ = B.tg_assemble_backward(p, coords, kappa, ctx.layout, ctx.c, lam=g, U=x, grad_kappa=need_k,
@@ -136,7 +150,7 @@ class _Residual(torch.autograd.Function):
             gf, _ = B.tg_assemble_load_backward(p, coords, f, ctx.f_layout, 1, -g,
                                                 grad_f=torch.zeros_like(f) if need_f else False,
                                                 grad_coords=gc if need_c else False, accumulate=True)
-        return gc, gk, gx_in, gf, None, None, None, None, None
+        return gc, gk, gx_in, gf, None, None, None, None, None, None
 
 
 def assemble(p, coords, kappa, layout, c=0.0):
@@ -155,5 +169,6 @@ def solve_assembled(p, coords, kappa, layout, f, f_layout, dirichlet=None, rtol=
     return _SolveAssembled.apply(coords, kappa, f, p, layout, f_layout, dirichlet, float(rtol), int(maxit))
 
 
-def residual(p, coords, kappa, layout, c, x, f=None, f_layout=B.PER_NODE, dirichlet=None):
-    return _Residual.apply(coords, kappa, x, f, p, layout, float(c), f_layout, dirichlet)
+def residual(p, coords, kappa, layout, c, x, f=None, f_layout=B.PER_NODE, dirichlet=None, reaction=None):
+    r = tuple(float(v) for v in reaction) if reaction is not None else None
+    return _Residual.apply(coords, kappa, x, f, p, layout, float(c), f_layout, dirichlet, r)

@@ -65,6 +65,8 @@ def lib():
         "tg_assemble_load_backward": (i32, [vp, i32, vp, vp, i32, i32, vp, vp, vp, i32, vp]),
         "tg_assemble_elasticity_backward": (i32, [vp, i32, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]),
         "tg_residual": (i32, [vp, i32, vp, vp, i32, dbl, vp, vp, i32, vp, vp, vp, vp]),
+        "tg_semilinear_residual": (i32, [vp, i32, vp, vp, i32, dbl, vp, vp, i32, C.POINTER(dbl), vp, vp, vp, vp,
+                                         vp]),
         "tg_build_facets": (i32, [vp, vp, i64, vp, C.POINTER(vp)]),
         "tg_assemble_facets": (i32, [vp, i32, vp, vp, i32, vp, i32, vp, vp, vp]),
         "tg_facets_shape": (i32, [vp, C.POINTER(i64), C.POINTER(i64)]),
@@ -316,6 +318,23 @@ def tg_residual(p: Pattern, coords, kappa, layout: int, c: float, x, f=None, f_l
                              float(c), _ptr(x, dt, "x"), _ptr(f, dt, "f"), f_layout,
                              _ptr(dirichlet, torch.uint8, "dirichlet"), _ptr(y, dt, "y"), _ptr(ls, dt, "loss"),
                              _stream(stream)), "tg_residual")
+    return y, ls
+
+
+def tg_semilinear_residual(p: Pattern, coords, kappa, layout: int, c: float, x, reaction, f=None,
+                           f_layout: int = PER_NODE, x_react=None, dirichlet=None, y=None, loss=True, stream=None):
+    """y = K x + N(x) - F with the reaction r(u) = sum_k reaction[k] u^k (or,
+    with x_react, its Jacobian at x_react applied to x); returns (y, loss)."""
+    dt = coords.dtype
+    if y is None:
+        y = torch.empty_like(x)
+    ls = _out(loss, lambda: torch.empty(1, dtype=dt, device=coords.device))
+    r = (dbl * 4)(*[float(v) for v in reaction])
+    _check(lib().tg_semilinear_residual(p.handle, _dt(coords), _ptr(coords, dt, "coords"), _ptr(kappa, dt, "kappa"),
+                                        layout, float(c), _ptr(x, dt, "x"), _ptr(f, dt, "f"), f_layout, r,
+                                        _ptr(x_react, dt, "x_react"), _ptr(dirichlet, torch.uint8, "dirichlet"),
+                                        _ptr(y, dt, "y"), _ptr(ls, dt, "loss"), _stream(stream)),
+           "tg_semilinear_residual")
     return y, ls
 
 

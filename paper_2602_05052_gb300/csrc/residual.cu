@@ -6,6 +6,10 @@
 // the Reduce sums the NV element results of every node in increasing
 // element order (the node-level routing S_vec of Algorithm 2).
 //
+// With a reaction polynomial r (the semilinear forms of the method of lines,
+// e.g. the Allen-Cahn reaction), the Map also integrates r(u_h) phi_i (or,
+// for the Jacobian action, r'(u_h) v_h phi_i) with the element's rule.
+//
 // Two forms, with the same per-element arithmetic and the same summation
 // order, hence identical bits:
 //   k_residual_blk    - element-once row blocks (blocks.cuh): each distinct
@@ -31,6 +35,8 @@ template <typename T>
 struct ResArgs {
   tg::FwdArgs<T> fa;  // coords, coef (kappa), layout, c, f, f_layout, status, cells, inc_ptr, inc_e
   const T* __restrict__ x;
+  const T* __restrict__ xr;  // state of the reaction's Jacobian (NL == 2)
+  T r[4];                    // reaction r(u) = r0 + r1 u + r2 u^2 + r3 u^3
   const uint8_t* __restrict__ dir;
   T* __restrict__ y;
   T* loss;
@@ -59,9 +65,10 @@ struct ResIn {
   tg::ElemIn<EL, T> in;
   T xv[tg::Elem<EL>::nv];
   T fv[tg::Elem<EL>::nv];
+  T xr[tg::Elem<EL>::nv];
 };
 
-template <int EL, typename T, bool LOADF>
+template <int EL, typename T, bool LOADF, int NL>
 __device__ __forceinline__ void result_inputs(const ResArgs<T>& r, int64_t e, const int (&vid)[tg::Elem<EL>::nv],
                                               ResIn<EL, T>& d) {
   constexpr int NV = tg::Elem<EL>::nv, NG = tg::Elem<EL>::ngeo;
@@ -71,11 +78,48 @@ __device__ __forceinline__ void result_inputs(const ResArgs<T>& r, int64_t e, co
 #pragma unroll
   for (int c = 0; c < NV; ++c) d.xv[c] = __ldg(r.x + vid[c]);
   if constexpr (LOADF) tg::p1_load_f<NV, T>(r.fa.f, r.fa.f_layout, e, vid, d.fv);
+  if constexpr (NL == 2) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) d.xr[c] = __ldg(r.xr + vid[c]);
+  }
+}
+
+// Reaction term of the element at local node a, |det J| sum_q w_q s_q
+// phi_a(x_q): NL == 1, s_q = r(u_q) with u_q = sum_b phi_b(x_q) x_b (the
+// semilinear load of the reaction); NL == 2, s_q = r'(ur_q) v_q with ur_q
+// from the state xr and v_q from x (its Jacobian applied to x).
+template <int EL, typename T, int NL>
+__device__ __forceinline__ void reaction_rows(const ResArgs<T>& r, const tg::RefTab<T>& tab, T adet,
+                                              const ResIn<EL, T>& d, T (&out)[tg::Elem<EL>::nv]) {
+  constexpr int NV = tg::Elem<EL>::nv, NQ = tg::Elem<EL>::nq;
+  T sq[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    T u = T(0), v = T(0);
+#pragma unroll
+    for (int b = 0; b < NV; ++b) {
+      u = fma(tab.phi[q][b], NL == 2 ? d.xr[b] : d.xv[b], u);
+      if constexpr (NL == 2) v = fma(tab.phi[q][b], d.xv[b], v);
+    }
+    if constexpr (NL == 1) {
+      sq[q] = tab.w[q] * fma(fma(fma(r.r[3], u, r.r[2]), u, r.r[1]), u, r.r[0]);
+    } else {
+      const T dr = fma(fma(T(3) * r.r[3], u, T(2) * r.r[2]), u, r.r[1]);
+      sq[q] = tab.w[q] * dr * v;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) s = fma(sq[q], tab.phi[q][a], s);
+    out[a] = adet * s;
+  }
 }
 
 // The NV results of element e; zeros and a recorded error for a degenerate
 // element.
-template <int EL, typename T, bool LOADF>
+template <int EL, typename T, bool LOADF, int NL>
 __device__ __forceinline__ void result_compute(const ResArgs<T>& r, const tg::RefTab<T>& tab, int64_t e,
                                                const ResIn<EL, T>& d, T (&ye)[tg::Elem<EL>::nv]) {
   constexpr int NV = tg::Elem<EL>::nv;
@@ -90,9 +134,12 @@ __device__ __forceinline__ void result_compute(const ResArgs<T>& r, const tg::Re
     for (int a = 0; a < NV; ++a) ye[a] = T(0);
     return;
   }
+  T nr[NV];
+  if constexpr (NL != 0) reaction_rows<EL, T, NL>(r, tab, adet, d, nr);
 #pragma unroll
   for (int a = 0; a < NV; ++a) {
     T s = kx_row<NV, T>(K, d.xv, a);
+    if constexpr (NL != 0) s += nr[a];
     if constexpr (LOADF) s -= tg::p1_load_entry<NV, T>(r.fa.f_layout, adet, d.fv, tab, a);
     ye[a] = s;
   }
@@ -138,7 +185,7 @@ __device__ __forceinline__ void finish_loss(const ResArgs<T>& r, double part) {
 // Element-once row blocks: Map the block's distinct elements into
 // Ye[NV][capE], Reduce the rows (increasing element order), apply the
 // Dirichlet mask, write y and add y^2 to this thread's loss term.
-template <int EL, typename T, int UB, bool LOADF>
+template <int EL, typename T, int UB, bool LOADF, int NL>
 __global__ void __launch_bounds__(RT) k_residual_blk(const ResArgs<T> r, const __grid_constant__ tg::RefTab<T> tab,
                                                     const tg::BlkArgs g) {
   constexpr int NV = tg::Elem<EL>::nv;
@@ -159,14 +206,14 @@ __global__ void __launch_bounds__(RT) k_residual_blk(const ResArgs<T> r, const _
 #pragma unroll
       for (int c = 0; c < NV; ++c) vid[c] = v.vtx(c, j);
       e[u] = tg::bel_elem(v.be[j]);
-      result_inputs<EL, T, LOADF>(r, e[u], vid, d[u]);
+      result_inputs<EL, T, LOADF, NL>(r, e[u], vid, d[u]);
     }
 #pragma unroll
     for (int u = 0; u < UB; ++u) {
       const int j = j0 + u * NT_;
       if (j >= v.nbe) continue;
       T ye[NV];
-      result_compute<EL, T, LOADF>(r, tab, e[u], d[u], ye);
+      result_compute<EL, T, LOADF, NL>(r, tab, e[u], d[u], ye);
 #pragma unroll
       for (int a = 0; a < NV; ++a) Ye[a * g.capE + j] = ye[a];
     }
@@ -197,7 +244,7 @@ __global__ void __launch_bounds__(RT) k_residual_blk(const ResArgs<T> r, const _
 // consecutive elements).  Reduce: one thread per node sums its incidences'
 // results in increasing element order (the incidence lists are sorted by
 // element), so every y[i] carries the bits of the one-pass kernels.
-template <int EL, typename T, bool LOADF, int EPT>
+template <int EL, typename T, bool LOADF, int NL, int EPT>
 __global__ void __launch_bounds__(RT) k_residual_map(const ResArgs<T> r, const __grid_constant__ tg::RefTab<T> tab,
                                                     int64_t E, T* __restrict__ ye) {
   constexpr int NV = tg::Elem<EL>::nv;
@@ -211,13 +258,13 @@ __global__ void __launch_bounds__(RT) k_residual_map(const ResArgs<T> r, const _
     int vid[NV];
 #pragma unroll
     for (int c = 0; c < NV; ++c) vid[c] = __ldg(r.fa.cells + ee * NV + c);
-    result_inputs<EL, T, LOADF>(r, ee, vid, d[u]);
+    result_inputs<EL, T, LOADF, NL>(r, ee, vid, d[u]);
   }
 #pragma unroll
   for (int u = 0; u < EPT; ++u) {
     if (e[u] >= E) break;
     T out[NV];
-    result_compute<EL, T, LOADF>(r, tab, e[u], d[u], out);
+    result_compute<EL, T, LOADF, NL>(r, tab, e[u], d[u], out);
 #pragma unroll
     for (int a = 0; a < NV; ++a) ye[e[u] * NV + a] = out[a];
   }
@@ -241,13 +288,13 @@ __global__ void __launch_bounds__(RT) k_residual_reduce(const ResArgs<T> r, cons
   if (r.loss) finish_loss(r, part);
 }
 
-template <int EL, typename T, bool LOADF>
+template <int EL, typename T, bool LOADF, int NL>
 tg_status launch_two_pass(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t s) {
   constexpr int NV = tg::Elem<EL>::nv, EPT = 2;
   const tg::RefTab<T>& tab = tg::table<T>((tg_element)EL);
   T* ye = static_cast<T*>(p->elem_scratch);
   const int64_t gm = (p->E + RT * EPT - 1) / (RT * EPT);
-  k_residual_map<EL, T, LOADF, EPT><<<(unsigned)gm, RT, 0, s>>>(r, tab, p->E, ye);
+  k_residual_map<EL, T, LOADF, NL, EPT><<<(unsigned)gm, RT, 0, s>>>(r, tab, p->E, ye);
   TG_CK_LAUNCH("k_residual_map");
   const int64_t gr = tg::grid_for(p->N, RT);
   if (gr > (p->n_partials - 4) / kSlots) return TG_ERR_UNSUPPORTED;
@@ -256,7 +303,7 @@ tg_status launch_two_pass(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t
   return TG_OK;
 }
 
-template <int EL, typename T, bool LOADF>
+template <int EL, typename T, bool LOADF, int NL>
 tg_status launch_el(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t s) {
   // FP32 runs on the row blocks.  FP64, and patterns without row blocks,
   // take the two passes: FP64 is bound by the FP64 pipe, where evaluating
@@ -285,27 +332,40 @@ tg_status launch_el(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t s) {
         kern<<<grid, RT, smem, s>>>(r, tab, g);
       };
       if constexpr (EL == TG_P2_TRI) {
-        go(k_residual_blk<EL, T, 2, LOADF>);
+        go(k_residual_blk<EL, T, 2, LOADF, NL>);
       } else {
-        if (need <= 2) go(k_residual_blk<EL, T, 2, LOADF>);
-        else if (need == 3) go(k_residual_blk<EL, T, 3, LOADF>);
-        else go(k_residual_blk<EL, T, 4, LOADF>);
+        if (need <= 2) go(k_residual_blk<EL, T, 2, LOADF, NL>);
+        else if (need == 3) go(k_residual_blk<EL, T, 3, LOADF, NL>);
+        else go(k_residual_blk<EL, T, 4, LOADF, NL>);
       }
       if (st != TG_OK) return st;
       TG_CK_LAUNCH("k_residual_blk");
       return TG_OK;
     }
   }
-  if (p->elem_scratch) return launch_two_pass<EL, T, LOADF>(p, r, s);
+  if (p->elem_scratch) return launch_two_pass<EL, T, LOADF, NL>(p, r, s);
   // no elements: y = 0 and loss = 0
   TG_CK(cudaMemsetAsync(r.y, 0, (size_t)p->N * sizeof(T), s));
   if (r.loss) TG_CK(cudaMemsetAsync(r.loss, 0, sizeof(T), s));
   return TG_OK;
 }
 
+template <typename T, int NL>
+tg_status dispatch(const tg_pattern* p, const ResArgs<T>& r, bool lf, cudaStream_t s) {
+  switch (p->el) {
+    case TG_P1_TRI:
+      return lf ? launch_el<TG_P1_TRI, T, true, NL>(p, r, s) : launch_el<TG_P1_TRI, T, false, NL>(p, r, s);
+    case TG_P1_TET:
+      return lf ? launch_el<TG_P1_TET, T, true, NL>(p, r, s) : launch_el<TG_P1_TET, T, false, NL>(p, r, s);
+    default:
+      return launch_el<TG_P2_TRI, T, false, NL>(p, r, s);
+  }
+}
+
 template <typename T>
 tg_status residual(const tg_pattern* p, const void* coords, const void* kappa, tg_layout kl, double c, const void* x,
-                   const void* f, tg_layout fl, const uint8_t* dir, void* y, void* loss, cudaStream_t s) {
+                   const void* f, tg_layout fl, const double* reaction, const void* x_react, const uint8_t* dir,
+                   void* y, void* loss, cudaStream_t s) {
   ResArgs<T> r;
   std::memset(&r, 0, sizeof(r));
   r.fa.inc_ptr = p->inc_ptr;
@@ -320,31 +380,24 @@ tg_status residual(const tg_pattern* p, const void* coords, const void* kappa, t
   r.fa.f = static_cast<const T*>(f);
   r.fa.f_layout = fl;
   r.x = static_cast<const T*>(x);
+  r.xr = static_cast<const T*>(x_react);
+  if (reaction)
+    for (int k = 0; k < 4; ++k) r.r[k] = (T)reaction[k];
   r.dir = dir;
   r.y = static_cast<T*>(y);
   r.loss = static_cast<T*>(loss);
   r.partials = p->partials;
   r.arrivals = p->arrivals;
   const bool lf = f != nullptr;
-  switch (p->el) {
-    case TG_P1_TRI:
-      return lf ? launch_el<TG_P1_TRI, T, true>(p, r, s) : launch_el<TG_P1_TRI, T, false>(p, r, s);
-    case TG_P1_TET:
-      return lf ? launch_el<TG_P1_TET, T, true>(p, r, s) : launch_el<TG_P1_TET, T, false>(p, r, s);
-    default:
-      return launch_el<TG_P2_TRI, T, false>(p, r, s);
-  }
+  if (!reaction) return dispatch<T, 0>(p, r, lf, s);
+  return x_react ? dispatch<T, 2>(p, r, lf, s) : dispatch<T, 1>(p, r, lf, s);
 }
 
 bool aligned_to(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
-}  // namespace
-
-extern "C" {
-
-tg_status tg_residual(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
-                      tg_layout kappa_layout, double c, const void* x, const void* f, tg_layout f_layout,
-                      const uint8_t* dirichlet, void* y, void* loss, tg_stream stream) {
+tg_status entry(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa, tg_layout kappa_layout,
+                double c, const void* x, const void* f, tg_layout f_layout, const double* reaction,
+                const void* x_react, const uint8_t* dirichlet, void* y, void* loss, tg_stream stream) {
   if (!p || (dtype != TG_F32 && dtype != TG_F64)) return TG_ERR_INVALID_ARG;
   if (p->el == TG_P1_TET_VEC3) return TG_ERR_INVALID_ARG;
   if (!(kappa_layout == TG_PER_QP || kappa_layout == TG_PER_ELEMENT || kappa_layout == TG_CONSTANT)) return TG_ERR_INVALID_ARG;
@@ -353,13 +406,14 @@ tg_status tg_residual(const tg_pattern* p, tg_dtype dtype, const void* coords, c
     tg::set_error("tg_residual: the load term is built for P1 elements");
     return TG_ERR_UNSUPPORTED;
   }
+  if (x_react && !reaction) return TG_ERR_INVALID_ARG;
   const size_t es = dtype == TG_F32 ? 4 : 8;
   if (p->N > 0 && (!coords || !kappa || !x || !y)) return TG_ERR_INVALID_ARG;
   if (x && x == y) {
     tg::set_error("tg_residual: x and y must be distinct buffers");
     return TG_ERR_INVALID_ARG;
   }
-  if (f && f == y) return TG_ERR_INVALID_ARG;
+  if ((f && f == y) || (x_react && x_react == y)) return TG_ERR_INVALID_ARG;
   if (coords && !aligned_to(coords, tg::dim_of(p->el) == 2 ? 2 * es : es)) {
     tg::set_error("coords must be aligned to 2 * sizeof(dtype) for 2D meshes");
     return TG_ERR_INVALID_ARG;
@@ -369,8 +423,29 @@ tg_status tg_residual(const tg_pattern* p, tg_dtype dtype, const void* coords, c
     if (loss) TG_CK(cudaMemsetAsync(loss, 0, es, s));
     return TG_OK;
   }
-  return dtype == TG_F32 ? residual<float>(p, coords, kappa, kappa_layout, c, x, f, f_layout, dirichlet, y, loss, s)
-                         : residual<double>(p, coords, kappa, kappa_layout, c, x, f, f_layout, dirichlet, y, loss, s);
+  return dtype == TG_F32
+             ? residual<float>(p, coords, kappa, kappa_layout, c, x, f, f_layout, reaction, x_react, dirichlet, y, loss, s)
+             : residual<double>(p, coords, kappa, kappa_layout, c, x, f, f_layout, reaction, x_react, dirichlet, y, loss,
+                                s);
+}
+
+}  // namespace
+
+extern "C" {
+
+tg_status tg_residual(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
+                      tg_layout kappa_layout, double c, const void* x, const void* f, tg_layout f_layout,
+                      const uint8_t* dirichlet, void* y, void* loss, tg_stream stream) {
+  return entry(p, dtype, coords, kappa, kappa_layout, c, x, f, f_layout, nullptr, nullptr, dirichlet, y, loss, stream);
+}
+
+tg_status tg_semilinear_residual(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
+                                 tg_layout kappa_layout, double c, const void* x, const void* f, tg_layout f_layout,
+                                 const double* reaction, const void* x_react, const uint8_t* dirichlet, void* y,
+                                 void* loss, tg_stream stream) {
+  if (!reaction) return TG_ERR_INVALID_ARG;
+  return entry(p, dtype, coords, kappa, kappa_layout, c, x, f, f_layout, reaction, x_react, dirichlet, y, loss,
+               stream);
 }
 
 }  // extern "C"
