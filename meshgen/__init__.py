@@ -33,10 +33,10 @@ import numpy as np
 
 # --------------------------------------------------------------------------
 # element kinds (names shared with the C ABI enum by value, not by code)
-P1_TRI, P2_TRI, P1_TET, P1_TET_VEC3 = 0, 1, 2, 3
-NV = {P1_TRI: 3, P2_TRI: 6, P1_TET: 4, P1_TET_VEC3: 4}
-DIM = {P1_TRI: 2, P2_TRI: 2, P1_TET: 3, P1_TET_VEC3: 3}
-NQ = {P1_TRI: 3, P2_TRI: 6, P1_TET: 4, P1_TET_VEC3: 4}
+P1_TRI, P2_TRI, P1_TET, P1_TET_VEC3, Q1_QUAD_VEC2 = 0, 1, 2, 3, 4
+NV = {P1_TRI: 3, P2_TRI: 6, P1_TET: 4, P1_TET_VEC3: 4, Q1_QUAD_VEC2: 4}
+DIM = {P1_TRI: 2, P2_TRI: 2, P1_TET: 3, P1_TET_VEC3: 3, Q1_QUAD_VEC2: 2}
+NQ = {P1_TRI: 3, P2_TRI: 6, P1_TET: 4, P1_TET_VEC3: 4, Q1_QUAD_VEC2: 4}
 
 # coefficient layouts
 PER_ELEMENT, PER_QP, PER_NODE, CONSTANT = 0, 1, 2, 3
@@ -87,6 +87,39 @@ def tri_grid(n: int) -> Mesh:
     y = coords[:, 1]
     on_bnd = (ii.ravel() == 0) | (ii.ravel() == n) | (jj.ravel() == 0) | (jj.ravel() == n)
     return Mesh(P1_TRI, coords, cells, on_bnd, h=1.0 / n, meta={"n": n})
+
+
+def quad_grid(nx: int, ny: int, lx: float = 1.0, ly: float = 1.0) -> Mesh:
+    """[0, lx] x [0, ly] cut into nx x ny bilinear quadrilaterals; nodes
+    numbered lexicographically (id = j (nx + 1) + i), each cell's corners
+    counter-clockwise from its low corner."""
+    mx = nx + 1
+    ii, jj = np.meshgrid(np.arange(mx), np.arange(ny + 1), indexing="xy")
+    coords = np.stack([ii.ravel() * (lx / nx), jj.ravel() * (ly / ny)], axis=1).astype(np.float64)
+    ci, cj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    v00 = (cj * mx + ci).ravel()
+    cells = np.stack([v00, v00 + 1, v00 + mx + 1, v00 + mx], axis=1).astype(np.int32)
+    on_bnd = (ii.ravel() == 0) | (ii.ravel() == nx) | (jj.ravel() == 0) | (jj.ravel() == ny)
+    return Mesh(Q1_QUAD_VEC2, coords, cells, on_bnd, h=min(lx / nx, ly / ny), meta={"nx": nx, "ny": ny})
+
+
+def cantilever(nx: int = 60, ny: int = 30, lx: float = 60.0, ly: float = 30.0, load: float = -100.0) -> dict:
+    """Plane-stress cantilever of the SIMP compliance benchmark: quads,
+    clamped on x = 0, a downward traction on the part of x = lx with
+    y <= 0.1 ly, lumped to its nodes (each edge of length l gives l t / 2 to
+    its two ends), uniform density 0.5."""
+    mesh = quad_grid(nx, ny, lx, ly)
+    x, y = mesh.coords[:, 0], mesh.coords[:, 1]
+    F = np.zeros(2 * mesh.n_nodes)
+    edge_nodes = np.flatnonzero(np.isclose(x, lx) & (y <= 0.1 * ly + 1e-12))
+    edge_nodes = edge_nodes[np.argsort(y[edge_nodes])]
+    for a, b in zip(edge_nodes[:-1], edge_nodes[1:]):
+        le = y[b] - y[a]
+        F[2 * a + 1] += load * le / 2
+        F[2 * b + 1] += load * le / 2
+    clamped = np.repeat(np.isclose(x, 0.0), 2)
+    return {"mesh": mesh, "F": F, "dirichlet": clamped, "rho": np.full(mesh.n_elems, 0.5), "E_min": 70.0,
+            "E_max": 70000.0, "penal": 3.0, "nu": 0.3}
 
 
 def jitter(mesh: Mesh, seed: int, frac: float = 0.2) -> Mesh:
