@@ -71,7 +71,8 @@ typedef enum {
   TG_P1_TRI = 0,      /* linear triangle,      3 nodes, d = 2 */
   TG_P2_TRI = 1,      /* quadratic triangle,   6 nodes, d = 2 */
   TG_P1_TET = 2,      /* linear tetrahedron,   4 nodes, d = 3 */
-  TG_P1_TET_VEC3 = 3  /* linear tetrahedron, 3 DoF per node (elasticity), d = 3 */
+  TG_P1_TET_VEC3 = 3, /* linear tetrahedron, 3 DoF per node (elasticity), d = 3 */
+  TG_Q1_QUAD_VEC2 = 4  /* bilinear quadrilateral, 2 DoF per node (plane stress), d = 2 */
 } tg_element;
 
 typedef enum { TG_F32 = 0, TG_F64 = 1 } tg_dtype;
@@ -429,6 +430,29 @@ tg_status tg_assemble_facets(const tg_facets* fc, tg_dtype dtype, const void* co
 tg_status tg_facets_shape(const tg_facets* fc, int64_t* n_facets, int64_t* n_boundary_nodes);
 
 void tg_facets_destroy(tg_facets* fc);
+
+/* ------------------------------------------------------------------------
+ * Plane-stress bilinear quadrilaterals with the SIMP law (the SM's
+ * topology-optimisation benchmark; element kind TG_Q1_QUAD_VEC2, cells
+ * [E][4] counter-clockwise, DoF = 2 node + component).
+ *   E(rho_e) = e_min + rho_e^penal (e_max - e_min),
+ *   K(rho)   = sum_e E(rho_e) K0_e,  K0_e the unit-modulus element matrix
+ *              by the 2 x 2 Gauss rule (tg_quadrature(TG_Q1_QUAD_VEC2)),
+ *              plane-stress Lame constants nu / (1 - nu^2), 1 / (2 (1 + nu)).
+ * ---------------------------------------------------------------------- */
+
+/* vals_out [nnz of the DoF-level CSR of tg_pattern_info]; rho [E];
+ * -1 < nu < 1/2.  Each node's two DoF rows sum their elements in increasing
+ * element order (deterministic).  A non-positive Jacobian determinant at a
+ * Gauss point flags TG_ERR_DEGENERATE_ELEMENT. */
+tg_status tg_assemble_simp(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* rho, double e_min,
+                           double e_max, double penal, double nu, void* vals_out, tg_stream stream);
+
+/* Compliance sensitivity (SM): dc_out[e] = -penal rho_e^(penal-1)
+ * (e_max - e_min) u_e^T K0_e u_e for the displacement u [2 N] of
+ * K(rho) u = F (the compliance C = F^T u is self-adjoint). */
+tg_status tg_simp_sensitivity(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* rho, double e_min,
+                              double e_max, double penal, double nu, const void* u, void* dc_out, tg_stream stream);
 
 /* ------------------------------------------------------------------------
  * Measurement helper (no counterpart in the paper): sustained rate of

@@ -14,12 +14,12 @@ import torch
 
 from .build import LIB
 
-P1_TRI, P2_TRI, P1_TET, P1_TET_VEC3 = 0, 1, 2, 3
+P1_TRI, P2_TRI, P1_TET, P1_TET_VEC3, Q1_QUAD_VEC2 = 0, 1, 2, 3, 4
 F32, F64 = 0, 1
 PER_ELEMENT, PER_QP, PER_NODE, CONSTANT = 0, 1, 2, 3
-NV = {P1_TRI: 3, P2_TRI: 6, P1_TET: 4, P1_TET_VEC3: 4}
-DIM = {P1_TRI: 2, P2_TRI: 2, P1_TET: 3, P1_TET_VEC3: 3}
-NQ = {P1_TRI: 3, P2_TRI: 6, P1_TET: 4, P1_TET_VEC3: 4}
+NV = {P1_TRI: 3, P2_TRI: 6, P1_TET: 4, P1_TET_VEC3: 4, Q1_QUAD_VEC2: 4}
+DIM = {P1_TRI: 2, P2_TRI: 2, P1_TET: 3, P1_TET_VEC3: 3, Q1_QUAD_VEC2: 2}
+NQ = {P1_TRI: 3, P2_TRI: 6, P1_TET: 4, P1_TET_VEC3: 4, Q1_QUAD_VEC2: 4}
 
 STATUS = ["TG_OK", "TG_ERR_INVALID_ARG", "TG_ERR_INDEX_RANGE", "TG_ERR_DEGENERATE_ELEMENT", "TG_ERR_INDEX_OVERFLOW",
           "TG_ERR_OUT_OF_MEMORY", "TG_ERR_CUDA", "TG_ERR_TIMEOUT", "TG_ERR_UNSUPPORTED"]
@@ -67,6 +67,8 @@ def lib():
         "tg_residual": (i32, [vp, i32, vp, vp, i32, dbl, vp, vp, i32, vp, vp, vp, vp]),
         "tg_semilinear_residual": (i32, [vp, i32, vp, vp, i32, dbl, vp, vp, i32, C.POINTER(dbl), vp, vp, vp, vp,
                                          vp]),
+        "tg_assemble_simp": (i32, [vp, i32, vp, vp, dbl, dbl, dbl, dbl, vp, vp]),
+        "tg_simp_sensitivity": (i32, [vp, i32, vp, vp, dbl, dbl, dbl, dbl, vp, vp, vp]),
         "tg_build_facets": (i32, [vp, vp, i64, vp, C.POINTER(vp)]),
         "tg_assemble_facets": (i32, [vp, i32, vp, vp, i32, vp, i32, vp, vp, vp]),
         "tg_facets_shape": (i32, [vp, C.POINTER(i64), C.POINTER(i64)]),
@@ -336,6 +338,27 @@ def tg_semilinear_residual(p: Pattern, coords, kappa, layout: int, c: float, x, 
                                         _ptr(y, dt, "y"), _ptr(ls, dt, "loss"), _stream(stream)),
            "tg_semilinear_residual")
     return y, ls
+
+
+def tg_assemble_simp(p: Pattern, coords, rho, e_min: float, e_max: float, penal: float, nu: float, vals_out=None,
+                     stream=None):
+    if vals_out is None:
+        vals_out = torch.empty(p.nnz, dtype=coords.dtype, device=coords.device)
+    _check(lib().tg_assemble_simp(p.handle, _dt(coords), _ptr(coords, coords.dtype, "coords"),
+                                  _ptr(rho, coords.dtype, "rho"), float(e_min), float(e_max), float(penal), float(nu),
+                                  _ptr(vals_out, coords.dtype, "vals"), _stream(stream)), "tg_assemble_simp")
+    return vals_out
+
+
+def tg_simp_sensitivity(p: Pattern, coords, rho, e_min: float, e_max: float, penal: float, nu: float, u, dc_out=None,
+                        stream=None):
+    if dc_out is None:
+        dc_out = torch.empty_like(rho)
+    _check(lib().tg_simp_sensitivity(p.handle, _dt(coords), _ptr(coords, coords.dtype, "coords"),
+                                     _ptr(rho, coords.dtype, "rho"), float(e_min), float(e_max), float(penal),
+                                     float(nu), _ptr(u, coords.dtype, "u"), _ptr(dc_out, coords.dtype, "dc"),
+                                     _stream(stream)), "tg_simp_sensitivity")
+    return dc_out
 
 
 class Facets:

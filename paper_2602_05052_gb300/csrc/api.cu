@@ -36,7 +36,18 @@ int sm_count() {
 //    orbit the odd barycentric coordinate sits at l0, l1, l2 in turn.
 //  * tetrahedron: barycentric (a, b, b, b) permutations, a = (5 + 3 sqrt5)/20,
 //    b = (5 - sqrt5)/20, weights 1/24; point q has the large coordinate at l_q.
+//  * quadrilateral: the 2 x 2 Gauss-Legendre rule on [0, 1]^2, coordinates
+//    1/2 -+ sqrt(3)/6, weights 1/4; s varies fastest.
 int quadrature_rule(tg_element el, double* w, double* x) {
+  if (el == TG_Q1_QUAD_VEC2) {
+    const double h = std::sqrt(3.0) / 6.0, g[2] = {0.5 - h, 0.5 + h};
+    for (int q = 0; q < 4; ++q) {
+      x[2 * q] = g[q & 1];
+      x[2 * q + 1] = g[q >> 1];
+      w[q] = 0.25;
+    }
+    return 4;
+  }
   if (el == TG_P1_TRI) {
     const double pts[6] = {1.0 / 6, 1.0 / 6, 2.0 / 3, 1.0 / 6, 1.0 / 6, 2.0 / 3};
     for (int q = 0; q < 3; ++q) w[q] = 1.0 / 6;
@@ -69,6 +80,22 @@ static void ref_basis(tg_element el, const double* x, double* v, double (*g)[3])
   for (int a = 0; a < 6; ++a) {
     v[a] = 0;
     g[a][0] = g[a][1] = g[a][2] = 0;
+  }
+  if (el == TG_Q1_QUAD_VEC2) {  // bilinear corners (0,0), (1,0), (1,1), (0,1)
+    const double s = x[0], t = x[1];
+    v[0] = (1 - s) * (1 - t);
+    v[1] = s * (1 - t);
+    v[2] = s * t;
+    v[3] = (1 - s) * t;
+    g[0][0] = -(1 - t);
+    g[0][1] = -(1 - s);
+    g[1][0] = 1 - t;
+    g[1][1] = -s;
+    g[2][0] = t;
+    g[2][1] = s;
+    g[3][0] = -t;
+    g[3][1] = 1 - s;
+    return;
   }
   if (el == TG_P1_TRI || el == TG_P2_TRI) {
     const double l[3] = {1.0 - x[0] - x[1], x[0], x[1]};
@@ -158,7 +185,7 @@ const char* tg_status_string(tg_status s) {
 const char* tg_last_error_message(void) { return tg::g_last_error.c_str(); }
 
 int32_t tg_quadrature(tg_element el, double* w, double* xhat) {
-  if (el < TG_P1_TRI || el > TG_P1_TET_VEC3) return 0;
+  if (el < TG_P1_TRI || el > TG_Q1_QUAD_VEC2) return 0;
   if (el == TG_P1_TET_VEC3) el = TG_P1_TET;
   double ww[6], xx[18];
   const int nq = tg::quadrature_rule(el, ww, xx);
@@ -171,11 +198,12 @@ int32_t tg_quadrature(tg_element el, double* w, double* xhat) {
 tg_status tg_pattern_info(const tg_pattern* p, int64_t* n_rows, int64_t* nnz, const int32_t** row_ptr,
                           const int32_t** col_idx, const int32_t** elem_slot, int32_t* slot_stride) {
   if (!p) return TG_ERR_INVALID_ARG;
-  const bool vec = p->el == TG_P1_TET_VEC3;
-  if (n_rows) *n_rows = vec ? 3 * p->N : p->N;
-  if (nnz) *nnz = vec ? 9 * p->nnz : p->nnz;
-  if (row_ptr) *row_ptr = vec ? p->row_ptr3 : p->row_ptr;
-  if (col_idx) *col_idx = vec ? p->col_idx3 : p->col_idx;
+  const int nc = tg::ncomp_of(p->el);
+  const bool vec = nc > 1;
+  if (n_rows) *n_rows = nc * p->N;
+  if (nnz) *nnz = (int64_t)nc * nc * p->nnz;
+  if (row_ptr) *row_ptr = vec ? p->row_ptr_dof : p->row_ptr;
+  if (col_idx) *col_idx = vec ? p->col_idx_dof : p->col_idx;
   if (elem_slot) *elem_slot = p->elem_slot;
   if (slot_stride) *slot_stride = p->nv * p->nv;
   return TG_OK;
@@ -221,7 +249,7 @@ void tg_pattern_destroy(tg_pattern* p) {
   cudaGetDevice(&prev);
   cudaSetDevice(p->device);
   void* bufs[] = {p->cells,    p->inc_ptr,  p->inc_e,   p->inc_pos, p->row_ptr, p->col_idx, p->elem_slot,
-                  p->row_ptr3, p->col_idx3, p->status, p->partials, p->bel, p->boff, p->bvbase, p->bel_cnt,
+                  p->row_ptr_dof, p->col_idx_dof, p->status, p->partials, p->bel, p->boff, p->bvbase, p->bel_cnt,
                   p->brec, p->elem_pos, p->arrivals,
                   p->iperm, p->urp, p->iinc, p->irp, p->elem_scratch};
   for (void* b : bufs)

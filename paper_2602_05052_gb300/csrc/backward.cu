@@ -1381,7 +1381,7 @@ extern "C" tg_status tg_assemble_backward(const tg_pattern* p, tg_dtype dtype, c
                                           const void* U, void* grad_kappa, void* grad_coords, void* grad_c,
                                           tg_stream stream) {
   if (!p || (dtype != TG_F32 && dtype != TG_F64)) return TG_ERR_INVALID_ARG;
-  if (p->el == TG_P1_TET_VEC3 || !kappa || (p->N > 0 && !coords)) return TG_ERR_INVALID_ARG;
+  if (!tg::scalar_kind(p->el) || !kappa || (p->N > 0 && !coords)) return TG_ERR_INVALID_ARG;
   if (!(kappa_layout == TG_PER_QP || kappa_layout == TG_PER_ELEMENT || kappa_layout == TG_CONSTANT))
     return TG_ERR_INVALID_ARG;
   if (!grad_vals && !(lam && U)) return TG_ERR_INVALID_ARG;
@@ -1399,6 +1399,7 @@ extern "C" tg_status tg_assemble_load_backward(const tg_pattern* p, tg_dtype dty
                                                tg_layout f_layout, int32_t ncomp, const void* grad_F, void* grad_f,
                                                void* grad_coords, int32_t accumulate, tg_stream stream) {
   if (!p || (dtype != TG_F32 && dtype != TG_F64) || !f || !grad_F || (p->N > 0 && !coords)) return TG_ERR_INVALID_ARG;
+  if (p->el == TG_Q1_QUAD_VEC2) return TG_ERR_INVALID_ARG;
   if ((ncomp != 1 && ncomp != 3) || !(f_layout == TG_PER_NODE || f_layout == TG_PER_QP || f_layout == TG_CONSTANT))
     return TG_ERR_INVALID_ARG;
   const size_t es = dtype == TG_F32 ? 4 : 8;

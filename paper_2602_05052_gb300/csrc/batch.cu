@@ -382,7 +382,7 @@ tg_status tg_batch_create(const tg_pattern* const* pats, int32_t n_inst, tg_batc
   if (!out || !pats || n_inst < 1) return TG_ERR_INVALID_ARG;
   *out = nullptr;
   const tg_element el = pats[0] ? pats[0]->el : TG_P1_TRI;
-  if (el == TG_P1_TET_VEC3) return TG_ERR_INVALID_ARG;
+  if (!tg::scalar_kind(el)) return TG_ERR_INVALID_ARG;
   tg_batch* b = new tg_batch;
   b->el = el;
   b->n_inst = n_inst;

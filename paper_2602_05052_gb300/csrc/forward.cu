@@ -575,7 +575,7 @@ tg_status bilinear_entry(const tg_pattern* p, tg_dtype dtype, const void* coords
                          double c, void* vals, tg_stream stream, bool atomic) {
   tg_status st = check_common(p, dtype, coords);
   if (st != TG_OK) return st;
-  if (p->el == TG_P1_TET_VEC3 || !layout_ok(kl, false) || !kappa || (p->nnz > 0 && !vals)) return TG_ERR_INVALID_ARG;
+  if (!tg::scalar_kind(p->el) || !layout_ok(kl, false) || !kappa || (p->nnz > 0 && !vals)) return TG_ERR_INVALID_ARG;
   if (p->N == 0) return TG_OK;
   cudaStream_t s = (cudaStream_t)stream;
   return dtype == TG_F32 ? bilinear<float>(p, coords, kappa, kl, c, vals, s, atomic)
@@ -612,7 +612,7 @@ tg_status tg_assemble_system(const tg_pattern* p, tg_dtype dtype, const void* co
                              void* F_out, tg_stream stream) {
   tg_status st = check_common(p, dtype, coords);
   if (st != TG_OK) return st;
-  if (p->el == TG_P1_TET_VEC3 || !layout_ok(kappa_layout, false) || !kappa || (p->nnz > 0 && !vals_out) || !f ||
+  if (!tg::scalar_kind(p->el) || !layout_ok(kappa_layout, false) || !kappa || (p->nnz > 0 && !vals_out) || !f ||
       !F_out || !(f_layout == TG_PER_NODE || f_layout == TG_PER_QP || f_layout == TG_CONSTANT))
     return TG_ERR_INVALID_ARG;
   if (p->N == 0) return TG_OK;
@@ -626,7 +626,7 @@ tg_status tg_assemble_load(const tg_pattern* p, tg_dtype dtype, const void* coor
   tg_status st = check_common(p, dtype, coords);
   if (st != TG_OK) return st;
   if ((ncomp != 1 && ncomp != 3) || !f || !F_out || !(f_layout == TG_PER_NODE || f_layout == TG_PER_QP ||
-                                                       f_layout == TG_CONSTANT))
+                                                       f_layout == TG_CONSTANT) || p->el == TG_Q1_QUAD_VEC2)
     return TG_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   return dtype == TG_F32 ? load<float>(p, coords, f, f_layout, ncomp, F_out, s)

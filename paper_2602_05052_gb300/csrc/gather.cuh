@@ -391,7 +391,8 @@ inline const RefTab<T>& table(tg_element el) {
   static const RefTab<T> t0 = ref_table<T>(TG_P1_TRI);
   static const RefTab<T> t1 = ref_table<T>(TG_P2_TRI);
   static const RefTab<T> t2 = ref_table<T>(TG_P1_TET);
-  return el == TG_P1_TRI ? t0 : el == TG_P2_TRI ? t1 : t2;
+  static const RefTab<T> t3 = ref_table<T>(TG_Q1_QUAD_VEC2);
+  return el == TG_P1_TRI ? t0 : el == TG_P2_TRI ? t1 : el == TG_Q1_QUAD_VEC2 ? t3 : t2;
 }
 
 // Host: rows per CTA of the staged kernels and the shared-memory bytes of the

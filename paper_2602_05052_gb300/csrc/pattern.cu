@@ -156,7 +156,7 @@ __device__ __forceinline__ int lower_bound(const int* cols, int len, int v) {
 // per-incidence positions and the element-to-slot map.
 template <bool FILL>
 __global__ void __launch_bounds__(128) k_rows(const int32_t* __restrict__ cells, const int32_t* __restrict__ inc_ptr,
-                                              const int32_t* __restrict__ inc_e, int64_t N, int nv, int npw, bool vec3,
+                                              const int32_t* __restrict__ inc_e, int64_t N, int nv, int npw, int nc,
                                               int32_t* __restrict__ row_len, int* __restrict__ maxes,
                                               const int32_t* __restrict__ row_ptr, int32_t* __restrict__ col_idx,
                                               uint32_t* __restrict__ inc_pos, int32_t* __restrict__ elem_slot,
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(128) k_rows(const int32_t* __restrict__ cells,
       const uint32_t pos = (uint32_t)lower_bound(cols, len, cells[(int64_t)e * nv + b]);
       if (b < 4) w0 |= pos << (8 * b);
       else w1 |= pos << (8 * (b - 4));
-      const int64_t slot = vec3 ? 9ll * r0 + 3ll * pos : (int64_t)r0 + pos;
+      const int64_t slot = (int64_t)nc * nc * r0 + (int64_t)nc * pos;
       elem_slot[((int64_t)e * nv + a) * nv + b] = (int32_t)slot;
     }
     inc_pos[(int64_t)j * npw] = w0;
@@ -195,17 +195,21 @@ __global__ void __launch_bounds__(128) k_rows(const int32_t* __restrict__ cells,
   }
 }
 
-__global__ void k_expand3(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int64_t N,
-                          int32_t* __restrict__ row_ptr3, int32_t* __restrict__ col_idx3) {
+// DoF-level CSR of a vector kind with nc DoFs per node (DoF = nc node +
+// component): node row n becomes nc DoF rows of nc len entries, block
+// (n, m) at columns nc m .. nc m + nc - 1.
+__global__ void k_expand(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int64_t N, int nc,
+                         int32_t* __restrict__ row_ptr_dof, int32_t* __restrict__ col_idx_dof) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int r0 = row_ptr[n], len = row_ptr[n + 1] - r0;
-  for (int i = 0; i < 3; ++i) {
-    row_ptr3[3 * n + i] = 9 * r0 + 3 * i * len;
+  for (int i = 0; i < nc; ++i) {
+    row_ptr_dof[nc * n + i] = nc * nc * r0 + nc * i * len;
     for (int p = 0; p < len; ++p)
-      for (int j = 0; j < 3; ++j) col_idx3[9ll * r0 + (i * len + p) * 3 + j] = 3 * col_idx[r0 + p] + j;
+      for (int j = 0; j < nc; ++j)
+        col_idx_dof[(int64_t)nc * nc * r0 + (int64_t)(i * len + p) * nc + j] = nc * col_idx[r0 + p] + j;
   }
-  if (n == N - 1) row_ptr3[3 * N] = 9 * row_ptr[N];
+  if (n == N - 1) row_ptr_dof[nc * N] = nc * nc * row_ptr[N];
 }
 
 // ------------------------------------------------------------------ row blocks
@@ -666,7 +670,7 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
                                       tg_stream stream, tg_pattern** out) {
   if (!out) return TG_ERR_INVALID_ARG;
   *out = nullptr;
-  if (el < TG_P1_TRI || el > TG_P1_TET_VEC3 || n_elems < 0 || n_nodes < 1) return TG_ERR_INVALID_ARG;
+  if (el < TG_P1_TRI || el > TG_Q1_QUAD_VEC2 || n_elems < 0 || n_nodes < 1) return TG_ERR_INVALID_ARG;
   if (n_elems > 0 && !cells) return TG_ERR_INVALID_ARG;
   const int nv = tg::nv_of(el);
   if (n_nodes > INT32_MAX || n_elems >= (1ll << 28) || n_elems * nv > INT32_MAX) return TG_ERR_INDEX_OVERFLOW;
@@ -736,7 +740,8 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   TG_CK(tmp.alloc(&maxes, 2));
   TG_CK(cudaMemsetAsync(maxes, 0, 2 * sizeof(int), s));
   const bool vec3 = el == TG_P1_TET_VEC3;
-  k_rows<false><<<tg::grid_for(N, 128), 128, 0, s>>>(p->cells, p->inc_ptr, p->inc_e, N, nv, p->npw, vec3, row_len,
+  const int nc = tg::ncomp_of(el);
+  k_rows<false><<<tg::grid_for(N, 128), 128, 0, s>>>(p->cells, p->inc_ptr, p->inc_e, N, nv, p->npw, nc, row_len,
                                                       maxes, nullptr, nullptr, nullptr, nullptr, p->status);
   TG_CK_LAUNCH("k_rows<false>");
   int hmax[2];
@@ -748,7 +753,7 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   int64_t nnz = 0;
   TG_CK(cudaMemcpyAsync(&nnz, tmp64 + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   TG_CK(cudaStreamSynchronize(s));
-  if (nnz > INT32_MAX || (vec3 && 9 * nnz > INT32_MAX)) {
+  if ((int64_t)nc * nc * nnz > INT32_MAX) {
     tg::set_error("tg_build_pattern: nnz exceeds int32 indices");
     return TG_ERR_INDEX_OVERFLOW;
   }
@@ -761,23 +766,25 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   TG_CK(cudaMalloc(&p->col_idx, nnz * sizeof(int32_t) + 16));
   TG_CK(cudaMalloc(&p->inc_pos, nvE * p->npw * sizeof(uint32_t) + 16));
   TG_CK(cudaMalloc(&p->elem_slot, nvE * nv * sizeof(int32_t) + 16));
-  k_rows<true><<<tg::grid_for(N, 128), 128, 0, s>>>(p->cells, p->inc_ptr, p->inc_e, N, nv, p->npw, vec3, nullptr,
+  k_rows<true><<<tg::grid_for(N, 128), 128, 0, s>>>(p->cells, p->inc_ptr, p->inc_e, N, nv, p->npw, nc, nullptr,
                                                      nullptr, p->row_ptr, p->col_idx, p->inc_pos, p->elem_slot,
                                                      p->status);
   TG_CK_LAUNCH("k_rows<true>");
 
 
-  // 5. row blocks of the element-once P1 kernels
-  if (E > 0) {
+  // 5. row blocks of the element-once kernels (not for the quadrilaterals,
+  // which the plane-stress kernels serve per node row)
+  if (E > 0 && el != TG_Q1_QUAD_VEC2) {
     if ((st = build_blocks(p, s)) != TG_OK) return st;
   }
 
   // 6. DoF-level CSR for elasticity
-  if (vec3) {
-    TG_CK(cudaMalloc(&p->row_ptr3, (3 * N + 1) * sizeof(int32_t)));
-    TG_CK(cudaMalloc(&p->col_idx3, 9 * nnz * sizeof(int32_t) + 16));
-    k_expand3<<<tg::grid_for(N, kThreads), kThreads, 0, s>>>(p->row_ptr, p->col_idx, N, p->row_ptr3, p->col_idx3);
-    TG_CK_LAUNCH("k_expand3");
+  if (nc > 1) {
+    TG_CK(cudaMalloc(&p->row_ptr_dof, (nc * N + 1) * sizeof(int32_t)));
+    TG_CK(cudaMalloc(&p->col_idx_dof, (size_t)nc * nc * nnz * sizeof(int32_t) + 16));
+    k_expand<<<tg::grid_for(N, kThreads), kThreads, 0, s>>>(p->row_ptr, p->col_idx, N, nc, p->row_ptr_dof,
+                                                            p->col_idx_dof);
+    TG_CK_LAUNCH("k_expand");
   }
 
   // per-CTA partials of the backward's global sums (4 values per CTA of at
@@ -786,7 +793,7 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   TG_CK(cudaMalloc(&p->partials, p->n_partials * sizeof(double)));
   TG_CK(cudaMalloc(&p->arrivals, 16));
   TG_CK(cudaMemsetAsync(p->arrivals, 0, 16, s));
-  if (!vec3 && E > 0) TG_CK(cudaMalloc(&p->elem_scratch, (size_t)E * nv * tg::dim_of(el) * sizeof(double)));
+  if (nc == 1 && E > 0) TG_CK(cudaMalloc(&p->elem_scratch, (size_t)E * nv * tg::dim_of(el) * sizeof(double)));
   TG_CK(cudaStreamSynchronize(s));
   if ((st = read_status(p, s, "tg_build_pattern")) != TG_OK) return st;
   guard.ok = true;

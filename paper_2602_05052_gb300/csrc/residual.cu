@@ -399,7 +399,7 @@ tg_status entry(const tg_pattern* p, tg_dtype dtype, const void* coords, const v
                 double c, const void* x, const void* f, tg_layout f_layout, const double* reaction,
                 const void* x_react, const uint8_t* dirichlet, void* y, void* loss, tg_stream stream) {
   if (!p || (dtype != TG_F32 && dtype != TG_F64)) return TG_ERR_INVALID_ARG;
-  if (p->el == TG_P1_TET_VEC3) return TG_ERR_INVALID_ARG;
+  if (!tg::scalar_kind(p->el)) return TG_ERR_INVALID_ARG;
   if (!(kappa_layout == TG_PER_QP || kappa_layout == TG_PER_ELEMENT || kappa_layout == TG_CONSTANT)) return TG_ERR_INVALID_ARG;
   if (f && !(f_layout == TG_PER_NODE || f_layout == TG_PER_QP || f_layout == TG_CONSTANT)) return TG_ERR_INVALID_ARG;
   if (f && p->el == TG_P2_TRI) {

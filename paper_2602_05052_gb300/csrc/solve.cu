@@ -134,10 +134,11 @@ struct CgWork {
 template <typename T>
 tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8_t* mask, void* x_, double rtol,
              int maxit, int* iters, double* relres, const CgWork<T>& w, cudaStream_t s) {
-  const bool vec = p->el == TG_P1_TET_VEC3;
-  const int64_t n = vec ? 3 * p->N : p->N;
-  const int32_t* rp = vec ? p->row_ptr3 : p->row_ptr;
-  const int32_t* ci = vec ? p->col_idx3 : p->col_idx;
+  const int nc = tg::ncomp_of(p->el);
+  const bool vec = nc > 1;
+  const int64_t n = nc * p->N;
+  const int32_t* rp = vec ? p->row_ptr_dof : p->row_ptr;
+  const int32_t* ci = vec ? p->col_idx_dof : p->col_idx;
   const T* vals = static_cast<const T*>(vals_);
   const T* F = static_cast<const T*>(F_);
   T* x = static_cast<T*>(x_);
@@ -183,7 +184,7 @@ tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8
 template <typename T>
 tg_status cg_alloc(const tg_pattern* p, const void* vals, const void* F, const uint8_t* mask, void* x, double rtol,
                    int maxit, int* iters, double* relres, cudaStream_t s) {
-  const int64_t n = p->el == TG_P1_TET_VEC3 ? 3 * p->N : p->N;
+  const int64_t n = tg::ncomp_of(p->el) * p->N;
   Dev d;
   CgWork<T> w;
   w.nb = 2 * tg::sm_count();
@@ -240,7 +241,7 @@ inline size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 template <typename T>
 tg_status cg_noalloc(const tg_pattern* p, const void* vals, const void* F, const uint8_t* mask, void* x,
                      double rtol, int maxit, int* iters, double* relres, cudaStream_t s) {
-  const int64_t n = p->el == TG_P1_TET_VEC3 ? 3 * p->N : p->N;
+  const int64_t n = tg::ncomp_of(p->el) * p->N;
   const size_t vb = round256((size_t)n * sizeof(T));
   if (kNoAllocHead + 4 * vb > kNoAllocBytes) {
     tg::set_error("tg_cg_solve_noalloc: " + std::to_string(n) + " rows need " +
@@ -299,10 +300,11 @@ extern "C" {
 
 tg_status tg_spmv(const tg_pattern* p, tg_dtype dtype, const void* vals, const void* x, void* y, tg_stream stream) {
   if (!p || (dtype != TG_F32 && dtype != TG_F64) || !vals || !x || !y) return TG_ERR_INVALID_ARG;
-  const bool vec = p->el == TG_P1_TET_VEC3;
-  const int64_t n = vec ? 3 * p->N : p->N;
-  const int32_t* rp = vec ? p->row_ptr3 : p->row_ptr;
-  const int32_t* ci = vec ? p->col_idx3 : p->col_idx;
+  const int nc = tg::ncomp_of(p->el);
+  const bool vec = nc > 1;
+  const int64_t n = nc * p->N;
+  const int32_t* rp = vec ? p->row_ptr_dof : p->row_ptr;
+  const int32_t* ci = vec ? p->col_idx_dof : p->col_idx;
   cudaStream_t s = (cudaStream_t)stream;
   const int g = tg::grid_for(4 * n, ST);
   if (dtype == TG_F32)
@@ -345,10 +347,11 @@ tg_status tg_cg_solve_noalloc(const tg_pattern* p, tg_dtype dtype, const void* v
 tg_status tg_csr_outer(const tg_pattern* p, tg_dtype dtype, const void* lam, const void* U, double alpha, void* out,
                        tg_stream stream) {
   if (!p || (dtype != TG_F32 && dtype != TG_F64) || !lam || !U || !out) return TG_ERR_INVALID_ARG;
-  const bool vec = p->el == TG_P1_TET_VEC3;
-  const int64_t n = vec ? 3 * p->N : p->N;
-  const int32_t* rp = vec ? p->row_ptr3 : p->row_ptr;
-  const int32_t* ci = vec ? p->col_idx3 : p->col_idx;
+  const int nc = tg::ncomp_of(p->el);
+  const bool vec = nc > 1;
+  const int64_t n = nc * p->N;
+  const int32_t* rp = vec ? p->row_ptr_dof : p->row_ptr;
+  const int32_t* ci = vec ? p->col_idx_dof : p->col_idx;
   cudaStream_t s = (cudaStream_t)stream;
   const int g = tg::grid_for(n, ST / 8);
   if (dtype == TG_F32)

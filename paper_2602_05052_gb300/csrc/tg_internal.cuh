@@ -10,7 +10,8 @@
 //                             Algorithm 2 in compressed, row-owned form
 //   row_ptr  [N+1], col_idx [nnz]   node-level CSR
 //   elem_slot [E][nv][nv]     CSR slot of each local entry (API view)
-//   row_ptr3 [3N+1], col_idx3 [9 nnz]  DoF-level CSR (vector elasticity)
+//   row_ptr_dof [nc N+1], col_idx_dof [nc^2 nnz]  DoF-level CSR of the vector kinds
+//                         (nc DoFs per node: 3 tetrahedral elasticity, 2 plane-stress quads)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -35,8 +36,8 @@ struct tg_pattern {
   int32_t* row_ptr = nullptr;
   int32_t* col_idx = nullptr;
   int32_t* elem_slot = nullptr;
-  int32_t* row_ptr3 = nullptr;
-  int32_t* col_idx3 = nullptr;
+  int32_t* row_ptr_dof = nullptr;
+  int32_t* col_idx_dof = nullptr;
   // Row blocks of the element-once P1 kernels (P1 triangles, tetrahedra and
   // vector elasticity, built when the packed fields fit; bel == NULL
   // otherwise).  The kernels walk the rows in an internal order: iperm[i] is
@@ -117,9 +118,18 @@ struct Elem<TG_P1_TET> {
   static constexpr int nv = 4, dim = 3, nq = 4, ngeo = 4, npw = 1;
 };
 
+template <>
+struct Elem<TG_Q1_QUAD_VEC2> {
+  static constexpr int nv = 4, dim = 2, nq = 4, ngeo = 4, npw = 1;
+};
+
 inline int nv_of(tg_element el) { return el == TG_P1_TRI ? 3 : el == TG_P2_TRI ? 6 : 4; }
-inline int dim_of(tg_element el) { return (el == TG_P1_TRI || el == TG_P2_TRI) ? 2 : 3; }
+inline int dim_of(tg_element el) { return (el == TG_P1_TRI || el == TG_P2_TRI || el == TG_Q1_QUAD_VEC2) ? 2 : 3; }
 inline int nq_of(tg_element el) { return el == TG_P1_TRI ? 3 : el == TG_P2_TRI ? 6 : 4; }
+// DoFs per node: 3 for tetrahedral elasticity, 2 for plane-stress quads, 1 otherwise
+inline int ncomp_of(tg_element el) { return el == TG_P1_TET_VEC3 ? 3 : el == TG_Q1_QUAD_VEC2 ? 2 : 1; }
+// the scalar element kinds (the Poisson-type assembly, load, residual, backward)
+inline bool scalar_kind(tg_element el) { return el == TG_P1_TRI || el == TG_P2_TRI || el == TG_P1_TET; }
 
 // Reference tables of one element kind, built on the host from the
 // quadrature rule and the reference basis, passed to kernels by value.
