@@ -19,7 +19,10 @@
 
 namespace {
 
-constexpr int ST = 128;
+// Small CTAs: the benchmark's meshes are small (a few thousand nodes) and
+// the FP64 element arithmetic is bound by each SM's FP64 pipe, so the work
+// is spread over as many SMs as possible.
+constexpr int ST = 32;
 
 template <typename T>
 struct SimpArgs {
