@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / elasticity / batched breakdown")
+    ap.add_argument("--extras-only", choices=["residual", "facets"], default=None,
+                    help="run only this part of the breakdown (short runs, e.g. for profiling one kernel)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -420,7 +422,11 @@ def main():
                           "pipelined over two device buffer sets on copy-in, compute and copy-out streams"},
            "clocks": clocks}
 
-    if not args.no_extras and rank == 0:
+    if args.extras_only and rank == 0:
+        part = residual_extras if args.extras_only == "residual" else (
+            lambda *a: facet_extras(tg, torch, dev, m, p, flush))
+        out["breakdown"] = part(tg, torch, dev, m, cfg, p, peak, flush)
+    elif not args.no_extras and rank == 0:
         out["breakdown"] = extras(tg, torch, dev, m, cfg, p, peak, flush)
     if not args.no_cpu_baseline and rank == 0:
         reps = 3
