@@ -51,12 +51,38 @@ def test_batch_bitwise_equals_single_launches(tg, dtype):
 
 
 
+def test_batched_p2_full_size(tg):
+    """The 256-instance batched P2 workload as the benchmark runs it (FP32,
+    autotuned schedule, one launch): bitwise equal to 256 single launches,
+    and eight instances across the size range within the FP32 tolerance of
+    the oracle."""
+    insts = mg.batched_p2(256, seed=4)
+    pats, xs, ks = [], [], []
+    for k in insts:
+        m = k["mesh"]
+        pats.append(tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P2_TRI))
+        xs.append(dev(m.coords, torch.float32))
+        ks.append(dev(k["kappa"], torch.float32))
+    b = tg.tg_batch_create(pats)
+    cs = [0.0] * len(pats)
+    out = [torch.full((p.nnz,), float("nan"), dtype=torch.float32, device="cuda") for p in pats]
+    tg.tg_batch_autotune(b, xs, ks, mg.PER_QP, cs, out, reps=2)
+    tg.tg_batch_assemble(b, xs, ks, mg.PER_QP, cs, out)
+    for j, p in enumerate(pats):
+        assert torch.equal(out[j], tg.tg_assemble_bilinear(p, xs[j], ks[j], mg.PER_QP, 0.0)), j
+    order = np.argsort([k["mesh"].n_elems for k in insts])
+    for j in order[:: len(order) // 8][:8]:
+        m = insts[j]["mesh"]
+        ref = O.assemble_bilinear(O.P2_TRI, m.cells, host_as(m.coords, torch.float32),
+                                  host_as(insts[j]["kappa"], torch.float32), O.PER_QP, 0.0)
+        assert relfro(out[j].cpu().numpy(), ref.val) <= TOL[torch.float32], j
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 @pytest.mark.parametrize("el", [mg.P1_TRI, mg.P1_TET])
 def test_batch_p1_bitwise_equals_single_launches(tg, dtype, el):
-    """P1 single launches take the element-once row blocks, the batch the
-    per-incidence rows; the entries and the summation order are the same, so
-    the results are bitwise equal."""
+    """The batch runs each instance's row blocks with the single-instance
+    block body, so its results are bitwise equal to single launches."""
     meshes = []
     for k, n in enumerate([3, 17, 40] if el == mg.P1_TRI else [2, 5, 9]):
         m = mg.jitter(mg.tri_grid(n), 50 + k) if el == mg.P1_TRI else mg.kuhn_tet_grid(n)
