@@ -1029,9 +1029,11 @@ tg_status launch_blk(const tg_pattern* p, const BwdArgs<T>& a, bool fused, int* 
     if (fused) go(k_backward_blk<D, T, true, 1>);
     else go(k_backward_blk<D, T, false, 1>);
   } else {
-    if (need >= 3) {
-      if (fused) go(k_backward_blk<D, T, true, 3>);
-      else go(k_backward_blk<D, T, false, 3>);
+    // the fused adjoint path (lam U^T, no gvals gather) runs faster with two
+    // elements per thread and one CTA more per SM (61 against 67 us at
+    // 1024^2); the gvals path with three (69 against 70)
+    if (need >= 3 && !fused) {
+      go(k_backward_blk<D, T, false, 3>);
     } else {
       if (fused) go(k_backward_blk<D, T, true, 2>);
       else go(k_backward_blk<D, T, false, 2>);
