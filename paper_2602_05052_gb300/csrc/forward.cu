@@ -20,6 +20,7 @@
 namespace {
 
 constexpr int BS = 128;  // rows per CTA (scalar kernels)
+constexpr int BT = 128;  // threads per CTA of the element-once kernels (>= rows per block)
 constexpr int EB = 64;   // rows per CTA (elasticity: 9 * row length accumulators per thread)
 // Largest shared memory of an element-once CTA (two CTAs per SM); patterns
 // that need more use the generic kernels.
@@ -55,13 +56,21 @@ constexpr int blk_min_ctas() {
   return EL == TG_P1_TET ? 2 : EL == TG_P2_TRI ? 4 : sizeof(T) == 8 ? 4 : UB <= 4 ? 7 : 5;
 }
 
+// The same register budget for CTAs of BT threads (LOAD keeps one CTA of
+// 128 threads less).
+template <int EL, typename T, int UB, bool LOAD>
+constexpr int blk_min_ctas_bt() {
+  const int n = (blk_min_ctas<EL, T, UB>() - (LOAD ? 1 : 0)) * 128 / BT;
+  return n < 1 ? 1 : n;
+}
+
 // Scalar forward over element-once row blocks (blocks.cuh): the Map and
 // Reduce of blk_bilinear_block per row block.  LOAD also assembles the load
 // vector F (a.f, a.f_layout -> a.F), entry for entry the arithmetic of
 // k_load_blk: the system (K, F) in one pass.  acc_n = the accumulator count
 // (the longest row x BS), cleared here once and by every block after use.
 template <int EL, typename T, int UB, bool LOAD>
-__global__ void __launch_bounds__(BS, blk_min_ctas<EL, T, UB>() - (LOAD ? 1 : 0)) k_bilinear_blk(
+__global__ void __launch_bounds__(BT, blk_min_ctas_bt<EL, T, UB, LOAD>()) k_bilinear_blk(
     const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab, const tg::BlkArgs g, int acc_n) {
   constexpr int NV = tg::Elem<EL>::nv;
   static_assert(!LOAD || EL != TG_P2_TRI, "the one-pass system is built for P1");
@@ -80,14 +89,14 @@ template <int NV, typename T, bool LOAD>
 size_t bilinear_blk_smem(const tg_pattern* p) {
   const tg::BlkArgs g = tg::blk_args(p);
   return tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE, NV) +
-         tg::blk_bilinear_work_bytes<NV, T, LOAD>(g.capE, p->max_row_len, BS);
+         tg::blk_bilinear_work_bytes<NV, T, LOAD>(g.capE, p->max_row_len, BT);
 }
 
 // P1 load vector over element-once row blocks: Map F_e (NV values) per
 // distinct element, Reduce F[i] = sum of the incidences' entries in
 // increasing element order (second line of Eq. (matlclquad)).
 template <int D, typename T, int UB>
-__global__ void __launch_bounds__(BS) k_load_blk(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
+__global__ void __launch_bounds__(BT) k_load_blk(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
                                                  const tg::BlkArgs g) {
   constexpr int NV = D + 1, NQ = D == 2 ? 3 : 4;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -156,14 +165,14 @@ size_t load_blk_smem(const tg_pattern* p) {
 // rounds.
 template <typename T>
 int blk_ub(const tg_pattern* p) {
-  const int need = (p->blk_max_elems + BS - 1) / BS;
+  const int need = (p->blk_max_elems + BT - 1) / BT;
   if (p->el == TG_P2_TRI) return need <= 1 ? 1 : 2;
   if (sizeof(T) == 8) return need <= 2 ? 2 : 3;
-  return need <= 3 ? 3 : need <= 4 ? 4 : need <= 5 ? 5 : 6;
+  return need <= 2 ? 2 : need <= 3 ? 3 : need <= 4 ? 4 : need <= 5 ? 5 : 6;
 }
 
-// Threads per CTA of the element-once kernels (rows per block <= BS).
-inline int blk_threads(const tg_pattern*) { return BS; }
+// Threads per CTA of the element-once kernels (rows per block <= BT).
+inline int blk_threads(const tg_pattern*) { return BT; }
 
 // Persistent launch of an element-once kernel: one CTA per resident slot,
 // at most one per row block.
@@ -388,7 +397,7 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
       auto go = [&](auto kern) {
         dim3 grid;
         if ((st = launch_blk(kern, sb, p, &grid)) != TG_OK) return;
-        kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::blk_args(p), p->max_row_len * BS);
+        kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::blk_args(p), p->max_row_len * BT);
       };
       if constexpr (EL == TG_P2_TRI) {
         if (ub <= 1) go(k_bilinear_blk<EL, T, 1, false>);
@@ -397,7 +406,8 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
         if (ub == 2) go(k_bilinear_blk<EL, T, 2, false>);
         else go(k_bilinear_blk<EL, T, 3, false>);
       } else {
-        if (ub == 3) go(k_bilinear_blk<EL, T, 3, false>);
+        if (ub == 2) go(k_bilinear_blk<EL, T, 2, false>);
+        else if (ub == 3) go(k_bilinear_blk<EL, T, 3, false>);
         else if (ub == 4) go(k_bilinear_blk<EL, T, 4, false>);
         else if (ub == 5) go(k_bilinear_blk<EL, T, 5, false>);
         else go(k_bilinear_blk<EL, T, 6, false>);
@@ -542,14 +552,15 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
       auto go = [&](auto kern) {
         dim3 grid;
         if ((st = launch_blk(kern, sb, p, &grid)) != TG_OK) return;
-        kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::blk_args(p), p->max_row_len * BS);
+        kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::blk_args(p), p->max_row_len * BT);
       };
       if constexpr (sizeof(T) == 8) {
         if (tri) go(k_bilinear_blk<TG_P1_TRI, T, 2, true>);
         else go(k_bilinear_blk<TG_P1_TET, T, 2, true>);
       } else {
         if (tri) {
-          if (ub <= 3) go(k_bilinear_blk<TG_P1_TRI, T, 3, true>);
+          if (ub <= 2) go(k_bilinear_blk<TG_P1_TRI, T, 2, true>);
+          else if (ub <= 3) go(k_bilinear_blk<TG_P1_TRI, T, 3, true>);
           else if (ub <= 4) go(k_bilinear_blk<TG_P1_TRI, T, 4, true>);
           else go(k_bilinear_blk<TG_P1_TRI, T, 6, true>);
         } else {
