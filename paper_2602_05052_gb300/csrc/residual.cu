@@ -185,8 +185,15 @@ __device__ __forceinline__ void finish_loss(const ResArgs<T>& r, double part) {
 // Element-once row blocks: Map the block's distinct elements into
 // Ye[NV][capE], Reduce the rows (increasing element order), apply the
 // Dirichlet mask, write y and add y^2 to this thread's loss term.
+// FP32 triangles run two elements per thread at eight CTAs per SM (64
+// registers): 51 against 53 us for three elements at six CTAs (1024^2).
+template <int EL, typename T, int UB>
+constexpr int res_min_ctas() {
+  return (EL == TG_P1_TRI && sizeof(T) == 4 && UB == 2) ? 8 : 1;
+}
+
 template <int EL, typename T, int UB, bool LOADF, int NL>
-__global__ void __launch_bounds__(RT) k_residual_blk(const ResArgs<T> r, const __grid_constant__ tg::RefTab<T> tab,
+__global__ void __launch_bounds__(RT, res_min_ctas<EL, T, UB>()) k_residual_blk(const ResArgs<T> r, const __grid_constant__ tg::RefTab<T> tab,
                                                     const tg::BlkArgs g) {
   constexpr int NV = tg::Elem<EL>::nv;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -321,8 +328,14 @@ tg_status launch_el(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t s) {
       tg_status st = TG_OK;
       auto go = [&](auto kern) {
         if ((st = tg::set_smem((const void*)kern, smem)) != TG_OK) return;
+        // the most shared memory per SM, so that eight CTAs fit
+        cudaError_t ce = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (ce != cudaSuccess) {
+          st = tg::cuda_fail(ce, "cudaFuncSetAttribute", __FILE__, __LINE__);
+          return;
+        }
         int per_sm = 0;
-        cudaError_t ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RT, smem);
+        ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RT, smem);
         if (ce != cudaSuccess) {
           st = tg::cuda_fail(ce, "cudaOccupancyMaxActiveBlocksPerMultiprocessor", __FILE__, __LINE__);
           return;
@@ -331,7 +344,7 @@ tg_status launch_el(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t s) {
             (int)std::min<int64_t>({p->n_blk, (int64_t)std::max(per_sm, 1) * tg::sm_count(), cap_ctas});
         kern<<<grid, RT, smem, s>>>(r, tab, g);
       };
-      if constexpr (EL == TG_P2_TRI) {
+      if constexpr (EL == TG_P2_TRI || EL == TG_P1_TRI) {
         go(k_residual_blk<EL, T, 2, LOADF, NL>);
       } else {
         if (need <= 2) go(k_residual_blk<EL, T, 2, LOADF, NL>);
