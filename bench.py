@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / elasticity / batched breakdown")
-    ap.add_argument("--extras-only", choices=["residual", "facets"], default=None,
+    ap.add_argument("--extras-only", choices=["residual", "facets", "batch"], default=None,
                     help="run only this part of the breakdown (short runs, e.g. for profiling one kernel)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -423,9 +423,12 @@ def main():
            "clocks": clocks}
 
     if args.extras_only and rank == 0:
-        part = residual_extras if args.extras_only == "residual" else (
-            lambda *a: facet_extras(tg, torch, dev, m, p, flush))
-        out["breakdown"] = part(tg, torch, dev, m, cfg, p, peak, flush)
+        if args.extras_only == "residual":
+            out["breakdown"] = residual_extras(tg, torch, dev, m, cfg, p, peak, flush)
+        elif args.extras_only == "facets":
+            out["breakdown"] = facet_extras(tg, torch, dev, m, p, flush)
+        else:
+            out["breakdown"] = batch_extras(tg, torch, dev, peak, flush)
     elif not args.no_extras and rank == 0:
         out["breakdown"] = extras(tg, torch, dev, m, cfg, p, peak, flush)
     if not args.no_cpu_baseline and rank == 0:
@@ -523,7 +526,15 @@ def extras(tg, torch, dev, m, cfg, p, peak, flush):
                                       "bwd_ms": ms_eb, "bwd_alg_GBps": bb / ms_eb / 1e6,
                                       "bwd_frac_hbm": bb / ms_eb / 1e6 / peak}
     del pe
-    # batched P2: 256 instances, one persistent launch vs 256 launches
+    out.update(batch_extras(tg, torch, dev, peak, flush))
+    out.update(small_configs(tg, torch, dev))
+    return out
+
+
+def batch_extras(tg, torch, dev, peak, flush):
+    """Batched P2: 256 instances, one persistent launch against 256 launches
+    (plain and graph-captured)."""
+    out = {}
     insts = mg.batched_p2(256, seed=4)
     dt = torch.float32
     pats, xs, ks, vs = [], [], [], []
@@ -569,7 +580,6 @@ def extras(tg, torch, dev, m, cfg, p, peak, flush):
         "batched_frac_hbm": tot_b / ms_b / 1e6 / peak, "speedup_vs_looped": ms_l / ms_b,
         "speedup_vs_looped_graph": ms_lg / ms_bg, "bitwise_equal_to_looped": same}
     del b, pats, xs, ks, vs
-    out.update(small_configs(tg, torch, dev))
     return out
 
 
