@@ -51,6 +51,14 @@ def test_quadrature_rules_match_the_oracle(L):
         d = ox.shape[1]
         assert np.allclose(np.array(w[:]), ow, rtol=0, atol=1e-15)
         assert np.allclose(np.array(x[: nq * d]).reshape(nq, d), ox, rtol=0, atol=1e-15)
+    # the quadrilateral's 2 x 2 Gauss rule against the quad oracle's
+    from oracle import quad as Q
+    pts, ow = Q.gauss2()
+    w = (C.c_double * 4)()
+    x = (C.c_double * 8)()
+    assert L.tg_quadrature(4, w, x) == 4
+    assert np.allclose(np.array(w[:]), ow, rtol=0, atol=1e-15)
+    assert np.allclose(np.array(x[:]).reshape(4, 2), np.array(pts), rtol=0, atol=1e-15)
 
 
 def test_host_validation_without_gpu(L):
@@ -72,6 +80,24 @@ def test_host_validation_without_gpu(L):
     assert L.tg_diag_fma_rate(1, None, None) == 1
     L.tg_cg_solve.argtypes = [vp, C.c_int32, vp, vp, vp, vp, C.c_double, C.c_int32, vp, vp, vp]
     assert L.tg_cg_solve(None, 1, None, None, None, None, 1e-10, 10, None, None, None) == 1
+    L.tg_residual.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, C.c_double, vp, vp, C.c_int32, vp, vp, vp, vp]
+    assert L.tg_residual(None, 0, None, None, 1, 0.0, None, None, 2, None, None, None, None) == 1
+    L.tg_semilinear_residual.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, C.c_double, vp, vp, C.c_int32, vp, vp,
+                                         vp, vp, vp, vp]
+    assert L.tg_semilinear_residual(None, 0, None, None, 1, 0.0, None, None, 2, None, None, None, None, None,
+                                    None) == 1
+    L.tg_build_facets.argtypes = [vp, vp, C.c_int64, vp, C.POINTER(vp)]
+    assert L.tg_build_facets(None, None, 0, None, C.byref(out)) == 1
+    assert L.tg_build_facets(None, None, 0, None, None) == 1
+    L.tg_assemble_facets.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, vp, C.c_int32, vp, vp, vp]
+    assert L.tg_assemble_facets(None, 0, None, None, 3, None, 3, None, None, None) == 1
+    L.tg_assemble_simp.argtypes = [vp, C.c_int32, vp, vp] + [C.c_double] * 4 + [vp, vp]
+    assert L.tg_assemble_simp(None, 0, None, None, 1.0, 2.0, 3.0, 0.3, None, None) == 1
+    L.tg_simp_sensitivity.argtypes = [vp, C.c_int32, vp, vp] + [C.c_double] * 4 + [vp, vp, vp]
+    assert L.tg_simp_sensitivity(None, 0, None, None, 1.0, 2.0, 3.0, 0.3, None, None, None) == 1
+    L.tg_quadrature.argtypes = [C.c_int32, vp, vp]
+    assert L.tg_quadrature(4, None, None) == 4   # the 2 x 2 Gauss rule of the quadrilateral
+    assert L.tg_quadrature(5, None, None) == 0
 
 
 def test_python_binding_imports_without_gpu():
