@@ -311,7 +311,8 @@ tg_status tg_csr_outer(const tg_pattern* p, tg_dtype dtype, const void* lam, con
  * Stops when ||F_I - K_II x_I|| <= rtol ||F_I|| or after maxit iterations.
  * iters / relres are HOST outputs (may be NULL).  SYNCHRONISES the stream
  * (the residual is checked on the host every 8 iterations).  Allocates and
- * frees its work vectors. */
+ * frees its work vectors; runs each 8 iterations as one launch of a CUDA
+ * graph captured for the call (the same kernels in the same order). */
 tg_status tg_cg_solve(const tg_pattern* p, tg_dtype dtype, const void* vals, const void* F,
                       const uint8_t* dirichlet, void* x, double rtol, int32_t maxit, int32_t* iters,
                       double* relres, tg_stream stream);

@@ -131,9 +131,24 @@ struct CgWork {
   int nb;
 };
 
+// Eight CG iterations captured once as a CUDA graph: the small systems of
+// the solve are launch-bound, and one graph launch replaces 64 kernel
+// launches.  The graph runs the same kernels in the same order, so the
+// iterates are bitwise those of the plain loop.
+struct CgGraph {
+  cudaStream_t cs = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~CgGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+
 template <typename T>
 tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8_t* mask, void* x_, double rtol,
-             int maxit, int* iters, double* relres, const CgWork<T>& w, cudaStream_t s) {
+             int maxit, int* iters, double* relres, const CgWork<T>& w, cudaStream_t s, bool use_graph) {
   const int nc = tg::ncomp_of(p->el);
   const bool vec = nc > 1;
   const int64_t n = nc * p->N;
@@ -157,16 +172,39 @@ tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8
   TG_CK(cudaStreamSynchronize(s));
   const double fnorm = std::sqrt(h[3]);
   double rel = fnorm > 0 ? std::sqrt(h[0]) / fnorm : 0.0;
-  int it = 0;
-  while (fnorm > 0 && rel > rtol && it < maxit) {
-    k_spmv<T><<<gs, ST, 0, s>>>(rp, ci, vals, pp, Ap, n, mask);
-    if ((st = dot<T>(pp, Ap, n, partials, nb, sc + 1, s)) != TG_OK) return st;
-    k_cg_xr<T><<<gv, ST, 0, s>>>(x, r, pp, Ap, sc, n);
-    if ((st = dot<T>(r, r, n, partials, nb, sc + 2, s)) != TG_OK) return st;
-    k_cg_p<T><<<gv, ST, 0, s>>>(pp, r, sc, n);
-    k_cg_shift<<<1, 1, 0, s>>>(sc);
+  auto iteration = [&](cudaStream_t q) -> tg_status {
+    k_spmv<T><<<gs, ST, 0, q>>>(rp, ci, vals, pp, Ap, n, mask);
+    tg_status e;
+    if ((e = dot<T>(pp, Ap, n, partials, nb, sc + 1, q)) != TG_OK) return e;
+    k_cg_xr<T><<<gv, ST, 0, q>>>(x, r, pp, Ap, sc, n);
+    if ((e = dot<T>(r, r, n, partials, nb, sc + 2, q)) != TG_OK) return e;
+    k_cg_p<T><<<gv, ST, 0, q>>>(pp, r, sc, n);
+    k_cg_shift<<<1, 1, 0, q>>>(sc);
     TG_CK_LAUNCH("cg iteration");
-    ++it;
+    return TG_OK;
+  };
+  int it = 0;
+  CgGraph g;
+  if (use_graph && fnorm > 0 && rel > rtol && maxit >= 8) {
+    TG_CK(cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking));
+    TG_CK(cudaStreamBeginCapture(g.cs, cudaStreamCaptureModeThreadLocal));
+    tg_status e = TG_OK;
+    for (int k = 0; k < 8 && e == TG_OK; ++k) e = iteration(g.cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(g.cs, &graph);
+    g.graph = graph;
+    if (e != TG_OK) return e;
+    TG_CK(ce);
+    TG_CK(cudaGraphInstantiate(&g.exec, g.graph, 0));
+  }
+  while (fnorm > 0 && rel > rtol && it < maxit) {
+    if (g.exec && it + 8 <= maxit) {
+      TG_CK(cudaGraphLaunch(g.exec, s));
+      it += 8;
+    } else {
+      if ((st = iteration(s)) != TG_OK) return st;
+      ++it;
+    }
     if ((it & 7) == 0 || it == maxit) {
       TG_CK(cudaMemcpyAsync(h, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
       TG_CK(cudaStreamSynchronize(s));
@@ -194,7 +232,7 @@ tg_status cg_alloc(const tg_pattern* p, const void* vals, const void* F, const u
   TG_CK(d.alloc((void**)&w.b, n * sizeof(T)));
   TG_CK(d.alloc((void**)&w.sc, 4 * sizeof(double)));
   TG_CK(d.alloc((void**)&w.partials, w.nb * sizeof(double)));
-  return cg<T>(p, vals, F, mask, x, rtol, maxit, iters, relres, w, s);
+  return cg<T>(p, vals, F, mask, x, rtol, maxit, iters, relres, w, s, true);
 }
 
 // ---------------------------------------------------------------- no-alloc form
@@ -263,7 +301,8 @@ tg_status cg_noalloc(const tg_pattern* p, const void* vals, const void* F, const
   // The scalars start at zero so that nothing of an earlier call can be read
   // back; the vectors and partials are fully written before they are read.
   TG_CK(cudaMemsetAsync(w.sc, 0, 4 * sizeof(double), s));
-  return cg<T>(p, vals, F, mask, x, rtol, maxit, iters, relres, w, s);
+  // no graph here: instantiating one may allocate
+  return cg<T>(p, vals, F, mask, x, rtol, maxit, iters, relres, w, s, false);
 }
 
 // out[s] = alpha * lam[row(s)] * U[col(s)]: the adjoint outer product
