@@ -314,7 +314,7 @@ def main():
         if ev:
             ev[2].record()
 
-    launches_per_step = 3  # system (K and F), backward, backward final sum
+    launches_per_step = 2  # system (K and F in one kernel), backward (its global sums finish in-kernel)
     for _ in range(max(args.warmup, 3)):
         flush()
         step()
