@@ -368,10 +368,8 @@ std::string cache_key(const tg_batch* b, tg_dtype dtype) {
   cudaGetDeviceProperties(&prop, b->device);
   int bucket = 0;
   for (int64_t r = b->total_rows; r > 1; r >>= 1) ++bucket;
-  char buf[256];
-  std::snprintf(buf, sizeof(buf), "%s|el%d|dt%d|rows2^%d|inst%d|blk%d", prop.name, (int)b->el, (int)dtype, bucket,
-                b->n_inst, b->blk ? 1 : 0);
-  return buf;
+  return std::string(prop.name) + "|el" + std::to_string((int)b->el) + "|dt" + std::to_string((int)dtype) +
+         "|rows2^" + std::to_string(bucket) + "|inst" + std::to_string(b->n_inst) + "|blk" + (b->blk ? "1" : "0");
 }
 
 }  // namespace

@@ -253,7 +253,7 @@ __device__ __forceinline__ bool bel_owner(uint32_t w) { return (w >> 31) != 0u; 
 #define TG_BLK_PIPELINE_BEGIN(pipe, g, status)                                          \
   const int64_t G_ = gridDim.x;                                                         \
   const int R_ = (g).R;                                                                 \
-  const int NT_ = blockDim.x;                                                           \
+  [[maybe_unused]] const int NT_ = blockDim.x;                                          \
   int64_t b_ = blockIdx.x;                                                              \
   tg::BlkPipe::Peek nq_;                                                                \
   if (threadIdx.x == 0 && b_ < (g).nblocks) {                                           \

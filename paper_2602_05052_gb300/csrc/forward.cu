@@ -98,7 +98,7 @@ size_t bilinear_blk_smem(const tg_pattern* p) {
 template <int D, typename T, int UB>
 __global__ void __launch_bounds__(BT) k_load_blk(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
                                                  const tg::BlkArgs g) {
-  constexpr int NV = D + 1, NQ = D == 2 ? 3 : 4;
+  constexpr int NV = D + 1;
   extern __shared__ __align__(16) unsigned char smem[];
   const tg::RefTab<T>& ts = tab;
   tg::BlkPipe pipe;

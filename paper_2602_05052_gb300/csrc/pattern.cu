@@ -739,7 +739,6 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   TG_CK(tmp.alloc(&row_len, N));
   TG_CK(tmp.alloc(&maxes, 2));
   TG_CK(cudaMemsetAsync(maxes, 0, 2 * sizeof(int), s));
-  const bool vec3 = el == TG_P1_TET_VEC3;
   const int nc = tg::ncomp_of(el);
   k_rows<false><<<tg::grid_for(N, 128), 128, 0, s>>>(p->cells, p->inc_ptr, p->inc_e, N, nv, p->npw, nc, row_len,
                                                       maxes, nullptr, nullptr, nullptr, nullptr, p->status);
