@@ -248,6 +248,15 @@ tg_status tg_semilinear_residual(const tg_pattern* p, tg_dtype dtype, const void
                                  const double* reaction, const void* x_react, const uint8_t* dirichlet, void* y,
                                  void* loss, tg_stream stream);
 
+/* r(u_q) at the quadrature points of every element, out [E][Q] (the
+ * element's rule), u_q = sum_b phi_b(x_q) x[g(b)], r as in
+ * tg_semilinear_residual.  As the per-point load f of
+ * tg_assemble_load_backward (grad_F = the upstream gradient of y) it gives
+ * the reaction term's coordinate gradient: only |det J| depends on the
+ * coordinates. */
+tg_status tg_reaction_points(const tg_pattern* p, tg_dtype dtype, const void* x, const double* reaction, void* out,
+                             tg_stream stream);
+
 /* ------------------------------------------------------------------------
  * Backward (reverse mode) of the scalar bilinear assembly.
  * For an upstream gradient W of the assembled values, either

@@ -19,8 +19,8 @@ is the adjoint solve of Eq. (adj).
   matrix-free call; K is symmetric), dL/dkappa and dL/dcoords from the fused
   adjoint backward with lam = g, U = x, and dL/df from the load backward
   with grad_F = -g.  With ``reaction`` (the four coefficients of r(u)) y
-  gains the semilinear term N(x) and dL/dx gains J(x) g (coordinate
-  gradients of that term are not built).
+  gains the semilinear term N(x), dL/dx gains J(x) g, and dL/dcoords the
+  reaction's |det J| term (a per-point load of r(u_q), load backward).
 """
 from __future__ import annotations
 
@@ -132,8 +132,6 @@ class _Residual(torch.autograd.Function):
             g = g.masked_fill(ctx.dirichlet.bool(), 0.0)
         need_x, need_k, need_f = ctx.needs_input_grad[2], ctx.needs_input_grad[1], ctx.needs_input_grad[3]
         need_c = ctx.needs_input_grad[0]
-        if need_c and ctx.reaction is not None:
-            raise NotImplementedError("coordinate gradients of the reaction term are not built")
         gx_in = None
         if need_x and ctx.reaction is None:
             gx_in = B.tg_residual(p, coords, kappa, ctx.layout, ctx.c, g, loss=False)[0]
@@ -150,6 +148,10 @@ class _Residual(torch.autograd.Function):
             gf, _ = B.tg_assemble_load_backward(p, coords, f, ctx.f_layout, 1, -g,
                                                 grad_f=torch.zeros_like(f) if need_f else False,
                                                 grad_coords=gc if need_c else False, accumulate=True)
+        if need_c and ctx.reaction is not None:
+            # the reaction term's |det J| scaling: a per-point load of r(u_q) with upstream gradient +g
+            rq = B.tg_reaction_points(p, x, ctx.reaction)
+            B.tg_assemble_load_backward(p, coords, rq, B.PER_QP, 1, g, grad_f=False, grad_coords=gc, accumulate=True)
         return gc, gk, gx_in, gf, None, None, None, None, None, None
 
 

@@ -69,6 +69,7 @@ def lib():
                                          vp]),
         "tg_assemble_simp": (i32, [vp, i32, vp, vp, dbl, dbl, dbl, dbl, vp, vp]),
         "tg_simp_sensitivity": (i32, [vp, i32, vp, vp, dbl, dbl, dbl, dbl, vp, vp, vp]),
+        "tg_reaction_points": (i32, [vp, i32, vp, C.POINTER(dbl), vp, vp]),
         "tg_build_facets": (i32, [vp, vp, i64, vp, C.POINTER(vp)]),
         "tg_assemble_facets": (i32, [vp, i32, vp, vp, i32, vp, i32, vp, vp, vp]),
         "tg_facets_shape": (i32, [vp, C.POINTER(i64), C.POINTER(i64)]),
@@ -359,6 +360,16 @@ def tg_simp_sensitivity(p: Pattern, coords, rho, e_min: float, e_max: float, pen
                                      float(nu), _ptr(u, coords.dtype, "u"), _ptr(dc_out, coords.dtype, "dc"),
                                      _stream(stream)), "tg_simp_sensitivity")
     return dc_out
+
+
+def tg_reaction_points(p: Pattern, x, reaction, out=None, stream=None):
+    """r(u_q) at the quadrature points of every element: [E * Q]."""
+    if out is None:
+        out = torch.empty(p.n_elems * NQ[p.el], dtype=x.dtype, device=x.device)
+    r = (dbl * 4)(*[float(v) for v in reaction])
+    _check(lib().tg_reaction_points(p.handle, _dt(x), _ptr(x, x.dtype, "x"), r, _ptr(out, x.dtype, "out"),
+                                    _stream(stream)), "tg_reaction_points")
+    return out
 
 
 class Facets:

@@ -363,6 +363,49 @@ tg_status launch_el(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t s) {
   return TG_OK;
 }
 
+// r(u_q) at every quadrature point of every element, u_q = sum_b phi_b(x_q)
+// x_b: the same interpolation and Horner evaluation as reaction_rows.  With
+// these values as a per-point load, the load backward gives the reaction
+// term's coordinate gradient (only |det J| depends on the coordinates).
+template <int EL, typename T>
+__global__ void __launch_bounds__(RT) k_reaction_points(const int32_t* __restrict__ cells, const T* __restrict__ x,
+                                                       const __grid_constant__ tg::RefTab<T> tab, T r0, T r1, T r2,
+                                                       T r3, int64_t E, T* __restrict__ out) {
+  constexpr int NV = tg::Elem<EL>::nv, NQ = tg::Elem<EL>::nq;
+  const int64_t e = (int64_t)blockIdx.x * RT + threadIdx.x;
+  if (e >= E) return;
+  T xv[NV];
+#pragma unroll
+  for (int b = 0; b < NV; ++b) xv[b] = __ldg(x + __ldg(cells + e * NV + b));
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    T u = T(0);
+#pragma unroll
+    for (int b = 0; b < NV; ++b) u = fma(tab.phi[q][b], xv[b], u);
+    out[e * NQ + q] = fma(fma(fma(r3, u, r2), u, r1), u, r0);
+  }
+}
+
+template <typename T>
+tg_status reaction_points(const tg_pattern* p, const void* x, const double* rc, void* out, cudaStream_t s) {
+  const unsigned grid = (unsigned)tg::grid_for(p->E, RT);
+  const T r0 = (T)rc[0], r1 = (T)rc[1], r2 = (T)rc[2], r3 = (T)rc[3];
+  const T* xx = static_cast<const T*>(x);
+  T* o = static_cast<T*>(out);
+  switch (p->el) {
+    case TG_P1_TRI:
+      k_reaction_points<TG_P1_TRI, T><<<grid, RT, 0, s>>>(p->cells, xx, tg::table<T>(TG_P1_TRI), r0, r1, r2, r3, p->E, o);
+      break;
+    case TG_P2_TRI:
+      k_reaction_points<TG_P2_TRI, T><<<grid, RT, 0, s>>>(p->cells, xx, tg::table<T>(TG_P2_TRI), r0, r1, r2, r3, p->E, o);
+      break;
+    default:
+      k_reaction_points<TG_P1_TET, T><<<grid, RT, 0, s>>>(p->cells, xx, tg::table<T>(TG_P1_TET), r0, r1, r2, r3, p->E, o);
+  }
+  TG_CK_LAUNCH("k_reaction_points");
+  return TG_OK;
+}
+
 template <typename T, int NL>
 tg_status dispatch(const tg_pattern* p, const ResArgs<T>& r, bool lf, cudaStream_t s) {
   switch (p->el) {
@@ -450,6 +493,15 @@ tg_status tg_residual(const tg_pattern* p, tg_dtype dtype, const void* coords, c
                       tg_layout kappa_layout, double c, const void* x, const void* f, tg_layout f_layout,
                       const uint8_t* dirichlet, void* y, void* loss, tg_stream stream) {
   return entry(p, dtype, coords, kappa, kappa_layout, c, x, f, f_layout, nullptr, nullptr, dirichlet, y, loss, stream);
+}
+
+tg_status tg_reaction_points(const tg_pattern* p, tg_dtype dtype, const void* x, const double* reaction, void* out,
+                             tg_stream stream) {
+  if (!p || (dtype != TG_F32 && dtype != TG_F64) || !tg::scalar_kind(p->el) || !reaction) return TG_ERR_INVALID_ARG;
+  if (p->E == 0) return TG_OK;
+  if (!x || !out) return TG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  return dtype == TG_F32 ? reaction_points<float>(p, x, reaction, out, s) : reaction_points<double>(p, x, reaction, out, s);
 }
 
 tg_status tg_semilinear_residual(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,

@@ -45,6 +45,20 @@ def test_semilinear_matches_oracle(tg, el, jac, dtype):
     assert tg.tg_get_device_status(p) == (0, -1)
 
 
+@pytest.mark.parametrize("el", [mg.P1_TRI, mg.P2_TRI, mg.P1_TET])
+def test_reaction_points_match_oracle_interpolation(tg, el):
+    m = mesh_for(el)
+    x = np.random.default_rng(104).uniform(-1, 1, m.n_nodes)
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, el)
+    rq = tg.tg_reaction_points(p, dev(x, torch.float64), R).cpu().numpy().reshape(m.n_elems, -1)
+    w, xq = O.quadrature(el)
+    for q in range(len(w)):
+        phi, _ = O.basis(el, xq[q])
+        u = sum(phi[b] * x[m.cells[:, b]] for b in range(m.cells.shape[1]))
+        want = R[0] + R[1] * u + R[2] * u ** 2 + R[3] * u ** 3
+        assert np.allclose(rq[:, q], want, rtol=1e-13, atol=1e-14)
+
+
 def test_semilinear_without_row_blocks_equals_blocks(tg):
     m = jittered_tri(300)
     g = np.random.default_rng(101)
@@ -78,9 +92,11 @@ def test_semilinear_reverse_mode(tg):
     f = dev(g.uniform(-1, 1, m.n_nodes), torch.float64).requires_grad_(True)
     fn = lambda k_, x_, f_: A.residual(p, coords, k_, mg.PER_QP, 0.3, x_, f_, mg.PER_NODE, mask, reaction=R)
     assert torch.autograd.gradcheck(fn, (k, x, f), eps=1e-6, atol=1e-8)
-    with pytest.raises(NotImplementedError):
-        c2 = coords.clone().requires_grad_(True)
-        A.residual(p, c2, k, mg.PER_QP, 0.3, x, f, mg.PER_NODE, mask, reaction=R).sum().backward()
+    # coordinates too (the reaction's |det J| term through the per-point load backward)
+    c2 = coords.clone().requires_grad_(True)
+    fc = lambda c_: A.residual(p, c_, k.detach(), mg.PER_QP, 0.3, x.detach(), f.detach(), mg.PER_NODE, mask,
+                               reaction=R)
+    assert torch.autograd.gradcheck(fc, (c2,), eps=1e-6, atol=1e-8)
 
 
 def test_allen_cahn_step_residual(tg):
