@@ -232,3 +232,24 @@ def test_elasticity_backward_central_differences(tg):
         fd = (L(x + eps * dx, l + eps * dl, u + eps * du) - L(x - eps * dx, l - eps * dl, u - eps * du)) / (2 * eps)
         an = float((gx * dx).sum() + (gl * dl).sum() + (gm * du).sum())
         assert abs(fd - an) <= 1e-7 * max(1.0, abs(an)), (k, fd, an)
+
+
+def test_backward_diffusion2d_full_size(tg):
+    """The benchmark's backward on the 1024^2 workload in FP32 (the launch
+    configuration bench.py times) against the oracle's analytic gradients
+    of every element and node."""
+    cfg = mg.diffusion2d(1024)
+    m = cfg["mesh"]
+    dtype = torch.float32
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
+    xs, ks = host_as(m.coords, dtype), host_as(cfg["kappa"], dtype)
+    gv = host_as(np.random.default_rng(1).normal(size=p.nnz), dtype)
+    gk, gx, gc = tg.tg_assemble_backward(p, dev(m.coords, dtype), dev(cfg["kappa"], dtype), mg.PER_QP, cfg["c"],
+                                         grad_vals=dev(gv, dtype))
+    ref = O.assemble_bilinear(mg.P1_TRI, m.cells, xs, ks, O.PER_QP, cfg["c"])
+    rk, rx, rc = O.assemble_backward(mg.P1_TRI, m.cells, xs, ks, O.PER_QP, cfg["c"],
+                                     grad_csr=O.CSR(ref.row_ptr, ref.col, gv))
+    assert relfro(gk.cpu().numpy().ravel(), rk) <= GTOL[dtype]
+    assert relfro(gx.cpu().numpy(), rx) <= GTOL[dtype]
+    assert relfro(gc.cpu().numpy(), [rc]) <= GTOL[dtype]
+    assert tg.tg_get_device_status(p) == (0, -1)
