@@ -625,13 +625,16 @@ def residual_extras(tg, torch, dev, m, cfg, p, peak, flush):
         ms_ac = timed(torch, ac, flush)
         acj = lambda: tg.tg_semilinear_residual(p, X, a2, tg.CONSTANT, 1e3, g, r, x_react=x, y=gx_in, loss=False)
         ms_acj = timed(torch, acj, flush)
+        ba = E * 3 * 4 + N * 2 * s + 3 * N * s + N  # cells, coords, x, U0 / dt, y, mask (constant a^2)
         out[f"allen_cahn2d_{dtn}"] = {"step_residual_us": ms_ac * 1e3, "jacobian_action_us": ms_acj * 1e3,
-                                      "elements_per_s": E / ms_ac * 1e3,
+                                      "elements_per_s": E / ms_ac * 1e3, "alg_GBps": ba / ms_ac / 1e6,
+                                      "frac_hbm": ba / ms_ac / 1e6 / peak,
                                       "note": "one launch each; constant a^2, nodal U0 / dt, mask and loss"}
     return out
 
 
 def facet_extras(tg, torch, dev, m, p, flush):
+    # (the boundary is 0.4% of the nodes: a latency-bound launch, reported in microseconds)
     """Robin matrix term and Neumann/Robin load on the 4,096 boundary edges
     of the 1024^2 workload, added onto assembled values (one launch)."""
     fac = mg.boundary_facets(m)
@@ -644,7 +647,13 @@ def facet_extras(tg, torch, dev, m, p, flush):
         v = torch.zeros(p.nnz, dtype=dt, device=dev)
         F = torch.zeros(m.n_nodes, dtype=dt, device=dev)
         ms = timed(torch, lambda: tg.tg_assemble_facets(fc, X, al, tg.PER_QP, g, tg.PER_NODE, v, F), flush)
+        es = 4 if dt == torch.float32 else 8
+        # facet ids, their nodes' coordinates and g, alpha per point, and a read-modify-write of the touched
+        # CSR entries (3 per boundary node) and of F
+        fb = len(fac) * 2 * 4 + fc.n_boundary_nodes * (2 * es + es) + len(fac) * 2 * es \
+            + fc.n_boundary_nodes * 4 * es * 2
         out[f"facets2d_{dtn}"] = {"facets": len(fac), "boundary_nodes": fc.n_boundary_nodes, "us": ms * 1e3,
+                                  "alg_GBps": fb / ms / 1e6,
                                   "note": "Robin alpha per facet point and nodal g, added into CSR values and F"}
     return out
 
