@@ -470,6 +470,14 @@ tg_status tg_simp_sensitivity(const tg_pattern* p, tg_dtype dtype, const void* c
  * GPU, in FLOP/s (2 per FMA), written to *flops (host).  SYNCHRONISES. */
 tg_status tg_diag_fma_rate(tg_dtype dtype, double* flops, tg_stream stream);
 
+/* Failure-path check (no counterpart in the paper): one CTA waits, bounded
+ * by max_tries polls (1 .. 2^22), on a shared-memory barrier that nothing
+ * completes, exactly as the pipelined kernels wait for their bulk copies;
+ * the wait gives up and records TG_ERR_TIMEOUT in p's device status, which
+ * tg_get_device_status then returns (and clears).  Nothing hangs or
+ * faults. */
+tg_status tg_diag_wait_timeout(const tg_pattern* p, int32_t max_tries, tg_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

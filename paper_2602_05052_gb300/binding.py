@@ -70,6 +70,7 @@ def lib():
         "tg_assemble_simp": (i32, [vp, i32, vp, vp, dbl, dbl, dbl, dbl, vp, vp]),
         "tg_simp_sensitivity": (i32, [vp, i32, vp, vp, dbl, dbl, dbl, dbl, vp, vp, vp]),
         "tg_reaction_points": (i32, [vp, i32, vp, C.POINTER(dbl), vp, vp]),
+        "tg_diag_wait_timeout": (i32, [vp, i32, vp]),
         "tg_build_facets": (i32, [vp, vp, i64, vp, C.POINTER(vp)]),
         "tg_assemble_facets": (i32, [vp, i32, vp, vp, i32, vp, i32, vp, vp, vp]),
         "tg_facets_shape": (i32, [vp, C.POINTER(i64), C.POINTER(i64)]),
@@ -370,6 +371,10 @@ def tg_reaction_points(p: Pattern, x, reaction, out=None, stream=None):
     _check(lib().tg_reaction_points(p.handle, _dt(x), _ptr(x, x.dtype, "x"), r, _ptr(out, x.dtype, "out"),
                                     _stream(stream)), "tg_reaction_points")
     return out
+
+
+def tg_diag_wait_timeout(p: Pattern, max_tries: int = 1000, stream=None):
+    _check(lib().tg_diag_wait_timeout(p.handle, int(max_tries), _stream(stream)), "tg_diag_wait_timeout")
 
 
 class Facets:

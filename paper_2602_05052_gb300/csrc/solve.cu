@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "async.cuh"
 #include "tg_internal.cuh"
 
 namespace {
@@ -398,6 +399,35 @@ tg_status tg_csr_outer(const tg_pattern* p, tg_dtype dtype, const void* lam, con
   else
     k_csr_outer<double><<<g, ST, 0, s>>>(rp, ci, (const double*)lam, (const double*)U, alpha, (double*)out, n);
   TG_CK_LAUNCH("k_csr_outer");
+  return TG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The bounded wait of the pipelined kernels on a shared-memory barrier that
+// nothing completes (no arrival, no copy): the wait gives up after max_tries
+// polls and records TG_ERR_TIMEOUT in the status word, as the kernels do.
+__global__ void k_diag_wait_timeout(unsigned long long* status, uint32_t max_tries) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tg::mbar_init(&bar, 1);
+    tg::fence_mbar_init();
+  }
+  __syncthreads();
+  const bool ok = tg::mbar_wait(&bar, 0, max_tries);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) tg::record_error(status, TG_ERR_TIMEOUT, 0);
+}
+
+}  // namespace
+
+extern "C" {
+
+tg_status tg_diag_wait_timeout(const tg_pattern* p, int32_t max_tries, tg_stream stream) {
+  if (!p || max_tries < 1 || max_tries > (1 << 22)) return TG_ERR_INVALID_ARG;
+  k_diag_wait_timeout<<<1, 32, 0, (cudaStream_t)stream>>>(p->status, (uint32_t)max_tries);
+  TG_CK_LAUNCH("k_diag_wait_timeout");
   return TG_OK;
 }
 
