@@ -728,8 +728,8 @@ __global__ void __launch_bounds__(BB) k_backward_node(const BwdArgs<T> a, const 
 }
 
 // ------------------------------------------------------------ elasticity
-// Backward of the vector P1 elasticity assembly over element-once row
-// blocks.  With G = grad(phi) (G[:, a] = n_a / det J) and the upstream
+// Backward of the vector P1 elasticity assembly, in two passes (each
+// element evaluated once, then a per-node sum).  With G = grad(phi) (G[:, a] = n_a / det J) and the upstream
 // weights W of one element (12 x 12, DoF (a, i) = 3a + i), the element's
 //   L_e = |det J| (sl T1 + sm (T2 + T3)),  sl = sum_q w_q lam_q, sm likewise,
 //   T1 = sum W_{ai,bj} G_ia G_jb,  T2 = sum W_{ai,bj} G_ja G_ib,
@@ -755,190 +755,229 @@ struct ElBwdArgs {
   unsigned long long* status;
 };
 
-template <typename T, bool FUSED>
-__global__ void __launch_bounds__(BB) k_elastic_backward_blk(const ElBwdArgs<T> a,
-                                                             const __grid_constant__ tg::RefTab<T> tab,
-                                                             const tg::BlkArgs g, const uint64_t* __restrict__ elem_pos,
-                                                             const int32_t* __restrict__ row_ptr) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  tg::BlkPipe pipe;
-  T* Gx = reinterpret_cast<T*>(pipe.init(smem, g));  // [12][capE]
-  __syncthreads();
-  TG_BLK_PIPELINE_BEGIN(pipe, g, a.status)
-  for (int j = threadIdx.x; j < v.nbe; j += NT_) {
-    const uint32_t w0 = v.be[j];
-    const int e = (int)tg::bel_elem(w0);
-    const bool own = tg::bel_owner(w0);
-    int vid[4];
-    T x[4][3];
+// The contractions of one element's upstream blocks with G: T1, T2, T3 and
+// their derivatives dT/dG (d1, d2, d3, zero on entry).  wblk(p, q, w)
+// yields the 3 x 3 block of vertex pair (p, q).
+template <typename T, typename WBlk>
+__device__ __forceinline__ void el_bwd_sums(const T (&G)[3][4], WBlk wblk, T& t1, T& t2, T& t3, T (&d1)[3][4],
+                                            T (&d2)[3][4], T (&d3)[3][4]) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      vid[c] = v.vtx(c, j);
-      tg::load_x<3, T>(a.coords, vid[c], x[c]);
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      T w[3][3];
+      wblk(p, q, w);
+      // w G_q, w^T G_q, w G_p, w^T G_p
+      T wGq[3], wtGq[3], wGp[3], wtGp[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        wGq[i] = w[i][0] * G[0][q] + w[i][1] * G[1][q] + w[i][2] * G[2][q];
+        wtGq[i] = w[0][i] * G[0][q] + w[1][i] * G[1][q] + w[2][i] * G[2][q];
+        wGp[i] = w[i][0] * G[0][p] + w[i][1] * G[1][p] + w[i][2] * G[2][p];
+        wtGp[i] = w[0][i] * G[0][p] + w[1][i] * G[1][p] + w[2][i] * G[2][p];
+      }
+      const T cpq = w[0][0] + w[1][1] + w[2][2];
+      const T gpq = G[0][p] * G[0][q] + G[1][p] * G[1][q] + G[2][p] * G[2][q];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        t1 += G[i][p] * wGq[i];
+        t2 += G[i][q] * wGp[i];
+        d1[i][p] += wGq[i];
+        d1[i][q] += wtGp[i];
+        d2[i][p] += wtGq[i];
+        d2[i][q] += wGp[i];
+        d3[i][p] += cpq * G[i][q];
+        d3[i][q] += cpq * G[i][p];
+      }
+      t3 += cpq * gpq;
     }
-    T lq[4], mq[4];
-    if (a.layout == TG_PER_QP) {
+}
+
+// dL/dx_c = P G[:, c] of one element from the sums of el_bwd_sums.
+template <typename T>
+__device__ __forceinline__ void el_bwd_gx(const T (&G)[3][4], T adet, T sl, T sm, T t1, T t2, T t3,
+                                          const T (&d1)[3][4], const T (&d2)[3][4], const T (&d3)[3][4],
+                                          T (&gx)[4][3]) {
+  const T Le = adet * (sl * t1 + sm * (t2 + t3));
+  T P[3][3];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        lq[q] = __ldg(a.lam + 4ll * e + q);
-        mq[q] = __ldg(a.mu + 4ll * e + q);
-      }
-    } else {
-      const T l0 = __ldg(a.lam + e), m0 = __ldg(a.mu + e);
+  for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        lq[q] = l0;
-        mq[q] = m0;
-      }
+    for (int s2 = 0; s2 < 3; ++s2) {
+      T acc = T(0);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc += G[r][c] * (adet * (sl * d1[s2][c] + sm * (d2[s2][c] + d3[s2][c])));
+      P[r][s2] = (r == s2 ? Le : T(0)) - acc;
     }
-    tg::Geom<3, T> gm;
-    tg::tet_geom_x(x[0], x[1], x[2], x[3], gm);
-    const T adet = tg::absv(gm.det);
-    T gx[4][3];
-    if (!(adet > tg::det_tiny<T>())) {
-      tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
-      if (own) {
-        const int nc = a.layout == TG_PER_QP ? 4 : 1;
-        for (int q = 0; q < nc; ++q) {
-          if (a.grad_lam) a.grad_lam[(int64_t)e * nc + q] = T(0);
-          if (a.grad_mu) a.grad_mu[(int64_t)e * nc + q] = T(0);
-        }
-      }
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
+  for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int r = 0; r < 3; ++r) gx[c][r] = T(0);
-    } else {
-      const T id = T(1) / gm.det;
-      T G[3][4];  // G[r][c] = d phi_c / d x_r
+    for (int r = 0; r < 3; ++r) gx[c][r] = P[r][0] * G[0][c] + P[r][1] * G[1][c] + P[r][2] * G[2][c];
+}
+
+// The element's vertices, coordinates and quadrature sums of lam and mu.
+template <typename T>
+__device__ __forceinline__ void el_bwd_coefs(const ElBwdArgs<T>& a, const tg::RefTab<T>& tab, int64_t e, T& sl,
+                                             T& sm) {
+  sl = T(0);
+  sm = T(0);
+  if (a.layout == TG_PER_QP) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int r = 0; r < 3; ++r) G[r][c] = gm.n[c][r] * id;
-      T t1 = T(0), t2 = T(0), t3 = T(0);
-      T d1[3][4], d2[3][4], d3[3][4];
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) d1[r][c] = d2[r][c] = d3[r][c] = T(0);
-      uint64_t ep = 0;
-      int rpa[4] = {0, 0, 0, 0}, lena[4] = {0, 0, 0, 0};
-      T la[4][3], ua[4][3];
-      if constexpr (FUSED) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            la[c][i] = __ldg(a.lam_adj + 3ll * vid[c] + i);
-            ua[c][i] = __ldg(a.U + 3ll * vid[c] + i);
-          }
-      } else {
-        ep = __ldg(reinterpret_cast<const unsigned long long*>(elem_pos) + e);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          rpa[c] = __ldg(row_ptr + vid[c]);
-          lena[c] = __ldg(row_ptr + vid[c] + 1) - rpa[c];
-        }
-      }
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          T w[3][3];
-          if constexpr (FUSED) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-              for (int jj = 0; jj < 3; ++jj) w[i][jj] = la[p][i] * ua[q][jj];
-          } else {
-            const int pos = (int)((ep >> (4 * (p * 4 + q))) & 15u);
-            const T* base = a.gvals + 9ll * rpa[p] + 3ll * pos;
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-              for (int jj = 0; jj < 3; ++jj) w[i][jj] = __ldg(base + 3ll * i * lena[p] + jj);
-          }
-          // w G_q, w^T G_q, w G_p, w^T G_p
-          T wGq[3], wtGq[3], wGp[3], wtGp[3];
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            wGq[i] = w[i][0] * G[0][q] + w[i][1] * G[1][q] + w[i][2] * G[2][q];
-            wtGq[i] = w[0][i] * G[0][q] + w[1][i] * G[1][q] + w[2][i] * G[2][q];
-            wGp[i] = w[i][0] * G[0][p] + w[i][1] * G[1][p] + w[i][2] * G[2][p];
-            wtGp[i] = w[0][i] * G[0][p] + w[1][i] * G[1][p] + w[2][i] * G[2][p];
-          }
-          const T cpq = w[0][0] + w[1][1] + w[2][2];
-          const T gpq = G[0][p] * G[0][q] + G[1][p] * G[1][q] + G[2][p] * G[2][q];
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            t1 += G[i][p] * wGq[i];
-            t2 += G[i][q] * wGp[i];
-            d1[i][p] += wGq[i];
-            d1[i][q] += wtGp[i];
-            d2[i][p] += wtGq[i];
-            d2[i][q] += wGp[i];
-            d3[i][p] += cpq * G[i][q];
-            d3[i][q] += cpq * G[i][p];
-          }
-          t3 += cpq * gpq;
-        }
-      T sl = T(0), sm = T(0);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        sl += tab.w[q] * lq[q];
-        sm += tab.w[q] * mq[q];
-      }
-      if (own) {
-        if (a.layout == TG_PER_QP) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (a.grad_lam) a.grad_lam[4ll * e + q] = tab.w[q] * adet * t1;
-            if (a.grad_mu) a.grad_mu[4ll * e + q] = tab.w[q] * adet * (t2 + t3);
-          }
-        } else {
-          if (a.grad_lam) a.grad_lam[e] = tab.wsum * adet * t1;
-          if (a.grad_mu) a.grad_mu[e] = tab.wsum * adet * (t2 + t3);
-        }
-      }
-      const T Le = adet * (sl * t1 + sm * (t2 + t3));
-      T P[3][3];
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int s2 = 0; s2 < 3; ++s2) {
-          T acc = T(0);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc += G[r][c] * (adet * (sl * d1[s2][c] + sm * (d2[s2][c] + d3[s2][c])));
-          P[r][s2] = (r == s2 ? Le : T(0)) - acc;
-        }
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int r = 0; r < 3; ++r) gx[c][r] = P[r][0] * G[0][c] + P[r][1] * G[1][c] + P[r][2] * G[2][c];
+    for (int q = 0; q < 4; ++q) {
+      sl += tab.w[q] * __ldg(a.lam + 4 * e + q);
+      sm += tab.w[q] * __ldg(a.mu + 4 * e + q);
     }
+  } else {
+    const T l0 = __ldg(a.lam + e), m0 = __ldg(a.mu + e);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      sl += tab.w[q] * l0;
+      sm += tab.w[q] * m0;
+    }
+  }
+}
+
+// dL/dlam and dL/dmu of element e (written by one thread per element).
+template <typename T>
+__device__ __forceinline__ void el_bwd_write_coef(const ElBwdArgs<T>& a, const tg::RefTab<T>& tab, int64_t e,
+                                                  T adet, T t1, T t23) {
+  if (a.layout == TG_PER_QP) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (a.grad_lam) a.grad_lam[4 * e + q] = tab.w[q] * adet * t1;
+      if (a.grad_mu) a.grad_mu[4 * e + q] = tab.w[q] * adet * t23;
+    }
+  } else {
+    if (a.grad_lam) a.grad_lam[e] = tab.wsum * adet * t1;
+    if (a.grad_mu) a.grad_mu[e] = tab.wsum * adet * t23;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void el_bwd_zero_coef(const ElBwdArgs<T>& a, int64_t e) {
+  const int nc = a.layout == TG_PER_QP ? 4 : 1;
+  for (int q = 0; q < nc; ++q) {
+    if (a.grad_lam) a.grad_lam[e * nc + q] = T(0);
+    if (a.grad_mu) a.grad_mu[e * nc + q] = T(0);
+  }
+}
+
+// One element of the elasticity backward: writes dL/dlam, dL/dmu and
+// returns the vertex terms gx.  FUSED: W = lam_adj U^T on the element's DoFs;
+// otherwise the blocks are read from grad_vals at
+// base(p, q) + 3 i len_p + j, base(p, q) = 9 row_ptr[v_p] + 3 pos_pq.
+template <typename T, bool FUSED, typename Base>
+__device__ __forceinline__ void el_bwd_element(const ElBwdArgs<T>& a, const tg::RefTab<T>& tab, int64_t e,
+                                               const int (&vid)[4], const int (&lena)[4], Base base,
+                                               T (&gx)[4][3]) {
+  T x[4][3];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) tg::load_x<3, T>(a.coords, vid[c], x[c]);
+  T sl, sm;
+  el_bwd_coefs<T>(a, tab, e, sl, sm);
+  T la[4][3], ua[4][3];
+  if constexpr (FUSED) {
 #pragma unroll
     for (int c = 0; c < 4; ++c)
 #pragma unroll
-      for (int r = 0; r < 3; ++r) Gx[(c * 3 + r) * g.capE + j] = gx[c][r];
-  }
-  __syncthreads();
-  if (a.grad_coords) {
-    const int i = v.r0 + (int)threadIdx.x;
-    if (i < v.r1) {
-      T gs[3] = {T(0), T(0), T(0)};
-      const int je = v.ip[i + 1];
-      for (int j = v.ip[i]; j < je; ++j) {
-        const auto rr = tg::blk_rec<4>(v.rc, j);
-        const T* gp = Gx + rr.a() * 3 * g.capE + rr.le();
-#pragma unroll
-        for (int r = 0; r < 3; ++r) gs[r] += gp[r * g.capE];
+      for (int i = 0; i < 3; ++i) {
+        la[c][i] = __ldg(a.lam_adj + 3ll * vid[c] + i);
+        ua[c][i] = __ldg(a.U + 3ll * vid[c] + i);
       }
+  }
+  tg::Geom<3, T> gm;
+  tg::tet_geom_x(x[0], x[1], x[2], x[3], gm);
+  const T adet = tg::absv(gm.det);
+  if (!(adet > tg::det_tiny<T>())) {
+    tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
+    el_bwd_zero_coef<T>(a, e);
 #pragma unroll
-      for (int r = 0; r < 3; ++r) a.grad_coords[3ll * v.pm[i] + r] = gs[r];
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) gx[c][r] = T(0);
+    return;
+  }
+  const T id = T(1) / gm.det;
+  T G[3][4];  // G[r][c] = d phi_c / d x_r
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) G[r][c] = gm.n[c][r] * id;
+  T t1 = T(0), t2 = T(0), t3 = T(0);
+  T d1[3][4], d2[3][4], d3[3][4];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) d1[r][c] = d2[r][c] = d3[r][c] = T(0);
+  auto wblk = [&](int p, int q, T (&w)[3][3]) {
+    if constexpr (FUSED) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) w[i][jj] = la[p][i] * ua[q][jj];
+    } else {
+      const T* b = a.gvals + base(p, q);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) w[i][jj] = __ldg(b + 3ll * i * lena[p] + jj);
+    }
+  };
+  el_bwd_sums<T>(G, wblk, t1, t2, t3, d1, d2, d3);
+  el_bwd_write_coef<T>(a, tab, e, adet, t1, t2 + t3);
+  el_bwd_gx<T>(G, adet, sl, sm, t1, t2, t3, d1, d2, d3, gx);
+}
+
+// Pass 1: one thread per element writes dL/dlam, dL/dmu and the element's
+// vertex terms gxe[e][c][r]; pass 2 (k_elastic_backward_node) sums every
+// node's terms in increasing element order.  The blocks of W are found
+// through the slot map (elem_slot[e][p][q] = 9 row_ptr[v_p] + 3 pos_pq).
+// Row blocks would evaluate an element once per block holding one of its
+// vertices, about three times on tetrahedral grids; here the 24 incident
+// tetrahedra of a node cost one pass over an E x 12 scratch instead.
+template <typename T, bool FUSED>
+__global__ void __launch_bounds__(BB) k_elastic_backward_map(const ElBwdArgs<T> a,
+                                                             const __grid_constant__ tg::RefTab<T> tab,
+                                                             const int32_t* __restrict__ cells,
+                                                             const int32_t* __restrict__ elem_slot,
+                                                             const int32_t* __restrict__ row_ptr, int64_t E,
+                                                             T* __restrict__ gxe) {
+  for (int64_t e = (int64_t)blockIdx.x * BB + threadIdx.x; e < E; e += (int64_t)gridDim.x * BB) {
+    int vid[4], lena[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) vid[c] = __ldg(cells + 4 * e + c);
+    if constexpr (!FUSED) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) lena[c] = __ldg(row_ptr + vid[c] + 1) - __ldg(row_ptr + vid[c]);
+    }
+    auto base = [&](int p, int q) { return (int64_t)__ldg(elem_slot + 16 * e + 4 * p + q); };
+    T gx[4][3];
+    el_bwd_element<T, FUSED>(a, tab, e, vid, lena, base, gx);
+    if (gxe) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) gxe[(4 * e + c) * 3 + r] = gx[c][r];
     }
   }
-  __syncthreads();
-  TG_BLK_PIPELINE_END
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BB) k_elastic_backward_node(const int32_t* __restrict__ inc_ptr,
+                                                              const int32_t* __restrict__ inc_e, int64_t N,
+                                                              const T* __restrict__ gxe, T* __restrict__ grad_coords) {
+  const int64_t i = (int64_t)blockIdx.x * BB + threadIdx.x;
+  if (i >= N) return;
+  T gs[3] = {T(0), T(0), T(0)};
+  const int j1 = __ldg(inc_ptr + i + 1);
+  for (int j = __ldg(inc_ptr + i); j < j1; ++j) {
+    const int ea = __ldg(inc_e + j);
+    const T* gp = gxe + ((int64_t)(ea >> 3) * 4 + (ea & 7)) * 3;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) gs[r] += gp[r];
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) grad_coords[3 * i + r] = gs[r];
 }
 
 // Sum the per-CTA partials (kSlots doubles per CTA) in a fixed order and
@@ -1073,9 +1112,12 @@ tg_status launch(const tg_pattern* p, const BwdArgs<T>& a, bool fused, T* grad_c
     ab.arrivals = p->arrivals;
     ab.sum_out[0] = grad_c;
     ab.sum_out[1] = (a.layout == TG_CONSTANT) ? a.grad_kappa : nullptr;
-    // FP32 runs on the row blocks; FP64 is bound by the FP64 pipe and takes
-    // the two passes, which evaluate each element once instead of 1.2 times
-    if constexpr (sizeof(T) == 8) {
+    // Two passes evaluate each element once, row blocks once per block
+    // holding one of its vertices: 1.2 times on the Hilbert-ordered
+    // triangles, where FP32 runs on the row blocks, about 3 times on
+    // tetrahedral grids.  FP64 is bound by the FP64 pipe and always takes
+    // the two passes.
+    if constexpr (sizeof(T) == 8 || EL == TG_P1_TET) {
       if (p->elem_scratch && p->elem_pos && p->E > 0) return launch_two_pass<tg::Elem<EL>::dim, T>(p, ab, fused, s);
     }
     tg_status st = launch_blk<tg::Elem<EL>::dim, T>(p, ab, fused, &grid, &used, s);
@@ -1427,11 +1469,10 @@ extern "C" tg_status tg_assemble_elasticity_backward(const tg_pattern* p, tg_dty
     return TG_OK;
   }
   if (!grad_lam && !grad_mu && !grad_coords) return TG_OK;
-  if (!p->bel || !p->elem_pos) {
-    tg::set_error("tg_assemble_elasticity_backward: the mesh has node rows longer than 16");
+  if (!p->elem_scratch) {
+    tg::set_error("tg_assemble_elasticity_backward: the pattern has no element scratch");
     return TG_ERR_UNSUPPORTED;
   }
-  const tg::BlkArgs g = tg::blk_args(p);
   auto run = [&](auto zero) -> tg_status {
     using T = decltype(zero);
     ElBwdArgs<T> a;
@@ -1446,36 +1487,19 @@ extern "C" tg_status tg_assemble_elasticity_backward(const tg_pattern* p, tg_dty
     a.grad_mu = static_cast<T*>(grad_mu);
     a.grad_coords = static_cast<T*>(grad_coords);
     a.status = p->status;
-    const size_t smem = tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE, 4) + (size_t)12 * g.capE * sizeof(T);
-    if (smem > 200 * 1024 || p->blk_rows > BB) {
-      tg::set_error("tg_assemble_elasticity_backward: row blocks too large for shared memory");
-      return TG_ERR_UNSUPPORTED;
-    }
     const tg::RefTab<T>& tab = tg::table<T>(TG_P1_TET);
-    tg_status st = TG_OK;
-    auto go = [&](auto kern) {
-      if ((st = tg::set_smem((const void*)kern, smem)) != TG_OK) return;
-      // The W gathers of neighbouring elements hit in L1: prefer a shared
-      // memory carveout of 3/4, leaving L1 room (measured: about 1.9x
-      // faster than the largest carveout on the 64^3 workload).
-      cudaError_t ce = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 75);
-      if (ce != cudaSuccess) {
-        st = tg::cuda_fail(ce, "cudaFuncSetAttribute(carveout)", __FILE__, __LINE__);
-        return;
-      }
-      int per_sm = 0;
-      ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BB, smem);
-      if (ce != cudaSuccess) {
-        st = tg::cuda_fail(ce, "cudaOccupancyMaxActiveBlocksPerMultiprocessor", __FILE__, __LINE__);
-        return;
-      }
-      const int grid = (int)std::min<int64_t>(p->n_blk, (int64_t)std::max(per_sm, 1) * tg::sm_count());
-      kern<<<grid, BB, smem, s>>>(a, tab, g, p->elem_pos, p->row_ptr);
-    };
-    if (grad_vals) go(k_elastic_backward_blk<T, false>);
-    else go(k_elastic_backward_blk<T, true>);
-    if (st != TG_OK) return st;
-    TG_CK_LAUNCH("k_elastic_backward_blk");
+    T* gxe = grad_coords ? static_cast<T*>(p->elem_scratch) : nullptr;
+    const int grid = tg::grid_for(p->E, BB);
+    if (grad_vals)
+      k_elastic_backward_map<T, false><<<grid, BB, 0, s>>>(a, tab, p->cells, p->elem_slot, p->row_ptr, p->E, gxe);
+    else
+      k_elastic_backward_map<T, true><<<grid, BB, 0, s>>>(a, tab, p->cells, p->elem_slot, p->row_ptr, p->E, gxe);
+    TG_CK_LAUNCH("k_elastic_backward_map");
+    if (grad_coords) {
+      k_elastic_backward_node<T><<<tg::grid_for(p->N, BB), BB, 0, s>>>(p->inc_ptr, p->inc_e, p->N, gxe,
+                                                                       static_cast<T*>(grad_coords));
+      TG_CK_LAUNCH("k_elastic_backward_node");
+    }
     return TG_OK;
   };
   return dtype == TG_F32 ? run(0.0f) : run(0.0);

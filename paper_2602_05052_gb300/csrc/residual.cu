@@ -312,19 +312,19 @@ tg_status launch_two_pass(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t
 
 template <int EL, typename T, bool LOADF, int NL>
 tg_status launch_el(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t s) {
-  // FP32 runs on the row blocks.  FP64, and patterns without row blocks,
-  // take the two passes: FP64 is bound by the FP64 pipe, where evaluating
-  // each element exactly once beats the 1.2 evaluations per element of the
-  // row blocks.
+  // FP32 triangles run on the row blocks.  Tetrahedra, FP64 and patterns
+  // without row blocks take the two passes, which evaluate each element
+  // once: the row blocks evaluate it 1.2 times on Hilbert-ordered triangles
+  // but about 3 times on tetrahedral grids, and FP64 is bound by the FP64
+  // pipe.
   constexpr int NV = tg::Elem<EL>::nv;
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4 && EL != TG_P1_TET) {
     const tg::RefTab<T>& tab = tg::table<T>((tg_element)EL);
     const int64_t cap_ctas = (p->n_partials - 4) / kSlots;  // partial slots of the pattern
     const tg::BlkArgs g = tg::blk_args(p);
     const size_t smem = p->bel ? tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE, NV) + (size_t)NV * g.capE * sizeof(T)
                                : 0;
     if (p->bel && p->blk_rows <= RT && smem <= 113 * 1024) {
-      const int need = (p->blk_max_elems + RT - 1) / RT;
       tg_status st = TG_OK;
       auto go = [&](auto kern) {
         if ((st = tg::set_smem((const void*)kern, smem)) != TG_OK) return;
@@ -344,13 +344,7 @@ tg_status launch_el(const tg_pattern* p, const ResArgs<T>& r, cudaStream_t s) {
             (int)std::min<int64_t>({p->n_blk, (int64_t)std::max(per_sm, 1) * tg::sm_count(), cap_ctas});
         kern<<<grid, RT, smem, s>>>(r, tab, g);
       };
-      if constexpr (EL == TG_P2_TRI || EL == TG_P1_TRI) {
-        go(k_residual_blk<EL, T, 2, LOADF, NL>);
-      } else {
-        if (need <= 2) go(k_residual_blk<EL, T, 2, LOADF, NL>);
-        else if (need == 3) go(k_residual_blk<EL, T, 3, LOADF, NL>);
-        else go(k_residual_blk<EL, T, 4, LOADF, NL>);
-      }
+      go(k_residual_blk<EL, T, 2, LOADF, NL>);
       if (st != TG_OK) return st;
       TG_CK_LAUNCH("k_residual_blk");
       return TG_OK;

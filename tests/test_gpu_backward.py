@@ -208,6 +208,50 @@ def test_elasticity_backward_matches_oracle(tg, layout, dtype, fused):
     assert tg.tg_get_device_status(p) == (0, -1)
 
 
+def _fan_tets(m=20, seed=75):
+    """2m tetrahedra around the z axis: a centre node, an apex above and one
+    below, a ring of m nodes; the centre node has m + 2 neighbours, so its
+    row is longer than 16 and the pattern gets no row blocks."""
+    g = np.random.default_rng(seed)
+    ang = 2 * np.pi * np.arange(m) / m
+    ring = np.stack([np.cos(ang), np.sin(ang), g.uniform(-0.1, 0.1, m)], 1)
+    coords = np.vstack([[0.0, 0.0, 0.0], [0.0, 0.0, 1.0], [0.0, 0.0, -1.0], ring])
+    cells = []
+    for i in range(m):
+        a, b = 3 + i, 3 + (i + 1) % m
+        cells += [[0, a, b, 1], [0, b, a, 2]]
+    return np.asarray(cells, dtype=np.int32), coords
+
+
+@pytest.mark.parametrize("fused", [False, True])
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_elasticity_backward_without_row_blocks(tg, dtype, fused):
+    """The two-pass elasticity backward (every pattern without row blocks)."""
+    cells, coords = _fan_tets()
+    n, E = coords.shape[0], cells.shape[0]
+    g = np.random.default_rng(76)
+    lam, mu = g.uniform(0.5, 2.0, E), g.uniform(0.3, 1.0, E)
+    p = tg.tg_build_pattern(dev(cells, torch.int32), n, mg.P1_TET_VEC3)
+    assert p.n_blocks == 0
+    xs, ls, ms = host_as(coords, dtype), host_as(lam, dtype), host_as(mu, dtype)
+    args = (p, dev(coords, dtype), dev(lam, dtype), dev(mu, dtype), mg.PER_ELEMENT)
+    if fused:
+        la, U = host_as(g.normal(size=3 * n), dtype), host_as(g.normal(size=3 * n), dtype)
+        kw = dict(lam_adj=dev(la, dtype), U=dev(U, dtype))
+        want = O.elasticity_backward(cells, xs, ls, ms, mg.PER_ELEMENT, lam_adj=la, U=U)
+    else:
+        ref = O.assemble_elasticity(cells, xs, ls, ms, mg.PER_ELEMENT)
+        gv = host_as(g.normal(size=ref.nnz), dtype)
+        kw = dict(grad_vals=dev(gv, dtype))
+        want = O.elasticity_backward(cells, xs, ls, ms, mg.PER_ELEMENT, grad_csr=O.CSR(ref.row_ptr, ref.col, gv))
+    got = tg.tg_assemble_elasticity_backward(*args, **kw)
+    for a, b in zip(got, want):
+        assert relfro(a.cpu().numpy().reshape(-1), np.asarray(b).reshape(-1)) <= GTOL[dtype]
+    again = tg.tg_assemble_elasticity_backward(*args, **kw)
+    assert all(torch.equal(a, b) for a, b in zip(got, again))
+    assert tg.tg_get_device_status(p) == (0, -1)
+
+
 def test_elasticity_backward_central_differences(tg):
     """FP64: directional derivatives of L = <W, K(lam, mu, x)> against central
     differences of the GPU forward."""
