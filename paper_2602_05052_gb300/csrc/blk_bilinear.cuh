@@ -142,9 +142,34 @@ __device__ __forceinline__ void blk_bilinear_block(const FwdArgs<T>& a, const Re
       if constexpr (LOAD) a.F[v.pm[i]] = fs;
       const int len = v.rp[i + 1] - v.rp[i];
       T* out = a.out + v.up[i];
-      for (int q = 0; q < len; ++q) {
-        out[q] = acc[q * NT + t];
-        acc[q * NT + t] = T(0);
+      if constexpr (EL == TG_P2_TRI) {
+        // P2 rows are long (up to 19 entries): 16-byte stores from the first
+        // 16-byte boundary on, so that a warp's stores (one row per thread,
+        // each in its own lines) write four FP32 values per sector
+        const int head = (int)(((16u - ((unsigned)(uintptr_t)out & 15u)) & 15u) / sizeof(T));
+        int q = 0;
+        for (; q < head && q < len; ++q) {
+          out[q] = acc[q * NT + t];
+          acc[q * NT + t] = T(0);
+        }
+        for (; q + VN <= len; q += VN) {
+          T x[VN];
+#pragma unroll
+          for (int k = 0; k < VN; ++k) {
+            x[k] = acc[(q + k) * NT + t];
+            acc[(q + k) * NT + t] = T(0);
+          }
+          *reinterpret_cast<V*>(out + q) = Vec16<T>::make(x);
+        }
+        for (; q < len; ++q) {
+          out[q] = acc[q * NT + t];
+          acc[q * NT + t] = T(0);
+        }
+      } else {
+        for (int q = 0; q < len; ++q) {
+          out[q] = acc[q * NT + t];
+          acc[q * NT + t] = T(0);
+        }
       }
     }
     __syncthreads();  // stage s and the work buffers are free again

@@ -283,17 +283,77 @@ __global__ void __launch_bounds__(BS) k_load_gather(const FwdArgs<T> a, const __
   }
 }
 
+// Store the n values acc[p * stride] to out[0, n) (out aligned to T):
+// scalar stores up to the first 16-byte boundary, then 16-byte vectors, then
+// the tail.  Rows written by one thread each land in different lines across
+// a warp, so every vector store moves four (FP32) values per sector written
+// instead of one.
+template <typename T>
+__device__ __forceinline__ void store_row(T* __restrict__ out, const T* acc, int stride, int n) {
+  using V = typename tg::Vec16<T>::type;
+  constexpr int VN = tg::Vec16<T>::n;
+  const int head = (int)(((16u - ((unsigned)(uintptr_t)out & 15u)) & 15u) / sizeof(T));
+  int p = 0;
+  for (; p < head && p < n; ++p) out[p] = acc[p * stride];
+  for (; p + VN <= n; p += VN) {
+    T x[VN];
+#pragma unroll
+    for (int k = 0; k < VN; ++k) x[k] = acc[(p + k) * stride];
+    *reinterpret_cast<V*>(out + p) = tg::Vec16<T>::make(x);
+  }
+  for (; p < n; ++p) out[p] = acc[p * stride];
+}
+
 // Vector P1 elasticity, one thread per node: the node's three DoF rows are
 // consecutive in the DoF CSR and together hold 9 * len entries in the order
-// [component i][column node p][component j], accumulated in shared memory.
-//   block (a, b) = (1/|det|) ( L n_a n_b^T + M n_b n_a^T + M (n_a.n_b) I ),
-//   L = sum_q w_q lam_q, M = sum_q w_q mu_q.
+// [component i][column node p][component j], accumulated in shared memory
+// over the node's incidences in increasing element order:
+//   block (a, b) = L n_a n_b^T + M n_b n_a^T + M (n_a.n_b) I,
+// n_c = |det J| grad(phi_c), L = sum_q w_q lam_q / |det J|, M likewise.
+// The row goes out in 16-byte stores (every thread writes its own 9 * len
+// values, so scalar stores would write one value per sector).
+// In FP64 the element terms are computed once per element by
+// k_elastic_geom into geo[16 e + 4 c + r] = n_c[r], geo[16 e + 3] = L,
+// geo[16 e + 7] = M (zeros for a degenerate element, which is flagged and
+// adds nothing); in FP32 every thread computes them from the gathered
+// coordinates, which is cheaper than the records' extra L1 footprint.
 template <typename T>
-__global__ void __launch_bounds__(EB) k_elastic_gather(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab) {
+__global__ void __launch_bounds__(128) k_elastic_geom(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
+                                                      int64_t E, T* __restrict__ geo) {
+  using V = typename tg::Vec16<T>::type;
+  constexpr int VN = tg::Vec16<T>::n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t* cl = a.cells + e * 4;
+    tg::Geom<3, T> g;
+    tg::tet_geom(a.coords, __ldg(cl), __ldg(cl + 1), __ldg(cl + 2), __ldg(cl + 3), g);
+    const T adet = absv(g.det);
+    T o[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) o[k] = T(0);
+    if (!(adet > tg::det_tiny<T>())) {
+      tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
+    } else {
+      const T inv = T(1) / adet;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) o[4 * c + r] = g.n[c][r];
+      o[3] = tg::weighted_coef<T, 4>(a.coef, a.layout, e, tab.w, tab.wsum) * inv;
+      o[7] = tg::weighted_coef<T, 4>(a.coef2, a.layout, e, tab.w, tab.wsum) * inv;
+    }
+    V* dst = reinterpret_cast<V*>(geo + 16 * e);
+#pragma unroll
+    for (int k = 0; k < 16 / VN; ++k) dst[k] = tg::Vec16<T>::make(o + k * VN);
+  }
+}
+
+template <typename T, bool GEO>
+__global__ void __launch_bounds__(EB) k_elastic_gather(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
+                                                       const T* __restrict__ geo) {
+  using V = typename tg::Vec16<T>::type;
+  constexpr int VN = tg::Vec16<T>::n;
   extern __shared__ __align__(16) unsigned char smem[];
-  auto& ts = *reinterpret_cast<tg::RefTab<T>*>(smem);
-  T* acc = reinterpret_cast<T*>(smem + tab_bytes<T>()) + threadIdx.x;
-  copy_table(ts, tab);
+  T* acc = reinterpret_cast<T*>(smem) + threadIdx.x;
   const int64_t i = (int64_t)blockIdx.x * EB + threadIdx.x;
   if (i >= a.n) return;
   const int r0 = __ldg(a.row_ptr + i), len = __ldg(a.row_ptr + i + 1) - r0;
@@ -304,39 +364,55 @@ __global__ void __launch_bounds__(EB) k_elastic_gather(const FwdArgs<T> a, const
     const int64_t e = ea >> 3;
     const int la = ea & 7;
     const uint32_t w0 = __ldg(a.inc_pos + j);
-    const int32_t* cl = a.cells + e * 4;
-    tg::Geom<3, T> g;
-    tg::tet_geom(a.coords, __ldg(cl), __ldg(cl + 1), __ldg(cl + 2), __ldg(cl + 3), g);
-    const T adet = absv(g.det);
-    if (!(adet > tg::det_tiny<T>())) {
-      tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
-      continue;
+    T o[16];
+    if constexpr (GEO) {
+      const V* src = reinterpret_cast<const V*>(geo + 16 * e);
+#pragma unroll
+      for (int k = 0; k < 16 / VN; ++k) {
+        const V x = __ldg(src + k);
+#pragma unroll
+        for (int q = 0; q < VN; ++q) o[k * VN + q] = tg::Vec16<T>::get(x, q);
+      }
+    } else {
+      const int32_t* cl = a.cells + e * 4;
+      tg::Geom<3, T> g;
+      tg::tet_geom(a.coords, __ldg(cl), __ldg(cl + 1), __ldg(cl + 2), __ldg(cl + 3), g);
+      const T adet = absv(g.det);
+      if (!(adet > tg::det_tiny<T>())) {
+        tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
+        continue;
+      }
+      const T inv = T(1) / adet;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) o[4 * c + r] = g.n[c][r];
+      o[3] = tg::weighted_coef<T, 4>(a.coef, a.layout, e, tab.w, tab.wsum) * inv;
+      o[7] = tg::weighted_coef<T, 4>(a.coef2, a.layout, e, tab.w, tab.wsum) * inv;
     }
-    const T inv = T(1) / adet;
-    const T L = tg::weighted_coef<T, 4>(a.coef, a.layout, e, ts.w, ts.wsum) * inv;
-    const T M = tg::weighted_coef<T, 4>(a.coef2, a.layout, e, ts.w, ts.wsum) * inv;
+    const T L = o[3], M = o[7];
     T na[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      const T col[4] = {g.n[0][r], g.n[1][r], g.n[2][r], g.n[3][r]};
+      const T col[4] = {o[r], o[4 + r], o[8 + r], o[12 + r]};
       na[r] = tg::sel(la, col);
     }
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int pos = tg::pos_of(w0, 0u, b);
-      const T d = na[0] * g.n[b][0] + na[1] * g.n[b][1] + na[2] * g.n[b][2];
+      const T* nb = o + 4 * b;
+      const T d = na[0] * nb[0] + na[1] * nb[1] + na[2] * nb[2];
 #pragma unroll
       for (int ii = 0; ii < 3; ++ii)
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
-          T v = L * na[ii] * g.n[b][jj] + M * g.n[b][ii] * na[jj];
+          T v = L * na[ii] * nb[jj] + M * nb[ii] * na[jj];
           if (ii == jj) v += M * d;
           acc[((ii * len + pos) * 3 + jj) * EB] += v;
         }
     }
   }
-  T* out = a.out + 9ll * r0;
-  for (int p = 0; p < 9 * len; ++p) out[p] = acc[p * EB];
+  store_row<T>(a.out + 9ll * r0, acc, EB, 9 * len);
 }
 
 // ---------------------------------------------------------------- host side
@@ -521,10 +597,24 @@ tg_status elastic(const tg_pattern* p, const void* coords, const void* lam, cons
   a.coef2 = static_cast<const T*>(mu);
   a.layout = l;
   a.out = static_cast<T*>(vals);
-  const size_t smem = tab_bytes<T>() + (size_t)EB * 9 * p->max_row_len * sizeof(T);
-  tg_status st = set_smem((const void*)k_elastic_gather<T>, smem);
+  if (p->N == 0) return TG_OK;
+  constexpr bool use_geo = sizeof(T) == 8;
+  T* geo = static_cast<T*>(p->elem_scratch);  // 16 values per element
+  if constexpr (use_geo) {
+    if (p->E > 0) {
+      if (!geo) return TG_ERR_UNSUPPORTED;
+      k_elastic_geom<T><<<tg::grid_for(p->E, 128), 128, 0, s>>>(a, table<T>(TG_P1_TET), p->E, geo);
+      TG_CK_LAUNCH("k_elastic_geom");
+    }
+  }
+  const size_t smem = (size_t)EB * 9 * p->max_row_len * sizeof(T);
+  tg_status st = TG_OK;
+  auto go = [&](auto kern) {
+    if ((st = set_smem((const void*)kern, smem)) != TG_OK) return;
+    kern<<<tg::grid_for(p->N, EB), EB, smem, s>>>(a, table<T>(TG_P1_TET), geo);
+  };
+  go(k_elastic_gather<T, use_geo>);
   if (st != TG_OK) return st;
-  k_elastic_gather<T><<<tg::grid_for(p->N, EB), EB, smem, s>>>(a, table<T>(TG_P1_TET));
   TG_CK_LAUNCH("k_elastic_gather");
   return TG_OK;
 }

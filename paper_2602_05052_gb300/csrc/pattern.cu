@@ -792,7 +792,10 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   TG_CK(cudaMalloc(&p->partials, p->n_partials * sizeof(double)));
   TG_CK(cudaMalloc(&p->arrivals, 16));
   TG_CK(cudaMemsetAsync(p->arrivals, 0, 16, s));
-  if ((nc == 1 || el == TG_P1_TET_VEC3) && E > 0) TG_CK(cudaMalloc(&p->elem_scratch, (size_t)E * nv * tg::dim_of(el) * sizeof(double)));
+  // per-element results of the two-pass kernels: nv * dim values per
+  // element, 16 for vector elasticity (its forward's geometry)
+  if ((nc == 1 || el == TG_P1_TET_VEC3) && E > 0)
+    TG_CK(cudaMalloc(&p->elem_scratch, (size_t)E * (nc == 1 ? nv * tg::dim_of(el) : 16) * sizeof(double)));
   TG_CK(cudaStreamSynchronize(s));
   if ((st = read_status(p, s, "tg_build_pattern")) != TG_OK) return st;
   guard.ok = true;
