@@ -454,9 +454,8 @@ __global__ void k_bel_words(const int32_t* __restrict__ cnt, int64_t nblk, int n
 }
 
 // Per element: the position of every vertex's column in every vertex's row.
-// (Vector elasticity: the slot map is DoF-level, slot = 9 * row_ptr + 3 * pos.)
 __global__ void k_elem_pos(const int32_t* __restrict__ cells, const int32_t* __restrict__ elem_slot,
-                           const int32_t* __restrict__ row_ptr, int64_t E, int nv, int pb, bool vec3,
+                           const int32_t* __restrict__ row_ptr, int64_t E, int nv, int pb,
                            uint64_t* __restrict__ out) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
@@ -465,7 +464,7 @@ __global__ void k_elem_pos(const int32_t* __restrict__ cells, const int32_t* __r
     const int ra = row_ptr[cells[e * nv + a]];
     for (int b = 0; b < nv; ++b) {
       const int sl = elem_slot[(e * nv + a) * nv + b];
-      const int pos = vec3 ? (sl - 9 * ra) / 3 : sl - ra;
+      const int pos = sl - ra;
       w |= (uint64_t)pos << ((a * nv + b) * pb);
     }
   }
@@ -534,7 +533,7 @@ tg_status read_status(const tg_pattern* p, cudaStream_t s, const char* stage) {
 // threads.  Tetrahedra touch about 18 distinct elements per row; vector
 // elasticity keeps 12 values per element in shared memory, hence 32 rows.
 int blk_rows_of(tg_element el) {
-  return el == TG_P1_TRI ? 120 : el == TG_P2_TRI ? 128 : el == TG_P1_TET ? 64 : 32;
+  return el == TG_P1_TRI ? 120 : el == TG_P2_TRI ? 128 : 64;
 }
 
 // Row blocks (step 5).  Leaves p->bel == NULL when the packed fields do not
@@ -656,8 +655,7 @@ tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
   p->blk_max_elems = h[2];
   if (nv * nv * pb <= 64) {
     TG_CK(cudaMalloc(&p->elem_pos, E * sizeof(uint64_t) + 16));
-    k_elem_pos<<<tg::grid_for(E, kThreads), kThreads, 0, s>>>(p->cells, p->elem_slot, p->row_ptr, E, nv, pb,
-                                                              p->el == TG_P1_TET_VEC3, p->elem_pos);
+    k_elem_pos<<<tg::grid_for(E, kThreads), kThreads, 0, s>>>(p->cells, p->elem_slot, p->row_ptr, E, nv, pb, p->elem_pos);
     TG_CK_LAUNCH("k_elem_pos");
   }
   TG_CK(cudaStreamSynchronize(s));  // tmp buffers are freed on return
@@ -771,9 +769,10 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   TG_CK_LAUNCH("k_rows<true>");
 
 
-  // 5. row blocks of the element-once kernels (not for the quadrilaterals,
-  // which the plane-stress kernels serve per node row)
-  if (E > 0 && el != TG_Q1_QUAD_VEC2) {
+  // 5. row blocks of the element-once kernels (not for the vector kinds:
+  // the plane-stress and elasticity kernels work per node row and per
+  // element)
+  if (E > 0 && nc == 1) {
     if ((st = build_blocks(p, s)) != TG_OK) return st;
   }
 

@@ -38,13 +38,12 @@ struct tg_pattern {
   int32_t* elem_slot = nullptr;
   int32_t* row_ptr_dof = nullptr;
   int32_t* col_idx_dof = nullptr;
-  // Row blocks of the element-once P1 kernels (P1 triangles, tetrahedra and
-  // vector elasticity, built when the packed fields fit; bel == NULL
-  // otherwise).  The kernels walk the rows in an internal order: iperm[i] is
-  // the node of internal row i (nodes by smallest incident element, then
-  // each block of blk_rows rows in ascending node id); iinc and irp are the
-  // incidence and CSR-value prefix sums in that order, urp[i] =
-  // row_ptr[iperm[i]].  Block b owns the internal rows [b*blk_rows,
+  // Row blocks of the element-once kernels (scalar kinds only, built when
+  // the packed fields fit; bel == NULL otherwise).  The kernels walk the
+  // rows in an internal order: iperm[i] is the node of internal row i
+  // (nodes by smallest incident element, then each block of blk_rows rows
+  // in ascending node id); iinc and irp are the incidence and CSR-value
+  // prefix sums in that order, urp[i] = row_ptr[iperm[i]].  Block b owns the internal rows [b*blk_rows,
   // (b+1)*blk_rows) and hence the internal incidences [J0, J1) =
   // [iinc[b*blk_rows], iinc[min((b+1)*blk_rows, N)]).
   //   bel + boff[b]: the block's distinct elements (nbe = bel_cnt[b] of

@@ -183,7 +183,7 @@ def test_differentiable3d_small_matches_oracle_gradient(tg):
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("layout", [mg.PER_ELEMENT, mg.PER_QP])
 def test_elasticity_backward_matches_oracle(tg, layout, dtype, fused):
-    m = jittered_tet(6)  # 343 nodes: 10 full row blocks of 32 and a ragged one
+    m = jittered_tet(6)  # 343 nodes, 1,296 tetrahedra
     lam = coef(layout, m.n_elems, 4, seed=71, lo=0.5, hi=2.0)
     mu = coef(layout, m.n_elems, 4, seed=72, lo=0.3, hi=1.0)
     p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TET_VEC3)
