@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / elasticity / batched breakdown")
-    ap.add_argument("--extras-only", choices=["residual", "facets", "batch"], default=None,
+    ap.add_argument("--extras-only", choices=["residual", "facets", "batch", "elasticity"], default=None,
                     help="run only this part of the breakdown (short runs, e.g. for profiling one kernel)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -427,6 +427,8 @@ def main():
             out["breakdown"] = residual_extras(tg, torch, dev, m, cfg, p, peak, flush)
         elif args.extras_only == "facets":
             out["breakdown"] = facet_extras(tg, torch, dev, m, p, flush)
+        elif args.extras_only == "elasticity":
+            out["breakdown"] = elasticity_extras(tg, torch, dev, peak, flush)
         else:
             out["breakdown"] = batch_extras(tg, torch, dev, peak, flush)
     elif not args.no_extras and rank == 0:
@@ -506,7 +508,16 @@ def extras(tg, torch, dev, m, cfg, p, peak, flush):
     out.update(facet_extras(tg, torch, dev, m, p, flush))
     out["fp64_fma_peak_tflops"] = tg.tg_diag_fma_rate(torch.float64) / 1e12
     out["fp32_fma_peak_tflops"] = tg.tg_diag_fma_rate(torch.float32) / 1e12
-    # elasticity 64^3
+    out.update(elasticity_extras(tg, torch, dev, peak, flush))
+    out.update(batch_extras(tg, torch, dev, peak, flush))
+    out.update(small_configs(tg, torch, dev))
+    return out
+
+
+def elasticity_extras(tg, torch, dev, peak, flush):
+    """Vector P1 elasticity on 64^3 Kuhn tetrahedra: forward and backward for
+    an upstream gradient of the values, FP32 and FP64."""
+    out = {}
     ce = mg.elasticity3d(64)
     me = ce["mesh"]
     pe = tg.tg_build_pattern(torch.as_tensor(me.cells, device=dev), me.n_nodes, tg.P1_TET_VEC3)
@@ -526,8 +537,6 @@ def extras(tg, torch, dev, m, cfg, p, peak, flush):
                                       "bwd_ms": ms_eb, "bwd_alg_GBps": bb / ms_eb / 1e6,
                                       "bwd_frac_hbm": bb / ms_eb / 1e6 / peak}
     del pe
-    out.update(batch_extras(tg, torch, dev, peak, flush))
-    out.update(small_configs(tg, torch, dev))
     return out
 
 

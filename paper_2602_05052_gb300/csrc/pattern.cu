@@ -454,8 +454,9 @@ __global__ void k_bel_words(const int32_t* __restrict__ cnt, int64_t nblk, int n
 }
 
 // Per element: the position of every vertex's column in every vertex's row.
+// (Vector elasticity: the slot map is DoF-level, slot = 9 * row_ptr + 3 * pos.)
 __global__ void k_elem_pos(const int32_t* __restrict__ cells, const int32_t* __restrict__ elem_slot,
-                           const int32_t* __restrict__ row_ptr, int64_t E, int nv, int pb,
+                           const int32_t* __restrict__ row_ptr, int64_t E, int nv, int pb, bool vec3,
                            uint64_t* __restrict__ out) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
@@ -464,7 +465,7 @@ __global__ void k_elem_pos(const int32_t* __restrict__ cells, const int32_t* __r
     const int ra = row_ptr[cells[e * nv + a]];
     for (int b = 0; b < nv; ++b) {
       const int sl = elem_slot[(e * nv + a) * nv + b];
-      const int pos = sl - ra;
+      const int pos = vec3 ? (sl - 9 * ra) / 3 : sl - ra;
       w |= (uint64_t)pos << ((a * nv + b) * pb);
     }
   }
@@ -655,7 +656,8 @@ tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
   p->blk_max_elems = h[2];
   if (nv * nv * pb <= 64) {
     TG_CK(cudaMalloc(&p->elem_pos, E * sizeof(uint64_t) + 16));
-    k_elem_pos<<<tg::grid_for(E, kThreads), kThreads, 0, s>>>(p->cells, p->elem_slot, p->row_ptr, E, nv, pb, p->elem_pos);
+    k_elem_pos<<<tg::grid_for(E, kThreads), kThreads, 0, s>>>(p->cells, p->elem_slot, p->row_ptr, E, nv, pb, false,
+                                                              p->elem_pos);
     TG_CK_LAUNCH("k_elem_pos");
   }
   TG_CK(cudaStreamSynchronize(s));  // tmp buffers are freed on return
@@ -777,6 +779,14 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   }
 
   // 6. DoF-level CSR for elasticity
+  // packed positions of the elasticity backward (4-bit fields: rows of at
+  // most 16 nodes); it reads the 32-bit slot map otherwise
+  if (el == TG_P1_TET_VEC3 && E > 0 && p->max_row_len <= 16) {
+    TG_CK(cudaMalloc(&p->elem_pos, E * sizeof(uint64_t) + 16));
+    k_elem_pos<<<tg::grid_for(E, kThreads), kThreads, 0, s>>>(p->cells, p->elem_slot, p->row_ptr, E, nv, 4, true,
+                                                              p->elem_pos);
+    TG_CK_LAUNCH("k_elem_pos");
+  }
   if (nc > 1) {
     TG_CK(cudaMalloc(&p->row_ptr_dof, (nc * N + 1) * sizeof(int32_t)));
     TG_CK(cudaMalloc(&p->col_idx_dof, (size_t)nc * nc * nnz * sizeof(int32_t) + 16));
