@@ -34,6 +34,13 @@ def test_every_declared_symbol_is_exported(L):
         assert hasattr(L, n), n
 
 
+def test_build_compiles_every_cuda_source():
+    """Every translation unit under csrc/ is in the build's source list."""
+    from paper_2602_05052_gb300 import build
+    csrc = os.path.join(ROOT, "paper_2602_05052_gb300", "csrc")
+    assert sorted(f for f in os.listdir(csrc) if f.endswith(".cu")) == sorted(build.SOURCES)
+
+
 def test_status_strings(L):
     L.tg_status_string.restype = C.c_char_p
     assert L.tg_status_string(0) == b"TG_OK"
