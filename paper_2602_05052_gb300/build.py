@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libtg.so")
 
-SOURCES = ["api.cu", "pattern.cu", "forward.cu", "backward.cu", "elastic_bwd.cu", "residual.cu", "facets.cu", "simp.cu", "batch.cu", "solve.cu"]
+SOURCES = ["api.cu", "pattern.cu", "forward.cu", "elastic_fwd.cu", "backward.cu", "elastic_bwd.cu", "residual.cu", "facets.cu", "simp.cu", "batch.cu", "solve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

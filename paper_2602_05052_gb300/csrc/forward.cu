@@ -21,7 +21,6 @@ namespace {
 
 constexpr int BS = 128;  // rows per CTA (scalar kernels)
 constexpr int BT = 128;  // threads per CTA of the element-once kernels (>= rows per block)
-constexpr int EB = 64;   // rows per CTA (elasticity: 9 * row length accumulators per thread)
 // Largest shared memory of an element-once CTA (two CTAs per SM); patterns
 // that need more use the generic kernels.
 constexpr size_t kBlkSmemMax = 113 * 1024;
@@ -283,138 +282,6 @@ __global__ void __launch_bounds__(BS) k_load_gather(const FwdArgs<T> a, const __
   }
 }
 
-// Store the n values acc[p * stride] to out[0, n) (out aligned to T):
-// scalar stores up to the first 16-byte boundary, then 16-byte vectors, then
-// the tail.  Rows written by one thread each land in different lines across
-// a warp, so every vector store moves four (FP32) values per sector written
-// instead of one.
-template <typename T>
-__device__ __forceinline__ void store_row(T* __restrict__ out, const T* acc, int stride, int n) {
-  using V = typename tg::Vec16<T>::type;
-  constexpr int VN = tg::Vec16<T>::n;
-  const int head = (int)(((16u - ((unsigned)(uintptr_t)out & 15u)) & 15u) / sizeof(T));
-  int p = 0;
-  for (; p < head && p < n; ++p) out[p] = acc[p * stride];
-  for (; p + VN <= n; p += VN) {
-    T x[VN];
-#pragma unroll
-    for (int k = 0; k < VN; ++k) x[k] = acc[(p + k) * stride];
-    *reinterpret_cast<V*>(out + p) = tg::Vec16<T>::make(x);
-  }
-  for (; p < n; ++p) out[p] = acc[p * stride];
-}
-
-// Vector P1 elasticity, one thread per node: the node's three DoF rows are
-// consecutive in the DoF CSR and together hold 9 * len entries in the order
-// [component i][column node p][component j], accumulated in shared memory
-// over the node's incidences in increasing element order:
-//   block (a, b) = L n_a n_b^T + M n_b n_a^T + M (n_a.n_b) I,
-// n_c = |det J| grad(phi_c), L = sum_q w_q lam_q / |det J|, M likewise.
-// The row goes out in 16-byte stores (every thread writes its own 9 * len
-// values, so scalar stores would write one value per sector).
-// In FP64 the element terms are computed once per element by
-// k_elastic_geom into geo[16 e + 4 c + r] = n_c[r], geo[16 e + 3] = L,
-// geo[16 e + 7] = M (zeros for a degenerate element, which is flagged and
-// adds nothing); in FP32 every thread computes them from the gathered
-// coordinates, which is cheaper than the records' extra L1 footprint.
-template <typename T>
-__global__ void __launch_bounds__(128) k_elastic_geom(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
-                                                      int64_t E, T* __restrict__ geo) {
-  using V = typename tg::Vec16<T>::type;
-  constexpr int VN = tg::Vec16<T>::n;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t* cl = a.cells + e * 4;
-    tg::Geom<3, T> g;
-    tg::tet_geom(a.coords, __ldg(cl), __ldg(cl + 1), __ldg(cl + 2), __ldg(cl + 3), g);
-    const T adet = absv(g.det);
-    T o[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) o[k] = T(0);
-    if (!(adet > tg::det_tiny<T>())) {
-      tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
-    } else {
-      const T inv = T(1) / adet;
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int r = 0; r < 3; ++r) o[4 * c + r] = g.n[c][r];
-      o[3] = tg::weighted_coef<T, 4>(a.coef, a.layout, e, tab.w, tab.wsum) * inv;
-      o[7] = tg::weighted_coef<T, 4>(a.coef2, a.layout, e, tab.w, tab.wsum) * inv;
-    }
-    V* dst = reinterpret_cast<V*>(geo + 16 * e);
-#pragma unroll
-    for (int k = 0; k < 16 / VN; ++k) dst[k] = tg::Vec16<T>::make(o + k * VN);
-  }
-}
-
-template <typename T, bool GEO>
-__global__ void __launch_bounds__(EB) k_elastic_gather(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
-                                                       const T* __restrict__ geo) {
-  using V = typename tg::Vec16<T>::type;
-  constexpr int VN = tg::Vec16<T>::n;
-  extern __shared__ __align__(16) unsigned char smem[];
-  T* acc = reinterpret_cast<T*>(smem) + threadIdx.x;
-  const int64_t i = (int64_t)blockIdx.x * EB + threadIdx.x;
-  if (i >= a.n) return;
-  const int r0 = __ldg(a.row_ptr + i), len = __ldg(a.row_ptr + i + 1) - r0;
-  for (int p = 0; p < 9 * len; ++p) acc[p * EB] = T(0);
-  const int j0 = __ldg(a.inc_ptr + i), j1 = __ldg(a.inc_ptr + i + 1);
-  for (int j = j0; j < j1; ++j) {
-    const int ea = __ldg(a.inc_e + j);
-    const int64_t e = ea >> 3;
-    const int la = ea & 7;
-    const uint32_t w0 = __ldg(a.inc_pos + j);
-    T o[16];
-    if constexpr (GEO) {
-      const V* src = reinterpret_cast<const V*>(geo + 16 * e);
-#pragma unroll
-      for (int k = 0; k < 16 / VN; ++k) {
-        const V x = __ldg(src + k);
-#pragma unroll
-        for (int q = 0; q < VN; ++q) o[k * VN + q] = tg::Vec16<T>::get(x, q);
-      }
-    } else {
-      const int32_t* cl = a.cells + e * 4;
-      tg::Geom<3, T> g;
-      tg::tet_geom(a.coords, __ldg(cl), __ldg(cl + 1), __ldg(cl + 2), __ldg(cl + 3), g);
-      const T adet = absv(g.det);
-      if (!(adet > tg::det_tiny<T>())) {
-        tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
-        continue;
-      }
-      const T inv = T(1) / adet;
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int r = 0; r < 3; ++r) o[4 * c + r] = g.n[c][r];
-      o[3] = tg::weighted_coef<T, 4>(a.coef, a.layout, e, tab.w, tab.wsum) * inv;
-      o[7] = tg::weighted_coef<T, 4>(a.coef2, a.layout, e, tab.w, tab.wsum) * inv;
-    }
-    const T L = o[3], M = o[7];
-    T na[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const T col[4] = {o[r], o[4 + r], o[8 + r], o[12 + r]};
-      na[r] = tg::sel(la, col);
-    }
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int pos = tg::pos_of(w0, 0u, b);
-      const T* nb = o + 4 * b;
-      const T d = na[0] * nb[0] + na[1] * nb[1] + na[2] * nb[2];
-#pragma unroll
-      for (int ii = 0; ii < 3; ++ii)
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-          T v = L * na[ii] * nb[jj] + M * nb[ii] * na[jj];
-          if (ii == jj) v += M * d;
-          acc[((ii * len + pos) * 3 + jj) * EB] += v;
-        }
-    }
-  }
-  store_row<T>(a.out + 9ll * r0, acc, EB, 9 * len);
-}
-
 // ---------------------------------------------------------------- host side
 using tg::table;
 using tg::set_smem;
@@ -589,36 +456,6 @@ tg_status load(const tg_pattern* p, const void* coords, const void* f, tg_layout
   return TG_OK;
 }
 
-template <typename T>
-tg_status elastic(const tg_pattern* p, const void* coords, const void* lam, const void* mu, tg_layout l, void* vals,
-                  cudaStream_t s) {
-  FwdArgs<T> a = base_args<T>(p, coords);
-  a.coef = static_cast<const T*>(lam);
-  a.coef2 = static_cast<const T*>(mu);
-  a.layout = l;
-  a.out = static_cast<T*>(vals);
-  if (p->N == 0) return TG_OK;
-  constexpr bool use_geo = sizeof(T) == 8;
-  T* geo = static_cast<T*>(p->elem_scratch);  // 16 values per element
-  if constexpr (use_geo) {
-    if (p->E > 0) {
-      if (!geo) return TG_ERR_UNSUPPORTED;
-      k_elastic_geom<T><<<tg::grid_for(p->E, 128), 128, 0, s>>>(a, table<T>(TG_P1_TET), p->E, geo);
-      TG_CK_LAUNCH("k_elastic_geom");
-    }
-  }
-  const size_t smem = (size_t)EB * 9 * p->max_row_len * sizeof(T);
-  tg_status st = TG_OK;
-  auto go = [&](auto kern) {
-    if ((st = set_smem((const void*)kern, smem)) != TG_OK) return;
-    kern<<<tg::grid_for(p->N, EB), EB, smem, s>>>(a, table<T>(TG_P1_TET), geo);
-  };
-  go(k_elastic_gather<T, use_geo>);
-  if (st != TG_OK) return st;
-  TG_CK_LAUNCH("k_elastic_gather");
-  return TG_OK;
-}
-
 // The system (K, F) in one pass where the element-once kernels apply, else
 // the two assemblies one after the other (same values either way).
 template <typename T>
@@ -695,17 +532,6 @@ tg_status tg_assemble_bilinear(const tg_pattern* p, tg_dtype dtype, const void* 
 tg_status tg_assemble_bilinear_atomic(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
                                       tg_layout kappa_layout, double c, void* vals_out, tg_stream stream) {
   return bilinear_entry(p, dtype, coords, kappa, kappa_layout, c, vals_out, stream, true);
-}
-
-tg_status tg_assemble_elasticity(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* lam,
-                                 const void* mu, tg_layout layout, void* vals_out, tg_stream stream) {
-  tg_status st = check_common(p, dtype, coords);
-  if (st != TG_OK) return st;
-  if (p->el != TG_P1_TET_VEC3 || !layout_ok(layout, false) || !lam || !mu || (p->nnz > 0 && !vals_out))
-    return TG_ERR_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  return dtype == TG_F32 ? elastic<float>(p, coords, lam, mu, layout, vals_out, s)
-                         : elastic<double>(p, coords, lam, mu, layout, vals_out, s);
 }
 
 tg_status tg_assemble_system(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
