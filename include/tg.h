@@ -180,7 +180,10 @@ tg_status tg_assemble_bilinear_atomic(const tg_pattern* p, tg_dtype dtype, const
  * (Hooke's law, SM B.1 Benchmark II):
  *   K[(a,i),(b,j)] = sum_q w_q |det J| ( lam_q g_ai g_bj + mu_q g_aj g_bi + mu_q delta_ij g_a . g_b ).
  *   lam, mu     per layout (PER_ELEMENT, PER_QP or CONSTANT); vals_out [9 nnz_node]
- *               in the DoF-level CSR.  Pattern kind TG_P1_TET_VEC3. */
+ *               in the DoF-level CSR.  Pattern kind TG_P1_TET_VEC3.
+ * In FP64 the element terms go through the pattern's per-element scratch
+ * (computed once per element): FP64 calls on one pattern that overlap
+ * (several streams) race. */
 tg_status tg_assemble_elasticity(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* lam,
                                  const void* mu, tg_layout layout, void* vals_out, tg_stream stream);
 
@@ -268,7 +271,10 @@ tg_status tg_reaction_points(const tg_pattern* p, tg_dtype dtype, const void* x,
  *   grad_kappa  same layout as kappa (PER_QP, PER_ELEMENT or CONSTANT), or NULL;
  *   grad_coords [N][d], or NULL;
  *   grad_c      device scalar of dtype, or NULL.
- * All outputs are overwritten; sums run in a fixed order (deterministic). */
+ * All outputs are overwritten; sums run in a fixed order (deterministic).
+ * Uses the pattern's partial-sum buffers and, for tetrahedra and in FP64,
+ * its per-element scratch: calls on one pattern that overlap (several
+ * streams) race. */
 tg_status tg_assemble_backward(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
                                tg_layout kappa_layout, double c, const void* grad_vals, const void* lam,
                                const void* U, void* grad_kappa, void* grad_coords, void* grad_c,
@@ -283,8 +289,10 @@ tg_status tg_assemble_backward(const tg_pattern* p, tg_dtype dtype, const void* 
  *   grad_lam, grad_mu  in the layout of lam and mu (PER_ELEMENT [E] or
  *                      PER_QP [E][4]), or NULL;
  *   grad_coords        [N][3], or NULL.
- * All outputs are overwritten; sums run in a fixed order (deterministic).
- * Needs node rows of at most 16 entries (TG_ERR_UNSUPPORTED otherwise). */
+ * All outputs are overwritten; sums run in a fixed order (deterministic):
+ * one thread per element writes its terms to the pattern's per-element
+ * scratch, then every node sums its elements' terms in increasing element
+ * order.  Calls on one pattern that overlap (several streams) race. */
 tg_status tg_assemble_elasticity_backward(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* lam,
                                           const void* mu, tg_layout layout, const void* grad_vals,
                                           const void* lam_adj, const void* U, void* grad_lam, void* grad_mu,
