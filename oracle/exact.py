@@ -134,19 +134,61 @@ def _grad_terms(S: Simplex, p):
 
 
 def stiffness(verts, kind="p1", kappa=1):
-    """K_ab = kappa * int grad phi_a . grad phi_b (constant kappa)."""
+    """K_ab = int kappa grad phi_a . grad phi_b.  kappa is a constant, or a
+    polynomial in the barycentric coordinates of the simplex (a dict, see
+    ``coef_poly``) for a coefficient that varies over the element."""
     S = Simplex(verts)
     B = basis_polys(kind, S.d)
     G = [_grad_terms(S, b) for b in B]
     k = len(B)
+    kp = kappa if isinstance(kappa, dict) else {tuple([0] * (S.d + 1)): Fr(kappa)}
     K = [[Fr(0)] * k for _ in range(k)]
     for a in range(k):
         for b in range(k):
             s = Fr(0)
             for r in range(S.d):
-                s += S.integrate(_mul(G[a][r], G[b][r]))
-            K[a][b] = Fr(kappa) * s
+                s += S.integrate(_mul(kp, _mul(G[a][r], G[b][r])))
+            K[a][b] = s
     return K
+
+
+def coef_poly(verts, coeffs):
+    """A polynomial coefficient c(x) = sum_m coeffs[m] * x^m (m an exponent
+    tuple over the spatial coordinates) written in the barycentric
+    coordinates of the simplex, using x_r = sum_i l_i v_i[r]."""
+    n = len(verts)
+    xs = [{tuple(int(k == i) for k in range(n)): Fr(verts[i][r]) for i in range(n)} for r in range(len(verts[0]))]
+    out = {}
+    for m, c in coeffs.items():
+        term = {tuple([0] * n): Fr(c)}
+        for r, e in enumerate(m):
+            for _ in range(e):
+                term = _mul(term, xs[r])
+        out = _add(out, term)
+    return out
+
+
+def eval_poly_at(coeffs, x):
+    """sum_m coeffs[m] * x^m at a point given as Fractions."""
+    s = Fr(0)
+    for m, c in coeffs.items():
+        t = Fr(c)
+        for r, e in enumerate(m):
+            t *= Fr(x[r]) ** e
+        s += t
+    return s
+
+
+def load_poly(verts, kind, f_bary):
+    """F_a = int f phi_a for f given as a barycentric polynomial."""
+    S = Simplex(verts)
+    return [S.integrate(_mul(f_bary, p)) for p in basis_polys(kind, S.d)]
+
+
+def mean_over(verts, coeffs):
+    """(1/|T|) int_T c(x) for a spatial polynomial c."""
+    S = Simplex(verts)
+    return S.integrate(coef_poly(verts, coeffs)) / S.vol
 
 
 def mass(verts, kind="p1"):

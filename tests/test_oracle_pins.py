@@ -519,3 +519,118 @@ def test_load_backward_matches_central_differences(el, layout, ncomp):
             cm[node, r] -= eps
             num = (L(f, cp) - L(f, cm)) / (2 * eps)
             assert abs(num - gx[node, r]) < 1e-7 * max(1, abs(gx[node, r])), (node, r, num, gx[node, r])
+
+
+# ---------------------------------------------------------------- coefficients that vary over the element
+# Eq. (matlclquad) pairs the coefficient value kappa[e][q] with the
+# quadrature point x_q of element e.  For P1 the gradients are constant and
+# only the weights matter; for P2 the point matters.  A coefficient that is a
+# polynomial in x, sampled at the physical quadrature points, has an exact
+# integral that the rule reproduces when the integrand's degree is within
+# the rule's (kappa quadratic: kappa grad phi_a . grad phi_b has degree 4 for
+# P2, the 6-point rule's degree).  Pairing kappa_q with any other point, or a
+# point with the wrong vertex, changes the result.
+def _phys_points(el, V):
+    w, xq = O.quadrature(el)
+    V = np.asarray(V, dtype=float)
+    J = (V[1:len(V)] - V[0]).T  # columns: edge vectors from vertex 0
+    return xq @ J.T + V[0]
+
+
+def _rand_poly(g, d, deg):
+    import itertools
+    out = {}
+    for m in itertools.product(range(deg + 1), repeat=d):
+        if sum(m) <= deg:
+            out[m] = Fr(int(g.integers(-8, 9)), 8)
+    out[tuple([0] * d)] = Fr(4)  # keep the coefficient away from zero
+    return out
+
+
+def _poly_at(P, pts):
+    return np.array([float(X.eval_poly_at(P, [Fr(float(v)) for v in p])) for p in pts])
+
+
+def test_p2_per_point_kappa_element_matches_exact_integral():
+    g = np.random.default_rng(31)
+    for _ in range(5):
+        V = _dyadic_simplex(g, 2)
+        P = _rand_poly(g, 2, 2)
+        kq = _poly_at(P, _phys_points(O.P2_TRI, V))
+        Ke = np.array(X.stiffness(V, "p2", X.coef_poly(V, P)), dtype=float)
+        Ko = O.element_matrix(O.P2_TRI, np.array(V, dtype=float), kq, 0.0)
+        assert np.allclose(Ko, Ke, rtol=1e-13, atol=1e-13 * np.abs(Ke).max())
+        # the same values with the points' order reversed give another matrix
+        Kr = O.element_matrix(O.P2_TRI, np.array(V, dtype=float), kq[::-1], 0.0)
+        assert np.abs(Kr - Ke).max() > 1e-6 * np.abs(Ke).max()
+
+
+def test_p2_per_point_kappa_assembly_matches_exact_assembly():
+    # per-QP layout kappa[e * 6 + q] through the global scatter-add
+    m = mg.p2_tri_grid(2, jitter_seed=None)
+    g = np.random.default_rng(32)
+    P = _rand_poly(g, 2, 2)
+    cells, coords = m.cells, m.coords
+    kq = np.concatenate([_poly_at(P, _phys_points(O.P2_TRI, coords[cl[:3]])) for cl in cells])
+    verts = [[Fr(float(v)) for v in p] for p in coords]
+    c = 0.375
+
+    def local(Xs):
+        V = Xs[:3]
+        K = X.stiffness(V, "p2", X.coef_poly(V, P))
+        M_ = X.mass(V, "p2")
+        return [[K[a][b] + Fr(c) * M_[a][b] for b in range(6)] for a in range(6)]
+
+    dok = X.assemble_dok([list(map(int, cl)) for cl in cells], verts, local)
+    res = O.assemble_bilinear(O.P2_TRI, cells, coords, kq, O.PER_QP, c)
+    keys = sorted(dok)
+    assert list(zip(res.rows_of().tolist(), res.col.tolist())) == keys
+    want = np.array([float(dok[k]) for k in keys])
+    assert np.allclose(res.val, want, rtol=1e-13, atol=1e-13 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("el,kind,d,deg", [(O.P2_TRI, "p2", 2, 2), (O.P1_TRI, "p1", 2, 1), (O.P1_TET, "p1", 3, 1)])
+def test_per_point_load_matches_exact_integral(el, kind, d, deg):
+    # F_a = int f phi_a with f a polynomial of degree deg sampled at the points
+    # (integrand degree deg + basis degree = the rule's degree)
+    g = np.random.default_rng(33)
+    for _ in range(4):
+        V = _dyadic_simplex(g, d)
+        P = _rand_poly(g, d, deg)
+        fq = _poly_at(P, _phys_points(el, V))
+        Fe = np.array(X.load_poly(V, kind, X.coef_poly(V, P)), dtype=float)
+        Vf = np.array(V, dtype=float)
+        if kind == "p2":
+            coords = np.vstack([Vf, (Vf[0] + Vf[1]) / 2, (Vf[1] + Vf[2]) / 2, (Vf[2] + Vf[0]) / 2])
+        else:
+            coords = Vf
+        cells = np.arange(coords.shape[0])[None, :]
+        Fo = O.assemble_load(el, cells, coords, fq, O.PER_QP)
+        assert np.allclose(Fo, Fe, rtol=1e-13, atol=1e-14 * np.abs(Fe).max())
+
+
+def test_elasticity_per_point_lame_matches_exact():
+    # P1 gradients are constant, so K depends on int lambda and int mu only:
+    # |e| B^T D(mean lambda, mean mu) B in the Voigt form.  lambda and mu
+    # linear in x (the 4-point rule has degree 2), sampled at the points of
+    # each element of a small Kuhn mesh, in the per-QP layout [e * 4 + q].
+    t = mg.kuhn_tet_grid(2)
+    g = np.random.default_rng(34)
+    PL, PM = _rand_poly(g, 3, 1), _rand_poly(g, 3, 1)
+    PM[(0, 0, 0)] = Fr(2)
+    lq = np.concatenate([_poly_at(PL, _phys_points(O.P1_TET, t.coords[cl])) for cl in t.cells])
+    mq = np.concatenate([_poly_at(PM, _phys_points(O.P1_TET, t.coords[cl])) for cl in t.cells])
+    verts = [[Fr(float(v)) for v in p] for p in t.coords]
+
+    def local(Xs):
+        return X.elasticity(Xs, X.mean_over(Xs, PL), X.mean_over(Xs, PM))
+
+    dok = X.assemble_dok([list(map(int, cl)) for cl in t.cells], verts, local, ndof_per_node=3)
+    res = O.assemble_elasticity(t.cells, t.coords, lq, mq, O.PER_QP)
+    keys = sorted(dok)
+    assert list(zip(res.rows_of().tolist(), res.col.tolist())) == keys
+    want = np.array([float(dok[k]) for k in keys])
+    assert np.allclose(res.val, want, rtol=1e-12, atol=1e-13 * np.abs(want).max())
+    # lambda and mu exchanged give another matrix
+    sw = O.assemble_elasticity(t.cells, t.coords, mq, lq, O.PER_QP)
+    assert np.abs(sw.val - want).max() > 1e-6 * np.abs(want).max()
