@@ -322,6 +322,15 @@ tg_status tg_spmv(const tg_pattern* p, tg_dtype dtype, const void* vals, const v
 tg_status tg_csr_outer(const tg_pattern* p, tg_dtype dtype, const void* lam, const void* U, double alpha, void* out,
                        tg_stream stream);
 
+/* out[i] = alpha * x[i] on the rows where dirichlet[i] == 0 (uint8 [n], or
+ * NULL for none) and out[i] = 0 on the others; out may be x itself.  The
+ * adjoint relations of Eq. (adj) carry signs (dGamma/dF = -lam) and the
+ * condensed system of SM B.1 drops the Dirichlet rows: this call applies
+ * both to an upstream gradient before it enters the assembly backward
+ * calls.  n = 0 does nothing. */
+tg_status tg_scale_masked(tg_dtype dtype, const void* x, const uint8_t* dirichlet, double alpha, void* out,
+                          int64_t n, tg_stream stream);
+
 /* Conjugate gradients on K x = F restricted to the rows/columns where
  * dirichlet[i] == 0 (uint8 [n_rows], or NULL for none); entries of x on
  * Dirichlet rows are set to 0.  x holds the initial guess on entry.

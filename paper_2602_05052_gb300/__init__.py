@@ -10,7 +10,7 @@ from .binding import (CONSTANT, DIM, F32, F64, NQ, NV, P1_TET, P1_TET_VEC3, P1_T
                       tg_assemble_bilinear_atomic, tg_assemble_elasticity, tg_assemble_facets, tg_build_facets, tg_assemble_elasticity_backward,
                       tg_assemble_load, tg_assemble_load_backward, tg_assemble_system, tg_batch_assemble,
                       tg_batch_autotune, tg_batch_create, tg_batch_set_schedule, tg_build_pattern, tg_cg_solve, tg_cg_solve_noalloc,
-                      tg_csr_outer,
+                      tg_csr_outer, tg_scale_masked,
                       tg_diag_fma_rate, tg_diag_wait_timeout, tg_reaction_points, tg_residual, tg_semilinear_residual, tg_get_device_status, tg_quadrature, tg_spmv)
 
 __all__ = [n for n in dir() if n.startswith("tg_")] + [

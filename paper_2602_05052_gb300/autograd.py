@@ -97,7 +97,7 @@ class _SolveAssembled(torch.autograd.Function):
         p = ctx.p
         lam, _, _ = B.tg_cg_solve(p, vals, gu.contiguous(), ctx.dirichlet, rtol=ctx.rtol, maxit=ctx.maxit)
         # Eq. (adj) with lam_adj = -lam: dGamma/dK = -lam u^T, dGamma/dF = lam
-        neg = -lam
+        neg = B.tg_scale_masked(lam, -1.0)
         gk, gx, _ = B.tg_assemble_backward(p, coords, kappa, ctx.layout, 0.0, lam=neg, U=u,
                                            grad_kappa=ctx.needs_input_grad[1], grad_coords=True, grad_c=False)
         # accumulate adds into both outputs: grad_f starts from zero
@@ -127,9 +127,9 @@ class _Residual(torch.autograd.Function):
     def backward(ctx, gy):
         coords, kappa, x, f = ctx.saved_tensors
         p = ctx.p
-        g = gy.contiguous()
-        if ctx.dirichlet is not None:
-            g = g.masked_fill(ctx.dirichlet.bool(), 0.0)
+        # the upstream gradient restricted to the free rows (the Dirichlet
+        # rows of y are zero whatever x is)
+        g = B.tg_scale_masked(gy.contiguous(), 1.0, ctx.dirichlet)
         need_x, need_k, need_f = ctx.needs_input_grad[2], ctx.needs_input_grad[1], ctx.needs_input_grad[3]
         need_c = ctx.needs_input_grad[0]
         gx_in = None
@@ -145,7 +145,7 @@ class _Residual(torch.autograd.Function):
         gf = None
         if ctx.has_f and (need_f or need_c):
             # accumulate adds into both outputs: grad_f starts from zero
-            gf, _ = B.tg_assemble_load_backward(p, coords, f, ctx.f_layout, 1, -g,
+            gf, _ = B.tg_assemble_load_backward(p, coords, f, ctx.f_layout, 1, B.tg_scale_masked(g, -1.0),
                                                 grad_f=torch.zeros_like(f) if need_f else False,
                                                 grad_coords=gc if need_c else False, accumulate=True)
         if need_c and ctx.reaction is not None:

@@ -77,6 +77,7 @@ def lib():
         "tg_facets_destroy": (None, [vp]),
         "tg_spmv": (i32, [vp, i32, vp, vp, vp, vp]),
         "tg_csr_outer": (i32, [vp, i32, vp, vp, dbl, vp, vp]),
+        "tg_scale_masked": (i32, [i32, vp, vp, dbl, vp, i64, vp]),
         "tg_cg_solve": (i32, [vp, i32, vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl), vp]),
         "tg_cg_solve_noalloc": (i32, [vp, i32, vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl), vp]),
         "tg_batch_create": (i32, [C.POINTER(vp), i32, C.POINTER(vp)]),
@@ -115,16 +116,44 @@ def _dt(t: torch.Tensor) -> int:
     raise TypeError(f"unsupported dtype {t.dtype}")
 
 
-def _ptr(t, dtype=None, name="tensor"):
+def _ptr(t, dtype=None, name="tensor", n=None):
+    """Raw device pointer of a tensor argument after checking it: a
+    contiguous CUDA tensor of the expected dtype on the current device, with
+    exactly n elements when n is given (the library reads and writes raw
+    pointers, so a short or misplaced buffer must be refused here)."""
     if t is None:
         return None
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on {t.device}, the current device is cuda:{torch.cuda.current_device()}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     if dtype is not None and t.dtype != dtype:
         raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
     return C.c_void_p(t.data_ptr())
+
+
+def _n_x(p):
+    """Elements of the coordinate array of pattern p's mesh: [N][d]."""
+    return p.n_nodes * DIM[p.el]
+
+
+def _n_coef(p, layout, ncomp=1, n_per_elem=None, per_node=True):
+    """Elements of a coefficient array of the given layout on pattern p
+    (None for a layout the library rejects itself: PER_NODE where only
+    per_node=True admits it, or an unknown value)."""
+    if layout == PER_QP:
+        return p.n_elems * (n_per_elem or NQ[p.el]) * ncomp
+    if layout == PER_ELEMENT:
+        return p.n_elems * ncomp
+    if layout == PER_NODE and per_node:
+        return p.n_nodes * ncomp
+    if layout == CONSTANT:
+        return ncomp
+    return None
 
 
 def _out(arg, make):
@@ -219,9 +248,9 @@ def tg_assemble_bilinear(p: Pattern, coords, kappa, layout: int, c: float = 0.0,
     if vals_out is None:
         vals_out = torch.empty(p.nnz, dtype=coords.dtype, device=coords.device)
     dt = _dt(coords)
-    _check(lib().tg_assemble_bilinear(p.handle, dt, _ptr(coords, coords.dtype, "coords"),
-                                      _ptr(kappa, coords.dtype, "kappa"), layout, float(c),
-                                      _ptr(vals_out, coords.dtype, "vals_out"), _stream(stream)),
+    _check(lib().tg_assemble_bilinear(p.handle, dt, _ptr(coords, coords.dtype, "coords", _n_x(p)),
+                                      _ptr(kappa, coords.dtype, "kappa", _n_coef(p, layout, per_node=False)), layout, float(c),
+                                      _ptr(vals_out, coords.dtype, "vals_out", p.nnz), _stream(stream)),
            "tg_assemble_bilinear")
     return vals_out
 
@@ -229,9 +258,10 @@ def tg_assemble_bilinear(p: Pattern, coords, kappa, layout: int, c: float = 0.0,
 def tg_assemble_bilinear_atomic(p: Pattern, coords, kappa, layout: int, c: float = 0.0, vals_out=None, stream=None):
     if vals_out is None:
         vals_out = torch.empty(p.nnz, dtype=coords.dtype, device=coords.device)
-    _check(lib().tg_assemble_bilinear_atomic(p.handle, _dt(coords), _ptr(coords, coords.dtype, "coords"),
-                                             _ptr(kappa, coords.dtype, "kappa"), layout, float(c),
-                                             _ptr(vals_out, coords.dtype, "vals_out"), _stream(stream)),
+    _check(lib().tg_assemble_bilinear_atomic(p.handle, _dt(coords), _ptr(coords, coords.dtype, "coords", _n_x(p)),
+                                             _ptr(kappa, coords.dtype, "kappa", _n_coef(p, layout, per_node=False)), layout,
+                                             float(c), _ptr(vals_out, coords.dtype, "vals_out", p.nnz),
+                                             _stream(stream)),
            "tg_assemble_bilinear_atomic")
     return vals_out
 
@@ -239,9 +269,10 @@ def tg_assemble_bilinear_atomic(p: Pattern, coords, kappa, layout: int, c: float
 def tg_assemble_elasticity(p: Pattern, coords, lam, mu, layout: int, vals_out=None, stream=None):
     if vals_out is None:
         vals_out = torch.empty(p.nnz, dtype=coords.dtype, device=coords.device)
-    _check(lib().tg_assemble_elasticity(p.handle, _dt(coords), _ptr(coords, coords.dtype, "coords"),
-                                        _ptr(lam, coords.dtype, "lam"), _ptr(mu, coords.dtype, "mu"), layout,
-                                        _ptr(vals_out, coords.dtype, "vals_out"), _stream(stream)),
+    _check(lib().tg_assemble_elasticity(p.handle, _dt(coords), _ptr(coords, coords.dtype, "coords", _n_x(p)),
+                                        _ptr(lam, coords.dtype, "lam", _n_coef(p, layout, per_node=False)),
+                                        _ptr(mu, coords.dtype, "mu", _n_coef(p, layout, per_node=False)), layout,
+                                        _ptr(vals_out, coords.dtype, "vals_out", p.nnz), _stream(stream)),
            "tg_assemble_elasticity")
     return vals_out
 
@@ -249,9 +280,10 @@ def tg_assemble_elasticity(p: Pattern, coords, lam, mu, layout: int, vals_out=No
 def tg_assemble_load(p: Pattern, coords, f, layout: int, ncomp: int = 1, F_out=None, stream=None):
     if F_out is None:
         F_out = torch.empty(p.n_nodes * ncomp, dtype=coords.dtype, device=coords.device)
-    _check(lib().tg_assemble_load(p.handle, _dt(coords), _ptr(coords, coords.dtype, "coords"),
-                                  _ptr(f, coords.dtype, "f"), layout, int(ncomp), _ptr(F_out, coords.dtype, "F_out"),
-                                  _stream(stream)), "tg_assemble_load")
+    _check(lib().tg_assemble_load(p.handle, _dt(coords), _ptr(coords, coords.dtype, "coords", _n_x(p)),
+                                  _ptr(f, coords.dtype, "f", _n_coef(p, layout, ncomp)), layout, int(ncomp),
+                                  _ptr(F_out, coords.dtype, "F_out", p.n_nodes * ncomp), _stream(stream)),
+           "tg_assemble_load")
     return F_out
 
 
@@ -261,9 +293,11 @@ def tg_assemble_system(p: Pattern, coords, kappa, kappa_layout: int, c: float, f
     dt = coords.dtype
     vals = _out(vals, lambda: torch.empty(p.nnz, dtype=dt, device=coords.device))
     F = _out(F, lambda: torch.empty(p.n_nodes, dtype=dt, device=coords.device))
-    _check(lib().tg_assemble_system(p.handle, _dt(coords), _ptr(coords, dt, "coords"), _ptr(kappa, dt, "kappa"),
-                                    kappa_layout, float(c), _ptr(f, dt, "f"), f_layout, _ptr(vals, dt, "vals"),
-                                    _ptr(F, dt, "F"), _stream(stream)), "tg_assemble_system")
+    _check(lib().tg_assemble_system(p.handle, _dt(coords), _ptr(coords, dt, "coords", _n_x(p)),
+                                    _ptr(kappa, dt, "kappa", _n_coef(p, kappa_layout, per_node=False)), kappa_layout, float(c),
+                                    _ptr(f, dt, "f", _n_coef(p, f_layout)), f_layout,
+                                    _ptr(vals, dt, "vals", p.nnz), _ptr(F, dt, "F", p.n_nodes), _stream(stream)),
+           "tg_assemble_system")
     return vals, F
 
 
@@ -275,10 +309,13 @@ def tg_assemble_backward(p: Pattern, coords, kappa, layout: int, c: float = 0.0,
     gk = _out(grad_kappa, lambda: torch.empty_like(kappa))
     gx = _out(grad_coords, lambda: torch.empty_like(coords))
     gc = _out(grad_c, lambda: torch.empty(1, dtype=dt, device=dev))
-    _check(lib().tg_assemble_backward(p.handle, _dt(coords), _ptr(coords, dt, "coords"), _ptr(kappa, dt, "kappa"),
-                                      layout, float(c), _ptr(grad_vals, dt, "grad_vals"), _ptr(lam, dt, "lam"),
-                                      _ptr(U, dt, "U"), _ptr(gk, dt, "grad_kappa"), _ptr(gx, dt, "grad_coords"),
-                                      _ptr(gc, dt, "grad_c"), _stream(stream)), "tg_assemble_backward")
+    nk = _n_coef(p, layout, per_node=False)
+    _check(lib().tg_assemble_backward(p.handle, _dt(coords), _ptr(coords, dt, "coords", _n_x(p)),
+                                      _ptr(kappa, dt, "kappa", nk), layout, float(c),
+                                      _ptr(grad_vals, dt, "grad_vals", p.nnz), _ptr(lam, dt, "lam", p.n_rows),
+                                      _ptr(U, dt, "U", p.n_rows), _ptr(gk, dt, "grad_kappa", nk),
+                                      _ptr(gx, dt, "grad_coords", _n_x(p)), _ptr(gc, dt, "grad_c", 1),
+                                      _stream(stream)), "tg_assemble_backward")
     return gk, gx, gc
 
 
@@ -288,9 +325,12 @@ def tg_assemble_load_backward(p: Pattern, coords, f, layout: int, ncomp: int, gr
     dt = coords.dtype
     gf = _out(grad_f, lambda: torch.empty_like(f))
     gx = _out(grad_coords, lambda: torch.empty_like(coords))
-    _check(lib().tg_assemble_load_backward(p.handle, _dt(coords), _ptr(coords, dt, "coords"), _ptr(f, dt, "f"), layout,
-                                           int(ncomp), _ptr(grad_F, dt, "grad_F"), _ptr(gf, dt, "grad_f"),
-                                           _ptr(gx, dt, "grad_coords"), int(bool(accumulate)), _stream(stream)),
+    nf = _n_coef(p, layout, ncomp)
+    _check(lib().tg_assemble_load_backward(p.handle, _dt(coords), _ptr(coords, dt, "coords", _n_x(p)),
+                                           _ptr(f, dt, "f", nf), layout, int(ncomp),
+                                           _ptr(grad_F, dt, "grad_F", p.n_nodes * ncomp), _ptr(gf, dt, "grad_f", nf),
+                                           _ptr(gx, dt, "grad_coords", _n_x(p)), int(bool(accumulate)),
+                                           _stream(stream)),
            "tg_assemble_load_backward")
     return gf, gx
 
@@ -302,11 +342,13 @@ def tg_assemble_elasticity_backward(p: Pattern, coords, lam, mu, layout: int, gr
     gl = _out(grad_lam, lambda: torch.empty_like(lam))
     gm = _out(grad_mu, lambda: torch.empty_like(mu))
     gx = _out(grad_coords, lambda: torch.empty_like(coords))
-    _check(lib().tg_assemble_elasticity_backward(p.handle, _dt(coords), _ptr(coords, dt, "coords"), _ptr(lam, dt, "lam"),
-                                                 _ptr(mu, dt, "mu"), layout, _ptr(grad_vals, dt, "grad_vals"),
-                                                 _ptr(lam_adj, dt, "lam_adj"), _ptr(U, dt, "U"),
-                                                 _ptr(gl, dt, "grad_lam"), _ptr(gm, dt, "grad_mu"),
-                                                 _ptr(gx, dt, "grad_coords"), _stream(stream)),
+    nc = _n_coef(p, layout, per_node=False)
+    _check(lib().tg_assemble_elasticity_backward(p.handle, _dt(coords), _ptr(coords, dt, "coords", _n_x(p)),
+                                                 _ptr(lam, dt, "lam", nc), _ptr(mu, dt, "mu", nc), layout,
+                                                 _ptr(grad_vals, dt, "grad_vals", p.nnz),
+                                                 _ptr(lam_adj, dt, "lam_adj", p.n_rows), _ptr(U, dt, "U", p.n_rows),
+                                                 _ptr(gl, dt, "grad_lam", nc), _ptr(gm, dt, "grad_mu", nc),
+                                                 _ptr(gx, dt, "grad_coords", _n_x(p)), _stream(stream)),
            "tg_assemble_elasticity_backward")
     return gl, gm, gx
 
@@ -318,10 +360,11 @@ def tg_residual(p: Pattern, coords, kappa, layout: int, c: float, x, f=None, f_l
     if y is None:
         y = torch.empty_like(x)
     ls = _out(loss, lambda: torch.empty(1, dtype=dt, device=coords.device))
-    _check(lib().tg_residual(p.handle, _dt(coords), _ptr(coords, dt, "coords"), _ptr(kappa, dt, "kappa"), layout,
-                             float(c), _ptr(x, dt, "x"), _ptr(f, dt, "f"), f_layout,
-                             _ptr(dirichlet, torch.uint8, "dirichlet"), _ptr(y, dt, "y"), _ptr(ls, dt, "loss"),
-                             _stream(stream)), "tg_residual")
+    _check(lib().tg_residual(p.handle, _dt(coords), _ptr(coords, dt, "coords", _n_x(p)),
+                             _ptr(kappa, dt, "kappa", _n_coef(p, layout, per_node=False)), layout, float(c),
+                             _ptr(x, dt, "x", p.n_nodes), _ptr(f, dt, "f", _n_coef(p, f_layout)), f_layout,
+                             _ptr(dirichlet, torch.uint8, "dirichlet", p.n_nodes), _ptr(y, dt, "y", p.n_nodes),
+                             _ptr(ls, dt, "loss", 1), _stream(stream)), "tg_residual")
     return y, ls
 
 
@@ -334,10 +377,12 @@ def tg_semilinear_residual(p: Pattern, coords, kappa, layout: int, c: float, x, 
         y = torch.empty_like(x)
     ls = _out(loss, lambda: torch.empty(1, dtype=dt, device=coords.device))
     r = (dbl * 4)(*[float(v) for v in reaction])
-    _check(lib().tg_semilinear_residual(p.handle, _dt(coords), _ptr(coords, dt, "coords"), _ptr(kappa, dt, "kappa"),
-                                        layout, float(c), _ptr(x, dt, "x"), _ptr(f, dt, "f"), f_layout, r,
-                                        _ptr(x_react, dt, "x_react"), _ptr(dirichlet, torch.uint8, "dirichlet"),
-                                        _ptr(y, dt, "y"), _ptr(ls, dt, "loss"), _stream(stream)),
+    _check(lib().tg_semilinear_residual(p.handle, _dt(coords), _ptr(coords, dt, "coords", _n_x(p)),
+                                        _ptr(kappa, dt, "kappa", _n_coef(p, layout, per_node=False)), layout, float(c),
+                                        _ptr(x, dt, "x", p.n_nodes), _ptr(f, dt, "f", _n_coef(p, f_layout)),
+                                        f_layout, r, _ptr(x_react, dt, "x_react", p.n_nodes),
+                                        _ptr(dirichlet, torch.uint8, "dirichlet", p.n_nodes),
+                                        _ptr(y, dt, "y", p.n_nodes), _ptr(ls, dt, "loss", 1), _stream(stream)),
            "tg_semilinear_residual")
     return y, ls
 
@@ -346,9 +391,10 @@ def tg_assemble_simp(p: Pattern, coords, rho, e_min: float, e_max: float, penal:
                      stream=None):
     if vals_out is None:
         vals_out = torch.empty(p.nnz, dtype=coords.dtype, device=coords.device)
-    _check(lib().tg_assemble_simp(p.handle, _dt(coords), _ptr(coords, coords.dtype, "coords"),
-                                  _ptr(rho, coords.dtype, "rho"), float(e_min), float(e_max), float(penal), float(nu),
-                                  _ptr(vals_out, coords.dtype, "vals"), _stream(stream)), "tg_assemble_simp")
+    _check(lib().tg_assemble_simp(p.handle, _dt(coords), _ptr(coords, coords.dtype, "coords", _n_x(p)),
+                                  _ptr(rho, coords.dtype, "rho", p.n_elems), float(e_min), float(e_max), float(penal),
+                                  float(nu), _ptr(vals_out, coords.dtype, "vals", p.nnz), _stream(stream)),
+           "tg_assemble_simp")
     return vals_out
 
 
@@ -356,10 +402,11 @@ def tg_simp_sensitivity(p: Pattern, coords, rho, e_min: float, e_max: float, pen
                         stream=None):
     if dc_out is None:
         dc_out = torch.empty_like(rho)
-    _check(lib().tg_simp_sensitivity(p.handle, _dt(coords), _ptr(coords, coords.dtype, "coords"),
-                                     _ptr(rho, coords.dtype, "rho"), float(e_min), float(e_max), float(penal),
-                                     float(nu), _ptr(u, coords.dtype, "u"), _ptr(dc_out, coords.dtype, "dc"),
-                                     _stream(stream)), "tg_simp_sensitivity")
+    _check(lib().tg_simp_sensitivity(p.handle, _dt(coords), _ptr(coords, coords.dtype, "coords", _n_x(p)),
+                                     _ptr(rho, coords.dtype, "rho", p.n_elems), float(e_min), float(e_max),
+                                     float(penal), float(nu), _ptr(u, coords.dtype, "u", p.n_rows),
+                                     _ptr(dc_out, coords.dtype, "dc", p.n_elems), _stream(stream)),
+           "tg_simp_sensitivity")
     return dc_out
 
 
@@ -368,8 +415,9 @@ def tg_reaction_points(p: Pattern, x, reaction, out=None, stream=None):
     if out is None:
         out = torch.empty(p.n_elems * NQ[p.el], dtype=x.dtype, device=x.device)
     r = (dbl * 4)(*[float(v) for v in reaction])
-    _check(lib().tg_reaction_points(p.handle, _dt(x), _ptr(x, x.dtype, "x"), r, _ptr(out, x.dtype, "out"),
-                                    _stream(stream)), "tg_reaction_points")
+    _check(lib().tg_reaction_points(p.handle, _dt(x), _ptr(x, x.dtype, "x", p.n_nodes), r,
+                                    _ptr(out, x.dtype, "out", p.n_elems * NQ[p.el]), _stream(stream)),
+           "tg_reaction_points")
     return out
 
 
@@ -407,25 +455,42 @@ def tg_assemble_facets(fc: Facets, coords, alpha=None, alpha_layout: int = CONST
                        vals=None, F=None, stream=None):
     """Adds the Robin matrix term to vals and the facet load to F (in place)."""
     dt = coords.dtype
-    _check(lib().tg_assemble_facets(fc.handle, _dt(coords), _ptr(coords, dt, "coords"), _ptr(alpha, dt, "alpha"),
-                                    alpha_layout, _ptr(g, dt, "g"), g_layout, _ptr(vals, dt, "vals"), _ptr(F, dt, "F"),
-                                    _stream(stream)), "tg_assemble_facets")
+    p, nqf = fc.pattern, DIM[fc.pattern.el]  # points per facet: 2 on an edge, 3 on a face
+    n_fc = lambda lay: (fc.n_facets * nqf if lay == PER_QP else fc.n_facets if lay == PER_ELEMENT
+                        else p.n_nodes if lay == PER_NODE else 1 if lay == CONSTANT else None)
+    _check(lib().tg_assemble_facets(fc.handle, _dt(coords), _ptr(coords, dt, "coords", _n_x(p)),
+                                    _ptr(alpha, dt, "alpha", n_fc(alpha_layout)), alpha_layout,
+                                    _ptr(g, dt, "g", n_fc(g_layout)), g_layout, _ptr(vals, dt, "vals", p.nnz),
+                                    _ptr(F, dt, "F", p.n_nodes), _stream(stream)), "tg_assemble_facets")
     return vals, F
 
 
 def tg_csr_outer(p: Pattern, lam, U, alpha: float = 1.0, out=None, stream=None):
     if out is None:
         out = torch.empty(p.nnz, dtype=lam.dtype, device=lam.device)
-    _check(lib().tg_csr_outer(p.handle, _dt(lam), _ptr(lam, lam.dtype, "lam"), _ptr(U, lam.dtype, "U"), float(alpha),
-                              _ptr(out, lam.dtype, "out"), _stream(stream)), "tg_csr_outer")
+    _check(lib().tg_csr_outer(p.handle, _dt(lam), _ptr(lam, lam.dtype, "lam", p.n_rows),
+                              _ptr(U, lam.dtype, "U", p.n_rows), float(alpha), _ptr(out, lam.dtype, "out", p.nnz),
+                              _stream(stream)), "tg_csr_outer")
+    return out
+
+
+def tg_scale_masked(x, alpha: float = 1.0, dirichlet=None, out=None, stream=None):
+    """alpha * x with zeros on the rows where dirichlet != 0 (out may be x)."""
+    if out is None:
+        out = torch.empty_like(x)
+    n = x.numel()
+    _check(lib().tg_scale_masked(_dt(x), _ptr(x, x.dtype, "x"), _ptr(dirichlet, torch.uint8, "dirichlet", n),
+                                 float(alpha), _ptr(out, x.dtype, "out", n), n, _stream(stream)),
+           "tg_scale_masked")
     return out
 
 
 def tg_spmv(p: Pattern, vals, x, y=None, stream=None):
     if y is None:
         y = torch.empty(p.n_rows, dtype=vals.dtype, device=vals.device)
-    _check(lib().tg_spmv(p.handle, _dt(vals), _ptr(vals, vals.dtype, "vals"), _ptr(x, vals.dtype, "x"),
-                         _ptr(y, vals.dtype, "y"), _stream(stream)), "tg_spmv")
+    _check(lib().tg_spmv(p.handle, _dt(vals), _ptr(vals, vals.dtype, "vals", p.nnz),
+                         _ptr(x, vals.dtype, "x", p.n_rows), _ptr(y, vals.dtype, "y", p.n_rows), _stream(stream)),
+           "tg_spmv")
     return y
 
 
@@ -433,9 +498,10 @@ def tg_cg_solve(p: Pattern, vals, F, dirichlet=None, x=None, rtol: float = 1e-10
     if x is None:
         x = torch.zeros(p.n_rows, dtype=vals.dtype, device=vals.device)
     it, rr = i32(), dbl()
-    _check(lib().tg_cg_solve(p.handle, _dt(vals), _ptr(vals, vals.dtype, "vals"), _ptr(F, vals.dtype, "F"),
-                             _ptr(dirichlet, torch.uint8, "dirichlet"), _ptr(x, vals.dtype, "x"), float(rtol),
-                             int(maxit), C.byref(it), C.byref(rr), _stream(stream)), "tg_cg_solve")
+    _check(lib().tg_cg_solve(p.handle, _dt(vals), _ptr(vals, vals.dtype, "vals", p.nnz),
+                             _ptr(F, vals.dtype, "F", p.n_rows), _ptr(dirichlet, torch.uint8, "dirichlet", p.n_rows),
+                             _ptr(x, vals.dtype, "x", p.n_rows), float(rtol), int(maxit), C.byref(it), C.byref(rr),
+                             _stream(stream)), "tg_cg_solve")
     return x, it.value, rr.value
 
 
@@ -449,9 +515,11 @@ def tg_cg_solve_noalloc(p: Pattern, vals, F, dirichlet=None, x=None, rtol: float
     if x is None:
         x = torch.zeros(p.n_rows, dtype=vals.dtype, device=vals.device)
     it, rr = i32(), dbl()
-    _check(lib().tg_cg_solve_noalloc(p.handle, _dt(vals), _ptr(vals, vals.dtype, "vals"), _ptr(F, vals.dtype, "F"),
-                                     _ptr(dirichlet, torch.uint8, "dirichlet"), _ptr(x, vals.dtype, "x"),
-                                     float(rtol), int(maxit), C.byref(it), C.byref(rr), _stream(stream)),
+    _check(lib().tg_cg_solve_noalloc(p.handle, _dt(vals), _ptr(vals, vals.dtype, "vals", p.nnz),
+                                     _ptr(F, vals.dtype, "F", p.n_rows),
+                                     _ptr(dirichlet, torch.uint8, "dirichlet", p.n_rows),
+                                     _ptr(x, vals.dtype, "x", p.n_rows), float(rtol), int(maxit), C.byref(it),
+                                     C.byref(rr), _stream(stream)),
            "tg_cg_solve_noalloc")
     return x, it.value, rr.value
 
@@ -481,16 +549,25 @@ def tg_batch_create(pats: list[Pattern]) -> Batch:
     return Batch(h, list(pats))
 
 
-def _ptr_array(ts, dtype, name):
-    return (vp * len(ts))(*[_ptr(t, dtype, name) for t in ts])
+def _ptr_array(ts, dtype, name, sizes=None):
+    if sizes is not None and len(sizes) != len(ts):
+        raise ValueError(f"{name}: {len(ts)} tensors for {len(sizes)} instances")
+    return (vp * len(ts))(*[_ptr(t, dtype, f"{name}[{k}]", None if sizes is None else sizes[k])
+                            for k, t in enumerate(ts)])
+
+
+def _batch_sizes(b: Batch, layout: int):
+    """Expected element counts of every instance's coords, kappa and values."""
+    return ([_n_x(q) for q in b.pats], [_n_coef(q, layout, per_node=False) for q in b.pats], [q.nnz for q in b.pats])
 
 
 def tg_batch_assemble(b: Batch, coords: list, kappa: list, layout: int, c: list, vals_out: list, stream=None):
     dt = coords[0].dtype
     n = len(coords)
-    _check(lib().tg_batch_assemble(b.handle, _dt(coords[0]), _ptr_array(coords, dt, "coords"),
-                                   _ptr_array(kappa, dt, "kappa"), layout, (dbl * n)(*map(float, c)),
-                                   _ptr_array(vals_out, dt, "vals_out"), _stream(stream)), "tg_batch_assemble")
+    nx, nk, nv = _batch_sizes(b, layout)
+    _check(lib().tg_batch_assemble(b.handle, _dt(coords[0]), _ptr_array(coords, dt, "coords", nx),
+                                   _ptr_array(kappa, dt, "kappa", nk), layout, (dbl * n)(*map(float, c)),
+                                   _ptr_array(vals_out, dt, "vals_out", nv), _stream(stream)), "tg_batch_assemble")
     return vals_out
 
 
@@ -503,9 +580,11 @@ def tg_batch_autotune(b: Batch, coords: list, kappa: list, layout: int, c: list,
     dt = coords[0].dtype
     n = len(coords)
     ms = C.c_float()
-    _check(lib().tg_batch_autotune(b.handle, _dt(coords[0]), _ptr_array(coords, dt, "coords"),
-                                   _ptr_array(kappa, dt, "kappa"), layout, (dbl * n)(*map(float, c)),
-                                   _ptr_array(vals_out, dt, "vals_out"), int(reps), C.byref(ms), _stream(stream)),
+    nx, nk, nv = _batch_sizes(b, layout)
+    _check(lib().tg_batch_autotune(b.handle, _dt(coords[0]), _ptr_array(coords, dt, "coords", nx),
+                                   _ptr_array(kappa, dt, "kappa", nk), layout, (dbl * n)(*map(float, c)),
+                                   _ptr_array(vals_out, dt, "vals_out", nv), int(reps), C.byref(ms),
+                                   _stream(stream)),
            "tg_batch_autotune")
     return ms.value
 

@@ -23,7 +23,7 @@
 // order by a second kernel.  Everything is deterministic.
 #include <cstdint>
 
-#include "blocks.cuh"
+#include "fan.cuh"
 
 namespace {
 
@@ -416,34 +416,40 @@ __device__ __forceinline__ bool bwd_p1_element(const T (&x)[D + 1][D], const T (
   return true;
 }
 
-// P1 backward over element-once row blocks (blocks.cuh).  Each distinct
-// element of a block gathers its upstream weights W (through row_ptr and
-// the element's packed column positions, or from lam and U) and computes
-// the coordinate-gradient contributions of all its vertices into
-// Gx[NV*D][capE]; the block that owns the element also writes its
-// coefficient gradient and adds its dL/dc term.  Rows then sum their
-// incidences' contributions in increasing element order.  Per-CTA FP64
-// partials of the global sums are reduced by k_backward_final.
-template <int D, typename T, bool FUSED, int UB>
-__global__ void __launch_bounds__(BB, (D == 2 && sizeof(T) == 4) ? (UB >= 3 ? 5 : 6) : 2) k_backward_blk(const BwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
-                                                     const tg::BlkArgs g, const uint64_t* __restrict__ elem_pos,
-                                                     const int32_t* __restrict__ row_ptr) {
+// Shared-memory layout of the Map's coordinate-gradient contributions: one
+// D-vector per (vertex c, element slot j), at Gx[(c * capE + j) * D]
+// (triangles: one 8- or 16-byte load per incidence in the Reduce).
+template <int D, typename T>
+__device__ __forceinline__ void gx_store(T* Gx, int capE, int c, int j, const T (&g)[D]) {
+  T* q = Gx + ((size_t)c * capE + j) * D;
+  if constexpr (D == 2) {
+    *reinterpret_cast<typename tg::Vec2<T>::type*>(q) = {g[0], g[1]};
+  } else {
+#pragma unroll
+    for (int r = 0; r < D; ++r) q[r] = g[r];
+  }
+}
+
+// The Map of the P1 backward over one block (any view with nbe, be[] and
+// vtx(c, k)).  Each distinct element of the block gathers its upstream
+// weights W (through row_ptr and the element's packed column positions, or
+// from lam and U) and computes the coordinate-gradient contributions of all
+// its vertices into Gx (gx_store); the block that owns the element also
+// writes its coefficient gradient and adds its dL/dc and constant-kappa
+// terms to bc and bk.
+template <int D, typename T, bool FUSED, int UB, typename View>
+__device__ __forceinline__ void bwd_blk_map(const BwdArgs<T>& a, const tg::RefTab<T>& tab, int capE, const View& v,
+                                            const uint64_t* __restrict__ elem_pos,
+                                            const int32_t* __restrict__ row_ptr, T* Gx, T& bc, T& bk) {
   constexpr int NV = D + 1, NQ = D == 2 ? 3 : 4;
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[2][BB / 32];
-  tg::BlkPipe pipe;
-  T* Gx = reinterpret_cast<T*>(pipe.init(smem, g));
-  __syncthreads();  // publishes the mbarrier initialisation
-  double pc = 0.0, pk = 0.0;
-  TG_BLK_PIPELINE_BEGIN(pipe, g, a.status)
-  T bc = T(0), bk = T(0);  // this thread's terms of the block, added to pc, pk once per block
-  for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * NT_) {
+  const int NT = blockDim.x;
+  for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * NT) {
     int e[UB], vid[UB][NV];
     bool own[UB];
 #pragma unroll
     for (int u = 0; u < UB; ++u) {
-      const bool live = j0 + u * NT_ < v.nbe;
-      const int j = live ? j0 + u * NT_ : 0;
+      const bool live = j0 + u * NT < v.nbe;
+      const int j = live ? j0 + u * NT : 0;
       const uint32_t w0 = v.be[j];
       e[u] = (int)tg::bel_elem(w0);
       own[u] = live && tg::bel_owner(w0);
@@ -493,7 +499,7 @@ __global__ void __launch_bounds__(BB, (D == 2 && sizeof(T) == 4) ? (UB >= 3 ? 5 
     }
 #pragma unroll
     for (int u = 0; u < UB; ++u) {
-      const int j = j0 + u * NT_;
+      const int j = j0 + u * NT;
       if (j >= v.nbe) continue;
       tg::Geom<D, T> gm;
       if constexpr (D == 2) tg::tri_geom_x(x[u][0], x[u][1], x[u][2], gm);
@@ -588,9 +594,29 @@ __global__ void __launch_bounds__(BB, (D == 2 && sizeof(T) == 4) ? (UB >= 3 ? 5 
 #pragma unroll
       for (int c = 0; c < NV; ++c)
 #pragma unroll
-        for (int r = 0; r < D; ++r) Gx[(c * D + r) * g.capE + j] = gx[c][r];
+        for (int r = 0; r < D; ++r) gx_store<D>(Gx, capE, c, j, gx[c]);
     }
   }
+}
+
+// P1 backward over element-once row blocks (blocks.cuh): the Map of
+// bwd_blk_map, then rows sum their incidences' contributions in increasing
+// element order.  Per-CTA FP64 partials of the global sums are added by the
+// last CTA to finish (finish_sums).
+template <int D, typename T, bool FUSED, int UB>
+__global__ void __launch_bounds__(BB, (D == 2 && sizeof(T) == 4) ? (UB >= 3 ? 5 : 6) : 2) k_backward_blk(const BwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
+                                                     const tg::BlkArgs g, const uint64_t* __restrict__ elem_pos,
+                                                     const int32_t* __restrict__ row_ptr) {
+  constexpr int NV = D + 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[2][BB / 32];
+  tg::BlkPipe pipe;
+  T* Gx = reinterpret_cast<T*>(pipe.init(smem, g));
+  __syncthreads();  // publishes the mbarrier initialisation
+  double pc = 0.0, pk = 0.0;
+  TG_BLK_PIPELINE_BEGIN(pipe, g, a.status)
+  T bc = T(0), bk = T(0);  // this thread's terms of the block, added to pc, pk once per block
+  bwd_blk_map<D, T, FUSED, UB>(a, tab, g.capE, v, elem_pos, row_ptr, Gx, bc, bk);
   pc += (double)bc;
   pk += (double)bk;
   __syncthreads();
@@ -603,9 +629,9 @@ __global__ void __launch_bounds__(BB, (D == 2 && sizeof(T) == 4) ? (UB >= 3 ? 5 
       const int je = v.ip[i + 1];
       for (int j = v.ip[i]; j < je; ++j) {
         const auto rr = tg::blk_rec<NV>(v.rc, j);
-        const T* gp = Gx + rr.a() * D * g.capE + rr.le();
+        const T* gp = Gx + ((size_t)rr.a() * g.capE + rr.le()) * D;
 #pragma unroll
-        for (int r = 0; r < D; ++r) gs[r] += gp[r * g.capE];
+        for (int r = 0; r < D; ++r) gs[r] += gp[r];
       }
 #pragma unroll
       for (int r = 0; r < D; ++r) a.grad_coords[(int64_t)v.pm[i] * D + r] = gs[r];
@@ -613,6 +639,45 @@ __global__ void __launch_bounds__(BB, (D == 2 && sizeof(T) == 4) ? (UB >= 3 ? 5 
   }
   __syncthreads();  // stage s and Gx are free again
   TG_BLK_PIPELINE_END
+  finish_sums(a, pc, pk, red);
+}
+
+// P1 triangle backward with the fan-ordered Reduce (fan.cuh): the same Map;
+// each row sums its fan triangles' contributions in fan order.
+template <typename T, bool FUSED, int UB>
+__global__ void __launch_bounds__(BB, sizeof(T) == 4 ? (UB >= 3 ? 5 : 6) : 2) k_backward_fan(
+    const BwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab, const tg::FanArgs g,
+    const uint64_t* __restrict__ elem_pos, const int32_t* __restrict__ row_ptr) {
+  using T2 = typename tg::Vec2<T>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[2][BB / 32];
+  tg::FanPipe pipe;
+  T* Gx = reinterpret_cast<T*>(pipe.init(smem, g));
+  __syncthreads();  // publishes the mbarrier initialisation
+  double pc = 0.0, pk = 0.0;
+  TG_FAN_PIPELINE_BEGIN(pipe, g, a.status)
+  T bc = T(0), bk = T(0);
+  bwd_blk_map<2, T, FUSED, UB>(a, tab, g.capE, v, elem_pos, row_ptr, Gx, bc, bk);
+  pc += (double)bc;
+  pk += (double)bk;
+  __syncthreads();
+  if (a.grad_coords) {
+    const int t = (int)threadIdx.x;
+    if (v.r0 + t < v.r1) {
+      const int deg = (int)(v.info[t] & 31u);
+      const T2* G2 = reinterpret_cast<const T2*>(Gx);
+      T gx0 = T(0), gx1 = T(0);
+      for (int k = 0; k < deg; ++k) {
+        const unsigned r = v.rec[k * v.rs + t];
+        const T2 q = G2[tg::fan_a(r) * g.capE + tg::fan_le(r)];
+        gx0 += q.x;
+        gx1 += q.y;
+      }
+      reinterpret_cast<T2*>(a.grad_coords)[v.pm[t]] = T2{gx0, gx1};
+    }
+  }
+  __syncthreads();  // stage s and Gx are free again
+  TG_FAN_PIPELINE_END
   finish_sums(a, pc, pk, red);
 }
 
@@ -789,6 +854,43 @@ tg_status launch_blk(const tg_pattern* p, const BwdArgs<T>& a, bool fused, int* 
                      cudaStream_t s) {
   *used = false;
   if (!p->bel || !p->elem_pos) return TG_OK;
+  if constexpr (D == 2) {
+    if (p->fan) {
+      const tg::FanArgs gf = tg::fan_args(p);
+      const size_t smem = tg::fan_stage_bytes(gf.R, gf.capF, gf.capE, 3) + (size_t)3 * 2 * gf.capE * sizeof(T);
+      if (smem <= 113 * 1024 && p->blk_rows <= BB) {
+        const tg::RefTab<T>& tab = tg::table<T>(p->el);
+        const int need = (p->blk_max_elems + BB - 1) / BB;
+        tg_status st = TG_OK;
+        auto go = [&](auto kern) {
+          if ((st = tg::set_smem((const void*)kern, smem)) != TG_OK) return;
+          int per_sm = 0;
+          cudaError_t ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BB, smem);
+          if (ce != cudaSuccess) {
+            st = tg::cuda_fail(ce, "cudaOccupancyMaxActiveBlocksPerMultiprocessor", __FILE__, __LINE__);
+            return;
+          }
+          const int64_t cap_ctas = (p->n_partials - 4) / kSlots;
+          const int grid =
+              (int)std::min<int64_t>({p->n_blk, (int64_t)std::max(per_sm, 1) * tg::sm_count(), cap_ctas});
+          kern<<<grid, BB, smem, s>>>(a, tab, gf, p->elem_pos, p->row_ptr);
+          *grid_out = grid;
+        };
+        if constexpr (sizeof(T) == 8) {
+          if (fused) go(k_backward_fan<T, true, 1>);
+          else go(k_backward_fan<T, false, 1>);
+        } else {
+          if (need >= 3 && !fused) go(k_backward_fan<T, false, 3>);
+          else if (fused) go(k_backward_fan<T, true, 2>);
+          else go(k_backward_fan<T, false, 2>);
+        }
+        if (st != TG_OK) return st;
+        TG_CK_LAUNCH("k_backward_fan");
+        *used = true;
+        return TG_OK;
+      }
+    }
+  }
   const tg::BlkArgs g = tg::blk_args(p);
   const size_t smem = tg::blk_stage_bytes(p->blk_rows, g.capJ, g.capE, D + 1) +
                       (size_t)(D + 1) * D * g.capE * sizeof(T);

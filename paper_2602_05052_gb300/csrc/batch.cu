@@ -18,7 +18,7 @@
 #include <string>
 #include <vector>
 
-#include "blk_bilinear.cuh"
+#include "fan.cuh"
 
 namespace {
 
@@ -89,6 +89,9 @@ struct InstBlk {
   const int32_t* bvbase;
   const int32_t* bel_cnt;
   const uint32_t* brec;
+  const uint16_t* fan;  // fan regions (P1 triangles; NULL: the row-owner Reduce)
+  const int64_t* fan_off;
+  int fan_rs;
   int64_t N;
   int R;
   unsigned long long* status;
@@ -125,6 +128,28 @@ __global__ void __launch_bounds__(128) k_batch_blk(const InstBlk* __restrict__ d
     a.f = nullptr;
     a.f_layout = 0;
     a.F = nullptr;
+    if constexpr (EL == TG_P1_TRI) {
+      if (d.fan != nullptr) {  // the fan-ordered Reduce, as tg_assemble_bilinear takes it
+        tg::FanArgs g;
+        g.urp = d.urp;
+        g.iperm = d.iperm;
+        g.fan = d.fan;
+        g.fan_off = d.fan_off;
+        g.bel = d.bel;
+        g.boff = d.boff;
+        g.bvbase = d.bvbase;
+        g.bel_cnt = d.bel_cnt;
+        g.N = d.N;
+        g.R = d.R;
+        g.rs = d.fan_rs;
+        const tg::FanView fv = tg::fan_view_global(g, w.y);
+        tg::blk_bilinear_map<EL, T, UB, false>(a, tab, capE, fv, smem);
+        __syncthreads();
+        tg::fan_reduce_bilinear<T, false>(a, capE, fv, smem);
+        __syncthreads();
+        continue;
+      }
+    }
     tg::BlkView v;
     const int64_t r0 = (int64_t)w.y * d.R;
     v.r0 = (int)r0;
@@ -347,7 +372,7 @@ tg_status setup_blocks(tg_batch* b) {
   for (int i = 0; i < b->n_inst; ++i) {
     const tg_pattern* p = b->pats[i];
     h[i] = InstBlk{p->iinc, p->irp, p->urp, p->iperm, p->bel, p->boff, p->bvbase, p->bel_cnt, p->brec,
-                   p->N, p->blk_rows, p->status};
+                   p->fan, p->fan_off, p->fan_rs, p->N, p->blk_rows, p->status};
     if (p->E > 0)
       for (int64_t k = 0; k < p->n_blk; ++k) items.push_back(make_int2(i, (int)k));
     if ((i + 1) % kMaxInst == 0 || i + 1 == b->n_inst) b->blk_chunk_items.push_back((int64_t)items.size());

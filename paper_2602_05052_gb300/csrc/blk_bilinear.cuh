@@ -41,29 +41,16 @@ size_t blk_bilinear_work_bytes(int capE, int max_row_len, int rs) {
   return (size_t)NV * kf_vecs<NV, T, LOAD>() * capE * 16 + (size_t)max_row_len * rs * sizeof(T);
 }
 
-//   Map    - every distinct element of the block computes K_e (and with
-//            LOAD F_e) once (UB elements per thread, one round when
-//            UB * blockDim.x >= the block's element count) and stores its
-//            NV output rows: vector w of row a of element j at
-//            KF[(a * NW + w) * capE + j];
-//   Reduce - thread t owns row i = r0 + t; for each incidence (e, a) in
-//            increasing e it adds row a of K_e: the diagonal entry (rotated
-//            column 0) in a register, the others into acc[pos * rs + t]
-//            (pos = the column's position in the row; the records hold the
-//            positions in the same rotated order).  The row is then written
-//            to its node's CSR row and acc cleared for the next block; with
-//            LOAD also F of the node.  Ends with a CTA barrier.
-// Every CSR entry is the sum of its contributions in increasing element
-// order, starting from the first one.
-template <int EL, typename T, int UB, bool LOAD>
-__device__ __forceinline__ void blk_bilinear_block(const FwdArgs<T>& a, const RefTab<T>& tab, int capE,
-                                                   const BlkView& v, void* kf_buf, T* acc) {
+// The Map of a block (any view with nbe, be[] and vtx(c, k)): every
+// distinct element's output rows into KF.
+template <int EL, typename T, int UB, bool LOAD, typename View>
+__device__ __forceinline__ void blk_bilinear_map(const FwdArgs<T>& a, const RefTab<T>& tab, int capE, const View& v,
+                                                 void* kf_buf) {
   constexpr int NV = Elem<EL>::nv, NG = Elem<EL>::ngeo, NS = NV * (NV + 1) / 2;
   constexpr int NW = kf_vecs<NV, T, LOAD>(), VN = Vec16<T>::n;
   using V = typename Vec16<T>::type;
   V* KF = reinterpret_cast<V*>(kf_buf);
   const int NT = blockDim.x;
-  // Map
   for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * NT) {
     int e[UB];
     ElemIn<EL, T> in[UB];
@@ -111,6 +98,31 @@ __device__ __forceinline__ void blk_bilinear_block(const FwdArgs<T>& a, const Re
       }
     }
   }
+}
+
+//   Map    - every distinct element of the block computes K_e (and with
+//            LOAD F_e) once (UB elements per thread, one round when
+//            UB * blockDim.x >= the block's element count) and stores its
+//            NV output rows: vector w of row a of element j at
+//            KF[(a * NW + w) * capE + j];
+//   Reduce - thread t owns row i = r0 + t; for each incidence (e, a) in
+//            increasing e it adds row a of K_e: the diagonal entry (rotated
+//            column 0) in a register, the others into acc[pos * rs + t]
+//            (pos = the column's position in the row; the records hold the
+//            positions in the same rotated order).  The row is then written
+//            to its node's CSR row and acc cleared for the next block; with
+//            LOAD also F of the node.  Ends with a CTA barrier.
+// Every CSR entry is the sum of its contributions in increasing element
+// order, starting from the first one.
+template <int EL, typename T, int UB, bool LOAD>
+__device__ __forceinline__ void blk_bilinear_block(const FwdArgs<T>& a, const RefTab<T>& tab, int capE,
+                                                   const BlkView& v, void* kf_buf, T* acc) {
+  constexpr int NV = Elem<EL>::nv;
+  constexpr int NW = kf_vecs<NV, T, LOAD>(), VN = Vec16<T>::n;
+  using V = typename Vec16<T>::type;
+  const V* KF = reinterpret_cast<const V*>(kf_buf);
+  const int NT = blockDim.x;
+  blk_bilinear_map<EL, T, UB, LOAD>(a, tab, capE, v, kf_buf);
   __syncthreads();
   // Reduce
   {

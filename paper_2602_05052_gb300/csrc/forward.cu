@@ -15,7 +15,7 @@
 // the memory traffic.
 #include <cstdint>
 
-#include "blk_bilinear.cuh"
+#include "fan.cuh"
 
 namespace {
 
@@ -91,25 +91,19 @@ size_t bilinear_blk_smem(const tg_pattern* p) {
          tg::blk_bilinear_work_bytes<NV, T, LOAD>(g.capE, p->max_row_len, BT);
 }
 
-// P1 load vector over element-once row blocks: Map F_e (NV values) per
-// distinct element, Reduce F[i] = sum of the incidences' entries in
-// increasing element order (second line of Eq. (matlclquad)).
-template <int D, typename T, int UB>
-__global__ void __launch_bounds__(BT) k_load_blk(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
-                                                 const tg::BlkArgs g) {
+// Map of the P1 load vector over a block (any view with nbe, be[] and
+// vtx(c, k)): F_e of every distinct element into Fe[c * capE + j].
+template <int D, typename T, int UB, typename View>
+__device__ __forceinline__ void blk_load_map(const FwdArgs<T>& a, const tg::RefTab<T>& ts, int capE, const View& v,
+                                             T* Fe) {
   constexpr int NV = D + 1;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const tg::RefTab<T>& ts = tab;
-  tg::BlkPipe pipe;
-  T* Fe = reinterpret_cast<T*>(pipe.init(smem, g));
-  __syncthreads();  // publishes the mbarrier initialisation
-  TG_BLK_PIPELINE_BEGIN(pipe, g, a.status)
-  for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * NT_) {
+  const int NT = blockDim.x;
+  for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * NT) {
     int e[UB];
     int vid[UB][NV];
 #pragma unroll
     for (int u = 0; u < UB; ++u) {
-      const int j = j0 + u * NT_ < v.nbe ? j0 + u * NT_ : 0;
+      const int j = j0 + u * NT < v.nbe ? j0 + u * NT : 0;
       e[u] = tg::bel_elem(v.be[j]);
 #pragma unroll
       for (int c = 0; c < NV; ++c) vid[u][c] = v.vtx(c, j);
@@ -124,7 +118,7 @@ __global__ void __launch_bounds__(BT) k_load_blk(const FwdArgs<T> a, const __gri
     }
 #pragma unroll
     for (int u = 0; u < UB; ++u) {
-      const int j = j0 + u * NT_;
+      const int j = j0 + u * NT;
       if (j >= v.nbe) continue;
       tg::Geom<D, T> gm;
       if constexpr (D == 2) tg::tri_geom_x(x[u][0], x[u][1], x[u][2], gm);
@@ -133,9 +127,24 @@ __global__ void __launch_bounds__(BT) k_load_blk(const FwdArgs<T> a, const __gri
       const bool ok = adet > tg::det_tiny<T>();
       if (!ok) tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e[u]);
 #pragma unroll
-      for (int c = 0; c < NV; ++c) Fe[c * g.capE + j] = ok ? tg::p1_load_entry<NV, T>(a.layout, adet, fv[u], ts, c) : T(0);
+      for (int c = 0; c < NV; ++c) Fe[c * capE + j] = ok ? tg::p1_load_entry<NV, T>(a.layout, adet, fv[u], ts, c) : T(0);
     }
   }
+}
+
+// P1 load vector over element-once row blocks: Map F_e (NV values) per
+// distinct element, Reduce F[i] = sum of the incidences' entries in
+// increasing element order (second line of Eq. (matlclquad)).
+template <int D, typename T, int UB>
+__global__ void __launch_bounds__(BT) k_load_blk(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
+                                                 const tg::BlkArgs g) {
+  constexpr int NV = D + 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  tg::BlkPipe pipe;
+  T* Fe = reinterpret_cast<T*>(pipe.init(smem, g));
+  __syncthreads();  // publishes the mbarrier initialisation
+  TG_BLK_PIPELINE_BEGIN(pipe, g, a.status)
+  blk_load_map<D, T, UB>(a, tab, g.capE, v, Fe);
   __syncthreads();
   {
     const int i = v.r0 + (int)threadIdx.x;
@@ -151,6 +160,50 @@ __global__ void __launch_bounds__(BT) k_load_blk(const FwdArgs<T> a, const __gri
     __syncthreads();
   }
   TG_BLK_PIPELINE_END
+}
+
+// The fan-ordered kernels (P1 triangles, fan.cuh): the same Map, the Reduce
+// along each row's fan in registers.  LOAD assembles the system (K, F).
+template <typename T, int UB, bool LOAD>
+__global__ void __launch_bounds__(BT, blk_min_ctas_bt<TG_P1_TRI, T, UB, LOAD>()) k_bilinear_fan(
+    const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab, const tg::FanArgs g) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  tg::FanPipe pipe;
+  unsigned char* kf = pipe.init(smem, g);
+  __syncthreads();  // publishes the mbarrier initialisation
+  TG_FAN_PIPELINE_BEGIN(pipe, g, a.status)
+  tg::blk_bilinear_map<TG_P1_TRI, T, UB, LOAD>(a, tab, g.capE, v, kf);
+  __syncthreads();
+  tg::fan_reduce_bilinear<T, LOAD>(a, g.capE, v, kf);
+  __syncthreads();  // stage s and the Map's rows are free again
+  TG_FAN_PIPELINE_END
+}
+
+template <typename T, bool LOAD>
+size_t bilinear_fan_smem(const tg_pattern* p) {
+  const tg::FanArgs g = tg::fan_args(p);
+  return tg::fan_stage_bytes(g.R, g.capF, g.capE, 3) + (size_t)3 * tg::kf_vecs<3, T, LOAD>() * g.capE * 16;
+}
+
+template <typename T, int UB>
+__global__ void __launch_bounds__(BT) k_load_fan(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
+                                                 const tg::FanArgs g) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  tg::FanPipe pipe;
+  T* Fe = reinterpret_cast<T*>(pipe.init(smem, g));
+  __syncthreads();  // publishes the mbarrier initialisation
+  TG_FAN_PIPELINE_BEGIN(pipe, g, a.status)
+  blk_load_map<2, T, UB>(a, tab, g.capE, v, Fe);
+  __syncthreads();
+  tg::fan_reduce_load<T>(a.out, g.capE, v, Fe);
+  __syncthreads();
+  TG_FAN_PIPELINE_END
+}
+
+template <typename T>
+size_t load_fan_smem(const tg_pattern* p) {
+  const tg::FanArgs g = tg::fan_args(p);
+  return tg::fan_stage_bytes(g.R, g.capF, g.capE, 3) + (size_t)3 * g.capE * sizeof(T);
 }
 
 template <int D, typename T>
@@ -189,6 +242,25 @@ tg_status launch_blk(K kern, size_t smem, const tg_pattern* p, dim3* grid_out) {
 template <typename T>
 bool use_blk(const tg_pattern* p, size_t smem) {
   return p->bel != nullptr && smem <= kBlkSmemMax;
+}
+
+// Whether the fan-ordered kernels serve this pattern.
+inline bool use_fan(const tg_pattern* p, size_t smem) {
+  return p->fan != nullptr && p->bel != nullptr && smem <= kBlkSmemMax;
+}
+
+// The fan kernel for ub elements per thread (as k_bilinear_blk picks them).
+template <typename T, bool LOAD, typename Go>
+void fan_dispatch(int ub, Go&& go) {
+  if constexpr (sizeof(T) == 8) {
+    if (ub <= 2) go(k_bilinear_fan<T, 2, LOAD>);
+    else go(k_bilinear_fan<T, 3, LOAD>);
+  } else {
+    if (ub <= 2) go(k_bilinear_fan<T, 2, LOAD>);
+    else if (ub <= 3) go(k_bilinear_fan<T, 3, LOAD>);
+    else if (ub <= 4) go(k_bilinear_fan<T, 4, LOAD>);
+    else go(k_bilinear_fan<T, 6, LOAD>);
+  }
 }
 
 // Comparison point: classic scatter-add (Eq. (scatter_add)) with atomics,
@@ -332,6 +404,21 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
   }
   const size_t smem = tab_bytes<T>() + stage;
   const int cap = std::max(1, R * p->max_deg);
+  if constexpr (EL == TG_P1_TRI) {
+    const size_t sb = bilinear_fan_smem<T, false>(p);
+    if (use_fan(p, sb)) {
+      tg_status st = TG_OK;
+      auto go = [&](auto kern) {
+        dim3 grid;
+        if ((st = launch_blk(kern, sb, p, &grid)) != TG_OK) return;
+        kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::fan_args(p));
+      };
+      fan_dispatch<T, false>(blk_ub<T>(p), go);
+      if (st != TG_OK) return st;
+      TG_CK_LAUNCH("k_bilinear_fan");
+      return TG_OK;
+    }
+  }
   {
     const size_t sb = bilinear_blk_smem<El::nv, T, false>(p);
     if (use_blk<T>(p, sb)) {
@@ -402,6 +489,21 @@ tg_status load(const tg_pattern* p, const void* coords, const void* f, tg_layout
   a.out = static_cast<T*>(F);
   const tg_element el = p->el == TG_P1_TET_VEC3 ? TG_P1_TET : p->el;
   const tg::RefTab<T>& tab = table<T>(el);
+  if (ncomp == 1 && el == TG_P1_TRI && use_fan(p, load_fan_smem<T>(p))) {
+    const size_t sb = load_fan_smem<T>(p);
+    tg_status st = TG_OK;
+    auto go = [&](auto kern) {
+      dim3 grid;
+      if ((st = launch_blk(kern, sb, p, &grid)) != TG_OK) return;
+      kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::fan_args(p));
+    };
+    if constexpr (sizeof(T) == 8) go(k_load_fan<T, 2>);
+    else if (blk_ub<T>(p) <= 4) go(k_load_fan<T, 4>);
+    else go(k_load_fan<T, 6>);
+    if (st != TG_OK) return st;
+    TG_CK_LAUNCH("k_load_fan");
+    return TG_OK;
+  }
   if (ncomp == 1 && (el == TG_P1_TRI || el == TG_P1_TET) && p->bel) {
     const bool tri = el == TG_P1_TRI;
     const size_t sb = tri ? load_blk_smem<2, T>(p) : load_blk_smem<3, T>(p);
@@ -471,6 +573,20 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
     a.f_layout = fl;
     a.F = static_cast<T*>(F);
     const bool tri = p->el == TG_P1_TRI;
+    if (tri && use_fan(p, bilinear_fan_smem<T, true>(p))) {
+      const size_t sb = bilinear_fan_smem<T, true>(p);
+      const tg::RefTab<T>& tab = table<T>(p->el);
+      tg_status st = TG_OK;
+      auto go = [&](auto kern) {
+        dim3 grid;
+        if ((st = launch_blk(kern, sb, p, &grid)) != TG_OK) return;
+        kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::fan_args(p));
+      };
+      fan_dispatch<T, true>(blk_ub<T>(p), go);
+      if (st != TG_OK) return st;
+      TG_CK_LAUNCH("k_bilinear_fan<load>");
+      return TG_OK;
+    }
     const size_t sb = tri ? bilinear_blk_smem<3, T, true>(p) : bilinear_blk_smem<4, T, true>(p);
     if (use_blk<T>(p, sb)) {
       const int ub = blk_ub<T>(p);

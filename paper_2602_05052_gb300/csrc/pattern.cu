@@ -472,6 +472,209 @@ __global__ void k_elem_pos(const int32_t* __restrict__ cells, const int32_t* __r
   out[e] = w;
 }
 
+// ------------------------------------------------------------------ fans
+// P1 triangles: the triangles around a node, walked across the edges they
+// share, form its fan (closed around an interior node, open at the boundary).
+// Triangle k of the fan lies between the row's neighbours j_k and j_{k+1},
+// so every off-diagonal entry of the row is the sum of at most two
+// consecutive triangles' entries: the Reduce keeps the row in registers.
+
+constexpr int kFanMax = 15;  // fan steps per row (rows of at most 16 entries)
+
+// Per internal row i: its fan from the row's incidence records (brec, in
+// element order): deg, open flag, diagonal position (info), neighbour
+// positions in fan order (pos64), and the records of the fan's triangles in
+// fan order (rec[i * kFanMax + k]).  The walk starts, for an open fan, at the
+// triangle holding the boundary neighbour of smaller position, else at the
+// row's first triangle in element order.  A node whose triangles are not one
+// fan sets *bad.  Per block: the largest deg (kmax, atomicMax).
+__global__ void k_fan_rows(const int32_t* __restrict__ iinc, const int32_t* __restrict__ irp,
+                           const uint32_t* __restrict__ brec, int64_t N, int R, uint16_t* __restrict__ info,
+                           unsigned long long* __restrict__ pos64, uint16_t* __restrict__ rec,
+                           int* __restrict__ kmax, int* __restrict__ bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int j0 = iinc[i], deg = iinc[i + 1] - j0, len = irp[i + 1] - irp[i];
+  if (deg == 0) {
+    info[i] = 0;
+    pos64[i] = 0ull;
+    return;
+  }
+  if (deg > kFanMax) {
+    atomicOr(bad, 1);
+    return;
+  }
+  // records (nv = 3): positions of vertices a, a + 1, a + 2 in bits
+  // [0, 4), [4, 8), [8, 12); a in [12, 14); local element index from 14
+  uint32_t r[kFanMax];
+  int cnt[16];
+  for (int q = 0; q < 16; ++q) cnt[q] = 0;
+  int dpos = -1;
+  for (int m = 0; m < deg; ++m) {
+    r[m] = brec[j0 + m];
+    cnt[(r[m] >> 4) & 15u]++;
+    cnt[(r[m] >> 8) & 15u]++;
+    const int d = (int)(r[m] & 15u);
+    if (dpos >= 0 && d != dpos) atomicOr(bad, 1);
+    dpos = d;
+  }
+  int start = 0, prev = (int)((r[0] >> 4) & 15u);
+  bool open = false;
+  for (int q = 0; q < 16 && !open; ++q) {
+    if (cnt[q] > 2) {
+      atomicOr(bad, 1);
+      return;
+    }
+    if (cnt[q] == 1) {
+      for (int m = 0; m < deg; ++m)
+        if ((int)((r[m] >> 4) & 15u) == q || (int)((r[m] >> 8) & 15u) == q) {
+          start = m;
+          break;
+        }
+      prev = q;
+      open = true;
+    }
+  }
+  for (int q = 0; q < 16; ++q)
+    if (cnt[q] > 2) {
+      atomicOr(bad, 1);
+      return;
+    }
+  unsigned used = 0;
+  unsigned long long pw = 0;
+  int m = start, k = 0, next = -1;
+  while (true) {
+    used |= 1u << m;
+    const int p1 = (int)((r[m] >> 4) & 15u), p2 = (int)((r[m] >> 8) & 15u);
+    const bool swap = prev == p2;
+    next = swap ? p1 : p2;
+    const uint32_t le = r[m] >> 14, a = (r[m] >> 12) & 3u;
+    if (le >= 2048u) {
+      atomicOr(bad, 1);
+      return;
+    }
+    rec[i * kFanMax + k] = (uint16_t)(le | (a << 11) | ((swap ? 1u : 0u) << 13));
+    pw |= (unsigned long long)prev << (4 * k);
+    ++k;
+    int nm = -1;
+    for (int q = 0; q < deg; ++q)
+      if (!((used >> q) & 1u) && ((int)((r[q] >> 4) & 15u) == next || (int)((r[q] >> 8) & 15u) == next)) {
+        nm = q;
+        break;
+      }
+    if (nm < 0) break;
+    prev = next;
+    m = nm;
+  }
+  const int nn = open ? deg + 1 : deg;  // neighbours
+  if (open) pw |= (unsigned long long)next << (4 * deg);
+  if (k != deg || (!open && next != (int)(pw & 15ull)) || nn != len - 1) {
+    atomicOr(bad, 1);
+    return;
+  }
+  info[i] = (uint16_t)(deg | (open ? 32 : 0) | (dpos << 6));
+  pos64[i] = pw;
+  atomicMax(kmax + i / R, deg);
+}
+
+// Start and direction of every fan, chosen so that the Reduce's shared-memory
+// reads are spread over the banks.  Step k of the Reduce reads, for each row
+// of the block, the 16-byte output row of its k-th fan triangle at index le
+// of the element list; the eight lanes that a 16-byte access serves together
+// (rows 8q .. 8q + 7 of a block) meet in one bank group when their le agree
+// modulo 8 (the kernels keep the per-vertex arrays a multiple of 8 rows
+// long), and each such collision costs a pass.  A closed fan may start at
+// any triangle and run either way, an open one from either end; one thread
+// per group of eight rows picks, row after row, the start and direction that
+// collide least with the rows placed before.  Only the summation order of
+// the diagonal and the load entry depends on the choice.
+__global__ void k_fan_rotate(uint16_t* __restrict__ info, unsigned long long* __restrict__ pos64,
+                             uint16_t* __restrict__ rec, int64_t N, int R) {
+  const int64_t qid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nq = (R + 7) / 8;
+  const int64_t b = qid / nq;
+  const int q = (int)(qid % nq);
+  const int64_t i0 = b * R + 8 * q;
+  if (i0 >= N || 8 * q >= R) return;
+  unsigned char used[kFanMax][8];
+  for (int k = 0; k < kFanMax; ++k)
+    for (int g = 0; g < 8; ++g) used[k][g] = 0;
+  for (int t = 0; t < 8 && 8 * q + t < R && i0 + t < N; ++t) {
+    const int64_t i = i0 + t;
+    const int deg = info[i] & 31;
+    if (deg == 0) continue;
+    const bool open = (info[i] & 32) != 0;
+    uint16_t r0[kFanMax];
+    for (int k = 0; k < deg; ++k) r0[k] = rec[i * kFanMax + k];
+    const int nrot = open ? 1 : deg;
+    int best = 0, best_cost = 1 << 30;
+    for (int c = 0; c < 2 * nrot; ++c) {
+      const int rot = c % nrot;
+      const bool rev = c >= nrot;
+      int cost = 0;
+      for (int m = 0; m < deg; ++m) {
+        const int src = rev ? (open ? deg - 1 - m : (rot - m + deg) % deg) : (rot + m) % deg;
+        cost += used[m][r0[src] & 7];
+      }
+      if (cost < best_cost) {
+        best_cost = cost;
+        best = c;
+      }
+    }
+    const int rot = best % nrot;
+    const bool rev = best >= nrot;
+    const unsigned long long pw = pos64[i];
+    const int nn = open ? deg + 1 : deg;
+    unsigned long long npw = 0;
+    for (int m = 0; m < deg; ++m) {
+      const int src = rev ? (open ? deg - 1 - m : (rot - m + deg) % deg) : (rot + m) % deg;
+      const uint16_t r = rev ? (uint16_t)(r0[src] ^ (1u << 13)) : r0[src];
+      rec[i * kFanMax + m] = r;
+      used[m][r & 7]++;
+    }
+    for (int m = 0; m < nn; ++m) {
+      // neighbour m of the new order: j_{rot + m} forward; reversed, the
+      // next neighbour of triangle rot - m (open: of triangle deg - 1 - m)
+      const int src = rev ? (open ? deg - m : (rot - m + 1 + deg) % deg) : (rot + m) % nn;
+      npw |= ((pw >> (4 * src)) & 15ull) << (4 * m);
+    }
+    pos64[i] = npw;
+  }
+}
+
+__global__ void k_blk_max(const int* __restrict__ v, int64_t n, int* __restrict__ out) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < n) atomicMax(out, v[b]);
+}
+
+// Region words of block b: (5 + kmax) * rs.
+__global__ void k_fan_words(const int* __restrict__ kmax, int64_t nblk, int rs, int32_t* __restrict__ words) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < nblk) words[b] = (5 + kmax[b]) * rs;
+}
+
+// Scatter the rows' fan data into the blocks' regions (layout in
+// tg_internal.cuh); rows past the end of the last block and fan steps past
+// a row's deg are zero (a zero record is never read).
+__global__ void k_fan_place(const uint16_t* __restrict__ info, const unsigned long long* __restrict__ pos64,
+                            const uint16_t* __restrict__ rec, const int64_t* __restrict__ off,
+                            const int* __restrict__ kmax, int64_t N, int R, int rs, int64_t nblk,
+                            uint16_t* __restrict__ fan) {
+  const int64_t b = blockIdx.x;
+  if (b >= nblk) return;
+  uint16_t* g = fan + off[b];
+  const int kb = kmax[b];
+  for (int t = threadIdx.x; t < rs; t += blockDim.x) {
+    const int64_t i = b * R + t;
+    const bool live = t < R && i < N;
+    const unsigned long long pw = live ? pos64[i] : 0ull;
+    for (int q = 0; q < 4; ++q) g[4 * t + q] = (uint16_t)(pw >> (16 * q));
+    g[4 * rs + t] = live ? info[i] : (uint16_t)0;
+    const int d = live ? (info[i] & 31) : 0;
+    for (int k = 0; k < kb; ++k) g[(5 + k) * rs + t] = k < d ? rec[i * kFanMax + k] : (uint16_t)0;
+  }
+}
+
 // Device buffers freed on scope exit unless released.
 struct Tmp {
   std::vector<void*> bufs;
@@ -535,6 +738,58 @@ tg_status read_status(const tg_pattern* p, cudaStream_t s, const char* stage) {
 // elasticity keeps 12 values per element in shared memory, hence 32 rows.
 int blk_rows_of(tg_element el) {
   return el == TG_P1_TRI ? 120 : el == TG_P2_TRI ? 128 : 64;
+}
+
+// Fans of a P1 triangle pattern with row blocks; leaves p->fan == NULL when
+// some node's triangles are not one fan.
+tg_status build_fans(tg_pattern* p, cudaStream_t s) {
+  const int R = p->blk_rows, rs = (R + 7) & ~7;
+  const int64_t N = p->N, nblk = p->n_blk;
+  Tmp tmp;
+  uint16_t *info = nullptr, *rec = nullptr;
+  unsigned long long* pos64 = nullptr;
+  int *kmax = nullptr, *bad = nullptr;
+  int32_t* words = nullptr;
+  int64_t* off = nullptr;
+  TG_CK(tmp.alloc(&info, N));
+  TG_CK(tmp.alloc(&rec, N * kFanMax));
+  TG_CK(tmp.alloc(&pos64, N));
+  TG_CK(tmp.alloc(&kmax, nblk));
+  TG_CK(tmp.alloc(&bad, 1));
+  TG_CK(tmp.alloc(&words, nblk));
+  TG_CK(cudaMemsetAsync(kmax, 0, nblk * sizeof(int), s));
+  TG_CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  k_fan_rows<<<tg::grid_for(N, kThreads), kThreads, 0, s>>>(p->iinc, p->irp, p->brec, N, R, info, pos64, rec, kmax,
+                                                            bad);
+  TG_CK_LAUNCH("k_fan_rows");
+  int hb = 0;
+  TG_CK(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  if (hb) return TG_OK;
+  const int64_t nphase = nblk * ((R + 7) / 8);
+  k_fan_rotate<<<tg::grid_for(nphase, 64), 64, 0, s>>>(info, pos64, rec, N, R);
+  TG_CK_LAUNCH("k_fan_rotate");
+  k_fan_words<<<tg::grid_for(nblk, kThreads), kThreads, 0, s>>>(kmax, nblk, rs, words);
+  TG_CK_LAUNCH("k_fan_words");
+  TG_CK(cudaMalloc(&p->fan_off, (nblk + 1) * sizeof(int64_t) + 16));
+  tg_status st = scan_exclusive<int32_t>(words, p->fan_off, nblk, s);
+  if (st != TG_OK) return st;
+  int64_t total = 0;
+  int* kmax_all = bad;  // reuse
+  TG_CK(cudaMemsetAsync(kmax_all, 0, sizeof(int), s));
+  k_blk_max<<<tg::grid_for(nblk, kThreads), kThreads, 0, s>>>(kmax, nblk, kmax_all);
+  TG_CK_LAUNCH("k_blk_max");
+  int hk = 0;
+  TG_CK(cudaMemcpyAsync(&total, p->fan_off + nblk, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaMemcpyAsync(&hk, kmax_all, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  TG_CK(cudaMalloc(&p->fan, total * sizeof(uint16_t) + 16));
+  k_fan_place<<<(unsigned)nblk, 128, 0, s>>>(info, pos64, rec, p->fan_off, kmax, N, R, rs, nblk, p->fan);
+  TG_CK_LAUNCH("k_fan_place");
+  TG_CK(cudaStreamSynchronize(s));  // tmp buffers are freed on return
+  p->fan_rs = rs;
+  p->fan_kmax = hk;
+  return TG_OK;
 }
 
 // Row blocks (step 5).  Leaves p->bel == NULL when the packed fields do not
@@ -654,6 +909,7 @@ tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
   p->blk_max_inc = h[0];
   p->blk_max_nz = h[1];
   p->blk_max_elems = h[2];
+  if (p->el == TG_P1_TRI && h[2] <= 2048 && (st = build_fans(p, s)) != TG_OK) return st;
   if (nv * nv * pb <= 64) {
     TG_CK(cudaMalloc(&p->elem_pos, E * sizeof(uint64_t) + 16));
     k_elem_pos<<<tg::grid_for(E, kThreads), kThreads, 0, s>>>(p->cells, p->elem_slot, p->row_ptr, E, nv, pb, false,

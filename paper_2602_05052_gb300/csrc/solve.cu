@@ -172,7 +172,15 @@ tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8
   TG_CK(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
   TG_CK(cudaStreamSynchronize(s));
   const double fnorm = std::sqrt(h[3]);
-  double rel = fnorm > 0 ? std::sqrt(h[0]) / fnorm : 0.0;
+  if (!(fnorm > 0)) {
+    // F_I = 0: the solution of K_II x_I = 0 is x = 0, whatever the initial guess
+    TG_CK(cudaMemsetAsync(x, 0, (size_t)n * sizeof(T), s));
+    TG_CK(cudaStreamSynchronize(s));
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return TG_OK;
+  }
+  double rel = std::sqrt(h[0]) / fnorm;
   auto iteration = [&](cudaStream_t q) -> tg_status {
     k_spmv<T><<<gs, ST, 0, q>>>(rp, ci, vals, pp, Ap, n, mask);
     tg_status e;
@@ -186,7 +194,7 @@ tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8
   };
   int it = 0;
   CgGraph g;
-  if (use_graph && fnorm > 0 && rel > rtol && maxit >= 8) {
+  if (use_graph && rel > rtol && maxit >= 8) {
     TG_CK(cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking));
     TG_CK(cudaStreamBeginCapture(g.cs, cudaStreamCaptureModeThreadLocal));
     tg_status e = TG_OK;
@@ -198,7 +206,7 @@ tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8
     TG_CK(ce);
     TG_CK(cudaGraphInstantiate(&g.exec, g.graph, 0));
   }
-  while (fnorm > 0 && rel > rtol && it < maxit) {
+  while (rel > rtol && it < maxit) {
     if (g.exec && it + 8 <= maxit) {
       TG_CK(cudaGraphLaunch(g.exec, s));
       it += 8;
@@ -215,9 +223,16 @@ tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8
   TG_CK(cudaMemcpyAsync(h, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
   TG_CK(cudaStreamSynchronize(s));
   if (iters) *iters = it;
-  if (relres) *relres = fnorm > 0 ? std::sqrt(h[0]) / fnorm : 0.0;
+  if (relres) *relres = std::sqrt(h[0]) / fnorm;
   return TG_OK;
 }
+
+// Partial dot products per reduction: twice the SM count, capped so that both
+// forms of the solve (the no-alloc one keeps its partials in a 4 KB head)
+// reduce over the same grid and give the same bits on any GPU.
+constexpr size_t kNoAllocHead = 4096;
+constexpr int kMaxPartials = (int)(kNoAllocHead / sizeof(double)) - 4;
+inline int cg_partials() { return std::min(2 * tg::sm_count(), kMaxPartials); }
 
 // Allocating form: the work vectors live for one call.
 template <typename T>
@@ -226,7 +241,7 @@ tg_status cg_alloc(const tg_pattern* p, const void* vals, const void* F, const u
   const int64_t n = tg::ncomp_of(p->el) * p->N;
   Dev d;
   CgWork<T> w;
-  w.nb = 2 * tg::sm_count();
+  w.nb = cg_partials();
   TG_CK(d.alloc((void**)&w.r, n * sizeof(T)));
   TG_CK(d.alloc((void**)&w.pp, n * sizeof(T)));
   TG_CK(d.alloc((void**)&w.Ap, n * sizeof(T)));
@@ -242,17 +257,46 @@ tg_status cg_alloc(const tg_pattern* p, const void* vals, const void* F, const u
 // dot products (up to kNoAllocMaxPartials doubles), then the four work
 // vectors, each rounded up to 256 bytes.
 constexpr size_t kNoAllocBytes = TG_CG_NOALLOC_SCRATCH_BYTES;
-constexpr size_t kNoAllocHead = 4096;
-constexpr int kNoAllocMaxPartials = (int)(kNoAllocHead / sizeof(double)) - 4;
 static __device__ __align__(256) unsigned char g_cg_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+struct ScratchEntry {
+  void* addr = nullptr;
+  unsigned long long ctx = 0;  // identity of the context the address belongs to
+};
+ScratchEntry g_scratch[kMaxDevices];
 
-// Device address of g_cg_scratch on the current device, looked up once per
-// device (the lookup may load this module; it must not happen inside a
-// stream capture, so the first call on a device has to come before any).
+// Unique identity of the current CUDA context (cuCtxGetCurrent + cuCtxGetId,
+// reached through the runtime's driver entry points, so nothing links the
+// driver library), or 0 when it cannot be read.  A context created after
+// cudaDeviceReset has a new identity, and this module a new address in it.
+unsigned long long current_ctx_id() {
+  using GetCurrentFn = int (*)(void**);
+  using GetIdFn = int (*)(void*, unsigned long long*);
+  static GetCurrentFn get_cur = nullptr;
+  static GetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, nullptr) == cudaSuccess)
+      get_cur = reinterpret_cast<GetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, nullptr) == cudaSuccess)
+      get_id = reinterpret_cast<GetIdFn>(f);
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_cur || !get_id || get_cur(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of g_cg_scratch on the current device.  It is looked up
+// once per device and context (the first call on a device, and the first
+// after a cudaDeviceReset; every call when the context identity cannot be
+// read); the lookup may load this module, so it must not happen inside a
+// stream capture.
 tg_status noalloc_scratch(unsigned char** out) {
   int dev = 0;
   TG_CK(cudaGetDevice(&dev));
@@ -261,7 +305,9 @@ tg_status noalloc_scratch(unsigned char** out) {
     return TG_ERR_UNSUPPORTED;
   }
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (g_scratch_addr[dev] == nullptr) {
+  const unsigned long long ctx = current_ctx_id();
+  ScratchEntry& ent = g_scratch[dev];
+  if (ent.addr == nullptr || ctx == 0 || ent.ctx != ctx) {
     void* a = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&a, g_cg_scratch);
     if (e != cudaSuccess) return tg::cuda_fail(e, "cudaGetSymbolAddress(g_cg_scratch)", __FILE__, __LINE__);
@@ -269,9 +315,10 @@ tg_status noalloc_scratch(unsigned char** out) {
       tg::set_error("cudaGetSymbolAddress(g_cg_scratch) returned a null address");
       return TG_ERR_CUDA;
     }
-    g_scratch_addr[dev] = a;
+    ent.addr = a;
+    ent.ctx = current_ctx_id();  // the lookup made the device's context current
   }
-  *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  *out = static_cast<unsigned char*>(ent.addr);
   return TG_OK;
 }
 
@@ -294,7 +341,7 @@ tg_status cg_noalloc(const tg_pattern* p, const void* vals, const void* F, const
   CgWork<T> w;
   w.sc = reinterpret_cast<double*>(base);
   w.partials = w.sc + 4;
-  w.nb = std::min(2 * tg::sm_count(), kNoAllocMaxPartials);
+  w.nb = cg_partials();
   w.r = reinterpret_cast<T*>(base + kNoAllocHead);
   w.pp = reinterpret_cast<T*>(base + kNoAllocHead + vb);
   w.Ap = reinterpret_cast<T*>(base + kNoAllocHead + 2 * vb);
@@ -317,6 +364,14 @@ __global__ void __launch_bounds__(ST) k_csr_outer(const int32_t* __restrict__ rp
   const T l = alpha * lam[row];
   const int k1 = __ldg(rp + row + 1);
   for (int k = __ldg(rp + row) + (threadIdx.x & 7); k < k1; k += 8) out[k] = l * __ldg(U + __ldg(ci + k));
+}
+
+// out[i] = alpha x[i], zero on the rows the condensed system drops.
+template <typename T>
+__global__ void __launch_bounds__(ST) k_scale_masked(const T* __restrict__ x, const uint8_t* __restrict__ mask,
+                                                     T alpha, T* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * ST + threadIdx.x; i < n; i += (int64_t)gridDim.x * ST)
+    out[i] = (mask && mask[i]) ? T(0) : alpha * x[i];
 }
 
 template <typename T>
@@ -399,6 +454,20 @@ tg_status tg_csr_outer(const tg_pattern* p, tg_dtype dtype, const void* lam, con
   else
     k_csr_outer<double><<<g, ST, 0, s>>>(rp, ci, (const double*)lam, (const double*)U, alpha, (double*)out, n);
   TG_CK_LAUNCH("k_csr_outer");
+  return TG_OK;
+}
+
+tg_status tg_scale_masked(tg_dtype dtype, const void* x, const uint8_t* dirichlet, double alpha, void* out,
+                          int64_t n, tg_stream stream) {
+  if ((dtype != TG_F32 && dtype != TG_F64) || n < 0 || (n > 0 && (!x || !out))) return TG_ERR_INVALID_ARG;
+  if (n == 0) return TG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int g = (int)std::min<int64_t>(tg::grid_for(n, ST), 8 * tg::sm_count());
+  if (dtype == TG_F32)
+    k_scale_masked<float><<<g, ST, 0, s>>>((const float*)x, dirichlet, (float)alpha, (float*)out, n);
+  else
+    k_scale_masked<double><<<g, ST, 0, s>>>((const double*)x, dirichlet, alpha, (double*)out, n);
+  TG_CK_LAUNCH("k_scale_masked");
   return TG_OK;
 }
 

@@ -60,6 +60,24 @@ struct tg_pattern {
   //     (3 bits) and the local index in the second word.
   //   elem_pos[e] (64 bit): position of vertex b's column in vertex a's row
   //     at bits [4(a*nv + b), ...).
+  //   fan (P1 triangles whose every node has a single fan of triangles
+  //     around it): per block b, a region of 16-bit words at fan + fan_off[b]
+  //     (kf = (fan_off[b + 1] - fan_off[b]) / fan_rs - 5 fan steps, fan_rs =
+  //     blk_rows rounded up to a multiple of 8):
+  //       4 * fan_rs words: per row t, a 64-bit word of 4-bit CSR positions of
+  //         the row's neighbours j_0, j_1, ... in the order of the fan;
+  //       fan_rs words: per row t, deg (bits 0-4), open fan (bit 5), CSR
+  //         position of the diagonal (bits 6-9);
+  //       kf * fan_rs words: record [k][t] of the k-th triangle of row t's fan
+  //         (the triangle between neighbours j_k and j_{k+1}): its index in the
+  //         block's element list (bits 0-10), the row's local vertex a in it
+  //         (bits 11-12), and whether j_k is vertex a + 2 rather than a + 1
+  //         (bit 13).
+  //     NULL when some node's triangles do not form one fan (or a block
+  //     holds more than 2048 elements); the row-owner Reduce serves then.
+  uint16_t* fan = nullptr;
+  int64_t* fan_off = nullptr;
+  int fan_rs = 0, fan_kmax = 0;
   int blk_rows = 0, blk_pb = 0;
   int blk_max_elems = 0, blk_max_inc = 0, blk_max_nz = 0;  // per-block maxima
   int64_t n_blk = 0;

@@ -329,3 +329,33 @@ def test_generic_path_when_blocks_do_not_fit(tg):
     out = [torch.empty(p.nnz, dtype=torch.float64, device="cuda") for _ in range(2)]
     tg.tg_batch_assemble(b, [x, x], [kd, kd], mg.PER_QP, [0.2, 0.2], out)
     assert torch.equal(out[0], vals) and torch.equal(out[1], vals)
+
+
+def test_vertex_joining_two_fans(tg):
+    """A vertex where two separate fans of triangles meet (a triangle hung on
+    the corner of a grid by that vertex alone): the pattern then keeps the
+    element-order Reduce, and every output matches the oracle."""
+    m = jittered_tri(12, seed=41)
+    X = np.vstack([m.coords, [[-0.30, -0.05], [-0.05, -0.30]]])
+    corner = int(np.flatnonzero((m.coords[:, 0] == 0) & (m.coords[:, 1] == 0))[0])
+    N = m.n_nodes + 2
+    cells = np.vstack([m.cells, [[corner, N - 2, N - 1]]])
+    g = np.random.default_rng(42)
+    k = g.uniform(0.5, 2.0, size=(len(cells), 3))
+    f = g.uniform(-1, 1, N)
+    p = tg.tg_build_pattern(dev(cells, torch.int32), N, mg.P1_TRI)
+    assert p.n_blocks > 0
+    x = dev(X, torch.float64)
+    vals, F = tg.tg_assemble_system(p, x, dev(k, torch.float64), mg.PER_QP, 0.6, dev(f, torch.float64), mg.PER_NODE)
+    ref = O.assemble_bilinear(mg.P1_TRI, cells, X, k, O.PER_QP, 0.6)
+    assert np.array_equal(p.col_idx.cpu().numpy(), ref.col)
+    assert relfro(vals.cpu().numpy(), ref.val) <= 1e-12
+    assert relfro(F.cpu().numpy(), O.assemble_load(mg.P1_TRI, cells, X, f, O.PER_NODE)) <= 1e-12
+    gv = g.normal(size=p.nnz)
+    gk, gx, gc = tg.tg_assemble_backward(p, x, dev(k, torch.float64), mg.PER_QP, 0.6, grad_vals=dev(gv, torch.float64))
+    rk, rx, rc = O.assemble_backward(mg.P1_TRI, cells, X, k, O.PER_QP, 0.6, grad_csr=O.CSR(ref.row_ptr, ref.col, gv))
+    assert relfro(gk.cpu().numpy().ravel(), rk) <= 1e-12 and relfro(gx.cpu().numpy(), rx) <= 1e-12
+    xf, kf = dev(X, torch.float32), dev(k, torch.float32)
+    v32 = tg.tg_assemble_bilinear(p, xf, kf, mg.PER_QP, 0.6)
+    r32 = O.assemble_bilinear(mg.P1_TRI, cells, host_as(X, torch.float32), host_as(k, torch.float32), O.PER_QP, 0.6)
+    assert relfro(v32.cpu().numpy(), r32.val) <= 2e-6
