@@ -109,6 +109,24 @@ def alg_bytes(kind, E, N, nnz, s, nv=3, Q=3, d=2):
     raise ValueError(kind)
 
 
+# Algorithmic floating-point operations per element of the minimal
+# formulation of each assembly (an FMA counts as two, a division as one; the
+# counts are derived in the design notes): the roof that FP64 runs meet on
+# the FP64 pipe, next to the HBM roof.
+ALU_FLOPS = {"fwd": 46, "system": 55, "bwd": 111, "elastic": 453}
+
+
+def two_roofs(ms, bytes_, flops, hbm_gbs, fp64_flops):
+    """Achieved fractions of the HBM roof, of the FP64 ALU roof, and of the
+    lower of the two (the binding bound: max of the two times over the
+    measured time)."""
+    t_hbm = bytes_ / (hbm_gbs * 1e9)
+    t_alu = flops / fp64_flops
+    t = ms * 1e-3
+    return {"hbm_frac": t_hbm / t, "alu_frac": t_alu / t, "frac_min_roof": max(t_hbm, t_alu) / t,
+            "flops_per_launch": flops, "alu_tflops": flops / t / 1e12, "bound": "alu" if t_alu > t_hbm else "hbm"}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -119,13 +137,12 @@ def load_peaks():
 
 
 # translation units and headers each timed kernel is built from
+_FWD_SRC = ["forward.cu", "fan.cuh", "blk_bilinear.cuh", "gather.cuh", "elements.cuh", "blocks.cuh", "async.cuh",
+            "tg_internal.cuh"]
 KERNEL_SOURCES = {
-    "system": ["forward.cu", "blk_bilinear.cuh", "gather.cuh", "elements.cuh", "blocks.cuh", "async.cuh",
-               "tg_internal.cuh"],
-    "fwd": ["forward.cu", "blk_bilinear.cuh", "gather.cuh", "elements.cuh", "blocks.cuh", "async.cuh",
+    "system": _FWD_SRC, "fwd": _FWD_SRC, "load": _FWD_SRC,
+    "bwd": ["backward.cu", "fan.cuh", "blk_bilinear.cuh", "gather.cuh", "elements.cuh", "blocks.cuh", "async.cuh",
             "tg_internal.cuh"],
-    "load": ["forward.cu", "gather.cuh", "elements.cuh", "blocks.cuh", "async.cuh", "tg_internal.cuh"],
-    "bwd": ["backward.cu", "gather.cuh", "elements.cuh", "blocks.cuh", "async.cuh", "tg_internal.cuh"],
 }
 
 
@@ -208,62 +225,77 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ------------------------------------------------------------------ reference arm: the CPU oracle
-def oracle_sample(m, cfg, n_elems=None):
-    """The workload restricted to its first n_elems elements (a contiguous run
-    of the Hilbert order, so a compact patch of the domain); all nodes kept."""
-    if n_elems is None or n_elems >= m.n_elems:
-        return m.cells, cfg["kappa"]
-    return m.cells[:n_elems], cfg["kappa"][:n_elems]
+# ------------------------------------------------------------------ the CPU oracle
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
 
 
-def oracle_step(m, cfg, cells, kappa, G=None):
-    """One pass of the path by the FP64 oracle: forward DOK scatter-add, load,
-    backward for an upstream gradient G of the values (drawn once per sample)."""
-    import oracle as O
-    K = O.assemble_bilinear(O.P1_TRI, cells, m.coords, kappa, O.PER_QP, cfg["c"])
-    O.assemble_load(O.P1_TRI, cells, m.coords, cfg["f"], O.PER_NODE)
-    if G is None or len(G) != K.nnz:
-        G = np.random.default_rng(0).normal(size=K.nnz)
-    O.assemble_backward(O.P1_TRI, cells, m.coords, kappa, O.PER_QP, cfg["c"], grad_csr=O.CSR(K.row_ptr, K.col, G))
-    return G
+def cpu_model():
+    """The host CPU's model name as lscpu reports it (None if unavailable)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+    except (OSError, subprocess.SubprocessError):
+        return None
+    for line in out.splitlines():
+        if line.lower().startswith("model name"):
+            return line.split(":", 1)[1].strip()
+    return None
 
 
-def cpu_oracle_rate(m, cfg, reps):
-    cells, kappa = oracle_sample(m, cfg)
-    G = oracle_step(m, cfg, cells, kappa)  # untimed: sizes G
+def f32_host(a):
+    """An input as the FP32 GPU run reads it, promoted back to FP64 for the oracle."""
+    return np.asarray(a, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def oracle_for(m, cfg, threads, G=None):
+    """The chunked FP64 oracle on the workload with FP32-rounded inputs (the
+    inputs of the FP32 GPU run), so one oracle pass serves both the CPU
+    timing and the FP32 error; G the upstream gradient of the values."""
+    from oracle.chunked import ChunkedOracle
+    return ChunkedOracle(m.cells, f32_host(m.coords), f32_host(cfg["kappa"]), f32_host(cfg["f"]), cfg["c"], threads,
+                         seed=1, G=G)
+
+
+def time_oracle(orc, reps):
+    """Seconds per pass of the oracle over its workload (after one untimed
+    pass), and that pass's results."""
+    res = orc.step()
     t0 = time.perf_counter()
     for _ in range(reps):
-        oracle_step(m, cfg, cells, kappa, G)
-    dt = time.perf_counter() - t0
-    return len(cells) * reps / dt, dt
-
-
-REF_SAMPLE = 262144  # elements per reference-arm step: 1/8 of the workload, about 1 s of oracle work
+        orc.step()
+    return (time.perf_counter() - t0) / reps, res
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on all host cores (elements in
+    contiguous chunks, one process each, partial results added in chunk
+    order), a full pass over the workload per step."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     m, cfg = workload()
-    cells, kappa = oracle_sample(m, cfg, REF_SAMPLE)
-    G = None
-    for _ in range(max(args.warmup, 1)):
-        G = oracle_step(m, cfg, cells, kappa, G)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle_step(m, cfg, cells, kappa, G)
-    dt = time.perf_counter() - t0
-    v = len(cells) * args.steps / dt
-    sample = (f"each step: the first {len(cells)} of {m.n_elems} Hilbert-ordered elements of the workload (all "
-              f"{m.n_nodes} nodes); forward DOK scatter-add, load and backward by the FP64 oracle, one host core")
+    cores = host_cores()
+    orc = oracle_for(m, cfg, cores)
+    try:
+        for _ in range(max(args.warmup, 1)):
+            orc.step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            orc.step()
+        dt = time.perf_counter() - t0
+    finally:
+        orc.close()
+    v = m.n_elems * args.steps / dt
+    sample = (f"each step: the full workload ({m.n_elems} elements, {m.n_nodes} nodes); forward DOK scatter-add, "
+              f"load and backward by the FP64 oracle in {cores} processes of contiguous element chunks, partial "
+              f"results added in chunk order")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "elements/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "elements": m.n_elems, "nodes": m.n_nodes},
-        "cpu_baseline": {"value": v, "unit": "elements/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "elements/s", "cores": cores, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": v, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -344,13 +376,47 @@ def main():
     kern = {"system": (statistics.mean(t_sys), alg_bytes("system", E, N, nnz, s)),
             "bwd": (statistics.mean(t_bwd), alg_bytes("bwd", E, N, nnz, s))}
     dom = max(kern, key=lambda k: kern[k][0])
-    names = {"system": "k_bilinear_blk<P1_TRI,float,UB,load>", "bwd": "k_backward_blk<2,float,gvals,UB>"}
+    names = {"system": "k_bilinear_fan<float,UB,load>", "bwd": "k_backward_fan<float,gvals,UB>"}
     ach = kern[dom][1] / (kern[dom][0] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "traffic": ncu_traffic(dom), "peak_source": f"{peak_src} (copy, burst)",
                 "algorithmic_bytes_per_launch": kern[dom][1]}
     per_kernel = {k: {"ms": v[0], "alg_GBps": v[1] / (v[0] * 1e-3) / 1e9, "frac_of_peak": v[1] / (v[0] * 1e-3) / 1e9 / peak,
                       "elements_per_s": E / (v[0] * 1e-3)} for k, v in kern.items()}
+
+    # ---------------- the same step, median of 30, and with the outputs' write-back inside the events
+    # The L2 flush between steps only reads, so a timed step ends with its
+    # outputs still dirty in L2.  A second read of the flush buffer right
+    # after the step, inside the events, evicts them (their write-back lands
+    # there); the same read timed alone on a clean L2 is subtracted.
+    def median_of(n, evict):
+        ts = []
+        for _ in range(n):
+            flush()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            step()
+            if evict:
+                flush(spin_us=0)
+            a1.record()
+            torch.cuda.synchronize()
+            ts.append(a0.elapsed_time(a1))
+        return statistics.median(ts)
+
+    def evict_alone(n):
+        ts = []
+        for _ in range(n):
+            flush()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            flush(spin_us=0)
+            a1.record()
+            torch.cuda.synchronize()
+            ts.append(a0.elapsed_time(a1))
+        return statistics.median(ts)
+
+    ms_med = max_over_ranks(median_of(30, False))
+    ms_wb = max_over_ranks(median_of(30, True) - evict_alone(30))
 
     # ---------------- end to end: pinned host inputs -> C-ABI calls -> host results
     # Every step copies all of its inputs host -> device and all of its
@@ -414,6 +480,11 @@ def main():
                       "l2": "flushed between steps by reading a 512 MB buffer (leaves L2 clean), outside the "
                             "per-step CUDA events",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+           "ms_per_step_median30": ms_med, "value_median30": replica_throughput(E, world, ms_med),
+           "ms_per_step_with_writeback": ms_wb,
+           "writeback_how": "median of 30 steps, each followed inside its events by a 512 MB read that evicts the "
+                            "step's outputs from L2 (their DRAM write-back included), minus the median of 30 such "
+                            "reads alone on a clean L2",
            "wall_s_timed_region": wall, "gpu_launches": launches_per_step * args.steps,
            "roofline": roofline, "kernels": per_kernel,
            "e2e": {"value": replica_throughput(E, world, e2e_ms), "unit": "elements/s", "h2d_bytes_per_step": bi,
@@ -433,12 +504,41 @@ def main():
             out["breakdown"] = batch_extras(tg, torch, dev, peak, flush)
     elif not args.no_extras and rank == 0:
         out["breakdown"] = extras(tg, torch, dev, m, cfg, p, peak, flush)
+    for k in list(out.get("breakdown", {})):
+        if k.startswith("fp32_err_"):
+            out.setdefault("fp32_err", {})[k[len("fp32_err_"):]] = out["breakdown"].pop(k)
     if not args.no_cpu_baseline and rank == 0:
-        reps = 3
-        rate, secs = cpu_oracle_rate(m, cfg, reps)
-        out["cpu_baseline"] = {"value": rate, "unit": "elements/s", "cores": 1, "kind": "oracle",
-                               "sample": f"{reps} passes over the full workload ({E} elements: forward DOK "
-                                         f"scatter-add, load, backward), {secs:.1f} s, FP64, one host core"}
+        # the FP64 oracle on the FP32-rounded inputs of this run: its timing
+        # on all host cores and on one, and the FP32 error of the step
+        G = f32_host(np.random.default_rng(1).normal(size=nnz))
+        cores = host_cores()
+        orc = oracle_for(m, cfg, cores, G)
+        try:
+            sec_n, (rv, rF, rk, rx, rc) = time_oracle(orc, 3)
+        finally:
+            orc.close()
+        orc = oracle_for(m, cfg, 1, G)
+        try:
+            sec_1, _ = time_oracle(orc, 1)
+        finally:
+            orc.close()
+        step()
+        torch.cuda.synchronize()
+        rel = lambda got, want: float(np.linalg.norm(np.asarray(got, np.float64).ravel() - np.ravel(want))
+                                      / np.linalg.norm(np.ravel(want)))
+        out.setdefault("fp32_err", {})["diffusion2d_1024"] = {
+            "vals": rel(vals.cpu().numpy(), rv), "F": rel(F.cpu().numpy(), rF),
+            "grad_kappa": rel(gk.cpu().numpy(), rk), "grad_coords": rel(gx.cpu().numpy(), rx),
+            "grad_c": rel(gc.cpu().numpy(), [rc]),
+            "how": "relative Frobenius error of the step's FP32 outputs against the FP64 oracle fed the same "
+                   "FP32-rounded inputs, every entry"}
+        out["cpu_baseline"] = {
+            "value": E / sec_n, "unit": "elements/s", "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": f"the full workload ({E} elements: forward DOK scatter-add, load, backward), FP64, in {cores} "
+                      f"processes of contiguous element chunks with partial results added in chunk order; mean of "
+                      f"3 passes ({sec_n:.2f} s each)",
+            "single_core": {"value": E / sec_1, "cores": 1,
+                            "sample": f"the same pass in one process, 1 pass ({sec_1:.2f} s)"}}
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -485,6 +585,9 @@ def extras(tg, torch, dev, m, cfg, p, peak, flush):
     """Breakdown: FP64, atomic comparison, elasticity, batched vs looped."""
     out = {}
     E, N, nnz = m.n_elems, m.n_nodes, p.nnz
+    fp64 = tg.tg_diag_fma_rate(torch.float64)
+    out["fp64_fma_peak_tflops"] = fp64 / 1e12
+    out["fp32_fma_peak_tflops"] = tg.tg_diag_fma_rate(torch.float32) / 1e12
     for dtn, dt, s in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
         d = lambda a, t=dt: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device=dev)
         x, k, f = d(m.coords), d(cfg["kappa"]), d(cfg["f"])
@@ -504,17 +607,21 @@ def extras(tg, torch, dev, m, cfg, p, peak, flush):
             "bwd_ms": ms_b, "bwd_alg_GBps": bb / ms_b / 1e6, "bwd_frac_hbm": bb / ms_b / 1e6 / peak,
             "fwd_plus_bwd_elements_per_s": E / (ms_f + ms_b) * 1e3, "load_ms": ms_l,
             "system_ms": ms_s, "system_alg_GBps": alg_bytes("system", E, N, nnz, s) / ms_s / 1e6}
+        if dt == torch.float64:
+            out[f"diffusion2d_{dtn}"]["roofs"] = {
+                "fwd": two_roofs(ms_f, bf, ALU_FLOPS["fwd"] * E, peak, fp64),
+                "system": two_roofs(ms_s, alg_bytes("system", E, N, nnz, s), ALU_FLOPS["system"] * E, peak, fp64),
+                "bwd": two_roofs(ms_b, bb, ALU_FLOPS["bwd"] * E, peak, fp64),
+                "fp64_peak_tflops": fp64 / 1e12}
     out.update(residual_extras(tg, torch, dev, m, cfg, p, peak, flush))
     out.update(facet_extras(tg, torch, dev, m, p, flush))
-    out["fp64_fma_peak_tflops"] = tg.tg_diag_fma_rate(torch.float64) / 1e12
-    out["fp32_fma_peak_tflops"] = tg.tg_diag_fma_rate(torch.float32) / 1e12
-    out.update(elasticity_extras(tg, torch, dev, peak, flush))
+    out.update(elasticity_extras(tg, torch, dev, peak, flush, fp64))
     out.update(batch_extras(tg, torch, dev, peak, flush))
     out.update(small_configs(tg, torch, dev))
     return out
 
 
-def elasticity_extras(tg, torch, dev, peak, flush):
+def elasticity_extras(tg, torch, dev, peak, flush, fp64=None):
     """Vector P1 elasticity on 64^3 Kuhn tetrahedra: forward and backward for
     an upstream gradient of the values, FP32 and FP64."""
     out = {}
@@ -536,8 +643,36 @@ def elasticity_extras(tg, torch, dev, peak, flush):
                                       "alg_GBps": be / ms_e / 1e6, "frac_hbm": be / ms_e / 1e6 / peak,
                                       "bwd_ms": ms_eb, "bwd_alg_GBps": bb / ms_eb / 1e6,
                                       "bwd_frac_hbm": bb / ms_eb / 1e6 / peak}
+        if dt == torch.float64 and fp64:
+            out[f"elasticity3d_{dtn}"]["roofs"] = {"fwd": two_roofs(ms_e, be, ALU_FLOPS["elastic"] * me.n_elems,
+                                                                    peak, fp64), "fp64_peak_tflops": fp64 / 1e12}
+        if dt == torch.float32:
+            tg.tg_assemble_elasticity(pe, x, lam, mu, tg.PER_ELEMENT, v)
+            out["fp32_err_elasticity3d_64"] = elasticity_sample_err(pe, me, ce, v)
     del pe
     return out
+
+
+def elasticity_sample_err(pe, me, ce, v, n_rows=2048, seed=12):
+    """FP32 error of the elasticity values on sampled node rows: the FP64
+    oracle (fed the FP32-rounded inputs) assembles the elements incident to
+    2,048 random nodes, which complete those nodes' rows; relative Frobenius
+    error over the sampled rows' 3 x 3 blocks."""
+    import oracle as O
+    g = np.random.default_rng(seed)
+    nodes = np.sort(g.choice(me.n_nodes, size=n_rows, replace=False))
+    hit = np.isin(me.cells, nodes).any(axis=1)
+    R = O.assemble_elasticity(me.cells[hit], f32_host(me.coords), f32_host(ce["lam"][hit]), f32_host(ce["mu"][hit]),
+                              O.PER_ELEMENT)
+    rows = (3 * nodes[:, None] + np.arange(3)[None, :]).ravel()
+    rp = pe.row_ptr.cpu().numpy().astype(np.int64)
+    vals = v.cpu().numpy().astype(np.float64)
+    got = np.concatenate([vals[rp[r]:rp[r + 1]] for r in rows])
+    want = np.concatenate([R.val[R.row_ptr[r]:R.row_ptr[r + 1]] for r in rows])
+    return {"vals": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+            "how": f"relative Frobenius error over the complete rows of {n_rows} random nodes (3 DoF rows each, "
+                   f"{len(want)} entries) against the FP64 oracle on the elements incident to them, FP32-rounded "
+                   f"inputs"}
 
 
 def batch_extras(tg, torch, dev, peak, flush):
@@ -581,6 +716,19 @@ def batch_extras(tg, torch, dev, peak, flush):
     ref = [v.clone() for v in vs]
     looped()
     same = all(torch.equal(a, b_) for a, b_ in zip(ref, vs))
+    # FP32 error of 8 instances (every 32nd) against the FP64 oracle on their FP32-rounded inputs
+    import oracle as O
+    num = den = 0.0
+    for j in range(0, len(insts), 32):
+        mi = insts[j]["mesh"]
+        R = O.assemble_bilinear(O.P2_TRI, mi.cells, f32_host(mi.coords), f32_host(insts[j]["kappa"]), O.PER_QP, 0.0)
+        got = ref[j].cpu().numpy().astype(np.float64)
+        num += float(np.sum((got - R.val) ** 2))
+        den += float(np.sum(R.val ** 2))
+    out["fp32_err_batched_p2"] = {"vals": (num / den) ** 0.5,
+                                  "how": "relative Frobenius error of the batched launch's values of 8 of the 256 "
+                                         "instances (every 32nd, all entries) against the FP64 oracle fed the "
+                                         "FP32-rounded inputs"}
     out["batched_p2_f32"] = {
         "instances": len(pats), "elements": tot_e, "alg_bytes": tot_b, "schedule": b.schedule(),
         "autotune_best_ms": tune_ms,

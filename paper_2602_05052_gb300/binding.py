@@ -116,17 +116,19 @@ def _dt(t: torch.Tensor) -> int:
     raise TypeError(f"unsupported dtype {t.dtype}")
 
 
-def _ptr(t, dtype=None, name="tensor", n=None):
+def _ptr(t, dtype=None, name="tensor", n=None, cur=None):
     """Raw device pointer of a tensor argument after checking it: a
-    contiguous CUDA tensor of the expected dtype on the current device, with
-    exactly n elements when n is given (the library reads and writes raw
-    pointers, so a short or misplaced buffer must be refused here)."""
+    contiguous CUDA tensor of the expected dtype on the current device (cur,
+    looked up when not given), with exactly n elements when n is given (the
+    library reads and writes raw pointers, so a short or misplaced buffer
+    must be refused here)."""
     if t is None:
         return None
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
-    if t.device.index != torch.cuda.current_device():
-        raise ValueError(f"{name} is on {t.device}, the current device is cuda:{torch.cuda.current_device()}")
+    cur = torch.cuda.current_device() if cur is None else cur
+    if t.get_device() != cur:
+        raise ValueError(f"{name} is on {t.device}, the current device is cuda:{cur}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     if dtype is not None and t.dtype != dtype:
@@ -552,8 +554,8 @@ def tg_batch_create(pats: list[Pattern]) -> Batch:
 def _ptr_array(ts, dtype, name, sizes=None):
     if sizes is not None and len(sizes) != len(ts):
         raise ValueError(f"{name}: {len(ts)} tensors for {len(sizes)} instances")
-    return (vp * len(ts))(*[_ptr(t, dtype, f"{name}[{k}]", None if sizes is None else sizes[k])
-                            for k, t in enumerate(ts)])
+    cur = torch.cuda.current_device()
+    return (vp * len(ts))(*[_ptr(t, dtype, name, None if sizes is None else sizes[k], cur) for k, t in enumerate(ts)])
 
 
 def _batch_sizes(b: Batch, layout: int):

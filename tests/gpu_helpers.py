@@ -22,11 +22,32 @@ def host_as(a, dtype):
     return a.astype(np.float32).astype(np.float64) if dtype == torch.float32 else a
 
 
+# every relative error computed during the session: (test id, value); the
+# conftest prints the largest per test at the end of the run
+ERRORS: list = []
+CURRENT = {"test": None}
+
+
+def rel_scalar(got, want):
+    """|got - want| / |want| of a scalar (recorded like relfro)."""
+    err = abs(float(got) - float(want)) / (abs(float(want)) if want != 0 else 1.0)
+    ERRORS.append((CURRENT["test"], err))
+    return err
+
+
+# A loss sum_i y_i^2 whose vector y is within relative Frobenius error t of
+# the oracle's is within 2 t + t^2 of the oracle's loss (|dL| <= 2 |y| |dy|
+# + |dy|^2): twice the vector bounds.
+LOSS_TOL = {torch.float64: 2e-12, torch.float32: 4e-6}
+
+
 def relfro(got, want):
     got = np.asarray(got, dtype=np.float64)
     want = np.asarray(want, dtype=np.float64)
     n = np.linalg.norm(want)
-    return float(np.linalg.norm(got - want) / (n if n > 0 else 1.0))
+    err = float(np.linalg.norm(got - want) / (n if n > 0 else 1.0))
+    ERRORS.append((CURRENT["test"], err))
+    return err
 
 
 def jittered_tri(n, seed=3, hilbert=True):

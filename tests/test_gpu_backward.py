@@ -14,8 +14,10 @@ pytestmark = pytest.mark.gpu
 
 ELS = [mg.P1_TRI, mg.P2_TRI, mg.P1_TET]
 DTYPES = [torch.float64, torch.float32]
-# gradients carry one more level of cancellation than the forward values
-GTOL = {torch.float64: 1e-12, torch.float32: 1e-5}
+# the gradients meet the same relative Frobenius bounds as the assembled
+# values: 1e-12 in FP64, 2e-6 in FP32 against the FP64 oracle fed the
+# FP32-rounded inputs (measured on GB300: at most about 6e-7)
+GTOL = TOL
 
 
 @pytest.fixture(scope="module")

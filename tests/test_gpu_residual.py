@@ -8,12 +8,11 @@ import torch
 
 import meshgen as mg
 import oracle as O
-from gpu_helpers import TOL, coef, dev, host_as, jittered_tri, mesh_for, relfro
+from gpu_helpers import LOSS_TOL, TOL, coef, dev, host_as, jittered_tri, mesh_for, rel_scalar, relfro
 
 pytestmark = pytest.mark.gpu
 
 DTYPES = [torch.float64, torch.float32]
-LOSS_TOL = {torch.float64: 1e-11, torch.float32: 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -45,7 +44,7 @@ def _check(tg, p, m, el, layout, c, k, x, f, fl, dtype, dirichlet=None):
                           host_as(f, dtype) if f is not None else None, fl if fl is not None else O.PER_NODE,
                           dirichlet)
     assert relfro(y.cpu().numpy(), want) <= TOL[dtype]
-    assert abs(loss.item() - wl) <= LOSS_TOL[dtype] * wl
+    assert rel_scalar(loss.item(), wl) <= LOSS_TOL[dtype]
     assert tg.tg_get_device_status(p) == (0, -1)
     return y, loss
 
@@ -107,7 +106,7 @@ def test_residual_without_row_blocks(tg):
                                  dev(dirichlet.astype(np.uint8), torch.uint8))
         want, wl = O.residual(mg.P1_TRI, cells, host_as(X, dt), host_as(k, dt), O.PER_QP, 0.2, host_as(xr, dt),
                               host_as(fr, dt), O.PER_NODE, dirichlet)
-        assert relfro(y.cpu().numpy(), want) <= TOL[dt] and abs(loss.item() - wl) <= LOSS_TOL[dt] * wl
+        assert relfro(y.cpu().numpy(), want) <= TOL[dt] and rel_scalar(loss.item(), wl) <= LOSS_TOL[dt]
         q = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
         assert q.n_blocks > 0
         yb, lb = tg.tg_residual(q, dev(m.coords, dt), dev(k, dt), mg.PER_QP, 0.2, dev(x, dt), dev(f, dt),

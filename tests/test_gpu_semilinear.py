@@ -8,7 +8,7 @@ import torch
 
 import meshgen as mg
 import oracle as O
-from gpu_helpers import TOL, dev, host_as, jittered_tri, mesh_for, relfro
+from gpu_helpers import LOSS_TOL, TOL, dev, host_as, jittered_tri, mesh_for, rel_scalar, relfro
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +41,7 @@ def test_semilinear_matches_oracle(tg, el, jac, dtype):
                                      host_as(x, dtype), R, host_as(f, dtype) if f is not None else None, O.PER_NODE,
                                      m.boundary, host_as(xr, dtype) if jac else None)
     assert relfro(y.cpu().numpy(), want) <= TOL[dtype]
-    assert abs(loss.item() - wl) <= (1e-11 if dtype == torch.float64 else 1e-5) * wl
+    assert rel_scalar(loss.item(), wl) <= LOSS_TOL[dtype]
     assert tg.tg_get_device_status(p) == (0, -1)
 
 
