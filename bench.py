@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / elasticity / batched breakdown")
-    ap.add_argument("--extras-only", choices=["residual", "facets", "batch", "elasticity"], default=None,
+    ap.add_argument("--extras-only", choices=["diffusion", "residual", "facets", "batch", "elasticity"], default=None,
                     help="run only this part of the breakdown (short runs, e.g. for profiling one kernel)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -494,7 +494,9 @@ def main():
            "clocks": clocks}
 
     if args.extras_only and rank == 0:
-        if args.extras_only == "residual":
+        if args.extras_only == "diffusion":
+            out["breakdown"] = diffusion_extras(tg, torch, dev, m, cfg, p, peak, flush)
+        elif args.extras_only == "residual":
             out["breakdown"] = residual_extras(tg, torch, dev, m, cfg, p, peak, flush)
         elif args.extras_only == "facets":
             out["breakdown"] = facet_extras(tg, torch, dev, m, p, flush)
@@ -583,6 +585,19 @@ def timed(torch, fn, flush, reps=10, warm=3):
 
 def extras(tg, torch, dev, m, cfg, p, peak, flush):
     """Breakdown: FP64, atomic comparison, elasticity, batched vs looped."""
+    out = diffusion_extras(tg, torch, dev, m, cfg, p, peak, flush)
+    fp64 = out["fp64_fma_peak_tflops"] * 1e12
+    out.update(residual_extras(tg, torch, dev, m, cfg, p, peak, flush))
+    out.update(facet_extras(tg, torch, dev, m, p, flush))
+    out.update(elasticity_extras(tg, torch, dev, peak, flush, fp64))
+    out.update(batch_extras(tg, torch, dev, peak, flush))
+    out.update(small_configs(tg, torch, dev))
+    return out
+
+
+def diffusion_extras(tg, torch, dev, m, cfg, p, peak, flush):
+    """The 2D diffusion kernels one by one in FP32 and FP64 (forward, atomic
+    comparison, backward, load, system), with the FP64 ALU roof."""
     out = {}
     E, N, nnz = m.n_elems, m.n_nodes, p.nnz
     fp64 = tg.tg_diag_fma_rate(torch.float64)
@@ -613,11 +628,6 @@ def extras(tg, torch, dev, m, cfg, p, peak, flush):
                 "system": two_roofs(ms_s, alg_bytes("system", E, N, nnz, s), ALU_FLOPS["system"] * E, peak, fp64),
                 "bwd": two_roofs(ms_b, bb, ALU_FLOPS["bwd"] * E, peak, fp64),
                 "fp64_peak_tflops": fp64 / 1e12}
-    out.update(residual_extras(tg, torch, dev, m, cfg, p, peak, flush))
-    out.update(facet_extras(tg, torch, dev, m, p, flush))
-    out.update(elasticity_extras(tg, torch, dev, peak, flush, fp64))
-    out.update(batch_extras(tg, torch, dev, peak, flush))
-    out.update(small_configs(tg, torch, dev))
     return out
 
 

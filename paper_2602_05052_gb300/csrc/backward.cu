@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(BB) k_backward_gather(const BwdArgs<T> a, cons
       for (int p = 0; p < NV; ++p)
 #pragma unroll
         for (int q = 0; q < NV; ++q) wm += Ws[p][q] * ts.M[p][q];
-      const T inv = T(1) / adet;
+      const T inv = tg::recip(adet);
       const T sgn = g.det > T(0) ? T(1) : T(-1);
       // Q = Nd Rbar Nd^T (d x d) and t = <Rbar, Nd^T Nd>; gk[q] = <R_q, Nd^T Nd>
       T Q[D][D], t;
@@ -365,7 +365,7 @@ __device__ __forceinline__ bool bwd_p1_element(const T (&x)[D + 1][D], const T (
   for (int p = 0; p < NV; ++p)
 #pragma unroll
     for (int q = 0; q < NV; ++q) wm += W[p][q] * tab.M[p][q];
-  const T inv = T(1) / adet;
+  const T inv = tg::recip(adet);
   const T sgn = gm.det > T(0) ? T(1) : T(-1);
   T y[NV][D];  // y[b][r] = sum_p W[p][b] n[p][r]
 #pragma unroll
@@ -490,12 +490,18 @@ __device__ __forceinline__ void bwd_blk_map(const BwdArgs<T>& a, const tg::RefTa
     }
     if constexpr (!FUSED) {
 #pragma unroll
-      for (int u = 0; u < UB; ++u)
+      for (int u = 0; u < UB; ++u) {
+        const uint32_t lo = (uint32_t)ep[u], hi = (uint32_t)(ep[u] >> 32);
 #pragma unroll
-        for (int p = 0; p < NV; ++p)
+        for (int p = 0; p < NV; ++p) {
+          const T* row = a.gvals + rpv[u][p];
 #pragma unroll
-          for (int q = 0; q < NV; ++q)
-            W[u][p][q] = __ldg(a.gvals + rpv[u][p] + (int)((ep[u] >> (4 * (p * NV + q))) & 15u));
+          for (int q = 0; q < NV; ++q) {
+            const int sh = 4 * (p * NV + q);
+            W[u][p][q] = __ldg(row + ((sh < 32 ? lo >> sh : hi >> (sh - 32)) & 15u));
+          }
+        }
+      }
     }
 #pragma unroll
     for (int u = 0; u < UB; ++u) {
@@ -525,7 +531,7 @@ __device__ __forceinline__ void bwd_blk_map(const BwdArgs<T>& a, const tg::RefTa
         for (int p = 0; p < NV; ++p)
 #pragma unroll
           for (int q = 0; q < NV; ++q) wm += W[u][p][q] * tab.M[p][q];
-        const T inv = T(1) / adet;
+        const T inv = tg::recip(adet);
         const T sgn = gm.det > T(0) ? T(1) : T(-1);
         T y[NV][D];  // y[b][r] = sum_p W[p][b] n[p][r]
 #pragma unroll

@@ -191,7 +191,7 @@ __device__ __forceinline__ void el_bwd_element(const ElBwdArgs<T>& a, const tg::
       for (int r = 0; r < 3; ++r) gx[c][r] = T(0);
     return;
   }
-  const T id = T(1) / gm.det;
+  const T id = tg::recip(gm.det);
   T G[3][4];  // G[r][c] = d phi_c / d x_r
 #pragma unroll
   for (int c = 0; c < 4; ++c)

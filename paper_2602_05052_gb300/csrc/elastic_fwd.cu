@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(128) k_elastic_geom(const FwdArgs<T> a, const 
     if (!(adet > tg::det_tiny<T>())) {
       tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
     } else {
-      const T inv = T(1) / adet;
+      const T inv = tg::recip(adet);
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(EB) k_elastic_gather(const FwdArgs<T> a, const
         tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
         continue;
       }
-      const T inv = T(1) / adet;
+      const T inv = tg::recip(adet);
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll

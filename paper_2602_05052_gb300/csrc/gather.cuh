@@ -109,7 +109,7 @@ __device__ __forceinline__ void p1_scales(const T (&kq)[NQ], const RefTab<T>& ts
   T s = ts.w[0] * kq[0];
 #pragma unroll
   for (int q = 1; q < NQ; ++q) s = fma(ts.w[q], kq[q], s);
-  sc = s * (T(1) / adet);
+  sc = s * recip(adet);
   mc = c * adet;
 }
 
@@ -161,7 +161,7 @@ __device__ __forceinline__ bool p2_elem_sym(const ElemIn<TG_P2_TRI, T>& in, T c,
 #pragma unroll
       for (int b = a; b < 6; ++b, ++k) K[k] += hx[a] * tc.gh[q][b][0] + hy[a] * tc.gh[q][b][1];
   }
-  const T inv = T(1) / adet, mc = c * adet;
+  const T inv = recip(adet), mc = c * adet;
   int k = 0;
 #pragma unroll
   for (int a = 0; a < 6; ++a)
@@ -222,7 +222,7 @@ __device__ __forceinline__ bool elem_row(const ElemIn<EL, T>& in, T c, const Ref
       p1_scales<3, T>(in.kq, ts, adet, c, sc, mc);
       p1_row<2, T>(g, la, sc, mc, ts.M[la], Krow);
     } else {
-      p2_row<T>(g, la, in.kq, T(1) / adet, c * adet, ts, tc, Krow);
+      p2_row<T>(g, la, in.kq, recip(adet), c * adet, ts, tc, Krow);
     }
   } else {
     Geom<3, T> g;

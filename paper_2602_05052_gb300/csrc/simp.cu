@@ -60,7 +60,7 @@ __device__ __forceinline__ bool quad_point(const T (&x)[4][2], const tg::RefTab<
   const T det = J00 * J11 - J01 * J10;
   const T ad = det < T(0) ? -det : det;
   if (!(ad > simp_tiny<T>())) return false;
-  const T inv = T(1) / det;
+  const T inv = tg::recip(det);
   // g = ghat J^{-1}:  J^{-1} = [[J11, -J01], [-J10, J00]] / det
 #pragma unroll
   for (int b = 0; b < 4; ++b) {

@@ -199,6 +199,10 @@ __host__ __device__ constexpr double det_tiny<double>() {
   return 1e-300;
 }
 
+// 1 / x rounded to nearest (IEEE), bitwise the quotient T(1) / x.
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+
 // Coefficient sum over quadrature points with the rule's weights.
 template <typename T, int NQ>
 __device__ __forceinline__ T weighted_coef(const T* __restrict__ v, int layout, int64_t e, const T (&w)[6], T wsum) {
