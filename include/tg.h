@@ -39,9 +39,11 @@
  *   columns sorted ascending, structural zeros kept, int32 indices.
  * - Determinism: for a fixed pattern every forward and backward call is
  *   bitwise reproducible from run to run (each output is summed in a fixed
- *   order: incident elements by increasing element index).  The only
- *   exception is tg_assemble_bilinear_atomic, the atomicAdd comparison
- *   variant.
+ *   order that the pattern determines: incident elements by increasing
+ *   element index, or, for P1 triangle meshes whose every node has a single
+ *   fan of triangles, the order of that fan, each off-diagonal entry being
+ *   the sum of its two terms).  The only exception is
+ *   tg_assemble_bilinear_atomic, the atomicAdd comparison variant.
  */
 #ifndef TG_H_
 #define TG_H_
