@@ -183,9 +183,10 @@ tg_status tg_assemble_bilinear_atomic(const tg_pattern* p, tg_dtype dtype, const
  *   K[(a,i),(b,j)] = sum_q w_q |det J| ( lam_q g_ai g_bj + mu_q g_aj g_bi + mu_q delta_ij g_a . g_b ).
  *   lam, mu     per layout (PER_ELEMENT, PER_QP or CONSTANT); vals_out [9 nnz_node]
  *               in the DoF-level CSR.  Pattern kind TG_P1_TET_VEC3.
- * In FP64 the element terms go through the pattern's per-element scratch
- * (computed once per element): FP64 calls on one pattern that overlap
- * (several streams) race. */
+ * The element terms go through the pattern's per-element scratch (computed
+ * once per element) in FP64, and in both precisions when the mesh's rows
+ * hold at most 16 nodes and its nodes at most 32 elements: such calls on one
+ * pattern that overlap (several streams) race. */
 tg_status tg_assemble_elasticity(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* lam,
                                  const void* mu, tg_layout layout, void* vals_out, tg_stream stream);
 

@@ -251,7 +251,7 @@ void tg_pattern_destroy(tg_pattern* p) {
   void* bufs[] = {p->cells,    p->inc_ptr,  p->inc_e,   p->inc_pos, p->row_ptr, p->col_idx, p->elem_slot,
                   p->row_ptr_dof, p->col_idx_dof, p->status, p->partials, p->bel, p->boff, p->bvbase, p->bel_cnt,
                   p->brec, p->elem_pos, p->arrivals,
-                  p->iperm, p->urp, p->iinc, p->irp, p->elem_scratch, p->fan, p->fan_off};
+                  p->iperm, p->urp, p->iinc, p->irp, p->elem_scratch, p->fan, p->fan_off, p->emask};
   for (void* b : bufs)
     if (b) cudaFree(b);
   cudaSetDevice(prev);

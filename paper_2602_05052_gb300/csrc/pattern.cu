@@ -453,6 +453,27 @@ __global__ void k_bel_words(const int32_t* __restrict__ cnt, int64_t nblk, int n
   if (b < nblk) words[b] = ((cnt[b] + 3) & ~3) + nv * (((cnt[b] + 7) & ~7) / 2);
 }
 
+// Vector elasticity: per node-level CSR entry (i, j) the mask of node i's
+// incident elements (bit m = the m-th in inc_e order) that also hold node
+// j, the elements around edge (i, j); 0 on the diagonal.  One thread per row
+// (at most 16 entries and 32 incident elements).
+__global__ void k_edge_masks(const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc_e,
+                             const uint32_t* __restrict__ inc_pos, const int32_t* __restrict__ row_ptr, int64_t N,
+                             uint32_t* __restrict__ emask) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  uint32_t mk[16];
+  for (int q = 0; q < 16; ++q) mk[q] = 0u;
+  const int j0 = inc_ptr[i], deg = inc_ptr[i + 1] - j0, r0 = row_ptr[i], len = row_ptr[i + 1] - r0;
+  for (int m = 0; m < deg; ++m) {
+    const uint32_t w = inc_pos[j0 + m];
+    const int la = inc_e[j0 + m] & 7;
+    for (int c = 0; c < 4; ++c)
+      if (c != la) mk[(w >> (8 * c)) & 15u] |= 1u << m;
+  }
+  for (int q = 0; q < len; ++q) emask[r0 + q] = mk[q];
+}
+
 // Per element: the position of every vertex's column in every vertex's row.
 // (Vector elasticity: the slot map is DoF-level, slot = 9 * row_ptr + 3 * pos.)
 __global__ void k_elem_pos(const int32_t* __restrict__ cells, const int32_t* __restrict__ elem_slot,
@@ -1037,6 +1058,12 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   // 6. DoF-level CSR for elasticity
   // packed positions of the elasticity backward (4-bit fields: rows of at
   // most 16 nodes); it reads the 32-bit slot map otherwise
+  if (el == TG_P1_TET_VEC3 && E > 0 && p->max_row_len <= 16 && p->max_deg <= 32) {
+    TG_CK(cudaMalloc(&p->emask, nnz * sizeof(uint32_t) + 16));
+    k_edge_masks<<<tg::grid_for(N, kThreads), kThreads, 0, s>>>(p->inc_ptr, p->inc_e, p->inc_pos, p->row_ptr, N,
+                                                                p->emask);
+    TG_CK_LAUNCH("k_edge_masks");
+  }
   if (el == TG_P1_TET_VEC3 && E > 0 && p->max_row_len <= 16) {
     TG_CK(cudaMalloc(&p->elem_pos, E * sizeof(uint64_t) + 16));
     k_elem_pos<<<tg::grid_for(E, kThreads), kThreads, 0, s>>>(p->cells, p->elem_slot, p->row_ptr, E, nv, 4, true,
@@ -1058,9 +1085,9 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   TG_CK(cudaMalloc(&p->arrivals, 16));
   TG_CK(cudaMemsetAsync(p->arrivals, 0, 16, s));
   // per-element results of the two-pass kernels: nv * dim values per
-  // element, 16 for vector elasticity (its forward's geometry)
+  // element, 20 for vector elasticity (its forward's geometry records)
   if ((nc == 1 || el == TG_P1_TET_VEC3) && E > 0)
-    TG_CK(cudaMalloc(&p->elem_scratch, (size_t)E * (nc == 1 ? nv * tg::dim_of(el) : 16) * sizeof(double)));
+    TG_CK(cudaMalloc(&p->elem_scratch, (size_t)E * (nc == 1 ? nv * tg::dim_of(el) : 20) * sizeof(double)));
   TG_CK(cudaStreamSynchronize(s));
   if ((st = read_status(p, s, "tg_build_pattern")) != TG_OK) return st;
   guard.ok = true;

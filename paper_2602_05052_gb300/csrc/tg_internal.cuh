@@ -76,6 +76,11 @@ struct tg_pattern {
   //     NULL when some node's triangles do not form one fan (or a block
   //     holds more than 2048 elements); the row-owner Reduce serves then.
   uint16_t* fan = nullptr;
+  // emask[s] (vector elasticity with rows of at most 16 nodes and at most 32
+  // incident elements per node): bit m set when the m-th incident element
+  // of the row's node (inc_e order) also holds the column node of node-level
+  // CSR entry s; 0 on the diagonal.  NULL otherwise.
+  uint32_t* emask = nullptr;
   int64_t* fan_off = nullptr;
   int fan_rs = 0, fan_kmax = 0;
   int blk_rows = 0, blk_pb = 0;
@@ -197,6 +202,18 @@ __host__ __device__ constexpr float det_tiny<float>() {
 template <>
 __host__ __device__ constexpr double det_tiny<double>() {
   return 1e-300;
+}
+
+// A 32-bit pattern carried in a T slot of shared memory, and back.
+template <typename T>
+__device__ __forceinline__ T bits_as(uint32_t b) {
+  if constexpr (sizeof(T) == 4) return __uint_as_float(b);
+  else return __longlong_as_double((long long)b);
+}
+template <typename T>
+__device__ __forceinline__ uint32_t as_bits(T x) {
+  if constexpr (sizeof(T) == 4) return __float_as_uint(x);
+  else return (uint32_t)__double_as_longlong(x);
 }
 
 // 1 / x rounded to nearest (IEEE), bitwise the quotient T(1) / x.
