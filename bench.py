@@ -566,14 +566,15 @@ class L2Flush:
             self.torch.cuda._sleep(int(spin_us * 2000))
 
 
-def timed(torch, fn, flush, reps=10, warm=3):
-    """Median of per-call CUDA-event times, L2 flushed before each call."""
+def timed(torch, fn, flush, reps=10, warm=3, spin_us=400):
+    """Median of per-call CUDA-event times, L2 flushed before each call (and
+    the GPU kept busy for spin_us while the host enqueues the call)."""
     for _ in range(warm):
         flush()
         fn()
     ts = []
     for _ in range(reps):
-        flush()
+        flush(spin_us)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         fn()
@@ -705,7 +706,9 @@ def batch_extras(tg, torch, dev, peak, flush):
     b = tg.tg_batch_create(pats)
     cs = [0.0] * len(pats)
     tune_ms = tg.tg_batch_autotune(b, xs, ks, tg.PER_QP, cs, vs, reps=3)
-    ms_b = timed(torch, lambda: tg.tg_batch_assemble(b, xs, ks, tg.PER_QP, cs, vs), flush)
+    # the host marshals and checks 768 tensors per batched call (about 0.5 ms
+    # in Python): a longer spin keeps that out of the device time
+    ms_b = timed(torch, lambda: tg.tg_batch_assemble(b, xs, ks, tg.PER_QP, cs, vs), flush, spin_us=2000)
 
     def looped():
         for pi, xi, ki, vi in zip(pats, xs, ks, vs):

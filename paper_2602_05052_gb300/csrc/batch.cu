@@ -100,10 +100,14 @@ struct InstBlk {
 template <int EL, typename T, int UB>
 __global__ void __launch_bounds__(128) k_batch_blk(const InstBlk* __restrict__ desc, const int2* __restrict__ items,
                                                    int64_t n_items, const __grid_constant__ BatchCall<T> call,
-                                                   const __grid_constant__ tg::RefTab<T> tab, int capE, int acc_n) {
+                                                   const __grid_constant__ tg::RefTab<T> tab, int capE, int acc_n,
+                                                   int fan_words) {
   constexpr int NV = tg::Elem<EL>::nv;
   extern __shared__ __align__(16) unsigned char smem[];
   T* acc = reinterpret_cast<T*>(smem + (size_t)NV * tg::kf_vecs<NV, T, false>() * capE * 16);
+  // a copy of the item's fan region (fan_words 16-bit words at most)
+  uint4* frs = reinterpret_cast<uint4*>(smem + (((size_t)NV * tg::kf_vecs<NV, T, false>() * capE * 16 +
+                                                  (size_t)acc_n * sizeof(T) + 15) & ~size_t(15)));
   for (int q = threadIdx.x; q < acc_n; q += blockDim.x) acc[q] = T(0);
   __syncthreads();
   for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -128,7 +132,7 @@ __global__ void __launch_bounds__(128) k_batch_blk(const InstBlk* __restrict__ d
     a.f = nullptr;
     a.f_layout = 0;
     a.F = nullptr;
-    if constexpr (EL == TG_P1_TRI) {
+    if constexpr (EL == TG_P1_TRI || EL == TG_P2_TRI) {
       if (d.fan != nullptr) {  // the fan-ordered Reduce, as tg_assemble_bilinear takes it
         tg::FanArgs g;
         g.urp = d.urp;
@@ -142,10 +146,22 @@ __global__ void __launch_bounds__(128) k_batch_blk(const InstBlk* __restrict__ d
         g.N = d.N;
         g.R = d.R;
         g.rs = d.fan_rs;
-        const tg::FanView fv = tg::fan_view_global(g, w.y);
-        tg::blk_bilinear_map<EL, T, UB, false>(a, tab, capE, fv, smem);
+        tg::FanView fv = tg::fan_view_global(g, w.y);
+        {  // the region into shared memory (read by the Reduce after the Map's barrier)
+          const int64_t f0 = d.fan_off[w.y], nq = (d.fan_off[w.y + 1] - f0) / 8;
+          const uint4* src = reinterpret_cast<const uint4*>(d.fan + f0);
+          for (int q = threadIdx.x; q < nq; q += blockDim.x) frs[q] = __ldg(src + q);
+          const uint16_t* f = reinterpret_cast<const uint16_t*>(frs);
+          fv.pos = reinterpret_cast<const unsigned long long*>(f);
+          fv.info = f + 4 * g.rs;
+          fv.rec = f + 5 * g.rs;
+          fv.info32 = reinterpret_cast<const uint32_t*>(f);
+          fv.rec32 = fv.info32 + g.rs;
+        }
+        tg::blk_bilinear_map<EL, T, UB, false, EL == TG_P2_TRI>(a, tab, capE, fv, smem);
         __syncthreads();
-        tg::fan_reduce_bilinear<T, false>(a, capE, fv, smem);
+        if constexpr (EL == TG_P2_TRI) tg::fan_reduce_p2<T>(a, capE, fv, smem);
+        else tg::fan_reduce_bilinear<T, false>(a, capE, fv, smem);
         __syncthreads();
         continue;
       }
@@ -197,6 +213,7 @@ struct tg_batch {
   int2* d_blk_items = nullptr;
   std::vector<int64_t> blk_chunk_items;
   int capE = 0, max_elems = 0;
+  int fan_words = 0;  // largest fan region of the instances (16-bit words)
 };
 
 namespace {
@@ -269,7 +286,8 @@ tg_status launch_blk_t(tg_batch* b, const void* const* coords, const void* const
                        void* const* vals, cudaStream_t s) {
   constexpr int NV = tg::Elem<EL>::nv;
   auto kern = k_batch_blk<EL, T, UB>;
-  const size_t smem = tg::blk_bilinear_work_bytes<NV, T, false>(b->capE, b->max_row_len, 128);
+  const size_t smem = ((tg::blk_bilinear_work_bytes<NV, T, false>(b->capE, b->max_row_len, 128) + 15) & ~size_t(15)) +
+                      (size_t)b->fan_words * 2;
   tg_status st = tg::set_smem((const void*)kern, smem);
   if (st != TG_OK) return st;
   int per_sm = b->sched.ctas_per_sm;
@@ -294,7 +312,8 @@ tg_status launch_blk_t(tg_batch* b, const void* const* coords, const void* const
     const int64_t i0 = b->blk_chunk_items[ch], n_items = b->blk_chunk_items[ch + 1] - i0;
     if (n_items == 0) continue;
     const int grid = (int)std::min<int64_t>(n_items, (int64_t)per_sm * tg::sm_count());
-    kern<<<grid, 128, smem, s>>>(b->d_blk, b->d_blk_items + i0, n_items, call, tab, b->capE, b->max_row_len * 128);
+    kern<<<grid, 128, smem, s>>>(b->d_blk, b->d_blk_items + i0, n_items, call, tab, b->capE, b->max_row_len * 128,
+                                 b->fan_words);
     TG_CK_LAUNCH("k_batch_blk");
   }
   return TG_OK;
@@ -384,6 +403,7 @@ tg_status setup_blocks(tg_batch* b) {
     TG_CK(cudaMemcpy(b->d_blk_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
   b->capE = capE;
   b->max_elems = max_elems;
+  for (const tg_pattern* p : b->pats) b->fan_words = std::max(b->fan_words, p->fan ? p->fan_maxw : 0);
   b->blk = true;
   return TG_OK;
 }

@@ -41,9 +41,30 @@ size_t blk_bilinear_work_bytes(int capE, int max_row_len, int rs) {
   return (size_t)NV * kf_vecs<NV, T, LOAD>() * capE * 16 + (size_t)max_row_len * rs * sizeof(T);
 }
 
+// Column order of output row r of the Map.  Rotated (the row-owner Reduce
+// and the P1 fans): column c is local node (r + c) mod NV.  P2 fan order: a
+// vertex row r as (r, r+1, r+2, edge(r, r+1), edge(r+2, r), opposite edge);
+// the edge row of edge e = r - 3 from vertex e to e + 1 as (r, e, e+1, e+2,
+// edge(e+1, e+2), edge(e+2, e)) (vertices mod 3; edge(v, v+1) is local
+// node 3 + v).
+template <int NV, bool FANP2>
+__host__ __device__ constexpr int map_col(int r, int c) {
+  if constexpr (!FANP2) {
+    return (r + c) % NV;
+  } else {
+    if (r < 3) {
+      const int o[6] = {r, (r + 1) % 3, (r + 2) % 3, 3 + r, 3 + (r + 2) % 3, 3 + (r + 1) % 3};
+      return o[c];
+    }
+    const int e = r - 3;
+    const int o[6] = {r, e, (e + 1) % 3, (e + 2) % 3, 3 + (e + 1) % 3, 3 + (e + 2) % 3};
+    return o[c];
+  }
+}
+
 // The Map of a block (any view with nbe, be[] and vtx(c, k)): every
-// distinct element's output rows into KF.
-template <int EL, typename T, int UB, bool LOAD, typename View>
+// distinct element's output rows into KF, columns in map_col order.
+template <int EL, typename T, int UB, bool LOAD, bool FANP2 = false, typename View>
 __device__ __forceinline__ void blk_bilinear_map(const FwdArgs<T>& a, const RefTab<T>& tab, int capE, const View& v,
                                                  void* kf_buf) {
   constexpr int NV = Elem<EL>::nv, NG = Elem<EL>::ngeo, NS = NV * (NV + 1) / 2;
@@ -87,7 +108,7 @@ __device__ __forceinline__ void blk_bilinear_map(const FwdArgs<T>& a, const RefT
         T row[NW * VN];
 #pragma unroll
         for (int c = 0; c < NV; ++c) {
-          const int b = (r + c) % NV, lo = r < b ? r : b, hi = r < b ? b : r;
+          const int b = map_col<NV, FANP2>(r, c), lo = r < b ? r : b, hi = r < b ? b : r;
           row[c] = K[lo * NV - lo * (lo - 1) / 2 + (hi - lo)];  // K_sym[lo][hi], rows packed upper
         }
 #pragma unroll

@@ -64,7 +64,7 @@ inline FanArgs fan_args(const tg_pattern* p) {
   g.nv = p->nv;
   g.R = p->blk_rows;
   g.rs = p->fan_rs;
-  g.capF = (5 + p->fan_kmax) * p->fan_rs;
+  g.capF = p->fan_maxw;
   return g;
 }
 
@@ -85,6 +85,8 @@ struct FanView {
   const unsigned long long* pos;  // pos[t]: neighbour positions in fan order, 4 bits each
   const uint16_t* info;       // info[t]: deg | open << 5 | diagonal position << 6
   const uint16_t* rec;        // rec[k * rs + t]: fan triangle k of row t
+  const uint32_t* info32;     // P2: info32[t], rec32[k * rs + t] (32-bit layout)
+  const uint32_t* rec32;
   const uint32_t* be;         // be[k]: element k (with the owner bit)
   const uint16_t* vo;         // vo[c * bs16 + k]: vertex c of element k, minus vbase
   __device__ int vtx(int c, int k) const { return vbase + (int)vo[c * bs16 + k]; }
@@ -112,6 +114,8 @@ __device__ __forceinline__ FanView fan_view_global(const FanArgs& g, int64_t blk
   v.pos = reinterpret_cast<const unsigned long long*>(f);
   v.info = f + 4 * g.rs;
   v.rec = f + 5 * g.rs;
+  v.info32 = reinterpret_cast<const uint32_t*>(f);
+  v.rec32 = v.info32 + g.rs;
   v.be = g.bel + g.boff[blk];
   v.vo = reinterpret_cast<const uint16_t*>(v.be + ((v.nbe + 3) & ~3));
   return v;
@@ -206,6 +210,8 @@ class FanPipe {
     v.pos = reinterpret_cast<const unsigned long long*>(f);
     v.info = f + 4 * rs;
     v.rec = f + 5 * rs;
+    v.info32 = reinterpret_cast<const uint32_t*>(f);
+    v.rec32 = v.info32 + rs;
     v.be = el(s);
     v.vo = reinterpret_cast<const uint16_t*>(el(s) + ((v.nbe + 3) & ~3));
     return v;
@@ -272,6 +278,81 @@ __device__ __forceinline__ void fan_reduce_bilinear(const FwdArgs<T>& a, int cap
     out[(inf >> 6) & 15u] = diag;
   }
   if constexpr (LOAD) a.F[v.pm[t]] = fs;
+}
+
+// Reduce of the P2 bilinear form over the fans (32-bit records).  KF holds
+// the Map's output rows in the fan order of blk_bilinear_map: a vertex row
+// a as (a, a+1, a+2, edge(a, a+1), edge(a+2, a), opposite edge), an edge row
+// as (itself, its endpoints u and w, the third vertex z, edge(w, z),
+// edge(z, u)).  Vertex rows: triangle k contributes to the diagonal, to its
+// neighbour j_k and the edge node between the row's node and j_k (with the
+// previous triangle's entries), to the opposite edge node (alone) and, as
+// carries, to j_{k+1} and its edge node.  Edge rows: the one or two
+// triangles add the diagonal and the endpoints' entries; the rest is
+// theirs alone.
+template <typename T>
+__device__ __forceinline__ void fan_reduce_p2(const FwdArgs<T>& a, int capE, const FanView& v, const void* kf_buf) {
+  constexpr int NW = kf_vecs<6, T, false>(), VN = Vec16<T>::n;
+  using V = typename Vec16<T>::type;
+  const V* KF = reinterpret_cast<const V*>(kf_buf);
+  const int t = (int)threadIdx.x;
+  if (v.r0 + t >= v.r1) return;
+  const uint32_t inf = v.info32[t];
+  const int deg = (int)(inf & 31u);
+  if (deg == 0) return;
+  T* out = a.out + v.up[t];
+  auto put = [&](int q, T x) { out[q] = x; };
+  const int x1 = (int)((inf >> 12) & 31u), x2 = (int)((inf >> 17) & 31u);
+  T diag = T(0), c1 = T(0), c2 = T(0), f1 = T(0), f2 = T(0);
+  int p1 = 0, p2 = 0;
+  for (int k = 0; k < deg; ++k) {
+    const uint32_t r = v.rec32[k * v.rs + t];
+    const V* src = KF + (int)((r >> 11) & 7u) * NW * capE + (int)(r & 2047u);
+    V x[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) x[w] = src[w * capE];
+    T kv[NW * VN];
+#pragma unroll
+    for (int q = 0; q < NW * VN; ++q) kv[q] = Vec16<T>::get(x[q / VN], q % VN);
+    const bool sw = ((r >> 14) & 1u) != 0u;
+    const int pA = (int)((r >> 15) & 31u), pB = (int)((r >> 20) & 31u), pC = (int)((r >> 25) & 31u);
+    diag += kv[0];
+    const T s1 = sw ? kv[2] : kv[1], s2 = sw ? kv[1] : kv[2];
+    if (inf & 32u) {  // edge node: the endpoints' sums, the rest written directly
+      c1 += s1;
+      c2 += s2;
+      put(pA, kv[3]);
+      put(pB, kv[4]);
+      put(pC, kv[5]);
+    } else {
+      const T e1 = sw ? kv[4] : kv[3], e2 = sw ? kv[3] : kv[4];
+      if (k == 0) {
+        f1 = s1;
+        f2 = e1;
+        p1 = pA;
+        p2 = pB;
+      } else {
+        put(pA, c1 + s1);
+        put(pB, c2 + e1);
+      }
+      put(pC, kv[5]);
+      c1 = s2;
+      c2 = e2;
+    }
+  }
+  if (inf & 32u) {
+    put(x1, c1);
+    put(x2, c2);
+  } else if (inf & 64u) {  // open fan: its two ends have one triangle each
+    put(p1, f1);
+    put(p2, f2);
+    put(x1, c1);
+    put(x2, c2);
+  } else {
+    put(p1, c1 + f1);
+    put(p2, c2 + f2);
+  }
+  put((int)((inf >> 7) & 31u), diag);
 }
 
 // Reduce of the load vector alone: Fe[a * capE + le] = F_e[a].

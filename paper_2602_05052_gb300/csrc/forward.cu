@@ -179,10 +179,27 @@ __global__ void __launch_bounds__(BT, blk_min_ctas_bt<TG_P1_TRI, T, UB, LOAD>())
   TG_FAN_PIPELINE_END
 }
 
-template <typename T, bool LOAD>
+// P2 triangles over the fans: the Map in the P2 fan column order, the
+// Reduce of fan_reduce_p2.
+template <typename T, int UB>
+__global__ void __launch_bounds__(BT, blk_min_ctas_bt<TG_P2_TRI, T, UB, false>()) k_bilinear_fan_p2(
+    const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab, const tg::FanArgs g) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  tg::FanPipe pipe;
+  unsigned char* kf = pipe.init(smem, g);
+  __syncthreads();  // publishes the mbarrier initialisation
+  TG_FAN_PIPELINE_BEGIN(pipe, g, a.status)
+  tg::blk_bilinear_map<TG_P2_TRI, T, UB, false, true>(a, tab, g.capE, v, kf);
+  __syncthreads();
+  tg::fan_reduce_p2<T>(a, g.capE, v, kf);
+  __syncthreads();  // stage s and the Map's rows are free again
+  TG_FAN_PIPELINE_END
+}
+
+template <typename T, bool LOAD, int NV = 3>
 size_t bilinear_fan_smem(const tg_pattern* p) {
   const tg::FanArgs g = tg::fan_args(p);
-  return tg::fan_stage_bytes(g.R, g.capF, g.capE, 3) + (size_t)3 * tg::kf_vecs<3, T, LOAD>() * g.capE * 16;
+  return tg::fan_stage_bytes(g.R, g.capF, g.capE, NV) + (size_t)NV * tg::kf_vecs<NV, T, LOAD>() * g.capE * 16;
 }
 
 template <typename T, int UB>
@@ -404,6 +421,22 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
   }
   const size_t smem = tab_bytes<T>() + stage;
   const int cap = std::max(1, R * p->max_deg);
+  if constexpr (EL == TG_P2_TRI) {
+    const size_t sb = bilinear_fan_smem<T, false, 6>(p);
+    if (use_fan(p, sb)) {
+      tg_status st = TG_OK;
+      auto go = [&](auto kern) {
+        dim3 grid;
+        if ((st = launch_blk(kern, sb, p, &grid)) != TG_OK) return;
+        kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::fan_args(p));
+      };
+      if (blk_ub<T>(p) <= 1) go(k_bilinear_fan_p2<T, 1>);
+      else go(k_bilinear_fan_p2<T, 2>);
+      if (st != TG_OK) return st;
+      TG_CK_LAUNCH("k_bilinear_fan_p2");
+      return TG_OK;
+    }
+  }
   if constexpr (EL == TG_P1_TRI) {
     const size_t sb = bilinear_fan_smem<T, false>(p);
     if (use_fan(p, sb)) {

@@ -668,6 +668,176 @@ __global__ void k_blk_max(const int* __restrict__ v, int64_t n, int* __restrict_
   if (b < n) atomicMax(out, v[b]);
 }
 
+// P2 triangles: the same fans at the vertex rows, and the one or two
+// triangles of every edge-node row, as 32-bit records (layout in
+// tg_internal.cuh).  Vertex row, fan triangle k between neighbours j_k and
+// j_{k+1}: the positions of j_k, of the edge node between the row's node and
+// j_k, and of the opposite edge node.  Edge row (the node on edge (u, w)),
+// triangle k: the positions of its third vertex z and of its edge nodes on
+// (w, z) and (z, u), with the swap bit when the triangle's own (u, w) runs
+// the other way than the first triangle's.  The records come from the
+// rows' incidence records (brec, two words: the six 5-bit positions of
+// local nodes (a + c) mod 6, then a and the element's index in the block).
+__global__ void k_fan_rows_p2(const int32_t* __restrict__ iinc, const int32_t* __restrict__ irp,
+                              const uint32_t* __restrict__ brec, int64_t N, int R, uint32_t* __restrict__ info,
+                              uint32_t* __restrict__ rec, int* __restrict__ kmax, int* __restrict__ bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int j0 = iinc[i], deg = iinc[i + 1] - j0, len = irp[i + 1] - irp[i];
+  if (deg == 0) {
+    info[i] = 0;
+    return;
+  }
+  if (deg > kFanMax) {
+    atomicOr(bad, 1);
+    return;
+  }
+  uint8_t pos[kFanMax][6];
+  int la[kFanMax], le[kFanMax];
+  for (int m = 0; m < deg; ++m) {
+    const uint32_t x = brec[2 * (j0 + m)], y = brec[2 * (j0 + m) + 1];
+    la[m] = (int)(y & 7u);
+    le[m] = (int)(y >> 3);
+    for (int c = 0; c < 6; ++c) pos[m][(la[m] + c) % 6] = (uint8_t)((x >> (5 * c)) & 31u);
+    if (le[m] >= 2048 || (la[m] < 3) != (la[0] < 3)) {
+      atomicOr(bad, 1);
+      return;
+    }
+  }
+  const int dpos = pos[0][la[0]];
+  if (la[0] >= 3) {  // edge node: one or two triangles
+    const int a0 = la[0] - 3, u = pos[0][a0], w = pos[0][(a0 + 1) % 3];
+    if (deg > 2 || len != 3 + 3 * deg) {
+      atomicOr(bad, 1);
+      return;
+    }
+    for (int m = 0; m < deg; ++m) {
+      const int a = la[m] - 3, uT = pos[m][a], wT = pos[m][(a + 1) % 3];
+      const bool swap = uT != u;
+      if (swap ? (uT != w || wT != u) : (wT != w)) {
+        atomicOr(bad, 1);
+        return;
+      }
+      rec[i * kFanMax + m] = (uint32_t)le[m] | ((uint32_t)la[m] << 11) | ((swap ? 1u : 0u) << 14) |
+                             ((uint32_t)pos[m][(a + 2) % 3] << 15) | ((uint32_t)pos[m][3 + (a + 1) % 3] << 20) |
+                             ((uint32_t)pos[m][3 + (a + 2) % 3] << 25);
+    }
+    info[i] = (uint32_t)deg | 32u | ((uint32_t)dpos << 7) | ((uint32_t)u << 12) | ((uint32_t)w << 17);
+    atomicMax(kmax + i / R, deg);
+    return;
+  }
+  // vertex node: walk the fan over the vertex neighbours' positions
+  int cnt[32];
+  for (int q = 0; q < 32; ++q) cnt[q] = 0;
+  for (int m = 0; m < deg; ++m) {
+    cnt[pos[m][(la[m] + 1) % 3]]++;
+    cnt[pos[m][(la[m] + 2) % 3]]++;
+  }
+  int start = 0, prev = pos[0][(la[0] + 1) % 3];
+  bool open = false;
+  for (int q = 0; q < 32; ++q) {
+    if (cnt[q] > 2) {
+      atomicOr(bad, 1);
+      return;
+    }
+    if (cnt[q] == 1 && !open) {
+      for (int m = 0; m < deg; ++m)
+        if (pos[m][(la[m] + 1) % 3] == q || pos[m][(la[m] + 2) % 3] == q) {
+          start = m;
+          break;
+        }
+      prev = q;
+      open = true;
+    }
+  }
+  unsigned used = 0;
+  int m = start, k = 0, next = -1, next_e = -1, first = prev;
+  while (true) {
+    used |= 1u << m;
+    const int a = la[m], v1 = pos[m][(a + 1) % 3], v2 = pos[m][(a + 2) % 3];
+    const int e1 = pos[m][3 + a], e2 = pos[m][3 + (a + 2) % 3], op = pos[m][3 + (a + 1) % 3];
+    const bool swap = prev == v2;
+    next = swap ? v1 : v2;
+    next_e = swap ? e1 : e2;
+    rec[i * kFanMax + k] = (uint32_t)le[m] | ((uint32_t)a << 11) | ((swap ? 1u : 0u) << 14) | ((uint32_t)prev << 15) |
+                           ((uint32_t)(swap ? e2 : e1) << 20) | ((uint32_t)op << 25);
+    ++k;
+    int nm = -1;
+    for (int q = 0; q < deg; ++q)
+      if (!((used >> q) & 1u) && (pos[q][(la[q] + 1) % 3] == next || pos[q][(la[q] + 2) % 3] == next)) {
+        nm = q;
+        break;
+      }
+    if (nm < 0) break;
+    prev = next;
+    m = nm;
+  }
+  const int nn = open ? deg + 1 : deg;
+  if (k != deg || (!open && next != first) || len != 1 + 2 * nn + deg) {
+    atomicOr(bad, 1);
+    return;
+  }
+  info[i] = (uint32_t)deg | (open ? 64u : 0u) | ((uint32_t)dpos << 7) |
+            (open ? (((uint32_t)next << 12) | ((uint32_t)next_e << 17)) : 0u);
+  atomicMax(kmax + i / R, deg);
+}
+
+// Fan starts of the closed vertex fans of a P2 pattern, chosen as in
+// k_fan_rotate (rotations only: a record carries its first neighbour's
+// positions, which a reversal would change).
+__global__ void k_fan_rotate_p2(const uint32_t* __restrict__ info, uint32_t* __restrict__ rec, int64_t N, int R) {
+  const int64_t qid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nq = (R + 7) / 8;
+  const int64_t b = qid / nq;
+  const int q = (int)(qid % nq);
+  const int64_t i0 = b * R + 8 * q;
+  if (i0 >= N || 8 * q >= R) return;
+  unsigned char used[kFanMax][8];
+  for (int k = 0; k < kFanMax; ++k)
+    for (int g = 0; g < 8; ++g) used[k][g] = 0;
+  for (int t = 0; t < 8 && 8 * q + t < R && i0 + t < N; ++t) {
+    const int64_t i = i0 + t;
+    const int deg = (int)(info[i] & 31u);
+    uint32_t r0[kFanMax];
+    for (int k = 0; k < deg; ++k) r0[k] = rec[i * kFanMax + k];
+    const bool fixed = (info[i] & (32u | 64u)) != 0u;  // edge rows and open fans keep their order
+    const int nrot = fixed || deg == 0 ? 1 : deg;
+    int best = 0, best_cost = 1 << 30;
+    for (int rot = 0; rot < nrot; ++rot) {
+      int cost = 0;
+      for (int m = 0; m < deg; ++m) cost += used[m][r0[(rot + m) % deg] & 7u];
+      if (cost < best_cost) {
+        best_cost = cost;
+        best = rot;
+      }
+    }
+    for (int m = 0; m < deg; ++m) {
+      const uint32_t r = r0[(best + m) % deg];
+      rec[i * kFanMax + m] = r;
+      used[m][r & 7u]++;
+    }
+  }
+}
+
+// Scatter the P2 rows' fan data into the blocks' regions: info (32 bits per
+// row) then the records [k][t] (32 bits each), both padded to rs rows.
+__global__ void k_fan_place_p2(const uint32_t* __restrict__ info, const uint32_t* __restrict__ rec,
+                               const int64_t* __restrict__ off, const int* __restrict__ kmax, int64_t N, int R, int rs,
+                               int64_t nblk, uint16_t* __restrict__ fan) {
+  const int64_t b = blockIdx.x;
+  if (b >= nblk) return;
+  uint32_t* g = reinterpret_cast<uint32_t*>(fan + off[b]);
+  const int kb = kmax[b];
+  for (int t = threadIdx.x; t < rs; t += blockDim.x) {
+    const int64_t i = b * R + t;
+    const bool live = t < R && i < N;
+    const uint32_t inf = live ? info[i] : 0u;
+    g[t] = inf;
+    const int d = (int)(inf & 31u);
+    for (int k = 0; k < kb; ++k) g[(1 + k) * rs + t] = k < d ? rec[i * kFanMax + k] : 0u;
+  }
+}
+
 // Region words of block b: (5 + kmax) * rs.
 __global__ void k_fan_words(const int* __restrict__ kmax, int64_t nblk, int rs, int32_t* __restrict__ words) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -761,6 +931,58 @@ int blk_rows_of(tg_element el) {
   return el == TG_P1_TRI ? 120 : el == TG_P2_TRI ? 128 : 64;
 }
 
+// Region words of block b of a P2 pattern: (2 + 2 kmax) * rs (32-bit entries).
+__global__ void k_fan_words_p2(const int* __restrict__ kmax, int64_t nblk, int rs, int32_t* __restrict__ words) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < nblk) words[b] = (2 + 2 * kmax[b]) * rs;
+}
+
+tg_status build_fans_p2(tg_pattern* p, cudaStream_t s) {
+  const int R = p->blk_rows, rs = (R + 7) & ~7;
+  const int64_t N = p->N, nblk = p->n_blk;
+  Tmp tmp;
+  uint32_t *info = nullptr, *rec = nullptr;
+  int *kmax = nullptr, *bad = nullptr;
+  int32_t* words = nullptr;
+  TG_CK(tmp.alloc(&info, N));
+  TG_CK(tmp.alloc(&rec, N * kFanMax));
+  TG_CK(tmp.alloc(&kmax, nblk));
+  TG_CK(tmp.alloc(&bad, 1));
+  TG_CK(tmp.alloc(&words, nblk));
+  TG_CK(cudaMemsetAsync(kmax, 0, nblk * sizeof(int), s));
+  TG_CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  k_fan_rows_p2<<<tg::grid_for(N, kThreads), kThreads, 0, s>>>(p->iinc, p->irp, p->brec, N, R, info, rec, kmax, bad);
+  TG_CK_LAUNCH("k_fan_rows_p2");
+  int hb = 0;
+  TG_CK(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  if (hb) return TG_OK;
+  k_fan_rotate_p2<<<tg::grid_for(nblk * ((R + 7) / 8), 64), 64, 0, s>>>(info, rec, N, R);
+  TG_CK_LAUNCH("k_fan_rotate_p2");
+  k_fan_words_p2<<<tg::grid_for(nblk, kThreads), kThreads, 0, s>>>(kmax, nblk, rs, words);
+  TG_CK_LAUNCH("k_fan_words_p2");
+  TG_CK(cudaMalloc(&p->fan_off, (nblk + 1) * sizeof(int64_t) + 16));
+  tg_status st = scan_exclusive<int32_t>(words, p->fan_off, nblk, s);
+  if (st != TG_OK) return st;
+  int* kmax_all = bad;  // reuse
+  TG_CK(cudaMemsetAsync(kmax_all, 0, sizeof(int), s));
+  k_blk_max<<<tg::grid_for(nblk, kThreads), kThreads, 0, s>>>(kmax, nblk, kmax_all);
+  TG_CK_LAUNCH("k_blk_max");
+  int64_t total = 0;
+  int hk = 0;
+  TG_CK(cudaMemcpyAsync(&total, p->fan_off + nblk, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaMemcpyAsync(&hk, kmax_all, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  TG_CK(cudaMalloc(&p->fan, total * sizeof(uint16_t) + 16));
+  k_fan_place_p2<<<(unsigned)nblk, 128, 0, s>>>(info, rec, p->fan_off, kmax, N, R, rs, nblk, p->fan);
+  TG_CK_LAUNCH("k_fan_place_p2");
+  TG_CK(cudaStreamSynchronize(s));  // tmp buffers are freed on return
+  p->fan_rs = rs;
+  p->fan_kmax = hk;
+  p->fan_maxw = (2 + 2 * hk) * rs;
+  return TG_OK;
+}
+
 // Fans of a P1 triangle pattern with row blocks; leaves p->fan == NULL when
 // some node's triangles are not one fan.
 tg_status build_fans(tg_pattern* p, cudaStream_t s) {
@@ -810,6 +1032,7 @@ tg_status build_fans(tg_pattern* p, cudaStream_t s) {
   TG_CK(cudaStreamSynchronize(s));  // tmp buffers are freed on return
   p->fan_rs = rs;
   p->fan_kmax = hk;
+  p->fan_maxw = (5 + hk) * rs;
   return TG_OK;
 }
 
@@ -931,6 +1154,7 @@ tg_status build_blocks(tg_pattern* p, cudaStream_t s) {
   p->blk_max_nz = h[1];
   p->blk_max_elems = h[2];
   if (p->el == TG_P1_TRI && h[2] <= 2048 && (st = build_fans(p, s)) != TG_OK) return st;
+  if (p->el == TG_P2_TRI && h[2] <= 2048 && (st = build_fans_p2(p, s)) != TG_OK) return st;
   if (nv * nv * pb <= 64) {
     TG_CK(cudaMalloc(&p->elem_pos, E * sizeof(uint64_t) + 16));
     k_elem_pos<<<tg::grid_for(E, kThreads), kThreads, 0, s>>>(p->cells, p->elem_slot, p->row_ptr, E, nv, pb, false,

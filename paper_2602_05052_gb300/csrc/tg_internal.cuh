@@ -75,6 +75,12 @@ struct tg_pattern {
   //         (bit 13).
   //     NULL when some node's triangles do not form one fan (or a block
   //     holds more than 2048 elements); the row-owner Reduce serves then.
+  //     P2 triangles: per block, 32-bit words: info[t] (deg bits 0-4, edge
+  //     node bit 5, open fan bit 6, diagonal position bits 7-11, then two
+  //     5-bit positions: an open fan's last vertex neighbour and edge node,
+  //     or an edge node's endpoints u and w), then records [k][t]: the
+  //     element's list index (bits 0-10), the row's local node a (bits 11-13),
+  //     a swap bit (14) and three 5-bit positions (bits 15-29).
   uint16_t* fan = nullptr;
   // emask[s] (vector elasticity with rows of at most 16 nodes and at most 32
   // incident elements per node): bit m set when the m-th incident element
@@ -82,7 +88,7 @@ struct tg_pattern {
   // CSR entry s; 0 on the diagonal.  NULL otherwise.
   uint32_t* emask = nullptr;
   int64_t* fan_off = nullptr;
-  int fan_rs = 0, fan_kmax = 0;
+  int fan_rs = 0, fan_kmax = 0, fan_maxw = 0;  // fan_maxw: largest region, 16-bit words
   int blk_rows = 0, blk_pb = 0;
   int blk_max_elems = 0, blk_max_inc = 0, blk_max_nz = 0;  // per-block maxima
   int64_t n_blk = 0;
