@@ -148,6 +148,20 @@ tg_status tg_pattern_shape(const tg_pattern* p, tg_element* el, int64_t* n_elems
  * the generic row-owner kernels serve every call.  Either pointer may be NULL. */
 tg_status tg_pattern_row_blocks(const tg_pattern* p, int32_t* rows_per_block, int64_t* n_blocks);
 
+/* The optional layouts a pattern was built with (no counterpart in the
+ * paper), as the OR of these flags in *flags: row blocks (see above); fans,
+ * the fan-ordered Reduce of P1 and P2 triangles (built with row blocks when
+ * every node's triangles form one fan); packed positions (elem_pos, the
+ * backward's upstream-weight gather); elasticity edge masks (the two-pass
+ * FP32 elasticity forward).  They select the kernels that serve a call;
+ * results do not depend on them beyond the documented summation orders.
+ * Returns TG_ERR_INVALID_ARG for a NULL argument. */
+#define TG_LAYOUT_ROW_BLOCKS 1u
+#define TG_LAYOUT_FANS 2u
+#define TG_LAYOUT_ELEM_POS 4u
+#define TG_LAYOUT_EDGE_MASKS 8u
+tg_status tg_pattern_layouts(const tg_pattern* p, uint32_t* flags);
+
 /* Read and clear the device status word of a pattern.  SYNCHRONISES the
  * device.  Returns TG_OK or the first recorded data error; *first_bad_elem
  * (may be NULL) gets the smallest offending element index, or -1. */

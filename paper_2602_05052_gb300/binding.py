@@ -15,6 +15,8 @@ import torch
 from .build import LIB
 
 P1_TRI, P2_TRI, P1_TET, P1_TET_VEC3, Q1_QUAD_VEC2 = 0, 1, 2, 3, 4
+# Pattern.layouts flags (include/tg.h)
+LAYOUT_ROW_BLOCKS, LAYOUT_FANS, LAYOUT_ELEM_POS, LAYOUT_EDGE_MASKS = 1, 2, 4, 8
 F32, F64 = 0, 1
 PER_ELEMENT, PER_QP, PER_NODE, CONSTANT = 0, 1, 2, 3
 NV = {P1_TRI: 3, P2_TRI: 6, P1_TET: 4, P1_TET_VEC3: 4, Q1_QUAD_VEC2: 4}
@@ -54,6 +56,7 @@ def lib():
         "tg_pattern_shape": (i32, [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32),
                                    C.POINTER(i32)]),
         "tg_pattern_row_blocks": (i32, [vp, C.POINTER(i32), C.POINTER(i64)]),
+        "tg_pattern_layouts": (i32, [vp, C.POINTER(C.c_uint32)]),
         "tg_get_device_status": (i32, [vp, C.POINTER(i64)]),
         "tg_pattern_destroy": (None, [vp]),
         "tg_assemble_bilinear": (i32, [vp, i32, vp, vp, i32, dbl, vp, vp]),
@@ -205,6 +208,9 @@ class Pattern:
         rb, nb = i32(), i64()
         _check(L.tg_pattern_row_blocks(handle, C.byref(rb), C.byref(nb)), "tg_pattern_row_blocks")
         self.rows_per_block, self.n_blocks = rb.value, nb.value
+        lf = C.c_uint32()
+        _check(L.tg_pattern_layouts(handle, C.byref(lf)), "tg_pattern_layouts")
+        self.layouts = lf.value
         self._rp, self._ci, self._es, self.slot_stride = rp.value, ci.value, es.value, ss.value
 
     def _view(self, ptr, n):

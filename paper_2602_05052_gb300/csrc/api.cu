@@ -228,6 +228,14 @@ tg_status tg_pattern_row_blocks(const tg_pattern* p, int32_t* rows_per_block, in
   return TG_OK;
 }
 
+tg_status tg_pattern_layouts(const tg_pattern* p, uint32_t* flags) {
+  if (!p || !flags) return TG_ERR_INVALID_ARG;
+  *flags = (p->bel ? TG_LAYOUT_ROW_BLOCKS : 0u) | (p->fan ? TG_LAYOUT_FANS : 0u) |
+           (p->elem_pos ? TG_LAYOUT_ELEM_POS : 0u) |
+           (p->emask ? TG_LAYOUT_EDGE_MASKS : 0u);
+  return TG_OK;
+}
+
 tg_status tg_get_device_status(const tg_pattern* p, int64_t* first_bad_elem) {
   if (!p) return TG_ERR_INVALID_ARG;
   TG_CK(cudaSetDevice(p->device));

@@ -93,6 +93,9 @@ def test_host_validation_without_gpu(L):
                                          vp, vp, vp, vp]
     assert L.tg_semilinear_residual(None, 0, None, None, 1, 0.0, None, None, 2, None, None, None, None, None,
                                     None) == 1
+    L.tg_pattern_layouts.argtypes = [vp, vp]
+    flags = C.c_uint32(7)
+    assert L.tg_pattern_layouts(None, C.byref(flags)) == 1 and flags.value == 7
     L.tg_build_facets.argtypes = [vp, vp, C.c_int64, vp, C.POINTER(vp)]
     assert L.tg_build_facets(None, None, 0, None, C.byref(out)) == 1
     assert L.tg_build_facets(None, None, 0, None, None) == 1

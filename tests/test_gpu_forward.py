@@ -312,6 +312,7 @@ def test_generic_path_when_blocks_do_not_fit(tg):
     f = g.uniform(-1, 1, m.n_nodes)
     p = tg.tg_build_pattern(dev(cells, torch.int32), m.n_nodes, mg.P1_TRI)
     assert (p.rows_per_block, p.n_blocks) == (0, 0)
+    assert p.layouts & (tg.LAYOUT_ROW_BLOCKS | tg.LAYOUT_FANS) == 0
     q = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
     assert q.rows_per_block > 0 and q.n_blocks == -(-m.n_nodes // q.rows_per_block)
     x, kd, fd = dev(X, torch.float64), dev(k, torch.float64), dev(f, torch.float64)
@@ -345,6 +346,8 @@ def test_vertex_joining_two_fans(tg):
     f = g.uniform(-1, 1, N)
     p = tg.tg_build_pattern(dev(cells, torch.int32), N, mg.P1_TRI)
     assert p.n_blocks > 0
+    assert p.layouts & tg.LAYOUT_ROW_BLOCKS and not p.layouts & tg.LAYOUT_FANS
+    assert tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI).layouts & tg.LAYOUT_FANS
     x = dev(X, torch.float64)
     vals, F = tg.tg_assemble_system(p, x, dev(k, torch.float64), mg.PER_QP, 0.6, dev(f, torch.float64), mg.PER_NODE)
     ref = O.assemble_bilinear(mg.P1_TRI, cells, X, k, O.PER_QP, 0.6)
