@@ -504,6 +504,13 @@ tg_status tg_simp_sensitivity(const tg_pattern* p, tg_dtype dtype, const void* c
  * GPU, in FLOP/s (2 per FMA), written to *flops (host).  SYNCHRONISES. */
 tg_status tg_diag_fma_rate(tg_dtype dtype, double* flops, tg_stream stream);
 
+/* Accuracy check (no counterpart in the paper): y[i] = the FP64 reciprocal
+ * that the P1 forward kernels take of |det J| (Newton's iteration from an
+ * FP32 seed, within one unit in the last place of 1 / x[i]), for n values;
+ * x and y are device arrays of n doubles, n = 0 does nothing.  Asynchronous
+ * on the stream. */
+tg_status tg_diag_recip(const double* x, double* y, int64_t n, tg_stream stream);
+
 /* Failure-path check (no counterpart in the paper): one CTA waits, bounded
  * by max_tries polls (1 .. 2^22), on a shared-memory barrier that nothing
  * completes, exactly as the pipelined kernels wait for their bulk copies;

@@ -91,6 +91,7 @@ def lib():
                                     C.POINTER(C.c_float), vp]),
         "tg_batch_destroy": (None, [vp]),
         "tg_diag_fma_rate": (i32, [i32, C.POINTER(dbl), vp]),
+        "tg_diag_recip": (i32, [vp, vp, i64, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -595,6 +596,15 @@ def tg_batch_autotune(b: Batch, coords: list, kappa: list, layout: int, c: list,
                                    _stream(stream)),
            "tg_batch_autotune")
     return ms.value
+
+
+def tg_diag_recip(x, stream=None):
+    """The FP64 reciprocal the P1 forward kernels take of |det J|, elementwise."""
+    y = torch.empty_like(x)
+    n = x.numel()
+    _check(lib().tg_diag_recip(_ptr(x, torch.float64, "x", n), _ptr(y, torch.float64, "y", n), n, _stream(stream)),
+           "tg_diag_recip")
+    return y
 
 
 def tg_diag_fma_rate(dtype=torch.float64, stream=None) -> float:

@@ -110,33 +110,85 @@ __device__ __forceinline__ T tet_det(const T* __restrict__ coords, int v0, int v
   return g.det;
 }
 
-// Row la of the scalar local matrix of a P1 element (triangle or tet):
-//   K[la][b] = s * n_la.n_b + mc * M[la][b],  s = (sum_q w_q kappa_q)/|det|, mc = c |det|.
-// One entry of the P1 matrix from det-scaled gradients:
-//   K_ab = s (n_a . n_b) + mc M_ab,  s = sum_q w_q kappa_q / |det J|,  mc = c |det J|.
-// Written with explicit fused multiply-adds in a fixed order, so that the
-// entry is bitwise the same wherever it is evaluated (and K_ab == K_ba).
+// Index of (a, b), a <= b, in a packed upper triangle of NV rows.
+__host__ __device__ constexpr int sym_idx(int NV, int a, int b) { return a * NV - a * (a - 1) / 2 + (b - a); }
+
+// n_a . n_b: a product, then fused multiply-adds.
 template <int DIM, typename T>
-__device__ __forceinline__ T p1_entry(const T (&na)[DIM], const T (&nb)[DIM], T s, T mc, T Mab) {
-  T d = na[0] * nb[0];
+__device__ __forceinline__ T dot_n(const T (&na)[DIM], const T (&nb)[DIM]) {
+  T x = na[0] * nb[0];
 #pragma unroll
-  for (int r = 1; r < DIM; ++r) d = fma(na[r], nb[r], d);
-  return fma(s, d, mc * Mab);
+  for (int r = 1; r < DIM; ++r) x = fma(na[r], nb[r], x);
+  return x;
 }
 
+// The dot products d_ab = n_a . n_b of a P1 element's det-scaled gradients
+// in FP64, packed upper triangle (sym_idx).  The FP64 pipe bounds FP64
+// assembly, so only the DIM (DIM + 1) / 2 products among n_1 .. n_DIM are
+// formed; n_0 = -(n_1 + ... + n_DIM) gives the rest:
+//   d_0b = -(d_1b + ... + d_DIMb) (b >= 1),  d_00 = -(d_01 + ... + d_0DIM),
+// each summed in increasing index.  (FP32 forms every product directly:
+// fewer live registers, and the FP32 pipe has room.)
 template <int DIM, typename T>
-__device__ __forceinline__ void p1_row(const Geom<DIM, T>& g, int la, T s, T mc, const T (&Mla)[6],
-                                       T (&Krow)[DIM + 1]) {
-  T na[DIM];
+__device__ __forceinline__ void p1_dots(const Geom<DIM, T>& g, T (&d)[(DIM + 1) * (DIM + 2) / 2]) {
+  constexpr int NV = DIM + 1;
 #pragma unroll
-  for (int r = 0; r < DIM; ++r) {
-    T col[DIM + 1];
+  for (int a = 1; a < NV; ++a)
 #pragma unroll
-    for (int b = 0; b <= DIM; ++b) col[b] = g.n[b][r];
-    na[r] = sel(la, col);
+    for (int b = a; b < NV; ++b) d[sym_idx(NV, a, b)] = dot_n<DIM, T>(g.n[a], g.n[b]);
+#pragma unroll
+  for (int b = 1; b < NV; ++b) {
+    T x = d[sym_idx(NV, 1, b)];
+#pragma unroll
+    for (int c = 2; c < NV; ++c) x += d[c <= b ? sym_idx(NV, c, b) : sym_idx(NV, b, c)];
+    d[sym_idx(NV, 0, b)] = -x;
   }
+  T x = d[sym_idx(NV, 0, 1)];
 #pragma unroll
-  for (int b = 0; b <= DIM; ++b) Krow[b] = p1_entry<DIM, T>(na, g.n[b], s, mc, Mla[b]);
+  for (int b = 2; b < NV; ++b) x += d[sym_idx(NV, 0, b)];
+  d[0] = -x;
+}
+
+// One entry of the P1 matrix from its dot product:
+//   K_ab = s d_ab + mc M_ab,  s = sum_q w_q kappa_q / |det J|,  mc = c |det J|,
+// one multiply and one fused multiply-add in a fixed order (K_ab == K_ba).
+template <typename T>
+__device__ __forceinline__ T p1_entry(T dab, T s, T mc, T Mab) {
+  return fma(s, dab, mc * Mab);
+}
+
+// Row la of the scalar local matrix of a P1 element (triangle or tet),
+// entry for entry the values of p1_elem_sym.  M: the reference mass table;
+// FP64 uses its two values M[0][0] (diagonal) and M[0][1] (off the
+// diagonal), each scaled by mc once, as the P1 mass matrix has no others.
+template <int DIM, typename T>
+__device__ __forceinline__ void p1_row(const Geom<DIM, T>& g, int la, T s, T mc, const T (&M)[6][6],
+                                       T (&Krow)[DIM + 1]) {
+  constexpr int NV = DIM + 1;
+  if constexpr (sizeof(T) == 8) {
+    T d[NV * (NV + 1) / 2];
+    p1_dots<DIM, T>(g, d);
+    const T md = mc * M[0][0], mo = mc * M[0][1];
+#pragma unroll
+    for (int b = 0; b < NV; ++b) {
+      T col[NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) col[a] = d[a <= b ? sym_idx(NV, a, b) : sym_idx(NV, b, a)];
+      Krow[b] = fma(s, sel(la, col), la == b ? md : mo);
+    }
+  } else {
+    const T (&Mla)[6] = M[la];
+    T na[DIM];
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      T col[NV];
+#pragma unroll
+      for (int b = 0; b < NV; ++b) col[b] = g.n[b][r];
+      na[r] = sel(la, col);
+    }
+#pragma unroll
+    for (int b = 0; b < NV; ++b) Krow[b] = p1_entry<T>(dot_n<DIM, T>(na, g.n[b]), s, mc, Mla[b]);
+  }
 }
 // Row la of the P2 triangle matrix with kappa at the 6 points:
 //   K[la][b] = (1/|det|) sum_q w_q kappa_q gh_q,la^T C gh_q,b + c |det| M[la][b]

@@ -109,7 +109,7 @@ __device__ __forceinline__ void p1_scales(const T (&kq)[NQ], const RefTab<T>& ts
   T s = ts.w[0] * kq[0];
 #pragma unroll
   for (int q = 1; q < NQ; ++q) s = fma(ts.w[q], kq[q], s);
-  sc = s * recip(adet);
+  sc = s * recip_fast(adet);
   mc = c * adet;
 }
 
@@ -220,7 +220,7 @@ __device__ __forceinline__ bool elem_row(const ElemIn<EL, T>& in, T c, const Ref
     if constexpr (EL == TG_P1_TRI) {
       T sc, mc;
       p1_scales<3, T>(in.kq, ts, adet, c, sc, mc);
-      p1_row<2, T>(g, la, sc, mc, ts.M[la], Krow);
+      p1_row<2, T>(g, la, sc, mc, ts.M, Krow);
     } else {
       p2_row<T>(g, la, in.kq, recip(adet), c * adet, ts, tc, Krow);
     }
@@ -231,7 +231,7 @@ __device__ __forceinline__ bool elem_row(const ElemIn<EL, T>& in, T c, const Ref
     if (!(adet > det_tiny<T>())) return false;
     T sc, mc;
     p1_scales<4, T>(in.kq, ts, adet, c, sc, mc);
-    p1_row<3, T>(g, la, sc, mc, ts.M[la], Krow);
+    p1_row<3, T>(g, la, sc, mc, ts.M, Krow);
   }
   return true;
 }
@@ -251,10 +251,21 @@ __device__ __forceinline__ bool p1_elem_sym(const ElemIn<EL, T>& in, T c, const 
   T sc, mc;
   p1_scales<Elem<EL>::nq, T>(in.kq, ts, adet, c, sc, mc);
   int k = 0;
+  if constexpr (sizeof(T) == 8) {
+    // the P1 mass matrix has one value on the diagonal and one off it
+    T d[NV * (NV + 1) / 2];
+    p1_dots<D, T>(g, d);
+    const T md = mc * ts.M[0][0], mo = mc * ts.M[0][1];
 #pragma unroll
-  for (int a = 0; a < NV; ++a)
+    for (int a = 0; a < NV; ++a)
 #pragma unroll
-    for (int b = a; b < NV; ++b) K[k++] = p1_entry<D, T>(g.n[a], g.n[b], sc, mc, ts.M[a][b]);
+      for (int b = a; b < NV; ++b, ++k) K[k] = fma(sc, d[k], a == b ? md : mo);
+  } else {
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+      for (int b = a; b < NV; ++b, ++k) K[k] = p1_entry<T>(dot_n<D, T>(g.n[a], g.n[b]), sc, mc, ts.M[a][b]);
+  }
   return true;
 }
 

@@ -489,9 +489,23 @@ __global__ void k_diag_wait_timeout(unsigned long long* status, uint32_t max_tri
   if (__syncthreads_or(!ok) && threadIdx.x == 0) tg::record_error(status, TG_ERR_TIMEOUT, 0);
 }
 
+// y[i] = the FP64 reciprocal the P1 forward takes of |det J|.
+__global__ void k_diag_recip(const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = tg::recip_fast(x[i]);
+}
+
 }  // namespace
 
 extern "C" {
+
+tg_status tg_diag_recip(const double* x, double* y, int64_t n, tg_stream stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return TG_ERR_INVALID_ARG;
+  if (n == 0) return TG_OK;
+  k_diag_recip<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, (cudaStream_t)stream>>>(x, y, n);
+  TG_CK_LAUNCH("k_diag_recip");
+  return TG_OK;
+}
 
 tg_status tg_diag_wait_timeout(const tg_pattern* p, int32_t max_tries, tg_stream stream) {
   if (!p || max_tries < 1 || max_tries > (1 << 22)) return TG_ERR_INVALID_ARG;

@@ -226,6 +226,26 @@ __device__ __forceinline__ uint32_t as_bits(T x) {
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
 
+// FP32: recip.  FP64: 1 / x within one unit in the last place, by Newton's
+// iteration for the reciprocal, y <- y + y (1 - x y), from the FP32
+// approximate reciprocal of x rounded to FP32 as the seed (relative error
+// below 2^-21): two steps take it below 2^-84 before the last rounding.
+// Four FP64 fused multiply-adds and two conversions, fewer FP64-pipe
+// operations than the correctly rounded quotient; the P1 forward, bound by
+// that pipe in FP64, takes its 1 / |det J| here.  |x| outside [2^-120,
+// 2^120] (no normal FP32 seed), zero, infinities and NaN take the quotient
+// 1.0 / x.
+__device__ __forceinline__ float recip_fast(float x) { return recip(x); }
+__device__ __forceinline__ double recip_fast(double x) {
+  const uint32_t ex = ((uint32_t)(__double_as_longlong(x) >> 52)) & 0x7ffu;
+  if (ex < 1023u - 120u || ex > 1023u + 119u) return 1.0 / x;
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__double2float_rn(x)));
+  double y = (double)yf;
+  y = fma(y, fma(-x, y, 1.0), y);
+  return fma(y, fma(-x, y, 1.0), y);
+}
+
 // Coefficient sum over quadrature points with the rule's weights.
 template <typename T, int NQ>
 __device__ __forceinline__ T weighted_coef(const T* __restrict__ v, int layout, int64_t e, const T (&w)[6], T wsum) {

@@ -362,3 +362,26 @@ def test_vertex_joining_two_fans(tg):
     v32 = tg.tg_assemble_bilinear(p, xf, kf, mg.PER_QP, 0.6)
     r32 = O.assemble_bilinear(mg.P1_TRI, cells, host_as(X, torch.float32), host_as(k, torch.float32), O.PER_QP, 0.6)
     assert relfro(v32.cpu().numpy(), r32.val) <= 2e-6
+
+
+def test_fp64_reciprocal_within_one_ulp(tg):
+    """The FP64 reciprocal that the P1 forward kernels take of |det J|
+    (Newton's iteration from an FP32 seed) is within one unit in the last
+    place of the correctly rounded 1/x over the seed's range, at its edges and
+    at powers of two, for both signs; outside that range it is the quotient
+    itself."""
+    g = np.random.default_rng(77)
+    inside = 2.0 ** g.uniform(-120, 119, 400000) * g.uniform(1, 2, 400000)
+    edges = np.array([2.0 ** -120, np.nextafter(2.0 ** -120, 1), 2.0 ** 119.9999, np.nextafter(2.0 ** 120, 0), 1.0,
+                      3.0, 1 / 3, np.nextafter(1.0, 2), np.nextafter(1.0, 0), 0.1, 1e-30, 1e30])
+    pow2 = 2.0 ** np.arange(-120, 120)
+    near = np.concatenate([np.nextafter(pow2[1:], 0), np.nextafter(pow2[:-1], np.inf)])
+    x = np.concatenate([inside, edges, pow2, near])
+    x = np.concatenate([x, -x])
+    outside = np.array([1e-300, 2.0 ** -121, np.nextafter(2.0 ** -120, 0), 2.0 ** 120, 1e300, -1e-300, -2.0 ** 121])
+    y = tg.tg_diag_recip(torch.as_tensor(np.concatenate([x, outside]), device="cuda")).cpu().numpy()
+    want = 1.0 / x
+    err = np.abs(y[:len(x)] - want) / np.spacing(np.abs(want))
+    assert err.max() <= 1.0, err.max()
+    assert np.array_equal(y[len(x):], 1.0 / outside)
+    assert tg.tg_diag_recip(torch.empty(0, dtype=torch.float64, device="cuda")).numel() == 0
