@@ -366,7 +366,6 @@ __device__ __forceinline__ bool bwd_p1_element(const T (&x)[D + 1][D], const T (
 #pragma unroll
     for (int q = 0; q < NV; ++q) wm += W[p][q] * tab.M[p][q];
   const T inv = tg::recip(adet);
-  const T sgn = gm.det > T(0) ? T(1) : T(-1);
   T y[NV][D];  // y[b][r] = sum_p W[p][b] n[p][r]
 #pragma unroll
   for (int b2 = 0; b2 < NV; ++b2)
@@ -393,26 +392,40 @@ __device__ __forceinline__ bool bwd_p1_element(const T (&x)[D + 1][D], const T (
   T S = T(0);
 #pragma unroll
   for (int q = 0; q < NQ; ++q) S += tab.w[q] * kq[q];
+  const T ti = trq * inv;
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) gk[q] = tab.w[q] * trq * inv;
+  for (int q = 0; q < NQ; ++q) gk[q] = tab.w[q] * ti;
   cterm = adet * wm;
-  const T inv2 = inv * inv;
-  const T d0 = sgn * (S * trq * inv2 + c * wm);
-  const T f2 = -sgn * S * inv2;  // times 2 Q = P + P^T
+  // A = sgn [(S tr Q / det^2 + c <W,M>) I - (2 S / det^2) Q] with 2 Q = P + P^T;
+  // the sign of det enters by negation, not by a multiply
+  const T Si2 = S * (inv * inv);
+  const T d0u = fma(Si2, trq, c * wm), f2u = -Si2;
+  const bool pos = gm.det > T(0);
+  const T d0 = pos ? d0u : -d0u, f2 = pos ? f2u : -f2u;
   T A[D][D];
 #pragma unroll
-  for (int r = 0; r < D; ++r)
+  for (int r = 0; r < D; ++r) {
+    A[r][r] = fma(f2 + f2, P[r][r], d0);
 #pragma unroll
-    for (int s2 = 0; s2 < D; ++s2) A[r][s2] = f2 * (P[r][s2] + P[s2][r]) + (r == s2 ? d0 : T(0));
+    for (int s2 = r + 1; s2 < D; ++s2) A[r][s2] = A[s2][r] = f2 * (P[r][s2] + P[s2][r]);
+  }
+  // dL/dx_c = A n_c; the n_c sum to zero, so the first is minus the others' sum
 #pragma unroll
-  for (int cc = 0; cc < NV; ++cc)
+  for (int cc = 1; cc < NV; ++cc)
 #pragma unroll
     for (int r = 0; r < D; ++r) {
-      T sacc = T(0);
+      T sacc = A[r][0] * gm.n[cc][0];
 #pragma unroll
-      for (int s2 = 0; s2 < D; ++s2) sacc += A[r][s2] * gm.n[cc][s2];
+      for (int s2 = 1; s2 < D; ++s2) sacc = fma(A[r][s2], gm.n[cc][s2], sacc);
       gx[cc][r] = sacc;
     }
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    T sacc = gx[1][r];
+#pragma unroll
+    for (int cc = 2; cc < NV; ++cc) sacc += gx[cc][r];
+    gx[0][r] = -sacc;
+  }
   return true;
 }
 

@@ -103,6 +103,11 @@ __device__ __forceinline__ void blk_bilinear_map(const FwdArgs<T>& a, const RefT
 #pragma unroll
         for (int q = 0; q < NS; ++q) K[q] = T(0);
       }
+      // FP64: the element's load entries at once (shared terms); FP32: row by
+      // row, the same values with fewer live registers
+      constexpr bool FE = LOAD && sizeof(T) == 8;
+      T fe[FE ? NV : 1];
+      if constexpr (FE) tg::p1_load_entries<NV, T>(a.f_layout, adet, fv[u], tab, fe);
 #pragma unroll
       for (int r = 0; r < NV; ++r) {
         T row[NW * VN];
@@ -113,7 +118,8 @@ __device__ __forceinline__ void blk_bilinear_map(const FwdArgs<T>& a, const RefT
         }
 #pragma unroll
         for (int c = NV; c < NW * VN; ++c) row[c] = T(0);
-        if constexpr (LOAD) row[NV] = ok ? p1_load_entry<NV, T>(a.f_layout, adet, fv[u], tab, r) : T(0);
+        if constexpr (FE) row[NV] = ok ? fe[r] : T(0);
+        else if constexpr (LOAD) row[NV] = ok ? p1_load_entry<NV, T>(a.f_layout, adet, fv[u], tab, r) : T(0);
 #pragma unroll
         for (int w = 0; w < NW; ++w) KF[(r * NW + w) * capE + j] = Vec16<T>::make(row + w * VN);
       }

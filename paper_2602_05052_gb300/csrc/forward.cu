@@ -126,8 +126,15 @@ __device__ __forceinline__ void blk_load_map(const FwdArgs<T>& a, const tg::RefT
       const T adet = absv(gm.det);
       const bool ok = adet > tg::det_tiny<T>();
       if (!ok) tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e[u]);
+      if constexpr (sizeof(T) == 8) {  // the element's entries at once (shared terms)
+        T fe[NV];
+        tg::p1_load_entries<NV, T>(a.layout, adet, fv[u], ts, fe);
 #pragma unroll
-      for (int c = 0; c < NV; ++c) Fe[c * capE + j] = ok ? tg::p1_load_entry<NV, T>(a.layout, adet, fv[u], ts, c) : T(0);
+        for (int c = 0; c < NV; ++c) Fe[c * capE + j] = ok ? fe[c] : T(0);
+      } else {  // the same values entry by entry, fewer live registers
+#pragma unroll
+        for (int c = 0; c < NV; ++c) Fe[c * capE + j] = ok ? tg::p1_load_entry<NV, T>(a.layout, adet, fv[u], ts, c) : T(0);
+      }
     }
   }
 }

@@ -207,6 +207,29 @@ __device__ __forceinline__ T p1_load_entry(int layout, T adet, const T (&fv)[NV]
   return adet * ts.m1[c] * fv[0];
 }
 
+// All NV entries of F_e (the values of p1_load_entry).  In FP64 (bound by
+// the FP64 pipe) the nodal case instead uses that the P1 mass matrix has
+// one value m_d on the diagonal and one m_o off it:
+//   F_c = (|det J| m_o) sum_b f_b + |det J| (m_d - m_o) f_c,
+// the common terms formed once per element.
+template <int NV, typename T>
+__device__ __forceinline__ void p1_load_entries(int layout, T adet, const T (&fv)[NV], const RefTab<T>& ts,
+                                                T (&F)[NV]) {
+  if constexpr (sizeof(T) == 8 && NV <= 4) {
+    if (layout == TG_PER_NODE) {
+      T fs = fv[0];
+#pragma unroll
+      for (int b = 1; b < NV; ++b) fs += fv[b];
+      const T base = (adet * ts.M[0][1]) * fs, ad = adet * (ts.M[0][0] - ts.M[0][1]);
+#pragma unroll
+      for (int c = 0; c < NV; ++c) F[c] = fma(ad, fv[c], base);
+      return;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NV; ++c) F[c] = p1_load_entry<NV, T>(layout, adet, fv, ts, c);
+}
+
 // Row la of the local matrix from loaded inputs; false for a degenerate
 // element.  Same arithmetic, operation for operation, as scalar_row.
 template <int EL, typename T>

@@ -136,11 +136,13 @@ __device__ __forceinline__ void result_compute(const ResArgs<T>& r, const tg::Re
   }
   T nr[NV];
   if constexpr (NL != 0) reaction_rows<EL, T, NL>(r, tab, adet, d, nr);
+  T fe[LOADF ? NV : 1];
+  if constexpr (LOADF) tg::p1_load_entries<NV, T>(r.fa.f_layout, adet, d.fv, tab, fe);
 #pragma unroll
   for (int a = 0; a < NV; ++a) {
     T s = kx_row<NV, T>(K, d.xv, a);
     if constexpr (NL != 0) s += nr[a];
-    if constexpr (LOADF) s -= tg::p1_load_entry<NV, T>(r.fa.f_layout, adet, d.fv, tab, a);
+    if constexpr (LOADF) s -= fe[a];
     ye[a] = s;
   }
 }
