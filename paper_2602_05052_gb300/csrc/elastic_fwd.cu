@@ -128,19 +128,27 @@ __global__ void __launch_bounds__(EB) k_elastic_gather(const FwdArgs<T> a, const
       const T col[4] = {o[r], o[4 + r], o[8 + r], o[12 + r]};
       na[r] = tg::sel(la, col);
     }
+    // each entry accumulates by two fused multiply-adds onto the running
+    // sum (the FP64 pipe bounds the FP64 kernel)
+    T Lna[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) Lna[r] = L * na[r];
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int pos = tg::pos_of(w0, 0u, b);
       const T nb[3] = {o[4 * b], o[4 * b + 1], o[4 * b + 2]};
-      const T d = na[0] * nb[0] + na[1] * nb[1] + na[2] * nb[2];
+      const T Md = M * (na[0] * nb[0] + na[1] * nb[1] + na[2] * nb[2]);
 #pragma unroll
-      for (int ii = 0; ii < 3; ++ii)
+      for (int ii = 0; ii < 3; ++ii) {
+        const T Mnb = M * nb[ii];
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
-          T v = L * na[ii] * nb[jj] + M * nb[ii] * na[jj];
-          if (ii == jj) v += M * d;
-          acc[((ii * len + pos) * 3 + jj) * EB] += v;
+          T* q = acc + ((ii * len + pos) * 3 + jj) * EB;
+          T v = fma(Mnb, na[jj], fma(Lna[ii], nb[jj], *q));
+          if (ii == jj) v += Md;
+          *q = v;
         }
+      }
     }
   }
   store_row<T>(a.out + 9ll * r0, acc, EB, 9 * len);
