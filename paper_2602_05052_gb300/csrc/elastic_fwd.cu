@@ -206,7 +206,8 @@ __global__ void __launch_bounds__(128) k_elastic_rec(const FwdArgs<T> a, const _
 // Pass 2: 16 lanes per node row i (two rows per warp), lane p owning the
 // 3 x 3 block of the row's p-th column node j in registers.  The block is
 // summed over the elements around edge (i, j) (the bits of emask,
-// increasing element order):
+// increasing element order), each entry by two fused multiply-adds onto its
+// running sum:
 //   L n_a n_b^T + M n_b n_a^T + M (n_a . n_b) I,
 // a, b the local indices of i and j.  An element's diagonal-block terms
 // (L + M) n_a n_a^T + M |n_a|^2 I are added by the lane of its neighbour of
@@ -277,15 +278,16 @@ __global__ void __launch_bounds__(128) k_elastic_lanes(const FwdArgs<T> a, const
     ld_vec4(re + 4 * la, na);
     ld_vec4(re + 4 * lb, nb);
     const T L = na[3], M = __ldg(re + 16);
-    const T d = na[0] * nb[0] + na[1] * nb[1] + na[2] * nb[2];
+    const T Md = M * (na[0] * nb[0] + na[1] * nb[1] + na[2] * nb[2]);
 #pragma unroll
-    for (int u = 0; u < 3; ++u)
+    for (int u = 0; u < 3; ++u) {
+      const T Lna = L * na[u], Mnb = M * nb[u];
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
-        T x = L * na[u] * nb[v] + M * nb[u] * na[v];
-        if (u == v) x += M * d;
-        B[u][v] += x;
+        const T x = fma(Mnb, na[v], fma(Lna, nb[v], B[u][v]));
+        B[u][v] = u == v ? x + Md : x;
       }
+    }
     if (p == pmin) {
       const T S = L + M, q = M * (na[0] * na[0] + na[1] * na[1] + na[2] * na[2]);
       D[0] += S * na[0] * na[0] + q;
