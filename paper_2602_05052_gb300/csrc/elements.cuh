@@ -191,7 +191,7 @@ __device__ __forceinline__ void p1_row(const Geom<DIM, T>& g, int la, T s, T mc,
   }
 }
 // Row la of the P2 triangle matrix with kappa at the 6 points:
-//   K[la][b] = (1/|det|) sum_q w_q kappa_q gh_q,la^T C gh_q,b + c |det| M[la][b]
+//   K[la][b] = sum_q (w_q kappa_q / |det|) gh_q,la^T C gh_q,b + c |det| M[la][b]
 // with C = det^2 J^{-1} J^{-T} = [[n1.n1, n1.n2], [n1.n2, n2.n2]].
 // ts serves the reads indexed by the runtime la (a shared-memory copy), tc
 // the ones with compile-time indices (the kernel's constant parameter).
@@ -206,14 +206,15 @@ __device__ __forceinline__ void p2_row(const Geom<2, T>& g, int la, const T (&kq
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     const T ga0 = ts.gh[q][la][0], ga1 = ts.gh[q][la][1];
-    const T wk = tc.w[q] * kq[q];
-    const T hx = wk * (c00 * ga0 + c01 * ga1);
-    const T hy = wk * (c01 * ga0 + c11 * ga1);
+    const T wk = (tc.w[q] * kq[q]) * inv;
+    const T w00 = wk * c00, w01 = wk * c01, w11 = wk * c11;
+    const T hx = fma(w00, ga0, w01 * ga1);
+    const T hy = fma(w01, ga0, w11 * ga1);
 #pragma unroll
-    for (int b = 0; b < 6; ++b) Krow[b] += hx * tc.gh[q][b][0] + hy * tc.gh[q][b][1];
+    for (int b = 0; b < 6; ++b) Krow[b] = fma(hx, tc.gh[q][b][0], fma(hy, tc.gh[q][b][1], Krow[b]));
   }
 #pragma unroll
-  for (int b = 0; b < 6; ++b) Krow[b] = Krow[b] * inv + mc * ts.M[la][b];
+  for (int b = 0; b < 6; ++b) Krow[b] = fma(mc, ts.M[la][b], Krow[b]);
 }
 
 __device__ __forceinline__ int pos_of(uint32_t w0, uint32_t w1, int b) {

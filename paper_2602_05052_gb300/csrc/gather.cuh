@@ -143,30 +143,33 @@ __device__ __forceinline__ bool p2_elem_sym(const ElemIn<TG_P2_TRI, T>& in, T c,
   const T c00 = g.n[1][0] * g.n[1][0] + g.n[1][1] * g.n[1][1];
   const T c01 = g.n[1][0] * g.n[2][0] + g.n[1][1] * g.n[2][1];
   const T c11 = g.n[2][0] * g.n[2][0] + g.n[2][1] * g.n[2][1];
+  // 1/|det J| enters the per-point scale w_q kappa_q / |det J| of C, and
+  // every product accumulates by fused multiply-adds
+  const T inv = recip(adet), mc = c * adet;
 #pragma unroll
   for (int k = 0; k < 21; ++k) K[k] = T(0);
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
-    const T wk = tc.w[q] * in.kq[q];
+    const T wk = (tc.w[q] * in.kq[q]) * inv;
+    const T w00 = wk * c00, w01 = wk * c01, w11 = wk * c11;
     T hx[6], hy[6];
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
       const T g0 = tc.gh[q][a][0], g1 = tc.gh[q][a][1];
-      hx[a] = wk * (c00 * g0 + c01 * g1);
-      hy[a] = wk * (c01 * g0 + c11 * g1);
+      hx[a] = fma(w00, g0, w01 * g1);
+      hy[a] = fma(w01, g0, w11 * g1);
     }
     int k = 0;
 #pragma unroll
     for (int a = 0; a < 6; ++a)
 #pragma unroll
-      for (int b = a; b < 6; ++b, ++k) K[k] += hx[a] * tc.gh[q][b][0] + hy[a] * tc.gh[q][b][1];
+      for (int b = a; b < 6; ++b, ++k) K[k] = fma(hx[a], tc.gh[q][b][0], fma(hy[a], tc.gh[q][b][1], K[k]));
   }
-  const T inv = recip(adet), mc = c * adet;
   int k = 0;
 #pragma unroll
   for (int a = 0; a < 6; ++a)
 #pragma unroll
-    for (int b = a; b < 6; ++b, ++k) K[k] = K[k] * inv + mc * tc.M[a][b];
+    for (int b = a; b < 6; ++b, ++k) K[k] = fma(mc, tc.M[a][b], K[k]);
   return true;
 }
 
