@@ -186,6 +186,95 @@ __global__ void __launch_bounds__(128) k_batch_blk(const InstBlk* __restrict__ d
   }
 }
 
+// Fan mode (every instance has fans): one 80-byte record per (instance, row
+// block) item, built when the batch is created, with everything the item's
+// Map and Reduce need to start: its instance, block rows, element list and
+// fan region.  A CTA copies the record of its next item into shared memory
+// while it works on the current one, and the item's fan region while its Map
+// runs (asynchronous 16-byte copies), so an item starts without a chain of
+// dependent global loads.  Same Map, Reduce and item order as k_batch_blk:
+// the results are bitwise those of tg_assemble_bilinear.
+struct ItemRec {
+  const uint32_t* be;   // the block's element list (bel + boff[b])
+  const uint4* fan;     // its fan region
+  const int32_t* up;    // CSR row starts of its rows (urp + r0)
+  const int32_t* pm;    // node of each of its rows (iperm + r0)
+  unsigned long long* status;
+  int inst, nbe, vbase, nfq;  // nfq: fan region size in 16-byte groups
+  int r0, r1, rs;
+  int pad[3];
+};
+static_assert(sizeof(ItemRec) == 80, "ItemRec is five 16-byte groups");
+
+template <int EL, typename T, int UB>
+__global__ void __launch_bounds__(128) k_batch_fan(const ItemRec* __restrict__ recs, int64_t n_items,
+                                                   const __grid_constant__ BatchCall<T> call,
+                                                   const __grid_constant__ tg::RefTab<T> tab, int capE, int fan_words) {
+  constexpr int NV = tg::Elem<EL>::nv;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const size_t kf_bytes = (size_t)NV * tg::kf_vecs<NV, T, false>() * capE * 16;
+  uint4* frs = reinterpret_cast<uint4*>(smem + kf_bytes);
+  ItemRec* slot = reinterpret_cast<ItemRec*>(smem + kf_bytes + (((size_t)fan_words * 2 + 15) & ~size_t(15)));
+  const int tid = (int)threadIdx.x;
+  const int64_t G = gridDim.x;
+  if (tid < 5 && blockIdx.x < n_items)
+    tg::cp_async16(reinterpret_cast<uint4*>(slot) + tid, reinterpret_cast<const uint4*>(recs + blockIdx.x) + tid);
+  tg::cp_async_commit();
+  tg::cp_async_wait_all();
+  __syncthreads();
+  int kk = 0;
+  for (int64_t it = blockIdx.x; it < n_items; it += G, ++kk) {
+    const ItemRec r = slot[kk & 1];
+    if (tid < 5 && it + G < n_items)  // the next item's record
+      tg::cp_async16(reinterpret_cast<uint4*>(slot + ((kk + 1) & 1)) + tid,
+                     reinterpret_cast<const uint4*>(recs + it + G) + tid);
+    for (int q = tid; q < r.nfq; q += blockDim.x) tg::cp_async16(frs + q, r.fan + q);  // read by the Reduce
+    tg::cp_async_commit();
+    const int k = r.inst - call.inst0;
+    tg::FwdArgs<T> a;
+    a.row_ptr = nullptr;
+    a.inc_ptr = nullptr;
+    a.inc_e = nullptr;
+    a.inc_pos = nullptr;
+    a.cells = nullptr;
+    a.elem_slot = nullptr;
+    a.coords = call.coords[k];
+    a.coef = call.kappa[k];
+    a.coef2 = nullptr;
+    a.layout = call.layout;
+    a.c = call.c[k];
+    a.out = call.vals[k];
+    a.n = 0;
+    a.status = r.status;
+    a.f = nullptr;
+    a.f_layout = 0;
+    a.F = nullptr;
+    tg::FanView fv;
+    fv.r0 = r.r0;
+    fv.r1 = r.r1;
+    fv.nbe = r.nbe;
+    fv.vbase = r.vbase;
+    fv.bs16 = (r.nbe + 7) & ~7;
+    fv.rs = r.rs;
+    fv.up = r.up;
+    fv.pm = r.pm;
+    const uint16_t* f = reinterpret_cast<const uint16_t*>(frs);
+    fv.pos = reinterpret_cast<const unsigned long long*>(f);
+    fv.info = f + 4 * r.rs;
+    fv.rec = f + 5 * r.rs;
+    fv.info32 = reinterpret_cast<const uint32_t*>(f);
+    fv.rec32 = fv.info32 + r.rs;
+    fv.be = r.be;
+    fv.vo = reinterpret_cast<const uint16_t*>(r.be + ((r.nbe + 3) & ~3));
+    tg::blk_bilinear_map<EL, T, UB, false, EL == TG_P2_TRI>(a, tab, capE, fv, smem);
+    tg::cp_async_wait_all();
+    __syncthreads();  // the Map's rows, the fan region and the next record are in place
+    if constexpr (EL == TG_P2_TRI) tg::fan_reduce_p2<T>(a, capE, fv, smem);
+    else tg::fan_reduce_bilinear<T, false>(a, capE, fv, smem);
+    __syncthreads();
+  }
+}
+
 struct Sched {
   int threads, rows_per_item, ctas_per_sm;
 };
@@ -214,6 +303,8 @@ struct tg_batch {
   std::vector<int64_t> blk_chunk_items;
   int capE = 0, max_elems = 0;
   int fan_words = 0;  // largest fan region of the instances (16-bit words)
+  // fan mode (triangle instances that all have fans): the item records
+  ItemRec* d_recs = nullptr;
 };
 
 namespace {
@@ -286,13 +377,21 @@ tg_status launch_blk_t(tg_batch* b, const void* const* coords, const void* const
                        void* const* vals, cudaStream_t s) {
   constexpr int NV = tg::Elem<EL>::nv;
   auto kern = k_batch_blk<EL, T, UB>;
-  const size_t smem = ((tg::blk_bilinear_work_bytes<NV, T, false>(b->capE, b->max_row_len, 128) + 15) & ~size_t(15)) +
-                      (size_t)b->fan_words * 2;
-  tg_status st = tg::set_smem((const void*)kern, smem);
+  const void* kf = (const void*)kern;
+  size_t smem = ((tg::blk_bilinear_work_bytes<NV, T, false>(b->capE, b->max_row_len, 128) + 15) & ~size_t(15)) +
+                (size_t)b->fan_words * 2;
+  if constexpr (EL == TG_P1_TRI || EL == TG_P2_TRI) {
+    if (b->d_recs) {
+      kf = (const void*)k_batch_fan<EL, T, UB>;
+      smem = (size_t)NV * tg::kf_vecs<NV, T, false>() * b->capE * 16 + (((size_t)b->fan_words * 2 + 15) & ~size_t(15)) +
+             2 * sizeof(ItemRec);
+    }
+  }
+  tg_status st = tg::set_smem(kf, smem);
   if (st != TG_OK) return st;
   int per_sm = b->sched.ctas_per_sm;
   if (per_sm <= 0) {
-    TG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem));
+    TG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, 128, smem));
     per_sm = std::max(per_sm, 1);
   }
   const tg::RefTab<T>& tab = tg::table<T>(b->el);
@@ -312,6 +411,13 @@ tg_status launch_blk_t(tg_batch* b, const void* const* coords, const void* const
     const int64_t i0 = b->blk_chunk_items[ch], n_items = b->blk_chunk_items[ch + 1] - i0;
     if (n_items == 0) continue;
     const int grid = (int)std::min<int64_t>(n_items, (int64_t)per_sm * tg::sm_count());
+    if (b->d_recs) {
+      if constexpr (EL == TG_P1_TRI || EL == TG_P2_TRI) {
+        k_batch_fan<EL, T, UB><<<grid, 128, smem, s>>>(b->d_recs + i0, n_items, call, tab, b->capE, b->fan_words);
+        TG_CK_LAUNCH("k_batch_fan");
+      }
+      continue;
+    }
     kern<<<grid, 128, smem, s>>>(b->d_blk, b->d_blk_items + i0, n_items, call, tab, b->capE, b->max_row_len * 128,
                                  b->fan_words);
     TG_CK_LAUNCH("k_batch_blk");
@@ -405,6 +511,43 @@ tg_status setup_blocks(tg_batch* b) {
   b->max_elems = max_elems;
   for (const tg_pattern* p : b->pats) b->fan_words = std::max(b->fan_words, p->fan ? p->fan_maxw : 0);
   b->blk = true;
+  // fan mode: every instance with elements has fans (triangles)
+  bool fans = b->el == TG_P1_TRI || b->el == TG_P2_TRI;
+  for (const tg_pattern* p : b->pats) fans = fans && (p->E == 0 || p->fan);
+  if (!fans || items.empty()) return TG_OK;
+  std::vector<ItemRec> recs;
+  recs.reserve(items.size());
+  for (int i = 0; i < b->n_inst; ++i) {
+    const tg_pattern* p = b->pats[i];
+    if (p->E == 0) continue;
+    const int64_t nb = p->n_blk;
+    std::vector<int64_t> boff(nb), foff(nb + 1);
+    std::vector<int32_t> cnt(nb), vbase(nb);
+    TG_CK(cudaMemcpy(boff.data(), p->boff, nb * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    TG_CK(cudaMemcpy(foff.data(), p->fan_off, (nb + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    TG_CK(cudaMemcpy(cnt.data(), p->bel_cnt, nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    TG_CK(cudaMemcpy(vbase.data(), p->bvbase, nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < nb; ++k) {
+      const int64_t r0 = k * p->blk_rows, r1 = std::min<int64_t>(p->N, r0 + p->blk_rows);
+      ItemRec r{};
+      r.be = p->bel + boff[k];
+      r.fan = reinterpret_cast<const uint4*>(p->fan + foff[k]);
+      r.up = p->urp + r0;
+      r.pm = p->iperm + r0;
+      r.status = p->status;
+      r.inst = i;
+      r.nbe = cnt[k];
+      r.vbase = vbase[k];
+      r.nfq = (int)((foff[k + 1] - foff[k]) / 8);
+      r.r0 = (int)r0;
+      r.r1 = (int)r1;
+      r.rs = p->fan_rs;
+      recs.push_back(r);
+    }
+  }
+  if (recs.size() != items.size()) return TG_OK;  // not expected; the block mode serves then
+  TG_CK(cudaMalloc(&b->d_recs, recs.size() * sizeof(ItemRec)));
+  TG_CK(cudaMemcpy(b->d_recs, recs.data(), recs.size() * sizeof(ItemRec), cudaMemcpyHostToDevice));
   return TG_OK;
 }
 
@@ -555,6 +698,7 @@ void tg_batch_destroy(tg_batch* b) {
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_blk) cudaFree(b->d_blk);
   if (b->d_blk_items) cudaFree(b->d_blk_items);
+  if (b->d_recs) cudaFree(b->d_recs);
   delete b;
 }
 
