@@ -483,7 +483,7 @@ tg_status setup_blocks(tg_batch* b) {
   int capE = 0, max_elems = 0;
   for (const tg_pattern* p : b->pats) {
     if (p->E > 0 && !p->bel) return TG_OK;  // stays in row-range mode
-    capE = std::max(capE, (p->blk_max_elems + 3) & ~3);
+    capE = std::max(capE, (p->blk_max_elems + 7) & ~7);  // a multiple of 8, as the fans' bank-group choice assumes
     max_elems = std::max(max_elems, p->blk_max_elems);
   }
   // the FP64 budget bounds both dtypes
