@@ -87,6 +87,81 @@ __device__ __forceinline__ void el_bwd_sums(const T (&G)[3][4], WBlk wblk, T& t1
     }
 }
 
+// The same sums in FP64 from the symmetrised blocks U_pq = W_pq + W_qp^T of
+// each unordered pair (U_qp = U_pq^T; U_pp = W_pp + W_pp^T):
+//   dT1/dG_p = sum_q U_pq G_q,  dT2/dG_p = sum_q U_pq^T G_q,
+//   dT3/dG_p = sum_q tr(U_pq) G_q,  T_k = (1/2) sum_p G_p . dT_k/dG_p,
+// each derivative accumulated by fused multiply-adds onto its running sum
+// (pairs in the order of el_bwd_sums): about 40% fewer FP64 operations than
+// accumulating every term of each pair separately.
+template <typename T, typename WBlk>
+__device__ __forceinline__ void el_bwd_sums_sym(const T (&G)[3][4], WBlk wblk, T& t1, T& t2, T& t3, T (&d1)[3][4],
+                                                T (&d2)[3][4], T (&d3)[3][4]) {
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = p; q < 4; ++q) {
+      T u[3][3];
+      wblk(p, q, u);
+      if (q != p) {
+        T w2[3][3];
+        wblk(q, p, w2);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) u[i][j] += w2[j][i];
+        const T tr = u[0][0] + u[1][1] + u[2][2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          T a1 = d1[i][p], b1 = d1[i][q], a2 = d2[i][p], b2 = d2[i][q];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            a1 = fma(u[i][j], G[j][q], a1);  // U G_q
+            b1 = fma(u[j][i], G[j][p], b1);  // U^T G_p
+            a2 = fma(u[j][i], G[j][q], a2);  // U^T G_q
+            b2 = fma(u[i][j], G[j][p], b2);  // U G_p
+          }
+          d1[i][p] = a1;
+          d1[i][q] = b1;
+          d2[i][p] = a2;
+          d2[i][q] = b2;
+          d3[i][p] = fma(tr, G[i][q], d3[i][p]);
+          d3[i][q] = fma(tr, G[i][p], d3[i][q]);
+        }
+      } else {
+        // U_pp is symmetric: U_pp G_p serves both derivatives
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = i + 1; j < 3; ++j) u[i][j] = u[j][i] = u[i][j] + u[j][i];
+        const T tr = u[0][0] + u[1][1] + u[2][2];  // half the trace of U_pp
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          T v = u[i][0] * G[0][p];
+          v = fma(u[i][1], G[1][p], v);
+          v = fma(u[i][2], G[2][p], v);
+          // the diagonal of U_pp is 2 W_pp[i][i]: v holds U_pp G_p minus W_pp[i][i] G_ip
+          v = fma(u[i][i], G[i][p], v);
+          d1[i][p] += v;
+          d2[i][p] += v;
+          d3[i][p] = fma(tr + tr, G[i][p], d3[i][p]);
+        }
+      }
+    }
+  T s1 = T(0), s2 = T(0), s3 = T(0);
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      s1 = fma(G[i][p], d1[i][p], s1);
+      s2 = fma(G[i][p], d2[i][p], s2);
+      s3 = fma(G[i][p], d3[i][p], s3);
+    }
+  t1 = T(0.5) * s1;
+  t2 = T(0.5) * s2;
+  t3 = T(0.5) * s3;
+}
+
 // dL/dx_c = P G[:, c] of one element from the sums of el_bwd_sums.
 template <typename T>
 __device__ __forceinline__ void el_bwd_gx(const T (&G)[3][4], T adet, T sl, T sm, T t1, T t2, T t3,
@@ -217,7 +292,8 @@ __device__ __forceinline__ void el_bwd_element(const ElBwdArgs<T>& a, const tg::
         for (int jj = 0; jj < 3; ++jj) w[i][jj] = __ldg(b + 3ll * i * lena[p] + jj);
     }
   };
-  el_bwd_sums<T>(G, wblk, t1, t2, t3, d1, d2, d3);
+  if constexpr (sizeof(T) == 8) el_bwd_sums_sym<T>(G, wblk, t1, t2, t3, d1, d2, d3);
+  else el_bwd_sums<T>(G, wblk, t1, t2, t3, d1, d2, d3);
   el_bwd_write_coef<T>(a, tab, e, adet, t1, t2 + t3);
   el_bwd_gx<T>(G, adet, sl, sm, t1, t2, t3, d1, d2, d3, gx);
 }
