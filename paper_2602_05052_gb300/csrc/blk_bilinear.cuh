@@ -63,8 +63,10 @@ __host__ __device__ constexpr int map_col(int r, int c) {
 }
 
 // The Map of a block (any view with nbe, be[] and vtx(c, k)): every
-// distinct element's output rows into KF, columns in map_col order.
-template <int EL, typename T, int UB, bool LOAD, bool FANP2 = false, typename View>
+// distinct element's output rows into KF, columns in map_col order.  SCR:
+// the element's K_e and, with LOAD, F_e come from a first pass (a.scr, NS
+// values per element, NS + NV with LOAD) instead of being computed here.
+template <int EL, typename T, int UB, bool LOAD, bool FANP2 = false, bool SCR = false, typename View>
 __device__ __forceinline__ void blk_bilinear_map(const FwdArgs<T>& a, const RefTab<T>& tab, int capE, const View& v,
                                                  void* kf_buf) {
   constexpr int NV = Elem<EL>::nv, NG = Elem<EL>::ngeo, NS = NV * (NV + 1) / 2;
@@ -72,6 +74,43 @@ __device__ __forceinline__ void blk_bilinear_map(const FwdArgs<T>& a, const RefT
   using V = typename Vec16<T>::type;
   V* KF = reinterpret_cast<V*>(kf_buf);
   const int NT = blockDim.x;
+  if constexpr (SCR) {
+    constexpr int SS = NS + (LOAD ? NV : 0);
+    for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * NT) {
+      T K[UB][NS], fe[UB][LOAD ? NV : 1];
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int j = j0 + u * NT < v.nbe ? j0 + u * NT : 0;
+        const T* src = a.scr + bel_elem(v.be[j]) * SS;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) K[u][k] = __ldg(src + k);
+        if constexpr (LOAD) {
+#pragma unroll
+          for (int r = 0; r < NV; ++r) fe[u][r] = __ldg(src + NS + r);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int j = j0 + u * NT;
+        if (j >= v.nbe) continue;
+#pragma unroll
+        for (int r = 0; r < NV; ++r) {
+          T row[NW * VN];
+#pragma unroll
+          for (int c = 0; c < NV; ++c) {
+            const int b = map_col<NV, FANP2>(r, c), lo = r < b ? r : b, hi = r < b ? b : r;
+            row[c] = K[u][lo * NV - lo * (lo - 1) / 2 + (hi - lo)];
+          }
+#pragma unroll
+          for (int c = NV; c < NW * VN; ++c) row[c] = T(0);
+          if constexpr (LOAD) row[NV] = fe[u][r];
+#pragma unroll
+          for (int w = 0; w < NW; ++w) KF[(r * NW + w) * capE + j] = Vec16<T>::make(row + w * VN);
+        }
+      }
+    }
+    return;
+  }
   for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * NT) {
     int e[UB];
     ElemIn<EL, T> in[UB];

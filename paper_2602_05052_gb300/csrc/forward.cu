@@ -171,7 +171,9 @@ __global__ void __launch_bounds__(BT) k_load_blk(const FwdArgs<T> a, const __gri
 
 // The fan-ordered kernels (P1 triangles, fan.cuh): the same Map, the Reduce
 // along each row's fan in registers.  LOAD assembles the system (K, F).
-template <typename T, int UB, bool LOAD>
+// SCR: the Map takes each element's K_e and F_e from k_p1_tri_map (the FP64
+// two-pass form), the same values as computing them here.
+template <typename T, int UB, bool LOAD, bool SCR = false>
 __global__ void __launch_bounds__(BT, blk_min_ctas_bt<TG_P1_TRI, T, UB, LOAD>()) k_bilinear_fan(
     const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab, const tg::FanArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(BT, blk_min_ctas_bt<TG_P1_TRI, T, UB, LOAD>())
   unsigned char* kf = pipe.init(smem, g);
   __syncthreads();  // publishes the mbarrier initialisation
   TG_FAN_PIPELINE_BEGIN(pipe, g, a.status)
-  tg::blk_bilinear_map<TG_P1_TRI, T, UB, LOAD>(a, tab, g.capE, v, kf);
+  tg::blk_bilinear_map<TG_P1_TRI, T, UB, LOAD, false, SCR>(a, tab, g.capE, v, kf);
   __syncthreads();
   tg::fan_reduce_bilinear<T, LOAD>(a, g.capE, v, kf);
   __syncthreads();  // stage s and the Map's rows are free again
@@ -284,6 +286,55 @@ void fan_dispatch(int ub, Go&& go) {
     else if (ub <= 3) go(k_bilinear_fan<T, 3, LOAD>);
     else if (ub <= 4) go(k_bilinear_fan<T, 4, LOAD>);
     else go(k_bilinear_fan<T, 6, LOAD>);
+  }
+}
+
+// FP64 P1 triangles, pass 1 of 2 (the FP64 pipe bounds FP64 assembly, and
+// the row blocks would evaluate an element 1.23 times): one thread per
+// element computes K_e (packed upper triangle, 6 values) and, with LOAD, F_e
+// (3 values) once, exactly as the Map of k_bilinear_fan does, into
+// rec[SS e ...] (SS = 6, 9 with LOAD); a degenerate element is flagged and
+// gets zeros.  A CTA's 128 records go to HBM as contiguous 16-byte vectors
+// through shared memory.
+template <bool LOAD>
+__global__ void __launch_bounds__(128) k_p1_tri_map(const FwdArgs<double> a, const __grid_constant__ tg::RefTab<double> tab,
+                                                   int64_t E, double* __restrict__ rec) {
+  constexpr int SS = LOAD ? 9 : 6;
+  __shared__ double2 buf[128 * SS / 2];
+  double* bd = reinterpret_cast<double*>(buf);
+  for (int64_t e0 = (int64_t)blockIdx.x * 128; e0 < E; e0 += (int64_t)gridDim.x * 128) {
+    const int64_t e = e0 + threadIdx.x;
+    double o[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) o[k] = 0.0;
+    if (e < E) {
+      tg::ElemIn<TG_P1_TRI, double> in;
+      tg::elem_ids<TG_P1_TRI, double>(a, e, in);
+      tg::elem_data<TG_P1_TRI, double>(a, e, in);
+      double fv[3];
+      if constexpr (LOAD) tg::p1_load_f<3, double>(a.f, a.f_layout, e, in.v, fv);
+      double K[6], adet;
+      if (!tg::p1_elem_sym<TG_P1_TRI, double>(in, a.c, tab, K, &adet)) {
+        tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) o[k] = K[k];
+        if constexpr (LOAD) {
+          double fe[3];
+          tg::p1_load_entries<3, double>(a.f_layout, adet, fv, tab, fe);
+#pragma unroll
+          for (int r = 0; r < 3; ++r) o[6 + r] = fe[r];
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < SS; ++k) bd[threadIdx.x * SS + k] = o[k];
+    __syncthreads();
+    const int64_t nd = (E - e0 < 128 ? E - e0 : 128) * SS;  // doubles of this CTA's records
+    double2* dst = reinterpret_cast<double2*>(rec + SS * e0);
+    for (int64_t k = threadIdx.x; k < nd / 2; k += 128) dst[k] = buf[k];
+    if ((nd & 1) && threadIdx.x == 0) rec[SS * e0 + nd - 1] = bd[nd - 1];
+    __syncthreads();
   }
 }
 
@@ -402,10 +453,36 @@ FwdArgs<T> base_args(const tg_pattern* p, const void* coords) {
   a.f = nullptr;
   a.f_layout = 0;
   a.F = nullptr;
+  a.scr = nullptr;
   return a;
 }
 
 bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+// FP64 P1 triangles with fans, in two passes through the pattern's element
+// scratch (9 doubles per element): k_p1_tri_map evaluates every element
+// once, then the fan kernel reduces the stored K_e (and F_e) in fan order.
+// The same values and summation order as the one-pass kernel, hence the
+// same bits; overlapping calls on one pattern share the scratch.
+template <bool LOAD>
+tg_status tri_two_pass_f64(const tg_pattern* p, FwdArgs<double> a, cudaStream_t s) {
+  const tg::RefTab<double>& tab = table<double>(p->el);
+  double* rec = static_cast<double*>(p->elem_scratch);
+  if (p->E > 0) {
+    const int g1 = (int)std::min<int64_t>(tg::grid_for(p->E, 128), 32ll * tg::sm_count());
+    k_p1_tri_map<LOAD><<<g1, 128, 0, s>>>(a, tab, p->E, rec);
+    TG_CK_LAUNCH("k_p1_tri_map");
+  }
+  a.scr = rec;
+  const size_t sb = bilinear_fan_smem<double, LOAD>(p);
+  auto kern = k_bilinear_fan<double, 3, LOAD, true>;
+  dim3 grid;
+  tg_status st = launch_blk(kern, sb, p, &grid);
+  if (st != TG_OK) return st;
+  kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::fan_args(p));
+  TG_CK_LAUNCH("k_bilinear_fan<scratch>");
+  return TG_OK;
+}
 
 template <int EL, typename T>
 tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, bool atomic) {
@@ -447,6 +524,9 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
   if constexpr (EL == TG_P1_TRI) {
     const size_t sb = bilinear_fan_smem<T, false>(p);
     if (use_fan(p, sb)) {
+      if constexpr (sizeof(T) == 8) {
+        if (p->elem_scratch) return tri_two_pass_f64<false>(p, a, s);
+      }
       tg_status st = TG_OK;
       auto go = [&](auto kern) {
         dim3 grid;
@@ -614,6 +694,9 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
     a.F = static_cast<T*>(F);
     const bool tri = p->el == TG_P1_TRI;
     if (tri && use_fan(p, bilinear_fan_smem<T, true>(p))) {
+      if constexpr (sizeof(T) == 8) {
+        if (p->elem_scratch) return tri_two_pass_f64<true>(p, a, s);
+      }
       const size_t sb = bilinear_fan_smem<T, true>(p);
       const tg::RefTab<T>& tab = table<T>(p->el);
       tg_status st = TG_OK;

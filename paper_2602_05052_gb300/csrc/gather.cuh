@@ -29,6 +29,9 @@ struct FwdArgs {
   const T* __restrict__ f;  // load of the fused system assembly (NULL otherwise)
   int f_layout;
   T* __restrict__ F;
+  // per-element K_e (packed upper triangle) then F_e, written by a first
+  // pass (FP64 two-pass assembly; NULL otherwise)
+  const T* __restrict__ scr;
 };
 
 template <typename T>

@@ -1309,9 +1309,12 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   TG_CK(cudaMalloc(&p->arrivals, 16));
   TG_CK(cudaMemsetAsync(p->arrivals, 0, 16, s));
   // per-element results of the two-pass kernels: nv * dim values per
-  // element, 20 for vector elasticity (its forward's geometry records)
-  if ((nc == 1 || el == TG_P1_TET_VEC3) && E > 0)
-    TG_CK(cudaMalloc(&p->elem_scratch, (size_t)E * (nc == 1 ? nv * tg::dim_of(el) : 20) * sizeof(double)));
+  // element (9 for P1 triangles: the FP64 forward's K_e and F_e), 20 for
+  // vector elasticity (its forward's geometry records)
+  if ((nc == 1 || el == TG_P1_TET_VEC3) && E > 0) {
+    const int per = nc != 1 ? 20 : el == TG_P1_TRI ? 9 : nv * tg::dim_of(el);
+    TG_CK(cudaMalloc(&p->elem_scratch, (size_t)E * per * sizeof(double)));
+  }
   TG_CK(cudaStreamSynchronize(s));
   if ((st = read_status(p, s, "tg_build_pattern")) != TG_OK) return st;
   guard.ok = true;
