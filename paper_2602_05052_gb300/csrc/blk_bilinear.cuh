@@ -64,8 +64,9 @@ __host__ __device__ constexpr int map_col(int r, int c) {
 
 // The Map of a block (any view with nbe, be[] and vtx(c, k)): every
 // distinct element's output rows into KF, columns in map_col order.  SCR:
-// the element's K_e and, with LOAD, F_e come from a first pass (a.scr, NS
-// values per element, NS + NV with LOAD) instead of being computed here.
+// the element's K_e (a.scr, NS values per element) and, with LOAD, F_e
+// (a.scrF, NV per element) come from a first pass instead of being computed
+// here.
 template <int EL, typename T, int UB, bool LOAD, bool FANP2 = false, bool SCR = false, typename View>
 __device__ __forceinline__ void blk_bilinear_map(const FwdArgs<T>& a, const RefTab<T>& tab, int capE, const View& v,
                                                  void* kf_buf) {
@@ -75,18 +76,18 @@ __device__ __forceinline__ void blk_bilinear_map(const FwdArgs<T>& a, const RefT
   V* KF = reinterpret_cast<V*>(kf_buf);
   const int NT = blockDim.x;
   if constexpr (SCR) {
-    constexpr int SS = NS + (LOAD ? NV : 0);
     for (int j0 = threadIdx.x; j0 < v.nbe; j0 += UB * NT) {
       T K[UB][NS], fe[UB][LOAD ? NV : 1];
 #pragma unroll
       for (int u = 0; u < UB; ++u) {
         const int j = j0 + u * NT < v.nbe ? j0 + u * NT : 0;
-        const T* src = a.scr + bel_elem(v.be[j]) * SS;
+        const int64_t e = bel_elem(v.be[j]);
+        const T* src = a.scr + e * NS;
 #pragma unroll
         for (int k = 0; k < NS; ++k) K[u][k] = __ldg(src + k);
         if constexpr (LOAD) {
 #pragma unroll
-          for (int r = 0; r < NV; ++r) fe[u][r] = __ldg(src + NS + r);
+          for (int r = 0; r < NV; ++r) fe[u][r] = __ldg(a.scrF + e * NV + r);
         }
       }
 #pragma unroll
@@ -180,7 +181,7 @@ __device__ __forceinline__ void blk_bilinear_map(const FwdArgs<T>& a, const RefT
 //            LOAD also F of the node.  Ends with a CTA barrier.
 // Every CSR entry is the sum of its contributions in increasing element
 // order, starting from the first one.
-template <int EL, typename T, int UB, bool LOAD>
+template <int EL, typename T, int UB, bool LOAD, bool SCR = false>
 __device__ __forceinline__ void blk_bilinear_block(const FwdArgs<T>& a, const RefTab<T>& tab, int capE,
                                                    const BlkView& v, void* kf_buf, T* acc) {
   constexpr int NV = Elem<EL>::nv;
@@ -188,7 +189,7 @@ __device__ __forceinline__ void blk_bilinear_block(const FwdArgs<T>& a, const Re
   using V = typename Vec16<T>::type;
   const V* KF = reinterpret_cast<const V*>(kf_buf);
   const int NT = blockDim.x;
-  blk_bilinear_map<EL, T, UB, LOAD>(a, tab, capE, v, kf_buf);
+  blk_bilinear_map<EL, T, UB, LOAD, false, SCR>(a, tab, capE, v, kf_buf);
   __syncthreads();
   // Reduce
   {

@@ -34,7 +34,8 @@ using tg::scalar_row;
 
 // One CTA per block of R consecutive rows (staged gather, gather.cuh).
 // Shared memory: the reference tables, then the stage buffer.
-template <int EL, typename T>
+// SCR: the rows come from k_p1_map's per-element K_e (FP64 two passes).
+template <int EL, typename T, bool SCR = false>
 __global__ void __launch_bounds__(BS) k_bilinear_gather(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
                                                         int cap) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -42,7 +43,7 @@ __global__ void __launch_bounds__(BS) k_bilinear_gather(const FwdArgs<T> a, cons
   copy_table(ts, tab);
   const int64_t r0 = (int64_t)blockIdx.x * blockDim.x;
   const int64_t r1 = r0 + blockDim.x < a.n ? r0 + blockDim.x : a.n;
-  tg::assemble_rows<EL, T>(a, ts, tab, smem + tab_bytes<T>(), cap, r0, r1);
+  tg::assemble_rows<EL, T, SCR>(a, ts, tab, smem + tab_bytes<T>(), cap, r0, r1);
 }
 
 
@@ -68,7 +69,9 @@ constexpr int blk_min_ctas_bt() {
 // vector F (a.f, a.f_layout -> a.F), entry for entry the arithmetic of
 // k_load_blk: the system (K, F) in one pass.  acc_n = the accumulator count
 // (the longest row x BS), cleared here once and by every block after use.
-template <int EL, typename T, int UB, bool LOAD>
+// SCR: the Map takes each element's K_e and F_e from k_p1_map (FP64 two
+// passes).
+template <int EL, typename T, int UB, bool LOAD, bool SCR = false>
 __global__ void __launch_bounds__(BT, blk_min_ctas_bt<EL, T, UB, LOAD>()) k_bilinear_blk(
     const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab, const tg::BlkArgs g, int acc_n) {
   constexpr int NV = tg::Elem<EL>::nv;
@@ -80,7 +83,7 @@ __global__ void __launch_bounds__(BT, blk_min_ctas_bt<EL, T, UB, LOAD>()) k_bili
   for (int q = threadIdx.x; q < acc_n; q += blockDim.x) acc[q] = T(0);
   __syncthreads();  // publishes the mbarrier initialisation and the cleared acc
   TG_BLK_PIPELINE_BEGIN(pipe, g, a.status)
-  tg::blk_bilinear_block<EL, T, UB, LOAD>(a, tab, g.capE, v, kf, acc);
+  tg::blk_bilinear_block<EL, T, UB, LOAD, SCR>(a, tab, g.capE, v, kf, acc);
   TG_BLK_PIPELINE_END
 }
 
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(BT) k_load_blk(const FwdArgs<T> a, const __gri
 
 // The fan-ordered kernels (P1 triangles, fan.cuh): the same Map, the Reduce
 // along each row's fan in registers.  LOAD assembles the system (K, F).
-// SCR: the Map takes each element's K_e and F_e from k_p1_tri_map (the FP64
+// SCR: the Map takes each element's K_e and F_e from k_p1_map (the FP64
 // two-pass form), the same values as computing them here.
 template <typename T, int UB, bool LOAD, bool SCR = false>
 __global__ void __launch_bounds__(BT, blk_min_ctas_bt<TG_P1_TRI, T, UB, LOAD>()) k_bilinear_fan(
@@ -289,53 +292,72 @@ void fan_dispatch(int ub, Go&& go) {
   }
 }
 
-// FP64 P1 triangles, pass 1 of 2 (the FP64 pipe bounds FP64 assembly, and
-// the row blocks would evaluate an element 1.23 times): one thread per
-// element computes K_e (packed upper triangle, 6 values) and, with LOAD, F_e
-// (3 values) once, exactly as the Map of k_bilinear_fan does, into
-// rec[SS e ...] (SS = 6, 9 with LOAD); a degenerate element is flagged and
-// gets zeros.  A CTA's 128 records go to HBM as contiguous 16-byte vectors
-// through shared memory.
-template <bool LOAD>
-__global__ void __launch_bounds__(128) k_p1_tri_map(const FwdArgs<double> a, const __grid_constant__ tg::RefTab<double> tab,
-                                                   int64_t E, double* __restrict__ rec) {
-  constexpr int SS = LOAD ? 9 : 6;
-  __shared__ double2 buf[128 * SS / 2];
+// FP64 P1 simplices, pass 1 of 2 (the FP64 pipe bounds FP64 assembly, and
+// the row blocks would evaluate an element 1.23 times on triangles, about 3
+// times on tetrahedra): one thread per element computes K_e (packed upper
+// triangle, NS = NV (NV + 1) / 2 values) into rec[NS e ...] and, with LOAD,
+// F_e into recF[NV e ...], once, exactly as the block Map does; a
+// degenerate element is flagged and gets zeros.  A CTA's 128 K records go
+// to HBM as contiguous 16-byte vectors through shared memory.
+template <int EL, bool LOAD>
+__global__ void __launch_bounds__(128) k_p1_map(const FwdArgs<double> a, const __grid_constant__ tg::RefTab<double> tab,
+                                               int64_t E, double* __restrict__ rec, double* __restrict__ recF) {
+  constexpr int NV = tg::Elem<EL>::nv, NS = NV * (NV + 1) / 2;
+  __shared__ double2 buf[128 * NS / 2];
   double* bd = reinterpret_cast<double*>(buf);
   for (int64_t e0 = (int64_t)blockIdx.x * 128; e0 < E; e0 += (int64_t)gridDim.x * 128) {
     const int64_t e = e0 + threadIdx.x;
-    double o[9];
+    double o[NS];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) o[k] = 0.0;
+    for (int k = 0; k < NS; ++k) o[k] = 0.0;
     if (e < E) {
-      tg::ElemIn<TG_P1_TRI, double> in;
-      tg::elem_ids<TG_P1_TRI, double>(a, e, in);
-      tg::elem_data<TG_P1_TRI, double>(a, e, in);
-      double fv[3];
-      if constexpr (LOAD) tg::p1_load_f<3, double>(a.f, a.f_layout, e, in.v, fv);
-      double K[6], adet;
-      if (!tg::p1_elem_sym<TG_P1_TRI, double>(in, a.c, tab, K, &adet)) {
+      tg::ElemIn<EL, double> in;
+      tg::elem_ids<EL, double>(a, e, in);
+      tg::elem_data<EL, double>(a, e, in);
+      double fv[NV], fe[NV];
+      if constexpr (LOAD) tg::p1_load_f<NV, double>(a.f, a.f_layout, e, in.v, fv);
+      double adet;
+      if (!tg::p1_elem_sym<EL, double>(in, a.c, tab, o, &adet)) {
         tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
-      } else {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) o[k] = K[k];
-        if constexpr (LOAD) {
-          double fe[3];
-          tg::p1_load_entries<3, double>(a.f_layout, adet, fv, tab, fe);
+        for (int k = 0; k < NS; ++k) o[k] = 0.0;
 #pragma unroll
-          for (int r = 0; r < 3; ++r) o[6 + r] = fe[r];
-        }
+        for (int r = 0; r < NV; ++r) fe[r] = 0.0;
+      } else if constexpr (LOAD) {
+        tg::p1_load_entries<NV, double>(a.f_layout, adet, fv, tab, fe);
+      }
+      if constexpr (LOAD) {
+#pragma unroll
+        for (int r = 0; r < NV; ++r) recF[e * NV + r] = fe[r];
       }
     }
 #pragma unroll
-    for (int k = 0; k < SS; ++k) bd[threadIdx.x * SS + k] = o[k];
+    for (int k = 0; k < NS; ++k) bd[threadIdx.x * NS + k] = o[k];
     __syncthreads();
-    const int64_t nd = (E - e0 < 128 ? E - e0 : 128) * SS;  // doubles of this CTA's records
-    double2* dst = reinterpret_cast<double2*>(rec + SS * e0);
+    const int64_t nd = (E - e0 < 128 ? E - e0 : 128) * NS;  // doubles of this CTA's records
+    double* dst0 = rec + NS * e0;  // 16-byte aligned: NS * 128 is even
+    double2* dst = reinterpret_cast<double2*>(dst0);
     for (int64_t k = threadIdx.x; k < nd / 2; k += 128) dst[k] = buf[k];
-    if ((nd & 1) && threadIdx.x == 0) rec[SS * e0 + nd - 1] = bd[nd - 1];
+    if ((nd & 1) && threadIdx.x == 0) dst0[nd - 1] = bd[nd - 1];
     __syncthreads();
   }
+}
+
+// FP64 P1, pass 2 of the load vector: F[i] = the sum of F_e[a] over node
+// i's incidences (e, a) in increasing element order, starting from the
+// first (the order and the values of the row-block load kernel).
+template <int EL>
+__global__ void __launch_bounds__(128) k_p1_load_reduce(const FwdArgs<double> a, const double* __restrict__ recF) {
+  constexpr int NV = tg::Elem<EL>::nv;
+  const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
+  if (i >= a.n) return;
+  double fs = 0.0;
+  const int j1 = __ldg(a.inc_ptr + i + 1);
+  for (int j = __ldg(a.inc_ptr + i); j < j1; ++j) {
+    const int ea = __ldg(a.inc_e + j);
+    fs += __ldg(recF + (int64_t)(ea >> 3) * NV + (ea & 7));
+  }
+  a.F[i] = fs;
 }
 
 // Comparison point: classic scatter-add (Eq. (scatter_add)) with atomics,
@@ -454,33 +476,46 @@ FwdArgs<T> base_args(const tg_pattern* p, const void* coords) {
   a.f_layout = 0;
   a.F = nullptr;
   a.scr = nullptr;
+  a.scrF = nullptr;
   return a;
 }
 
 bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
-// FP64 P1 triangles with fans, in two passes through the pattern's element
-// scratch (9 doubles per element): k_p1_tri_map evaluates every element
-// once, then the fan kernel reduces the stored K_e (and F_e) in fan order.
-// The same values and summation order as the one-pass kernel, hence the
-// same bits; overlapping calls on one pattern share the scratch.
-template <bool LOAD>
-tg_status tri_two_pass_f64(const tg_pattern* p, FwdArgs<double> a, cudaStream_t s) {
+// FP64 P1 simplices with row blocks, in two passes through the pattern's
+// element scratch: k_p1_map evaluates every element once, then the block
+// kernel (triangles: the fan kernel) reduces the stored K_e (and F_e).  The
+// same values and summation order as the one-pass kernels, hence the same
+// bits; overlapping calls on one pattern share the scratch.
+template <int EL, bool LOAD>
+tg_status two_pass_f64(const tg_pattern* p, FwdArgs<double> a, cudaStream_t s) {
   const tg::RefTab<double>& tab = table<double>(p->el);
+  constexpr int NV = tg::Elem<EL>::nv, NS = NV * (NV + 1) / 2;
   double* rec = static_cast<double*>(p->elem_scratch);
+  double* recF = rec + p->E * NS;
   if (p->E > 0) {
     const int g1 = (int)std::min<int64_t>(tg::grid_for(p->E, 128), 32ll * tg::sm_count());
-    k_p1_tri_map<LOAD><<<g1, 128, 0, s>>>(a, tab, p->E, rec);
-    TG_CK_LAUNCH("k_p1_tri_map");
+    k_p1_map<EL, LOAD><<<g1, 128, 0, s>>>(a, tab, p->E, rec, recF);
+    TG_CK_LAUNCH("k_p1_map");
   }
   a.scr = rec;
-  const size_t sb = bilinear_fan_smem<double, LOAD>(p);
-  auto kern = k_bilinear_fan<double, 3, LOAD, true>;
+  a.scrF = recF;
   dim3 grid;
-  tg_status st = launch_blk(kern, sb, p, &grid);
-  if (st != TG_OK) return st;
-  kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::fan_args(p));
-  TG_CK_LAUNCH("k_bilinear_fan<scratch>");
+  if constexpr (EL == TG_P1_TRI) {
+    const size_t sb = bilinear_fan_smem<double, LOAD>(p);
+    auto kern = k_bilinear_fan<double, 3, LOAD, true>;
+    tg_status st = launch_blk(kern, sb, p, &grid);
+    if (st != TG_OK) return st;
+    kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::fan_args(p));
+    TG_CK_LAUNCH("k_bilinear_fan<scratch>");
+  } else {
+    const size_t sb = bilinear_blk_smem<tg::Elem<EL>::nv, double, LOAD>(p);
+    auto kern = k_bilinear_blk<EL, double, 2, LOAD, true>;
+    tg_status st = launch_blk(kern, sb, p, &grid);
+    if (st != TG_OK) return st;
+    kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::blk_args(p), p->max_row_len * BT);
+    TG_CK_LAUNCH("k_bilinear_blk<scratch>");
+  }
   return TG_OK;
 }
 
@@ -525,7 +560,7 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
     const size_t sb = bilinear_fan_smem<T, false>(p);
     if (use_fan(p, sb)) {
       if constexpr (sizeof(T) == 8) {
-        if (p->elem_scratch) return tri_two_pass_f64<false>(p, a, s);
+        if (p->elem_scratch) return two_pass_f64<TG_P1_TRI, false>(p, a, s);
       }
       tg_status st = TG_OK;
       auto go = [&](auto kern) {
@@ -542,6 +577,9 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
   {
     const size_t sb = bilinear_blk_smem<El::nv, T, false>(p);
     if (use_blk<T>(p, sb)) {
+      if constexpr (sizeof(T) == 8 && EL == TG_P1_TET) {
+        if (p->elem_scratch) return two_pass_f64<TG_P1_TET, false>(p, a, s);
+      }
       const int ub = blk_ub<T>(p);
       tg_status st = TG_OK;
       auto go = [&](auto kern) {
@@ -564,6 +602,19 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
       }
       if (st != TG_OK) return st;
       TG_CK_LAUNCH("k_bilinear_blk");
+      return TG_OK;
+    }
+  }
+  if constexpr (sizeof(T) == 8 && EL != TG_P2_TRI) {
+    if (p->elem_scratch && p->E > 0) {  // FP64 P1: every element once, then the rows' sums
+      const int g1 = (int)std::min<int64_t>(tg::grid_for(p->E, 128), 32ll * tg::sm_count());
+      k_p1_map<EL, false><<<g1, 128, 0, s>>>(a, tab, p->E, static_cast<double*>(p->elem_scratch), nullptr);
+      TG_CK_LAUNCH("k_p1_map");
+      a.scr = static_cast<const T*>(p->elem_scratch);
+      tg_status st = set_smem((const void*)k_bilinear_gather<EL, T, true>, smem);
+      if (st != TG_OK) return st;
+      k_bilinear_gather<EL, T, true><<<tg::grid_for(p->N, R), R, smem, s>>>(a, tab, cap);
+      TG_CK_LAUNCH("k_bilinear_gather<scratch>");
       return TG_OK;
     }
   }
@@ -695,7 +746,7 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
     const bool tri = p->el == TG_P1_TRI;
     if (tri && use_fan(p, bilinear_fan_smem<T, true>(p))) {
       if constexpr (sizeof(T) == 8) {
-        if (p->elem_scratch) return tri_two_pass_f64<true>(p, a, s);
+        if (p->elem_scratch) return two_pass_f64<TG_P1_TRI, true>(p, a, s);
       }
       const size_t sb = bilinear_fan_smem<T, true>(p);
       const tg::RefTab<T>& tab = table<T>(p->el);
@@ -712,6 +763,9 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
     }
     const size_t sb = tri ? bilinear_blk_smem<3, T, true>(p) : bilinear_blk_smem<4, T, true>(p);
     if (use_blk<T>(p, sb)) {
+      if constexpr (sizeof(T) == 8) {
+        if (!tri && p->elem_scratch) return two_pass_f64<TG_P1_TET, true>(p, a, s);
+      }
       const int ub = blk_ub<T>(p);
       const tg::RefTab<T>& tab = table<T>(p->el);
       tg_status st = TG_OK;
@@ -736,6 +790,52 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
       }
       if (st != TG_OK) return st;
       TG_CK_LAUNCH("k_bilinear_blk<load>");
+      return TG_OK;
+    }
+  }
+  if constexpr (sizeof(T) == 8) {
+    if ((p->el == TG_P1_TRI || p->el == TG_P1_TET) && p->elem_scratch && p->E > 0) {
+      // FP64 P1 in two passes: every element's K_e and F_e once, then the rows'
+      // and the nodes' sums (the values and orders of the one-pass kernels)
+      FwdArgs<T> a = base_args<T>(p, coords);
+      a.coef = static_cast<const T*>(kappa);
+      a.layout = kl;
+      a.c = (T)c;
+      a.out = static_cast<T*>(vals);
+      a.f = static_cast<const T*>(f);
+      a.f_layout = fl;
+      a.F = static_cast<T*>(F);
+      const bool tri = p->el == TG_P1_TRI;
+      const int NS = tri ? 6 : 10;
+      double* rec = static_cast<double*>(p->elem_scratch);
+      double* recF = rec + p->E * NS;
+      const tg::RefTab<T>& tab = table<T>(p->el);
+      const int g1 = (int)std::min<int64_t>(tg::grid_for(p->E, 128), 32ll * tg::sm_count());
+      if (tri) k_p1_map<TG_P1_TRI, true><<<g1, 128, 0, s>>>(a, tab, p->E, rec, recF);
+      else k_p1_map<TG_P1_TET, true><<<g1, 128, 0, s>>>(a, tab, p->E, rec, recF);
+      TG_CK_LAUNCH("k_p1_map<load>");
+      a.scr = rec;
+      using El3 = tg::Elem<TG_P1_TRI>;
+      using El4 = tg::Elem<TG_P1_TET>;
+      size_t stage = 0;
+      const int R = tri ? tg::staged_rows<T, El3::nv, El3::npw>(p->max_deg, p->max_row_len, &stage)
+                        : tg::staged_rows<T, El4::nv, El4::npw>(p->max_deg, p->max_row_len, &stage);
+      if (R == 0) {
+        tg::set_error("mesh degree too large for the staged gather");
+        return TG_ERR_UNSUPPORTED;
+      }
+      const size_t smem = tab_bytes<T>() + stage;
+      const int cap = std::max(1, R * p->max_deg);
+      const void* kern = tri ? (const void*)k_bilinear_gather<TG_P1_TRI, T, true>
+                             : (const void*)k_bilinear_gather<TG_P1_TET, T, true>;
+      tg_status st = set_smem(kern, smem);
+      if (st != TG_OK) return st;
+      if (tri) k_bilinear_gather<TG_P1_TRI, T, true><<<tg::grid_for(p->N, R), R, smem, s>>>(a, tab, cap);
+      else k_bilinear_gather<TG_P1_TET, T, true><<<tg::grid_for(p->N, R), R, smem, s>>>(a, tab, cap);
+      TG_CK_LAUNCH("k_bilinear_gather<scratch>");
+      if (tri) k_p1_load_reduce<TG_P1_TRI><<<tg::grid_for(p->N, 128), 128, 0, s>>>(a, recF);
+      else k_p1_load_reduce<TG_P1_TET><<<tg::grid_for(p->N, 128), 128, 0, s>>>(a, recF);
+      TG_CK_LAUNCH("k_p1_load_reduce");
       return TG_OK;
     }
   }

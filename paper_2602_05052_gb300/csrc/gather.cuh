@@ -29,9 +29,10 @@ struct FwdArgs {
   const T* __restrict__ f;  // load of the fused system assembly (NULL otherwise)
   int f_layout;
   T* __restrict__ F;
-  // per-element K_e (packed upper triangle) then F_e, written by a first
-  // pass (FP64 two-pass assembly; NULL otherwise)
+  // per-element K_e (packed upper triangles, scr) and F_e (scrF), written
+  // by a first pass (FP64 two-pass assembly; NULL otherwise)
   const T* __restrict__ scr;
+  const T* __restrict__ scrF;
 };
 
 template <typename T>
@@ -369,7 +370,10 @@ __host__ __device__ constexpr int ub_of() {
   return EL == TG_P1_TRI ? 4 : EL == TG_P2_TRI ? 2 : (sizeof(T) == 4 ? 3 : 2);
 }
 
-template <int EL, typename T>
+// SCR (P1, FP64 two passes): the incidences' rows come from the per-element
+// K_e of a first pass (a.scr, packed upper triangles of NV (NV + 1) / 2
+// values), the values elem_row would compute.
+template <int EL, typename T, bool SCR = false>
 __device__ __forceinline__ void assemble_rows(const FwdArgs<T>& a, const RefTab<T>& ts, const RefTab<T>& tc, unsigned char* buf, int cap,
                                               int64_t r0, int64_t r1) {
   using El = Elem<EL>;
@@ -379,6 +383,25 @@ __device__ __forceinline__ void assemble_rows(const FwdArgs<T>& a, const RefTab<
   uint32_t* posw = reinterpret_cast<uint32_t*>(contrib + (size_t)NV * cap);
   T* acc = reinterpret_cast<T*>(buf + staged_head<T, NV, NPW>(cap));
   const int J0 = __ldg(a.inc_ptr + r0), J1 = __ldg(a.inc_ptr + r1);
+  if constexpr (SCR) {
+    constexpr int NS = NV * (NV + 1) / 2;
+    for (int j = J0 + (int)threadIdx.x; j < J1; j += R) {
+      const int ea = __ldg(a.inc_e + j);
+      posw[j - J0] = __ldg(a.inc_pos + (int64_t)j * NPW);
+      if (NPW == 2) posw[cap + j - J0] = __ldg(a.inc_pos + (int64_t)j * NPW + 1);
+      const T* src = a.scr + (int64_t)(ea >> 3) * NS;
+      const int la = ea & 7;
+#pragma unroll
+      for (int b = 0; b < NV; ++b) {
+        // entry (la, b) of the packed triangle, la chosen at run time
+        contrib[b * cap + (j - J0)] = __ldg(src + (la <= b ? la * NV - la * (la - 1) / 2 + (b - la)
+                                                              : b * NV - b * (b - 1) / 2 + (la - b)));
+      }
+    }
+    __syncthreads();
+    reduce_rows<T, NV, NPW>(a, contrib, posw, acc, cap, r0, r1, J0);
+    return;
+  }
   // UB incidences per thread in flight: every load of one dependency level
   // (incidence record, then vertex ids, then coordinates and coefficients)
   // is issued for all of them before any is used.

@@ -1309,10 +1309,11 @@ extern "C" tg_status tg_build_pattern(const int32_t* cells, int64_t n_elems, int
   TG_CK(cudaMalloc(&p->arrivals, 16));
   TG_CK(cudaMemsetAsync(p->arrivals, 0, 16, s));
   // per-element results of the two-pass kernels: nv * dim values per
-  // element (9 for P1 triangles: the FP64 forward's K_e and F_e), 20 for
-  // vector elasticity (its forward's geometry records)
+  // element (for P1 at least the FP64 forward's K_e and F_e: 9 for
+  // triangles, 14 for tetrahedra), 20 for vector elasticity (its forward's
+  // geometry records)
   if ((nc == 1 || el == TG_P1_TET_VEC3) && E > 0) {
-    const int per = nc != 1 ? 20 : el == TG_P1_TRI ? 9 : nv * tg::dim_of(el);
+    const int per = nc != 1 ? 20 : el == TG_P1_TRI ? 9 : el == TG_P1_TET ? 14 : nv * tg::dim_of(el);
     TG_CK(cudaMalloc(&p->elem_scratch, (size_t)E * per * sizeof(double)));
   }
   TG_CK(cudaStreamSynchronize(s));
