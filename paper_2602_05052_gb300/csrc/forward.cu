@@ -487,6 +487,10 @@ bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 // kernel (triangles: the fan kernel) reduces the stored K_e (and F_e).  The
 // same values and summation order as the one-pass kernels, hence the same
 // bits; overlapping calls on one pattern share the scratch.
+// Below this many elements one pass is faster (a second launch costs more
+// than the repeated element work); both give the same bits.
+constexpr int64_t kTwoPassMinElems = 1 << 16;
+
 template <int EL, bool LOAD>
 tg_status two_pass_f64(const tg_pattern* p, FwdArgs<double> a, cudaStream_t s) {
   const tg::RefTab<double>& tab = table<double>(p->el);
@@ -560,7 +564,7 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
     const size_t sb = bilinear_fan_smem<T, false>(p);
     if (use_fan(p, sb)) {
       if constexpr (sizeof(T) == 8) {
-        if (p->elem_scratch) return two_pass_f64<TG_P1_TRI, false>(p, a, s);
+        if (p->elem_scratch && p->E >= kTwoPassMinElems) return two_pass_f64<TG_P1_TRI, false>(p, a, s);
       }
       tg_status st = TG_OK;
       auto go = [&](auto kern) {
@@ -578,7 +582,7 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
     const size_t sb = bilinear_blk_smem<El::nv, T, false>(p);
     if (use_blk<T>(p, sb)) {
       if constexpr (sizeof(T) == 8 && EL == TG_P1_TET) {
-        if (p->elem_scratch) return two_pass_f64<TG_P1_TET, false>(p, a, s);
+        if (p->elem_scratch && p->E >= kTwoPassMinElems) return two_pass_f64<TG_P1_TET, false>(p, a, s);
       }
       const int ub = blk_ub<T>(p);
       tg_status st = TG_OK;
@@ -606,7 +610,7 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
     }
   }
   if constexpr (sizeof(T) == 8 && EL != TG_P2_TRI) {
-    if (p->elem_scratch && p->E > 0) {  // FP64 P1: every element once, then the rows' sums
+    if (p->elem_scratch && p->E >= kTwoPassMinElems) {  // FP64 P1: every element once, then the rows' sums
       const int g1 = (int)std::min<int64_t>(tg::grid_for(p->E, 128), 32ll * tg::sm_count());
       k_p1_map<EL, false><<<g1, 128, 0, s>>>(a, tab, p->E, static_cast<double*>(p->elem_scratch), nullptr);
       TG_CK_LAUNCH("k_p1_map");
@@ -746,7 +750,7 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
     const bool tri = p->el == TG_P1_TRI;
     if (tri && use_fan(p, bilinear_fan_smem<T, true>(p))) {
       if constexpr (sizeof(T) == 8) {
-        if (p->elem_scratch) return two_pass_f64<TG_P1_TRI, true>(p, a, s);
+        if (p->elem_scratch && p->E >= kTwoPassMinElems) return two_pass_f64<TG_P1_TRI, true>(p, a, s);
       }
       const size_t sb = bilinear_fan_smem<T, true>(p);
       const tg::RefTab<T>& tab = table<T>(p->el);
@@ -764,7 +768,7 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
     const size_t sb = tri ? bilinear_blk_smem<3, T, true>(p) : bilinear_blk_smem<4, T, true>(p);
     if (use_blk<T>(p, sb)) {
       if constexpr (sizeof(T) == 8) {
-        if (!tri && p->elem_scratch) return two_pass_f64<TG_P1_TET, true>(p, a, s);
+        if (!tri && p->elem_scratch && p->E >= kTwoPassMinElems) return two_pass_f64<TG_P1_TET, true>(p, a, s);
       }
       const int ub = blk_ub<T>(p);
       const tg::RefTab<T>& tab = table<T>(p->el);
@@ -794,7 +798,7 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
     }
   }
   if constexpr (sizeof(T) == 8) {
-    if ((p->el == TG_P1_TRI || p->el == TG_P1_TET) && p->elem_scratch && p->E > 0) {
+    if ((p->el == TG_P1_TRI || p->el == TG_P1_TET) && p->elem_scratch && p->E >= kTwoPassMinElems) {
       // FP64 P1 in two passes: every element's K_e and F_e once, then the rows'
       // and the nodes' sums (the values and orders of the one-pass kernels)
       FwdArgs<T> a = base_args<T>(p, coords);
