@@ -180,10 +180,12 @@ void tg_pattern_destroy(tg_pattern* p);
  *             sum_q w_q |det J_e| ( kappa_eq G_qa . G_qb + c phi_a(x_q) phi_b(x_q) ).
  *   coords      [N][d]; kappa per kappa_layout (PER_QP, PER_ELEMENT or
  *               CONSTANT); vals_out [nnz] (node-level CSR of the pattern).
- * Element kinds TG_P1_TRI, TG_P2_TRI, TG_P1_TET.  FP64 on P1 elements goes
- * through the pattern's per-element scratch (each element evaluated once,
- * then reduced): such calls on one pattern that overlap (several streams)
- * race, as do FP64 tg_assemble_system calls on P1 elements. */
+ * Element kinds TG_P1_TRI, TG_P2_TRI, TG_P1_TET.  On meshes of at least
+ * 65,536 elements, FP64 calls on P1 elements and FP32 calls on P1
+ * tetrahedra go through the pattern's per-element scratch (each element
+ * evaluated once, then reduced; the same bits as one pass): such calls on
+ * one pattern that overlap (several streams) race, as do the corresponding
+ * tg_assemble_system calls. */
 tg_status tg_assemble_bilinear(const tg_pattern* p, tg_dtype dtype, const void* coords, const void* kappa,
                                tg_layout kappa_layout, double c, void* vals_out, tg_stream stream);
 

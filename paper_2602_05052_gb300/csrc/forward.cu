@@ -292,39 +292,42 @@ void fan_dispatch(int ub, Go&& go) {
   }
 }
 
-// FP64 P1 simplices, pass 1 of 2 (the FP64 pipe bounds FP64 assembly, and
-// the row blocks would evaluate an element 1.23 times on triangles, about 3
-// times on tetrahedra): one thread per element computes K_e (packed upper
-// triangle, NS = NV (NV + 1) / 2 values) into rec[NS e ...] and, with LOAD,
-// F_e into recF[NV e ...], once, exactly as the block Map does; a
-// degenerate element is flagged and gets zeros.  A CTA's 128 K records go
-// to HBM as contiguous 16-byte vectors through shared memory.
-template <int EL, bool LOAD>
-__global__ void __launch_bounds__(128) k_p1_map(const FwdArgs<double> a, const __grid_constant__ tg::RefTab<double> tab,
-                                               int64_t E, double* __restrict__ rec, double* __restrict__ recF) {
+// P1 simplices, pass 1 of 2 (FP64, bound by the FP64 pipe, where the row
+// blocks would evaluate an element 1.23 times on triangles and about 3
+// times on tetrahedra; FP32 tetrahedra): one thread per element computes
+// K_e (packed upper triangle, NS = NV (NV + 1) / 2 values) into
+// rec[NS e ...] and, with LOAD, F_e into recF[NV e ...], once, exactly as
+// the block Map does; a degenerate element is flagged and gets zeros.  A
+// CTA's 128 K records go to HBM as contiguous 16-byte vectors through
+// shared memory.
+template <int EL, typename T, bool LOAD>
+__global__ void __launch_bounds__(128) k_p1_map(const FwdArgs<T> a, const __grid_constant__ tg::RefTab<T> tab,
+                                               int64_t E, T* __restrict__ rec, T* __restrict__ recF) {
   constexpr int NV = tg::Elem<EL>::nv, NS = NV * (NV + 1) / 2;
-  __shared__ double2 buf[128 * NS / 2];
-  double* bd = reinterpret_cast<double*>(buf);
+  using V = typename tg::Vec16<T>::type;
+  constexpr int VN = tg::Vec16<T>::n;
+  __shared__ V buf[(128 * NS + VN - 1) / VN];
+  T* bd = reinterpret_cast<T*>(buf);
   for (int64_t e0 = (int64_t)blockIdx.x * 128; e0 < E; e0 += (int64_t)gridDim.x * 128) {
     const int64_t e = e0 + threadIdx.x;
-    double o[NS];
+    T o[NS];
 #pragma unroll
-    for (int k = 0; k < NS; ++k) o[k] = 0.0;
+    for (int k = 0; k < NS; ++k) o[k] = T(0);
     if (e < E) {
-      tg::ElemIn<EL, double> in;
-      tg::elem_ids<EL, double>(a, e, in);
-      tg::elem_data<EL, double>(a, e, in);
-      double fv[NV], fe[NV];
-      if constexpr (LOAD) tg::p1_load_f<NV, double>(a.f, a.f_layout, e, in.v, fv);
-      double adet;
-      if (!tg::p1_elem_sym<EL, double>(in, a.c, tab, o, &adet)) {
+      tg::ElemIn<EL, T> in;
+      tg::elem_ids<EL, T>(a, e, in);
+      tg::elem_data<EL, T>(a, e, in);
+      T fv[NV], fe[NV];
+      if constexpr (LOAD) tg::p1_load_f<NV, T>(a.f, a.f_layout, e, in.v, fv);
+      T adet;
+      if (!tg::p1_elem_sym<EL, T>(in, a.c, tab, o, &adet)) {
         tg::record_error(a.status, TG_ERR_DEGENERATE_ELEMENT, e);
 #pragma unroll
-        for (int k = 0; k < NS; ++k) o[k] = 0.0;
+        for (int k = 0; k < NS; ++k) o[k] = T(0);
 #pragma unroll
-        for (int r = 0; r < NV; ++r) fe[r] = 0.0;
+        for (int r = 0; r < NV; ++r) fe[r] = T(0);
       } else if constexpr (LOAD) {
-        tg::p1_load_entries<NV, double>(a.f_layout, adet, fv, tab, fe);
+        tg::p1_load_entries<NV, T>(a.f_layout, adet, fv, tab, fe);
       }
       if constexpr (LOAD) {
 #pragma unroll
@@ -334,24 +337,24 @@ __global__ void __launch_bounds__(128) k_p1_map(const FwdArgs<double> a, const _
 #pragma unroll
     for (int k = 0; k < NS; ++k) bd[threadIdx.x * NS + k] = o[k];
     __syncthreads();
-    const int64_t nd = (E - e0 < 128 ? E - e0 : 128) * NS;  // doubles of this CTA's records
-    double* dst0 = rec + NS * e0;  // 16-byte aligned: NS * 128 is even
-    double2* dst = reinterpret_cast<double2*>(dst0);
-    for (int64_t k = threadIdx.x; k < nd / 2; k += 128) dst[k] = buf[k];
-    if ((nd & 1) && threadIdx.x == 0) dst0[nd - 1] = bd[nd - 1];
+    const int64_t nd = (E - e0 < 128 ? E - e0 : 128) * NS;  // values of this CTA's records
+    T* dst0 = rec + NS * e0;  // 16-byte aligned: NS * 128 values are
+    V* dst = reinterpret_cast<V*>(dst0);
+    for (int64_t k = threadIdx.x; k < nd / VN; k += 128) dst[k] = buf[k];
+    for (int64_t k = (nd / VN) * VN + threadIdx.x; k < nd; k += 128) dst0[k] = bd[k];
     __syncthreads();
   }
 }
 
-// FP64 P1, pass 2 of the load vector: F[i] = the sum of F_e[a] over node
-// i's incidences (e, a) in increasing element order, starting from the
-// first (the order and the values of the row-block load kernel).
-template <int EL>
-__global__ void __launch_bounds__(128) k_p1_load_reduce(const FwdArgs<double> a, const double* __restrict__ recF) {
+// P1, pass 2 of the load vector: F[i] = the sum of F_e[a] over node i's
+// incidences (e, a) in increasing element order, starting from the first
+// (the order and the values of the row-block load kernel).
+template <int EL, typename T>
+__global__ void __launch_bounds__(128) k_p1_load_reduce(const FwdArgs<T> a, const T* __restrict__ recF) {
   constexpr int NV = tg::Elem<EL>::nv;
   const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
   if (i >= a.n) return;
-  double fs = 0.0;
+  T fs = T(0);
   const int j1 = __ldg(a.inc_ptr + i + 1);
   for (int j = __ldg(a.inc_ptr + i); j < j1; ++j) {
     const int ea = __ldg(a.inc_e + j);
@@ -482,39 +485,44 @@ FwdArgs<T> base_args(const tg_pattern* p, const void* coords) {
 
 bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
-// FP64 P1 simplices with row blocks, in two passes through the pattern's
-// element scratch: k_p1_map evaluates every element once, then the block
-// kernel (triangles: the fan kernel) reduces the stored K_e (and F_e).  The
-// same values and summation order as the one-pass kernels, hence the same
-// bits; overlapping calls on one pattern share the scratch.
-// Below this many elements one pass is faster (a second launch costs more
-// than the repeated element work); both give the same bits.
+// P1 simplices with row blocks in two passes through the pattern's element
+// scratch (FP64 triangles and tetrahedra, FP32 tetrahedra): k_p1_map
+// evaluates every element once, then the block kernel (triangles: the fan
+// kernel) reduces the stored K_e (and F_e).  The same values and summation
+// order as the one-pass kernels, hence the same bits; overlapping calls on
+// one pattern share the scratch.  Below kTwoPassMinElems elements one pass
+// is faster (a second launch costs more than the repeated element work).
 constexpr int64_t kTwoPassMinElems = 1 << 16;
 
-template <int EL, bool LOAD>
-tg_status two_pass_f64(const tg_pattern* p, FwdArgs<double> a, cudaStream_t s) {
-  const tg::RefTab<double>& tab = table<double>(p->el);
+template <typename T, int EL>
+bool two_pass_applies(const tg_pattern* p) {
+  return p->elem_scratch && p->E >= kTwoPassMinElems && (sizeof(T) == 8 || EL == TG_P1_TET);
+}
+
+template <int EL, typename T, bool LOAD>
+tg_status two_pass(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s) {
+  const tg::RefTab<T>& tab = table<T>(p->el);
   constexpr int NV = tg::Elem<EL>::nv, NS = NV * (NV + 1) / 2;
-  double* rec = static_cast<double*>(p->elem_scratch);
-  double* recF = rec + p->E * NS;
+  T* rec = static_cast<T*>(p->elem_scratch);
+  T* recF = rec + p->E * NS;
   if (p->E > 0) {
     const int g1 = (int)std::min<int64_t>(tg::grid_for(p->E, 128), 32ll * tg::sm_count());
-    k_p1_map<EL, LOAD><<<g1, 128, 0, s>>>(a, tab, p->E, rec, recF);
+    k_p1_map<EL, T, LOAD><<<g1, 128, 0, s>>>(a, tab, p->E, rec, recF);
     TG_CK_LAUNCH("k_p1_map");
   }
   a.scr = rec;
   a.scrF = recF;
   dim3 grid;
   if constexpr (EL == TG_P1_TRI) {
-    const size_t sb = bilinear_fan_smem<double, LOAD>(p);
-    auto kern = k_bilinear_fan<double, 3, LOAD, true>;
+    const size_t sb = bilinear_fan_smem<T, LOAD>(p);
+    auto kern = k_bilinear_fan<T, 3, LOAD, true>;
     tg_status st = launch_blk(kern, sb, p, &grid);
     if (st != TG_OK) return st;
     kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::fan_args(p));
     TG_CK_LAUNCH("k_bilinear_fan<scratch>");
   } else {
-    const size_t sb = bilinear_blk_smem<tg::Elem<EL>::nv, double, LOAD>(p);
-    auto kern = k_bilinear_blk<EL, double, 2, LOAD, true>;
+    const size_t sb = bilinear_blk_smem<tg::Elem<EL>::nv, T, LOAD>(p);
+    auto kern = k_bilinear_blk<EL, T, sizeof(T) == 8 ? 2 : 4, LOAD, true>;
     tg_status st = launch_blk(kern, sb, p, &grid);
     if (st != TG_OK) return st;
     kern<<<grid, blk_threads(p), sb, s>>>(a, tab, tg::blk_args(p), p->max_row_len * BT);
@@ -564,7 +572,7 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
     const size_t sb = bilinear_fan_smem<T, false>(p);
     if (use_fan(p, sb)) {
       if constexpr (sizeof(T) == 8) {
-        if (p->elem_scratch && p->E >= kTwoPassMinElems) return two_pass_f64<TG_P1_TRI, false>(p, a, s);
+        if (two_pass_applies<T, TG_P1_TRI>(p)) return two_pass<TG_P1_TRI, T, false>(p, a, s);
       }
       tg_status st = TG_OK;
       auto go = [&](auto kern) {
@@ -581,8 +589,8 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
   {
     const size_t sb = bilinear_blk_smem<El::nv, T, false>(p);
     if (use_blk<T>(p, sb)) {
-      if constexpr (sizeof(T) == 8 && EL == TG_P1_TET) {
-        if (p->elem_scratch && p->E >= kTwoPassMinElems) return two_pass_f64<TG_P1_TET, false>(p, a, s);
+      if constexpr (EL == TG_P1_TET) {
+        if (two_pass_applies<T, TG_P1_TET>(p)) return two_pass<TG_P1_TET, T, false>(p, a, s);
       }
       const int ub = blk_ub<T>(p);
       tg_status st = TG_OK;
@@ -609,10 +617,10 @@ tg_status launch_bilinear(const tg_pattern* p, FwdArgs<T> a, cudaStream_t s, boo
       return TG_OK;
     }
   }
-  if constexpr (sizeof(T) == 8 && EL != TG_P2_TRI) {
-    if (p->elem_scratch && p->E >= kTwoPassMinElems) {  // FP64 P1: every element once, then the rows' sums
+  if constexpr (EL != TG_P2_TRI) {
+    if (two_pass_applies<T, EL>(p)) {  // P1: every element once, then the rows' sums
       const int g1 = (int)std::min<int64_t>(tg::grid_for(p->E, 128), 32ll * tg::sm_count());
-      k_p1_map<EL, false><<<g1, 128, 0, s>>>(a, tab, p->E, static_cast<double*>(p->elem_scratch), nullptr);
+      k_p1_map<EL, T, false><<<g1, 128, 0, s>>>(a, tab, p->E, static_cast<T*>(p->elem_scratch), nullptr);
       TG_CK_LAUNCH("k_p1_map");
       a.scr = static_cast<const T*>(p->elem_scratch);
       tg_status st = set_smem((const void*)k_bilinear_gather<EL, T, true>, smem);
@@ -750,7 +758,7 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
     const bool tri = p->el == TG_P1_TRI;
     if (tri && use_fan(p, bilinear_fan_smem<T, true>(p))) {
       if constexpr (sizeof(T) == 8) {
-        if (p->elem_scratch && p->E >= kTwoPassMinElems) return two_pass_f64<TG_P1_TRI, true>(p, a, s);
+        if (two_pass_applies<T, TG_P1_TRI>(p)) return two_pass<TG_P1_TRI, T, true>(p, a, s);
       }
       const size_t sb = bilinear_fan_smem<T, true>(p);
       const tg::RefTab<T>& tab = table<T>(p->el);
@@ -767,9 +775,7 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
     }
     const size_t sb = tri ? bilinear_blk_smem<3, T, true>(p) : bilinear_blk_smem<4, T, true>(p);
     if (use_blk<T>(p, sb)) {
-      if constexpr (sizeof(T) == 8) {
-        if (!tri && p->elem_scratch && p->E >= kTwoPassMinElems) return two_pass_f64<TG_P1_TET, true>(p, a, s);
-      }
+      if (!tri && two_pass_applies<T, TG_P1_TET>(p)) return two_pass<TG_P1_TET, T, true>(p, a, s);
       const int ub = blk_ub<T>(p);
       const tg::RefTab<T>& tab = table<T>(p->el);
       tg_status st = TG_OK;
@@ -797,9 +803,10 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
       return TG_OK;
     }
   }
-  if constexpr (sizeof(T) == 8) {
-    if ((p->el == TG_P1_TRI || p->el == TG_P1_TET) && p->elem_scratch && p->E >= kTwoPassMinElems) {
-      // FP64 P1 in two passes: every element's K_e and F_e once, then the rows'
+  {
+    if ((p->el == TG_P1_TRI && two_pass_applies<T, TG_P1_TRI>(p)) ||
+        (p->el == TG_P1_TET && two_pass_applies<T, TG_P1_TET>(p))) {
+      // P1 in two passes: every element's K_e and F_e once, then the rows'
       // and the nodes' sums (the values and orders of the one-pass kernels)
       FwdArgs<T> a = base_args<T>(p, coords);
       a.coef = static_cast<const T*>(kappa);
@@ -811,12 +818,12 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
       a.F = static_cast<T*>(F);
       const bool tri = p->el == TG_P1_TRI;
       const int NS = tri ? 6 : 10;
-      double* rec = static_cast<double*>(p->elem_scratch);
-      double* recF = rec + p->E * NS;
+      T* rec = static_cast<T*>(p->elem_scratch);
+      T* recF = rec + p->E * NS;
       const tg::RefTab<T>& tab = table<T>(p->el);
       const int g1 = (int)std::min<int64_t>(tg::grid_for(p->E, 128), 32ll * tg::sm_count());
-      if (tri) k_p1_map<TG_P1_TRI, true><<<g1, 128, 0, s>>>(a, tab, p->E, rec, recF);
-      else k_p1_map<TG_P1_TET, true><<<g1, 128, 0, s>>>(a, tab, p->E, rec, recF);
+      if (tri) k_p1_map<TG_P1_TRI, T, true><<<g1, 128, 0, s>>>(a, tab, p->E, rec, recF);
+      else k_p1_map<TG_P1_TET, T, true><<<g1, 128, 0, s>>>(a, tab, p->E, rec, recF);
       TG_CK_LAUNCH("k_p1_map<load>");
       a.scr = rec;
       using El3 = tg::Elem<TG_P1_TRI>;
@@ -837,8 +844,8 @@ tg_status system_asm(const tg_pattern* p, const void* coords, const void* kappa,
       if (tri) k_bilinear_gather<TG_P1_TRI, T, true><<<tg::grid_for(p->N, R), R, smem, s>>>(a, tab, cap);
       else k_bilinear_gather<TG_P1_TET, T, true><<<tg::grid_for(p->N, R), R, smem, s>>>(a, tab, cap);
       TG_CK_LAUNCH("k_bilinear_gather<scratch>");
-      if (tri) k_p1_load_reduce<TG_P1_TRI><<<tg::grid_for(p->N, 128), 128, 0, s>>>(a, recF);
-      else k_p1_load_reduce<TG_P1_TET><<<tg::grid_for(p->N, 128), 128, 0, s>>>(a, recF);
+      if (tri) k_p1_load_reduce<TG_P1_TRI, T><<<tg::grid_for(p->N, 128), 128, 0, s>>>(a, recF);
+      else k_p1_load_reduce<TG_P1_TET, T><<<tg::grid_for(p->N, 128), 128, 0, s>>>(a, recF);
       TG_CK_LAUNCH("k_p1_load_reduce");
       return TG_OK;
     }

@@ -387,30 +387,32 @@ def test_fp64_reciprocal_within_one_ulp(tg):
     assert tg.tg_diag_recip(torch.empty(0, dtype=torch.float64, device="cuda")).numel() == 0
 
 
-@pytest.mark.parametrize("el", [mg.P1_TRI, mg.P1_TET])
-def test_fp64_two_pass_forward_and_system(tg, el):
-    """FP64 P1 meshes of at least 65,536 elements are assembled in two passes
-    (every element's K_e and F_e once into the pattern's scratch, then the
-    rows' and nodes' sums): the system equals the separate forward and load
-    calls bitwise, both meet the oracle, and a degenerate element is
-    flagged with zero entries as in one pass."""
+@pytest.mark.parametrize("el,dtype", [(mg.P1_TRI, torch.float64), (mg.P1_TET, torch.float64),
+                                      (mg.P1_TET, torch.float32)])
+def test_two_pass_forward_and_system(tg, el, dtype):
+    """P1 meshes of at least 65,536 elements in FP64, and tetrahedral ones in
+    FP32, are assembled in two passes (every element's K_e and F_e once into
+    the pattern's scratch, then the rows' and nodes' sums): the system equals
+    the separate forward and load calls bitwise, both meet the oracle, and a
+    degenerate element is flagged with zero entries as in one pass."""
     m = jittered_tri(192) if el == mg.P1_TRI else jittered_tet(24)
     assert m.n_elems >= 1 << 16
     k = coef(mg.PER_QP, m.n_elems, mg.NQ[el], seed=91)
     f = np.random.default_rng(92).uniform(-1, 1, m.n_nodes)
     p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, el)
-    x, kd, fd = dev(m.coords, torch.float64), dev(k, torch.float64), dev(f, torch.float64)
+    x, kd, fd = dev(m.coords, dtype), dev(k, dtype), dev(f, dtype)
     vals, F = tg.tg_assemble_system(p, x, kd, mg.PER_QP, 0.4, fd, mg.PER_NODE)
     assert torch.equal(vals, tg.tg_assemble_bilinear(p, x, kd, mg.PER_QP, 0.4))
     assert torch.equal(F, tg.tg_assemble_load(p, x, fd, mg.PER_NODE))
-    ref = O.assemble_bilinear(el, m.cells, m.coords, k, O.PER_QP, 0.4)
-    assert relfro(vals.cpu().numpy(), ref.val) <= 1e-12
-    assert relfro(F.cpu().numpy(), O.assemble_load(el, m.cells, m.coords, f, O.PER_NODE)) <= 1e-12
+    xs, ks, fs = host_as(m.coords, dtype), host_as(k, dtype), host_as(f, dtype)
+    ref = O.assemble_bilinear(el, m.cells, xs, ks, O.PER_QP, 0.4)
+    assert relfro(vals.cpu().numpy(), ref.val) <= TOL[dtype]
+    assert relfro(F.cpu().numpy(), O.assemble_load(el, m.cells, xs, fs, O.PER_NODE)) <= TOL[dtype]
     # a collapsed element: flagged, and it adds nothing
     X = m.coords.copy()
     a, b = m.cells[17][0], m.cells[17][1]
     X[b] = X[a]
-    vals2 = tg.tg_assemble_bilinear(p, dev(X, torch.float64), kd, mg.PER_QP, 0.4)
+    vals2 = tg.tg_assemble_bilinear(p, dev(X, dtype), kd, mg.PER_QP, 0.4)
     st, bad = tg.tg_get_device_status(p)
     assert st != 0 and bad <= 17
     assert torch.isfinite(vals2).all()
