@@ -103,6 +103,191 @@ __global__ void k_cg_p(T* __restrict__ p, const T* __restrict__ r, const double*
 
 __global__ void k_cg_shift(double* sc) { sc[0] = sc[2]; }
 
+// ---------------------------------------------------------------- one-launch CG
+// A barrier across the CTAs of a cooperative launch (all resident) on a
+// 64-bit arrival counter that is 0 when the launch starts: barrier number k
+// completes when the counter reaches k * gridDim.x (release on arrival,
+// acquire on the poll).  Bounded: after about 4M polls a CTA sets *err and
+// gives up; the others give up at their next barrier.
+__device__ __forceinline__ bool grid_sync(unsigned long long* count, unsigned long long& target, int* err) {
+  __syncthreads();
+  int bad = 0;
+  if (threadIdx.x == 0) {
+    target += gridDim.x;
+    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(count) : "memory");
+    for (unsigned int t = 0;; ++t) {
+      unsigned long long v;
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(count) : "memory");
+      if (v >= target) break;
+      if (t > (1u << 22)) {
+        bad = 1;
+        atomicExch(err, 1);
+        break;
+      }
+    }
+  }
+  return __syncthreads_or(bad) == 0;
+}
+
+// Fixed-order tree sum over the CTA (the order of k_dot_partial and
+// k_dot_final); every thread gets the result.
+__device__ __forceinline__ double cta_tree_sum(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = ST / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// The CG iterations of cg() in one cooperative launch.  The dot products of
+// the launch-per-kernel loop reduce over nb partial blocks, thread t of
+// block b summing the entries i = b*ST + t + q*nb*ST (q = 0, 1, ...).  Here
+// that thread owns exactly those rows, for q < KM: it keeps their x, r, p
+// and row bounds in registers and forms their (A p)_i itself, with the four
+// strided partial sums of k_spmv's four lanes added in the lanes' shuffle
+// order, (s0 + s1) + (s2 + s3).  The launch has min(nb, ceil(n/ST)) CTAs
+// (the partials of blocks past the last row are 0).  So A p, p.Ap, the x and
+// r updates and r.r need no exchange, and two grid barriers per iteration
+// remain: after the p.Ap partials and after the r.r partials.  The direction
+// update p = r + beta p is folded into the next product: a column the
+// product reads forms r + beta p_old from the previous iterate (the
+// expression of k_cg_p, so the same bits), and each thread publishes its
+// rows of p_new in the other buffer (p_old / p_new alternate; the first
+// iteration uses p = r as k_cg_init left it) and its rows of r.  Per
+// iteration the sums, their order and the updates are those of the separate
+// kernels, so the iterates are bitwise those of the launch-per-kernel loop.
+// Convergence is checked, as there, after every eighth iteration and at
+// maxit.  pa / pb: the partial arrays of the two dot products (a CTA never
+// overwrites partials another CTA still reads).  Values other CTAs wrote
+// during the launch are read through L2 (__ldcg).  On a barrier timeout
+// *err is set and every CTA leaves (x is then not written).
+template <typename T, int KM>
+__global__ void __launch_bounds__(ST) k_cg_loop(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                const T* __restrict__ vals, const uint8_t* __restrict__ mask, T* x,
+                                                T* r, T* p0, T* p1, int64_t n, int nb, double* sc, double* pa,
+                                                double* pb, unsigned long long* count, double fnorm, double rtol,
+                                                int maxit, int* it_out, int* err) {
+  __shared__ double red[ST];
+  const int64_t G = (int64_t)nb * ST, g0 = (int64_t)blockIdx.x * ST + threadIdx.x;
+  unsigned long long target = 0;
+  if (blockIdx.x == 0)
+    for (int k = (int)gridDim.x + threadIdx.x; k < nb; k += ST) pa[k] = pb[k] = 0.0;
+  bool own[KM], dm[KM];
+  int kb[KM], ke[KM];
+  T xi[KM], ri[KM], pi[KM], api[KM];
+#pragma unroll
+  for (int q = 0; q < KM; ++q) {
+    const int64_t i = g0 + q * G;
+    own[q] = i < n;
+    kb[q] = own[q] ? __ldg(rp + i) : 0;
+    ke[q] = own[q] ? __ldg(rp + i + 1) : 0;
+    dm[q] = own[q] && mask && mask[i];
+    xi[q] = own[q] ? x[i] : T(0);
+    ri[q] = own[q] ? r[i] : T(0);
+    pi[q] = own[q] ? p0[i] : T(0);
+    api[q] = T(0);
+  }
+  double rr = sc[0];
+  T beta = T(0);
+  bool first = true;
+  const T* pold = p0;
+  T* pnew = p1;
+  int it = 0;
+  while (it < maxit) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < KM; ++q) {
+      if (!own[q]) continue;
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+      // p_new at column c: r + beta p_old (p_old itself in the first iteration)
+      for (int k = kb[q]; k < ke[q]; k += 4) {
+        T v[4], pcol[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bool in = k + j < ke[q];
+          const int c = in ? __ldg(ci + k + j) : 0;
+          v[j] = in ? __ldg(vals + k + j) : T(0);
+          const T po = in ? __ldcg(pold + c) : T(0);
+          pcol[j] = first ? po : (in ? __ldcg(r + c) : T(0)) + beta * po;
+        }
+        s0 += v[0] * pcol[0];
+        if (k + 1 < ke[q]) s1 += v[1] * pcol[1];
+        if (k + 2 < ke[q]) s2 += v[2] * pcol[2];
+        if (k + 3 < ke[q]) s3 += v[3] * pcol[3];
+      }
+      api[q] = dm[q] ? T(0) : (s0 + s1) + (s2 + s3);
+      const T pn = first ? pi[q] : ri[q] + beta * pi[q];
+      pi[q] = pn;
+      pnew[g0 + q * G] = pn;
+      s += (double)pn * (double)api[q];
+    }
+    s = cta_tree_sum(s, red);
+    if (threadIdx.x == 0) pa[blockIdx.x] = s;
+    if (!grid_sync(count, target, err)) return;
+    double f = 0.0;
+    for (int k = threadIdx.x; k < nb; k += ST) f += __ldcg(pa + k);
+    const double pAp = cta_tree_sum(f, red);
+    const T alpha = (T)(rr / pAp);
+    double s2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < KM; ++q) {
+      if (!own[q]) continue;
+      xi[q] += alpha * pi[q];
+      ri[q] -= alpha * api[q];
+      r[g0 + q * G] = ri[q];
+      s2 += (double)ri[q] * (double)ri[q];
+    }
+    s2 = cta_tree_sum(s2, red);
+    if (threadIdx.x == 0) pb[blockIdx.x] = s2;
+    if (!grid_sync(count, target, err)) return;
+    double f2 = 0.0;
+    for (int k = threadIdx.x; k < nb; k += ST) f2 += __ldcg(pb + k);
+    const double rr_new = cta_tree_sum(f2, red);
+    beta = (T)(rr_new / rr);
+    rr = rr_new;
+    first = false;
+    T* t = const_cast<T*>(pold);
+    pold = pnew;
+    pnew = t;
+    ++it;
+    if (((it & 7) == 0 || it == maxit) && !(std::sqrt(rr) / fnorm > rtol)) break;
+  }
+#pragma unroll
+  for (int q = 0; q < KM; ++q)
+    if (own[q]) x[g0 + q * G] = xi[q];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc[0] = rr;
+    *it_out = it;
+  }
+}
+
+// Launches the one-launch CG with KM row chunks per thread; false when its
+// CTAs cannot all be resident at once.
+template <typename T, int KM>
+tg_status cg_loop_launch(const int32_t* rp, const int32_t* ci, const T* vals, const uint8_t* mask, T* x, T* r, T* p0,
+                         T* p1, int64_t n, int nb, double* sc, double* pa, double* pb, unsigned int* loop,
+                         double fnorm, double rtol, int maxit, cudaStream_t s, bool* launched) {
+  *launched = false;
+  int per_sm = 0;
+  TG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_loop<T, KM>, ST, 0));
+  const int ncta = (int)std::min<int64_t>((int64_t)nb, (n + ST - 1) / ST);
+  if ((int64_t)per_sm * tg::sm_count() < ncta) return TG_OK;
+  unsigned long long* count = reinterpret_cast<unsigned long long*>(loop);
+  int* it_out = reinterpret_cast<int*>(loop + 2);
+  int* err = reinterpret_cast<int*>(loop + 3);
+  void* args[] = {(void*)&rp,  (void*)&ci,    (void*)&vals,  (void*)&mask, (void*)&x,     (void*)&r,
+                  (void*)&p0,  (void*)&p1,    (void*)&n,     (void*)&nb,   (void*)&sc,    (void*)&pa,
+                  (void*)&pb,  (void*)&count, (void*)&fnorm, (void*)&rtol, (void*)&maxit, (void*)&it_out,
+                  (void*)&err};
+  TG_CK(cudaLaunchCooperativeKernel((const void*)k_cg_loop<T, KM>, dim3(ncta), dim3(ST), args, 0, s));
+  *launched = true;
+  return TG_OK;
+}
+
 struct Dev {
   std::vector<void*> bufs;
   ~Dev() {
@@ -128,8 +313,11 @@ template <typename T>
 struct CgWork {
   T *r, *pp, *Ap, *b;
   double* sc;        // [4]: rr, pAp, rr_new, ||F_I||^2
-  double* partials;  // [nb]
+  double* partials;  // [nb] (the one-launch loop: [2 nb])
   int nb;
+  // the one-launch loop (NULL: launch per kernel): four zeroed words, the
+  // 64-bit barrier arrival count, the iteration count and the error flag
+  unsigned int* loop = nullptr;
 };
 
 // Eight CG iterations captured once as a CUDA graph: the small systems of
@@ -193,6 +381,37 @@ tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8
     return TG_OK;
   };
   int it = 0;
+  if (w.loop && rel > rtol && maxit > 0) {
+    // one cooperative launch for all iterations: up to four row chunks per
+    // thread, and all CTAs resident at once
+    const int64_t chunks = (n + (int64_t)nb * ST - 1) / ((int64_t)nb * ST);
+    bool launched = false;
+    double* pb = partials + nb;
+    T* p1 = b;  // F_I is no longer needed: the second direction buffer
+    if (chunks <= 1)
+      st = cg_loop_launch<T, 1>(rp, ci, vals, mask, x, r, pp, p1, n, nb, sc, partials, pb, w.loop, fnorm, rtol, maxit,
+                                s, &launched);
+    else if (chunks <= 2)
+      st = cg_loop_launch<T, 2>(rp, ci, vals, mask, x, r, pp, p1, n, nb, sc, partials, pb, w.loop, fnorm, rtol, maxit,
+                                s, &launched);
+    else if (chunks <= 4)
+      st = cg_loop_launch<T, 4>(rp, ci, vals, mask, x, r, pp, p1, n, nb, sc, partials, pb, w.loop, fnorm, rtol, maxit,
+                                s, &launched);
+    if (st != TG_OK) return st;
+    if (launched) {
+      int hw[2] = {0, 0};
+      TG_CK(cudaMemcpyAsync(h, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+      TG_CK(cudaMemcpyAsync(hw, w.loop + 2, sizeof(hw), cudaMemcpyDeviceToHost, s));
+      TG_CK(cudaStreamSynchronize(s));
+      if (hw[1]) {
+        tg::set_error("tg_cg_solve: a grid barrier of the one-launch CG timed out");
+        return TG_ERR_TIMEOUT;
+      }
+      if (iters) *iters = hw[0];
+      if (relres) *relres = std::sqrt(h[0]) / fnorm;
+      return TG_OK;
+    }
+  }
   CgGraph g;
   if (use_graph && rel > rtol && maxit >= 8) {
     TG_CK(cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking));
@@ -247,7 +466,9 @@ tg_status cg_alloc(const tg_pattern* p, const void* vals, const void* F, const u
   TG_CK(d.alloc((void**)&w.Ap, n * sizeof(T)));
   TG_CK(d.alloc((void**)&w.b, n * sizeof(T)));
   TG_CK(d.alloc((void**)&w.sc, 4 * sizeof(double)));
-  TG_CK(d.alloc((void**)&w.partials, w.nb * sizeof(double)));
+  TG_CK(d.alloc((void**)&w.partials, 2 * w.nb * sizeof(double)));
+  TG_CK(d.alloc((void**)&w.loop, 4 * sizeof(unsigned int)));
+  TG_CK(cudaMemsetAsync(w.loop, 0, 4 * sizeof(unsigned int), s));
   return cg<T>(p, vals, F, mask, x, rtol, maxit, iters, relres, w, s, true);
 }
 

@@ -168,6 +168,50 @@ def test_cg_poisson_structured_matches_closed_form(tg):
     assert np.linalg.norm(r[inner]) / np.linalg.norm(F.cpu().numpy()[inner]) <= 1e-9
 
 
+def _cg_system(tg, kind, dtype):
+    """Seeded SPD systems for the CG equality checks: a jittered 300x300 P1
+    triangle grid (90,601 rows, more than the 2*SM*256 rows of one pass of
+    the partial-dot grid), a 30^3 P1 tetrahedral grid and a 10^3 P1
+    elasticity grid (3 DoFs per node, one clamped face)."""
+    rng = np.random.default_rng(41)
+    if kind == "elastic":
+        m = mg.kuhn_tet_grid(10)
+        p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TET_VEC3)
+        lam = dev(rng.uniform(0.5, 2.0, m.n_elems), dtype)
+        mu = dev(rng.uniform(0.3, 1.0, m.n_elems), dtype)
+        vals = tg.tg_assemble_elasticity(p, dev(m.coords, dtype), lam, mu, mg.PER_ELEMENT)
+        clamp = np.repeat(m.coords[:, 0] == 0.0, 3).astype(np.uint8)
+        return p, vals, dev(rng.uniform(-1, 1, p.n_rows), dtype), dev(clamp, torch.uint8)
+    m = mg.jitter(mg.tri_grid(300), 5) if kind == "tri" else mg.kuhn_tet_grid(30)
+    el = mg.P1_TRI if kind == "tri" else mg.P1_TET
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, el)
+    k = mg.lognormal((m.n_elems,), 42)
+    vals = tg.tg_assemble_bilinear(p, dev(m.coords, dtype), dev(k, dtype), mg.PER_ELEMENT, 0.1)
+    return p, vals, dev(rng.uniform(-1, 1, m.n_nodes), dtype), dev(m.boundary.astype(np.uint8), torch.uint8)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("kind", ["tri", "tet", "elastic"])
+def test_cg_one_launch_equals_launch_per_kernel_loop(tg, kind, dtype):
+    """tg_cg_solve runs its iterations in one cooperative launch;
+    tg_cg_solve_noalloc keeps one launch per kernel.  Same iterates bit for
+    bit: at convergence, and when maxit (not a multiple of the check period
+    of 8) stops the loop first."""
+    p, vals, F, mask = _cg_system(tg, kind, dtype)
+    rtol = 1e-9 if dtype == torch.float64 else 1e-4
+    full = None
+    for maxit in (100000, 37):
+        x1, it1, rel1 = tg.tg_cg_solve(p, vals, F, mask, rtol=rtol, maxit=maxit)
+        x2, it2, rel2 = tg.tg_cg_solve_noalloc(p, vals, F, mask, rtol=rtol, maxit=maxit)
+        assert (it1, rel1) == (it2, rel2)
+        assert torch.equal(x1, x2)
+        if full is None:
+            full = it1
+            assert 0 < it1 < maxit and rel1 <= rtol
+        else:
+            assert it1 == min(37, full)
+
+
 def test_spmv_and_outer_match_scipy(tg):
     m = mg.jitter(mg.tri_grid(30), 3)
     p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
