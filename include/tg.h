@@ -357,10 +357,13 @@ tg_status tg_scale_masked(tg_dtype dtype, const void* x, const uint8_t* dirichle
  * dirichlet[i] == 0 (uint8 [n_rows], or NULL for none); entries of x on
  * Dirichlet rows are set to 0.  x holds the initial guess on entry.
  * Stops when ||F_I - K_II x_I|| <= rtol ||F_I|| or after maxit iterations.
- * iters / relres are HOST outputs (may be NULL).  SYNCHRONISES the stream
- * (the residual is checked on the host every 8 iterations).  Allocates and
- * frees its work vectors; runs each 8 iterations as one launch of a CUDA
- * graph captured for the call (the same kernels in the same order). */
+ * The residual norm is checked every 8 iterations and at maxit.
+ * iters / relres are HOST outputs (may be NULL).  SYNCHRONISES the stream.
+ * Allocates and frees its work vectors.  Systems of up to 8 x (SM count) x
+ * 256 rows run all iterations in one cooperative launch when its CTAs can
+ * be resident together (bounded grid barriers: TG_ERR_TIMEOUT if one runs
+ * out); otherwise each 8 iterations run as one launch of a CUDA graph
+ * captured for the call.  Both forms give the iterates bit for bit. */
 tg_status tg_cg_solve(const tg_pattern* p, tg_dtype dtype, const void* vals, const void* F,
                       const uint8_t* dirichlet, void* x, double rtol, int32_t maxit, int32_t* iters,
                       double* relres, tg_stream stream);

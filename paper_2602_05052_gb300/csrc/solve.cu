@@ -461,13 +461,20 @@ tg_status cg_alloc(const tg_pattern* p, const void* vals, const void* F, const u
   Dev d;
   CgWork<T> w;
   w.nb = cg_partials();
-  TG_CK(d.alloc((void**)&w.r, n * sizeof(T)));
-  TG_CK(d.alloc((void**)&w.pp, n * sizeof(T)));
-  TG_CK(d.alloc((void**)&w.Ap, n * sizeof(T)));
-  TG_CK(d.alloc((void**)&w.b, n * sizeof(T)));
-  TG_CK(d.alloc((void**)&w.sc, 4 * sizeof(double)));
-  TG_CK(d.alloc((void**)&w.partials, 2 * w.nb * sizeof(double)));
-  TG_CK(d.alloc((void**)&w.loop, 4 * sizeof(unsigned int)));
+  // one allocation: scalars, barrier words and partials, then the four work
+  // vectors, each rounded up to 256 bytes
+  const size_t head = 16384, vb = ((size_t)n * sizeof(T) + 255) / 256 * 256;
+  static_assert(4 * sizeof(double) + 4 * sizeof(unsigned int) + 2 * kMaxPartials * sizeof(double) <= 16384,
+                "CG head");
+  unsigned char* base = nullptr;
+  TG_CK(d.alloc((void**)&base, head + 4 * vb));
+  w.sc = reinterpret_cast<double*>(base);
+  w.loop = reinterpret_cast<unsigned int*>(base + 4 * sizeof(double));
+  w.partials = reinterpret_cast<double*>(base + 64);
+  w.r = reinterpret_cast<T*>(base + head);
+  w.pp = reinterpret_cast<T*>(base + head + vb);
+  w.Ap = reinterpret_cast<T*>(base + head + 2 * vb);
+  w.b = reinterpret_cast<T*>(base + head + 3 * vb);
   TG_CK(cudaMemsetAsync(w.loop, 0, 4 * sizeof(unsigned int), s));
   return cg<T>(p, vals, F, mask, x, rtol, maxit, iters, relres, w, s, true);
 }
