@@ -129,18 +129,28 @@ __device__ __forceinline__ bool grid_sync(unsigned long long* count, unsigned lo
   return __syncthreads_or(bad) == 0;
 }
 
-// Fixed-order tree sum over the CTA (the order of k_dot_partial and
-// k_dot_final); every thread gets the result.
+// The tree sum of k_dot_partial and k_dot_final over the CTA's 256 values
+// (level w adds value t + w to value t, w = 128, 64, ..., 1), every thread
+// getting the result.  One warp evaluates it: each lane adds its four pairs
+// of level 128 and carries them through levels 64 and 32 in registers, and
+// shuffles take levels 16 to 1.  The pairs and their order are the tree's,
+// so the sum carries its bits, with two CTA barriers instead of ten (the
+// FP64 additions are slow on this GPU; the barrier per level cost more).
 __device__ __forceinline__ double cta_tree_sum(double v, double* red) {
+  static_assert(ST == 256, "the tree below has eight levels");
   red[threadIdx.x] = v;
   __syncthreads();
-  for (int w = ST / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
+  if (threadIdx.x < 32) {
+    const int l = threadIdx.x;
+    const double a0 = red[l] + red[l + 128], a1 = red[l + 32] + red[l + 160];
+    const double a2 = red[l + 64] + red[l + 192], a3 = red[l + 96] + red[l + 224];
+    double c = (a0 + a2) + (a1 + a3);
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) c += __shfl_down_sync(0xffffffffu, c, w);
+    if (l == 0) red[ST] = c;
   }
-  const double r = red[0];
   __syncthreads();
-  return r;
+  return red[ST];
 }
 
 // The CG iterations of cg() in one cooperative launch.  The dot products of
@@ -171,7 +181,7 @@ __global__ void __launch_bounds__(ST) k_cg_loop(const int32_t* __restrict__ rp, 
                                                 T* r, T* p0, T* p1, int64_t n, int nb, double* sc, double* pa,
                                                 double* pb, unsigned long long* count, double fnorm, double rtol,
                                                 int maxit, int* it_out, int* err) {
-  __shared__ double red[ST];
+  __shared__ double red[ST + 1];
   const int64_t G = (int64_t)nb * ST, g0 = (int64_t)blockIdx.x * ST + threadIdx.x;
   unsigned long long target = 0;
   if (blockIdx.x == 0)
@@ -203,11 +213,13 @@ __global__ void __launch_bounds__(ST) k_cg_loop(const int32_t* __restrict__ rp, 
     for (int q = 0; q < KM; ++q) {
       if (!own[q]) continue;
       T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-      // p_new at column c: r + beta p_old (p_old itself in the first iteration)
-      for (int k = kb[q]; k < ke[q]; k += 4) {
-        T v[4], pcol[4];
+      // p_new at column c: r + beta p_old (p_old itself in the first
+      // iteration); eight entries' loads in flight at once, partial sum
+      // k mod 4 taking entries in increasing order
+      for (int k = kb[q]; k < ke[q]; k += 8) {
+        T v[8], pcol[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < 8; ++j) {
           const bool in = k + j < ke[q];
           const int c = in ? __ldg(ci + k + j) : 0;
           v[j] = in ? __ldg(vals + k + j) : T(0);
@@ -218,6 +230,10 @@ __global__ void __launch_bounds__(ST) k_cg_loop(const int32_t* __restrict__ rp, 
         if (k + 1 < ke[q]) s1 += v[1] * pcol[1];
         if (k + 2 < ke[q]) s2 += v[2] * pcol[2];
         if (k + 3 < ke[q]) s3 += v[3] * pcol[3];
+        if (k + 4 < ke[q]) s0 += v[4] * pcol[4];
+        if (k + 5 < ke[q]) s1 += v[5] * pcol[5];
+        if (k + 6 < ke[q]) s2 += v[6] * pcol[6];
+        if (k + 7 < ke[q]) s3 += v[7] * pcol[7];
       }
       api[q] = dm[q] ? T(0) : (s0 + s1) + (s2 + s3);
       const T pn = first ? pi[q] : ri[q] + beta * pi[q];
