@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / elasticity / batched breakdown")
-    ap.add_argument("--extras-only", choices=["diffusion", "residual", "facets", "batch", "elasticity"], default=None,
+    ap.add_argument("--extras-only", choices=["diffusion", "residual", "facets", "batch", "elasticity", "small"],
+                    default=None,
                     help="run only this part of the breakdown (short runs, e.g. for profiling one kernel)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -502,6 +503,8 @@ def main():
             out["breakdown"] = facet_extras(tg, torch, dev, m, p, flush)
         elif args.extras_only == "elasticity":
             out["breakdown"] = elasticity_extras(tg, torch, dev, peak, flush)
+        elif args.extras_only == "small":
+            out["breakdown"] = small_configs(tg, torch, dev)
         else:
             out["breakdown"] = batch_extras(tg, torch, dev, peak, flush)
     elif not args.no_extras and rank == 0:
