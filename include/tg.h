@@ -527,6 +527,15 @@ tg_status tg_diag_recip(const double* x, double* y, int64_t n, tg_stream stream)
  * faults. */
 tg_status tg_diag_wait_timeout(const tg_pattern* p, int32_t max_tries, tg_stream stream);
 
+/* Failure-path check of the grid barrier of tg_cg_solve's one-launch loop
+ * (no counterpart in the paper): a cooperative launch of two CTAs in which
+ * one leaves without arriving, so the barrier never completes; the other
+ * polls at most max_polls times (1 .. 2^22, the CG's own limit), gives up,
+ * and the call returns TG_ERR_TIMEOUT, as tg_cg_solve does when its barrier
+ * gives up.  Nothing hangs or faults.  Synchronises the stream; allocates 16
+ * bytes of device memory for the call. */
+tg_status tg_diag_grid_barrier_timeout(int32_t max_polls, tg_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,7 +12,7 @@ from .binding import (CONSTANT, DIM, F32, F64, LAYOUT_EDGE_MASKS, LAYOUT_ELEM_PO
                       tg_assemble_load, tg_assemble_load_backward, tg_assemble_system, tg_batch_assemble,
                       tg_batch_autotune, tg_batch_create, tg_batch_set_schedule, tg_build_pattern, tg_cg_solve, tg_cg_solve_noalloc,
                       tg_csr_outer, tg_scale_masked,
-                      tg_diag_fma_rate, tg_diag_recip, tg_diag_wait_timeout, tg_reaction_points, tg_residual, tg_semilinear_residual, tg_get_device_status, tg_quadrature, tg_spmv)
+                      tg_diag_fma_rate, tg_diag_grid_barrier_timeout, tg_diag_recip, tg_diag_wait_timeout, tg_reaction_points, tg_residual, tg_semilinear_residual, tg_get_device_status, tg_quadrature, tg_spmv)
 
 __all__ = [n for n in dir() if n.startswith("tg_")] + [
     "Pattern", "Batch", "Facets", "TGError", "lib", "P1_TRI", "P2_TRI", "P1_TET", "P1_TET_VEC3", "Q1_QUAD_VEC2", "PER_ELEMENT", "PER_QP",

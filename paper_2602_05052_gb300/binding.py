@@ -74,6 +74,7 @@ def lib():
         "tg_simp_sensitivity": (i32, [vp, i32, vp, vp, dbl, dbl, dbl, dbl, vp, vp, vp]),
         "tg_reaction_points": (i32, [vp, i32, vp, C.POINTER(dbl), vp, vp]),
         "tg_diag_wait_timeout": (i32, [vp, i32, vp]),
+        "tg_diag_grid_barrier_timeout": (i32, [i32, vp]),
         "tg_build_facets": (i32, [vp, vp, i64, vp, C.POINTER(vp)]),
         "tg_assemble_facets": (i32, [vp, i32, vp, vp, i32, vp, i32, vp, vp, vp]),
         "tg_facets_shape": (i32, [vp, C.POINTER(i64), C.POINTER(i64)]),
@@ -432,6 +433,12 @@ def tg_reaction_points(p: Pattern, x, reaction, out=None, stream=None):
 
 def tg_diag_wait_timeout(p: Pattern, max_tries: int = 1000, stream=None):
     _check(lib().tg_diag_wait_timeout(p.handle, int(max_tries), _stream(stream)), "tg_diag_wait_timeout")
+
+
+def tg_diag_grid_barrier_timeout(max_polls: int = 1000, stream=None) -> int:
+    """Runs the grid-barrier failure check and returns its status code
+    (TG_ERR_TIMEOUT = 7 when the barrier gave up, as it should)."""
+    return int(lib().tg_diag_grid_barrier_timeout(int(max_polls), _stream(stream)))
 
 
 class Facets:

@@ -107,9 +107,11 @@ __global__ void k_cg_shift(double* sc) { sc[0] = sc[2]; }
 // A barrier across the CTAs of a cooperative launch (all resident) on a
 // 64-bit arrival counter that is 0 when the launch starts: barrier number k
 // completes when the counter reaches k * gridDim.x (release on arrival,
-// acquire on the poll).  Bounded: after about 4M polls a CTA sets *err and
-// gives up; the others give up at their next barrier.
-__device__ __forceinline__ bool grid_sync(unsigned long long* count, unsigned long long& target, int* err) {
+// acquire on the poll).  Bounded: after `limit` polls (the CG takes 2^22) a
+// CTA sets *err and gives up; the others give up at their next barrier.
+constexpr unsigned int kGridPolls = 1u << 22;
+__device__ __forceinline__ bool grid_sync(unsigned long long* count, unsigned long long& target, int* err,
+                                          unsigned int limit = kGridPolls) {
   __syncthreads();
   int bad = 0;
   if (threadIdx.x == 0) {
@@ -119,7 +121,7 @@ __device__ __forceinline__ bool grid_sync(unsigned long long* count, unsigned lo
       unsigned long long v;
       asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(count) : "memory");
       if (v >= target) break;
-      if (t > (1u << 22)) {
+      if (t >= limit) {
         bad = 1;
         atomicExch(err, 1);
         break;
@@ -733,6 +735,14 @@ __global__ void k_diag_wait_timeout(unsigned long long* status, uint32_t max_tri
   if (__syncthreads_or(!ok) && threadIdx.x == 0) tg::record_error(status, TG_ERR_TIMEOUT, 0);
 }
 
+// A grid barrier that never completes: CTA 1 leaves without arriving, CTA 0
+// waits at most `limit` polls and gives up (err = 1).
+__global__ void k_diag_grid_barrier(unsigned long long* count, int* err, unsigned int limit) {
+  if (blockIdx.x != 0) return;
+  unsigned long long target = 0;
+  grid_sync(count, target, err, limit);
+}
+
 // y[i] = the FP64 reciprocal the P1 forward takes of |det J|.
 __global__ void k_diag_recip(const double* __restrict__ x, double* __restrict__ y, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -755,6 +765,28 @@ tg_status tg_diag_wait_timeout(const tg_pattern* p, int32_t max_tries, tg_stream
   if (!p || max_tries < 1 || max_tries > (1 << 22)) return TG_ERR_INVALID_ARG;
   k_diag_wait_timeout<<<1, 32, 0, (cudaStream_t)stream>>>(p->status, (uint32_t)max_tries);
   TG_CK_LAUNCH("k_diag_wait_timeout");
+  return TG_OK;
+}
+
+tg_status tg_diag_grid_barrier_timeout(int32_t max_polls, tg_stream stream) {
+  if (max_polls < 1 || max_polls > (int32_t)kGridPolls) return TG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Dev d;
+  unsigned char* w = nullptr;
+  TG_CK(d.alloc((void**)&w, 16));
+  TG_CK(cudaMemsetAsync(w, 0, 16, s));
+  unsigned long long* count = reinterpret_cast<unsigned long long*>(w);
+  int* err = reinterpret_cast<int*>(w + 8);
+  unsigned int limit = (unsigned int)max_polls;
+  void* args[] = {(void*)&count, (void*)&err, (void*)&limit};
+  TG_CK(cudaLaunchCooperativeKernel((const void*)k_diag_grid_barrier, dim3(2), dim3(ST), args, 0, s));
+  int he = 0;
+  TG_CK(cudaMemcpyAsync(&he, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  if (he) {
+    tg::set_error("tg_diag_grid_barrier_timeout: the grid barrier gave up, as intended");
+    return TG_ERR_TIMEOUT;
+  }
   return TG_OK;
 }
 

@@ -85,6 +85,9 @@ def test_host_validation_without_gpu(L):
     assert L.tg_batch_create(None, 0, C.byref(out)) == 1
     L.tg_diag_fma_rate.argtypes = [C.c_int32, vp, vp]
     assert L.tg_diag_fma_rate(1, None, None) == 1
+    L.tg_diag_grid_barrier_timeout.argtypes = [C.c_int32, vp]
+    assert L.tg_diag_grid_barrier_timeout(0, None) == 1
+    assert L.tg_diag_grid_barrier_timeout((1 << 22) + 1, None) == 1
     L.tg_cg_solve.argtypes = [vp, C.c_int32, vp, vp, vp, vp, C.c_double, C.c_int32, vp, vp, vp]
     assert L.tg_cg_solve(None, 1, None, None, None, None, 1e-10, 10, None, None, None) == 1
     L.tg_residual.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, C.c_double, vp, vp, C.c_int32, vp, vp, vp, vp]
