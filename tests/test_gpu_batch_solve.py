@@ -171,8 +171,10 @@ def test_cg_poisson_structured_matches_closed_form(tg):
 def _cg_system(tg, kind, dtype):
     """Seeded SPD systems for the CG equality checks: a jittered 300x300 P1
     triangle grid (90,601 rows, more than the 2*SM*256 rows of one pass of
-    the partial-dot grid), a 30^3 P1 tetrahedral grid and a 10^3 P1
-    elasticity grid (3 DoFs per node, one clamped face)."""
+    the partial-dot grid), a 30^3 P1 tetrahedral grid, a 10^3 P1
+    elasticity grid (3 DoFs per node, one clamped face) and a 640x640 P1
+    triangle grid (410,881 rows, which tg_cg_solve runs as graph-captured
+    launches)."""
     rng = np.random.default_rng(41)
     if kind == "elastic":
         m = mg.kuhn_tet_grid(10)
@@ -182,8 +184,11 @@ def _cg_system(tg, kind, dtype):
         vals = tg.tg_assemble_elasticity(p, dev(m.coords, dtype), lam, mu, mg.PER_ELEMENT)
         clamp = np.repeat(m.coords[:, 0] == 0.0, 3).astype(np.uint8)
         return p, vals, dev(rng.uniform(-1, 1, p.n_rows), dtype), dev(clamp, torch.uint8)
-    m = mg.jitter(mg.tri_grid(300), 5) if kind == "tri" else mg.kuhn_tet_grid(30)
-    el = mg.P1_TRI if kind == "tri" else mg.P1_TET
+    if kind == "big":  # 410,881 rows: past the one-launch loop's four rows per thread
+        m = mg.tri_grid(640)
+    else:
+        m = mg.jitter(mg.tri_grid(300), 5) if kind == "tri" else mg.kuhn_tet_grid(30)
+    el = mg.P1_TET if kind == "tet" else mg.P1_TRI
     p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, el)
     k = mg.lognormal((m.n_elems,), 42)
     vals = tg.tg_assemble_bilinear(p, dev(m.coords, dtype), dev(k, dtype), mg.PER_ELEMENT, 0.1)
@@ -191,12 +196,12 @@ def _cg_system(tg, kind, dtype):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("kind", ["tri", "tet", "elastic"])
+@pytest.mark.parametrize("kind", ["tri", "tet", "elastic", "big"])
 def test_cg_one_launch_equals_launch_per_kernel_loop(tg, kind, dtype):
-    """tg_cg_solve runs its iterations in one cooperative launch;
-    tg_cg_solve_noalloc keeps one launch per kernel.  Same iterates bit for
-    bit: at convergence, and when maxit (not a multiple of the check period
-    of 8) stops the loop first."""
+    """tg_cg_solve runs its iterations in one cooperative launch (on the
+    largest system: 8-iteration CUDA graphs); tg_cg_solve_noalloc keeps one
+    launch per kernel.  Same iterates bit for bit: at convergence, and when
+    maxit (not a multiple of the check period of 8) stops the loop first."""
     p, vals, F, mask = _cg_system(tg, kind, dtype)
     rtol = 1e-9 if dtype == torch.float64 else 1e-4
     full = None
