@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "async.cuh"
@@ -110,6 +111,11 @@ __global__ void k_cg_shift(double* sc) { sc[0] = sc[2]; }
 // acquire on the poll).  Bounded: after `limit` polls (the CG takes 2^22) a
 // CTA sets *err and gives up; the others give up at their next barrier.
 constexpr unsigned int kGridPolls = 1u << 22;
+// FP64 systems with at least this many matrix entries take the one-launch
+// CG's three-barrier form: the second read and the FP64 FMA per entry cost
+// more than the third barrier there (48^3 tetrahedral system, 1.76M
+// entries: 27 instead of 34 us per iteration).
+constexpr int64_t kCgP3MinEntries = int64_t(1) << 19;
 __device__ __forceinline__ bool grid_sync(unsigned long long* count, unsigned long long& target, int* err,
                                           unsigned int limit = kGridPolls) {
   __syncthreads();
@@ -177,7 +183,12 @@ __device__ __forceinline__ double cta_tree_sum(double v, double* red) {
 // overwrites partials another CTA still reads).  Values other CTAs wrote
 // during the launch are read through L2 (__ldcg).  On a barrier timeout
 // *err is set and every CTA leaves (x is then not written).
-template <typename T, int KM>
+// P3 (FP64 systems with many entries): forming r + beta p_old per entry read
+// costs a second L2 read and an FP64 FMA per matrix entry, more than a third
+// grid barrier; each thread then updates its rows of p in p0 first, a
+// barrier follows, and the product reads p itself (the same values, so the
+// same bits).
+template <typename T, int KM, bool P3>
 __global__ void __launch_bounds__(ST) k_cg_loop(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                                 const T* __restrict__ vals, const uint8_t* __restrict__ mask, T* x,
                                                 T* r, T* p0, T* p1, int64_t n, int nb, double* sc, double* pa,
@@ -210,6 +221,17 @@ __global__ void __launch_bounds__(ST) k_cg_loop(const int32_t* __restrict__ rp, 
   T* pnew = p1;
   int it = 0;
   while (it < maxit) {
+    if constexpr (P3) {
+      if (!first) {
+#pragma unroll
+        for (int q = 0; q < KM; ++q) {
+          if (!own[q]) continue;
+          pi[q] = ri[q] + beta * pi[q];
+          p0[g0 + q * G] = pi[q];
+        }
+        if (!grid_sync(count, target, err)) return;
+      }
+    }
     double s = 0.0;
 #pragma unroll
     for (int q = 0; q < KM; ++q) {
@@ -226,7 +248,7 @@ __global__ void __launch_bounds__(ST) k_cg_loop(const int32_t* __restrict__ rp, 
           const int c = in ? __ldg(ci + k + j) : 0;
           v[j] = in ? __ldg(vals + k + j) : T(0);
           const T po = in ? __ldcg(pold + c) : T(0);
-          pcol[j] = first ? po : (in ? __ldcg(r + c) : T(0)) + beta * po;
+          pcol[j] = (P3 || first) ? po : (in ? __ldcg(r + c) : T(0)) + beta * po;
         }
         s0 += v[0] * pcol[0];
         if (k + 1 < ke[q]) s1 += v[1] * pcol[1];
@@ -238,10 +260,12 @@ __global__ void __launch_bounds__(ST) k_cg_loop(const int32_t* __restrict__ rp, 
         if (k + 7 < ke[q]) s3 += v[7] * pcol[7];
       }
       api[q] = dm[q] ? T(0) : (s0 + s1) + (s2 + s3);
-      const T pn = first ? pi[q] : ri[q] + beta * pi[q];
-      pi[q] = pn;
-      pnew[g0 + q * G] = pn;
-      s += (double)pn * (double)api[q];
+      if constexpr (!P3) {
+        const T pn = first ? pi[q] : ri[q] + beta * pi[q];
+        pi[q] = pn;
+        pnew[g0 + q * G] = pn;
+      }
+      s += (double)pi[q] * (double)api[q];
     }
     s = cta_tree_sum(s, red);
     if (threadIdx.x == 0) pa[blockIdx.x] = s;
@@ -268,9 +292,11 @@ __global__ void __launch_bounds__(ST) k_cg_loop(const int32_t* __restrict__ rp, 
     beta = (T)(rr_new / rr);
     rr = rr_new;
     first = false;
-    T* t = const_cast<T*>(pold);
-    pold = pnew;
-    pnew = t;
+    if constexpr (!P3) {
+      T* t = const_cast<T*>(pold);
+      pold = pnew;
+      pnew = t;
+    }
     ++it;
     if (((it & 7) == 0 || it == maxit) && !(std::sqrt(rr) / fnorm > rtol)) break;
   }
@@ -285,13 +311,13 @@ __global__ void __launch_bounds__(ST) k_cg_loop(const int32_t* __restrict__ rp, 
 
 // Launches the one-launch CG with KM row chunks per thread; false when its
 // CTAs cannot all be resident at once.
-template <typename T, int KM>
+template <typename T, int KM, bool P3>
 tg_status cg_loop_launch(const int32_t* rp, const int32_t* ci, const T* vals, const uint8_t* mask, T* x, T* r, T* p0,
                          T* p1, int64_t n, int nb, double* sc, double* pa, double* pb, unsigned int* loop,
                          double fnorm, double rtol, int maxit, cudaStream_t s, bool* launched) {
   *launched = false;
   int per_sm = 0;
-  TG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_loop<T, KM>, ST, 0));
+  TG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_loop<T, KM, P3>, ST, 0));
   const int ncta = (int)std::min<int64_t>((int64_t)nb, (n + ST - 1) / ST);
   if ((int64_t)per_sm * tg::sm_count() < ncta) return TG_OK;
   unsigned long long* count = reinterpret_cast<unsigned long long*>(loop);
@@ -301,7 +327,7 @@ tg_status cg_loop_launch(const int32_t* rp, const int32_t* ci, const T* vals, co
                   (void*)&p0,  (void*)&p1,    (void*)&n,     (void*)&nb,   (void*)&sc,    (void*)&pa,
                   (void*)&pb,  (void*)&count, (void*)&fnorm, (void*)&rtol, (void*)&maxit, (void*)&it_out,
                   (void*)&err};
-  TG_CK(cudaLaunchCooperativeKernel((const void*)k_cg_loop<T, KM>, dim3(ncta), dim3(ST), args, 0, s));
+  TG_CK(cudaLaunchCooperativeKernel((const void*)k_cg_loop<T, KM, P3>, dim3(ncta), dim3(ST), args, 0, s));
   *launched = true;
   return TG_OK;
 }
@@ -406,15 +432,22 @@ tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8
     bool launched = false;
     double* pb = partials + nb;
     T* p1 = b;  // F_I is no longer needed: the second direction buffer
-    if (chunks <= 1)
-      st = cg_loop_launch<T, 1>(rp, ci, vals, mask, x, r, pp, p1, n, nb, sc, partials, pb, w.loop, fnorm, rtol, maxit,
-                                s, &launched);
-    else if (chunks <= 2)
-      st = cg_loop_launch<T, 2>(rp, ci, vals, mask, x, r, pp, p1, n, nb, sc, partials, pb, w.loop, fnorm, rtol, maxit,
-                                s, &launched);
-    else if (chunks <= 4)
-      st = cg_loop_launch<T, 4>(rp, ci, vals, mask, x, r, pp, p1, n, nb, sc, partials, pb, w.loop, fnorm, rtol, maxit,
-                                s, &launched);
+    // FP64 systems of at least kCgP3MinEntries matrix entries: the variant
+    // with a third barrier (the FP64 FMA per entry read costs more)
+    bool p3 = false;
+    if constexpr (sizeof(T) == 8) p3 = (int64_t)nc * nc * p->nnz >= kCgP3MinEntries;
+    auto launch = [&](auto km, auto p3c) {
+      return cg_loop_launch<T, decltype(km)::value, decltype(p3c)::value>(
+          rp, ci, vals, mask, x, r, pp, p1, n, nb, sc, partials, pb, w.loop, fnorm, rtol, maxit, s, &launched);
+    };
+    using K1 = std::integral_constant<int, 1>;
+    using K2 = std::integral_constant<int, 2>;
+    using K4 = std::integral_constant<int, 4>;
+    using P2 = std::false_type;
+    using P3 = std::integral_constant<bool, sizeof(T) == 8>;  // no FP32 instance of the P3 form
+    if (chunks <= 1) st = p3 ? launch(K1{}, P3{}) : launch(K1{}, P2{});
+    else if (chunks <= 2) st = p3 ? launch(K2{}, P3{}) : launch(K2{}, P2{});
+    else if (chunks <= 4) st = p3 ? launch(K4{}, P3{}) : launch(K4{}, P2{});
     if (st != TG_OK) return st;
     if (launched) {
       int hw[2] = {0, 0};
