@@ -309,8 +309,9 @@ __global__ void __launch_bounds__(ST) k_cg_loop(const int32_t* __restrict__ rp, 
   }
 }
 
-// Launches the one-launch CG with KM row chunks per thread; false when its
-// CTAs cannot all be resident at once.
+// Launches the one-launch CG with KM row chunks per thread; *launched stays
+// false when its CTAs cannot all be resident at once (by the occupancy query,
+// or when the launch itself reports too few SMs).
 template <typename T, int KM, bool P3>
 tg_status cg_loop_launch(const int32_t* rp, const int32_t* ci, const T* vals, const uint8_t* mask, T* x, T* r, T* p0,
                          T* p1, int64_t n, int nb, double* sc, double* pa, double* pb, unsigned int* loop,
@@ -327,7 +328,13 @@ tg_status cg_loop_launch(const int32_t* rp, const int32_t* ci, const T* vals, co
                   (void*)&p0,  (void*)&p1,    (void*)&n,     (void*)&nb,   (void*)&sc,    (void*)&pa,
                   (void*)&pb,  (void*)&count, (void*)&fnorm, (void*)&rtol, (void*)&maxit, (void*)&it_out,
                   (void*)&err};
-  TG_CK(cudaLaunchCooperativeKernel((const void*)k_cg_loop<T, KM, P3>, dim3(ncta), dim3(ST), args, 0, s));
+  const cudaError_t e =
+      cudaLaunchCooperativeKernel((const void*)k_cg_loop<T, KM, P3>, dim3(ncta), dim3(ST), args, 0, s);
+  if (e == cudaErrorCooperativeLaunchTooLarge) {
+    (void)cudaGetLastError();  // fewer SMs than the occupancy query saw: the graph-captured loop serves
+    return TG_OK;
+  }
+  TG_CK(e);
   *launched = true;
   return TG_OK;
 }
