@@ -611,7 +611,9 @@ __device__ __forceinline__ void bwd_blk_map(const BwdArgs<T>& a, const tg::RefTa
           }
       }
 #pragma unroll
-      for (int c = 0; c < NV; ++c) gx_store<D>(Gx, capE, c, j, gx[c]);
+      for (int c = 0; c < NV; ++c)
+#pragma unroll
+        for (int r = 0; r < D; ++r) gx_store<D>(Gx, capE, c, j, gx[c]);
     }
   }
 }
