@@ -355,7 +355,8 @@ tg_status tg_scale_masked(tg_dtype dtype, const void* x, const uint8_t* dirichle
 
 /* Conjugate gradients on K x = F restricted to the rows/columns where
  * dirichlet[i] == 0 (uint8 [n_rows], or NULL for none); entries of x on
- * Dirichlet rows are set to 0.  x holds the initial guess on entry.
+ * Dirichlet rows are set to 0.  x holds the initial guess on entry (its
+ * Dirichlet entries are set to 0 before the initial residual is formed).
  * Stops when ||F_I - K_II x_I|| <= rtol ||F_I|| or after maxit iterations.
  * The residual norm is checked every 8 iterations and at maxit.
  * iters / relres are HOST outputs (may be NULL).  SYNCHRONISES the stream.

@@ -68,6 +68,14 @@ __global__ void __launch_bounds__(ST) k_dot_final(const double* __restrict__ par
   if (threadIdx.x == 0) *out = red[0];
 }
 
+// x = 0 on the rows the condensed system drops, before the initial residual
+// F - K x is formed: an initial guess's values there must not enter it.
+template <typename T>
+__global__ void k_cg_zero_masked(T* __restrict__ x, const uint8_t* __restrict__ mask, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * ST + threadIdx.x;
+  if (i < n && mask[i]) x[i] = T(0);
+}
+
 // r = mask ? 0 : F - Kx ;  b = mask ? 0 : F ;  x = mask ? 0 : x ;  p = r
 template <typename T>
 __global__ void k_cg_init(const T* __restrict__ F, const T* __restrict__ Kx, const uint8_t* __restrict__ mask,
@@ -401,6 +409,7 @@ tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8
   double *sc = w.sc, *partials = w.partials;
   const int nb = w.nb;
   const int gv = tg::grid_for(n, ST), gs = tg::grid_for(4 * n, ST);
+  if (mask) k_cg_zero_masked<T><<<gv, ST, 0, s>>>(x, mask, n);
   k_spmv<T><<<gs, ST, 0, s>>>(rp, ci, vals, x, Ap, n, mask);
   k_cg_init<T><<<gv, ST, 0, s>>>(F, Ap, mask, x, r, pp, b, n);
   TG_CK_LAUNCH("cg init");

@@ -217,6 +217,36 @@ def test_cg_one_launch_equals_launch_per_kernel_loop(tg, kind, dtype):
             assert it1 == min(37, full)
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_cg_initial_guess_and_zero_load(tg, dtype):
+    """A nonzero initial guess: both forms give the same iterates bit for bit
+    and the true residual of the condensed system meets the tolerance.  A
+    zero load: the solution of K_II x_I = 0 is x = 0 whatever the guess, with
+    no iteration and relres 0."""
+    m = mg.jitter(mg.tri_grid(40), 7)
+    p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
+    k = np.random.default_rng(8).uniform(0.5, 2.0, m.n_elems)
+    vals = tg.tg_assemble_bilinear(p, dev(m.coords, dtype), dev(k, dtype), mg.PER_ELEMENT, 0.1)
+    F = dev(np.random.default_rng(9).uniform(-1, 1, m.n_nodes), dtype)
+    mask = dev(m.boundary.astype(np.uint8), torch.uint8)
+    x0 = dev(np.random.default_rng(10).normal(size=m.n_nodes), dtype)
+    rtol = 1e-10 if dtype == torch.float64 else 1e-4
+    x1, it1, rel1 = tg.tg_cg_solve(p, vals, F, mask, x=x0.clone(), rtol=rtol)
+    x2, it2, rel2 = tg.tg_cg_solve_noalloc(p, vals, F, mask, x=x0.clone(), rtol=rtol)
+    assert (it1, rel1) == (it2, rel2) and torch.equal(x1, x2)
+    assert 0 < it1 and rel1 <= rtol
+    xs = x1.double().cpu().numpy()
+    inner = ~m.boundary
+    assert np.all(xs[m.boundary] == 0)
+    r = tg.tg_spmv(p, vals.double(), x1.double()).cpu().numpy() - F.double().cpu().numpy()
+    assert np.linalg.norm(r[inner]) / np.linalg.norm(F.double().cpu().numpy()[inner]) <= 100 * rtol
+    zero = torch.zeros_like(F)
+    for solve in (tg.tg_cg_solve, tg.tg_cg_solve_noalloc):
+        x, it, rel = solve(p, vals, zero, mask, x=x0.clone(), rtol=rtol)
+        assert it == 0 and rel == 0.0
+        assert torch.count_nonzero(x).item() == 0
+
+
 def test_spmv_and_outer_match_scipy(tg):
     m = mg.jitter(mg.tri_grid(30), 3)
     p = tg.tg_build_pattern(dev(m.cells, torch.int32), m.n_nodes, mg.P1_TRI)
