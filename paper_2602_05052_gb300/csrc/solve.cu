@@ -408,6 +408,11 @@ tg_status cg(const tg_pattern* p, const void* vals_, const void* F_, const uint8
   T *r = w.r, *pp = w.pp, *Ap = w.Ap, *b = w.b;
   double *sc = w.sc, *partials = w.partials;
   const int nb = w.nb;
+  if (n == 0) {  // no rows: nothing to solve (and no launch of zero CTAs)
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return TG_OK;
+  }
   const int gv = tg::grid_for(n, ST), gs = tg::grid_for(4 * n, ST);
   if (mask) k_cg_zero_masked<T><<<gv, ST, 0, s>>>(x, mask, n);
   k_spmv<T><<<gs, ST, 0, s>>>(rp, ci, vals, x, Ap, n, mask);
