@@ -335,12 +335,14 @@ tg_status tg_assemble_load_backward(const tg_pattern* p, tg_dtype dtype, const v
  * system (SM B.1 solver configuration; used by the adjoint of Eq. (adj)).
  * ---------------------------------------------------------------------- */
 
-/* y = K x over the pattern's CSR (DoF level for elasticity). */
+/* y = K x over the pattern's CSR (DoF level for elasticity).  A pattern
+ * with no rows does nothing; vals may be NULL when it has no entries. */
 tg_status tg_spmv(const tg_pattern* p, tg_dtype dtype, const void* vals, const void* x, void* y, tg_stream stream);
 
 /* out[s] = alpha * lam[row(s)] * U[col(s)] for every CSR slot s: the adjoint
  * outer product dGamma/dK = lam U^T of Eq. (adj) on the pattern (DoF level
- * for elasticity).  lam, U [n_rows]; out [nnz]. */
+ * for elasticity).  lam, U [n_rows]; out [nnz].  A pattern with no entries
+ * does nothing. */
 tg_status tg_csr_outer(const tg_pattern* p, tg_dtype dtype, const void* lam, const void* U, double alpha, void* out,
                        tg_stream stream);
 

@@ -694,10 +694,12 @@ __global__ void __launch_bounds__(256) k_fma_rate(T* __restrict__ out, int iters
 extern "C" {
 
 tg_status tg_spmv(const tg_pattern* p, tg_dtype dtype, const void* vals, const void* x, void* y, tg_stream stream) {
-  if (!p || (dtype != TG_F32 && dtype != TG_F64) || !vals || !x || !y) return TG_ERR_INVALID_ARG;
+  if (!p || (dtype != TG_F32 && dtype != TG_F64)) return TG_ERR_INVALID_ARG;
   const int nc = tg::ncomp_of(p->el);
   const bool vec = nc > 1;
   const int64_t n = nc * p->N;
+  if (n == 0) return TG_OK;
+  if ((nc * nc * p->nnz > 0 && !vals) || !x || !y) return TG_ERR_INVALID_ARG;
   const int32_t* rp = vec ? p->row_ptr_dof : p->row_ptr;
   const int32_t* ci = vec ? p->col_idx_dof : p->col_idx;
   cudaStream_t s = (cudaStream_t)stream;
@@ -741,10 +743,12 @@ tg_status tg_cg_solve_noalloc(const tg_pattern* p, tg_dtype dtype, const void* v
 
 tg_status tg_csr_outer(const tg_pattern* p, tg_dtype dtype, const void* lam, const void* U, double alpha, void* out,
                        tg_stream stream) {
-  if (!p || (dtype != TG_F32 && dtype != TG_F64) || !lam || !U || !out) return TG_ERR_INVALID_ARG;
+  if (!p || (dtype != TG_F32 && dtype != TG_F64)) return TG_ERR_INVALID_ARG;
   const int nc = tg::ncomp_of(p->el);
   const bool vec = nc > 1;
   const int64_t n = nc * p->N;
+  if (nc * nc * p->nnz == 0) return TG_OK;  // no slot to write
+  if (!lam || !U || !out) return TG_ERR_INVALID_ARG;
   const int32_t* rp = vec ? p->row_ptr_dof : p->row_ptr;
   const int32_t* ci = vec ? p->col_idx_dof : p->col_idx;
   cudaStream_t s = (cudaStream_t)stream;
